@@ -1,0 +1,312 @@
+/*
+ * sph.h -- C ABI of libsph, the GB300 (sm_103a) implementation of the
+ * truncated-kernel SPH hot path of "An efficient truncation scheme for Eulerian
+ * and total Lagrangian SPH methods" (arXiv 2405.05155).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers: every array argument is a DEVICE pointer unless its name ends in
+ *   _host.  Arrays are structure-of-arrays, component-major: a vector field of
+ *   dimension d over n particles is stored as x[k*n + i], k < d.  The packed
+ *   FP32 records described below are array-of-records, 16-byte aligned.
+ * Ownership: the caller allocates and owns every argument array.  A context
+ *   (sph_ctx) owns only internal scratch (cell lists, scan buffers, flags),
+ *   grown on demand and freed by sph_destroy.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls enqueue work and return without waiting, except where a
+ *   comment says the call synchronises the stream (every call that returns a
+ *   value through a _host pointer does).
+ * Status: every entry point returns SPH_OK (0) or one of the SPH_ERR_* codes;
+ *   no call aborts, traps or prints.  sph_status_string() names a code and
+ *   sph_last_cuda_error() gives the CUDA error behind SPH_ERR_CUDA.
+ * Geometry: r_ij = r_i - r_j (minimum image on periodic axes: dx > L/2 -> dx-L,
+ *   dx < -L/2 -> dx+L), grad W_ij = (dW/dr) r_ij/|r_ij| (the gradient with
+ *   respect to r_i).  j is a neighbour of i when j != i and the float64
+ *   squared distance ((dx*dx)+dy*dy)+dz*dz, every operation rounded on its own,
+ *   is <= (kappa*h)*(kappa*h): the compact support of Eq. 5 (Sec. 2.2) with
+ *   cut-off 2h (standard) or 1.6h (truncated, Sec. 2.3.1).
+ * Symmetric 2x2 / 3x3 matrices are stored by their unique entries row by row:
+ *   2D (m00, m01, m11), 3D (m00, m01, m02, m11, m12, m22): nsym = 3 or 6.
+ * Full d x d matrices (F - I, stresses) are stored row-major: entry (a,b) is
+ *   component a*d + b.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SPH_OK            0
+#define SPH_ERR_ARG       1  /* bad argument: null pointer, dim not 2/3, n < 0, h <= 0,
+                                kappa not in (0,2], periodic box < 2 kappa h, bad enum,
+                                position not finite or outside a periodic box */
+#define SPH_ERR_CAPACITY  2  /* output array too small; the required size is returned */
+#define SPH_ERR_CUDA      3  /* a CUDA runtime call failed; see sph_last_cuda_error */
+#define SPH_ERR_TIMEOUT   4  /* a bounded device-side wait expired */
+#define SPH_ERR_NONFINITE 5  /* a reduction met a NaN or infinity */
+
+/* ---- enums ---- */
+#define SPH_WENDLAND_C2     0  /* Eq. 6; cut-off kappa*h, kappa = 2 or 1.6 */
+#define SPH_LAGUERRE_GAUSS  1  /* Eq. 8, normalised by ahat_d = 8/(7 sqrt(pi)),
+                                  6/(5 pi), 8/(7 pi^1.5); cut-off 2h */
+#define SPH_FP64            0  /* every operation in float64 */
+#define SPH_FP32_KAHAN      1  /* float32 pair loops with compensated (Kahan) sums */
+#define SPH_TWO_PASS        0  /* Eulerian step: momentum pass, then continuity pass */
+#define SPH_FUSED           1  /* Eulerian step: one forward-Euler pass */
+#define SPH_SVK             0  /* St Venant-Kirchhoff, Eq. 29 */
+#define SPH_NEO_HOOKEAN     1  /* compressible neo-Hookean S = G(I - C^-1) + lambda ln J C^-1 */
+
+#define SPH_MAX_SPHERES    16
+
+typedef struct sph_ctx sph_ctx;
+
+/* Particle set geometry.  dim 2 or 3; n particles; smoothing length h; cut-off
+ * factor kappa (support radius kappa*h); box [lo, lo+len) per axis, used for
+ * the cell grid (every axis) and the minimum image (axes whose bit is set in
+ * periodic_mask).  Cells: n_k = max(1, floor(len_k/(kappa h))) per axis of size
+ * len_k/n_k; particles outside the box of a non-periodic axis go to the edge
+ * cell.  On a periodic axis positions must lie in [lo, lo+len] and
+ * len >= 2 kappa h. */
+typedef struct {
+    int32_t  dim;
+    uint32_t periodic_mask;
+    int64_t  n;
+    double   h;
+    double   kappa;
+    double   lo[3];
+    double   len[3];
+} sph_domain;
+
+/* ---- context ---- */
+
+/* Create a context on CUDA device `device`; *ctx receives it.  Allocates no
+ * device memory until a call needs scratch. */
+int sph_create(sph_ctx** ctx, int device);
+/* Free the context and its scratch (synchronises the device). */
+int sph_destroy(sph_ctx* ctx);
+/* Static string naming a status code. */
+const char* sph_status_string(int status);
+/* The cudaError_t value of the most recent failed CUDA call in this context. */
+int sph_last_cuda_error(const sph_ctx* ctx);
+
+/* Launch shape of the float32 pair passes: `lanes` (1, 2, 4 or 8) consecutive
+ * lanes of a warp share one particle's neighbour row and combine their partial
+ * sums with shuffles.  pass: SPH_PASS_*.  Results of different shapes differ
+ * only by float32 rounding.  Defaults to 4.  sph_get_lanes returns the setting
+ * (or -1 on a bad argument).  Not part of the paper: a GPU launch parameter. */
+#define SPH_PASS_EULERIAN 0
+#define SPH_PASS_TLSPH    1
+#define SPH_PASS_RELAX    2
+int sph_set_lanes(sph_ctx* ctx, int pass, int lanes);
+int sph_get_lanes(const sph_ctx* ctx, int pass);
+
+/* Per-kernel device timing (not part of the paper: measurement support).
+ * sph_timing_enable(ctx, 1) clears the counters and makes the step entry points
+ * record a CUDA event pair around every kernel launch they make, on the launch
+ * stream; sph_timing_enable(ctx, 0) stops recording.  sph_timing_read
+ * synchronises on the recorded events and returns, for one SPH_TIMER_* slot,
+ * the summed device time in milliseconds and the number of launches. */
+#define SPH_TIMER_TL_STRESS    0
+#define SPH_TIMER_TL_MOMENTUM  1
+#define SPH_TIMER_TL_DEFORM    2
+#define SPH_TIMER_EU_MOMENTUM  3
+#define SPH_TIMER_EU_MASS      4
+#define SPH_TIMER_EU_FUSED     5
+#define SPH_TIMER_NEIGHBORS    6
+#define SPH_TIMER_RELAX_ACCEL  7
+#define SPH_TIMER_RELAX_UPDATE 8
+#define SPH_TIMER_SLOTS        16
+int sph_timing_enable(sph_ctx* ctx, int on);
+int sph_timing_read(sph_ctx* ctx, int slot, double* total_ms_host, int64_t* launches_host);
+
+/* ---- a3: kernel values and radial derivatives ----
+ * Eq. 6 (Wendland C2, Sec. 2.3.1) or Eq. 8 (Laguerre-Gauss, Sec. 2.3.2).
+ * For n distances r[i] >= 0 writes w[i] = W(r) and dwdr[i] = dW/dr, computed in
+ * `precision` (results widened to float64), with the cut at q = r/h <= kappa
+ * (values beyond are 0).  w or dwdr may be NULL. */
+int sph_kernel_eval(int kernel, int dim, double h, double kappa, int precision,
+                    const double* r, double* w, double* dwdr, int64_t n, void* stream);
+
+/* ---- a1: cell binning and order ----
+ * Permutation order[k] (int64, length n) sorting the particles by
+ * (linear cell id, original index), stable.  Linear cell id
+ * (c_z n_y + c_y) n_x + c_x with c_k = floor((x_k - lo_k)/size_k), wrapped on
+ * periodic axes and clamped otherwise.  pos: float64 [dim][n].
+ * Synchronises the stream (to validate positions). */
+int sph_cell_order(sph_ctx* ctx, const sph_domain* dom, const double* pos,
+                   int64_t* order, void* stream);
+
+/* ---- a2: CSR neighbour lists ----
+ * Compact-support neighbour sets of Eq. 5 with cut-off kappa*h: row i holds
+ * every j != i with float64 d^2 <= (kappa h)^2 (see the header comment), sorted
+ * ascending.  pos float64 [dim][n]; row_ptr int64 [n+1]; col int32 [cap].
+ * *nnz_host receives row_ptr[n].  If cap < nnz nothing is written to col and
+ * SPH_ERR_CAPACITY is returned with *nnz_host = the required capacity
+ * (row_ptr is valid).  Synchronises the stream.  Bit-exact with the float64
+ * definition: candidates are screened in float32 with a proven error band and
+ * every candidate inside the band is decided in float64. */
+int sph_build_neighbors(sph_ctx* ctx, const sph_domain* dom, const double* pos,
+                        int64_t* row_ptr, int32_t* col, int64_t cap,
+                        int64_t* nnz_host, void* stream);
+
+/* ---- a4: kernel gradient correction ----
+ * Eq. 9 (Sec. 2.3.2): A_i = -sum_j V_j r_ij (x) grad W_ij over the CSR row,
+ * B_i = A_i^-1 (adjugate formula), all float64, kernel `kernel` with the cut-off
+ * of dom->kappa.  B: float64 [nsym][n].  A particle whose A_i is not finite, has
+ * trace <= 0 or det A <= 1e-8 (tr A/d)^d gets B_i = I and fallback[i] = 1
+ * (else 0); fallback may be NULL.  If n_fallback_host is not NULL it receives
+ * the number of such particles and the call synchronises the stream. */
+int sph_kgc(sph_ctx* ctx, const sph_domain* dom, int kernel, const double* pos,
+            const double* vol, const int64_t* row_ptr, const int32_t* col,
+            double* B, uint8_t* fallback, int64_t* n_fallback_host, void* stream);
+
+/* ---- a5/a6: Eulerian weakly-compressible SPH (Sec. 3.1) ----
+ * Fixed particles with volume V_i, density rho0 + drho_i, velocity v_i and
+ * pressure p = c0^2 drho (Sec. 3.1.1).  Rates (Eq. 18 divided by w_i):
+ *   d rho_i/dt      = -2 sum_j V_j rho* (v* . g)
+ *   d (rho v)_i/dt  = -2 sum_j V_j [rho* v* (v* . g) + p* g]
+ *                     + 2 mu sum_j V_j (v_i - v_j)(r_ij . grad W_ij)/(r^2 + 0.01 h^2)
+ * with g = (B_i + B_j)/2 grad W_ij (Eq. 27, Wendland with cut-off dom.kappa),
+ * normal n = -r_ij/r, u_l = v_i.n, u_r = v_j.n, rho* = (rho_i+rho_j)/2,
+ * beta = min(eta max((u_l-u_r)/c0, 0), 1), u* = (u_l+u_r)/2 + beta^2 (p_i-p_j)/(2 rho* c0),
+ * p* = (p_i+p_j)/2 + beta rho* c0 (u_l-u_r)/2 (Eqs. 25-26), v* = (v_i+v_j)/2 + (u* - (u_l+u_r)/2) n.
+ * Time step (integrator SPH_TWO_PASS): momentum pass from (rho^n, v^n) gives
+ * (rho v)^{n+1} and v' = (rho v)^{n+1}/rho^n; continuity pass from (rho^n, v')
+ * gives rho^{n+1}; v^{n+1} = (rho v)^{n+1}/rho^{n+1}.  SPH_FUSED evaluates both
+ * rates at (rho^n, v^n). */
+typedef struct {
+    sph_domain dom;
+    double dt, rho0, c0, mu, eta;   /* eta = 15 in the paper (Eq. 26) */
+    int32_t precision;              /* SPH_FP64 or SPH_FP32_KAHAN */
+    int32_t integrator;             /* SPH_TWO_PASS or SPH_FUSED */
+} sph_eulerian_params;
+
+/* State arrays.  FP64 steps use pos/vol/B/drho/v and the drho_tmp/v_tmp
+ * scratch (same shapes as drho/v).  FP32 steps use the packed records, made by
+ * sph_eulerian_pack from the FP64 arrays and read back by sph_eulerian_unpack:
+ *   geo  [n][8] (2D): (xh, yh, xl, yl), (V, B00, B01, B11)
+ *        [n][16] (3D): (xh, yh, zh, V), (xl, yl, zl, B00), (B01, B02, B11, B12), (B22, 0, 0, 0)
+ *        where x = xh + xl is the float64 position split into two floats;
+ *   q, q_tmp [n][4]: (v0, v1, drho, 0) in 2D, (v0, v1, v2, drho) in 3D. */
+typedef struct {
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const double*  pos;
+    const double*  vol;
+    const double*  B;
+    double* drho;
+    double* v;
+    double* drho_tmp;
+    double* v_tmp;
+    float*  geo;
+    float*  q;
+    float*  q_tmp;
+} sph_eulerian_state;
+
+/* float64 (pos, vol, B, drho, v) -> packed float32 (geo, q). */
+int sph_eulerian_pack(sph_ctx* ctx, const sph_eulerian_params* prm,
+                      const sph_eulerian_state* st, void* stream);
+/* packed float32 q -> float64 (drho, v). */
+int sph_eulerian_unpack(sph_ctx* ctx, const sph_eulerian_params* prm,
+                        const sph_eulerian_state* st, void* stream);
+/* Both rates at the current state (FP64 arrays or, for FP32, the packed q):
+ * drho_dt float64 [n], dmom_dt float64 [dim][n]. */
+int sph_eulerian_rates(sph_ctx* ctx, const sph_eulerian_params* prm,
+                       const sph_eulerian_state* st, double* drho_dt,
+                       double* dmom_dt, void* stream);
+/* Advance nsteps time steps in place (drho/v for FP64, q for FP32). */
+int sph_eulerian_step(sph_ctx* ctx, const sph_eulerian_params* prm,
+                      const sph_eulerian_state* st, int nsteps, void* stream);
+
+/* ---- a7-a9: total-Lagrangian SPH for solids (Sec. 3.2) ----
+ * Reference configuration r0 with volumes V0, correction B0 (Eq. 9 at r0) and
+ * the CSR lists built at r0.  Per step: M_i = P(F_i) B0_i^T with P = F S
+ * (Eq. 29 or neo-Hookean), a_i = (1/rho0) sum_j (M_i + M_j) grad0 W_ij V0_j
+ * (Eq. 30), v += dt a, dF_i/dt = (sum_j V0_j (v_j - v_i) (x) grad0 W_ij) B0_i
+ * (Eq. 31), F += dt dF/dt, x += dt v.  Clamped particles (fixed[i] != 0) keep
+ * v = 0 and F = I. */
+typedef struct {
+    sph_domain dom;                 /* geometry of r0 (h, kappa, box) */
+    double dt, rho0, lambda, G;
+    int32_t law;                    /* SPH_SVK or SPH_NEO_HOOKEAN */
+    int32_t precision;              /* SPH_FP64 or SPH_FP32_KAHAN */
+} sph_tlsph_params;
+
+/* FP64 arrays: x, v [dim][n]; H = F - I [dim*dim][n]; M scratch [dim*dim][n].
+ * FP32 packed arrays (made by sph_tlsph_pack):
+ *   geo [n][8]: 3D (xh, yh, zh, V0), (xl, yl, zl, fixed); 2D (xh, yh, xl, yl), (V0, fixed, 0, 0)
+ *   vq  [n][4]: (v0, v1, v2 or 0, 0)
+ *   H32 [dim*dim][n], u32 [dim][n] (x - r0), B32 [nsym][n]
+ *   M32 [n][12] (3D: rows of M padded to 4) or [n][4] (2D). */
+typedef struct {
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const double*  r0;
+    const double*  V0;
+    const double*  B0;
+    const uint8_t* fixed;
+    double* x;
+    double* v;
+    double* H;
+    double* M;
+    float*  geo;
+    float*  vq;
+    float*  H32;
+    float*  u32;
+    float*  M32;
+    float*  B32;
+} sph_tlsph_state;
+
+int sph_tlsph_pack(sph_ctx* ctx, const sph_tlsph_params* prm,
+                   const sph_tlsph_state* st, void* stream);
+/* packed float32 (vq, H32, u32) -> float64 (v, H, x = r0 + u). */
+int sph_tlsph_unpack(sph_ctx* ctx, const sph_tlsph_params* prm,
+                     const sph_tlsph_state* st, void* stream);
+/* Rates at the current state: dvdt float64 [dim][n] (Eq. 30 / rho0) and
+ * dFdt float64 [dim*dim][n] (Eq. 31 with the current v). */
+int sph_tlsph_rates(sph_ctx* ctx, const sph_tlsph_params* prm,
+                    const sph_tlsph_state* st, double* dvdt, double* dFdt, void* stream);
+int sph_tlsph_step(sph_ctx* ctx, const sph_tlsph_params* prm,
+                   const sph_tlsph_state* st, int nsteps, void* stream);
+
+/* ---- a10/a11: Laguerre-Gauss particle relaxation (Sec. 2.3.2, Eqs. 7-8) ----
+ * 3D only.  Body = union of n_spheres spheres (cx, cy, cz, r) given by value,
+ * signed distance phi = min_k(|x-c_k| - r_k), normal grad phi of the first
+ * minimising sphere.  Per step: neighbour sets (cut-off 2h) from the current
+ * positions; a_i = -(2 p0/rho)(sum_j grad W^LG_ij V_j + I(max(-phi_i,0)) grad phi_i)
+ * with the half-space surface integral I(d) = 2 pi int_d^{2h} z (W(z) - W(2h)) dz;
+ * dt = 0.25 sqrt(h / max|a|); x += a dt^2/2; then particles with
+ * phi > -dp/2 are moved along grad phi to phi = -dp/2. */
+typedef struct {
+    sph_domain dom;                 /* dim 3, h, kappa = 2, cell box */
+    double dp, p0, rho;
+    int32_t kernel;                 /* SPH_LAGUERRE_GAUSS */
+    int32_t precision;              /* SPH_FP64 or SPH_FP32_KAHAN (pair sums) */
+    int32_t n_spheres;              /* 1..SPH_MAX_SPHERES */
+    int32_t reserved;
+    double spheres[4 * SPH_MAX_SPHERES];
+} sph_relax_params;
+
+/* Advance nsteps relaxation steps of pos (float64 [3][n], in place). */
+int sph_relax_step(sph_ctx* ctx, const sph_relax_params* prm, double* pos,
+                   const double* vol, int nsteps, void* stream);
+/* Acceleration a (float64 [3][n]) at the current positions (one neighbour
+ * build + pair pass). */
+int sph_relax_accel(sph_ctx* ctx, const sph_relax_params* prm, const double* pos,
+                    const double* vol, double* acc, void* stream);
+/* Relaxation residual over particles with phi < -2h:
+ * out_host[0] = sqrt(mean |h sum_j grad W^LG_ij V_j|^2),
+ * out_host[1] = the same with the truncated Wendland kernel (cut-off 1.6h),
+ * out_host[2] = number of such particles.  Float64, deterministic.
+ * Synchronises the stream. */
+int sph_relax_residual(sph_ctx* ctx, const sph_relax_params* prm, const double* pos,
+                       const double* vol, double* out_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_H */

@@ -1,0 +1,118 @@
+"""ctypes declarations of the libsph C ABI (include/sph.h).
+
+Argument marshalling only: every computation runs in libsph's CUDA kernels.
+The library is loaded on first use; a missing build raises immediately (there
+is no fallback path).
+"""
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "lib", "libsph.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "sph.h")
+
+SPH_OK, SPH_ERR_ARG, SPH_ERR_CAPACITY, SPH_ERR_CUDA, SPH_ERR_TIMEOUT, SPH_ERR_NONFINITE = range(6)
+SPH_WENDLAND_C2, SPH_LAGUERRE_GAUSS = 0, 1
+SPH_FP64, SPH_FP32_KAHAN = 0, 1
+SPH_TWO_PASS, SPH_FUSED = 0, 1
+SPH_SVK, SPH_NEO_HOOKEAN = 0, 1
+SPH_PASS_EULERIAN, SPH_PASS_TLSPH, SPH_PASS_RELAX = 0, 1, 2
+SPH_MAX_SPHERES = 16
+(SPH_TIMER_TL_STRESS, SPH_TIMER_TL_MOMENTUM, SPH_TIMER_TL_DEFORM, SPH_TIMER_EU_MOMENTUM, SPH_TIMER_EU_MASS,
+ SPH_TIMER_EU_FUSED, SPH_TIMER_NEIGHBORS, SPH_TIMER_RELAX_ACCEL, SPH_TIMER_RELAX_UPDATE) = range(9)
+
+c_i32, c_i64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+
+class SphDomain(ctypes.Structure):
+    _fields_ = [("dim", c_i32), ("periodic_mask", ctypes.c_uint32), ("n", c_i64), ("h", c_dbl),
+                ("kappa", c_dbl), ("lo", c_dbl * 3), ("len", c_dbl * 3)]
+
+
+class EulerianParams(ctypes.Structure):
+    _fields_ = [("dom", SphDomain), ("dt", c_dbl), ("rho0", c_dbl), ("c0", c_dbl), ("mu", c_dbl),
+                ("eta", c_dbl), ("precision", c_i32), ("integrator", c_i32)]
+
+
+class EulerianState(ctypes.Structure):
+    _fields_ = [(name, c_vp) for name in ("row_ptr", "col", "pos", "vol", "B", "drho", "v", "drho_tmp",
+                                          "v_tmp", "geo", "q", "q_tmp")]
+
+
+class TLParams(ctypes.Structure):
+    _fields_ = [("dom", SphDomain), ("dt", c_dbl), ("rho0", c_dbl), ("lam", c_dbl), ("G", c_dbl),
+                ("law", c_i32), ("precision", c_i32)]
+
+
+class TLState(ctypes.Structure):
+    _fields_ = [(name, c_vp) for name in ("row_ptr", "col", "r0", "V0", "B0", "fixed", "x", "v", "H", "M",
+                                          "geo", "vq", "H32", "u32", "M32", "B32")]
+
+
+class RelaxParams(ctypes.Structure):
+    _fields_ = [("dom", SphDomain), ("dp", c_dbl), ("p0", c_dbl), ("rho", c_dbl), ("kernel", c_i32),
+                ("precision", c_i32), ("n_spheres", c_i32), ("reserved", c_i32),
+                ("spheres", c_dbl * (4 * SPH_MAX_SPHERES))]
+
+
+_P = ctypes.POINTER
+_SIGNATURES = {
+    "sph_create": (ctypes.c_int, [_P(c_vp), ctypes.c_int]),
+    "sph_destroy": (ctypes.c_int, [c_vp]),
+    "sph_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "sph_last_cuda_error": (ctypes.c_int, [c_vp]),
+    "sph_set_lanes": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int]),
+    "sph_get_lanes": (ctypes.c_int, [c_vp, ctypes.c_int]),
+    "sph_timing_enable": (ctypes.c_int, [c_vp, ctypes.c_int]),
+    "sph_timing_read": (ctypes.c_int, [c_vp, ctypes.c_int, _P(c_dbl), _P(c_i64)]),
+    "sph_kernel_eval": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_dbl, c_dbl, ctypes.c_int, c_vp, c_vp, c_vp,
+                                       c_i64, c_vp]),
+    "sph_cell_order": (ctypes.c_int, [c_vp, _P(SphDomain), c_vp, c_vp, c_vp]),
+    "sph_build_neighbors": (ctypes.c_int, [c_vp, _P(SphDomain), c_vp, c_vp, c_vp, c_i64, _P(c_i64), c_vp]),
+    "sph_kgc": (ctypes.c_int, [c_vp, _P(SphDomain), ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, _P(c_i64),
+                               c_vp]),
+    "sph_eulerian_pack": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), c_vp]),
+    "sph_eulerian_unpack": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), c_vp]),
+    "sph_eulerian_rates": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), c_vp, c_vp, c_vp]),
+    "sph_eulerian_step": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), ctypes.c_int, c_vp]),
+    "sph_tlsph_pack": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp]),
+    "sph_tlsph_unpack": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp]),
+    "sph_tlsph_rates": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp, c_vp, c_vp]),
+    "sph_tlsph_step": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), ctypes.c_int, c_vp]),
+    "sph_relax_step": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, ctypes.c_int, c_vp]),
+    "sph_relax_accel": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, c_vp, c_vp]),
+    "sph_relax_residual": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, _P(c_dbl), c_vp]),
+}
+
+_lib = None
+
+
+class SphError(RuntimeError):
+    def __init__(self, name, status, cuda_error=0):
+        self.status = status
+        msg = "%s failed: %s" % (name, _lib.sph_status_string(status).decode() if _lib else status)
+        if status == SPH_ERR_CUDA:
+            msg += " (cudaError %d)" % cuda_error
+        super().__init__(msg)
+
+
+def load():
+    """Load libsph.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libsph.so is not built (%s); run __graft_entry__.build() first" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(name, status, ctx=None):
+    if status != SPH_OK:
+        err = _lib.sph_last_cuda_error(ctx) if (ctx and status == SPH_ERR_CUDA) else 0
+        raise SphError(name, status, err)

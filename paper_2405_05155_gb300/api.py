@@ -1,0 +1,291 @@
+"""Python binding of libsph: argument marshalling over the C ABI of include/sph.h.
+
+PyTorch provides device memory and the current CUDA stream; every step of the
+SPH path runs in libsph's kernels.  Names follow the C entry points.
+"""
+import ctypes
+
+import torch
+
+from . import _lib as L
+from ._lib import (SPH_FP32_KAHAN, SPH_FP64, SPH_FUSED, SPH_LAGUERRE_GAUSS,  # noqa: F401
+                   SPH_NEO_HOOKEAN, SPH_SVK, SPH_TWO_PASS, SPH_WENDLAND_C2, SPH_PASS_EULERIAN,
+                   SPH_PASS_RELAX, SPH_PASS_TLSPH)
+
+NSYM = {2: 3, 3: 6}
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev_f64(x, device):
+    return torch.as_tensor(x, dtype=torch.float64, device=device).contiguous()
+
+
+def make_domain(dom, n):
+    """sph_domain from the plain-dict description used by ``inputs``."""
+    d = L.SphDomain()
+    d.dim = dom["dim"]
+    d.periodic_mask = sum((1 << k) for k, p in enumerate(dom["periodic"][: dom["dim"]]) if p)
+    d.n = int(n)
+    d.h = dom["h"]
+    d.kappa = dom["kappa"]
+    for k in range(3):
+        d.lo[k] = dom["lo"][k] if k < dom["dim"] else 0.0
+        d.len[k] = dom["len"][k] if k < dom["dim"] else 1.0
+    return d
+
+
+class Context:
+    """Owns an sph_ctx (scratch arena and launch settings) on one CUDA device."""
+
+    def __init__(self, device=0):
+        self.lib = L.load()
+        self.device = torch.device("cuda", device)
+        h = ctypes.c_void_p()
+        L.check("sph_create", self.lib.sph_create(ctypes.byref(h), device))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.lib.sph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_lanes(self, which, lanes):
+        L.check("sph_set_lanes", self.lib.sph_set_lanes(self.h, which, lanes), self.h)
+
+    def get_lanes(self, which):
+        return self.lib.sph_get_lanes(self.h, which)
+
+    def timing(self, on):
+        """Start (clearing the counters) or stop per-kernel event timing."""
+        L.check("sph_timing_enable", self.lib.sph_timing_enable(self.h, 1 if on else 0), self.h)
+
+    def timer(self, slot):
+        """(total device milliseconds, launches) recorded for one SPH_TIMER_* slot."""
+        ms = ctypes.c_double()
+        cnt = ctypes.c_int64()
+        L.check("sph_timing_read", self.lib.sph_timing_read(self.h, slot, ctypes.byref(ms), ctypes.byref(cnt)),
+                self.h)
+        return ms.value, cnt.value
+
+
+def kernel_eval(kernel, dim, h, kappa, precision, r):
+    lib = L.load()
+    r = r.contiguous()
+    w = torch.empty_like(r)
+    dw = torch.empty_like(r)
+    L.check("sph_kernel_eval", lib.sph_kernel_eval(kernel, dim, h, kappa, precision, _p(r), _p(w), _p(dw),
+                                                     r.numel(), _stream()))
+    return w, dw
+
+
+def cell_order(ctx, dom, pos):
+    n = pos.shape[1]
+    d = make_domain(dom, n)
+    order = torch.empty(n, dtype=torch.int64, device=pos.device)
+    L.check("sph_cell_order", ctx.lib.sph_cell_order(ctx.h, ctypes.byref(d), _p(pos), _p(order), _stream()), ctx.h)
+    return order
+
+
+def build_neighbors(ctx, dom, pos, cap=None):
+    """CSR (row_ptr int64 [n+1], col int32 [nnz]) of the compact-support neighbour sets."""
+    n = pos.shape[1]
+    d = make_domain(dom, n)
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=pos.device)
+    if cap is None:
+        cap = max(16, n * (24 if dom["dim"] == 2 else 96))
+    for _ in range(2):
+        col = torch.empty(max(cap, 1), dtype=torch.int32, device=pos.device)
+        nnz = ctypes.c_int64(0)
+        st = ctx.lib.sph_build_neighbors(ctx.h, ctypes.byref(d), _p(pos), _p(row_ptr), _p(col), cap,
+                                         ctypes.byref(nnz), _stream())
+        if st == L.SPH_ERR_CAPACITY:
+            cap = nnz.value
+            continue
+        L.check("sph_build_neighbors", st, ctx.h)
+        return row_ptr, col[: nnz.value]
+    raise RuntimeError("sph_build_neighbors: capacity retry failed")
+
+
+def kgc(ctx, dom, pos, vol, row_ptr, col, kernel=SPH_WENDLAND_C2):
+    n = pos.shape[1]
+    d = make_domain(dom, n)
+    B = torch.empty((NSYM[dom["dim"]], n), dtype=torch.float64, device=pos.device)
+    fb = torch.empty(n, dtype=torch.uint8, device=pos.device)
+    nfb = ctypes.c_int64(0)
+    L.check("sph_kgc", ctx.lib.sph_kgc(ctx.h, ctypes.byref(d), kernel, _p(pos), _p(vol), _p(row_ptr), _p(col),
+                                        _p(B), _p(fb), ctypes.byref(nfb), _stream()), ctx.h)
+    return B, fb, nfb.value
+
+
+class Eulerian:
+    """Eulerian WCSPH state on the device (float64 arrays and, for float32 steps, packed records)."""
+
+    def __init__(self, ctx, dom, pos, vol, B, row_ptr, col, drho, v, dt, rho0, c0, mu, eta=15.0,
+                 precision=SPH_FP64, integrator=SPH_TWO_PASS):
+        self.ctx = ctx
+        dev = ctx.device
+        self.n = pos.shape[1]
+        self.dim = dom["dim"]
+        self.prm = L.EulerianParams()
+        self.prm.dom = make_domain(dom, self.n)
+        self.prm.dt, self.prm.rho0, self.prm.c0, self.prm.mu, self.prm.eta = dt, rho0, c0, mu, eta
+        self.prm.precision = precision
+        self.prm.integrator = integrator
+        self.pos = _dev_f64(pos, dev)
+        self.vol = _dev_f64(vol, dev)
+        self.B = _dev_f64(B, dev)
+        self.row_ptr = row_ptr
+        self.col = col
+        self.drho = _dev_f64(drho, dev).clone()
+        self.v = _dev_f64(v, dev).clone()
+        self.drho_tmp = torch.empty_like(self.drho)
+        self.v_tmp = torch.empty_like(self.v)
+        words = 8 if self.dim == 2 else 16
+        self.geo = torch.zeros(self.n * words, dtype=torch.float32, device=dev)
+        self.q = torch.zeros(self.n * 4, dtype=torch.float32, device=dev)
+        self.q_tmp = torch.zeros(self.n * 4, dtype=torch.float32, device=dev)
+        self.st = L.EulerianState()
+        for name in ("row_ptr", "col", "pos", "vol", "B", "drho", "v", "drho_tmp", "v_tmp", "geo", "q", "q_tmp"):
+            setattr(self.st, name, getattr(self, name).data_ptr())
+        if precision == SPH_FP32_KAHAN:
+            self.pack()
+
+    def _call(self, name, *args):
+        fn = getattr(self.ctx.lib, name)
+        L.check(name, fn(self.ctx.h, ctypes.byref(self.prm), ctypes.byref(self.st), *args), self.ctx.h)
+
+    def pack(self):
+        self._call("sph_eulerian_pack", _stream())
+
+    def unpack(self):
+        self._call("sph_eulerian_unpack", _stream())
+
+    def step(self, nsteps=1):
+        self._call("sph_eulerian_step", int(nsteps), _stream())
+
+    def rates(self):
+        drho_dt = torch.empty(self.n, dtype=torch.float64, device=self.ctx.device)
+        dmom_dt = torch.empty((self.dim, self.n), dtype=torch.float64, device=self.ctx.device)
+        self._call("sph_eulerian_rates", _p(drho_dt), _p(dmom_dt), _stream())
+        return drho_dt, dmom_dt
+
+    def fields(self):
+        """(drho, v) as float64 device tensors (unpacked for float32 runs)."""
+        if self.prm.precision == SPH_FP32_KAHAN:
+            self.unpack()
+        return self.drho, self.v
+
+
+class TLSolid:
+    """Total-Lagrangian solid state on the device."""
+
+    def __init__(self, ctx, dom, r0, V0, B0, fixed, row_ptr, col, v, dt, rho0, lam, G, law=SPH_NEO_HOOKEAN,
+                 precision=SPH_FP64, x=None, H=None):
+        self.ctx = ctx
+        dev = ctx.device
+        self.n = r0.shape[1]
+        self.dim = dom["dim"]
+        d = self.dim
+        self.prm = L.TLParams()
+        self.prm.dom = make_domain(dom, self.n)
+        self.prm.dt, self.prm.rho0, self.prm.lam, self.prm.G = dt, rho0, lam, G
+        self.prm.law = law
+        self.prm.precision = precision
+        self.r0 = _dev_f64(r0, dev)
+        self.V0 = _dev_f64(V0, dev)
+        self.B0 = _dev_f64(B0, dev)
+        self.fixed = torch.as_tensor(fixed, dtype=torch.uint8, device=dev).contiguous()
+        self.row_ptr, self.col = row_ptr, col
+        self.x = (self.r0.clone() if x is None else _dev_f64(x, dev).clone())
+        self.v = _dev_f64(v, dev).clone()
+        self.H = (torch.zeros((d * d, self.n), dtype=torch.float64, device=dev) if H is None
+                  else _dev_f64(H, dev).clone())
+        self.M = torch.zeros((d * d, self.n), dtype=torch.float64, device=dev)
+        self.geo = torch.zeros(self.n * 8, dtype=torch.float32, device=dev)
+        self.vq = torch.zeros(self.n * 4, dtype=torch.float32, device=dev)
+        self.H32 = torch.zeros(d * d * self.n, dtype=torch.float32, device=dev)
+        self.u32 = torch.zeros(d * self.n, dtype=torch.float32, device=dev)
+        self.M32 = torch.zeros(self.n * (12 if d == 3 else 4), dtype=torch.float32, device=dev)
+        self.B32 = torch.zeros(NSYM[d] * self.n, dtype=torch.float32, device=dev)
+        self.st = L.TLState()
+        for name in ("row_ptr", "col", "r0", "V0", "B0", "fixed", "x", "v", "H", "M", "geo", "vq", "H32", "u32",
+                     "M32", "B32"):
+            setattr(self.st, name, getattr(self, name).data_ptr())
+        if precision == SPH_FP32_KAHAN:
+            self.pack()
+
+    def _call(self, name, *args):
+        fn = getattr(self.ctx.lib, name)
+        L.check(name, fn(self.ctx.h, ctypes.byref(self.prm), ctypes.byref(self.st), *args), self.ctx.h)
+
+    def pack(self):
+        self._call("sph_tlsph_pack", _stream())
+
+    def unpack(self):
+        self._call("sph_tlsph_unpack", _stream())
+
+    def step(self, nsteps=1):
+        self._call("sph_tlsph_step", int(nsteps), _stream())
+
+    def rates(self):
+        d = self.dim
+        dvdt = torch.empty((d, self.n), dtype=torch.float64, device=self.ctx.device)
+        dFdt = torch.empty((d * d, self.n), dtype=torch.float64, device=self.ctx.device)
+        self._call("sph_tlsph_rates", _p(dvdt), _p(dFdt), _stream())
+        return dvdt, dFdt
+
+    def fields(self):
+        """(x, v, H = F - I) as float64 device tensors."""
+        if self.prm.precision == SPH_FP32_KAHAN:
+            self.unpack()
+        return self.x, self.v, self.H
+
+
+def relax_params(dom, spheres, dp, precision=SPH_FP32_KAHAN, p0=1.0, rho=1.0, n=0):
+    prm = L.RelaxParams()
+    prm.dom = make_domain(dom, n)
+    prm.dp, prm.p0, prm.rho = dp, p0, rho
+    prm.kernel = SPH_LAGUERRE_GAUSS
+    prm.precision = precision
+    prm.n_spheres = len(spheres)
+    for k, s in enumerate(spheres):
+        for c in range(4):
+            prm.spheres[4 * k + c] = float(s[c])
+    return prm
+
+
+def relax_step(ctx, prm, pos, vol, nsteps=1):
+    """Advance ``nsteps`` relaxation steps of pos (float64 [3][n] device tensor, in place)."""
+    prm.dom.n = pos.shape[1]
+    L.check("sph_relax_step", ctx.lib.sph_relax_step(ctx.h, ctypes.byref(prm), _p(pos), _p(vol), int(nsteps),
+                                                      _stream()), ctx.h)
+    return pos
+
+
+def relax_accel(ctx, prm, pos, vol):
+    prm.dom.n = pos.shape[1]
+    acc = torch.empty_like(pos)
+    L.check("sph_relax_accel", ctx.lib.sph_relax_accel(ctx.h, ctypes.byref(prm), _p(pos), _p(vol), _p(acc),
+                                                        _stream()), ctx.h)
+    return acc
+
+
+def relax_residual(ctx, prm, pos, vol):
+    prm.dom.n = pos.shape[1]
+    out = (ctypes.c_double * 3)()
+    L.check("sph_relax_residual", ctx.lib.sph_relax_residual(ctx.h, ctypes.byref(prm), _p(pos), _p(vol), out,
+                                                              _stream()), ctx.h)
+    return out[0], out[1], int(out[2])

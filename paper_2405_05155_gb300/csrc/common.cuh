@@ -1,0 +1,159 @@
+// Shared device helpers of libsph: context, error plumbing, kernel functions,
+// minimum image, compensated sums and a device-wide exclusive scan.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+#include <vector>
+
+#include "sph.h"
+
+struct TimerRec {
+    int slot;
+    cudaEvent_t start, stop;
+};
+
+struct sph_ctx {
+    // per-kernel timing (sph_timing_enable): events recorded around launches
+    bool timing = false;
+    std::vector<TimerRec> pending;
+    std::vector<cudaEvent_t> pool;
+    double t_ms[SPH_TIMER_SLOTS] = {};
+    long long t_n[SPH_TIMER_SLOTS] = {};
+    int device = 0;
+    int last_cuda_error = 0;
+    int num_sms = 0;
+    static const int kSlots = 24;
+    void* slot_ptr[kSlots] = {};
+    size_t slot_bytes[kSlots] = {};
+    int* flags = nullptr;          // device status words (see FLAG_*)
+    void* pinned = nullptr;        // small pinned host buffer for read-backs
+    int lanes[4] = {4, 4, 4, 4};   // lanes per particle of the float32 pair passes (SPH_PASS_*)
+};
+
+// scratch slots (each is a grow-only device buffer owned by the context)
+enum ScratchSlot {
+    S_CELL_ID = 0, S_CELL_COUNT, S_CELL_START, S_CELL_FILL, S_SORTED, S_P32SORTED,
+    S_ROW_LEN, S_SCAN_BLOCKS, S_ABSMAX, S_RELAX_ROWPTR, S_RELAX_COL, S_RELAX_ACC,
+    S_RELAX_AMAX, S_RED_PARTIAL, S_KGC_COUNT, S_MISC0, S_MISC1
+};
+
+// device status words
+enum { FLAG_BAD_INPUT = 0, FLAG_NONFINITE = 1, FLAG_CAPACITY = 2, FLAG_COUNT = 8 };
+
+#define SPH_CUDA(ctx, call)                                                     \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess) {                                                \
+            if (ctx) (ctx)->last_cuda_error = (int)e_;                          \
+            return SPH_ERR_CUDA;                                                \
+        }                                                                       \
+    } while (0)
+
+#define SPH_LAUNCH_CHECK(ctx) SPH_CUDA(ctx, cudaGetLastError())
+
+// Per-kernel timing: returns a token for sph_timer_end (or -1 when timing is off).
+int sph_timer_begin(sph_ctx* ctx, int slot, cudaStream_t s);
+void sph_timer_end(sph_ctx* ctx, int token, cudaStream_t s);
+
+// Returns a device buffer of at least `bytes` for `slot` (grown, never shrunk).
+void* sph_scratch(sph_ctx* ctx, int slot, size_t bytes, int* status);
+
+static inline cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+// Host-side domain validation shared by every entry point.
+int sph_check_domain(const sph_domain* dom);
+
+// ---------------------------------------------------------------------------
+// Cell grid (host side, float64, identical arithmetic to the definition)
+struct CellGrid {
+    int dim;
+    int n[3];
+    double size[3];
+    double lo[3];
+    double len[3];
+    double half[3];
+    uint32_t periodic;
+    int64_t total;
+    double rc2;          // (kappa h)^2
+};
+CellGrid sph_make_grid(const sph_domain* dom);
+
+// ---------------------------------------------------------------------------
+// Kernel functions.  Both return the factor gs with grad W_ij = gs * r_ij,
+// i.e. gs = (dW/dr)/r, written without a division by r:
+//   Wendland C2 (Eq. 6): gs = -5 alpha_d h^-(d+2) (1 - q/2)^3
+//   Laguerre-Gauss (Eq. 8): gs = -(ahat_d h^-(d+2)/3) e^{-q^2} (9 - 5 q^2 + q^4)
+#define SPH_PI 3.14159265358979323846
+
+static inline double wendland_alpha(int dim) {
+    return dim == 2 ? 7.0 / (4.0 * SPH_PI) : (dim == 3 ? 21.0 / (16.0 * SPH_PI) : 0.75);
+}
+static inline double lg_alpha(int dim) {
+    return dim == 2 ? 6.0 / (5.0 * SPH_PI)
+                    : (dim == 3 ? 8.0 / (7.0 * pow(SPH_PI, 1.5)) : 8.0 / (7.0 * sqrt(SPH_PI)));
+}
+
+template <typename R>
+__device__ __forceinline__ R wendland_gs(R q, R coef) {   // coef = -5 alpha h^-(d+2)
+    R t = R(1) - R(0.5) * q;
+    return coef * t * t * t;
+}
+template <typename R>
+__device__ __forceinline__ R lg_gs(R q, R coef) {          // coef = -ahat h^-(d+2) / 3
+    R q2 = q * q;
+    return coef * exp(-q2) * (R(9) - R(5) * q2 + q2 * q2);
+}
+template <>
+__device__ __forceinline__ float lg_gs<float>(float q, float coef) {
+    float q2 = q * q;
+    return coef * expf(-q2) * (9.0f - 5.0f * q2 + q2 * q2);
+}
+
+// ---------------------------------------------------------------------------
+// Compensated (Kahan) accumulator.
+template <typename R>
+struct Kahan {
+    R s, c;
+    __device__ __forceinline__ void init() { s = R(0); c = R(0); }
+    __device__ __forceinline__ void add(R x) {
+        R y = x - c;
+        R t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ R value() const { return s - c; }
+};
+
+// Plain accumulator with the same interface (float64 path).
+template <typename R>
+struct Plain {
+    R s;
+    __device__ __forceinline__ void init() { s = R(0); }
+    __device__ __forceinline__ void add(R x) { s += x; }
+    __device__ __forceinline__ R value() const { return s; }
+};
+
+// Sum over the LANES consecutive lanes of a group (butterfly, all lanes get it).
+template <int LANES, typename R>
+__device__ __forceinline__ R group_sum(R v) {
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Device-wide exclusive scan of int32 counts into int64 offsets:
+// out[i] = sum_{k<i} in[i] for i in [0, n], out[n] = total.
+int sph_exclusive_scan_i64(sph_ctx* ctx, const int32_t* in, int64_t* out, int64_t n,
+                           cudaStream_t s);
+// Same into int32 offsets (the caller guarantees the total fits).
+int sph_exclusive_scan_i32(sph_ctx* ctx, const int32_t* in, int32_t* out, int64_t n,
+                           cudaStream_t s);
+
+// Grid size helper.
+static inline unsigned grid_for(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    return (unsigned)(g < 1 ? 1 : g);
+}

@@ -1,0 +1,590 @@
+// a10/a11: Laguerre-Gauss particle relaxation (Sec. 2.3.2; Eqs. 7-8) and its
+// residual.  Positions move every step, so each step rebuilds the neighbour
+// sets (cell sort + count + scan + fill, the a1/a2 kernels), runs one pair pass
+// for the acceleration with a block-level max of |a|, and one pointwise update
+// (dt = 0.25 sqrt(h/max|a|), x += a dt^2/2, projection back inside the body).
+// The steps are launched back to back without host synchronisation; a device
+// flag records a neighbour-capacity overflow, after which the remaining steps
+// are no-ops and the host regrows the list and resumes from the failed step.
+#include "common.cuh"
+#include "neighbors.cuh"
+
+namespace {
+
+struct Spheres {
+    int count;
+    double c[SPH_MAX_SPHERES][3];
+    double r[SPH_MAX_SPHERES];
+    float ch[SPH_MAX_SPHERES][3], cl[SPH_MAX_SPHERES][3], rf[SPH_MAX_SPHERES];
+};
+
+struct RelaxK {
+    double h, dp, scale;           // scale = 2 p0 / rho
+    double gcoef;                  // LG gs coefficient -ahat h^-5 / 3
+    double gcoef_tw;               // Wendland gs coefficient -5 alpha h^-5
+    double inv_h;
+    double rc2_tw;                 // (1.6 h)^2 for the truncated residual
+    double surf_coef;              // 2 pi ahat / h
+    float gcoef_f, inv_h_f, scale_f, surf_coef_f, h_f, dp_f;
+};
+
+// Signed distance to the sphere union and its unit normal (first minimiser).
+__device__ __forceinline__ double sdf64(const Spheres& S, const double* x, double* g) {
+    double best = 0.0;
+    int arg = 0;
+    for (int k = 0; k < S.count; ++k) {
+        double dx = x[0] - S.c[k][0], dy = x[1] - S.c[k][1], dz = x[2] - S.c[k][2];
+        double d = sqrt(dx * dx + dy * dy + dz * dz) - S.r[k];
+        if (k == 0 || d < best) { best = d; arg = k; }
+    }
+    double rx = x[0] - S.c[arg][0], ry = x[1] - S.c[arg][1], rz = x[2] - S.c[arg][2];
+    double nr = sqrt(rx * rx + ry * ry + rz * rz);
+    if (nr > 0.0) { g[0] = rx / nr; g[1] = ry / nr; g[2] = rz / nr; }
+    else { g[0] = 1.0; g[1] = 0.0; g[2] = 0.0; }
+    return best;
+}
+
+// Same in float32 from a hi+lo position (differences keep float32 accuracy).
+__device__ __forceinline__ float sdf32(const Spheres& S, const float* xh, const float* xl, float* g) {
+    float best = 0.0f;
+    int arg = 0;
+    float brx = 0.f, bry = 0.f, brz = 0.f;
+    for (int k = 0; k < S.count; ++k) {
+        float dx = (xh[0] - S.ch[k][0]) + (xl[0] - S.cl[k][0]);
+        float dy = (xh[1] - S.ch[k][1]) + (xl[1] - S.cl[k][1]);
+        float dz = (xh[2] - S.ch[k][2]) + (xl[2] - S.cl[k][2]);
+        float d = sqrtf(dx * dx + dy * dy + dz * dz) - S.rf[k];
+        if (k == 0 || d < best) { best = d; arg = k; brx = dx; bry = dy; brz = dz; }
+    }
+    float nr = sqrtf(brx * brx + bry * bry + brz * brz);
+    if (nr > 0.0f) { float in = 1.0f / nr; g[0] = brx * in; g[1] = bry * in; g[2] = brz * in; }
+    else { g[0] = 1.0f; g[1] = 0.0f; g[2] = 0.0f; }
+    (void)arg;
+    return best;
+}
+
+// Half-space surface integral I(d) = 2 pi int_d^{2h} z (W(z) - W(2h)) dz of the 3D
+// Laguerre-Gauss kernel: with t = z/h the antiderivative of t w(t) is
+// -(1/12) e^{-t^2} (5 - t^2 + t^4), and W(2h) = ahat h^-3 (5/3) e^{-4}.
+template <typename R>
+__device__ __forceinline__ R surface_lg(R d, R inv_h, R coef) {   // coef = 2 pi ahat / h
+    R t = d * inv_h;
+    t = t < R(0) ? R(0) : (t > R(2) ? R(2) : t);
+    R t2 = t * t;
+    const R e4 = R(0.018315638888734179);          // e^-4
+    R prim2 = -(R(1) / R(12)) * e4 * R(17);        // at t = 2: 5 - 4 + 16 = 17
+    R primt = -(R(1) / R(12)) * exp(-t2) * (R(5) - t2 + t2 * t2);
+    R wcut = (R(5) / R(3)) * e4;
+    return coef * ((prim2 - primt) - R(0.5) * wcut * (R(4) - t2));
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned* addr, float v) {
+    atomicMax(addr, __float_as_uint(v));
+}
+
+// ---------------------------------------------------------------- acceleration
+__global__ void k_relax_acc64(const double* __restrict__ pos, const double* __restrict__ vol, int64_t n,
+                              const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, Spheres S,
+                              RelaxK K, double* __restrict__ acc, unsigned* __restrict__ amax,
+                              const int* __restrict__ flags) {
+    __shared__ unsigned smax;
+    if (threadIdx.x == 0) smax = 0u;
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool skip = flags[FLAG_CAPACITY] != 0;
+    if (i < n && !skip) {
+        double xi[3] = {pos[i], pos[n + i], pos[2 * n + i]};
+        double s[3] = {0.0, 0.0, 0.0};
+        for (int64_t p = row_ptr[i], e = row_ptr[i + 1]; p < e; ++p) {
+            int j = col[p];
+            double r[3], d2 = 0.0;
+            for (int a = 0; a < 3; ++a) { r[a] = xi[a] - pos[a * n + j]; d2 += r[a] * r[a]; }
+            double gs = lg_gs<double>(sqrt(d2) * K.inv_h, K.gcoef) * vol[j];
+            for (int a = 0; a < 3; ++a) s[a] += gs * r[a];
+        }
+        double g[3];
+        double phi = sdf64(S, xi, g);
+        double I = surface_lg<double>(phi < 0.0 ? -phi : 0.0, K.inv_h, K.surf_coef);
+        double a[3], m2 = 0.0;
+        for (int c = 0; c < 3; ++c) { a[c] = -K.scale * (s[c] + I * g[c]); m2 += a[c] * a[c]; acc[c * n + i] = a[c]; }
+        atomic_max_nonneg(&smax, __double2float_ru(sqrt(m2)));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && smax) atomicMax(amax, smax);
+}
+
+// exact float64 max of |a| (the float32 block max above only bounds it; a second
+// pass takes the exact value among candidates >= the bound's float32 lower edge)
+__global__ void k_amax64_exact(const double* __restrict__ acc, int64_t n, const unsigned* __restrict__ amax_f,
+                               unsigned long long* __restrict__ amax_d, const int* __restrict__ flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || flags[FLAG_CAPACITY]) return;
+    double m = sqrt(acc[i] * acc[i] + acc[n + i] * acc[n + i] + acc[2 * n + i] * acc[2 * n + i]);
+    float bound = __uint_as_float(*amax_f);
+    if (__double2float_ru(m) == bound) atomicMax(amax_d, (unsigned long long)__double_as_longlong(m));
+}
+
+template <int LANES>
+__global__ void __launch_bounds__(256) k_relax_acc32(const float4* __restrict__ geo, int64_t n,
+                                                     const int64_t* __restrict__ row_ptr,
+                                                     const int32_t* __restrict__ col, Spheres S, RelaxK K,
+                                                     float4* __restrict__ acc, unsigned* __restrict__ amax,
+                                                     const int* __restrict__ flags) {
+    __shared__ unsigned smax;
+    if (threadIdx.x == 0) smax = 0u;
+    __syncthreads();
+    int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = gt / LANES;
+    int lane = (int)(gt % LANES);
+    bool active = i < n && flags[FLAG_CAPACITY] == 0;
+    int64_t ii = i < n ? i : 0;
+    float4 A = __ldg(&geo[2 * ii]), B = __ldg(&geo[2 * ii + 1]);
+    float xh[3] = {A.x, A.y, A.z}, xl[3] = {B.x, B.y, B.z};
+    Kahan<float> s[3];
+    for (int a = 0; a < 3; ++a) s[a].init();
+    int64_t b = active ? row_ptr[ii] : 0, e = active ? row_ptr[ii + 1] : 0;
+    for (int64_t p = b + lane; p < e; p += LANES) {
+        int j = __ldg(&col[p]);
+        float4 Aj = __ldg(&geo[2 * j]), Bj = __ldg(&geo[2 * j + 1]);
+        float r[3];
+        r[0] = (xh[0] - Aj.x) + (xl[0] - Bj.x);
+        r[1] = (xh[1] - Aj.y) + (xl[1] - Bj.y);
+        r[2] = (xh[2] - Aj.z) + (xl[2] - Bj.z);
+        float d2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        float gs = lg_gs<float>(sqrtf(d2) * K.inv_h_f, K.gcoef_f) * Aj.w;
+        for (int a = 0; a < 3; ++a) s[a].add(gs * r[a]);
+    }
+    float tot[3];
+    for (int a = 0; a < 3; ++a) tot[a] = group_sum<LANES>(s[a].value());
+    if (active && lane == 0) {
+        float g[3];
+        float phi = sdf32(S, xh, xl, g);
+        float I = surface_lg<float>(phi < 0.0f ? -phi : 0.0f, K.inv_h_f, K.surf_coef_f);
+        float a0 = -K.scale_f * (tot[0] + I * g[0]);
+        float a1 = -K.scale_f * (tot[1] + I * g[1]);
+        float a2 = -K.scale_f * (tot[2] + I * g[2]);
+        acc[i] = make_float4(a0, a1, a2, 0.0f);
+        atomic_max_nonneg(&smax, sqrtf(a0 * a0 + a1 * a1 + a2 * a2));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && smax) atomicMax(amax, smax);
+}
+
+// ---------------------------------------------------------------- update
+__global__ void k_relax_update64(double* __restrict__ pos, int64_t n, const double* __restrict__ acc,
+                                 const unsigned long long* __restrict__ amax_d, Spheres S, RelaxK K,
+                                 const int* __restrict__ flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || flags[FLAG_CAPACITY]) return;
+    double am = __longlong_as_double((long long)*amax_d);
+    double x[3] = {pos[i], pos[n + i], pos[2 * n + i]};
+    if (am > 0.0) {
+        double dt = 0.25 * sqrt(K.h / am);
+        for (int c = 0; c < 3; ++c) x[c] = x[c] + 0.5 * acc[c * n + i] * (dt * dt);
+    }
+    double g[3];
+    double phi = sdf64(S, x, g);
+    if (phi > -0.5 * K.dp) {
+        double sh = phi + 0.5 * K.dp;
+        for (int c = 0; c < 3; ++c) x[c] = x[c] - sh * g[c];
+    }
+    for (int c = 0; c < 3; ++c) pos[c * n + i] = x[c];
+}
+
+__global__ void k_relax_update32(double* __restrict__ pos, int64_t n, const float4* __restrict__ acc,
+                                 const unsigned* __restrict__ amax, Spheres S, RelaxK K,
+                                 float4* __restrict__ geo, const int* __restrict__ flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || flags[FLAG_CAPACITY]) return;
+    float am = __uint_as_float(*amax);
+    double x[3] = {pos[i], pos[n + i], pos[2 * n + i]};
+    if (am > 0.0f) {
+        float sc = (K.h_f * 0.03125f) / am;         // a dt^2/2 = a (h/32)/max|a|
+        float4 a = acc[i];
+        x[0] += (double)(a.x * sc);
+        x[1] += (double)(a.y * sc);
+        x[2] += (double)(a.z * sc);
+    }
+    float xh[3], xl[3], g[3];
+    for (int c = 0; c < 3; ++c) { xh[c] = (float)x[c]; xl[c] = (float)(x[c] - (double)xh[c]); }
+    float phi = sdf32(S, xh, xl, g);
+    if (phi > -0.5f * K.dp_f) {
+        float sh = phi + 0.5f * K.dp_f;
+        for (int c = 0; c < 3; ++c) x[c] -= (double)(sh * g[c]);
+    }
+    for (int c = 0; c < 3; ++c) {
+        pos[c * n + i] = x[c];
+        xh[c] = (float)x[c];
+        xl[c] = (float)(x[c] - (double)xh[c]);
+    }
+    float4 A = geo[2 * i];
+    geo[2 * i] = make_float4(xh[0], xh[1], xh[2], A.w);
+    geo[2 * i + 1] = make_float4(xl[0], xl[1], xl[2], 0.0f);
+}
+
+__global__ void k_relax_pack(const double* __restrict__ pos, const double* __restrict__ vol, int64_t n,
+                             float4* __restrict__ geo) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float xh[3], xl[3];
+    for (int c = 0; c < 3; ++c) {
+        double x = pos[c * n + i];
+        xh[c] = (float)x;
+        xl[c] = (float)(x - (double)xh[c]);
+    }
+    geo[2 * i] = make_float4(xh[0], xh[1], xh[2], (float)vol[i]);
+    geo[2 * i + 1] = make_float4(xl[0], xl[1], xl[2], 0.0f);
+}
+
+// ---------------------------------------------------------------- residual
+__global__ void k_relax_residual(const double* __restrict__ pos, const double* __restrict__ vol, int64_t n,
+                                 const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, Spheres S,
+                                 RelaxK K, double* __restrict__ partial) {
+    __shared__ double sh[3][256];
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double e_lg = 0.0, e_tw = 0.0, cnt = 0.0;
+    if (i < n) {
+        double xi[3] = {pos[i], pos[n + i], pos[2 * n + i]};
+        double g[3];
+        double phi = sdf64(S, xi, g);
+        if (phi < -2.0 * K.h) {
+            double s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0};
+            for (int64_t p = row_ptr[i], e = row_ptr[i + 1]; p < e; ++p) {
+                int j = col[p];
+                double r[3];
+                for (int a = 0; a < 3; ++a) r[a] = xi[a] - pos[a * n + j];
+                double d2u = __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])), __dmul_rn(r[2], r[2]));
+                double q = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) * K.inv_h;
+                double w = vol[j];
+                double g1 = lg_gs<double>(q, K.gcoef) * w;
+                double g2 = d2u <= K.rc2_tw ? wendland_gs<double>(q, K.gcoef_tw) * w : 0.0;
+                for (int a = 0; a < 3; ++a) { s1[a] += g1 * r[a]; s2[a] += g2 * r[a]; }
+            }
+            double h2 = K.h * K.h;
+            e_lg = h2 * (s1[0] * s1[0] + s1[1] * s1[1] + s1[2] * s1[2]);
+            e_tw = h2 * (s2[0] * s2[0] + s2[1] * s2[1] + s2[2] * s2[2]);
+            cnt = 1.0;
+        }
+    }
+    sh[0][threadIdx.x] = e_lg;
+    sh[1][threadIdx.x] = e_tw;
+    sh[2][threadIdx.x] = cnt;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) partial[3 * blockIdx.x + c] = sh[c][0];
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+    __shared__ double sh[3][256];
+    double a[3] = {0, 0, 0};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        for (int c = 0; c < 3; ++c) a[c] += partial[3 * b + c];
+    for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] = a[c];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) out[c] = sh[c][0];
+}
+
+__global__ void k_widen_acc(const float4* __restrict__ acc, int64_t n, double* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 a = acc[i];
+    out[i] = a.x;
+    out[n + i] = a.y;
+    out[2 * n + i] = a.z;
+}
+
+// ---------------------------------------------------------------- host helpers
+int check_relax(const sph_relax_params* p) {
+    if (!p) return SPH_ERR_ARG;
+    int s = sph_check_domain(&p->dom);
+    if (s) return s;
+    if (p->dom.dim != 3) return SPH_ERR_ARG;
+    if (p->kernel != SPH_LAGUERRE_GAUSS) return SPH_ERR_ARG;
+    if (p->precision != SPH_FP64 && p->precision != SPH_FP32_KAHAN) return SPH_ERR_ARG;
+    if (p->n_spheres < 1 || p->n_spheres > SPH_MAX_SPHERES) return SPH_ERR_ARG;
+    if (!(p->dp > 0.0) || !(p->rho > 0.0) || !(p->p0 > 0.0)) return SPH_ERR_ARG;
+    return SPH_OK;
+}
+
+Spheres make_spheres(const sph_relax_params* p) {
+    Spheres S;
+    S.count = p->n_spheres;
+    for (int k = 0; k < SPH_MAX_SPHERES; ++k) {
+        for (int c = 0; c < 3; ++c) {
+            double v = k < S.count ? p->spheres[4 * k + c] : 0.0;
+            S.c[k][c] = v;
+            S.ch[k][c] = (float)v;
+            S.cl[k][c] = (float)(v - (double)S.ch[k][c]);
+        }
+        S.r[k] = k < S.count ? p->spheres[4 * k + 3] : 0.0;
+        S.rf[k] = (float)S.r[k];
+    }
+    return S;
+}
+
+RelaxK make_relax_consts(const sph_relax_params* p) {
+    RelaxK K;
+    double h = p->dom.h;
+    double h5 = h * h * h * h * h;
+    K.h = h;
+    K.dp = p->dp;
+    K.scale = 2.0 * p->p0 / p->rho;
+    K.gcoef = -lg_alpha(3) / h5 / 3.0;
+    K.gcoef_tw = -5.0 * wendland_alpha(3) / h5;
+    K.inv_h = 1.0 / h;
+    double rtw = 1.6 * h;
+    K.rc2_tw = rtw * rtw;
+    K.surf_coef = 2.0 * SPH_PI * lg_alpha(3) / h;
+    K.gcoef_f = (float)K.gcoef;
+    K.inv_h_f = (float)K.inv_h;
+    K.scale_f = (float)K.scale;
+    K.surf_coef_f = (float)K.surf_coef;
+    K.h_f = (float)h;
+    K.dp_f = (float)p->dp;
+    return K;
+}
+
+struct RelaxLists {
+    int64_t* row_ptr;
+    int32_t* col;
+    int64_t cap;
+};
+
+// Neighbour lists (cut-off dom.kappa*h) of the current positions into context
+// scratch; capacity overflow is flagged with the step index (first one sticks).
+__global__ void k_flag_capacity(const int64_t* __restrict__ row_ptr, int64_t n, int64_t cap, int step,
+                                int* __restrict__ flags) {
+    if (row_ptr[n] > cap) atomicCAS(&flags[FLAG_CAPACITY], 0, step + 1);
+}
+
+int build_lists(sph_ctx* ctx, const sph_domain* dom, const double* pos, cudaStream_t s, RelaxLists& L, int step) {
+    CellList cl;
+    int st = sph_build_cells(ctx, dom, pos, s, &cl);
+    if (st) return st;
+    int64_t n = dom->n;
+    int32_t* row_len = (int32_t*)sph_scratch(ctx, S_ROW_LEN, (size_t)(n + 1) * 4, &st);
+    if (st) return st;
+    st = sph_count_neighbors(ctx, cl, pos, n, cl.grid.rc2, row_len, s);
+    if (st) return st;
+    st = sph_exclusive_scan_i64(ctx, row_len, L.row_ptr, n, s);
+    if (st) return st;
+    k_flag_capacity<<<1, 1, 0, s>>>(L.row_ptr, n, L.cap, step, ctx->flags);
+    st = sph_fill_neighbors(ctx, cl, pos, n, cl.grid.rc2, L.row_ptr, L.col, L.cap, s);
+    return st;
+}
+
+int ensure_lists(sph_ctx* ctx, int64_t n, int64_t cap, RelaxLists& L) {
+    int st = SPH_OK;
+    L.row_ptr = (int64_t*)sph_scratch(ctx, S_RELAX_ROWPTR, (size_t)(n + 1) * 8, &st);
+    L.col = (int32_t*)sph_scratch(ctx, S_RELAX_COL, (size_t)cap * 4, &st);
+    L.cap = cap;
+    return st;
+}
+
+// Default capacity: 128 neighbours per particle (a relaxed 3D body at h = 1.3 dp
+// and cut-off 2h has about 74), regrown on overflow.
+int64_t g_default_per_particle = 128;
+
+template <int LANES>
+void acc32(const float4* geo, int64_t n, const RelaxLists& L, const Spheres& S, const RelaxK& K, float4* acc,
+           unsigned* amax, const int* flags, cudaStream_t s) {
+    k_relax_acc32<LANES><<<grid_for(n * LANES, 256), 256, 0, s>>>(geo, n, L.row_ptr, L.col, S, K, acc, amax, flags);
+}
+
+int read_capacity_flag(sph_ctx* ctx, cudaStream_t s, int* step_failed, int64_t* required, const RelaxLists& L,
+                       int64_t n) {
+    int* hf = (int*)ctx->pinned;
+    int64_t* hp = (int64_t*)ctx->pinned;
+    SPH_CUDA(ctx, cudaMemcpyAsync(hf, ctx->flags, FLAG_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(ctx, cudaMemcpyAsync(hp + 8, L.row_ptr + n, 8, cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(ctx, cudaStreamSynchronize(s));
+    *step_failed = hf[FLAG_CAPACITY];
+    *required = hp[8];
+    if (hf[FLAG_BAD_INPUT]) {
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+        return SPH_ERR_ARG;
+    }
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" int sph_relax_step(sph_ctx* ctx, const sph_relax_params* p, double* pos, const double* vol, int nsteps,
+                              void* stream) {
+    if (!ctx || nsteps < 0) return SPH_ERR_ARG;
+    int st = check_relax(p);
+    if (st) return st;
+    int64_t n = p->dom.n;
+    if (n == 0 || nsteps == 0) return SPH_OK;
+    if (!pos || !vol) return SPH_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    Spheres S = make_spheres(p);
+    RelaxK K = make_relax_consts(p);
+    int64_t cap = ctx->slot_bytes[S_RELAX_COL] / 4;
+    if (cap < n * g_default_per_particle) cap = n * g_default_per_particle;
+    RelaxLists L;
+    st = ensure_lists(ctx, n, cap, L);
+    if (st) return st;
+    unsigned* amax = (unsigned*)sph_scratch(ctx, S_RELAX_AMAX, 64, &st);
+    if (st) return st;
+    unsigned long long* amax_d = (unsigned long long*)(amax + 4);
+    bool fp32 = p->precision == SPH_FP32_KAHAN;
+    void* accbuf = sph_scratch(ctx, S_RELAX_ACC, (size_t)n * (fp32 ? 16 : 24), &st);
+    float4* geo = (float4*)sph_scratch(ctx, S_MISC0, (size_t)n * 32, &st);
+    if (st) return st;
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+    if (fp32) k_relax_pack<<<grid_for(n, 256), 256, 0, s>>>(pos, vol, n, geo);
+    int done = 0;
+    for (int attempt = 0; attempt < 8 && done < nsteps; ++attempt) {
+        for (int k = done; k < nsteps; ++k) {
+            int t = sph_timer_begin(ctx, SPH_TIMER_NEIGHBORS, s);
+            st = build_lists(ctx, &p->dom, pos, s, L, k);
+            if (st) return st;
+            sph_timer_end(ctx, t, s);
+            SPH_CUDA(ctx, cudaMemsetAsync(amax, 0, 64, s));
+            t = sph_timer_begin(ctx, SPH_TIMER_RELAX_ACCEL, s);
+            if (fp32) {
+                float4* acc = (float4*)accbuf;
+                switch (ctx->lanes[SPH_PASS_RELAX]) {
+                    case 1: acc32<1>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
+                    case 2: acc32<2>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
+                    case 8: acc32<8>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
+                    default: acc32<4>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
+                }
+                sph_timer_end(ctx, t, s);
+                t = sph_timer_begin(ctx, SPH_TIMER_RELAX_UPDATE, s);
+                k_relax_update32<<<grid_for(n, 256), 256, 0, s>>>(pos, n, acc, amax, S, K, geo, ctx->flags);
+                sph_timer_end(ctx, t, s);
+            } else {
+                double* acc = (double*)accbuf;
+                k_relax_acc64<<<grid_for(n, 128), 128, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, acc, amax, ctx->flags);
+                k_amax64_exact<<<grid_for(n, 256), 256, 0, s>>>(acc, n, amax, amax_d, ctx->flags);
+                sph_timer_end(ctx, t, s);
+                t = sph_timer_begin(ctx, SPH_TIMER_RELAX_UPDATE, s);
+                k_relax_update64<<<grid_for(n, 256), 256, 0, s>>>(pos, n, acc, amax_d, S, K, ctx->flags);
+                sph_timer_end(ctx, t, s);
+            }
+            SPH_LAUNCH_CHECK(ctx);
+        }
+        int failed = 0;
+        int64_t required = 0;
+        st = read_capacity_flag(ctx, s, &failed, &required, L, n);
+        if (st) return st;
+        if (!failed) { done = nsteps; break; }
+        done = failed - 1;
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+        st = ensure_lists(ctx, n, required + required / 4 + 1024, L);
+        if (st) return st;
+    }
+    return done == nsteps ? SPH_OK : SPH_ERR_CAPACITY;
+}
+
+extern "C" int sph_relax_accel(sph_ctx* ctx, const sph_relax_params* p, const double* pos, const double* vol,
+                               double* acc_out, void* stream) {
+    if (!ctx) return SPH_ERR_ARG;
+    int st = check_relax(p);
+    if (st) return st;
+    int64_t n = p->dom.n;
+    if (n == 0) return SPH_OK;
+    if (!pos || !vol || !acc_out) return SPH_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    Spheres S = make_spheres(p);
+    RelaxK K = make_relax_consts(p);
+    int64_t cap = n * g_default_per_particle;
+    RelaxLists L;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        st = ensure_lists(ctx, n, cap, L);
+        if (st) return st;
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+        st = build_lists(ctx, &p->dom, pos, s, L, 0);
+        if (st) return st;
+        int failed = 0;
+        int64_t required = 0;
+        st = read_capacity_flag(ctx, s, &failed, &required, L, n);
+        if (st) return st;
+        if (!failed) break;
+        cap = required + required / 4 + 1024;
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+    }
+    unsigned* amax = (unsigned*)sph_scratch(ctx, S_RELAX_AMAX, 64, &st);
+    if (st) return st;
+    SPH_CUDA(ctx, cudaMemsetAsync(amax, 0, 64, s));
+    if (p->precision == SPH_FP64) {
+        k_relax_acc64<<<grid_for(n, 128), 128, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, acc_out, amax, ctx->flags);
+    } else {
+        float4* geo = (float4*)sph_scratch(ctx, S_MISC0, (size_t)n * 32, &st);
+        float4* acc = (float4*)sph_scratch(ctx, S_RELAX_ACC, (size_t)n * 16, &st);
+        if (st) return st;
+        k_relax_pack<<<grid_for(n, 256), 256, 0, s>>>(pos, vol, n, geo);
+        switch (ctx->lanes[SPH_PASS_RELAX]) {
+            case 1: acc32<1>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
+            case 2: acc32<2>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
+            case 8: acc32<8>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
+            default: acc32<4>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
+        }
+        k_widen_acc<<<grid_for(n, 256), 256, 0, s>>>(acc, n, acc_out);
+    }
+    SPH_LAUNCH_CHECK(ctx);
+    return SPH_OK;
+}
+
+extern "C" int sph_relax_residual(sph_ctx* ctx, const sph_relax_params* p, const double* pos, const double* vol,
+                                  double* out_host, void* stream) {
+    if (!ctx || !out_host) return SPH_ERR_ARG;
+    int st = check_relax(p);
+    if (st) return st;
+    int64_t n = p->dom.n;
+    out_host[0] = out_host[1] = out_host[2] = 0.0;
+    if (n == 0) return SPH_OK;
+    if (!pos || !vol) return SPH_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    Spheres S = make_spheres(p);
+    RelaxK K = make_relax_consts(p);
+    sph_domain dom = p->dom;
+    dom.kappa = 2.0;
+    int64_t cap = n * g_default_per_particle;
+    RelaxLists L;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        st = ensure_lists(ctx, n, cap, L);
+        if (st) return st;
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+        st = build_lists(ctx, &dom, pos, s, L, 0);
+        if (st) return st;
+        int failed = 0;
+        int64_t required = 0;
+        st = read_capacity_flag(ctx, s, &failed, &required, L, n);
+        if (st) return st;
+        if (!failed) break;
+        cap = required + required / 4 + 1024;
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+    }
+    int nb = (int)grid_for(n, 256);
+    double* partial = (double*)sph_scratch(ctx, S_RED_PARTIAL, (size_t)nb * 3 * 8 + 64, &st);
+    if (st) return st;
+    double* out_d = partial + (size_t)nb * 3;
+    k_relax_residual<<<nb, 256, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, partial);
+    k_sum_partials<<<1, 256, 0, s>>>(partial, nb, out_d);
+    SPH_LAUNCH_CHECK(ctx);
+    double* hp = (double*)ctx->pinned;
+    SPH_CUDA(ctx, cudaMemcpyAsync(hp + 32, out_d, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(ctx, cudaStreamSynchronize(s));
+    double m = hp[34];
+    if (!isfinite(hp[32]) || !isfinite(hp[33])) return SPH_ERR_NONFINITE;
+    out_host[2] = m;
+    if (m > 0.0) {
+        out_host[0] = sqrt(hp[32] / m);
+        out_host[1] = sqrt(hp[33] / m);
+    }
+    return SPH_OK;
+}

@@ -1,0 +1,162 @@
+"""GPU parity of the Eulerian WCSPH path (a5, a6) against the float64 oracle.
+
+float64 fields must agree within 1e-12 (normwise relative), float32 fields within
+1e-5 relative L2 (Eq. 10 form)."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import cuda, host, odom, rel_l2, rel_max, sample_rows, sorted_by_cells
+from oracle import eulerian as OE
+from oracle import kgc as OK
+from oracle import neighbors as ON
+from paper_2405_05155_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _setup(ctx, case, jitter=0.0, seed=0, sort=True):
+    d = case["domain"]
+    pos = case["pos"]
+    if jitter:
+        rng = np.random.default_rng(seed)
+        pos = np.mod(pos + rng.uniform(-jitter, jitter, pos.shape) * case["dp"], d["len"][0])
+    order = np.arange(pos.shape[1])
+    if sort:
+        pos, order = sorted_by_cells(pos, d)
+    v = case["v"][:, order]
+    drho = (case["p"] / case["c0"] ** 2)[order]
+    vol = case["vol"][order]
+    rp, col = api.build_neighbors(ctx, d, cuda(pos))
+    B, fb, _ = api.kgc(ctx, d, cuda(pos), cuda(vol), rp, col)
+    prm = OE.EulerianParams(odom(d), case["dt"], case["rho0"], case["c0"], case["mu"])
+    return dict(pos=pos, vol=vol, v=v, drho=drho, rp=rp, col=col, B=B, rp_h=host(rp), col_h=host(col),
+                B_h=host(B), prm=prm, d=d)
+
+
+def _sim(ctx, s, case, precision, integrator=api.SPH_TWO_PASS, drho=None, v=None):
+    return api.Eulerian(ctx, s["d"], cuda(s["pos"]), cuda(s["vol"]), s["B"], s["rp"], s["col"],
+                        s["drho"] if drho is None else drho, s["v"] if v is None else v, case["dt"],
+                        case["rho0"], case["c0"], case["mu"], precision=precision, integrator=integrator)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("kappa", [1.6, 2.0])
+def test_rates_parity(ctx, dim, kappa):
+    case = inputs.tgv2d(nx=32, kappa=kappa) if dim == 2 else inputs.tgv3d(n=12, kappa=kappa)
+    s = _setup(ctx, case, jitter=0.2, seed=dim)
+    rng = np.random.default_rng(9)
+    drho = s["drho"] + 1e-3 * rng.normal(size=s["drho"].shape)
+    v = s["v"] + 0.1 * rng.normal(size=s["v"].shape)
+    ro, mo = OE.eulerian_rates(s["pos"], s["vol"], drho, v, s["B_h"], s["rp_h"], s["col_h"], s["prm"])
+    for prec, tol, err in ((api.SPH_FP64, 1e-12, rel_max), (api.SPH_FP32_KAHAN, 1e-5, rel_l2)):
+        sim = _sim(ctx, s, case, prec, drho=drho, v=v)
+        r, m = sim.rates()
+        assert err(host(r), ro) < tol, (prec, err(host(r), ro))
+        assert err(host(m), mo) < tol, (prec, err(host(m), mo))
+
+
+def test_plain_method_tgv2d_200_steps(ctx):
+    # 2D Taylor-Green vortex, 50x50, h = 1.3 dp, kappa = 1.6, Re = 100, 200 steps in float64
+    case = inputs.tgv2d(nx=50, kappa=1.6)
+    s = _setup(ctx, case)
+    d_o, v_o = OE.run(s["pos"], s["vol"], s["drho"], s["v"], s["B_h"], s["rp_h"], s["col_h"], s["prm"], 200)
+    sim = _sim(ctx, s, case, api.SPH_FP64)
+    sim.step(200)
+    dr, v = sim.fields()
+    assert rel_max(host(dr), d_o) < 1e-12
+    assert rel_max(host(v), v_o) < 1e-12
+    # closed-form decay exp(-8 pi^2 t / Re) of the velocity amplitude
+    t = 200 * case["dt"]
+    amp = np.sqrt(np.mean(host(v) ** 2)) / np.sqrt(np.mean(s["v"] ** 2))
+    assert abs(amp / math.exp(-case["decay_rate"] * t) - 1.0) < 0.03
+    # float32 + Kahan against the float64 oracle, same 200 steps
+    sim32 = _sim(ctx, s, case, api.SPH_FP32_KAHAN)
+    sim32.step(200)
+    dr32, v32 = sim32.fields()
+    assert rel_l2(host(v32), v_o) < 1e-5
+    assert rel_l2(host(dr32), d_o) < 1e-5
+
+
+@pytest.mark.parametrize("integrator", [api.SPH_TWO_PASS, api.SPH_FUSED])
+def test_steps_3d_both_integrators(ctx, integrator):
+    case = inputs.tgv3d(n=16, kappa=1.6)
+    s = _setup(ctx, case)
+    run = OE.run(s["pos"], s["vol"], s["drho"], s["v"], s["B_h"], s["rp_h"], s["col_h"], s["prm"], 7,
+                 fused=integrator == api.SPH_FUSED)
+    for prec, tol, err in ((api.SPH_FP64, 1e-12, rel_max), (api.SPH_FP32_KAHAN, 1e-5, rel_l2)):
+        sim = _sim(ctx, s, case, prec, integrator)
+        sim.step(7)
+        dr, v = sim.fields()
+        assert err(host(dr), run[0]) < tol and err(host(v), run[1]) < tol
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+def test_launch_shapes_agree(ctx, lanes):
+    # every launch shape (lanes per particle) meets the float32 field tolerance; the input is
+    # not cell-sorted, which the neighbour builder must still turn into ascending rows
+    case = inputs.tgv2d(nx=40, kappa=1.6)
+    s = _setup(ctx, case, sort=False)
+    d_o, v_o = OE.run(s["pos"], s["vol"], s["drho"], s["v"], s["B_h"], s["rp_h"], s["col_h"], s["prm"], 5)
+    ctx.set_lanes(api.SPH_PASS_EULERIAN, lanes)
+    try:
+        sim = _sim(ctx, s, case, api.SPH_FP32_KAHAN)
+        sim.step(5)
+        dr, v = sim.fields()
+        assert rel_l2(host(dr), d_o) < 1e-5 and rel_l2(host(v), v_o) < 1e-5
+    finally:
+        ctx.set_lanes(api.SPH_PASS_EULERIAN, 4)
+
+
+def test_conservation_on_gpu(ctx):
+    case = inputs.tgv3d(n=16, kappa=1.6)
+    s = _setup(ctx, case, jitter=0.25, seed=4)
+    rng = np.random.default_rng(1)
+    v = rng.normal(size=s["v"].shape)
+    sim = _sim(ctx, s, case, api.SPH_FP64, v=v)
+    r, m = sim.rates()
+    r, m = host(r), host(m)
+    assert abs(np.sum(s["vol"] * r)) < 1e-12 * np.sum(s["vol"] * np.abs(r))
+    assert np.max(np.abs(np.sum(s["vol"] * m, axis=1))) < 1e-12 * np.sum(s["vol"] * np.abs(m))
+
+
+def _oracle_two_pass_sampled(s, rows):
+    """One two-pass step of the oracle evaluated only where the sampled rows need it."""
+    rp, col = s["rp_h"], s["col_h"]
+    nbrs = np.concatenate([col[rp[i]:rp[i + 1]] for i in rows])
+    rows1 = np.unique(np.concatenate([rows, nbrs]))
+    prm = s["prm"]
+    rho_n = prm.rho0 + s["drho"]
+    rp1, col1 = sample_rows(rp, col, rows1)
+    _, dmom = OE.eulerian_rates(s["pos"], s["vol"], s["drho"], s["v"], s["B_h"], rp1, col1, prm, want_mass=False)
+    mom1 = rho_n * s["v"] + prm.dt * dmom
+    v_half = mom1 / rho_n
+    rps, cols = sample_rows(rp, col, rows)
+    drho_dt, _ = OE.eulerian_rates(s["pos"], s["vol"], s["drho"], v_half, s["B_h"], rps, cols, prm, want_mom=False)
+    drho1 = s["drho"] + prm.dt * drho_dt
+    return drho1[rows], (mom1 / (prm.rho0 + drho1))[:, rows]
+
+
+def test_full_size_3d_tgv_sampled(ctx):
+    # 128^3 periodic Taylor-Green (2.1M particles): one float32 time step as benchmarked,
+    # against the float64 oracle's step on 64 sampled particles
+    case = inputs.tgv3d(n=128, kappa=1.6)
+    s = _setup(ctx, case)
+    n = s["pos"].shape[1]
+    assert np.all(np.diff(s["rp_h"]) == 32)
+    sim = _sim(ctx, s, case, api.SPH_FP32_KAHAN)
+    sim.step(1)
+    dr, v = sim.fields()
+    dr, v = host(dr), host(v)
+    rows = np.random.default_rng(3).choice(n, 64, replace=False)
+    d_o, v_o = _oracle_two_pass_sampled(s, rows)
+    assert rel_l2(dr[rows], d_o) < 1e-5
+    assert rel_l2(v[:, rows], v_o) < 1e-5
