@@ -161,6 +161,23 @@ def sphere_body(seed, dp, jitter=0.25, count=8):
             "domain": dom, "dp": dp, "h": h}
 
 
+MLP_SHAPES = [(128, 128), (128,), (128, 128), (128,), (128, 128), (128,), (3, 128), (3,)]
+
+
+def mlp_init(seed):
+    """Seeded initial parameters of the 128-128-128-128-3 proposal network, flat float64:
+    weights U(-a, a) with a = sqrt(6 / (fan_in + fan_out)), biases zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for shape in MLP_SHAPES:
+        if len(shape) == 2:
+            a = math.sqrt(6.0 / (shape[0] + shape[1]))
+            parts.append(rng.uniform(-a, a, size=shape).ravel())
+        else:
+            parts.append(np.zeros(shape))
+    return np.concatenate(parts)
+
+
 def batched_tgv2d(seed=0, ncases=64, nmin=64, nmax=1024, kappa=KAPPA_TW, scale=1.0):
     """Uneven batch of 2D Taylor-Green cases: n_c = round(exp U(ln nmin, ln nmax)) per side,
     Re in {100, 1000} by a fair coin.  ``scale`` shrinks every side (for small tests)."""
