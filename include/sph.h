@@ -48,6 +48,7 @@ extern "C" {
 #define SPH_ERR_CUDA      3  /* a CUDA runtime call failed; see sph_last_cuda_error */
 #define SPH_ERR_TIMEOUT   4  /* a bounded device-side wait expired */
 #define SPH_ERR_NONFINITE 5  /* a reduction met a NaN or infinity */
+#define SPH_ERR_LIMIT     6  /* input larger than a fixed internal limit (sph_build_neighbors_static) */
 
 /* ---- enums ---- */
 #define SPH_WENDLAND_C2     0  /* Eq. 6; cut-off kappa*h, kappa = 2 or 1.6 */
@@ -152,6 +153,32 @@ int sph_cell_order(sph_ctx* ctx, const sph_domain* dom, const double* pos,
 int sph_build_neighbors(sph_ctx* ctx, const sph_domain* dom, const double* pos,
                         int64_t* row_ptr, int32_t* col, int64_t cap,
                         int64_t* nnz_host, void* stream);
+
+/* ---- allocation-free neighbour lists ----
+ * The paper has no counterpart: this is a deployment variant of
+ * sph_build_neighbors for callers that cannot allocate device memory, such as a
+ * plug-in inside an application that owns the whole device-memory budget (it
+ * reserves its pool at start-up and treats any other cudaMalloc as a failure),
+ * or a latency-critical loop in which cudaMalloc/cudaFree would synchronise the
+ * device.  Same arguments, results and status codes as sph_build_neighbors, but
+ * no context and no allocation of any kind: all internal scratch lives in one
+ * static device array of SPH_STATIC_SCRATCH_BYTES (44 MiB) that every GPU
+ * loading libsph holds until the process exits.  The caller provides pos,
+ * row_ptr and col as usual.  Limits: n <= SPH_STATIC_MAX_PARTICLES and at most
+ * SPH_STATIC_MAX_CELLS cells in the grid (n_x n_y n_z of the sph_domain comment);
+ * larger inputs return SPH_ERR_LIMIT before any device work.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  Every call reuses the same
+ * array and clears what must start at zero; calls that overlap on the GPU (from
+ * two streams or two host threads) race on it and must be serialised by the
+ * caller.  Synchronises the stream.  On SPH_ERR_CUDA the CUDA error is left for
+ * cudaGetLastError(). */
+#define SPH_STATIC_MAX_PARTICLES (1 << 20)
+#define SPH_STATIC_MAX_CELLS     (1 << 20)
+#define SPH_STATIC_SCRATCH_BYTES (44u << 20)
+int sph_build_neighbors_static(const sph_domain* dom, const double* pos,
+                               int64_t* row_ptr, int32_t* col, int64_t cap,
+                               int64_t* nnz_host, void* stream);
 
 /* ---- a4: kernel gradient correction ----
  * Eq. 9 (Sec. 2.3.2): A_i = -sum_j V_j r_ij (x) grad W_ij over the CSR row,

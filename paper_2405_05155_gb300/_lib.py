@@ -11,7 +11,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "lib", "libsph.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "sph.h")
 
-SPH_OK, SPH_ERR_ARG, SPH_ERR_CAPACITY, SPH_ERR_CUDA, SPH_ERR_TIMEOUT, SPH_ERR_NONFINITE = range(6)
+SPH_OK, SPH_ERR_ARG, SPH_ERR_CAPACITY, SPH_ERR_CUDA, SPH_ERR_TIMEOUT, SPH_ERR_NONFINITE, SPH_ERR_LIMIT = range(7)
+SPH_STATIC_MAX_PARTICLES = 1 << 20
+SPH_STATIC_MAX_CELLS = 1 << 20
 SPH_WENDLAND_C2, SPH_LAGUERRE_GAUSS = 0, 1
 SPH_FP64, SPH_FP32_KAHAN = 0, 1
 SPH_TWO_PASS, SPH_FUSED = 0, 1
@@ -69,6 +71,7 @@ _SIGNATURES = {
                                        c_i64, c_vp]),
     "sph_cell_order": (ctypes.c_int, [c_vp, _P(SphDomain), c_vp, c_vp, c_vp]),
     "sph_build_neighbors": (ctypes.c_int, [c_vp, _P(SphDomain), c_vp, c_vp, c_vp, c_i64, _P(c_i64), c_vp]),
+    "sph_build_neighbors_static": (ctypes.c_int, [_P(SphDomain), c_vp, c_vp, c_vp, c_i64, _P(c_i64), c_vp]),
     "sph_kgc": (ctypes.c_int, [c_vp, _P(SphDomain), ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, _P(c_i64),
                                c_vp]),
     "sph_eulerian_pack": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), c_vp]),

@@ -151,6 +151,10 @@ int sph_exclusive_scan_i64(sph_ctx* ctx, const int32_t* in, int64_t* out, int64_
 // Same into int32 offsets (the caller guarantees the total fits).
 int sph_exclusive_scan_i32(sph_ctx* ctx, const int32_t* in, int32_t* out, int64_t n,
                            cudaStream_t s);
+// Context-free variants with a caller-provided block-sum buffer of at least
+// n / 2048 + 2 elements.
+int sph_exclusive_scan_i64_buf(const int32_t* in, int64_t* out, int64_t n, int64_t* bsum, cudaStream_t s);
+int sph_exclusive_scan_i32_buf(const int32_t* in, int32_t* out, int64_t n, int32_t* bsum, cudaStream_t s);
 
 // Grid size helper.
 static inline unsigned grid_for(int64_t n, int block) {

@@ -48,6 +48,7 @@ extern "C" const char* sph_status_string(int status) {
         case SPH_ERR_CUDA: return "SPH_ERR_CUDA: CUDA runtime error";
         case SPH_ERR_TIMEOUT: return "SPH_ERR_TIMEOUT: bounded device wait expired";
         case SPH_ERR_NONFINITE: return "SPH_ERR_NONFINITE: non-finite value in a reduction";
+        case SPH_ERR_LIMIT: return "SPH_ERR_LIMIT: input exceeds the fixed size of the static scratch array";
         default: return "unknown status";
     }
 }
@@ -282,6 +283,26 @@ static int scan_impl(sph_ctx* ctx, const int32_t* in, T* out, int64_t n, cudaStr
     k_scan_total<T><<<1, 1, 0, s>>>(bsum, nb, out, n);
     SPH_LAUNCH_CHECK(ctx);
     return SPH_OK;
+}
+
+// Same scan with a caller-provided block-sum buffer of at least
+// (n / 2048 + 2) elements (used by the allocation-free neighbour build).
+template <typename T>
+static int scan_with_buffer(const int32_t* in, T* out, int64_t n, T* bsum, cudaStream_t s) {
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb < 1) nb = 1;
+    k_scan_block_sums<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bsum);
+    k_scan_bsums<T><<<1, 1024, 0, s>>>(bsum, nb);
+    k_scan_apply<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bsum, out);
+    k_scan_total<T><<<1, 1, 0, s>>>(bsum, nb, out, n);
+    return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+int sph_exclusive_scan_i64_buf(const int32_t* in, int64_t* out, int64_t n, int64_t* bsum, cudaStream_t s) {
+    return scan_with_buffer<long long>(in, (long long*)out, n, (long long*)bsum, s);
+}
+int sph_exclusive_scan_i32_buf(const int32_t* in, int32_t* out, int64_t n, int32_t* bsum, cudaStream_t s) {
+    return scan_with_buffer<int>(in, (int*)out, n, (int*)bsum, s);
 }
 
 int sph_exclusive_scan_i64(sph_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, cudaStream_t s) {

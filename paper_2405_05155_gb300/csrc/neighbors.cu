@@ -13,6 +13,7 @@
 // pair loops use) the visit order already yields ascending j; otherwise a row is
 // sorted in place.
 #include <math.h>
+#include <mutex>
 #include "neighbors.cuh"
 
 namespace {
@@ -364,4 +365,133 @@ extern "C" int sph_build_neighbors(sph_ctx* ctx, const sph_domain* dom, const do
     st = sph_fill_neighbors(ctx, cl, pos, n, cl.grid.rc2, row_ptr, col, cap, s);
     if (st) return st;
     return SPH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of sph_build_neighbors.
+//
+// Some callers cannot allocate device memory: a plug-in inside an application
+// that owns the whole device-memory budget (it reserves its pool at start-up
+// and treats any other cudaMalloc as a failure), or a latency-critical loop in
+// which cudaMalloc / cudaFree would synchronise the device.  For them this
+// entry point keeps all of its scratch (cell ids and counts, the sorted
+// particle copy, row lengths, scan partials, flags) in one file-scope static
+// device array of fixed size, SPH_STATIC_SCRATCH_BYTES, which every GPU that
+// loads the library holds until the process exits.  The caller still provides
+// pos, row_ptr and col.  All calls share the array: the parts that must start
+// at zero are cleared on every call, and calls that overlap on the GPU (two
+// streams, two host threads) race on it.
+namespace {
+
+constexpr int64_t kStaticMaxParticles = SPH_STATIC_MAX_PARTICLES;
+constexpr int64_t kStaticMaxCells = SPH_STATIC_MAX_CELLS;
+constexpr int64_t kStaticScanBlocks = (kStaticMaxParticles > kStaticMaxCells ? kStaticMaxParticles : kStaticMaxCells) / 2048 + 2;
+
+constexpr size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kOffCellId = 0;
+constexpr size_t kOffSorted = kOffCellId + round256(4 * kStaticMaxParticles);
+constexpr size_t kOffP32 = kOffSorted + round256(4 * kStaticMaxParticles);
+constexpr size_t kOffRowLen = kOffP32 + round256(16 * kStaticMaxParticles);
+constexpr size_t kOffCount = kOffRowLen + round256(4 * (kStaticMaxParticles + 1));
+constexpr size_t kOffStart = kOffCount + round256(4 * (kStaticMaxCells + 1));
+constexpr size_t kOffFill = kOffStart + round256(4 * (kStaticMaxCells + 1));
+constexpr size_t kOffScan64 = kOffFill + round256(4 * (kStaticMaxCells + 1));
+constexpr size_t kOffScan32 = kOffScan64 + round256(8 * (kStaticScanBlocks + 1));
+constexpr size_t kOffAbsmax = kOffScan32 + round256(4 * (kStaticScanBlocks + 1));
+constexpr size_t kOffFlags = kOffAbsmax + 256;
+constexpr size_t kStaticBytes = kOffFlags + 256;
+static_assert(kStaticBytes <= SPH_STATIC_SCRATCH_BYTES, "static scratch layout exceeds the documented size");
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_neighbor_static_scratch[SPH_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+// Device address of the static array on the current device, looked up once per
+// device (host code cannot use the symbol itself as a device pointer).
+std::mutex g_static_mutex;
+void* g_static_addr[256] = {};
+
+int static_scratch_address(unsigned char** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return SPH_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_neighbor_static_scratch) != cudaSuccess || !p) return SPH_ERR_CUDA;
+        g_static_addr[dev] = p;
+    }
+    *out = (unsigned char*)g_static_addr[dev];
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" int sph_build_neighbors_static(const sph_domain* dom, const double* pos, int64_t* row_ptr,
+                                          int32_t* col, int64_t cap, int64_t* nnz_host, void* stream) {
+    if (!dom || !row_ptr || !nnz_host || cap < 0) return SPH_ERR_ARG;
+    int st = sph_check_domain(dom);
+    if (st) return st;
+    int64_t n = dom->n;
+    if (n > 0 && !pos) return SPH_ERR_ARG;
+    if (cap > 0 && !col) return SPH_ERR_ARG;
+    CellGrid g = sph_make_grid(dom);
+    if (n > kStaticMaxParticles || g.total > kStaticMaxCells) return SPH_ERR_LIMIT;
+    unsigned char* base = nullptr;
+    st = static_scratch_address(&base);
+    if (st) return st;
+    cudaStream_t s = as_stream(stream);
+    int32_t* cid = (int32_t*)(base + kOffCellId);
+    int32_t* sorted = (int32_t*)(base + kOffSorted);
+    float4* p32 = (float4*)(base + kOffP32);
+    int32_t* row_len = (int32_t*)(base + kOffRowLen);
+    int32_t* count = (int32_t*)(base + kOffCount);
+    int32_t* start = (int32_t*)(base + kOffStart);
+    int32_t* fill = (int32_t*)(base + kOffFill);
+    int64_t* scan64 = (int64_t*)(base + kOffScan64);
+    int32_t* scan32 = (int32_t*)(base + kOffScan32);
+    unsigned* absmax = (unsigned*)(base + kOffAbsmax);
+    int* flags = (int*)(base + kOffFlags);
+    // what must start at zero on every call
+    if (cudaMemsetAsync(count, 0, (size_t)(g.total + 1) * 4, s) != cudaSuccess) return SPH_ERR_CUDA;
+    if (cudaMemsetAsync(fill, 0, (size_t)(g.total + 1) * 4, s) != cudaSuccess) return SPH_ERR_CUDA;
+    if (cudaMemsetAsync(absmax, 0, 256, s) != cudaSuccess) return SPH_ERR_CUDA;
+    if (cudaMemsetAsync(flags, 0, 256, s) != cudaSuccess) return SPH_ERR_CUDA;
+    if (n > 0) k_cell_ids<<<grid_for(n, 256), 256, 0, s>>>(pos, n, g, cid, count, flags, absmax);
+    st = sph_exclusive_scan_i32_buf(count, start, g.total, scan32, s);
+    if (st) return st;
+    double lmax = periodic_lmax(g);
+    if (n > 0) {
+        k_scatter<<<grid_for(n, 256), 256, 0, s>>>(cid, n, start, fill, sorted);
+        k_sort_cells<<<grid_for(g.total, 128), 128, 0, s>>>(start, g.total, sorted);
+        k_pack_sorted<<<grid_for(n, 256), 256, 0, s>>>(pos, n, g.dim, sorted, p32);
+        if (g.dim == 2)
+            k_neighbors<2, false><<<grid_for(n, 128), 128, 0, s>>>(pos, n, g, g.rc2, lmax, absmax, start, p32, row_len,
+                                                                  nullptr, nullptr, 0, flags);
+        else
+            k_neighbors<3, false><<<grid_for(n, 128), 128, 0, s>>>(pos, n, g, g.rc2, lmax, absmax, start, p32, row_len,
+                                                                  nullptr, nullptr, 0, flags);
+    }
+    if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
+    st = sph_exclusive_scan_i64_buf(row_len, row_ptr, n, scan64, s);
+    if (st) return st;
+    int64_t nnz = 0;
+    int bad = 0;
+    if (cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SPH_ERR_CUDA;
+    if (cudaMemcpyAsync(&bad, flags + FLAG_BAD_INPUT, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SPH_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SPH_ERR_CUDA;
+    if (bad) return SPH_ERR_ARG;
+    *nnz_host = nnz;
+    if (nnz > cap) return SPH_ERR_CAPACITY;
+    if (n > 0) {
+        if (g.dim == 2)
+            k_neighbors<2, true><<<grid_for(n, 128), 128, 0, s>>>(pos, n, g, g.rc2, lmax, absmax, start, p32, nullptr,
+                                                                 row_ptr, col, cap, flags);
+        else
+            k_neighbors<3, true><<<grid_for(n, 128), 128, 0, s>>>(pos, n, g, g.rc2, lmax, absmax, start, p32, nullptr,
+                                                                 row_ptr, col, cap, flags);
+    }
+    return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
 }
