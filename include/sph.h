@@ -333,6 +333,37 @@ int sph_relax_accel(sph_ctx* ctx, const sph_relax_params* prm, const double* pos
 int sph_relax_residual(sph_ctx* ctx, const sph_relax_params* prm, const double* pos,
                        const double* vol, double* out_host, void* stream);
 
+/* ---- a12: learned relaxation proposal (not in the paper) ----
+ * A 128 -> 128 -> 128 -> 128 -> 3 multilayer perceptron with GELU (erf form)
+ * after each hidden layer predicts a particle's displacement / h from its
+ * features.  Parameters are one float32 array of SPH_MLP_NPARAM values in the
+ * order W1 [128][128] (out x in), b1 [128], W2, b2, W3, b3, W4 [3][128], b4 [3];
+ * the dense layers run on BF16 tensor cores (operands rounded to bfloat16,
+ * float32 accumulation).  Features (float32 [n][128]): the offsets
+ * (x_j - x_i)/h of the 32 nearest neighbours within the Laguerre-Gauss support
+ * 2h, ordered by (float64 squared distance, j), zero-filled, then phi_i/h, then
+ * zeros.  Loss: mean squared error over the batch and the 3 outputs.  Optimiser:
+ * Adam, beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected. */
+#define SPH_MLP_NPARAM 49923
+/* features of the particles in pos (float64 [3][n]); geometry and body from prm */
+int sph_mlp_features(sph_ctx* ctx, const sph_relax_params* prm, const double* pos,
+                     float* feats, void* stream);
+/* out [n][3] = network(feats [n][128]) */
+int sph_mlp_forward(sph_ctx* ctx, const float* params, const float* feats, float* out,
+                    int64_t n, void* stream);
+/* gradient (float32 [SPH_MLP_NPARAM]) of the loss over a batch of b rows against
+ * target [b][3]; *loss_host (nullable; if set the call synchronises) gets the loss */
+int sph_mlp_grad(sph_ctx* ctx, const float* params, const float* feats, const float* target,
+                 int64_t b, float* grad, double* loss_host, void* stream);
+/* one Adam step (step counts from 1) on params with moments adam_m, adam_v */
+int sph_mlp_train_step(sph_ctx* ctx, float* params, float* adam_m, float* adam_v,
+                       int64_t step, double lr, const float* feats, const float* target,
+                       int64_t b, double* loss_host, void* stream);
+/* proposal move: features at pos, forward, pos += h * out, then particles with
+ * phi > -dp/2 are moved along grad phi to phi = -dp/2 */
+int sph_relax_propose(sph_ctx* ctx, const sph_relax_params* prm, const float* params,
+                      double* pos, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -289,3 +289,57 @@ def relax_residual(ctx, prm, pos, vol):
     L.check("sph_relax_residual", ctx.lib.sph_relax_residual(ctx.h, ctypes.byref(prm), _p(pos), _p(vol), out,
                                                               _stream()), ctx.h)
     return out[0], out[1], int(out[2])
+
+
+# --------------------------------------------------------------------------- learned proposal
+MLP_NPARAM = L.SPH_MLP_NPARAM
+
+
+def mlp_features(ctx, prm, pos):
+    prm.dom.n = pos.shape[1]
+    feats = torch.empty((pos.shape[1], 128), dtype=torch.float32, device=pos.device)
+    L.check("sph_mlp_features", ctx.lib.sph_mlp_features(ctx.h, ctypes.byref(prm), _p(pos), _p(feats), _stream()),
+            ctx.h)
+    return feats
+
+
+def mlp_forward(ctx, params, feats):
+    out = torch.empty((feats.shape[0], 3), dtype=torch.float32, device=feats.device)
+    L.check("sph_mlp_forward", ctx.lib.sph_mlp_forward(ctx.h, _p(params), _p(feats), _p(out), feats.shape[0],
+                                                        _stream()), ctx.h)
+    return out
+
+
+def mlp_grad(ctx, params, feats, target, with_loss=True):
+    grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=feats.device)
+    loss = ctypes.c_double(float("nan"))
+    L.check("sph_mlp_grad", ctx.lib.sph_mlp_grad(ctx.h, _p(params), _p(feats), _p(target), feats.shape[0], _p(grad),
+                                                  ctypes.byref(loss) if with_loss else None, _stream()), ctx.h)
+    return grad, loss.value
+
+
+class MLPTrainer:
+    """float32 master parameters and Adam moments on the device."""
+
+    def __init__(self, ctx, params, lr=1e-3):
+        self.ctx = ctx
+        self.params = torch.as_tensor(params, dtype=torch.float32, device=ctx.device).contiguous().clone()
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step_count = 0
+        self.lr = lr
+
+    def step(self, feats, target, with_loss=False):
+        self.step_count += 1
+        loss = ctypes.c_double(float("nan"))
+        L.check("sph_mlp_train_step", self.ctx.lib.sph_mlp_train_step(
+            self.ctx.h, _p(self.params), _p(self.m), _p(self.v), self.step_count, float(self.lr), _p(feats),
+            _p(target), feats.shape[0], ctypes.byref(loss) if with_loss else None, _stream()), self.ctx.h)
+        return loss.value
+
+
+def relax_propose(ctx, prm, params, pos):
+    prm.dom.n = pos.shape[1]
+    L.check("sph_relax_propose", ctx.lib.sph_relax_propose(ctx.h, ctypes.byref(prm), _p(params), _p(pos),
+                                                            _stream()), ctx.h)
+    return pos

@@ -1,0 +1,116 @@
+"""GPU parity of the learned proposal (a12): features exact in ranking, BF16 tensor-core
+forward and backward within 1e-2 relative L2 of the float64 oracle, Adam training that
+lowers the loss like the oracle's, and the gain of the trained proposal."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import cuda, host, odom, rel_l2, sorted_by_cells
+from oracle import mlp as OM
+from oracle import neighbors as ON
+from oracle import relax as OR
+from paper_2405_05155_gb300 import api, inputs, learned
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def test_features_parity(ctx):
+    b = inputs.sphere_body(4, 1.0 / 24.0)
+    pos, _ = sorted_by_cells(b["pos"], b["domain"])
+    dom = odom(b["domain"])
+    rp, col = ON.neighbors_cells(pos, dom)
+    phi, _ = OR.sdf_spheres(pos, b["spheres"])
+    X_o = OM.features(pos, rp, col, dom, phi)
+    prm = api.relax_params(b["domain"], b["spheres"], b["dp"])
+    X = host(api.mlp_features(ctx, prm, cuda(pos)))
+    # same neighbours in the same order: offsets agree to float32 rounding
+    assert np.max(np.abs(X - X_o)) < 1e-6 * max(1.0, np.max(np.abs(X_o)))
+    assert np.array_equal(X[:, :96] == 0.0, X_o[:, :96] == 0.0)
+
+
+def _batch(seed, rows):
+    rng = np.random.default_rng(seed)
+    X = np.zeros((rows, 128))
+    X[:, :97] = rng.normal(scale=0.8, size=(rows, 97))
+    T = rng.normal(scale=0.05, size=(rows, 3))
+    return X, T
+
+
+@pytest.mark.parametrize("rows", [7, 256, 5000])
+def test_forward_parity(ctx, rows):
+    flat = inputs.mlp_init(1)
+    flat[OM.N_PARAM - 3:] = [0.01, -0.02, 0.03]
+    X, _ = _batch(2, rows)
+    y_o, _ = OM.forward(flat, X)
+    y = host(api.mlp_forward(ctx, cuda(flat, torch.float32), cuda(X, torch.float32)))
+    assert rel_l2(y, y_o) < 1e-2
+
+
+def test_gradient_parity_per_block(ctx):
+    flat = inputs.mlp_init(5)
+    X, T = _batch(6, 4096)
+    loss_o, g_o = OM.loss_and_grad(flat, X, T)
+    g, loss = api.mlp_grad(ctx, cuda(flat, torch.float32), cuda(X, torch.float32), cuda(T, torch.float32))
+    g = host(g)
+    assert abs(loss - loss_o) < 1e-2 * loss_o
+    off = 0
+    for name, shape in OM.SHAPES:
+        k = int(np.prod(shape))
+        assert rel_l2(g[off:off + k], g_o[off:off + k]) < 1e-2, name
+        off += k
+
+
+def test_adam_training_tracks_the_oracle(ctx):
+    flat = inputs.mlp_init(7)
+    X, _ = _batch(8, 2048)
+    # a smooth target the network can fit
+    T = np.stack([np.tanh(X[:, 0]), 0.5 * X[:, 1] * X[:, 2], np.sin(X[:, 96])], axis=1) * 0.1
+    trainer = api.MLPTrainer(ctx, flat, lr=1e-3)
+    Xd, Td = cuda(X, torch.float32), cuda(T, torch.float32)
+    gpu_losses = [trainer.step(Xd, Td, with_loss=True) for _ in range(60)]
+    w, m, v = flat.copy(), np.zeros_like(flat), np.zeros_like(flat)
+    cpu_losses = []
+    for k in range(60):
+        loss, g = OM.loss_and_grad(w, X, T)
+        cpu_losses.append(loss)
+        w, m, v = OM.adam(w, g, m, v, k + 1, 1e-3)
+    assert gpu_losses[-1] < 0.5 * gpu_losses[0]
+    assert abs(gpu_losses[-1] - cpu_losses[-1]) < 0.1 * cpu_losses[-1]
+    # the parameters moved the same way (Adam steps are ~lr in size; BF16 moves a few signs)
+    assert rel_l2(host(trainer.params) - flat, w - flat) < 0.2
+
+
+def test_trained_proposal_reduces_relaxation_steps(ctx):
+    # train on plain trajectories of a few small seeded bodies, then relax held-out bodies to
+    # the residual plain relaxation reaches after 200 steps, with and without the proposal
+    feats, targets = [], []
+    for seed in range(12):
+        f, t = learned.trajectory_samples(ctx, seed, 1.0 / 24.0, steps=300, every=50)
+        feats.append(f)
+        targets.append(t)
+    feats, targets = torch.cat(feats), torch.cat(targets)
+    trainer, losses = learned.train(ctx, feats, targets, steps=2000, batch=4096, lr=1e-3, log_every=500)
+    assert losses[-1][1] < 0.2 * losses[0][1]
+    gains = []
+    for seed in (1000, 1001, 1002):
+        b, prm, pos, vol = learned.body_on_device(ctx, seed, 1.0 / 24.0)
+        ref = pos.clone()
+        api.relax_step(ctx, prm, ref, vol, 20)
+        target = api.relax_residual(ctx, prm, ref, vol)[0]
+        p_plain = pos.clone()
+        n_plain, r_plain = learned.steps_to_target(ctx, prm, p_plain, vol, target, 200, check_every=1)
+        p_learn = pos.clone()
+        n_learn, r_learn, kept = learned.learned_relax(ctx, prm, trainer.params, p_learn, vol, target, 200,
+                                                       check_every=1)
+        assert r_plain <= target and r_learn <= target
+        gains.append((n_plain, n_learn, kept))
+    print("plain steps, learned-run plain steps, proposals kept:", gains)
+    # the proposal saves plain steps on every held-out body
+    assert all(nl < npl for npl, nl, _ in gains)
