@@ -120,6 +120,7 @@ int sph_get_lanes(const sph_ctx* ctx, int pass);
 #define SPH_TIMER_NEIGHBORS    6
 #define SPH_TIMER_RELAX_ACCEL  7
 #define SPH_TIMER_RELAX_UPDATE 8
+#define SPH_TIMER_BATCH_STEP   9  /* one replay of the captured batched step (2 launches) */
 #define SPH_TIMER_SLOTS        16
 int sph_timing_enable(sph_ctx* ctx, int on);
 int sph_timing_read(sph_ctx* ctx, int slot, double* total_ms_host, int64_t* launches_host);
@@ -248,6 +249,44 @@ int sph_eulerian_rates(sph_ctx* ctx, const sph_eulerian_params* prm,
 /* Advance nsteps time steps in place (drho/v for FP64, q for FP32). */
 int sph_eulerian_step(sph_ctx* ctx, const sph_eulerian_params* prm,
                       const sph_eulerian_state* st, int nsteps, void* stream);
+
+/* ---- a13: batched Eulerian step (not in the paper: many cases per launch) ----
+ * ncases independent Eulerian cases (the float32 two-pass step of
+ * sph_eulerian_step, Sec. 3.1) whose packed records and CSR lists are
+ * concatenated: case c owns particles [offset, offset + n) of geo/q/q_tmp, its
+ * CSR rows are rows offset..offset+n-1 of row_ptr and its column indices are
+ * global (already shifted by offset).  One persistent launch per pass covers
+ * all cases; the two launches of a step are captured into a CUDA graph once and
+ * replayed (the graph is recaptured when the buffers, case table or launch
+ * shape change).  Results match sph_eulerian_step on each case alone (to float32
+ * rounding: the two kernels may contract multiply-adds differently).
+ * cases_host is a host array of ncases (<= 256) entries, offsets contiguous
+ * from 0.  The launch shape is the context's SPH_PASS_BATCHED lanes and batch
+ * block size, chosen by sph_autotune_batched. */
+#define SPH_PASS_BATCHED 3
+typedef struct {
+    int64_t offset, n;
+    int32_t dim;
+    uint32_t periodic_mask;
+    double h, dt, rho0, c0, mu, eta;
+    double len[3];                  /* box lengths (minimum image on periodic axes) */
+} sph_batch_case;
+typedef struct {
+    const int64_t* row_ptr;         /* [N+1] */
+    const int32_t* col;             /* global indices */
+    float* geo;                     /* [N][8] (2D) or [N][16] (3D), sph_eulerian_state layout */
+    float* q;                       /* [N][4] */
+    float* q_tmp;                   /* [N][4] scratch */
+} sph_batch_state;
+int sph_eulerian_step_batched(sph_ctx* ctx, const sph_batch_case* cases_host, int ncases,
+                              const sph_batch_state* st, int nsteps, void* stream);
+/* Autotuner: times trial_steps steps for every launch shape (lanes per particle in
+ * {1, 2, 4, 8} x block size in {128, 256}) on the caller's data, restores the state
+ * after each trial, keeps the fastest shape in the context and returns it
+ * (lanes, block, ms per step; any output pointer may be NULL).  Synchronises. */
+int sph_autotune_batched(sph_ctx* ctx, const sph_batch_case* cases_host, int ncases,
+                         const sph_batch_state* st, int trial_steps, int* lanes_host,
+                         int* block_host, double* ms_host, void* stream);
 
 /* ---- a7-a9: total-Lagrangian SPH for solids (Sec. 3.2) ----
  * Reference configuration r0 with volumes V0, correction B0 (Eq. 9 at r0) and

@@ -18,7 +18,8 @@ SPH_WENDLAND_C2, SPH_LAGUERRE_GAUSS = 0, 1
 SPH_FP64, SPH_FP32_KAHAN = 0, 1
 SPH_TWO_PASS, SPH_FUSED = 0, 1
 SPH_SVK, SPH_NEO_HOOKEAN = 0, 1
-SPH_PASS_EULERIAN, SPH_PASS_TLSPH, SPH_PASS_RELAX = 0, 1, 2
+SPH_PASS_EULERIAN, SPH_PASS_TLSPH, SPH_PASS_RELAX, SPH_PASS_BATCHED = 0, 1, 2, 3
+SPH_TIMER_BATCH_STEP = 9
 SPH_MAX_SPHERES = 16
 (SPH_TIMER_TL_STRESS, SPH_TIMER_TL_MOMENTUM, SPH_TIMER_TL_DEFORM, SPH_TIMER_EU_MOMENTUM, SPH_TIMER_EU_MASS,
  SPH_TIMER_EU_FUSED, SPH_TIMER_NEIGHBORS, SPH_TIMER_RELAX_ACCEL, SPH_TIMER_RELAX_UPDATE) = range(9)
@@ -49,6 +50,16 @@ class TLParams(ctypes.Structure):
 class TLState(ctypes.Structure):
     _fields_ = [(name, c_vp) for name in ("row_ptr", "col", "r0", "V0", "B0", "fixed", "x", "v", "H", "M",
                                           "geo", "vq", "H32", "u32", "M32", "B32")]
+
+
+class BatchCase(ctypes.Structure):
+    _fields_ = [("offset", c_i64), ("n", c_i64), ("dim", c_i32), ("periodic_mask", ctypes.c_uint32),
+                ("h", c_dbl), ("dt", c_dbl), ("rho0", c_dbl), ("c0", c_dbl), ("mu", c_dbl), ("eta", c_dbl),
+                ("len", c_dbl * 3)]
+
+
+class BatchState(ctypes.Structure):
+    _fields_ = [(name, c_vp) for name in ("row_ptr", "col", "geo", "q", "q_tmp")]
 
 
 class RelaxParams(ctypes.Structure):
@@ -91,6 +102,9 @@ _SIGNATURES = {
     "sph_mlp_train_step": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_vp, c_vp, c_i64, _P(c_dbl),
                                           c_vp]),
     "sph_relax_propose": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, c_vp]),
+    "sph_eulerian_step_batched": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int, _P(BatchState), ctypes.c_int, c_vp]),
+    "sph_autotune_batched": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int, _P(BatchState), ctypes.c_int,
+                                            _P(ctypes.c_int), _P(ctypes.c_int), _P(c_dbl), c_vp]),
 }
 SPH_MLP_NPARAM = 49923
 

@@ -9,8 +9,8 @@ import torch
 
 from . import _lib as L
 from ._lib import (SPH_FP32_KAHAN, SPH_FP64, SPH_FUSED, SPH_LAGUERRE_GAUSS,  # noqa: F401
-                   SPH_NEO_HOOKEAN, SPH_SVK, SPH_TWO_PASS, SPH_WENDLAND_C2, SPH_PASS_EULERIAN,
-                   SPH_PASS_RELAX, SPH_PASS_TLSPH)
+                   SPH_NEO_HOOKEAN, SPH_SVK, SPH_TWO_PASS, SPH_WENDLAND_C2, SPH_PASS_BATCHED,
+                   SPH_PASS_EULERIAN, SPH_PASS_RELAX, SPH_PASS_TLSPH)
 
 NSYM = {2: 3, 3: 6}
 

@@ -14,6 +14,18 @@ struct TimerRec {
     cudaEvent_t start, stop;
 };
 
+// What a captured batched step depends on (compared bytewise; zero-initialise).
+struct BatchGraphKey {
+    const void* row_ptr;
+    const void* col;
+    const void* geo;
+    const void* q;
+    const void* q_tmp;
+    const void* dK;
+    int64_t ntotal;
+    int ncases, lanes, block, grid, dim, pad;
+};
+
 struct sph_ctx {
     // per-kernel timing (sph_timing_enable): events recorded around launches
     bool timing = false;
@@ -30,13 +42,19 @@ struct sph_ctx {
     int* flags = nullptr;          // device status words (see FLAG_*)
     void* pinned = nullptr;        // small pinned host buffer for read-backs
     int lanes[4] = {4, 4, 4, 4};   // lanes per particle of the float32 pair passes (SPH_PASS_*)
+    // batched Eulerian step: launch shape, captured graph and the case table it was made for
+    int batch_block = 256;
+    cudaGraphExec_t batch_graph = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    BatchGraphKey batch_key = {};
+    std::vector<unsigned char> batch_blob;
 };
 
 // scratch slots (each is a grow-only device buffer owned by the context)
 enum ScratchSlot {
     S_CELL_ID = 0, S_CELL_COUNT, S_CELL_START, S_CELL_FILL, S_SORTED, S_P32SORTED,
     S_ROW_LEN, S_SCAN_BLOCKS, S_ABSMAX, S_RELAX_ROWPTR, S_RELAX_COL, S_RELAX_ACC,
-    S_RELAX_AMAX, S_RED_PARTIAL, S_KGC_COUNT, S_MISC0, S_MISC1, S_MISC2, S_MISC3
+    S_RELAX_AMAX, S_RED_PARTIAL, S_KGC_COUNT, S_MISC0, S_MISC1, S_MISC2, S_MISC3, S_BATCH
 };
 
 // device status words

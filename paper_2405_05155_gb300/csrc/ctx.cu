@@ -32,6 +32,8 @@ extern "C" int sph_destroy(sph_ctx* ctx) {
     ctx->pending.clear();
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
     ctx->pool.clear();
+    if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     for (int i = 0; i < sph_ctx::kSlots; ++i)
         if (ctx->slot_ptr[i]) cudaFree(ctx->slot_ptr[i]);
     if (ctx->flags) cudaFree(ctx->flags);
