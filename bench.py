@@ -179,11 +179,13 @@ def _sum_over_ranks(x, world):
 def _alg_bytes_tl(n, nnz):
     """Algorithmic bytes of one float32 TL step, by pass (see the roofline notes in the design doc).
 
-    momentum pass:  row_ptr 8 + geo 32 + own M 48 + v read/write 32 per particle, col 4 per pair;
-    deformation pass: row_ptr 8 + geo 32 + v 16 + B0 24 + H read/write 72 + u read/write 24
-                      + M write 48 per particle, col 4 per pair."""
-    mom = n * (8 + 32 + 48 + 32) + 4 * nnz
-    defo = n * (8 + 32 + 16 + 24 + 72 + 24 + 48) + 4 * nnz
+    momentum pass:  row_ptr 8 + own RM record 64 + own velocity read/write 32 per particle,
+                    col 4 per pair;
+    deformation pass: row_ptr 8 + own RD record 32 + B0 24 + H read/write 72 + u read/write 24
+                      + M write 48 per particle, col 4 per pair.
+    Neighbour records (RM, RD) are counted once per particle: they are re-read from L1/L2."""
+    mom = n * (8 + 64 + 32) + 4 * nnz
+    defo = n * (8 + 32 + 24 + 72 + 24 + 48) + 4 * nnz
     return mom, defo
 
 
@@ -212,6 +214,178 @@ def _cpu_baseline(steps_cap_s=12.0):
             "sample": "float64 numpy oracle, plate at dp=0.004 m (%d particles, nnz=%d), %d time steps in %.1f s "
                       "(%.1f ms/step); single-threaded numpy" % (n, col.size, steps, el, 1e3 * el / steps),
             "ms_per_step": 1e3 * el / steps, "particles": n}
+
+
+# --------------------------------------------------------------------------- other rows
+def _event_ms(fn):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _roof(bytes_per_launch, ms_per_launch, peak):
+    gbs = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "algorithmic_bytes_per_launch": bytes_per_launch}
+
+
+def _eulerian_case(api, ctx, case, precision):
+    import torch
+    d = case["domain"]
+    dev = ctx.device
+    pos = torch.tensor(case["pos"], dtype=torch.float64, device=dev)
+    order = api.cell_order(ctx, d, pos)
+    pos = pos[:, order].contiguous()
+    oh = order.cpu().numpy()
+    vol = torch.tensor(case["vol"][oh], dtype=torch.float64, device=dev)
+    rp, col = api.build_neighbors(ctx, d, pos)
+    B, _, nfb = api.kgc(ctx, d, pos, vol, rp, col)
+    sim = api.Eulerian(ctx, d, pos, vol, B, rp, col, case["p"][oh] / case["c0"] ** 2, case["v"][:, oh], case["dt"],
+                       case["rho0"], case["c0"], case["mu"], precision=precision)
+    return sim, int(col.numel()), oh
+
+
+def _bench_tgv3d(api, inputs, ctx, steps, peak):
+    """3D Taylor-Green, 128^3 periodic cube, Re = 1600: float32 at 1.6h and 2h, float64 at 1.6h."""
+    import torch
+    from paper_2405_05155_gb300._lib import SPH_TIMER_EU_MASS, SPH_TIMER_EU_MOMENTUM
+    out = {"workload": "3D Eulerian WCSPH Taylor-Green vortex, periodic cube 2*pi, 128^3 = 2,097,152 particles, "
+                       "Re=1600, h=1.3dp, two-pass step, FP32+Kahan (and FP64)"}
+    res = {}
+    for kappa in (1.6, 2.0):
+        case = inputs.tgv3d(n=128, kappa=kappa)
+        sim, nnz, _ = _eulerian_case(api, ctx, case, api.SPH_FP32_KAHAN)
+        lanes, _ = sim.autotune(3)
+        sim.step(3)
+        ctx.timing(True)
+        ms = _event_ms(lambda: sim.step(steps))
+        tm, nm = ctx.timer(SPH_TIMER_EU_MOMENTUM)
+        tc, nc = ctx.timer(SPH_TIMER_EU_MASS)
+        ctx.timing(False)
+        n = sim.n
+        per_pass = n * (8 + 64 + 16 + 16) + 4 * nnz
+        dom_ms = max(tm / max(nm, 1), tc / max(nc, 1))
+        r = {"ms_per_step": ms / steps, "pair_interactions_per_s": 2 * nnz * steps / (ms * 1e-3), "nnz": nnz,
+             "lanes": lanes, "pass_ms": {"momentum": tm / max(nm, 1), "continuity": tc / max(nc, 1)},
+             "roofline": _roof(per_pass, dom_ms, peak)}
+        if kappa == 1.6:
+            d32, v32 = [t.clone() for t in sim.fields()]
+            sim64, _, _ = _eulerian_case(api, ctx, case, api.SPH_FP64)
+            sim64.step(3)
+            n64 = max(5, steps // 10)
+            ms64 = _event_ms(lambda: sim64.step(n64))
+            r["fp64_ms_per_step"] = ms64 / n64
+            # same number of steps from the same state for the error
+            sim64b, _, _ = _eulerian_case(api, ctx, case, api.SPH_FP64)
+            sim64b.step(3 + steps)
+            d64, v64 = sim64b.fields()
+            r["l2_fp32_vs_fp64"] = {"drho": float(torch.linalg.norm(d32 - d64) / torch.linalg.norm(d64)),
+                                    "v": float(torch.linalg.norm(v32 - v64) / torch.linalg.norm(v64))}
+            del sim64, sim64b
+        res["kappa_%.1f" % kappa] = r
+        del sim
+    out.update(res)
+    out["alpha_TW_over_SW"] = res["kappa_1.6"]["ms_per_step"] / res["kappa_2.0"]["ms_per_step"]
+    return out
+
+
+def _bench_tgv2d(api, inputs, ctx):
+    """Plain method: 2D Taylor-Green 50x50, FP64, 200 steps, TW and SW, error vs the closed form."""
+    import torch
+    out = {"workload": "2D Eulerian WCSPH Taylor-Green vortex, periodic unit square 50x50, Re=100, FP64, 200 steps"}
+    for kappa in (1.6, 2.0):
+        case = inputs.tgv2d(nx=50, kappa=kappa)
+        sim, nnz, oh = _eulerian_case(api, ctx, case, api.SPH_FP64)
+        ms = _event_ms(lambda: sim.step(200))
+        _, v = sim.fields()
+        t = 200 * case["dt"]
+        exact = torch.tensor(inputs.tgv2d_exact_velocity(case["pos"][:, oh], case["U"], case["nu"], t),
+                             device=ctx.device)
+        out["kappa_%.1f" % kappa] = {"ms_per_step": ms / 200, "pair_interactions_per_s": 2 * nnz * 200 / (ms * 1e-3),
+                                     "l2_v_vs_closed_form": float(torch.linalg.norm(v - exact) /
+                                                                  torch.linalg.norm(exact))}
+    out["matched_accuracy"] = (out["kappa_1.6"]["l2_v_vs_closed_form"] <= 1.1 * out["kappa_2.0"]["l2_v_vs_closed_form"])
+    return out
+
+
+def _bench_batched(api, inputs, ctx, steps, peak):
+    """64 uneven 2D Taylor-Green cases (64^2 .. 1024^2, Re in {100, 1000}) in one persistent launch per pass."""
+    from paper_2405_05155_gb300 import batch
+    from paper_2405_05155_gb300._lib import SPH_TIMER_BATCH_STEP
+    cases = inputs.batched_tgv2d(seed=0, ncases=64)
+    b = batch.EulerianBatch(ctx, cases)
+    lanes, block, _ = b.autotune(trial_steps=3)
+    b.step(10)
+    ctx.timing(True)
+    ms = _event_ms(lambda: b.step(steps))
+    tstep, nstep = ctx.timer(SPH_TIMER_BATCH_STEP)
+    ctx.timing(False)
+    per_step_bytes = 2 * (b.ntotal * (8 + 32 + 16 + 16) + 4 * b.nnz)
+    return {"workload": "64 independent 2D Taylor-Green cases, sides log-uniform 64..1024 (seed 0), "
+                        "Re in {100,1000}, kappa=1.6, FP32+Kahan, persistent launch per pass, CUDA graph",
+            "particles": b.ntotal, "nnz": b.nnz, "ms_per_step": ms / steps,
+            "pair_interactions_per_s": 2 * b.nnz * steps / (ms * 1e-3), "lanes": lanes, "block": block,
+            "roofline": _roof(per_step_bytes, tstep / max(nstep, 1), peak)}
+
+
+def _bench_relax(api, inputs, ctx, steps, peak):
+    """Laguerre-Gauss relaxation of the 8-sphere body at dp = 1/128 (float32 pair sums)."""
+    import torch
+    from paper_2405_05155_gb300 import learned
+    from paper_2405_05155_gb300._lib import SPH_TIMER_NEIGHBORS, SPH_TIMER_RELAX_ACCEL, SPH_TIMER_RELAX_UPDATE
+    b, prm, pos, vol = learned.body_on_device(ctx, 0, 1.0 / 128.0)
+    n = pos.shape[1]
+    r0 = api.relax_residual(ctx, prm, pos, vol)
+    api.relax_step(ctx, prm, pos, vol, 2)
+    ctx.timing(True)
+    ms = _event_ms(lambda: api.relax_step(ctx, prm, pos, vol, steps))
+    tn, nn = ctx.timer(SPH_TIMER_NEIGHBORS)
+    ta, na = ctx.timer(SPH_TIMER_RELAX_ACCEL)
+    tu, nu = ctx.timer(SPH_TIMER_RELAX_UPDATE)
+    ctx.timing(False)
+    r1 = api.relax_residual(ctx, prm, pos, vol)
+    # pairs per step: the LG neighbour count of the current positions
+    rp, col = api.build_neighbors(ctx, b["domain"], pos)
+    nnz = int(col.numel())
+    acc_bytes = n * (32 + 8 + 16) + 4 * nnz
+    return {"workload": "Laguerre-Gauss relaxation, union of 8 seeded spheres (seed 0), dp=1/128, h=1.3dp, "
+                        "cut-off 2h, jitter 0.25dp, FP32+Kahan pair sums, list rebuilt every step",
+            "particles": n, "nnz": nnz, "ms_per_step": ms / steps,
+            "pair_interactions_per_s": nnz * steps / (ms * 1e-3),
+            "ms_breakdown": {"neighbour_rebuild": tn / max(nn, 1), "accel_pass": ta / max(na, 1),
+                             "update": tu / max(nu, 1)},
+            "residual_lg": [r0[0], r1[0]], "residual_tw": [r0[1], r1[1]], "steps": 2 + steps,
+            "roofline_accel_pass": _roof(acc_bytes, ta / max(na, 1), peak)}
+
+
+def _bench_mlp(api, inputs, ctx, peak_tflops):
+    """BF16 tensor-core MLP: proposal forward over a 2.2M-row feature set, and training steps."""
+    import torch
+    from paper_2405_05155_gb300 import learned
+    b, prm, pos, vol = learned.body_on_device(ctx, 1, 1.0 / 128.0)
+    feats = api.mlp_features(ctx, prm, pos)
+    rows = feats.shape[0]
+    params = torch.tensor(inputs.mlp_init(0), dtype=torch.float32, device=ctx.device)
+    api.mlp_forward(ctx, params, feats)
+    ms = _event_ms(lambda: [api.mlp_forward(ctx, params, feats) for _ in range(5)]) / 5
+    flops = 2.0 * rows * (128 * 128 * 3 + 128 * 3)
+    tr = api.MLPTrainer(ctx, inputs.mlp_init(0))
+    x = feats[:4096].contiguous()
+    t = torch.zeros((4096, 3), dtype=torch.float32, device=ctx.device)
+    tr.step(x, t)
+    ms_tr = _event_ms(lambda: [tr.step(x, t) for _ in range(20)]) / 20
+    tflops = flops / (ms * 1e-3) / 1e12
+    return {"workload": "128-128-128-128-3 GELU MLP, BF16 mma.sync tensor cores, FP32 accumulate; forward over the "
+                        "features of a dp=1/128 body; Adam step at batch 4096",
+            "rows": rows, "forward_ms": ms, "forward_tflops": tflops, "train_step_ms_batch4096": ms_tr,
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": tflops / peak_tflops}}
 
 
 # --------------------------------------------------------------------------- arms
@@ -249,6 +423,8 @@ def run_gpu(args):
     if args.profile:
         # profiling driver: the headline workload only (setup, then W + K float32 steps)
         s = _setup_plate(api, inputs, ctx, args.kappa)
+        if args.lanes:
+            ctx.set_lanes(api.SPH_PASS_TLSPH, args.lanes)
         sol = _solid(api, ctx, s, api.SPH_FP64 if args.profile == "fp64" else api.SPH_FP32_KAHAN)
         sol.step(W + K)
         torch.cuda.synchronize()
@@ -260,6 +436,11 @@ def run_gpu(args):
     # headline: truncated kernel (1.6h), float32 + Kahan, per-kernel timing on
     s16 = _setup_plate(api, inputs, ctx, 1.6)
     sol = _solid(api, ctx, s16, api.SPH_FP32_KAHAN)
+    if args.lanes:
+        ctx.set_lanes(api.SPH_PASS_TLSPH, args.lanes)
+        lanes16 = args.lanes
+    else:
+        lanes16, _ = sol.autotune(10)
     sol.step(W)
     torch.cuda.synchronize()
     ctx.timing(True)
@@ -287,6 +468,8 @@ def run_gpu(args):
     # standard kernel (2h), same precision
     s20 = _setup_plate(api, inputs, ctx, 2.0)
     sol20 = _solid(api, ctx, s20, api.SPH_FP32_KAHAN)
+    lanes20 = args.lanes or sol20.autotune(10)[0]
+    ctx.set_lanes(api.SPH_PASS_TLSPH, lanes20)
     ms20, _ = _time_steps(ctx, sol20, K, W, world)
     _, v20, H20 = sol20.fields()
     tw_vs_sw = {"v": rl2(v32, v20), "H": rl2(H32, H20)}
@@ -334,6 +517,21 @@ def run_gpu(args):
     e2e_ms = _max_over_ranks(t0.elapsed_time(t1), world)
     e2e_value = _sum_over_ranks(pairs_step * e2e_steps, world) / (e2e_ms * 1e-3)
 
+    workloads = {}
+    if not args.headline_only:
+        peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+        bf16 = peaks.get("bf16_tflops", 1900.0)
+        for name, fn in (("tgv3d_128", lambda: _bench_tgv3d(api, inputs, ctx, args.other_steps, peak)),
+                         ("tgv2d_50_plain_fp64", lambda: _bench_tgv2d(api, inputs, ctx)),
+                         ("batched_64_tgv2d", lambda: _bench_batched(api, inputs, ctx, args.other_steps, peak)),
+                         ("relax_8spheres_dp128", lambda: _bench_relax(api, inputs, ctx, 50, peak)),
+                         ("mlp_proposal", lambda: _bench_mlp(api, inputs, ctx, bf16))):
+            try:
+                workloads[name] = fn()
+            except Exception as exc:      # report, do not hide: the headline line still prints
+                workloads[name] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+            torch.cuda.empty_cache()
+
     if rank == 0:
         cb = _cpu_baseline(steps_cap_s=args.cpu_seconds) if world == 1 and not args.no_cpu else None
         ws = s16["n"] * (32 + 16 + 36 + 12 + 48 + 24) + 8 * (s16["n"] + 1) + 4 * s16["nnz"]
@@ -345,7 +543,8 @@ def run_gpu(args):
                        "pairs_per_step": pairs_step, "kappa": 1.6, "kgc_fallbacks": s16["nfb"],
                        "l2_policy": "inputs larger than L2 (working set %.0f MB > 129 MB L2), no flush" % (ws / 2 ** 20),
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "lanes_per_particle": ctx.get_lanes(api.SPH_PASS_TLSPH)},
+                       "lanes_per_particle": lanes16, "lanes_per_particle_2h": lanes20,
+                       "launch_shape": "autotuned (sph_autotune_tlsph)" if not args.lanes else "fixed"},
             "kappa_2.0": {"ms_per_step": ms20 / K, "pair_interactions_per_s": 2 * s20["nnz"] * K / (ms20 * 1e-3),
                           "nnz": s20["nnz"]},
             "alpha_TW_over_SW": ms_step / (ms20 / K),
@@ -362,6 +561,7 @@ def run_gpu(args):
                             "device -> pinned host, through the C ABI"},
             "gpu_launches": n_mom + n_def + n_str,
             "clocks": clk,
+            "workloads": workloads,
         }
         if cb is not None:
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -385,6 +585,9 @@ def main():
     ap.add_argument("--profile", choices=["fp32", "fp64"], default=None,
                     help="run only the plate workload (setup + warmup + steps) for ncu captures")
     ap.add_argument("--kappa", type=float, default=1.6)
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per particle of the TL passes (0: tuned)")
+    ap.add_argument("--headline-only", action="store_true", help="skip the other rows' workloads")
+    ap.add_argument("--other-steps", type=int, default=100, help="timed steps of the other Eulerian workloads")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured for this build")
     args = ap.parse_args()

@@ -249,6 +249,14 @@ int sph_eulerian_rates(sph_ctx* ctx, const sph_eulerian_params* prm,
 /* Advance nsteps time steps in place (drho/v for FP64, q for FP32). */
 int sph_eulerian_step(sph_ctx* ctx, const sph_eulerian_params* prm,
                       const sph_eulerian_state* st, int nsteps, void* stream);
+/* Autotuner of the float32 passes (not in the paper: a launch parameter): times
+ * trial_steps steps of the caller's float32 state for lanes per particle in
+ * {1, 2, 4, 8}, restores q after every trial, stores the fastest setting in the
+ * context (SPH_PASS_EULERIAN) and returns it with its ms per step (outputs may be
+ * NULL).  Synchronises the stream. */
+int sph_autotune_eulerian(sph_ctx* ctx, const sph_eulerian_params* prm,
+                          const sph_eulerian_state* st, int trial_steps, int* lanes_host,
+                          double* ms_host, void* stream);
 
 /* ---- a13: batched Eulerian step (not in the paper: many cases per launch) ----
  * ncases independent Eulerian cases (the float32 two-pass step of
@@ -303,11 +311,16 @@ typedef struct {
 } sph_tlsph_params;
 
 /* FP64 arrays: x, v [dim][n]; H = F - I [dim*dim][n]; M scratch [dim*dim][n].
- * FP32 packed arrays (made by sph_tlsph_pack):
- *   geo [n][8]: 3D (xh, yh, zh, V0), (xl, yl, zl, fixed); 2D (xh, yh, xl, yl), (V0, fixed, 0, 0)
- *   vq  [n][4]: (v0, v1, v2 or 0, 0)
- *   H32 [dim*dim][n], u32 [dim][n] (x - r0), B32 [nsym][n]
- *   M32 [n][12] (3D: rows of M padded to 4) or [n][4] (2D). */
+ * FP32 packed records (made by sph_tlsph_pack; rd and rm 32-byte aligned):
+ *   rd [n][8]:  3D (ox, oy, oz, cell, vx, vy, vz, V0); 2D (ox, oy, cell, V0, vx, vy, 0, 0)
+ *   rm [n][16]: 3D (ox, oy, oz, cell, M00, M10, M20, V0, M01, M11, M21, 0, M02, M12, M22, 0)
+ *   rm [n][8]:  2D (ox, oy, cell, V0, M00, M10, M01, M11)
+ *   with M = P B0^T and a cell-relative position: per axis a grid of
+ *   n_a = min(max(1, floor(len_a/h)), 1023 (3D) or 32767 (2D)) cells of size
+ *   S_a = len_a/n_a, integer cell c_a packed into `cell` (10 or 15 bits per axis,
+ *   bit 30 set on clamped particles) and float offset o_a = x_a - lo_a - c_a S_a;
+ *   H32 [dim*dim][n], u32 [dim][n] (x - r0), B32 [nsym][n].
+ *   The float32 path needs at least 4 grid cells along a periodic axis. */
 typedef struct {
     const int64_t* row_ptr;
     const int32_t* col;
@@ -319,17 +332,16 @@ typedef struct {
     double* v;
     double* H;
     double* M;
-    float*  geo;
-    float*  vq;
+    float*  rd;
+    float*  rm;
     float*  H32;
     float*  u32;
-    float*  M32;
     float*  B32;
 } sph_tlsph_state;
 
 int sph_tlsph_pack(sph_ctx* ctx, const sph_tlsph_params* prm,
                    const sph_tlsph_state* st, void* stream);
-/* packed float32 (vq, H32, u32) -> float64 (v, H, x = r0 + u). */
+/* packed float32 (rd, H32, u32) -> float64 (v, H, x = r0 + u). */
 int sph_tlsph_unpack(sph_ctx* ctx, const sph_tlsph_params* prm,
                      const sph_tlsph_state* st, void* stream);
 /* Rates at the current state: dvdt float64 [dim][n] (Eq. 30 / rho0) and
@@ -338,6 +350,10 @@ int sph_tlsph_rates(sph_ctx* ctx, const sph_tlsph_params* prm,
                     const sph_tlsph_state* st, double* dvdt, double* dFdt, void* stream);
 int sph_tlsph_step(sph_ctx* ctx, const sph_tlsph_params* prm,
                    const sph_tlsph_state* st, int nsteps, void* stream);
+/* Autotuner of the float32 passes, as sph_autotune_eulerian (rd, rm, H32 and u32
+ * are restored after every trial; setting stored as SPH_PASS_TLSPH). */
+int sph_autotune_tlsph(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_state* st,
+                       int trial_steps, int* lanes_host, double* ms_host, void* stream);
 
 /* ---- a10/a11: Laguerre-Gauss particle relaxation (Sec. 2.3.2, Eqs. 7-8) ----
  * 3D only.  Body = union of n_spheres spheres (cx, cy, cz, r) given by value,

@@ -49,7 +49,7 @@ class TLParams(ctypes.Structure):
 
 class TLState(ctypes.Structure):
     _fields_ = [(name, c_vp) for name in ("row_ptr", "col", "r0", "V0", "B0", "fixed", "x", "v", "H", "M",
-                                          "geo", "vq", "H32", "u32", "M32", "B32")]
+                                          "rd", "rm", "H32", "u32", "B32")]
 
 
 class BatchCase(ctypes.Structure):
@@ -102,7 +102,11 @@ _SIGNATURES = {
     "sph_mlp_train_step": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_vp, c_vp, c_i64, _P(c_dbl),
                                           c_vp]),
     "sph_relax_propose": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, c_vp]),
-    "sph_eulerian_step_batched": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int, _P(BatchState), ctypes.c_int, c_vp]),
+    "sph_autotune_eulerian": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), ctypes.c_int,
+                                             _P(ctypes.c_int), _P(c_dbl), c_vp]),
+    "sph_autotune_tlsph": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), ctypes.c_int, _P(ctypes.c_int),
+                                          _P(c_dbl), c_vp]),
+    "sph_eulerian_step_batched":(ctypes.c_int, [c_vp, c_vp, ctypes.c_int, _P(BatchState), ctypes.c_int, c_vp]),
     "sph_autotune_batched": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int, _P(BatchState), ctypes.c_int,
                                             _P(ctypes.c_int), _P(ctypes.c_int), _P(c_dbl), c_vp]),
 }

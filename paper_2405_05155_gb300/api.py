@@ -176,6 +176,12 @@ class Eulerian:
     def step(self, nsteps=1):
         self._call("sph_eulerian_step", int(nsteps), _stream())
 
+    def autotune(self, trial_steps=10):
+        """Pick the fastest lanes-per-particle for the float32 passes (state restored)."""
+        lanes, ms = ctypes.c_int(), ctypes.c_double()
+        self._call("sph_autotune_eulerian", int(trial_steps), ctypes.byref(lanes), ctypes.byref(ms), _stream())
+        return lanes.value, ms.value
+
     def rates(self):
         drho_dt = torch.empty(self.n, dtype=torch.float64, device=self.ctx.device)
         dmom_dt = torch.empty((self.dim, self.n), dtype=torch.float64, device=self.ctx.device)
@@ -214,15 +220,14 @@ class TLSolid:
         self.H = (torch.zeros((d * d, self.n), dtype=torch.float64, device=dev) if H is None
                   else _dev_f64(H, dev).clone())
         self.M = torch.zeros((d * d, self.n), dtype=torch.float64, device=dev)
-        self.geo = torch.zeros(self.n * 8, dtype=torch.float32, device=dev)
-        self.vq = torch.zeros(self.n * 4, dtype=torch.float32, device=dev)
+        self.rd = torch.zeros(self.n * 8, dtype=torch.float32, device=dev)
+        self.rm = torch.zeros(self.n * (16 if d == 3 else 8), dtype=torch.float32, device=dev)
         self.H32 = torch.zeros(d * d * self.n, dtype=torch.float32, device=dev)
         self.u32 = torch.zeros(d * self.n, dtype=torch.float32, device=dev)
-        self.M32 = torch.zeros(self.n * (12 if d == 3 else 4), dtype=torch.float32, device=dev)
         self.B32 = torch.zeros(NSYM[d] * self.n, dtype=torch.float32, device=dev)
         self.st = L.TLState()
-        for name in ("row_ptr", "col", "r0", "V0", "B0", "fixed", "x", "v", "H", "M", "geo", "vq", "H32", "u32",
-                     "M32", "B32"):
+        for name in ("row_ptr", "col", "r0", "V0", "B0", "fixed", "x", "v", "H", "M", "rd", "rm", "H32", "u32",
+                     "B32"):
             setattr(self.st, name, getattr(self, name).data_ptr())
         if precision == SPH_FP32_KAHAN:
             self.pack()
@@ -239,6 +244,12 @@ class TLSolid:
 
     def step(self, nsteps=1):
         self._call("sph_tlsph_step", int(nsteps), _stream())
+
+    def autotune(self, trial_steps=10):
+        """Pick the fastest lanes-per-particle for the float32 passes (state restored)."""
+        lanes, ms = ctypes.c_int(), ctypes.c_double()
+        self._call("sph_autotune_tlsph", int(trial_steps), ctypes.byref(lanes), ctypes.byref(ms), _stream())
+        return lanes.value, ms.value
 
     def rates(self):
         d = self.dim

@@ -144,6 +144,22 @@ struct Kahan {
     __device__ __forceinline__ R value() const { return s - c; }
 };
 
+// Two compensated accumulators in one register pair, on Blackwell's paired
+// float32 instructions (FADD2/FFMA2): the same operations as Kahan above, with the
+// compensation kept negated so that every step is an add (s - t is fma(t, -1, s),
+// exact negation, one rounding).
+struct Kahan2 {
+    float2 s, cn;
+    __device__ __forceinline__ void init() { s = make_float2(0.0f, 0.0f); cn = s; }
+    __device__ __forceinline__ void add(float2 x) {
+        float2 y = __fadd2_rn(x, cn);
+        float2 t = __fadd2_rn(s, y);
+        cn = __fadd2_rn(__ffma2_rn(t, make_float2(-1.0f, -1.0f), s), y);
+        s = t;
+    }
+    __device__ __forceinline__ float2 value() const { return __fadd2_rn(s, cn); }
+};
+
 // Plain accumulator with the same interface (float64 path).
 template <typename R>
 struct Plain {

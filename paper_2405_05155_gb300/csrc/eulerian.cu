@@ -413,3 +413,52 @@ extern "C" int sph_eulerian_step(sph_ctx* ctx, const sph_eulerian_params* p, con
         SPH_CUDA(ctx, cudaMemcpyAsync(st->q, q0, n * sizeof(float4), cudaMemcpyDeviceToDevice, s));
     return SPH_OK;
 }
+
+// Autotuner of the float32 pair passes (lanes per particle in {1, 2, 4, 8}); the
+// packed state q is saved before and restored after every trial.
+extern "C" int sph_autotune_eulerian(sph_ctx* ctx, const sph_eulerian_params* p, const sph_eulerian_state* st,
+                                     int trial_steps, int* lanes_host, double* ms_host, void* stream) {
+    if (!ctx || trial_steps < 1) return SPH_ERR_ARG;
+    int r = check_params(p, st);
+    if (r) return r;
+    if (p->precision != SPH_FP32_KAHAN || !st->geo || !st->q || !st->q_tmp) return SPH_ERR_ARG;
+    int64_t n = p->dom.n;
+    if (n == 0) return SPH_OK;
+    cudaStream_t s = as_stream(stream);
+    size_t bq = (size_t)n * 16;
+    void* save = sph_scratch(ctx, S_MISC3, bq, &r);
+    if (r) return r;
+    SPH_CUDA(ctx, cudaMemcpyAsync(save, st->q, bq, cudaMemcpyDeviceToDevice, s));
+    cudaEvent_t e0, e1;
+    SPH_CUDA(ctx, cudaEventCreate(&e0));
+    SPH_CUDA(ctx, cudaEventCreate(&e1));
+    const int lanes_set[4] = {1, 2, 4, 8};
+    int keep = ctx->lanes[SPH_PASS_EULERIAN];
+    bool timing = ctx->timing;
+    ctx->timing = false;
+    double best = 1e300;
+    int bl = keep;
+    for (int li = 0; li < 4; ++li) {
+        ctx->lanes[SPH_PASS_EULERIAN] = lanes_set[li];
+        r = sph_eulerian_step(ctx, p, st, 1, stream);
+        if (r) break;
+        SPH_CUDA(ctx, cudaEventRecord(e0, s));
+        r = sph_eulerian_step(ctx, p, st, trial_steps, stream);
+        if (r) break;
+        SPH_CUDA(ctx, cudaEventRecord(e1, s));
+        SPH_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        SPH_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; bl = lanes_set[li]; }
+        SPH_CUDA(ctx, cudaMemcpyAsync(st->q, save, bq, cudaMemcpyDeviceToDevice, s));
+    }
+    ctx->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r) { ctx->lanes[SPH_PASS_EULERIAN] = keep; return r; }
+    ctx->lanes[SPH_PASS_EULERIAN] = bl;
+    if (lanes_host) *lanes_host = bl;
+    if (ms_host) *ms_host = best / trial_steps;
+    SPH_CUDA(ctx, cudaStreamSynchronize(s));
+    return SPH_OK;
+}

@@ -21,6 +21,8 @@ struct TLK {
     R inv_rho0, dt, lam, G;
     int law;
     R half[3], Lh[3], Ll[3];
+    R S[3];              // float32 path: cell size of the cell-relative position encoding
+    int ncell[3];
     uint32_t periodic;
 };
 
@@ -256,59 +258,75 @@ __global__ void k_tl_defo64(const double* __restrict__ r0, const double* __restr
 }
 
 // ---------------------------------------------------------------- float32 path
-template <int DIM>
-__device__ __forceinline__ void load_geo(const float4* __restrict__ geo, int64_t i, float* xh, float* xl, float& V,
-                                         float& fx) {
-    float4 a = __ldg(&geo[2 * i]);
-    float4 b = __ldg(&geo[2 * i + 1]);
-    if (DIM == 2) { xh[0] = a.x; xh[1] = a.y; xl[0] = a.z; xl[1] = a.w; V = b.x; fx = b.y; }
-    else { xh[0] = a.x; xh[1] = a.y; xh[2] = a.z; V = a.w; xl[0] = b.x; xl[1] = b.y; xl[2] = b.z; fx = b.w; }
+// Each neighbour record is a 32-byte line read with one 256-bit load:
+//   RD [n][8]   3D (ox, oy, oz, cell, vx, vy, vz, V0)   2D (ox, oy, cell, V0, vx, vy, 0, 0)
+//   RM [n][16]  3D (ox, oy, oz, cell, M00, M10, M20, V0, M01, M11, M21, 0, M02, M12, M22, 0)
+//   RM [n][8]   2D (ox, oy, cell, V0, M00, M10, M01, M11)
+// Positions are cell-relative: x = lo + c S + o with an integer cell c per axis
+// (packed into `cell`, 10 bits per axis in 3D, 15 in 2D; bit 30 = clamped) and
+// a float32 offset o in [0, S).  r_ij = (c_i - c_j) S + (o_i - o_j) is then
+// accurate to float32 rounding of r itself in any box, with half the bytes of a
+// split hi+lo position.  The deformation pass gathers RD (position, velocity,
+// volume) and the momentum pass RM (position, M = P B0^T by columns, volume).
+constexpr uint32_t kFixedBit = 1u << 30;
+
+struct __align__(32) F8 {
+    float v[8];
+};
+
+// 256-bit read-only gather (the record is not written during the kernel).
+__device__ __forceinline__ F8 ldg8(const float* p) {
+    F8 r;
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]),
+          "=f"(r.v[7])
+        : "l"(p));
+    return r;
 }
 
 template <int DIM>
-__device__ __forceinline__ void load_M(const float4* __restrict__ M, int64_t i, float* m) {
-    if (DIM == 2) {
-        float4 a = __ldg(&M[i]);
-        m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w;
-    } else {
-        float4 a = __ldg(&M[3 * i]), b = __ldg(&M[3 * i + 1]), c = __ldg(&M[3 * i + 2]);
-        m[0] = a.x; m[1] = a.y; m[2] = a.z;
-        m[3] = b.x; m[4] = b.y; m[5] = b.z;
-        m[6] = c.x; m[7] = c.y; m[8] = c.z;
-    }
+__device__ __forceinline__ int cell_of(uint32_t bits, int a) {
+    return DIM == 3 ? (int)((bits >> (10 * a)) & 1023u) : (int)((bits >> (15 * a)) & 32767u);
 }
 
-template <int DIM>
-__device__ __forceinline__ void store_M(float4* M, int64_t i, const float* m) {
-    if (DIM == 2) {
-        M[i] = make_float4(m[0], m[1], m[2], m[3]);
-    } else {
-        M[3 * i] = make_float4(m[0], m[1], m[2], 0.0f);
-        M[3 * i + 1] = make_float4(m[3], m[4], m[5], 0.0f);
-        M[3 * i + 2] = make_float4(m[6], m[7], m[8], 0.0f);
-    }
-}
-
-template <int DIM>
-__device__ __forceinline__ void pair_r32(const float* xhi, const float* xli, const float* xhj, const float* xlj,
+template <int DIM, bool PER>
+__device__ __forceinline__ void pair_rel(const float* oi, uint32_t bi, const float* oj, uint32_t bj,
                                          const TLK<float>& K, float* r, float& d2) {
     d2 = 0.0f;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        float dh = xhi[a] - xhj[a];
-        float dl = xli[a] - xlj[a];
-        if ((K.periodic >> a) & 1u) {
-            if (dh > K.half[a]) { dh -= K.Lh[a]; dl -= K.Ll[a]; }
-            else if (dh < -K.half[a]) { dh += K.Lh[a]; dl += K.Ll[a]; }
+        int dc = cell_of<DIM>(bi, a) - cell_of<DIM>(bj, a);
+        if (PER && ((K.periodic >> a) & 1u)) {
+            if (2 * dc > K.ncell[a]) dc -= K.ncell[a];
+            else if (2 * dc < -K.ncell[a]) dc += K.ncell[a];
         }
-        r[a] = dh + dl;
+        r[a] = fmaf((float)dc, K.S[a], oi[a] - oj[a]);
         d2 = fmaf(r[a], r[a], d2);
+    }
+}
+
+// Wendland gradient factor gs = (dW/dr)/r from d^2 (q = sqrt(d2)/h, no division).
+__device__ __forceinline__ float gs_from_d2(float d2, const TLK<float>& K) {
+    float q = d2 * rsqrtf(fmaxf(d2, 1e-30f)) * K.inv_h;
+    float t = fmaf(-0.5f, q, 1.0f);
+    return K.coef * t * t * t;
+}
+
+template <int DIM>
+__device__ __forceinline__ void store_M(float* RM, int64_t i, const float* m) {
+    if (DIM == 2) {
+        *reinterpret_cast<float4*>(RM + 8 * i + 4) = make_float4(m[0], m[2], m[1], m[3]);
+    } else {
+        float* rec = RM + 16 * i;
+        rec[4] = m[0]; rec[5] = m[3]; rec[6] = m[6];
+        *reinterpret_cast<float4*>(rec + 8) = make_float4(m[1], m[4], m[7], 0.0f);
+        *reinterpret_cast<float4*>(rec + 12) = make_float4(m[2], m[5], m[8], 0.0f);
     }
 }
 
 template <int DIM>
 __global__ void k_tl_stress32(const float* __restrict__ H, const float* __restrict__ B0, int64_t n, TLK<float> K,
-                              float4* __restrict__ M) {
+                              float* __restrict__ RM) {
     constexpr int NS = DIM == 2 ? 3 : 6;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -316,97 +334,176 @@ __global__ void k_tl_stress32(const float* __restrict__ H, const float* __restri
     for (int k = 0; k < DIM * DIM; ++k) h[k] = H[k * n + i];
     for (int s = 0; s < NS; ++s) b[s] = B0[s * n + i];
     stress_factor<DIM, float>(h, b, K, m);
-    store_M<DIM>(M, i, m);
+    store_M<DIM>(RM, i, m);
 }
 
-template <int DIM, int OUT, int LANES>
-__global__ void __launch_bounds__(256) k_tl_mom32(const float4* __restrict__ geo, const int64_t* __restrict__ row_ptr,
-                                                  const int32_t* __restrict__ col, int64_t n, TLK<float> K,
-                                                  const float4* __restrict__ M, float4* __restrict__ vq,
-                                                  double* __restrict__ dvdt) {
+// Momentum pass (Eq. 30).  The next neighbour's record is loaded before the
+// current pair is evaluated.
+template <int DIM, int OUT, int LANES, bool PER>
+__global__ void __launch_bounds__(256, 4) k_tl_mom32(const float* __restrict__ RM, float* __restrict__ RD,
+                                                     const int64_t* __restrict__ row_ptr,
+                                                     const int32_t* __restrict__ col, int64_t n, TLK<float> K,
+                                                     double* __restrict__ dvdt) {
+    constexpr int W = DIM == 3 ? 16 : 8;
     int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = gt / LANES;
     int lane = (int)(gt % LANES);
     bool active = i < n;
     int64_t ii = active ? i : 0;
-    float xhi[DIM], xli[DIM], Vi, fx, Mi[DIM * DIM];
-    load_geo<DIM>(geo, ii, xhi, xli, Vi, fx);
-    load_M<DIM>(M, ii, Mi);
-    Kahan<float> acc[DIM];
+    F8 a0 = ldg8(RM + W * ii);
+    F8 a1 = DIM == 3 ? ldg8(RM + W * ii + 8) : a0;
+    float oi[DIM];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) acc[a].init();
-    int64_t b = active ? row_ptr[ii] : 0, e = active ? row_ptr[ii + 1] : 0;
-    for (int64_t p = b + lane; p < e; p += LANES) {
-        int j = __ldg(&col[p]);
-        float xhj[DIM], xlj[DIM], Vj, fj, Mj[DIM * DIM];
-        load_geo<DIM>(geo, j, xhj, xlj, Vj, fj);
-        load_M<DIM>(M, j, Mj);
-        float r[DIM], d2;
-        pair_r32<DIM>(xhi, xli, xhj, xlj, K, r, d2);
-        float gs = wendland_gs<float>(sqrtf(d2) * K.inv_h, K.coef) * Vj;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            float s = 0.0f;
-#pragma unroll
-            for (int c = 0; c < DIM; ++c) s = fmaf(Mi[a * DIM + c] + Mj[a * DIM + c], gs * r[c], s);
-            acc[a].add(s);
-        }
+    for (int a = 0; a < DIM; ++a) oi[a] = a0.v[a];
+    uint32_t bi = __float_as_uint(a0.v[DIM]);
+    // own M by columns
+    float2 mi01[DIM];
+    float mi2[3] = {0.0f, 0.0f, 0.0f};
+    if (DIM == 2) {
+        mi01[0] = make_float2(a0.v[4], a0.v[5]);
+        mi01[1] = make_float2(a0.v[6], a0.v[7]);
+    } else {
+        mi01[0] = make_float2(a0.v[4], a0.v[5]); mi2[0] = a0.v[6];
+        mi01[1] = make_float2(a1.v[0], a1.v[1]); mi2[1] = a1.v[2];
+        mi01[DIM - 1] = make_float2(a1.v[4], a1.v[5]); mi2[2] = a1.v[6];
     }
-    float tot[DIM];
+    Kahan2 acc01;
+    Kahan<float> acc2;
+    acc01.init();
+    acc2.init();
+    int64_t b = active ? row_ptr[ii] : 0, e = active ? row_ptr[ii + 1] : 0;
+    int64_t p = b + lane;
+    int j = p < e ? __ldg(&col[p]) : -1;
+    F8 r0 = a0, r1 = a1;
+    if (j >= 0) {
+        r0 = ldg8(RM + W * (int64_t)j);
+        if (DIM == 3) r1 = ldg8(RM + W * (int64_t)j + 8);
+    }
+    while (j >= 0) {
+        int64_t pn = p + LANES;
+        int jn = pn < e ? __ldg(&col[pn]) : -1;
+        F8 n0 = r0, n1 = r1;
+        if (jn >= 0) {
+            n0 = ldg8(RM + W * (int64_t)jn);
+            if (DIM == 3) n1 = ldg8(RM + W * (int64_t)jn + 8);
+        }
+        float oj[DIM], r[DIM], d2;
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) tot[a] = group_sum<LANES>(acc[a].value());
+        for (int a = 0; a < DIM; ++a) oj[a] = r0.v[a];
+        pair_rel<DIM, PER>(oi, bi, oj, __float_as_uint(r0.v[DIM]), K, r, d2);
+        float Vj = DIM == 3 ? r0.v[7] : r0.v[3];
+        float gs = gs_from_d2(d2, K) * Vj;
+        if (DIM == 2) {
+            float2 c0 = __fadd2_rn(mi01[0], make_float2(r0.v[4], r0.v[5]));
+            float2 c1 = __fadd2_rn(mi01[1], make_float2(r0.v[6], r0.v[7]));
+            float g0 = gs * r[0], g1 = gs * r[1];
+            acc01.add(__ffma2_rn(c1, make_float2(g1, g1), __fmul2_rn(c0, make_float2(g0, g0))));
+        } else {
+            float g0 = gs * r[0], g1 = gs * r[1], g2 = gs * r[DIM - 1];
+            float2 s0 = __fadd2_rn(mi01[0], make_float2(r0.v[4], r0.v[5]));
+            float2 s1 = __fadd2_rn(mi01[1], make_float2(r1.v[0], r1.v[1]));
+            float2 s2 = __fadd2_rn(mi01[DIM - 1], make_float2(r1.v[4], r1.v[5]));
+            float2 t01 = __ffma2_rn(s2, make_float2(g2, g2),
+                                    __ffma2_rn(s1, make_float2(g1, g1), __fmul2_rn(s0, make_float2(g0, g0))));
+            float t2 = fmaf(mi2[2] + r1.v[6], g2, fmaf(mi2[1] + r1.v[2], g1, (mi2[0] + r0.v[6]) * g0));
+            acc01.add(t01);
+            acc2.add(t2);
+        }
+        p = pn;
+        j = jn;
+        r0 = n0;
+        r1 = n1;
+    }
+    float2 v01 = acc01.value();
+    float tot[3] = {group_sum<LANES>(v01.x), group_sum<LANES>(v01.y), 0.0f};
+    if (DIM == 3) tot[2] = group_sum<LANES>(acc2.value());
     if (!active || lane != 0) return;
     if (OUT == OUT_RATES) {
         for (int a = 0; a < DIM; ++a) dvdt[a * n + i] = (double)(tot[a] * K.inv_rho0);
         return;
     }
-    float4 vv = vq[i];
-    float vn[3] = {vv.x, vv.y, vv.z};
+    bool fx = (bi & kFixedBit) != 0;
+    float* vrec = RD + 8 * i + 4;
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) vn[a] = fx != 0.0f ? 0.0f : vn[a] + K.dt * (tot[a] * K.inv_rho0);
-    vq[i] = make_float4(vn[0], vn[1], DIM == 3 ? vn[2] : 0.0f, 0.0f);
+    for (int a = 0; a < DIM; ++a) vrec[a] = fx ? 0.0f : vrec[a] + K.dt * (tot[a] * K.inv_rho0);
 }
 
-template <int DIM, int OUT, int LANES>
-__global__ void __launch_bounds__(256) k_tl_defo32(const float4* __restrict__ geo, const int64_t* __restrict__ row_ptr,
-                                                   const int32_t* __restrict__ col, int64_t n, TLK<float> K,
-                                                   const float4* __restrict__ vq, const float* __restrict__ B0,
-                                                   float* __restrict__ H, float* __restrict__ u,
-                                                   float4* __restrict__ M, double* __restrict__ dFdt) {
+// Deformation-rate pass (Eq. 31) with the fused stress update of the next step.
+// L = sum_j V0_j (v_j - v_i) (x) g_ij is accumulated column by column: rows 0-1 of
+// each column in one paired compensated accumulator, row 2 of columns 0-1 in a
+// second pair and L22 in a scalar one.
+template <int DIM, int OUT, int LANES, bool PER>
+__global__ void __launch_bounds__(256, 4) k_tl_defo32(const float* __restrict__ RD, float* __restrict__ RM,
+                                                      const int64_t* __restrict__ row_ptr,
+                                                      const int32_t* __restrict__ col, int64_t n, TLK<float> K,
+                                                      const float* __restrict__ B0, float* __restrict__ H,
+                                                      float* __restrict__ u, double* __restrict__ dFdt) {
     constexpr int NS = DIM == 2 ? 3 : 6;
     int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = gt / LANES;
     int lane = (int)(gt % LANES);
     bool active = i < n;
     int64_t ii = active ? i : 0;
-    float xhi[DIM], xli[DIM], Vi, fx, vi[DIM];
-    load_geo<DIM>(geo, ii, xhi, xli, Vi, fx);
-    float4 vv = __ldg(&vq[ii]);
-    vi[0] = vv.x; vi[1] = vv.y;
-    if (DIM == 3) vi[DIM - 1] = vv.z;
-    Kahan<float> L[DIM * DIM];
+    F8 me = ldg8(RD + 8 * ii);
+    float oi[DIM];
 #pragma unroll
-    for (int k = 0; k < DIM * DIM; ++k) L[k].init();
+    for (int a = 0; a < DIM; ++a) oi[a] = me.v[a];
+    uint32_t bi = __float_as_uint(me.v[DIM]);
+    float2 nv01 = make_float2(-me.v[4], -me.v[5]);
+    float nv2 = -me.v[6];
+    Kahan2 c01[DIM];          // (L0c, L1c) for column c
+    Kahan2 r2;                // (L20, L21)
+    Kahan<float> l22;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) c01[c].init();
+    r2.init();
+    l22.init();
     int64_t b = active ? row_ptr[ii] : 0, e = active ? row_ptr[ii + 1] : 0;
-    for (int64_t p = b + lane; p < e; p += LANES) {
-        int j = __ldg(&col[p]);
-        float xhj[DIM], xlj[DIM], Vj, fj;
-        load_geo<DIM>(geo, j, xhj, xlj, Vj, fj);
-        float4 vjv = __ldg(&vq[j]);
-        float vj[3] = {vjv.x, vjv.y, vjv.z};
-        float r[DIM], d2;
-        pair_r32<DIM>(xhi, xli, xhj, xlj, K, r, d2);
-        float gs = wendland_gs<float>(sqrtf(d2) * K.inv_h, K.coef);
+    int64_t p = b + lane;
+    int j = p < e ? __ldg(&col[p]) : -1;
+    F8 rj = me;
+    if (j >= 0) rj = ldg8(RD + 8 * (int64_t)j);
+    while (j >= 0) {
+        int64_t pn = p + LANES;
+        int jn = pn < e ? __ldg(&col[pn]) : -1;
+        F8 rn = rj;
+        if (jn >= 0) rn = ldg8(RD + 8 * (int64_t)jn);
+        float oj[DIM], r[DIM], d2;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            float dv = Vj * (vj[a] - vi[a]);
-#pragma unroll
-            for (int c = 0; c < DIM; ++c) L[a * DIM + c].add(dv * (gs * r[c]));
+        for (int a = 0; a < DIM; ++a) oj[a] = rj.v[a];
+        pair_rel<DIM, PER>(oi, bi, oj, __float_as_uint(rj.v[DIM]), K, r, d2);
+        float w = DIM == 3 ? rj.v[7] : rj.v[3];
+        float gs = gs_from_d2(d2, K);
+        float2 dv01 = __fmul2_rn(make_float2(w, w), __fadd2_rn(make_float2(rj.v[4], rj.v[5]), nv01));
+        if (DIM == 2) {
+            c01[0].add(__fmul2_rn(dv01, make_float2(gs * r[0], gs * r[0])));
+            c01[1].add(__fmul2_rn(dv01, make_float2(gs * r[1], gs * r[1])));
+        } else {
+            float g0 = gs * r[0], g1 = gs * r[1], g2 = gs * r[DIM - 1];
+            float dv2 = w * (rj.v[6] + nv2);
+            c01[0].add(__fmul2_rn(dv01, make_float2(g0, g0)));
+            c01[1].add(__fmul2_rn(dv01, make_float2(g1, g1)));
+            c01[DIM - 1].add(__fmul2_rn(dv01, make_float2(g2, g2)));
+            r2.add(__fmul2_rn(make_float2(dv2, dv2), make_float2(g0, g1)));
+            l22.add(dv2 * g2);
         }
+        p = pn;
+        j = jn;
+        rj = rn;
     }
     float Lt[DIM * DIM];
 #pragma unroll
-    for (int k = 0; k < DIM * DIM; ++k) Lt[k] = group_sum<LANES>(L[k].value());
+    for (int c = 0; c < DIM; ++c) {
+        float2 v = c01[c].value();
+        Lt[0 * DIM + c] = group_sum<LANES>(v.x);
+        Lt[1 * DIM + c] = group_sum<LANES>(v.y);
+    }
+    if (DIM == 3) {
+        float2 v = r2.value();
+        Lt[2 * DIM + 0] = group_sum<LANES>(v.x);
+        Lt[2 * DIM + 1] = group_sum<LANES>(v.y);
+        Lt[2 * DIM + 2] = group_sum<LANES>(l22.value());
+    }
     if (!active || lane != 0) return;
     float b0[NS], Fd[DIM * DIM];
 #pragma unroll
@@ -416,62 +513,97 @@ __global__ void __launch_bounds__(256) k_tl_defo32(const float4* __restrict__ ge
         for (int k = 0; k < DIM * DIM; ++k) dFdt[k * n + i] = (double)Fd[k];
         return;
     }
+    bool fx = (bi & kFixedBit) != 0;
     float h[DIM * DIM], m[DIM * DIM];
 #pragma unroll
     for (int k = 0; k < DIM * DIM; ++k) {
-        h[k] = fx != 0.0f ? 0.0f : H[k * n + i] + K.dt * Fd[k];
+        h[k] = fx ? 0.0f : H[k * n + i] + K.dt * Fd[k];
         H[k * n + i] = h[k];
     }
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) u[a * n + i] += K.dt * vi[a];
+    for (int a = 0; a < DIM; ++a) u[a * n + i] += K.dt * me.v[4 + a];
     stress_factor<DIM, float>(h, b0, K, m);
-    store_M<DIM>(M, i, m);
+    store_M<DIM>(RM, i, m);
 }
 
 // ---------------------------------------------------------------- pack / unpack
+struct RelGrid {
+    double lo[3], len[3], S[3];
+    int n[3];
+    uint32_t periodic;
+};
+
+RelGrid make_rel_grid(const sph_domain& d) {
+    RelGrid g;
+    int nmax = d.dim == 3 ? 1023 : 32767;
+    g.periodic = d.periodic_mask;
+    for (int a = 0; a < 3; ++a) {
+        if (a < d.dim) {
+            double m = floor(d.len[a] / d.h);
+            if (m < 1.0) m = 1.0;
+            if (m > nmax) m = nmax;
+            g.n[a] = (int)m;
+            g.lo[a] = d.lo[a];
+            g.len[a] = d.len[a];
+            g.S[a] = d.len[a] / m;
+        } else {
+            g.n[a] = 1; g.lo[a] = 0.0; g.len[a] = 1.0; g.S[a] = 1.0;
+        }
+    }
+    return g;
+}
+
 template <int DIM>
 __global__ void k_tl_pack(const double* __restrict__ r0, const double* __restrict__ V0,
                           const double* __restrict__ B0, const uint8_t* __restrict__ fixed,
                           const double* __restrict__ x, const double* __restrict__ v,
-                          const double* __restrict__ H, int64_t n, float* __restrict__ geo,
-                          float4* __restrict__ vq, float* __restrict__ H32, float* __restrict__ u32,
+                          const double* __restrict__ H, int64_t n, RelGrid g, float* __restrict__ RD,
+                          float* __restrict__ RM, float* __restrict__ H32, float* __restrict__ u32,
                           float* __restrict__ B32) {
     constexpr int NS = DIM == 2 ? 3 : 6;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float xh[3] = {0, 0, 0}, xl[3] = {0, 0, 0};
+    float o[3] = {0, 0, 0};
+    uint32_t bits = 0;
     for (int a = 0; a < DIM; ++a) {
-        double xv = r0[a * n + i];
-        xh[a] = (float)xv;
-        xl[a] = (float)(xv - (double)xh[a]);
+        double rel = r0[a * n + i] - g.lo[a];
+        double c = floor(rel / g.S[a]);
+        if (((g.periodic >> a) & 1u) && c >= g.n[a]) { rel -= g.len[a]; c = floor(rel / g.S[a]); }
+        if (c < 0.0) c = 0.0;
+        if (c > g.n[a] - 1) c = g.n[a] - 1;
+        o[a] = (float)(rel - c * g.S[a]);
+        bits |= (uint32_t)c << (DIM == 3 ? 10 * a : 15 * a);
     }
-    float fx = (fixed && fixed[i]) ? 1.0f : 0.0f;
-    float* g = geo + 8 * i;
-    if (DIM == 2) {
-        g[0] = xh[0]; g[1] = xh[1]; g[2] = xl[0]; g[3] = xl[1];
-        g[4] = (float)V0[i]; g[5] = fx; g[6] = 0.0f; g[7] = 0.0f;
-    } else {
-        g[0] = xh[0]; g[1] = xh[1]; g[2] = xh[2]; g[3] = (float)V0[i];
-        g[4] = xl[0]; g[5] = xl[1]; g[6] = xl[2]; g[7] = fx;
-    }
+    if (fixed && fixed[i]) bits |= kFixedBit;
+    float V = (float)V0[i];
     float vv[3] = {0, 0, 0};
     for (int a = 0; a < DIM; ++a) vv[a] = (float)v[a * n + i];
-    vq[i] = make_float4(vv[0], vv[1], vv[2], 0.0f);
+    float* d = RD + 8 * i;
+    float* m = RM + (DIM == 3 ? 16 : 8) * i;
+    if (DIM == 3) {
+        d[0] = o[0]; d[1] = o[1]; d[2] = o[2]; d[3] = __uint_as_float(bits);
+        d[4] = vv[0]; d[5] = vv[1]; d[6] = vv[2]; d[7] = V;
+        for (int k = 0; k < 16; ++k) m[k] = 0.0f;
+        m[0] = o[0]; m[1] = o[1]; m[2] = o[2]; m[3] = __uint_as_float(bits); m[7] = V;
+    } else {
+        d[0] = o[0]; d[1] = o[1]; d[2] = __uint_as_float(bits); d[3] = V;
+        d[4] = vv[0]; d[5] = vv[1]; d[6] = 0.0f; d[7] = 0.0f;
+        for (int k = 0; k < 8; ++k) m[k] = 0.0f;
+        m[0] = o[0]; m[1] = o[1]; m[2] = __uint_as_float(bits); m[3] = V;
+    }
     for (int k = 0; k < DIM * DIM; ++k) H32[k * n + i] = (float)H[k * n + i];
     for (int a = 0; a < DIM; ++a) u32[a * n + i] = (float)(x[a * n + i] - r0[a * n + i]);
     for (int s = 0; s < NS; ++s) B32[s * n + i] = (float)B0[s * n + i];
 }
 
 template <int DIM>
-__global__ void k_tl_unpack(const double* __restrict__ r0, const float4* __restrict__ vq,
+__global__ void k_tl_unpack(const double* __restrict__ r0, const float* __restrict__ RD,
                             const float* __restrict__ H32, const float* __restrict__ u32, int64_t n,
                             double* __restrict__ x, double* __restrict__ v, double* __restrict__ H) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float4 vv = vq[i];
-    float vc[3] = {vv.x, vv.y, vv.z};
     for (int a = 0; a < DIM; ++a) {
-        v[a * n + i] = vc[a];
+        v[a * n + i] = RD[8 * i + 4 + a];
         x[a * n + i] = r0[a * n + i] + (double)u32[a * n + i];
     }
     for (int k = 0; k < DIM * DIM; ++k) H[k * n + i] = H32[k * n + i];
@@ -491,10 +623,13 @@ TLK<R> make_tl_consts(const sph_tlsph_params* p) {
     K.G = (R)p->G;
     K.law = p->law;
     K.periodic = d.periodic_mask;
+    RelGrid g = make_rel_grid(d);
     for (int a = 0; a < 3; ++a) {
         K.half[a] = (R)(0.5 * d.len[a]);
         K.Lh[a] = (R)d.len[a];
         K.Ll[a] = (R)(d.len[a] - (double)K.Lh[a]);
+        K.S[a] = (R)g.S[a];
+        K.ncell[a] = g.n[a];
     }
     return K;
 }
@@ -507,44 +642,54 @@ int check_tl(const sph_tlsph_params* p, const sph_tlsph_state* st) {
     if (p->law != SPH_SVK && p->law != SPH_NEO_HOOKEAN) return SPH_ERR_ARG;
     if (!(p->rho0 > 0.0)) return SPH_ERR_ARG;
     if (p->dom.n > 0 && (!st->row_ptr || !st->col || !st->r0 || !st->V0 || !st->B0)) return SPH_ERR_ARG;
+    if (p->precision == SPH_FP32_KAHAN) {
+        // the cell-relative encoding needs at least 4 grid cells along a periodic axis
+        RelGrid g = make_rel_grid(p->dom);
+        for (int a = 0; a < p->dom.dim; ++a)
+            if (((p->dom.periodic_mask >> a) & 1u) && g.n[a] < 4) return SPH_ERR_ARG;
+    }
     return SPH_OK;
 }
 
-template <int DIM, int LANES>
+template <int DIM, int LANES, bool PER>
 void tl32_passes(int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K, double* r1, double* r2,
                  cudaStream_t s) {
     const int block = 256;
     dim3 g(grid_for(n * LANES, block)), b(block);
-    const float4* geo = reinterpret_cast<const float4*>(st->geo);
-    float4* M = reinterpret_cast<float4*>(st->M32);
-    float4* vq = reinterpret_cast<float4*>(st->vq);
     if (which == 0) {
-        if (out == OUT_RATES) k_tl_mom32<DIM, OUT_RATES, LANES><<<g, b, 0, s>>>(geo, st->row_ptr, st->col, n, K, M, vq, r1);
-        else k_tl_mom32<DIM, OUT_STEP, LANES><<<g, b, 0, s>>>(geo, st->row_ptr, st->col, n, K, M, vq, nullptr);
+        if (out == OUT_RATES)
+            k_tl_mom32<DIM, OUT_RATES, LANES, PER><<<g, b, 0, s>>>(st->rm, st->rd, st->row_ptr, st->col, n, K, r1);
+        else
+            k_tl_mom32<DIM, OUT_STEP, LANES, PER><<<g, b, 0, s>>>(st->rm, st->rd, st->row_ptr, st->col, n, K, nullptr);
     } else {
         if (out == OUT_RATES)
-            k_tl_defo32<DIM, OUT_RATES, LANES><<<g, b, 0, s>>>(geo, st->row_ptr, st->col, n, K, vq, st->B32, st->H32,
-                                                              st->u32, M, r2);
+            k_tl_defo32<DIM, OUT_RATES, LANES, PER><<<g, b, 0, s>>>(st->rd, st->rm, st->row_ptr, st->col, n, K,
+                                                                   st->B32, st->H32, st->u32, r2);
         else
-            k_tl_defo32<DIM, OUT_STEP, LANES><<<g, b, 0, s>>>(geo, st->row_ptr, st->col, n, K, vq, st->B32, st->H32,
-                                                             st->u32, M, nullptr);
+            k_tl_defo32<DIM, OUT_STEP, LANES, PER><<<g, b, 0, s>>>(st->rd, st->rm, st->row_ptr, st->col, n, K,
+                                                                  st->B32, st->H32, st->u32, nullptr);
+    }
+}
+
+template <int DIM, bool PER>
+void tl32_lanes(int lanes, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K, double* r1,
+                double* r2, cudaStream_t s) {
+    switch (lanes) {
+        case 1: tl32_passes<DIM, 1, PER>(which, out, n, st, K, r1, r2, s); break;
+        case 2: tl32_passes<DIM, 2, PER>(which, out, n, st, K, r1, r2, s); break;
+        case 8: tl32_passes<DIM, 8, PER>(which, out, n, st, K, r1, r2, s); break;
+        default: tl32_passes<DIM, 4, PER>(which, out, n, st, K, r1, r2, s); break;
     }
 }
 
 template <int DIM>
 void tl32(int lanes, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K, double* r1,
           double* r2, cudaStream_t s) {
-    switch (lanes) {
-        case 1: tl32_passes<DIM, 1>(which, out, n, st, K, r1, r2, s); break;
-        case 2: tl32_passes<DIM, 2>(which, out, n, st, K, r1, r2, s); break;
-        case 8: tl32_passes<DIM, 8>(which, out, n, st, K, r1, r2, s); break;
-        default: tl32_passes<DIM, 4>(which, out, n, st, K, r1, r2, s); break;
-    }
+    if (K.periodic) tl32_lanes<DIM, true>(lanes, which, out, n, st, K, r1, r2, s);
+    else tl32_lanes<DIM, false>(lanes, which, out, n, st, K, r1, r2, s);
 }
 
-bool fp32_ready(const sph_tlsph_state* st) {
-    return st->geo && st->vq && st->H32 && st->u32 && st->M32 && st->B32;
-}
+bool fp32_ready(const sph_tlsph_state* st) { return st->rd && st->rm && st->H32 && st->u32 && st->B32; }
 bool fp64_ready(const sph_tlsph_state* st) { return st->x && st->v && st->H && st->M; }
 
 }  // namespace
@@ -556,14 +701,15 @@ extern "C" int sph_tlsph_pack(sph_ctx* ctx, const sph_tlsph_params* p, const sph
     int64_t n = p->dom.n;
     if (n == 0) return SPH_OK;
     if (!fp32_ready(st) || !st->x || !st->v || !st->H) return SPH_ERR_ARG;
+    if (((uintptr_t)st->rd & 31u) || ((uintptr_t)st->rm & 31u)) return SPH_ERR_ARG;
     cudaStream_t s = as_stream(stream);
-    float4* vq = reinterpret_cast<float4*>(st->vq);
+    RelGrid g = make_rel_grid(p->dom);
     if (p->dom.dim == 2)
-        k_tl_pack<2><<<grid_for(n, 256), 256, 0, s>>>(st->r0, st->V0, st->B0, st->fixed, st->x, st->v, st->H, n, st->geo,
-                                                      vq, st->H32, st->u32, st->B32);
+        k_tl_pack<2><<<grid_for(n, 256), 256, 0, s>>>(st->r0, st->V0, st->B0, st->fixed, st->x, st->v, st->H, n, g,
+                                                      st->rd, st->rm, st->H32, st->u32, st->B32);
     else
-        k_tl_pack<3><<<grid_for(n, 256), 256, 0, s>>>(st->r0, st->V0, st->B0, st->fixed, st->x, st->v, st->H, n, st->geo,
-                                                      vq, st->H32, st->u32, st->B32);
+        k_tl_pack<3><<<grid_for(n, 256), 256, 0, s>>>(st->r0, st->V0, st->B0, st->fixed, st->x, st->v, st->H, n, g,
+                                                      st->rd, st->rm, st->H32, st->u32, st->B32);
     SPH_LAUNCH_CHECK(ctx);
     return SPH_OK;
 }
@@ -574,13 +720,12 @@ extern "C" int sph_tlsph_unpack(sph_ctx* ctx, const sph_tlsph_params* p, const s
     if (r) return r;
     int64_t n = p->dom.n;
     if (n == 0) return SPH_OK;
-    if (!st->vq || !st->H32 || !st->u32 || !st->x || !st->v || !st->H) return SPH_ERR_ARG;
+    if (!st->rd || !st->H32 || !st->u32 || !st->x || !st->v || !st->H) return SPH_ERR_ARG;
     cudaStream_t s = as_stream(stream);
-    const float4* vq = reinterpret_cast<const float4*>(st->vq);
     if (p->dom.dim == 2)
-        k_tl_unpack<2><<<grid_for(n, 256), 256, 0, s>>>(st->r0, vq, st->H32, st->u32, n, st->x, st->v, st->H);
+        k_tl_unpack<2><<<grid_for(n, 256), 256, 0, s>>>(st->r0, st->rd, st->H32, st->u32, n, st->x, st->v, st->H);
     else
-        k_tl_unpack<3><<<grid_for(n, 256), 256, 0, s>>>(st->r0, vq, st->H32, st->u32, n, st->x, st->v, st->H);
+        k_tl_unpack<3><<<grid_for(n, 256), 256, 0, s>>>(st->r0, st->rd, st->H32, st->u32, n, st->x, st->v, st->H);
     SPH_LAUNCH_CHECK(ctx);
     return SPH_OK;
 }
@@ -614,13 +759,12 @@ extern "C" int sph_tlsph_rates(sph_ctx* ctx, const sph_tlsph_params* p, const sp
         if (!fp32_ready(st)) return SPH_ERR_ARG;
         TLK<float> K = make_tl_consts<float>(p);
         int lanes = ctx->lanes[SPH_PASS_TLSPH];
-        float4* M = reinterpret_cast<float4*>(st->M32);
         if (dim == 2) {
-            k_tl_stress32<2><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, M);
+            k_tl_stress32<2><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm);
             tl32<2>(lanes, 0, OUT_RATES, n, st, K, dvdt, dFdt, s);
             tl32<2>(lanes, 1, OUT_RATES, n, st, K, dvdt, dFdt, s);
         } else {
-            k_tl_stress32<3><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, M);
+            k_tl_stress32<3><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm);
             tl32<3>(lanes, 0, OUT_RATES, n, st, K, dvdt, dFdt, s);
             tl32<3>(lanes, 1, OUT_RATES, n, st, K, dvdt, dFdt, s);
         }
@@ -668,10 +812,9 @@ extern "C" int sph_tlsph_step(sph_ctx* ctx, const sph_tlsph_params* p, const sph
     if (!fp32_ready(st)) return SPH_ERR_ARG;
     TLK<float> K = make_tl_consts<float>(p);
     int lanes = ctx->lanes[SPH_PASS_TLSPH];
-    float4* M = reinterpret_cast<float4*>(st->M32);
     int t = sph_timer_begin(ctx, SPH_TIMER_TL_STRESS, s);
-    if (dim == 2) k_tl_stress32<2><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, M);
-    else k_tl_stress32<3><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, M);
+    if (dim == 2) k_tl_stress32<2><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm);
+    else k_tl_stress32<3><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm);
     sph_timer_end(ctx, t, s);
     for (int k = 0; k < nsteps; ++k) {
         t = sph_timer_begin(ctx, SPH_TIMER_TL_MOMENTUM, s);
@@ -684,5 +827,63 @@ extern "C" int sph_tlsph_step(sph_ctx* ctx, const sph_tlsph_params* p, const sph
         sph_timer_end(ctx, t, s);
     }
     SPH_LAUNCH_CHECK(ctx);
+    return SPH_OK;
+}
+
+// Autotuner of the float32 pair passes: times trial_steps steps for each lanes
+// setting in {1, 2, 4, 8} on the caller's state, restores the state after each
+// trial, and keeps the fastest setting in the context.
+extern "C" int sph_autotune_tlsph(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st,
+                                  int trial_steps, int* lanes_host, double* ms_host, void* stream) {
+    if (!ctx || trial_steps < 1) return SPH_ERR_ARG;
+    int r = check_tl(p, st);
+    if (r) return r;
+    if (p->precision != SPH_FP32_KAHAN || !fp32_ready(st)) return SPH_ERR_ARG;
+    int64_t n = p->dom.n;
+    if (n == 0) return SPH_OK;
+    int dim = p->dom.dim;
+    cudaStream_t s = as_stream(stream);
+    size_t brd = (size_t)n * 8 * 4, brm = (size_t)n * (dim == 3 ? 16 : 8) * 4;
+    size_t bh = (size_t)n * dim * dim * 4, bu = (size_t)n * dim * 4;
+    unsigned char* save = (unsigned char*)sph_scratch(ctx, S_MISC3, brd + brm + bh + bu, &r);
+    if (r) return r;
+    SPH_CUDA(ctx, cudaMemcpyAsync(save, st->rd, brd, cudaMemcpyDeviceToDevice, s));
+    SPH_CUDA(ctx, cudaMemcpyAsync(save + brd, st->rm, brm, cudaMemcpyDeviceToDevice, s));
+    SPH_CUDA(ctx, cudaMemcpyAsync(save + brd + brm, st->H32, bh, cudaMemcpyDeviceToDevice, s));
+    SPH_CUDA(ctx, cudaMemcpyAsync(save + brd + brm + bh, st->u32, bu, cudaMemcpyDeviceToDevice, s));
+    cudaEvent_t e0, e1;
+    SPH_CUDA(ctx, cudaEventCreate(&e0));
+    SPH_CUDA(ctx, cudaEventCreate(&e1));
+    const int lanes_set[4] = {1, 2, 4, 8};
+    int keep = ctx->lanes[SPH_PASS_TLSPH];
+    bool timing = ctx->timing;
+    ctx->timing = false;
+    double best = 1e300;
+    int bl = keep;
+    for (int li = 0; li < 4; ++li) {
+        ctx->lanes[SPH_PASS_TLSPH] = lanes_set[li];
+        r = sph_tlsph_step(ctx, p, st, 1, stream);                  // warm
+        if (r) break;
+        SPH_CUDA(ctx, cudaEventRecord(e0, s));
+        r = sph_tlsph_step(ctx, p, st, trial_steps, stream);
+        if (r) break;
+        SPH_CUDA(ctx, cudaEventRecord(e1, s));
+        SPH_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        SPH_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; bl = lanes_set[li]; }
+        SPH_CUDA(ctx, cudaMemcpyAsync(st->rd, save, brd, cudaMemcpyDeviceToDevice, s));
+        SPH_CUDA(ctx, cudaMemcpyAsync(st->rm, save + brd, brm, cudaMemcpyDeviceToDevice, s));
+        SPH_CUDA(ctx, cudaMemcpyAsync(st->H32, save + brd + brm, bh, cudaMemcpyDeviceToDevice, s));
+        SPH_CUDA(ctx, cudaMemcpyAsync(st->u32, save + brd + brm + bh, bu, cudaMemcpyDeviceToDevice, s));
+    }
+    ctx->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r) { ctx->lanes[SPH_PASS_TLSPH] = keep; return r; }
+    ctx->lanes[SPH_PASS_TLSPH] = bl;
+    if (lanes_host) *lanes_host = bl;
+    if (ms_host) *ms_host = best / trial_steps;
+    SPH_CUDA(ctx, cudaStreamSynchronize(s));
     return SPH_OK;
 }
