@@ -1,11 +1,14 @@
 // a10/a11: Laguerre-Gauss particle relaxation (Sec. 2.3.2; Eqs. 7-8) and its
-// residual.  Positions move every step, so each step rebuilds the neighbour
-// sets (cell sort + count + scan + fill, the a1/a2 kernels), runs one pair pass
-// for the acceleration with a block-level max of |a|, and one pointwise update
-// (dt = 0.25 sqrt(h/max|a|), x += a dt^2/2, projection back inside the body).
-// The steps are launched back to back without host synchronisation; a device
-// flag records a neighbour-capacity overflow, after which the remaining steps
-// are no-ops and the host regrows the list and resumes from the failed step.
+// residual.  Positions move every step, so each step re-bins the particles into
+// cells and recomputes the neighbour sets.  The float32 step does this without a
+// list: one sweep over the 27 neighbouring cells screens every candidate (the
+// a2 screen and float64 band, so the pair set equals the list builder's) and
+// accumulates the acceleration at once, with a block-level max of |a|; a
+// pointwise update follows (dt = 0.25 sqrt(h/max|a|), x += a dt^2/2, projection
+// back inside the body).  The float64 step keeps explicit CSR lists (count,
+// scan, fill) launched back to back without host synchronisation; a device flag
+// records a list-capacity overflow, after which the remaining steps are no-ops
+// and the host regrows the list and resumes from the failed step.
 #include "common.cuh"
 #include "neighbors.cuh"
 
@@ -217,9 +220,11 @@ __global__ void k_relax_update32(double* __restrict__ pos, int64_t n, const floa
         xh[c] = (float)x[c];
         xl[c] = (float)(x[c] - (double)xh[c]);
     }
-    float4 A = geo[2 * i];
-    geo[2 * i] = make_float4(xh[0], xh[1], xh[2], A.w);
-    geo[2 * i + 1] = make_float4(xl[0], xl[1], xl[2], 0.0f);
+    if (geo) {
+        float4 A = geo[2 * i];
+        geo[2 * i] = make_float4(xh[0], xh[1], xh[2], A.w);
+        geo[2 * i + 1] = make_float4(xl[0], xl[1], xl[2], 0.0f);
+    }
 }
 
 __global__ void k_relax_pack(const double* __restrict__ pos, const double* __restrict__ vol, int64_t n,
@@ -295,6 +300,86 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int nb, doubl
         for (int c = 0; c < 3; ++c) out[c] = sh[c][0];
 }
 
+// ---------------------------------------------------------------- float32 cell sweep
+// The float32 step needs no neighbour list: one pass over the 27 neighbouring
+// cells screens every candidate with the float32 position copy of the cell sort
+// (the same screen and float64 band decision as the list builder, so the pair
+// set is the list's), and accumulates the Laguerre-Gauss gradient of the
+// accepted pairs at once.  Threads walk the particles in cell order, so the
+// candidates of neighbouring threads are the same cells (L1 reuse).
+
+// (x - float(x), V) per particle in sorted order: the float32 low parts of the position
+__global__ void k_relax_pack_lo(const double* __restrict__ pos, const double* __restrict__ vol, int64_t n,
+                                const int32_t* __restrict__ sorted, const float4* __restrict__ p32,
+                                float4* __restrict__ lo) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int j = sorted[k];
+    float4 h = p32[k];
+    lo[k] = make_float4((float)(pos[j] - (double)h.x), (float)(pos[n + j] - (double)h.y),
+                        (float)(pos[2 * n + j] - (double)h.z), (float)vol[j]);
+}
+
+__global__ void __launch_bounds__(256) k_relax_acc_cells(const float4* __restrict__ p32, const float4* __restrict__ lo,
+                                                        const int32_t* __restrict__ start, CellGrid g,
+                                                        const unsigned* __restrict__ absmax, double rc2,
+                                                        const double* __restrict__ pos, int64_t n, Spheres S,
+                                                        RelaxK K, float4* __restrict__ acc,
+                                                        unsigned* __restrict__ amax) {
+    __shared__ unsigned smax;
+    if (threadIdx.x == 0) smax = 0u;
+    __syncthreads();
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        float4 me = p32[k];
+        float4 ml = lo[k];
+        int i = __float_as_int(me.w);
+        float xh[3] = {me.x, me.y, me.z}, xl[3] = {ml.x, ml.y, ml.z};
+        double xi[3] = {pos[i], pos[n + i], pos[2 * n + i]};
+        int ci[3];
+        for (int a = 0; a < 3; ++a) ci[a] = nb::cell_coord(xi[a], a, g);
+        nb::Band band = nb::make_band(absmax, 0.0, rc2, 3);
+        int lx[3], ly[3], lz[3];
+        int mx = nb::axis_cells(ci[0], 0, g, lx);
+        int my = nb::axis_cells(ci[1], 1, g, ly);
+        int mz = nb::axis_cells(ci[2], 2, g, lz);
+        Kahan<float> s[3];
+        for (int a = 0; a < 3; ++a) s[a].init();
+        for (int az = 0; az < mz; ++az)
+            for (int ay = 0; ay < my; ++ay) {
+                int rowbase = (lz[az] * g.n[1] + ly[ay]) * g.n[0];
+                for (int ax = 0; ax < mx; ++ax) {
+                    int c = rowbase + lx[ax];
+                    int b = start[c], e = start[c + 1];
+                    for (int m = b; m < e; ++m) {
+                        float4 p = p32[m];
+                        int j = __float_as_int(p.w);
+                        if (j == i) continue;
+                        float dx = xh[0] - p.x, dy = xh[1] - p.y, dz = xh[2] - p.z;
+                        float d2s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        if (d2s > band.hi) continue;
+                        if (d2s >= band.lo && !nb::exact_within(pos, n, 3, xi, j, g, rc2)) continue;
+                        float4 q = lo[m];
+                        float r[3] = {dx + (xl[0] - q.x), dy + (xl[1] - q.y), dz + (xl[2] - q.z)};
+                        float d2 = fmaf(r[2], r[2], fmaf(r[1], r[1], r[0] * r[0]));
+                        float gs = lg_gs<float>(sqrtf(d2) * K.inv_h_f, K.gcoef_f) * q.w;
+                        for (int a = 0; a < 3; ++a) s[a].add(gs * r[a]);
+                    }
+                }
+            }
+        float g3[3];
+        float phi = sdf32(S, xh, xl, g3);
+        float I = surface_lg<float>(phi < 0.0f ? -phi : 0.0f, K.inv_h_f, K.surf_coef_f);
+        float a0 = -K.scale_f * (s[0].value() + I * g3[0]);
+        float a1 = -K.scale_f * (s[1].value() + I * g3[1]);
+        float a2 = -K.scale_f * (s[2].value() + I * g3[2]);
+        acc[i] = make_float4(a0, a1, a2, 0.0f);
+        atomic_max_nonneg(&smax, sqrtf(a0 * a0 + a1 * a1 + a2 * a2));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && smax) atomicMax(amax, smax);
+}
+
 __global__ void k_widen_acc(const float4* __restrict__ acc, int64_t n, double* __restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -309,7 +394,7 @@ int check_relax(const sph_relax_params* p) {
     if (!p) return SPH_ERR_ARG;
     int s = sph_check_domain(&p->dom);
     if (s) return s;
-    if (p->dom.dim != 3) return SPH_ERR_ARG;
+    if (p->dom.dim != 3 || p->dom.periodic_mask != 0) return SPH_ERR_ARG;   // a body: no periodic axes
     if (p->kernel != SPH_LAGUERRE_GAUSS) return SPH_ERR_ARG;
     if (p->precision != SPH_FP64 && p->precision != SPH_FP32_KAHAN) return SPH_ERR_ARG;
     if (p->n_spheres < 1 || p->n_spheres > SPH_MAX_SPHERES) return SPH_ERR_ARG;
@@ -402,6 +487,23 @@ void acc32(const float4* geo, int64_t n, const RelaxLists& L, const Spheres& S, 
     k_relax_acc32<LANES><<<grid_for(n * LANES, 256), 256, 0, s>>>(geo, n, L.row_ptr, L.col, S, K, acc, amax, flags);
 }
 
+// float32 acceleration by the cell sweep (cells of the LG support 2h).
+int acc_cells(sph_ctx* ctx, const sph_relax_params* p, const double* pos, const double* vol, const Spheres& S,
+              const RelaxK& K, float4* acc, unsigned* amax, cudaStream_t s) {
+    CellList cl;
+    int st = sph_build_cells(ctx, &p->dom, pos, s, &cl);
+    if (st) return st;
+    int64_t n = p->dom.n;
+    float4* lo = (float4*)sph_scratch(ctx, S_MISC1, (size_t)n * 16, &st);
+    if (st) return st;
+    k_relax_pack_lo<<<grid_for(n, 256), 256, 0, s>>>(pos, vol, n, cl.sorted, cl.p32, lo);
+    k_relax_acc_cells<<<grid_for(n, 256), 256, 0, s>>>(cl.p32, lo, cl.cell_start, cl.grid,
+                                                       (const unsigned*)cl.band, cl.grid.rc2, pos, n, S, K, acc,
+                                                       amax);
+    SPH_LAUNCH_CHECK(ctx);
+    return SPH_OK;
+}
+
 int read_capacity_flag(sph_ctx* ctx, cudaStream_t s, int* step_failed, int64_t* required, const RelaxLists& L,
                        int64_t n) {
     int* hf = (int*)ctx->pinned;
@@ -431,6 +533,31 @@ extern "C" int sph_relax_step(sph_ctx* ctx, const sph_relax_params* p, double* p
     cudaStream_t s = as_stream(stream);
     Spheres S = make_spheres(p);
     RelaxK K = make_relax_consts(p);
+    if (p->precision == SPH_FP32_KAHAN) {
+        unsigned* amax = (unsigned*)sph_scratch(ctx, S_RELAX_AMAX, 64, &st);
+        float4* acc = (float4*)sph_scratch(ctx, S_RELAX_ACC, (size_t)n * 16, &st);
+        if (st) return st;
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+        for (int k = 0; k < nsteps; ++k) {
+            SPH_CUDA(ctx, cudaMemsetAsync(amax, 0, 64, s));
+            int t = sph_timer_begin(ctx, SPH_TIMER_RELAX_ACCEL, s);
+            st = acc_cells(ctx, p, pos, vol, S, K, acc, amax, s);
+            if (st) return st;
+            sph_timer_end(ctx, t, s);
+            t = sph_timer_begin(ctx, SPH_TIMER_RELAX_UPDATE, s);
+            k_relax_update32<<<grid_for(n, 256), 256, 0, s>>>(pos, n, acc, amax, S, K, nullptr, ctx->flags);
+            sph_timer_end(ctx, t, s);
+            SPH_LAUNCH_CHECK(ctx);
+        }
+        int* hf = (int*)ctx->pinned;
+        SPH_CUDA(ctx, cudaMemcpyAsync(hf, ctx->flags, FLAG_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPH_CUDA(ctx, cudaStreamSynchronize(s));
+        if (hf[FLAG_BAD_INPUT]) {
+            SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+            return SPH_ERR_ARG;
+        }
+        return SPH_OK;
+    }
     int64_t cap = ctx->slot_bytes[S_RELAX_COL] / 4;
     if (cap < n * g_default_per_particle) cap = n * g_default_per_particle;
     RelaxLists L;
@@ -501,6 +628,21 @@ extern "C" int sph_relax_accel(sph_ctx* ctx, const sph_relax_params* p, const do
     cudaStream_t s = as_stream(stream);
     Spheres S = make_spheres(p);
     RelaxK K = make_relax_consts(p);
+    if (p->precision == SPH_FP32_KAHAN) {
+        unsigned* amax = (unsigned*)sph_scratch(ctx, S_RELAX_AMAX, 64, &st);
+        float4* acc = (float4*)sph_scratch(ctx, S_RELAX_ACC, (size_t)n * 16, &st);
+        if (st) return st;
+        SPH_CUDA(ctx, cudaMemsetAsync(amax, 0, 64, s));
+        st = acc_cells(ctx, p, pos, vol, S, K, acc, amax, s);
+        if (st) return st;
+        k_widen_acc<<<grid_for(n, 256), 256, 0, s>>>(acc, n, acc_out);
+        SPH_LAUNCH_CHECK(ctx);
+        int* hf = (int*)ctx->pinned;
+        SPH_CUDA(ctx, cudaMemcpyAsync(hf, ctx->flags, FLAG_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+        SPH_CUDA(ctx, cudaStreamSynchronize(s));
+        return hf[FLAG_BAD_INPUT] ? SPH_ERR_ARG : SPH_OK;
+    }
     int64_t cap = n * g_default_per_particle;
     RelaxLists L;
     for (int attempt = 0; attempt < 4; ++attempt) {
