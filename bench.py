@@ -269,7 +269,7 @@ def _bench_tgv3d(api, inputs, ctx, steps, peak):
         tc, nc = ctx.timer(SPH_TIMER_EU_MASS)
         ctx.timing(False)
         n = sim.n
-        per_pass = n * (8 + 64 + 16 + 16) + 4 * nnz
+        per_pass = n * (8 + 64 + 16) + 4 * nnz       # row_ptr, own 64-byte record, (v, drho) write, col
         dom_ms = max(tm / max(nm, 1), tc / max(nc, 1))
         r = {"ms_per_step": ms / steps, "pair_interactions_per_s": 2 * nnz * steps / (ms * 1e-3), "nnz": nnz,
              "lanes": lanes, "pass_ms": {"momentum": tm / max(nm, 1), "continuity": tc / max(nc, 1)},
@@ -326,7 +326,7 @@ def _bench_batched(api, inputs, ctx, steps, peak):
     ms = _event_ms(lambda: b.step(steps))
     tstep, nstep = ctx.timer(SPH_TIMER_BATCH_STEP)
     ctx.timing(False)
-    per_step_bytes = 2 * (b.ntotal * (8 + 32 + 16 + 16) + 4 * b.nnz)
+    per_step_bytes = 2 * (b.ntotal * (8 + 64 + 16) + 4 * b.nnz)
     return {"workload": "64 independent 2D Taylor-Green cases, sides log-uniform 64..1024 (seed 0), "
                         "Re in {100,1000}, kappa=1.6, FP32+Kahan, persistent launch per pass, CUDA graph",
             "particles": b.ntotal, "nnz": b.nnz, "ms_per_step": ms / steps,

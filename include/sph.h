@@ -214,12 +214,15 @@ typedef struct {
 } sph_eulerian_params;
 
 /* State arrays.  FP64 steps use pos/vol/B/drho/v and the drho_tmp/v_tmp
- * scratch (same shapes as drho/v).  FP32 steps use the packed records, made by
+ * scratch (same shapes as drho/v).  FP32 steps use packed records of 16 floats
+ * (two 32-byte lines; rec and rec_tmp 32-byte aligned), made by
  * sph_eulerian_pack from the FP64 arrays and read back by sph_eulerian_unpack:
- *   geo  [n][8] (2D): (xh, yh, xl, yl), (V, B00, B01, B11)
- *        [n][16] (3D): (xh, yh, zh, V), (xl, yl, zl, B00), (B01, B02, B11, B12), (B22, 0, 0, 0)
- *        where x = xh + xl is the float64 position split into two floats;
- *   q, q_tmp [n][4]: (v0, v1, drho, 0) in 2D, (v0, v1, v2, drho) in 3D. */
+ *   3D: (ox, oy, oz, cell, V, B00, B01, B02) (B11, B12, B22, 0, vx, vy, vz, drho)
+ *   2D: (ox, oy, cell, V, B00, B01, B11, 0) (0, 0, 0, 0, vx, vy, 0, drho)
+ * with the cell-relative position of the sph_tlsph_state comment (grid of
+ * n_a = min(max(1, floor(len_a/h)), 1023 or 32767) cells, at least 4 along a
+ * periodic axis).  Both buffers hold the static part; a pass writes only the
+ * (v, drho) float4 of the other buffer. */
 typedef struct {
     const int64_t* row_ptr;
     const int32_t* col;
@@ -230,18 +233,17 @@ typedef struct {
     double* v;
     double* drho_tmp;
     double* v_tmp;
-    float*  geo;
-    float*  q;
-    float*  q_tmp;
+    float*  rec;
+    float*  rec_tmp;
 } sph_eulerian_state;
 
-/* float64 (pos, vol, B, drho, v) -> packed float32 (geo, q). */
+/* float64 (pos, vol, B, drho, v) -> packed float32 records (rec, rec_tmp). */
 int sph_eulerian_pack(sph_ctx* ctx, const sph_eulerian_params* prm,
                       const sph_eulerian_state* st, void* stream);
-/* packed float32 q -> float64 (drho, v). */
+/* packed float32 rec -> float64 (drho, v). */
 int sph_eulerian_unpack(sph_ctx* ctx, const sph_eulerian_params* prm,
                         const sph_eulerian_state* st, void* stream);
-/* Both rates at the current state (FP64 arrays or, for FP32, the packed q):
+/* Both rates at the current state (FP64 arrays or, for FP32, the packed rec):
  * drho_dt float64 [n], dmom_dt float64 [dim][n]. */
 int sph_eulerian_rates(sph_ctx* ctx, const sph_eulerian_params* prm,
                        const sph_eulerian_state* st, double* drho_dt,
@@ -261,7 +263,7 @@ int sph_autotune_eulerian(sph_ctx* ctx, const sph_eulerian_params* prm,
 /* ---- a13: batched Eulerian step (not in the paper: many cases per launch) ----
  * ncases independent Eulerian cases (the float32 two-pass step of
  * sph_eulerian_step, Sec. 3.1) whose packed records and CSR lists are
- * concatenated: case c owns particles [offset, offset + n) of geo/q/q_tmp, its
+ * concatenated: case c owns particles [offset, offset + n) of rec/rec_tmp, its
  * CSR rows are rows offset..offset+n-1 of row_ptr and its column indices are
  * global (already shifted by offset).  One persistent launch per pass covers
  * all cases; the two launches of a step are captured into a CUDA graph once and
@@ -282,9 +284,8 @@ typedef struct {
 typedef struct {
     const int64_t* row_ptr;         /* [N+1] */
     const int32_t* col;             /* global indices */
-    float* geo;                     /* [N][8] (2D) or [N][16] (3D), sph_eulerian_state layout */
-    float* q;                       /* [N][4] */
-    float* q_tmp;                   /* [N][4] scratch */
+    float* rec;                     /* [N][16] records, sph_eulerian_state layout */
+    float* rec_tmp;                 /* [N][16] second buffer (static part filled) */
 } sph_batch_state;
 int sph_eulerian_step_batched(sph_ctx* ctx, const sph_batch_case* cases_host, int ncases,
                               const sph_batch_state* st, int nsteps, void* stream);

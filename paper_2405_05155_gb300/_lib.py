@@ -39,7 +39,7 @@ class EulerianParams(ctypes.Structure):
 
 class EulerianState(ctypes.Structure):
     _fields_ = [(name, c_vp) for name in ("row_ptr", "col", "pos", "vol", "B", "drho", "v", "drho_tmp",
-                                          "v_tmp", "geo", "q", "q_tmp")]
+                                          "v_tmp", "rec", "rec_tmp")]
 
 
 class TLParams(ctypes.Structure):
@@ -59,7 +59,7 @@ class BatchCase(ctypes.Structure):
 
 
 class BatchState(ctypes.Structure):
-    _fields_ = [(name, c_vp) for name in ("row_ptr", "col", "geo", "q", "q_tmp")]
+    _fields_ = [(name, c_vp) for name in ("row_ptr", "col", "rec", "rec_tmp")]
 
 
 class RelaxParams(ctypes.Structure):

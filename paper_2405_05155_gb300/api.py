@@ -153,12 +153,10 @@ class Eulerian:
         self.v = _dev_f64(v, dev).clone()
         self.drho_tmp = torch.empty_like(self.drho)
         self.v_tmp = torch.empty_like(self.v)
-        words = 8 if self.dim == 2 else 16
-        self.geo = torch.zeros(self.n * words, dtype=torch.float32, device=dev)
-        self.q = torch.zeros(self.n * 4, dtype=torch.float32, device=dev)
-        self.q_tmp = torch.zeros(self.n * 4, dtype=torch.float32, device=dev)
+        self.rec = torch.zeros(self.n * 16, dtype=torch.float32, device=dev)
+        self.rec_tmp = torch.zeros(self.n * 16, dtype=torch.float32, device=dev)
         self.st = L.EulerianState()
-        for name in ("row_ptr", "col", "pos", "vol", "B", "drho", "v", "drho_tmp", "v_tmp", "geo", "q", "q_tmp"):
+        for name in ("row_ptr", "col", "pos", "vol", "B", "drho", "v", "drho_tmp", "v_tmp", "rec", "rec_tmp"):
             setattr(self.st, name, getattr(self, name).data_ptr())
         if precision == SPH_FP32_KAHAN:
             self.pack()

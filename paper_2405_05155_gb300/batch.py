@@ -17,7 +17,7 @@ class EulerianBatch:
         self.cases = cases
         self.sims = []
         self.orders = []
-        geos, qs, rps, cols = [], [], [], []
+        recs, rps, cols = [], [], []
         off = 0
         nnz_off = 0
         self.table = (L.BatchCase * len(cases))()
@@ -40,8 +40,7 @@ class EulerianBatch:
             t.h, t.dt, t.rho0, t.c0, t.mu, t.eta = d["h"], case["dt"], case["rho0"], case["c0"], case["mu"], 15.0
             for k in range(3):
                 t.len[k] = d["len"][k] if k < d["dim"] else 1.0
-            geos.append(sim.geo)
-            qs.append(sim.q)
+            recs.append(sim.rec)
             rps.append(rp[:-1] + nnz_off)
             cols.append(col + off)
             self.sims.append(sim)
@@ -53,11 +52,10 @@ class EulerianBatch:
         self.nnz = nnz_off
         self.row_ptr = torch.cat(rps).contiguous()
         self.col = torch.cat(cols).to(torch.int32).contiguous()
-        self.geo = torch.cat(geos).contiguous()
-        self.q = torch.cat(qs).contiguous()
-        self.q_tmp = torch.zeros_like(self.q)
+        self.rec = torch.cat(recs).contiguous()
+        self.rec_tmp = self.rec.clone()
         self.st = L.BatchState()
-        for name in ("row_ptr", "col", "geo", "q", "q_tmp"):
+        for name in ("row_ptr", "col", "rec", "rec_tmp"):
             setattr(self.st, name, getattr(self, name).data_ptr())
 
     def step(self, nsteps=1):
@@ -76,6 +74,6 @@ class EulerianBatch:
         sim = self.sims[c]
         t = self.table[c]
         n = int(t.n)
-        sim.q.copy_(self.q[4 * t.offset: 4 * (t.offset + n)])
+        sim.rec.copy_(self.rec[16 * t.offset: 16 * (t.offset + n)])
         sim.unpack()
         return sim.drho, sim.v

@@ -22,12 +22,11 @@ namespace {
 constexpr int kMaxCases = 256;
 
 template <int DIM, int MODE, int OUT, int LANES>
-__global__ void __launch_bounds__(256) k_euler32_batched(const float4* __restrict__ geo,
+__global__ void __launch_bounds__(256) k_euler32_batched(const float* __restrict__ Rin, float* __restrict__ Rout,
                                                          const int64_t* __restrict__ row_ptr,
                                                          const int32_t* __restrict__ col, int64_t ntotal, int ncases,
                                                          const EulerK<float>* __restrict__ cases,
-                                                         const int64_t* __restrict__ offsets,
-                                                         const float4* __restrict__ q, float4* __restrict__ q_out) {
+                                                         const int64_t* __restrict__ offsets) {
     __shared__ EulerK<float> sK[kMaxCases];
     __shared__ int64_t sOff[kMaxCases + 1];
     for (int c = threadIdx.x; c < ncases; c += blockDim.x) sK[c] = cases[c];
@@ -48,59 +47,17 @@ __global__ void __launch_bounds__(256) k_euler32_batched(const float4* __restric
             else hi = mid - 1;
         }
         const EulerK<float>& K = sK[lo];
-        float xhi[DIM], xli[DIM], Vi, Bi[NS], vi[DIM], dri;
-        load_geo32<DIM>(geo, ii, xhi, xli, Vi, Bi);
-        load_q32<DIM>(q, ii, vi, dri);
-        Kahan<float> am;
-        Kahan<float> ap[DIM];
-        am.init();
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) ap[a].init();
+        F8 ma = ldg8(Rin + kRecWords * ii), mb = ldg8(Rin + kRecWords * ii + 8);
+        float oi[DIM], Vi, Bi[NS], vi[DIM], dri;
+        uint32_t bi;
+        unpack_rec<DIM>(ma, mb, oi, bi, Vi, Bi, vi, dri);
         int64_t b = active ? row_ptr[ii] : 0, e = active ? row_ptr[ii + 1] : 0;
-        for (int64_t p = b + lane; p < e; p += LANES) {
-            int j = __ldg(&col[p]);
-            float xhj[DIM], xlj[DIM], Vj, Bj[NS], vj[DIM], drj;
-            load_geo32<DIM>(geo, j, xhj, xlj, Vj, Bj);
-            load_q32<DIM>(q, j, vj, drj);
-            float r[DIM], d2 = 0.0f;
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) {
-                float dh = xhi[a] - xhj[a];
-                float dl = xli[a] - xlj[a];
-                if ((K.periodic >> a) & 1u) {
-                    if (dh > K.half[a]) { dh -= K.Lh[a]; dl -= K.Ll[a]; }
-                    else if (dh < -K.half[a]) { dh += K.Lh[a]; dl += K.Ll[a]; }
-                }
-                r[a] = dh + dl;
-                d2 = fmaf(r[a], r[a], d2);
-            }
-            float m = 0.0f, mo[DIM];
-            euler_pair<DIM, MODE, float>(r, d2, Bi, Bj, vi, vj, dri, drj, Vj, K, m, mo);
-            if (MODE & WANT_MASS) am.add(m);
-            if (MODE & WANT_MOM) {
-#pragma unroll
-                for (int a = 0; a < DIM; ++a) ap[a].add(mo[a]);
-            }
-        }
-        float rm = group_sum<LANES>(am.value());
-        float rp[DIM];
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) rp[a] = group_sum<LANES>(ap[a].value());
+        float rm, rp[DIM];
+        euler_row32<DIM, MODE, LANES, true>(Rin, col, b, e, lane, oi, bi, Bi, vi, dri, K, rm, rp);
         if (active && lane == 0) {
-            float rho_i = K.rho0 + dri;
-            float vn[DIM];
-            if (OUT == OUT_MOM) {
-#pragma unroll
-                for (int a = 0; a < DIM; ++a) vn[a] = vi[a] + K.dt * rp[a] / rho_i;
-                store_q32<DIM>(q_out, i, vn, dri);
-            } else {   // OUT_MASS
-                float ddr = K.dt * rm;
-                float dr1 = dri + ddr;
-                float ratio = 1.0f - ddr / (K.rho0 + dr1);
-#pragma unroll
-                for (int a = 0; a < DIM; ++a) vn[a] = vi[a] * ratio;
-                store_q32<DIM>(q_out, i, vn, dr1);
-            }
+            float vn[DIM], drn;
+            euler_update32<DIM, OUT>(vi, dri, rm, rp, K, vn, drn);
+            store_dyn<DIM>(Rout, i, vn, drn);
         }
     }
 }
@@ -120,10 +77,19 @@ EulerK<float> case_consts(const sph_batch_case& c, int dim) {
     K.eps_h2 = (float)(0.01 * h * h);
     K.dt = (float)c.dt;
     K.periodic = c.periodic_mask;
+    sph_domain d = {};
+    d.dim = dim;
+    d.h = c.h;
+    d.periodic_mask = c.periodic_mask;
+    for (int a = 0; a < 3; ++a) d.len[a] = c.len[a];
+    RelGrid g = make_rel_grid(d);
     for (int a = 0; a < 3; ++a) {
         K.half[a] = (float)(0.5 * c.len[a]);
         K.Lh[a] = (float)c.len[a];
         K.Ll[a] = (float)(c.len[a] - (double)K.Lh[a]);
+        K.S[a] = (float)g.S[a];
+        K.Sl[a] = (float)(g.S[a] - (double)K.S[a]);
+        K.ncell[a] = g.n[a];
     }
     return K;
 }
@@ -134,44 +100,44 @@ struct BatchPlan {
 
 template <int LANES>
 void launch_pass(int out, int dim, const BatchPlan& pl, const sph_batch_state* st, int64_t ntotal, int ncases,
-                 const EulerK<float>* dK, const int64_t* dOff, const float4* qin, float4* qout, cudaStream_t s) {
-    const float4* geo = reinterpret_cast<const float4*>(st->geo);
+                 const EulerK<float>* dK, const int64_t* dOff, const float* rin, float* rout, cudaStream_t s) {
     if (dim == 2) {
         if (out == OUT_MOM)
-            k_euler32_batched<2, WANT_MOM, OUT_MOM, LANES><<<pl.grid, pl.block, 0, s>>>(geo, st->row_ptr, st->col, ntotal,
-                                                                                      ncases, dK, dOff, qin, qout);
+            k_euler32_batched<2, WANT_MOM, OUT_MOM, LANES><<<pl.grid, pl.block, 0, s>>>(rin, rout, st->row_ptr, st->col,
+                                                                                      ntotal, ncases, dK, dOff);
         else
-            k_euler32_batched<2, WANT_MASS, OUT_MASS, LANES><<<pl.grid, pl.block, 0, s>>>(geo, st->row_ptr, st->col,
-                                                                                        ntotal, ncases, dK, dOff, qin, qout);
+            k_euler32_batched<2, WANT_MASS, OUT_MASS, LANES><<<pl.grid, pl.block, 0, s>>>(rin, rout, st->row_ptr,
+                                                                                        st->col, ntotal, ncases, dK, dOff);
     } else {
         if (out == OUT_MOM)
-            k_euler32_batched<3, WANT_MOM, OUT_MOM, LANES><<<pl.grid, pl.block, 0, s>>>(geo, st->row_ptr, st->col, ntotal,
-                                                                                      ncases, dK, dOff, qin, qout);
+            k_euler32_batched<3, WANT_MOM, OUT_MOM, LANES><<<pl.grid, pl.block, 0, s>>>(rin, rout, st->row_ptr, st->col,
+                                                                                      ntotal, ncases, dK, dOff);
         else
-            k_euler32_batched<3, WANT_MASS, OUT_MASS, LANES><<<pl.grid, pl.block, 0, s>>>(geo, st->row_ptr, st->col,
-                                                                                        ntotal, ncases, dK, dOff, qin, qout);
+            k_euler32_batched<3, WANT_MASS, OUT_MASS, LANES><<<pl.grid, pl.block, 0, s>>>(rin, rout, st->row_ptr,
+                                                                                        st->col, ntotal, ncases, dK, dOff);
     }
 }
 
 void launch_step(const BatchPlan& pl, int dim, const sph_batch_state* st, int64_t ntotal, int ncases,
                  const EulerK<float>* dK, const int64_t* dOff, cudaStream_t s) {
-    float4* q0 = reinterpret_cast<float4*>(st->q);
-    float4* q1 = reinterpret_cast<float4*>(st->q_tmp);
+    float* r0 = st->rec;
+    float* r1 = st->rec_tmp;
     switch (pl.lanes) {
-        case 1: launch_pass<1>(OUT_MOM, dim, pl, st, ntotal, ncases, dK, dOff, q0, q1, s);
-                launch_pass<1>(OUT_MASS, dim, pl, st, ntotal, ncases, dK, dOff, q1, q0, s); break;
-        case 2: launch_pass<2>(OUT_MOM, dim, pl, st, ntotal, ncases, dK, dOff, q0, q1, s);
-                launch_pass<2>(OUT_MASS, dim, pl, st, ntotal, ncases, dK, dOff, q1, q0, s); break;
-        case 8: launch_pass<8>(OUT_MOM, dim, pl, st, ntotal, ncases, dK, dOff, q0, q1, s);
-                launch_pass<8>(OUT_MASS, dim, pl, st, ntotal, ncases, dK, dOff, q1, q0, s); break;
-        default: launch_pass<4>(OUT_MOM, dim, pl, st, ntotal, ncases, dK, dOff, q0, q1, s);
-                 launch_pass<4>(OUT_MASS, dim, pl, st, ntotal, ncases, dK, dOff, q1, q0, s); break;
+        case 1: launch_pass<1>(OUT_MOM, dim, pl, st, ntotal, ncases, dK, dOff, r0, r1, s);
+                launch_pass<1>(OUT_MASS, dim, pl, st, ntotal, ncases, dK, dOff, r1, r0, s); break;
+        case 2: launch_pass<2>(OUT_MOM, dim, pl, st, ntotal, ncases, dK, dOff, r0, r1, s);
+                launch_pass<2>(OUT_MASS, dim, pl, st, ntotal, ncases, dK, dOff, r1, r0, s); break;
+        case 8: launch_pass<8>(OUT_MOM, dim, pl, st, ntotal, ncases, dK, dOff, r0, r1, s);
+                launch_pass<8>(OUT_MASS, dim, pl, st, ntotal, ncases, dK, dOff, r1, r0, s); break;
+        default: launch_pass<4>(OUT_MOM, dim, pl, st, ntotal, ncases, dK, dOff, r0, r1, s);
+                 launch_pass<4>(OUT_MASS, dim, pl, st, ntotal, ncases, dK, dOff, r1, r0, s); break;
     }
 }
 
 int check_batch(const sph_batch_case* cases, int ncases, const sph_batch_state* st, int64_t* ntotal, int* dim) {
     if (!cases || !st || ncases < 1 || ncases > kMaxCases) return SPH_ERR_ARG;
-    if (!st->row_ptr || !st->col || !st->geo || !st->q || !st->q_tmp) return SPH_ERR_ARG;
+    if (!st->row_ptr || !st->col || !st->rec || !st->rec_tmp) return SPH_ERR_ARG;
+    if (((uintptr_t)st->rec & 31u) || ((uintptr_t)st->rec_tmp & 31u)) return SPH_ERR_ARG;
     int64_t off = 0;
     *dim = cases[0].dim;
     for (int c = 0; c < ncases; ++c) {
@@ -179,6 +145,17 @@ int check_batch(const sph_batch_case* cases, int ncases, const sph_batch_state* 
         if (k.dim != *dim || (k.dim != 2 && k.dim != 3)) return SPH_ERR_ARG;
         if (k.offset != off || k.n < 1) return SPH_ERR_ARG;
         if (!(k.h > 0.0) || !(k.dt > 0.0) || !(k.c0 > 0.0) || !(k.rho0 > 0.0) || !(k.mu >= 0.0)) return SPH_ERR_ARG;
+        sph_domain d = {};
+        d.dim = k.dim;
+        d.h = k.h;
+        d.periodic_mask = k.periodic_mask;
+        for (int a = 0; a < 3; ++a) {
+            if (a < k.dim && !(k.len[a] > 0.0)) return SPH_ERR_ARG;
+            d.len[a] = k.len[a];
+        }
+        if (k.periodic_mask >> k.dim) return SPH_ERR_ARG;
+        // lists may hold pairs up to the widest support, 2h
+        if (!rel_grid_periodic_ok(make_rel_grid(d), k.dim, 2.0 * k.h)) return SPH_ERR_ARG;
         off += k.n;
     }
     *ntotal = off;
@@ -195,8 +172,10 @@ int upload_cases(sph_ctx* ctx, const sph_batch_case* cases, int ncases, int dim,
         off[c] = cases[c].offset;
     }
     off[ncases] = cases[ncases - 1].offset + cases[ncases - 1].n;
-    size_t kb = sizeof(EulerK<float>) * ncases, ob = sizeof(int64_t) * (ncases + 1);
-    std::vector<unsigned char> blob(kb + ob);
+    // the offsets follow the constants at a 16-byte boundary (int64 loads need 8-byte alignment
+    // and sizeof(EulerK<float>) is not a multiple of 8)
+    size_t kb = (sizeof(EulerK<float>) * ncases + 15) & ~size_t(15), ob = sizeof(int64_t) * (ncases + 1);
+    std::vector<unsigned char> blob(kb + ob, 0);
     std::memcpy(blob.data(), K.data(), kb);
     std::memcpy(blob.data() + kb, off.data(), ob);
     *changed = blob != ctx->batch_blob;
@@ -254,7 +233,7 @@ int run_steps(sph_ctx* ctx, const BatchPlan& pl, int dim, const sph_batch_state*
     // (re)capture one step as a graph when anything it depends on changed
     BatchGraphKey key;
     std::memset(&key, 0, sizeof(key));
-    key.row_ptr = st->row_ptr; key.col = st->col; key.geo = st->geo; key.q = st->q; key.q_tmp = st->q_tmp;
+    key.row_ptr = st->row_ptr; key.col = st->col; key.rec = st->rec; key.rec_tmp = st->rec_tmp;
     key.ntotal = ntotal; key.ncases = ncases; key.lanes = pl.lanes; key.block = pl.block; key.grid = pl.grid;
     key.dK = dK; key.dim = dim;
     if (!ctx->batch_graph || tables_changed || std::memcmp(&key, &ctx->batch_key, sizeof(key)) != 0) {
@@ -313,10 +292,10 @@ extern "C" int sph_autotune_batched(sph_ctx* ctx, const sph_batch_case* cases, i
     r = upload_cases(ctx, cases, ncases, dim, &dK, &dOff, s, &changed);
     if (r) return r;
     // the trial steps advance the caller's state: it is saved first and restored after every variant
-    int64_t qbytes = ntotal * 16;
+    int64_t qbytes = ntotal * kRecWords * 4;
     void* save = sph_scratch(ctx, S_MISC3, (size_t)qbytes, &r);
     if (r) return r;
-    SPH_CUDA(ctx, cudaMemcpyAsync(save, st->q, qbytes, cudaMemcpyDeviceToDevice, s));
+    SPH_CUDA(ctx, cudaMemcpyAsync(save, st->rec, qbytes, cudaMemcpyDeviceToDevice, s));
     cudaEvent_t e0, e1;
     SPH_CUDA(ctx, cudaEventCreate(&e0));
     SPH_CUDA(ctx, cudaEventCreate(&e1));
@@ -338,7 +317,7 @@ extern "C" int sph_autotune_batched(sph_ctx* ctx, const sph_batch_case* cases, i
             float ms = 0.0f;
             SPH_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
             if (ms < best) { best = ms; bl = lanes_set[li]; bb = block_set[bi]; }
-            SPH_CUDA(ctx, cudaMemcpyAsync(st->q, save, qbytes, cudaMemcpyDeviceToDevice, s));
+            SPH_CUDA(ctx, cudaMemcpyAsync(st->rec, save, qbytes, cudaMemcpyDeviceToDevice, s));
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

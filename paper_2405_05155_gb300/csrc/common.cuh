@@ -18,9 +18,8 @@ struct TimerRec {
 struct BatchGraphKey {
     const void* row_ptr;
     const void* col;
-    const void* geo;
-    const void* q;
-    const void* q_tmp;
+    const void* rec;
+    const void* rec_tmp;
     const void* dK;
     int64_t ntotal;
     int ncases, lanes, block, grid, dim, pad;
@@ -159,6 +158,108 @@ struct Kahan2 {
     }
     __device__ __forceinline__ float2 value() const { return __fadd2_rn(s, cn); }
 };
+
+// One 32-byte record, read with a single 256-bit load.
+struct __align__(32) F8 {
+    float v[8];
+};
+
+// 256-bit read-only gather (the record must not be written during the kernel).
+__device__ __forceinline__ F8 ldg8(const float* p) {
+    F8 r;
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]),
+          "=f"(r.v[7])
+        : "l"(p));
+    return r;
+}
+
+// Cell-relative float32 positions: per axis a grid of n_a cells of size S_a over the
+// box, x = lo + c S + o with the integer cell c packed 10 bits per axis (3D) or 15
+// (2D) into one 32-bit word, bit 30 free for a flag.  r_ij = (c_i - c_j) S + (o_i - o_j)
+// keeps float32 accuracy of r itself in any box.  The grid is finer than h (up to
+// kRelCellsPerH cells per h, as the bit width allows): the rounding of o_i shifts every
+// pair of particle i alike, so it adds up coherently in sums such as sum_j V_j grad W_ij
+// that nearly cancel, and a smaller S makes that shift small against the per-pair
+// rounding of r.
+constexpr double kRelCellsPerH = 16.0;
+
+struct RelGrid {
+    double lo[3], len[3], S[3];
+    int n[3];
+    uint32_t periodic;
+};
+
+static inline RelGrid make_rel_grid(const sph_domain& d) {
+    RelGrid g;
+    int nmax = d.dim == 3 ? 1023 : 32767;
+    g.periodic = d.periodic_mask;
+    for (int a = 0; a < 3; ++a) {
+        if (a < d.dim) {
+            double m = floor(kRelCellsPerH * d.len[a] / d.h);
+            if (m < 1.0) m = 1.0;
+            if (m > nmax) m = nmax;
+            g.n[a] = (int)m;
+            g.lo[a] = d.lo[a];
+            g.len[a] = d.len[a];
+            g.S[a] = d.len[a] / m;
+        } else {
+            g.n[a] = 1; g.lo[a] = 0.0; g.len[a] = 1.0; g.S[a] = 1.0;
+        }
+    }
+    return g;
+}
+
+// The minimum image taken in cell units (|c_i - c_j| <= n/2, then |r| < len/2 + S) picks
+// the true image of every pair closer than rc when len >= 2 rc + 2 S on each periodic axis:
+// the other images are at least len - rc away.
+static inline bool rel_grid_periodic_ok(const RelGrid& g, int dim, double rc) {
+    for (int a = 0; a < dim; ++a)
+        if (((g.periodic >> a) & 1u) && g.len[a] < 2.0 * rc + 2.0 * g.S[a]) return false;
+    return true;
+}
+
+template <int DIM>
+__device__ __forceinline__ int rel_cell_of(uint32_t bits, int a) {
+    return DIM == 3 ? (int)((bits >> (10 * a)) & 1023u) : (int)((bits >> (15 * a)) & 32767u);
+}
+
+// Encode one position (float64 x per axis) as offsets and packed cells.
+template <int DIM>
+__device__ __forceinline__ uint32_t rel_encode(const double* x, const RelGrid& g, float* o) {
+    uint32_t bits = 0;
+    for (int a = 0; a < DIM; ++a) {
+        double rel = x[a] - g.lo[a];
+        double c = floor(rel / g.S[a]);
+        if (((g.periodic >> a) & 1u) && c >= g.n[a]) { rel -= g.len[a]; c = floor(rel / g.S[a]); }
+        if (c < 0.0) c = 0.0;
+        if (c > g.n[a] - 1) c = g.n[a] - 1;
+        o[a] = (float)(rel - c * g.S[a]);
+        bits |= (uint32_t)c << (DIM == 3 ? 10 * a : 15 * a);
+    }
+    return bits;
+}
+
+// r_ij from two encoded positions; ncell per axis, cell size split S = Sh + Sl into
+// two floats (so the c S part carries no float32 rounding of S, which would bias
+// every pair of the same cell offset alike), minimum image in cell units.
+template <int DIM, bool PER>
+__device__ __forceinline__ void rel_pair(const float* oi, uint32_t bi, const float* oj, uint32_t bj,
+                                         const int* ncell, const float* Sh, const float* Sl, uint32_t periodic,
+                                         float* r, float& d2) {
+    d2 = 0.0f;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        int dc = rel_cell_of<DIM>(bi, a) - rel_cell_of<DIM>(bj, a);
+        if (PER && ((periodic >> a) & 1u)) {
+            if (2 * dc > ncell[a]) dc -= ncell[a];
+            else if (2 * dc < -ncell[a]) dc += ncell[a];
+        }
+        float fdc = (float)dc;
+        r[a] = fmaf(fdc, Sh[a], fmaf(fdc, Sl[a], oi[a] - oj[a]));
+        d2 = fmaf(r[a], r[a], d2);
+    }
+}
 
 // Plain accumulator with the same interface (float64 path).
 template <typename R>

@@ -15,6 +15,8 @@ struct EulerK {
     R rho0, c0, inv_c0, c0sq, eta, mu2, eps_h2, dt;
     R half[3];
     R Lh[3], Ll[3];   // box length split hi + lo (float32 path; Ll = 0 in float64)
+    R S[3], Sl[3];    // float32 path: cell size (hi + lo) of the cell-relative positions
+    int ncell[3];
     uint32_t periodic;
 };
 
@@ -82,43 +84,107 @@ __device__ __forceinline__ void euler_pair(const R* r, R d2, const R* Bi, const 
 }
 
 // ---------------------------------------------------------------- float32 path
-template <int DIM> struct Rec32;
-template <> struct Rec32<2> { static constexpr int words = 2; };
-template <> struct Rec32<3> { static constexpr int words = 4; };
+// Records of 16 floats (two 32-byte lines, two 256-bit loads per neighbour):
+//   3D: (ox, oy, oz, cell, V, B00, B01, B02) (B11, B12, B22, 0, vx, vy, vz, drho)
+//   2D: (ox, oy, cell, V, B00, B01, B11, 0) (0, 0, 0, 0, vx, vy, 0, drho)
+// positions cell-relative (see rel_pair); the dynamic part (v, drho) is the
+// float4 at offset 12, the only part a pass writes (into the other buffer).
+constexpr int kRecWords = 16;
 
 template <int DIM>
-__device__ __forceinline__ void load_geo32(const float4* __restrict__ geo, int64_t i, float* xh, float* xl,
-                                           float& V, float* Bs) {
-    if (DIM == 2) {
-        float4 a = __ldg(&geo[2 * i]);
-        float4 b = __ldg(&geo[2 * i + 1]);
-        xh[0] = a.x; xh[1] = a.y; xl[0] = a.z; xl[1] = a.w;
-        V = b.x; Bs[0] = b.y; Bs[1] = b.z; Bs[2] = b.w;
+__device__ __forceinline__ void unpack_rec(const F8& a, const F8& b, float* o, uint32_t& cell, float& V, float* Bs,
+                                           float* v, float& drho) {
+    if constexpr (DIM == 3) {
+        o[0] = a.v[0]; o[1] = a.v[1]; o[2] = a.v[2];
+        cell = __float_as_uint(a.v[3]);
+        V = a.v[4];
+        Bs[0] = a.v[5]; Bs[1] = a.v[6]; Bs[2] = a.v[7];
+        Bs[3] = b.v[0]; Bs[4] = b.v[1]; Bs[5] = b.v[2];
+        v[0] = b.v[4]; v[1] = b.v[5]; v[2] = b.v[6];
     } else {
-        float4 a = __ldg(&geo[4 * i]);
-        float4 b = __ldg(&geo[4 * i + 1]);
-        float4 c = __ldg(&geo[4 * i + 2]);
-        float d = __ldg(reinterpret_cast<const float*>(&geo[4 * i + 3]));
-        xh[0] = a.x; xh[1] = a.y; xh[2] = a.z; V = a.w;
-        xl[0] = b.x; xl[1] = b.y; xl[2] = b.z; Bs[0] = b.w;
-        Bs[1] = c.x; Bs[2] = c.y; Bs[3] = c.z; Bs[4] = c.w; Bs[5] = d;
+        o[0] = a.v[0]; o[1] = a.v[1];
+        cell = __float_as_uint(a.v[2]);
+        V = a.v[3];
+        Bs[0] = a.v[4]; Bs[1] = a.v[5]; Bs[2] = a.v[6];
+        v[0] = b.v[4]; v[1] = b.v[5];
+    }
+    drho = b.v[7];
+}
+
+template <int DIM>
+__device__ __forceinline__ void store_dyn(float* rec, int64_t i, const float* v, float drho) {
+    float vz = 0.0f;
+    if constexpr (DIM == 3) vz = v[2];
+    *reinterpret_cast<float4*>(rec + kRecWords * i + 12) = make_float4(v[0], v[1], vz, drho);
+}
+
+// Pair loop of one particle over its CSR row (LANES lanes per row, compensated
+// sums, next neighbour's record loaded before the current pair is evaluated).
+template <int DIM, int MODE, int LANES, bool PER>
+__device__ __forceinline__ void euler_row32(const float* __restrict__ R, const int32_t* __restrict__ col,
+                                            int64_t b, int64_t e, int lane, const float* oi, uint32_t bi,
+                                            const float* Bi, const float* vi, float dri, const EulerK<float>& K,
+                                            float& rm, float* rp) {
+    constexpr int NS = NSym<DIM>::v;
+    Kahan<float> am;
+    Kahan<float> ap[DIM];
+    am.init();
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) ap[a].init();
+    int64_t p = b + lane;
+    int j = p < e ? __ldg(&col[p]) : -1;
+    F8 ja, jb;
+    if (j >= 0) { ja = ldg8(R + kRecWords * (int64_t)j); jb = ldg8(R + kRecWords * (int64_t)j + 8); }
+    while (j >= 0) {
+        int64_t pn = p + LANES;
+        int jn = pn < e ? __ldg(&col[pn]) : -1;
+        F8 na = ja, nb2 = jb;
+        if (jn >= 0) { na = ldg8(R + kRecWords * (int64_t)jn); nb2 = ldg8(R + kRecWords * (int64_t)jn + 8); }
+        float oj[DIM], Vj, Bj[NS], vj[DIM], drj;
+        uint32_t bj;
+        unpack_rec<DIM>(ja, jb, oj, bj, Vj, Bj, vj, drj);
+        float r[DIM], d2;
+        rel_pair<DIM, PER>(oi, bi, oj, bj, K.ncell, K.S, K.Sl, K.periodic, r, d2);
+        float m = 0.0f, mo[DIM];
+        euler_pair<DIM, MODE, float>(r, d2, Bi, Bj, vi, vj, dri, drj, Vj, K, m, mo);
+        if (MODE & WANT_MASS) am.add(m);
+        if (MODE & WANT_MOM) {
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) ap[a].add(mo[a]);
+        }
+        p = pn;
+        j = jn;
+        ja = na;
+        jb = nb2;
+    }
+    rm = group_sum<LANES>(am.value());
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) rp[a] = group_sum<LANES>(ap[a].value());
+}
+
+// Epilogue of the two-pass step / fused step: new (v, drho) of particle i.
+template <int DIM, int OUT>
+__device__ __forceinline__ void euler_update32(const float* vi, float dri, float rm, const float* rp,
+                                               const EulerK<float>& K, float* vn, float& drn) {
+    float rho_i = K.rho0 + dri;
+    if (OUT == OUT_MOM) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) vn[a] = vi[a] + K.dt * rp[a] / rho_i;
+        drn = dri;
+    } else if (OUT == OUT_MASS) {
+        float ddr = K.dt * rm;
+        drn = dri + ddr;
+        float ratio = 1.0f - ddr / (K.rho0 + drn);     // rho^n / rho^{n+1}
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) vn[a] = vi[a] * ratio;
+    } else {
+        float ddr = K.dt * rm;
+        drn = dri + ddr;
+        float rho1 = K.rho0 + drn;
+        float ratio = 1.0f - ddr / rho1;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) vn[a] = vi[a] * ratio + K.dt * rp[a] / rho1;
     }
 }
-
-template <int DIM>
-__device__ __forceinline__ void load_q32(const float4* __restrict__ q, int64_t i, float* v, float& drho) {
-    float4 a = __ldg(&q[i]);
-    if (DIM == 2) { v[0] = a.x; v[1] = a.y; drho = a.z; }
-    else { v[0] = a.x; v[1] = a.y; v[2] = a.z; drho = a.w; }
-}
-
-template <int DIM>
-__device__ __forceinline__ void store_q32(float4* q, int64_t i, const float* v, float drho) {
-    float4 a;
-    if (DIM == 2) { a.x = v[0]; a.y = v[1]; a.z = drho; a.w = 0.0f; }
-    else { a.x = v[0]; a.y = v[1]; a.z = v[2]; a.w = drho; }
-    q[i] = a;
-}
-
 
 }  // namespace euler

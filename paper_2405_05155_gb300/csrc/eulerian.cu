@@ -2,9 +2,10 @@
 //
 // Two pair-pass kernels share one per-pair device function:
 //  * k_euler64: float64 structure-of-arrays state, one thread per particle;
-//  * k_euler32: float32 packed records (positions split hi+lo so that r_ij keeps
-//    ~1e-7 relative accuracy in any box), LANES consecutive lanes per particle
-//    striding over the CSR row, compensated (Kahan) sums, group shuffle reduce.
+//  * k_euler32: float32 records of 16 floats (two 32-byte lines: cell-relative
+//    position, volume, B, velocity, density; two 256-bit loads per neighbour),
+//    LANES consecutive lanes per particle striding over the CSR row, compensated
+//    (Kahan) sums, group shuffle reduce.
 // A pass computes the mass and/or momentum rates of a particle and applies the
 // pointwise part of the update in its epilogue (EOS p = c0^2 drho, velocity
 // from momentum), so a step is one (fused) or two (momentum, continuity) launches.
@@ -80,130 +81,79 @@ __global__ void k_euler64(const double* __restrict__ pos, const double* __restri
     }
 }
 
-template <int DIM, int MODE, int OUT, int LANES>
-__global__ void __launch_bounds__(256) k_euler32(const float4* __restrict__ geo, const int64_t* __restrict__ row_ptr,
-                                                 const int32_t* __restrict__ col, int64_t n, EulerK<float> K,
-                                                 const float4* __restrict__ q, float4* __restrict__ q_out,
-                                                 double* __restrict__ rate_mass, double* __restrict__ rate_mom) {
+// ---------------------------------------------------------------- float32 path
+template <int DIM, int MODE, int OUT, int LANES, bool PER>
+__global__ void __launch_bounds__(256) k_euler32(const float* __restrict__ Rin, float* __restrict__ Rout,
+                                                 const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                                 int64_t n, EulerK<float> K, double* __restrict__ rate_mass,
+                                                 double* __restrict__ rate_mom) {
     constexpr int NS = NSym<DIM>::v;
     int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = gt / LANES;
     int lane = (int)(gt % LANES);
     bool active = i < n;
     int64_t ii = active ? i : 0;
-    float xhi[DIM], xli[DIM], Vi, Bi[NS], vi[DIM], dri;
-    load_geo32<DIM>(reinterpret_cast<const float4*>(geo), ii, xhi, xli, Vi, Bi);
-    load_q32<DIM>(q, ii, vi, dri);
-    Kahan<float> am;
-    Kahan<float> ap[DIM];
-    am.init();
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) ap[a].init();
+    F8 ma = ldg8(Rin + kRecWords * ii), mb = ldg8(Rin + kRecWords * ii + 8);
+    float oi[DIM], Vi, Bi[NS], vi[DIM], dri;
+    uint32_t bi;
+    unpack_rec<DIM>(ma, mb, oi, bi, Vi, Bi, vi, dri);
     int64_t b = active ? row_ptr[ii] : 0, e = active ? row_ptr[ii + 1] : 0;
-    for (int64_t p = b + lane; p < e; p += LANES) {
-        int j = __ldg(&col[p]);
-        float xhj[DIM], xlj[DIM], Vj, Bj[NS], vj[DIM], drj;
-        load_geo32<DIM>(geo, j, xhj, xlj, Vj, Bj);
-        load_q32<DIM>(q, j, vj, drj);
-        float r[DIM], d2 = 0.0f;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            float dh = xhi[a] - xhj[a];
-            float dl = xli[a] - xlj[a];
-            if ((K.periodic >> a) & 1u) {
-                if (dh > K.half[a]) { dh -= K.Lh[a]; dl -= K.Ll[a]; }
-                else if (dh < -K.half[a]) { dh += K.Lh[a]; dl += K.Ll[a]; }
-            }
-            r[a] = dh + dl;
-            d2 = fmaf(r[a], r[a], d2);
-        }
-        float m = 0.0f, mo[DIM];
-        euler_pair<DIM, MODE, float>(r, d2, Bi, Bj, vi, vj, dri, drj, Vj, K, m, mo);
-        if (MODE & WANT_MASS) am.add(m);
-        if (MODE & WANT_MOM) {
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) ap[a].add(mo[a]);
-        }
-    }
-    float rm = group_sum<LANES>(am.value());
-    float rp[DIM];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) rp[a] = group_sum<LANES>(ap[a].value());
+    float rm, rp[DIM];
+    euler_row32<DIM, MODE, LANES, PER>(Rin, col, b, e, lane, oi, bi, Bi, vi, dri, K, rm, rp);
     if (!active || lane != 0) return;
-    float rho_i = K.rho0 + dri;
-    float vn[DIM];
     if (OUT == OUT_RATES) {
         if (MODE & WANT_MASS) rate_mass[i] = (double)rm;
         if (MODE & WANT_MOM)
             for (int a = 0; a < DIM; ++a) rate_mom[a * n + i] = (double)rp[a];
-    } else if (OUT == OUT_MOM) {
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) vn[a] = vi[a] + K.dt * rp[a] / rho_i;
-        store_q32<DIM>(q_out, i, vn, dri);
-    } else if (OUT == OUT_MASS) {
-        float ddr = K.dt * rm;
-        float dr1 = dri + ddr;
-        float ratio = 1.0f - ddr / (K.rho0 + dr1);     // rho^n / rho^{n+1}
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) vn[a] = vi[a] * ratio;
-        store_q32<DIM>(q_out, i, vn, dr1);
-    } else {
-        float ddr = K.dt * rm;
-        float dr1 = dri + ddr;
-        float rho1 = K.rho0 + dr1;
-        float ratio = 1.0f - ddr / rho1;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) vn[a] = vi[a] * ratio + K.dt * rp[a] / rho1;
-        store_q32<DIM>(q_out, i, vn, dr1);
+        return;
     }
+    float vn[DIM], drn;
+    euler_update32<DIM, OUT>(vi, dri, rm, rp, K, vn, drn);
+    store_dyn<DIM>(Rout, i, vn, drn);
 }
 
 // ---------------------------------------------------------------- pack / unpack
 template <int DIM>
-__global__ void k_pack_geo(const double* __restrict__ pos, const double* __restrict__ vol,
-                           const double* __restrict__ B, int64_t n, float* __restrict__ geo) {
+__global__ void k_pack_rec(const double* __restrict__ pos, const double* __restrict__ vol,
+                           const double* __restrict__ B, const double* __restrict__ drho,
+                           const double* __restrict__ v, int64_t n, RelGrid g, float* __restrict__ R0,
+                           float* __restrict__ R1) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float xh[3], xl[3];
-    for (int a = 0; a < DIM; ++a) {
-        double x = pos[a * n + i];
-        xh[a] = (float)x;
-        xl[a] = (float)(x - (double)xh[a]);
-    }
-    if (DIM == 2) {
-        float* g = geo + 8 * i;
-        g[0] = xh[0]; g[1] = xh[1]; g[2] = xl[0]; g[3] = xl[1];
-        g[4] = (float)vol[i]; g[5] = (float)B[i]; g[6] = (float)B[n + i]; g[7] = (float)B[2 * n + i];
+    double x[3] = {0, 0, 0};
+    for (int a = 0; a < DIM; ++a) x[a] = pos[a * n + i];
+    float o[3] = {0, 0, 0};
+    uint32_t bits = rel_encode<DIM>(x, g, o);
+    float rec[kRecWords];
+    for (int k = 0; k < kRecWords; ++k) rec[k] = 0.0f;
+    if (DIM == 3) {
+        rec[0] = o[0]; rec[1] = o[1]; rec[2] = o[2]; rec[3] = __uint_as_float(bits);
+        rec[4] = (float)vol[i];
+        for (int s = 0; s < 6; ++s) rec[5 + s] = (float)B[s * n + i];
     } else {
-        float* g = geo + 16 * i;
-        g[0] = xh[0]; g[1] = xh[1]; g[2] = xh[2]; g[3] = (float)vol[i];
-        g[4] = xl[0]; g[5] = xl[1]; g[6] = xl[2]; g[7] = (float)B[i];
-        g[8] = (float)B[n + i]; g[9] = (float)B[2 * n + i]; g[10] = (float)B[3 * n + i]; g[11] = (float)B[4 * n + i];
-        g[12] = (float)B[5 * n + i]; g[13] = 0.0f; g[14] = 0.0f; g[15] = 0.0f;
+        rec[0] = o[0]; rec[1] = o[1]; rec[2] = __uint_as_float(bits); rec[3] = (float)vol[i];
+        for (int s = 0; s < 3; ++s) rec[4 + s] = (float)B[s * n + i];
+    }
+    for (int a = 0; a < DIM; ++a) rec[12 + a] = (float)v[a * n + i];
+    rec[15] = (float)drho[i];
+    float4* d0 = reinterpret_cast<float4*>(R0 + kRecWords * i);
+    float4* d1 = reinterpret_cast<float4*>(R1 + kRecWords * i);
+    for (int k = 0; k < 4; ++k) {
+        float4 w = make_float4(rec[4 * k], rec[4 * k + 1], rec[4 * k + 2], rec[4 * k + 3]);
+        d0[k] = w;
+        d1[k] = w;
     }
 }
 
 template <int DIM>
-__global__ void k_pack_q(const double* __restrict__ drho, const double* __restrict__ v, int64_t n,
-                         float4* __restrict__ q) {
+__global__ void k_unpack_rec(const float* __restrict__ R, int64_t n, double* __restrict__ drho,
+                             double* __restrict__ v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float vv[DIM];
-    for (int a = 0; a < DIM; ++a) vv[a] = (float)v[a * n + i];
-    store_q32<DIM>(q, i, vv, (float)drho[i]);
-}
-
-template <int DIM>
-__global__ void k_unpack_q(const float4* __restrict__ q, int64_t n, double* __restrict__ drho,
-                           double* __restrict__ v) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float vv[DIM], dr;
-    float4 a = q[i];
-    if (DIM == 2) { vv[0] = a.x; vv[1] = a.y; dr = a.z; }
-    else { vv[0] = a.x; vv[1] = a.y; vv[2] = a.z; dr = a.w; }
-    drho[i] = dr;
-    for (int c = 0; c < DIM; ++c) v[c * n + i] = vv[c];
+    float4 d = *reinterpret_cast<const float4*>(R + kRecWords * i + 12);
+    float vv[3] = {d.x, d.y, d.z};
+    drho[i] = d.w;
+    for (int a = 0; a < DIM; ++a) v[a * n + i] = vv[a];
 }
 
 template <typename R>
@@ -223,10 +173,14 @@ EulerK<R> make_consts(const sph_eulerian_params* p) {
     K.eps_h2 = (R)(0.01 * h * h);
     K.dt = (R)p->dt;
     K.periodic = d.periodic_mask;
+    RelGrid g = make_rel_grid(d);
     for (int a = 0; a < 3; ++a) {
         K.half[a] = (R)(0.5 * d.len[a]);
         K.Lh[a] = (R)d.len[a];
         K.Ll[a] = (R)(d.len[a] - (double)K.Lh[a]);
+        K.S[a] = (R)g.S[a];
+        K.Sl[a] = (R)(g.S[a] - (double)K.S[a]);
+        K.ncell[a] = g.n[a];
     }
     return K;
 }
@@ -239,6 +193,11 @@ int check_params(const sph_eulerian_params* p, const sph_eulerian_state* st) {
     if (p->integrator != SPH_TWO_PASS && p->integrator != SPH_FUSED) return SPH_ERR_ARG;
     if (!(p->c0 > 0.0) || !(p->rho0 > 0.0) || !(p->mu >= 0.0) || !(p->eta >= 0.0)) return SPH_ERR_ARG;
     if (p->dom.n > 0 && (!st->row_ptr || !st->col)) return SPH_ERR_ARG;
+    if (p->precision == SPH_FP32_KAHAN) {
+        // the cell-relative minimum image needs len >= 2 kappa h + 2 S on periodic axes
+        if (!rel_grid_periodic_ok(make_rel_grid(p->dom), p->dom.dim, p->dom.kappa * p->dom.h)) return SPH_ERR_ARG;
+        if (((uintptr_t)st->rec & 31u) || ((uintptr_t)st->rec_tmp & 31u)) return SPH_ERR_ARG;
+    }
     return SPH_OK;
 }
 
@@ -257,14 +216,13 @@ void launch64(int mode, int out, const sph_eulerian_params* p, const sph_euleria
 #undef L64
 }
 
-template <int DIM, int LANES>
+template <int DIM, int LANES, bool PER>
 void launch32(int out, const sph_eulerian_params* p, const sph_eulerian_state* st, const EulerK<float>& K,
-              const float4* q, float4* q_out, double* rm, double* rp, cudaStream_t s) {
+              const float* rin, float* rout, double* rm, double* rp, cudaStream_t s) {
     int64_t n = p->dom.n;
     const int block = 256;
     dim3 g(grid_for(n * LANES, block)), b(block);
-    const float4* geo = reinterpret_cast<const float4*>(st->geo);
-#define L32(M, O) k_euler32<DIM, M, O, LANES><<<g, b, 0, s>>>(geo, st->row_ptr, st->col, n, K, q, q_out, rm, rp)
+#define L32(M, O) k_euler32<DIM, M, O, LANES, PER><<<g, b, 0, s>>>(rin, rout, st->row_ptr, st->col, n, K, rm, rp)
     if (out == OUT_RATES) L32(WANT_BOTH, OUT_RATES);
     else if (out == OUT_MOM) L32(WANT_MOM, OUT_MOM);
     else if (out == OUT_MASS) L32(WANT_MASS, OUT_MASS);
@@ -272,14 +230,26 @@ void launch32(int out, const sph_eulerian_params* p, const sph_eulerian_state* s
 #undef L32
 }
 
-template <int DIM>
-void dispatch32(int g_lanes, int out, const sph_eulerian_params* p, const sph_eulerian_state* st, const EulerK<float>& K,
-                const float4* q, float4* q_out, double* rm, double* rp, cudaStream_t s) {
-    switch (g_lanes) {
-        case 1: launch32<DIM, 1>(out, p, st, K, q, q_out, rm, rp, s); break;
-        case 2: launch32<DIM, 2>(out, p, st, K, q, q_out, rm, rp, s); break;
-        case 8: launch32<DIM, 8>(out, p, st, K, q, q_out, rm, rp, s); break;
-        default: launch32<DIM, 4>(out, p, st, K, q, q_out, rm, rp, s); break;
+template <int DIM, bool PER>
+void dispatch32p(int lanes, int out, const sph_eulerian_params* p, const sph_eulerian_state* st,
+                 const EulerK<float>& K, const float* rin, float* rout, double* rm, double* rp, cudaStream_t s) {
+    switch (lanes) {
+        case 1: launch32<DIM, 1, PER>(out, p, st, K, rin, rout, rm, rp, s); break;
+        case 2: launch32<DIM, 2, PER>(out, p, st, K, rin, rout, rm, rp, s); break;
+        case 8: launch32<DIM, 8, PER>(out, p, st, K, rin, rout, rm, rp, s); break;
+        default: launch32<DIM, 4, PER>(out, p, st, K, rin, rout, rm, rp, s); break;
+    }
+}
+
+void dispatch32(int lanes, int out, const sph_eulerian_params* p, const sph_eulerian_state* st,
+                const EulerK<float>& K, const float* rin, float* rout, double* rm, double* rp, cudaStream_t s) {
+    bool per = p->dom.periodic_mask != 0;
+    if (p->dom.dim == 2) {
+        if (per) dispatch32p<2, true>(lanes, out, p, st, K, rin, rout, rm, rp, s);
+        else dispatch32p<2, false>(lanes, out, p, st, K, rin, rout, rm, rp, s);
+    } else {
+        if (per) dispatch32p<3, true>(lanes, out, p, st, K, rin, rout, rm, rp, s);
+        else dispatch32p<3, false>(lanes, out, p, st, K, rin, rout, rm, rp, s);
     }
 }
 
@@ -292,15 +262,15 @@ extern "C" int sph_eulerian_pack(sph_ctx* ctx, const sph_eulerian_params* p, con
     if (r) return r;
     int64_t n = p->dom.n;
     if (n == 0) return SPH_OK;
-    if (!st->pos || !st->vol || !st->B || !st->drho || !st->v || !st->geo || !st->q) return SPH_ERR_ARG;
+    if (!st->pos || !st->vol || !st->B || !st->drho || !st->v || !st->rec || !st->rec_tmp) return SPH_ERR_ARG;
     cudaStream_t s = as_stream(stream);
-    if (p->dom.dim == 2) {
-        k_pack_geo<2><<<grid_for(n, 256), 256, 0, s>>>(st->pos, st->vol, st->B, n, st->geo);
-        k_pack_q<2><<<grid_for(n, 256), 256, 0, s>>>(st->drho, st->v, n, reinterpret_cast<float4*>(st->q));
-    } else {
-        k_pack_geo<3><<<grid_for(n, 256), 256, 0, s>>>(st->pos, st->vol, st->B, n, st->geo);
-        k_pack_q<3><<<grid_for(n, 256), 256, 0, s>>>(st->drho, st->v, n, reinterpret_cast<float4*>(st->q));
-    }
+    RelGrid g = make_rel_grid(p->dom);
+    if (p->dom.dim == 2)
+        k_pack_rec<2><<<grid_for(n, 256), 256, 0, s>>>(st->pos, st->vol, st->B, st->drho, st->v, n, g, st->rec,
+                                                       st->rec_tmp);
+    else
+        k_pack_rec<3><<<grid_for(n, 256), 256, 0, s>>>(st->pos, st->vol, st->B, st->drho, st->v, n, g, st->rec,
+                                                       st->rec_tmp);
     SPH_LAUNCH_CHECK(ctx);
     return SPH_OK;
 }
@@ -312,11 +282,10 @@ extern "C" int sph_eulerian_unpack(sph_ctx* ctx, const sph_eulerian_params* p, c
     if (r) return r;
     int64_t n = p->dom.n;
     if (n == 0) return SPH_OK;
-    if (!st->drho || !st->v || !st->q) return SPH_ERR_ARG;
+    if (!st->drho || !st->v || !st->rec) return SPH_ERR_ARG;
     cudaStream_t s = as_stream(stream);
-    const float4* q = reinterpret_cast<const float4*>(st->q);
-    if (p->dom.dim == 2) k_unpack_q<2><<<grid_for(n, 256), 256, 0, s>>>(q, n, st->drho, st->v);
-    else k_unpack_q<3><<<grid_for(n, 256), 256, 0, s>>>(q, n, st->drho, st->v);
+    if (p->dom.dim == 2) k_unpack_rec<2><<<grid_for(n, 256), 256, 0, s>>>(st->rec, n, st->drho, st->v);
+    else k_unpack_rec<3><<<grid_for(n, 256), 256, 0, s>>>(st->rec, n, st->drho, st->v);
     SPH_LAUNCH_CHECK(ctx);
     return SPH_OK;
 }
@@ -336,11 +305,9 @@ extern "C" int sph_eulerian_rates(sph_ctx* ctx, const sph_eulerian_params* p, co
         if (p->dom.dim == 2) launch64<2>(0, OUT_RATES, p, st, K, st->drho, st->v, nullptr, nullptr, drho_dt, dmom_dt, s);
         else launch64<3>(0, OUT_RATES, p, st, K, st->drho, st->v, nullptr, nullptr, drho_dt, dmom_dt, s);
     } else {
-        if (!st->geo || !st->q) return SPH_ERR_ARG;
+        if (!st->rec) return SPH_ERR_ARG;
         EulerK<float> K = make_consts<float>(p);
-        const float4* q = reinterpret_cast<const float4*>(st->q);
-        if (p->dom.dim == 2) dispatch32<2>(ctx->lanes[SPH_PASS_EULERIAN], OUT_RATES, p, st, K, q, nullptr, drho_dt, dmom_dt, s);
-        else dispatch32<3>(ctx->lanes[SPH_PASS_EULERIAN], OUT_RATES, p, st, K, q, nullptr, drho_dt, dmom_dt, s);
+        dispatch32(ctx->lanes[SPH_PASS_EULERIAN], OUT_RATES, p, st, K, st->rec, nullptr, drho_dt, dmom_dt, s);
     }
     SPH_LAUNCH_CHECK(ctx);
     return SPH_OK;
@@ -385,50 +352,47 @@ extern "C" int sph_eulerian_step(sph_ctx* ctx, const sph_eulerian_params* p, con
         }
         return SPH_OK;
     }
-    if (!st->geo || !st->q || !st->q_tmp) return SPH_ERR_ARG;
+    if (!st->rec || !st->rec_tmp) return SPH_ERR_ARG;
     EulerK<float> K = make_consts<float>(p);
-    float4* q0 = reinterpret_cast<float4*>(st->q);
-    float4* q1 = reinterpret_cast<float4*>(st->q_tmp);
+    float* r0 = st->rec;
+    float* r1 = st->rec_tmp;
     int lanes = ctx->lanes[SPH_PASS_EULERIAN];
     for (int k = 0; k < nsteps; ++k) {
         if (p->integrator == SPH_TWO_PASS) {
             int t = sph_timer_begin(ctx, SPH_TIMER_EU_MOMENTUM, s);
-            if (dim == 2) dispatch32<2>(lanes, OUT_MOM, p, st, K, q0, q1, nullptr, nullptr, s);
-            else dispatch32<3>(lanes, OUT_MOM, p, st, K, q0, q1, nullptr, nullptr, s);
+            dispatch32(lanes, OUT_MOM, p, st, K, r0, r1, nullptr, nullptr, s);
             sph_timer_end(ctx, t, s);
             t = sph_timer_begin(ctx, SPH_TIMER_EU_MASS, s);
-            if (dim == 2) dispatch32<2>(lanes, OUT_MASS, p, st, K, q1, q0, nullptr, nullptr, s);
-            else dispatch32<3>(lanes, OUT_MASS, p, st, K, q1, q0, nullptr, nullptr, s);
+            dispatch32(lanes, OUT_MASS, p, st, K, r1, r0, nullptr, nullptr, s);
             sph_timer_end(ctx, t, s);
         } else {
             int t = sph_timer_begin(ctx, SPH_TIMER_EU_FUSED, s);
-            if (dim == 2) dispatch32<2>(lanes, OUT_FUSED, p, st, K, q0, q1, nullptr, nullptr, s);
-            else dispatch32<3>(lanes, OUT_FUSED, p, st, K, q0, q1, nullptr, nullptr, s);
+            dispatch32(lanes, OUT_FUSED, p, st, K, r0, r1, nullptr, nullptr, s);
             sph_timer_end(ctx, t, s);
-            float4* tt = q0; q0 = q1; q1 = tt;
+            float* tt = r0; r0 = r1; r1 = tt;
         }
     }
     SPH_LAUNCH_CHECK(ctx);
-    if (q0 != reinterpret_cast<float4*>(st->q))
-        SPH_CUDA(ctx, cudaMemcpyAsync(st->q, q0, n * sizeof(float4), cudaMemcpyDeviceToDevice, s));
+    if (r0 != st->rec)
+        SPH_CUDA(ctx, cudaMemcpyAsync(st->rec, r0, (size_t)n * kRecWords * 4, cudaMemcpyDeviceToDevice, s));
     return SPH_OK;
 }
 
 // Autotuner of the float32 pair passes (lanes per particle in {1, 2, 4, 8}); the
-// packed state q is saved before and restored after every trial.
+// dynamic state is saved before and restored after every trial.
 extern "C" int sph_autotune_eulerian(sph_ctx* ctx, const sph_eulerian_params* p, const sph_eulerian_state* st,
                                      int trial_steps, int* lanes_host, double* ms_host, void* stream) {
     if (!ctx || trial_steps < 1) return SPH_ERR_ARG;
     int r = check_params(p, st);
     if (r) return r;
-    if (p->precision != SPH_FP32_KAHAN || !st->geo || !st->q || !st->q_tmp) return SPH_ERR_ARG;
+    if (p->precision != SPH_FP32_KAHAN || !st->rec || !st->rec_tmp) return SPH_ERR_ARG;
     int64_t n = p->dom.n;
     if (n == 0) return SPH_OK;
     cudaStream_t s = as_stream(stream);
-    size_t bq = (size_t)n * 16;
+    size_t bq = (size_t)n * kRecWords * 4;
     void* save = sph_scratch(ctx, S_MISC3, bq, &r);
     if (r) return r;
-    SPH_CUDA(ctx, cudaMemcpyAsync(save, st->q, bq, cudaMemcpyDeviceToDevice, s));
+    SPH_CUDA(ctx, cudaMemcpyAsync(save, st->rec, bq, cudaMemcpyDeviceToDevice, s));
     cudaEvent_t e0, e1;
     SPH_CUDA(ctx, cudaEventCreate(&e0));
     SPH_CUDA(ctx, cudaEventCreate(&e1));
@@ -450,7 +414,8 @@ extern "C" int sph_autotune_eulerian(sph_ctx* ctx, const sph_eulerian_params* p,
         float ms = 0.0f;
         SPH_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
         if (ms < best) { best = ms; bl = lanes_set[li]; }
-        SPH_CUDA(ctx, cudaMemcpyAsync(st->q, save, bq, cudaMemcpyDeviceToDevice, s));
+        SPH_CUDA(ctx, cudaMemcpyAsync(st->rec, save, bq, cudaMemcpyDeviceToDevice, s));
+        SPH_CUDA(ctx, cudaMemcpyAsync(st->rec_tmp, save, bq, cudaMemcpyDeviceToDevice, s));
     }
     ctx->timing = timing;
     cudaEventDestroy(e0);

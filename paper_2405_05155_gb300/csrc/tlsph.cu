@@ -21,7 +21,7 @@ struct TLK {
     R inv_rho0, dt, lam, G;
     int law;
     R half[3], Lh[3], Ll[3];
-    R S[3];              // float32 path: cell size of the cell-relative position encoding
+    R S[3], Sl[3];       // float32 path: cell size (hi + lo) of the cell-relative positions
     int ncell[3];
     uint32_t periodic;
 };
@@ -270,41 +270,6 @@ __global__ void k_tl_defo64(const double* __restrict__ r0, const double* __restr
 // volume) and the momentum pass RM (position, M = P B0^T by columns, volume).
 constexpr uint32_t kFixedBit = 1u << 30;
 
-struct __align__(32) F8 {
-    float v[8];
-};
-
-// 256-bit read-only gather (the record is not written during the kernel).
-__device__ __forceinline__ F8 ldg8(const float* p) {
-    F8 r;
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]),
-          "=f"(r.v[7])
-        : "l"(p));
-    return r;
-}
-
-template <int DIM>
-__device__ __forceinline__ int cell_of(uint32_t bits, int a) {
-    return DIM == 3 ? (int)((bits >> (10 * a)) & 1023u) : (int)((bits >> (15 * a)) & 32767u);
-}
-
-template <int DIM, bool PER>
-__device__ __forceinline__ void pair_rel(const float* oi, uint32_t bi, const float* oj, uint32_t bj,
-                                         const TLK<float>& K, float* r, float& d2) {
-    d2 = 0.0f;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-        int dc = cell_of<DIM>(bi, a) - cell_of<DIM>(bj, a);
-        if (PER && ((K.periodic >> a) & 1u)) {
-            if (2 * dc > K.ncell[a]) dc -= K.ncell[a];
-            else if (2 * dc < -K.ncell[a]) dc += K.ncell[a];
-        }
-        r[a] = fmaf((float)dc, K.S[a], oi[a] - oj[a]);
-        d2 = fmaf(r[a], r[a], d2);
-    }
-}
-
 // Wendland gradient factor gs = (dW/dr)/r from d^2 (q = sqrt(d2)/h, no division).
 __device__ __forceinline__ float gs_from_d2(float d2, const TLK<float>& K) {
     float q = d2 * rsqrtf(fmaxf(d2, 1e-30f)) * K.inv_h;
@@ -390,7 +355,7 @@ __global__ void __launch_bounds__(256, 4) k_tl_mom32(const float* __restrict__ R
         float oj[DIM], r[DIM], d2;
 #pragma unroll
         for (int a = 0; a < DIM; ++a) oj[a] = r0.v[a];
-        pair_rel<DIM, PER>(oi, bi, oj, __float_as_uint(r0.v[DIM]), K, r, d2);
+        rel_pair<DIM, PER>(oi, bi, oj, __float_as_uint(r0.v[DIM]), K.ncell, K.S, K.Sl, K.periodic, r, d2);
         float Vj = DIM == 3 ? r0.v[7] : r0.v[3];
         float gs = gs_from_d2(d2, K) * Vj;
         if (DIM == 2) {
@@ -471,7 +436,7 @@ __global__ void __launch_bounds__(256, 4) k_tl_defo32(const float* __restrict__ 
         float oj[DIM], r[DIM], d2;
 #pragma unroll
         for (int a = 0; a < DIM; ++a) oj[a] = rj.v[a];
-        pair_rel<DIM, PER>(oi, bi, oj, __float_as_uint(rj.v[DIM]), K, r, d2);
+        rel_pair<DIM, PER>(oi, bi, oj, __float_as_uint(rj.v[DIM]), K.ncell, K.S, K.Sl, K.periodic, r, d2);
         float w = DIM == 3 ? rj.v[7] : rj.v[3];
         float gs = gs_from_d2(d2, K);
         float2 dv01 = __fmul2_rn(make_float2(w, w), __fadd2_rn(make_float2(rj.v[4], rj.v[5]), nv01));
@@ -527,32 +492,6 @@ __global__ void __launch_bounds__(256, 4) k_tl_defo32(const float* __restrict__ 
 }
 
 // ---------------------------------------------------------------- pack / unpack
-struct RelGrid {
-    double lo[3], len[3], S[3];
-    int n[3];
-    uint32_t periodic;
-};
-
-RelGrid make_rel_grid(const sph_domain& d) {
-    RelGrid g;
-    int nmax = d.dim == 3 ? 1023 : 32767;
-    g.periodic = d.periodic_mask;
-    for (int a = 0; a < 3; ++a) {
-        if (a < d.dim) {
-            double m = floor(d.len[a] / d.h);
-            if (m < 1.0) m = 1.0;
-            if (m > nmax) m = nmax;
-            g.n[a] = (int)m;
-            g.lo[a] = d.lo[a];
-            g.len[a] = d.len[a];
-            g.S[a] = d.len[a] / m;
-        } else {
-            g.n[a] = 1; g.lo[a] = 0.0; g.len[a] = 1.0; g.S[a] = 1.0;
-        }
-    }
-    return g;
-}
-
 template <int DIM>
 __global__ void k_tl_pack(const double* __restrict__ r0, const double* __restrict__ V0,
                           const double* __restrict__ B0, const uint8_t* __restrict__ fixed,
@@ -564,16 +503,9 @@ __global__ void k_tl_pack(const double* __restrict__ r0, const double* __restric
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float o[3] = {0, 0, 0};
-    uint32_t bits = 0;
-    for (int a = 0; a < DIM; ++a) {
-        double rel = r0[a * n + i] - g.lo[a];
-        double c = floor(rel / g.S[a]);
-        if (((g.periodic >> a) & 1u) && c >= g.n[a]) { rel -= g.len[a]; c = floor(rel / g.S[a]); }
-        if (c < 0.0) c = 0.0;
-        if (c > g.n[a] - 1) c = g.n[a] - 1;
-        o[a] = (float)(rel - c * g.S[a]);
-        bits |= (uint32_t)c << (DIM == 3 ? 10 * a : 15 * a);
-    }
+    double xr[3] = {0, 0, 0};
+    for (int a = 0; a < DIM; ++a) xr[a] = r0[a * n + i];
+    uint32_t bits = rel_encode<DIM>(xr, g, o);
     if (fixed && fixed[i]) bits |= kFixedBit;
     float V = (float)V0[i];
     float vv[3] = {0, 0, 0};
@@ -629,6 +561,7 @@ TLK<R> make_tl_consts(const sph_tlsph_params* p) {
         K.Lh[a] = (R)d.len[a];
         K.Ll[a] = (R)(d.len[a] - (double)K.Lh[a]);
         K.S[a] = (R)g.S[a];
+        K.Sl[a] = (R)(g.S[a] - (double)K.S[a]);
         K.ncell[a] = g.n[a];
     }
     return K;
@@ -643,10 +576,8 @@ int check_tl(const sph_tlsph_params* p, const sph_tlsph_state* st) {
     if (!(p->rho0 > 0.0)) return SPH_ERR_ARG;
     if (p->dom.n > 0 && (!st->row_ptr || !st->col || !st->r0 || !st->V0 || !st->B0)) return SPH_ERR_ARG;
     if (p->precision == SPH_FP32_KAHAN) {
-        // the cell-relative encoding needs at least 4 grid cells along a periodic axis
-        RelGrid g = make_rel_grid(p->dom);
-        for (int a = 0; a < p->dom.dim; ++a)
-            if (((p->dom.periodic_mask >> a) & 1u) && g.n[a] < 4) return SPH_ERR_ARG;
+        // the cell-relative minimum image needs len >= 2 kappa h + 2 S on periodic axes
+        if (!rel_grid_periodic_ok(make_rel_grid(p->dom), p->dom.dim, p->dom.kappa * p->dom.h)) return SPH_ERR_ARG;
     }
     return SPH_OK;
 }

@@ -61,9 +61,9 @@ def test_struct_layouts_match_header():
     # sph_domain: int32, uint32, int64, 2 doubles, 2 x 3 doubles = 80 bytes
     assert ctypes.sizeof(_lib.SphDomain) == 80
     assert ctypes.sizeof(_lib.EulerianParams) == 80 + 5 * 8 + 8
-    assert ctypes.sizeof(_lib.EulerianState) == 12 * 8
+    assert ctypes.sizeof(_lib.EulerianState) == 11 * 8
     assert ctypes.sizeof(_lib.TLParams) == 80 + 4 * 8 + 8
     assert ctypes.sizeof(_lib.TLState) == 15 * 8
     assert ctypes.sizeof(_lib.BatchCase) == 96
-    assert ctypes.sizeof(_lib.BatchState) == 5 * 8
+    assert ctypes.sizeof(_lib.BatchState) == 4 * 8
     assert ctypes.sizeof(_lib.RelaxParams) == 80 + 3 * 8 + 16 + 64 * 8

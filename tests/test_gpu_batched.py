@@ -37,9 +37,9 @@ def test_batched_matches_single_case_runs(ctx):
             sim.pack()
             sim.step(6)
             torch.cuda.synchronize()
-            single = sim.q.clone()
+            single = sim.rec.clone()
             t = b.table[c]
-            got = b.q[4 * t.offset: 4 * (t.offset + t.n)]
+            got = b.rec[16 * t.offset: 16 * (t.offset + t.n)]
             # same arithmetic per particle; the two kernels may contract a multiply-add differently
             assert rel_l2(host(got).astype(np.float64), host(single).astype(np.float64)) < 1e-6, c
     ctx.set_lanes(api.SPH_PASS_EULERIAN, 4)
@@ -77,4 +77,4 @@ def test_graph_is_recaptured_when_buffers_change(ctx):
     b1.step(1)
     b2.step(1)
     torch.cuda.synchronize()
-    assert torch.equal(b1.q, b2.q)
+    assert torch.equal(b1.rec, b2.rec)
