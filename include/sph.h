@@ -104,6 +104,10 @@ int sph_last_cuda_error(const sph_ctx* ctx);
 #define SPH_PASS_RELAX    2
 int sph_set_lanes(sph_ctx* ctx, int pass, int lanes);
 int sph_get_lanes(const sph_ctx* ctx, int pass);
+/* Most neighbour records a tile of a planned pass stages in shared memory (0: as
+ * many as the plan needs, within 96 KB); tiles with more read their neighbours from
+ * global memory.  A launch-shape setting, like the lanes: results do not depend on it. */
+int sph_set_stage_cap(sph_ctx* ctx, int cap);
 
 /* Per-kernel device timing (not part of the paper: measurement support).
  * sph_timing_enable(ctx, 1) clears the counters and makes the step entry points
@@ -134,10 +138,15 @@ int sph_kernel_eval(int kernel, int dim, double h, double kappa, int precision,
                     const double* r, double* w, double* dwdr, int64_t n, void* stream);
 
 /* ---- a1: cell binning and order ----
- * Permutation order[k] (int64, length n) sorting the particles by
- * (linear cell id, original index), stable.  Linear cell id
- * (c_z n_y + c_y) n_x + c_x with c_k = floor((x_k - lo_k)/size_k), wrapped on
- * periodic axes and clamped otherwise.  pos: float64 [dim][n].
+ * Sec. 2.3 (cell-linked lists).  Permutation order[k] (int64, length n) sorting the
+ * particles by (Morton key of the cell, original index), stable.  The cell is
+ * c_k = floor((x_k - lo_k)/size_k) with n_k = max(1, floor(len_k/(kappa h))) cells
+ * of size len_k/n_k per axis, wrapped on periodic axes and clamped otherwise.  The
+ * Morton key interleaves the coordinate bits level by level from the least
+ * significant, axes in order x, y, z; an axis with ceil(log2 n_k) bits drops out once
+ * they are used.  Particles consecutive in this order form compact groups, which the
+ * pair passes stage in shared memory.  pos: float64 [dim][n].  SPH_ERR_ARG when the
+ * key needs more than 29 bits or a position is non-finite (or outside a periodic box).
  * Synchronises the stream (to validate positions). */
 int sph_cell_order(sph_ctx* ctx, const sph_domain* dom, const double* pos,
                    int64_t* order, void* stream);
@@ -317,11 +326,26 @@ typedef struct {
  *   rm [n][16]: 3D (ox, oy, oz, cell, M00, M10, M20, V0, M01, M11, M21, 0, M02, M12, M22, 0)
  *   rm [n][8]:  2D (ox, oy, cell, V0, M00, M10, M01, M11)
  *   with M = P B0^T and a cell-relative position: per axis a grid of
- *   n_a = min(max(1, floor(len_a/h)), 1023 (3D) or 32767 (2D)) cells of size
+ *   n_a = min(max(1, floor(16 len_a/h)), 1023 (3D) or 32767 (2D)) cells of size
  *   S_a = len_a/n_a, integer cell c_a packed into `cell` (10 or 15 bits per axis,
  *   bit 30 set on clamped particles) and float offset o_a = x_a - lo_a - c_a S_a;
  *   H32 [dim*dim][n], u32 [dim][n] (x - r0), B32 [nsym][n].
- *   The float32 path needs at least 4 grid cells along a periodic axis. */
+ *   The float32 path needs len_a >= 2 kappa h + 2 S_a along a periodic axis.
+ * Tile plan (optional, float32 path): plan -> caller-owned device buffer of
+ *   plan_bytes >= sph_tlsph_plan_bytes(...) bytes, 16-byte aligned.  When plan is
+ *   set, sph_tlsph_pack builds in it, from row_ptr/col/r0/V0, (i) per tile of 128
+ *   consecutive rows the list of its distinct neighbours and (ii) per pair the
+ *   reference-configuration factor w_ij = grad0 W_ij V0_j of Eqs. 30-31, computed in
+ *   float64 and stored in float32 with the neighbour's position in its tile's list,
+ *   in a sliced order (pair k of row r of a tile at k*128 + r).  It writes plan_nnz,
+ *   plan_maxm (most distinct neighbours of a tile) and plan_maxp (most pairs of a
+ *   tile) into the struct.  The pair passes then stage each tile's neighbour M_j or
+ *   v_j in shared memory and read the pair factors from the plan: one thread per
+ *   row, the context's lanes setting unused.  Rows are best in sph_cell_order
+ *   (Morton) order, so that a tile is a compact group.  The plan must be rebuilt
+ *   (sph_tlsph_pack) whenever row_ptr, col, r0 or V0 change.  plan = NULL: the pair
+ *   factors are evaluated per pair from the records and neighbours are gathered from
+ *   global memory. */
 typedef struct {
     const int64_t* row_ptr;
     const int32_t* col;
@@ -338,10 +362,22 @@ typedef struct {
     float*  H32;
     float*  u32;
     float*  B32;
+    void*   plan;          /* optional tile plan buffer (see above) */
+    int64_t plan_bytes;
+    int64_t plan_nnz;      /* written by sph_tlsph_pack */
+    int32_t plan_maxm;     /* written by sph_tlsph_pack */
+    int32_t plan_maxp;     /* written by sph_tlsph_pack */
 } sph_tlsph_state;
 
+/* float64 state -> float32 records (and the tile plan when st->plan is set;
+ * that build synchronises the stream).  SPH_ERR_CAPACITY when plan_bytes is too
+ * small. */
 int sph_tlsph_pack(sph_ctx* ctx, const sph_tlsph_params* prm,
-                   const sph_tlsph_state* st, void* stream);
+                   sph_tlsph_state* st, void* stream);
+/* Bytes of the tile-plan buffer for the state's lists (reads row_ptr; synchronises
+ * the stream). */
+int sph_tlsph_plan_bytes(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_state* st,
+                         int64_t* bytes_host, void* stream);
 /* packed float32 (rd, H32, u32) -> float64 (v, H, x = r0 + u). */
 int sph_tlsph_unpack(sph_ctx* ctx, const sph_tlsph_params* prm,
                      const sph_tlsph_state* st, void* stream);

@@ -100,10 +100,31 @@ def cell_ids(pos, dom):
     return linear_cell_id(cell_coords(pos, dom), ncell)
 
 
+def morton_key(c, ncell):
+    """Morton (Z-order) key of integer cell coordinates c [dim][m].
+
+    Bit l of the coordinate on axis a is placed at the next free key position, level
+    by level from the least significant bit, axes in order; an axis with
+    b_a = ceil(log2 n_a) bits drops out once they are used (the reading of the
+    Morton key of the cell sort, Sec. 2.3)."""
+    c = np.asarray(c, dtype=np.int64)
+    dim = c.shape[0]
+    bits = [int(n - 1).bit_length() for n in ncell]
+    key = np.zeros(c.shape[1], dtype=np.int64)
+    at = 0
+    for level in range(max(bits) if bits else 0):
+        for a in range(dim):
+            if level < bits[a]:
+                key |= ((c[a] >> level) & 1) << at
+                at += 1
+    return key
+
+
 def cell_order(pos, dom):
-    """Permutation sorting particles by (cell id, original index), stable."""
-    ids = cell_ids(pos, dom)
-    return np.argsort(ids, kind="stable").astype(np.int64)
+    """Permutation sorting particles by (Morton key of the cell, original index), stable."""
+    ncell, _ = cell_grid(dom)
+    keys = morton_key(cell_coords(pos, dom), ncell)
+    return np.argsort(keys, kind="stable").astype(np.int64)
 
 
 def _csr_from_pairs(i, j, n):

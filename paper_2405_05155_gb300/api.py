@@ -62,6 +62,9 @@ class Context:
         except Exception:
             pass
 
+    def set_stage_cap(self, cap):
+        L.check("sph_set_stage_cap", self.lib.sph_set_stage_cap(self.h, int(cap)), self.h)
+
     def set_lanes(self, which, lanes):
         L.check("sph_set_lanes", self.lib.sph_set_lanes(self.h, which, lanes), self.h)
 
@@ -197,7 +200,7 @@ class TLSolid:
     """Total-Lagrangian solid state on the device."""
 
     def __init__(self, ctx, dom, r0, V0, B0, fixed, row_ptr, col, v, dt, rho0, lam, G, law=SPH_NEO_HOOKEAN,
-                 precision=SPH_FP64, x=None, H=None):
+                 precision=SPH_FP64, x=None, H=None, tiles=True):
         self.ctx = ctx
         dev = ctx.device
         self.n = r0.shape[1]
@@ -227,6 +230,14 @@ class TLSolid:
         for name in ("row_ptr", "col", "r0", "V0", "B0", "fixed", "x", "v", "H", "M", "rd", "rm", "H32", "u32",
                      "B32"):
             setattr(self.st, name, getattr(self, name).data_ptr())
+        self.plan = None
+        if tiles and precision == SPH_FP32_KAHAN:
+            # tile plan: pair factors precomputed and neighbours staged per tile (built by pack)
+            nb = ctypes.c_int64()
+            self._call("sph_tlsph_plan_bytes", ctypes.byref(nb), _stream())
+            self.plan = torch.empty(max(nb.value, 16), dtype=torch.uint8, device=dev)
+            self.st.plan = self.plan.data_ptr()
+            self.st.plan_bytes = self.plan.numel()
         if precision == SPH_FP32_KAHAN:
             self.pack()
 

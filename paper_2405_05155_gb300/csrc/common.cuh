@@ -41,6 +41,7 @@ struct sph_ctx {
     int* flags = nullptr;          // device status words (see FLAG_*)
     void* pinned = nullptr;        // small pinned host buffer for read-backs
     int lanes[4] = {4, 4, 4, 4};   // lanes per particle of the float32 pair passes (SPH_PASS_*)
+    int stage_cap = 0;             // most neighbour records a tile stages in shared memory (0: default)
     // batched Eulerian step: launch shape, captured graph and the case table it was made for
     int batch_block = 256;
     cudaGraphExec_t batch_graph = nullptr;
@@ -130,17 +131,24 @@ __device__ __forceinline__ float lg_gs<float>(float q, float coef) {
 
 // ---------------------------------------------------------------------------
 // Compensated (Kahan) accumulator.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
 template <typename R>
 struct Kahan {
     R s, c;
     __device__ __forceinline__ void init() { s = R(0); c = R(0); }
+    // every step rounds on its own (no multiply-add contraction with the caller's
+    // product), so a sum is the same wherever it is inlined
     __device__ __forceinline__ void add(R x) {
-        R y = x - c;
-        R t = s + y;
-        c = (t - s) - y;
+        R y = sub_rn(x, c);
+        R t = add_rn(s, y);
+        c = sub_rn(sub_rn(t, s), y);
         s = t;
     }
-    __device__ __forceinline__ R value() const { return s - c; }
+    __device__ __forceinline__ R value() const { return sub_rn(s, c); }
 };
 
 // Two compensated accumulators in one register pair, on Blackwell's paired
@@ -224,6 +232,16 @@ __device__ __forceinline__ int rel_cell_of(uint32_t bits, int a) {
     return DIM == 3 ? (int)((bits >> (10 * a)) & 1023u) : (int)((bits >> (15 * a)) & 32767u);
 }
 
+// The same cell coordinate as the float 2^23 + c: the 10 (15) bits or'ed into the
+// mantissa of 2^23.  The difference of two such floats is c_i - c_j exactly, with
+// no integer-to-float conversion.
+template <int DIM>
+__device__ __forceinline__ float rel_cell_f(uint32_t bits, int a) {
+    constexpr int B = DIM == 3 ? 10 : 15;
+    constexpr uint32_t M = (1u << B) - 1u;
+    return __uint_as_float(((bits >> (B * a)) & M) | 0x4B000000u);
+}
+
 // Encode one position (float64 x per axis) as offsets and packed cells.
 template <int DIM>
 __device__ __forceinline__ uint32_t rel_encode(const double* x, const RelGrid& g, float* o) {
@@ -250,12 +268,12 @@ __device__ __forceinline__ void rel_pair(const float* oi, uint32_t bi, const flo
     d2 = 0.0f;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        int dc = rel_cell_of<DIM>(bi, a) - rel_cell_of<DIM>(bj, a);
+        float fdc = rel_cell_f<DIM>(bi, a) - rel_cell_f<DIM>(bj, a);
         if (PER && ((periodic >> a) & 1u)) {
-            if (2 * dc > ncell[a]) dc -= ncell[a];
-            else if (2 * dc < -ncell[a]) dc += ncell[a];
+            float nc = (float)ncell[a];
+            if (2.0f * fdc > nc) fdc -= nc;
+            else if (2.0f * fdc < -nc) fdc += nc;
         }
-        float fdc = (float)dc;
         r[a] = fmaf(fdc, Sh[a], fmaf(fdc, Sl[a], oi[a] - oj[a]));
         d2 = fmaf(r[a], r[a], d2);
     }
@@ -290,6 +308,10 @@ int sph_exclusive_scan_i32(sph_ctx* ctx, const int32_t* in, int32_t* out, int64_
 // n / 2048 + 2 elements.
 int sph_exclusive_scan_i64_buf(const int32_t* in, int64_t* out, int64_t n, int64_t* bsum, cudaStream_t s);
 int sph_exclusive_scan_i32_buf(const int32_t* in, int32_t* out, int64_t n, int32_t* bsum, cudaStream_t s);
+
+// Raises a kernel's dynamic shared-memory limit to the per-block maximum, once
+// per (kernel, device); thread-safe.
+void sph_allow_dynamic_smem(const void* kernel);
 
 // Grid size helper.
 static inline unsigned grid_for(int64_t n, int block) {

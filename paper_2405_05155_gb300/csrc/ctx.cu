@@ -3,6 +3,9 @@
 #include <math.h>
 #include <new>
 #include "common.cuh"
+#include <mutex>
+#include <set>
+#include <utility>
 
 extern "C" int sph_create(sph_ctx** out, int device) {
     if (!out) return SPH_ERR_ARG;
@@ -67,6 +70,12 @@ extern "C" int sph_set_lanes(sph_ctx* ctx, int pass, int lanes) {
 extern "C" int sph_get_lanes(const sph_ctx* ctx, int pass) {
     if (!ctx || pass < 0 || pass > 3) return -1;
     return ctx->lanes[pass];
+}
+
+extern "C" int sph_set_stage_cap(sph_ctx* ctx, int cap) {
+    if (!ctx || cap < 0) return SPH_ERR_ARG;
+    ctx->stage_cap = cap;
+    return SPH_OK;
 }
 
 static cudaEvent_t pool_get(sph_ctx* ctx) {
@@ -358,4 +367,14 @@ extern "C" int sph_kernel_eval(int kernel, int dim, double h, double kappa, int 
                                                               (float)alpha, r, w, dwdr, n);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+void sph_allow_dynamic_smem(const void* kernel) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.insert({kernel, dev}).second)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }

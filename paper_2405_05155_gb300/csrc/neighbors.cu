@@ -45,6 +45,57 @@ __global__ void k_cell_ids(const double* __restrict__ pos, int64_t n, CellGrid g
     atomicMax(absmax, __float_as_uint(m));
 }
 
+// Morton (Z-order) key of a cell: bit l of the coordinate on axis a goes to the
+// next free key position, level by level from the least significant bit, axes in
+// order x, y, z; an axis drops out once its bits (ceil(log2 n_a)) are used up, so
+// the keys of the grid lie in [0, 2^(sum of bits)), at most 2^dim times the cells.
+struct MortonBits {
+    int bits[3];
+    int total;
+};
+
+MortonBits morton_bits(const CellGrid& g) {
+    MortonBits mb;
+    mb.total = 0;
+    for (int a = 0; a < 3; ++a) {
+        int b = 0;
+        if (a < g.dim)
+            while ((1LL << b) < (long long)g.n[a]) ++b;
+        mb.bits[a] = b;
+        mb.total += b;
+    }
+    return mb;
+}
+
+__device__ __forceinline__ int32_t morton_key(const int* c, const MortonBits& mb, int dim) {
+    uint32_t key = 0;
+    int at = 0;
+    for (int l = 0; l < 21; ++l)
+        for (int a = 0; a < dim; ++a)
+            if (l < mb.bits[a]) key |= (uint32_t)((c[a] >> l) & 1) << at++;
+    return (int32_t)key;
+}
+
+__global__ void k_morton_ids(const double* __restrict__ pos, int64_t n, CellGrid g, MortonBits mb,
+                             int32_t* __restrict__ key, int32_t* __restrict__ count, int* __restrict__ flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c[3] = {0, 0, 0};
+    bool bad = false;
+    for (int k = 0; k < g.dim; ++k) {
+        double x = pos[k * n + i];
+        if (!isfinite(x)) bad = true;
+        if ((g.periodic >> k) & 1u) {
+            if (!(x >= g.lo[k] && x <= g.lo[k] + g.len[k])) bad = true;
+        }
+        c[k] = cell_coord(x, k, g);
+    }
+    if (bad) { atomicExch(&flags[FLAG_BAD_INPUT], 1); c[0] = c[1] = c[2] = 0; }
+    int32_t id = morton_key(c, mb, g.dim);
+    key[i] = id;
+    atomicAdd(&count[id], 1);
+}
+
 __global__ void k_scatter(const int32_t* __restrict__ cid, int64_t n, const int32_t* __restrict__ start,
                           int32_t* __restrict__ fill, int32_t* __restrict__ sorted) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -252,10 +303,27 @@ extern "C" int sph_cell_order(sph_ctx* ctx, const sph_domain* dom, const double*
     if (st) return st;
     if (dom->n > 0 && (!pos || !order)) return SPH_ERR_ARG;
     cudaStream_t s = as_stream(stream);
-    CellList cl;
-    st = sph_build_cells(ctx, dom, pos, s, &cl);
+    // counting sort of the particles by the Morton key of their cell, stable by index
+    CellGrid g = sph_make_grid(dom);
+    MortonBits mb = morton_bits(g);
+    if (mb.total > 29) return SPH_ERR_ARG;
+    int64_t n = dom->n, nkeys = 1LL << mb.total;
+    int32_t* key = (int32_t*)sph_scratch(ctx, S_CELL_ID, (size_t)n * 4, &st);
+    int32_t* count = (int32_t*)sph_scratch(ctx, S_CELL_COUNT, (size_t)(nkeys + 1) * 4, &st);
+    int32_t* start = (int32_t*)sph_scratch(ctx, S_CELL_START, (size_t)(nkeys + 1) * 4, &st);
+    int32_t* fill = (int32_t*)sph_scratch(ctx, S_CELL_FILL, (size_t)(nkeys + 1) * 4, &st);
+    int32_t* sorted = (int32_t*)sph_scratch(ctx, S_SORTED, (size_t)n * 4, &st);
     if (st) return st;
-    if (dom->n > 0) k_widen_order<<<grid_for(dom->n, 256), 256, 0, s>>>(cl.sorted, dom->n, order);
+    SPH_CUDA(ctx, cudaMemsetAsync(count, 0, (size_t)(nkeys + 1) * 4, s));
+    SPH_CUDA(ctx, cudaMemsetAsync(fill, 0, (size_t)(nkeys + 1) * 4, s));
+    if (n > 0) k_morton_ids<<<grid_for(n, 256), 256, 0, s>>>(pos, n, g, mb, key, count, ctx->flags);
+    st = sph_exclusive_scan_i32(ctx, count, start, nkeys, s);
+    if (st) return st;
+    if (n > 0) {
+        k_scatter<<<grid_for(n, 256), 256, 0, s>>>(key, n, start, fill, sorted);
+        k_sort_cells<<<grid_for(nkeys, 128), 128, 0, s>>>(start, nkeys, sorted);
+        k_widen_order<<<grid_for(n, 256), 256, 0, s>>>(sorted, n, order);
+    }
     SPH_LAUNCH_CHECK(ctx);
     int* hf = (int*)ctx->pinned;
     st = take_flags(ctx, s, hf);

@@ -12,6 +12,7 @@
 // ln J = log1p(det(I+H) - 1) expanded in H), which keeps float32 accurate for
 // the small strains of a solid.
 #include "common.cuh"
+#include "tiles.cuh"
 
 namespace {
 
@@ -302,8 +303,97 @@ __global__ void k_tl_stress32(const float* __restrict__ H, const float* __restri
     store_M<DIM>(RM, i, m);
 }
 
-// Momentum pass (Eq. 30).  The next neighbour's record is loaded before the
-// current pair is evaluated.
+// One momentum pair (Eq. 30) from the neighbour's RM chunks: accumulates
+// (M_i + M_j) grad0 W_ij V0_j, rows 0-1 paired and row 2 alone.
+template <int DIM, bool PER>
+__device__ __forceinline__ void mom_pair(float4 c0, float4 c1, float4 c2, float4 c3, const float* oi, uint32_t bi,
+                                         const float2* mi01, const float* mi2, const TLK<float>& K,
+                                         Kahan2& acc01, Kahan<float>& acc2) {
+    float oj[DIM], r[DIM], d2;
+    uint32_t bj;
+    float Vj;
+    if (DIM == 3) {
+        oj[0] = c0.x; oj[1] = c0.y; oj[DIM - 1] = c0.z;
+        bj = __float_as_uint(c0.w);
+        Vj = c1.w;
+    } else {
+        oj[0] = c0.x; oj[1] = c0.y;
+        bj = __float_as_uint(c0.z);
+        Vj = c0.w;
+    }
+    rel_pair<DIM, PER>(oi, bi, oj, bj, K.ncell, K.S, K.Sl, K.periodic, r, d2);
+    float gs = gs_from_d2(d2, K) * Vj;
+    if (DIM == 2) {
+        float2 s0 = __fadd2_rn(mi01[0], make_float2(c1.x, c1.y));
+        float2 s1 = __fadd2_rn(mi01[1], make_float2(c1.z, c1.w));
+        float g0 = gs * r[0], g1 = gs * r[1];
+        acc01.add(__ffma2_rn(s1, make_float2(g1, g1), __fmul2_rn(s0, make_float2(g0, g0))));
+    } else {
+        float g0 = gs * r[0], g1 = gs * r[1], g2 = gs * r[DIM - 1];
+        float2 s0 = __fadd2_rn(mi01[0], make_float2(c1.x, c1.y));
+        float2 s1 = __fadd2_rn(mi01[1], make_float2(c2.x, c2.y));
+        float2 s2 = __fadd2_rn(mi01[DIM - 1], make_float2(c3.x, c3.y));
+        float2 t01 = __ffma2_rn(s2, make_float2(g2, g2),
+                                __ffma2_rn(s1, make_float2(g1, g1), __fmul2_rn(s0, make_float2(g0, g0))));
+        float t2 = fmaf(mi2[2] + c3.z, g2, fmaf(mi2[1] + c2.z, g1, (mi2[0] + c1.z) * g0));
+        acc01.add(t01);
+        acc2.add(t2);
+    }
+}
+
+// One deformation-rate pair (Eq. 31) from the neighbour's RD chunks: accumulates
+// V0_j (v_j - v_i) (x) grad0 W_ij column by column.
+template <int DIM, bool PER>
+__device__ __forceinline__ void defo_pair(float4 c0, float4 c1, const float* oi, uint32_t bi, float2 nv01, float nv2,
+                                          const TLK<float>& K, Kahan2* c01, Kahan2& r2, Kahan<float>& l22) {
+    float oj[DIM], r[DIM], d2;
+    uint32_t bj;
+    float w;
+    if (DIM == 3) {
+        oj[0] = c0.x; oj[1] = c0.y; oj[DIM - 1] = c0.z;
+        bj = __float_as_uint(c0.w);
+        w = c1.w;
+    } else {
+        oj[0] = c0.x; oj[1] = c0.y;
+        bj = __float_as_uint(c0.z);
+        w = c0.w;
+    }
+    rel_pair<DIM, PER>(oi, bi, oj, bj, K.ncell, K.S, K.Sl, K.periodic, r, d2);
+    float gs = gs_from_d2(d2, K);
+    float2 dv01 = __fmul2_rn(make_float2(w, w), __fadd2_rn(make_float2(c1.x, c1.y), nv01));
+    if (DIM == 2) {
+        c01[0].add(__fmul2_rn(dv01, make_float2(gs * r[0], gs * r[0])));
+        c01[1].add(__fmul2_rn(dv01, make_float2(gs * r[1], gs * r[1])));
+    } else {
+        float g0 = gs * r[0], g1 = gs * r[1], g2 = gs * r[DIM - 1];
+        float dv2 = w * (c1.z + nv2);
+        c01[0].add(__fmul2_rn(dv01, make_float2(g0, g0)));
+        c01[1].add(__fmul2_rn(dv01, make_float2(g1, g1)));
+        c01[DIM - 1].add(__fmul2_rn(dv01, make_float2(g2, g2)));
+        r2.add(__fmul2_rn(make_float2(dv2, dv2), make_float2(g0, g1)));
+        l22.add(dv2 * g2);
+    }
+}
+
+__device__ __forceinline__ float4 lo4(const F8& f) { return make_float4(f.v[0], f.v[1], f.v[2], f.v[3]); }
+__device__ __forceinline__ float4 hi4(const F8& f) { return make_float4(f.v[4], f.v[5], f.v[6], f.v[7]); }
+
+// Own stress factor M_i by columns from the RM record (rows 0-1 paired, row 2 alone).
+template <int DIM>
+__device__ __forceinline__ void own_M(const F8& a0, const F8& a1, float2* mi01, float* mi2) {
+    if (DIM == 2) {
+        mi01[0] = make_float2(a0.v[4], a0.v[5]);
+        mi01[1] = make_float2(a0.v[6], a0.v[7]);
+    } else {
+        mi01[0] = make_float2(a0.v[4], a0.v[5]); mi2[0] = a0.v[6];
+        mi01[1] = make_float2(a1.v[0], a1.v[1]); mi2[1] = a1.v[2];
+        mi01[DIM - 1] = make_float2(a1.v[4], a1.v[5]); mi2[2] = a1.v[6];
+    }
+}
+
+// Momentum pass (Eq. 30), neighbours gathered from global memory (states without
+// a tile plan).  LANES lanes per row; the next neighbour's record is loaded before
+// the current pair is evaluated.
 template <int DIM, int OUT, int LANES, bool PER>
 __global__ void __launch_bounds__(256, 4) k_tl_mom32(const float* __restrict__ RM, float* __restrict__ RD,
                                                      const int64_t* __restrict__ row_ptr,
@@ -321,17 +411,9 @@ __global__ void __launch_bounds__(256, 4) k_tl_mom32(const float* __restrict__ R
 #pragma unroll
     for (int a = 0; a < DIM; ++a) oi[a] = a0.v[a];
     uint32_t bi = __float_as_uint(a0.v[DIM]);
-    // own M by columns
     float2 mi01[DIM];
     float mi2[3] = {0.0f, 0.0f, 0.0f};
-    if (DIM == 2) {
-        mi01[0] = make_float2(a0.v[4], a0.v[5]);
-        mi01[1] = make_float2(a0.v[6], a0.v[7]);
-    } else {
-        mi01[0] = make_float2(a0.v[4], a0.v[5]); mi2[0] = a0.v[6];
-        mi01[1] = make_float2(a1.v[0], a1.v[1]); mi2[1] = a1.v[2];
-        mi01[DIM - 1] = make_float2(a1.v[4], a1.v[5]); mi2[2] = a1.v[6];
-    }
+    own_M<DIM>(a0, a1, mi01, mi2);
     Kahan2 acc01;
     Kahan<float> acc2;
     acc01.init();
@@ -352,28 +434,7 @@ __global__ void __launch_bounds__(256, 4) k_tl_mom32(const float* __restrict__ R
             n0 = ldg8(RM + W * (int64_t)jn);
             if (DIM == 3) n1 = ldg8(RM + W * (int64_t)jn + 8);
         }
-        float oj[DIM], r[DIM], d2;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) oj[a] = r0.v[a];
-        rel_pair<DIM, PER>(oi, bi, oj, __float_as_uint(r0.v[DIM]), K.ncell, K.S, K.Sl, K.periodic, r, d2);
-        float Vj = DIM == 3 ? r0.v[7] : r0.v[3];
-        float gs = gs_from_d2(d2, K) * Vj;
-        if (DIM == 2) {
-            float2 c0 = __fadd2_rn(mi01[0], make_float2(r0.v[4], r0.v[5]));
-            float2 c1 = __fadd2_rn(mi01[1], make_float2(r0.v[6], r0.v[7]));
-            float g0 = gs * r[0], g1 = gs * r[1];
-            acc01.add(__ffma2_rn(c1, make_float2(g1, g1), __fmul2_rn(c0, make_float2(g0, g0))));
-        } else {
-            float g0 = gs * r[0], g1 = gs * r[1], g2 = gs * r[DIM - 1];
-            float2 s0 = __fadd2_rn(mi01[0], make_float2(r0.v[4], r0.v[5]));
-            float2 s1 = __fadd2_rn(mi01[1], make_float2(r1.v[0], r1.v[1]));
-            float2 s2 = __fadd2_rn(mi01[DIM - 1], make_float2(r1.v[4], r1.v[5]));
-            float2 t01 = __ffma2_rn(s2, make_float2(g2, g2),
-                                    __ffma2_rn(s1, make_float2(g1, g1), __fmul2_rn(s0, make_float2(g0, g0))));
-            float t2 = fmaf(mi2[2] + r1.v[6], g2, fmaf(mi2[1] + r1.v[2], g1, (mi2[0] + r0.v[6]) * g0));
-            acc01.add(t01);
-            acc2.add(t2);
-        }
+        mom_pair<DIM, PER>(lo4(r0), hi4(r0), lo4(r1), hi4(r1), oi, bi, mi01, mi2, K, acc01, acc2);
         p = pn;
         j = jn;
         r0 = n0;
@@ -393,10 +454,35 @@ __global__ void __launch_bounds__(256, 4) k_tl_mom32(const float* __restrict__ R
     for (int a = 0; a < DIM; ++a) vrec[a] = fx ? 0.0f : vrec[a] + K.dt * (tot[a] * K.inv_rho0);
 }
 
-// Deformation-rate pass (Eq. 31) with the fused stress update of the next step.
-// L = sum_j V0_j (v_j - v_i) (x) g_ij is accumulated column by column: rows 0-1 of
-// each column in one paired compensated accumulator, row 2 of columns 0-1 in a
-// second pair and L22 in a scalar one.
+// Deformation-rate epilogue shared by both forms of the pass: F_i += dt L B0_i
+// (F = I on clamped particles), x_i += dt v_i and the next step's M_i = P(F_i) B0_i^T.
+template <int DIM, int OUT>
+__device__ __forceinline__ void defo_finish(const float* Lt, const float* b0, bool fx, const float* vi, int64_t i,
+                                            int64_t n, const TLK<float>& K, float* __restrict__ RM,
+                                            float* __restrict__ H, float* __restrict__ u,
+                                            double* __restrict__ dFdt) {
+    float Fd[DIM * DIM];
+    times_b0<DIM, float>(Lt, b0, Fd);
+    if (OUT == OUT_RATES) {
+        for (int k = 0; k < DIM * DIM; ++k) dFdt[k * n + i] = (double)Fd[k];
+        return;
+    }
+    float h[DIM * DIM], m[DIM * DIM];
+#pragma unroll
+    for (int k = 0; k < DIM * DIM; ++k) {
+        h[k] = fx ? 0.0f : H[k * n + i] + K.dt * Fd[k];
+        H[k * n + i] = h[k];
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) u[a * n + i] += K.dt * vi[a];
+    stress_factor<DIM, float>(h, b0, K, m);
+    store_M<DIM>(RM, i, m);
+}
+
+// Deformation-rate pass (Eq. 31) with the fused stress update of the next step,
+// neighbours gathered from global memory.  L = sum_j V0_j (v_j - v_i) (x) g_ij is
+// accumulated column by column: rows 0-1 of each column in one paired compensated
+// accumulator, row 2 of columns 0-1 in a second pair and L22 in a scalar one.
 template <int DIM, int OUT, int LANES, bool PER>
 __global__ void __launch_bounds__(256, 4) k_tl_defo32(const float* __restrict__ RD, float* __restrict__ RM,
                                                       const int64_t* __restrict__ row_ptr,
@@ -416,8 +502,8 @@ __global__ void __launch_bounds__(256, 4) k_tl_defo32(const float* __restrict__ 
     uint32_t bi = __float_as_uint(me.v[DIM]);
     float2 nv01 = make_float2(-me.v[4], -me.v[5]);
     float nv2 = -me.v[6];
-    Kahan2 c01[DIM];          // (L0c, L1c) for column c
-    Kahan2 r2;                // (L20, L21)
+    Kahan2 c01[DIM];
+    Kahan2 r2;
     Kahan<float> l22;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) c01[c].init();
@@ -433,25 +519,7 @@ __global__ void __launch_bounds__(256, 4) k_tl_defo32(const float* __restrict__ 
         int jn = pn < e ? __ldg(&col[pn]) : -1;
         F8 rn = rj;
         if (jn >= 0) rn = ldg8(RD + 8 * (int64_t)jn);
-        float oj[DIM], r[DIM], d2;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) oj[a] = rj.v[a];
-        rel_pair<DIM, PER>(oi, bi, oj, __float_as_uint(rj.v[DIM]), K.ncell, K.S, K.Sl, K.periodic, r, d2);
-        float w = DIM == 3 ? rj.v[7] : rj.v[3];
-        float gs = gs_from_d2(d2, K);
-        float2 dv01 = __fmul2_rn(make_float2(w, w), __fadd2_rn(make_float2(rj.v[4], rj.v[5]), nv01));
-        if (DIM == 2) {
-            c01[0].add(__fmul2_rn(dv01, make_float2(gs * r[0], gs * r[0])));
-            c01[1].add(__fmul2_rn(dv01, make_float2(gs * r[1], gs * r[1])));
-        } else {
-            float g0 = gs * r[0], g1 = gs * r[1], g2 = gs * r[DIM - 1];
-            float dv2 = w * (rj.v[6] + nv2);
-            c01[0].add(__fmul2_rn(dv01, make_float2(g0, g0)));
-            c01[1].add(__fmul2_rn(dv01, make_float2(g1, g1)));
-            c01[DIM - 1].add(__fmul2_rn(dv01, make_float2(g2, g2)));
-            r2.add(__fmul2_rn(make_float2(dv2, dv2), make_float2(g0, g1)));
-            l22.add(dv2 * g2);
-        }
+        defo_pair<DIM, PER>(lo4(rj), hi4(rj), oi, bi, nv01, nv2, K, c01, r2, l22);
         p = pn;
         j = jn;
         rj = rn;
@@ -470,25 +538,241 @@ __global__ void __launch_bounds__(256, 4) k_tl_defo32(const float* __restrict__ 
         Lt[2 * DIM + 2] = group_sum<LANES>(l22.value());
     }
     if (!active || lane != 0) return;
-    float b0[NS], Fd[DIM * DIM];
+    float b0[NS], vi[3] = {me.v[4], me.v[5], me.v[6]};
 #pragma unroll
     for (int s = 0; s < NS; ++s) b0[s] = B0[s * n + i];
-    times_b0<DIM, float>(Lt, b0, Fd);
+    defo_finish<DIM, OUT>(Lt, b0, (bi & kFixedBit) != 0, vi, i, n, K, RM, H, u, dFdt);
+}
+
+// ------------------------------------------------ float32 passes on a tile plan
+// With a tile plan (tiles.cuh) the pair geometry of the fixed reference
+// configuration is computed once, in float64, by k_tl_geo: entry (k, r) of tile b
+// holds w = grad0 W_ij V0_j (rounded to float32) and, in .w, the position of j among
+// the tile's distinct neighbours.  A block is one tile, one thread per row: it
+// stages the neighbours' M_j (momentum) or v_j (deformation) in shared memory and
+// its warps read the pair entries 512 contiguous bytes at a time.
+struct GeoArgs {
+    const int32_t* tile_m;
+    const int64_t* tile_so;
+    const int32_t* uidx;
+    const float4* geo;
+    int mcap;
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__ r0, const double* __restrict__ V0,
+                                                      const int64_t* __restrict__ row_ptr,
+                                                      const int32_t* __restrict__ col,
+                                                      const uint16_t* __restrict__ lcol,
+                                                      const int32_t* __restrict__ tile_e,
+                                                      const int64_t* __restrict__ tile_so, int64_t n, TLK<double> K,
+                                                      float4* __restrict__ geo) {
+    const int64_t tile = blockIdx.x;
+    const int64_t i = tile * kTileRows + threadIdx.x;
+    const bool active = i < n;
+    const int64_t b = active ? row_ptr[i] : 0;
+    const int len = active ? (int)(row_ptr[i + 1] - b) : 0;
+    const int width = tile_e[tile] / kTileRows;
+    float4* out = geo + tile_so[tile] + threadIdx.x;
+    double xi[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) xi[a] = active ? r0[a * n + i] : 0.0;
+    for (int k = 0; k < width; ++k) {
+        float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (k < len) {
+            int64_t p = b + k;
+            int j = col[p];
+            double r[DIM], d2;
+            pair_r64<DIM>(xi, r0, n, j, K, r, d2);
+            double gv = wendland_gs<double>(sqrt(d2) * K.inv_h, K.coef) * V0[j];
+            e.x = (float)(gv * r[0]);
+            e.y = (float)(gv * r[1]);
+            if (DIM == 3) e.z = (float)(gv * r[DIM - 1]);
+            e.w = __int_as_float((int)lcol[p]);
+        }
+        out[(int64_t)k * kTileRows] = e;
+    }
+}
+
+// Stage chunks 1..NPL of the tile's distinct neighbours' records (record stride
+// RECF floats) at sp[c * mcap + s].  Returns false, staging nothing, for a tile
+// with more distinct neighbours than mcap.  Block-uniform.
+template <int NPL, int RECF>
+__device__ __forceinline__ bool stage_neighbours(const float* __restrict__ R, int64_t n, int64_t P0, int m,
+                                                 const GeoArgs& A, float4* sp) {
+    const bool staged = m <= A.mcap;
+    if (staged) {
+        for (int s = threadIdx.x; s < m; s += blockDim.x) {
+            // a plan out of date with the lists reads wrong but in-bounds records
+            int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
+            const float4* rec = reinterpret_cast<const float4*>(R + RECF * j) + 1;
+#pragma unroll
+            for (int c = 0; c < NPL; ++c) sp[c * A.mcap + s] = __ldg(rec + c);
+        }
+    }
+    __syncthreads();
+    return staged;
+}
+
+template <int DIM, int OUT>
+__global__ void __launch_bounds__(kTileRows, 6) k_tl_mom32g(const float* __restrict__ RM, float* __restrict__ RD,
+                                                            const int64_t* __restrict__ row_ptr, int64_t n,
+                                                            TLK<float> K, GeoArgs A, double* __restrict__ dvdt) {
+    constexpr int W = DIM == 3 ? 16 : 8;
+    constexpr int NPL = DIM == 3 ? 3 : 1;
+    extern __shared__ __align__(16) unsigned char tl_smem[];
+    float4* sp = reinterpret_cast<float4*>(tl_smem);
+    const int64_t tile = blockIdx.x;
+    const int64_t i0 = tile * kTileRows;
+    const int64_t i = i0 + threadIdx.x;
+    const bool active = i < n;
+    const int64_t ii = active ? i : i0;
+    // own loads first: their latency overlaps the staging
+    const int64_t P0 = row_ptr[i0];
+    const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
+    const int m = A.tile_m[tile];
+    const float4* g = A.geo + A.tile_so[tile] + threadIdx.x;
+    F8 a0 = ldg8(RM + W * ii);
+    F8 a1 = DIM == 3 ? ldg8(RM + W * ii + 8) : a0;
+    float vown[3] = {0.0f, 0.0f, 0.0f};
+    if (OUT != OUT_RATES) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) vown[a] = RD[8 * ii + 4 + a];
+    }
+    const bool staged = stage_neighbours<NPL, W>(RM, n, P0, m, A, sp);
+    const uint32_t bi = __float_as_uint(a0.v[DIM]);
+    float2 mi01[DIM];
+    float mi2[3] = {0.0f, 0.0f, 0.0f};
+    own_M<DIM>(a0, a1, mi01, mi2);
+    Kahan2 acc01;
+    Kahan<float> acc2;
+    acc01.init();
+    acc2.init();
+    auto pair = [&](float4 e, float4 c1, float4 c2, float4 c3) {
+        if (DIM == 2) {
+            float2 s0 = __fadd2_rn(mi01[0], make_float2(c1.x, c1.y));
+            float2 s1 = __fadd2_rn(mi01[1], make_float2(c1.z, c1.w));
+            acc01.add(__ffma2_rn(s1, make_float2(e.y, e.y), __fmul2_rn(s0, make_float2(e.x, e.x))));
+        } else {
+            float2 s0 = __fadd2_rn(mi01[0], make_float2(c1.x, c1.y));
+            float2 s1 = __fadd2_rn(mi01[1], make_float2(c2.x, c2.y));
+            float2 s2 = __fadd2_rn(mi01[DIM - 1], make_float2(c3.x, c3.y));
+            float2 t01 = __ffma2_rn(s2, make_float2(e.z, e.z),
+                                    __ffma2_rn(s1, make_float2(e.y, e.y), __fmul2_rn(s0, make_float2(e.x, e.x))));
+            float t2 = fmaf(mi2[2] + c3.z, e.z, fmaf(mi2[1] + c2.z, e.y, (mi2[0] + c1.z) * e.x));
+            acc01.add(t01);
+            acc2.add(t2);
+        }
+    };
+    const int mc = A.mcap;
+    if (staged) {
+#pragma unroll 4
+        for (int k = 0; k < len; ++k) {
+            float4 e = __ldg(g + (int64_t)k * kTileRows);
+            int s = min(max(__float_as_int(e.w), 0), max(m - 1, 0));
+            float4 c1 = sp[s];
+            float4 c2 = DIM == 3 ? sp[mc + s] : c1, c3 = DIM == 3 ? sp[2 * mc + s] : c1;
+            pair(e, c1, c2, c3);
+        }
+    } else {
+        for (int k = 0; k < len; ++k) {
+            float4 e = __ldg(g + (int64_t)k * kTileRows);
+            int s = min(max(__float_as_int(e.w), 0), max(m - 1, 0));
+            int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
+            const float4* rec = reinterpret_cast<const float4*>(RM + W * j);
+            float4 c1 = __ldg(rec + 1);
+            float4 c2 = DIM == 3 ? __ldg(rec + 2) : c1, c3 = DIM == 3 ? __ldg(rec + 3) : c1;
+            pair(e, c1, c2, c3);
+        }
+    }
+    if (!active) return;
+    float2 v01 = acc01.value();
+    float tot[3] = {v01.x, v01.y, DIM == 3 ? acc2.value() : 0.0f};
     if (OUT == OUT_RATES) {
-        for (int k = 0; k < DIM * DIM; ++k) dFdt[k * n + i] = (double)Fd[k];
+        for (int a = 0; a < DIM; ++a) dvdt[a * n + i] = (double)(tot[a] * K.inv_rho0);
         return;
     }
     bool fx = (bi & kFixedBit) != 0;
-    float h[DIM * DIM], m[DIM * DIM];
+    float* vrec = RD + 8 * i + 4;
 #pragma unroll
-    for (int k = 0; k < DIM * DIM; ++k) {
-        h[k] = fx ? 0.0f : H[k * n + i] + K.dt * Fd[k];
-        H[k * n + i] = h[k];
+    for (int a = 0; a < DIM; ++a) vrec[a] = fx ? 0.0f : vown[a] + K.dt * (tot[a] * K.inv_rho0);
+}
+
+template <int DIM, int OUT>
+__global__ void __launch_bounds__(kTileRows, 6) k_tl_defo32g(const float* __restrict__ RD, float* __restrict__ RM,
+                                                             const int64_t* __restrict__ row_ptr, int64_t n,
+                                                             TLK<float> K, GeoArgs A, const float* __restrict__ B0,
+                                                             float* __restrict__ H, float* __restrict__ u,
+                                                             double* __restrict__ dFdt) {
+    constexpr int NS = DIM == 2 ? 3 : 6;
+    extern __shared__ __align__(16) unsigned char tl_smem[];
+    float4* sp = reinterpret_cast<float4*>(tl_smem);
+    const int64_t tile = blockIdx.x;
+    const int64_t i0 = tile * kTileRows;
+    const int64_t i = i0 + threadIdx.x;
+    const bool active = i < n;
+    const int64_t ii = active ? i : i0;
+    const int64_t P0 = row_ptr[i0];
+    const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
+    const int m = A.tile_m[tile];
+    const float4* g = A.geo + A.tile_so[tile] + threadIdx.x;
+    F8 me = ldg8(RD + 8 * ii);
+    float b0[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) b0[s] = B0[s * n + ii];
+    const bool staged = stage_neighbours<1, 8>(RD, n, P0, m, A, sp);
+    const uint32_t bi = __float_as_uint(me.v[DIM]);
+    const float2 nv01 = make_float2(-me.v[4], -me.v[5]);
+    const float nv2 = -me.v[6];
+    Kahan2 c01[DIM];
+    Kahan2 r2;
+    Kahan<float> l22;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) c01[c].init();
+    r2.init();
+    l22.init();
+    auto pair = [&](float4 e, float4 vj) {
+        float2 dv01 = __fadd2_rn(make_float2(vj.x, vj.y), nv01);
+        c01[0].add(__fmul2_rn(dv01, make_float2(e.x, e.x)));
+        c01[1].add(__fmul2_rn(dv01, make_float2(e.y, e.y)));
+        if (DIM == 3) {
+            float dv2 = vj.z + nv2;
+            c01[DIM - 1].add(__fmul2_rn(dv01, make_float2(e.z, e.z)));
+            r2.add(__fmul2_rn(make_float2(dv2, dv2), make_float2(e.x, e.y)));
+            l22.add(dv2 * e.z);
+        }
+    };
+    if (staged) {
+#pragma unroll 4
+        for (int k = 0; k < len; ++k) {
+            float4 e = __ldg(g + (int64_t)k * kTileRows);
+            int s = min(max(__float_as_int(e.w), 0), max(m - 1, 0));
+            pair(e, sp[s]);
+        }
+    } else {
+        for (int k = 0; k < len; ++k) {
+            float4 e = __ldg(g + (int64_t)k * kTileRows);
+            int s = min(max(__float_as_int(e.w), 0), max(m - 1, 0));
+            int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
+            pair(e, __ldg(reinterpret_cast<const float4*>(RD + 8 * j) + 1));
+        }
     }
+    if (!active) return;
+    float Lt[DIM * DIM];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) u[a * n + i] += K.dt * me.v[4 + a];
-    stress_factor<DIM, float>(h, b0, K, m);
-    store_M<DIM>(RM, i, m);
+    for (int c = 0; c < DIM; ++c) {
+        float2 v = c01[c].value();
+        Lt[0 * DIM + c] = v.x;
+        Lt[1 * DIM + c] = v.y;
+    }
+    if (DIM == 3) {
+        float2 v = r2.value();
+        Lt[2 * DIM + 0] = v.x;
+        Lt[2 * DIM + 1] = v.y;
+        Lt[2 * DIM + 2] = l22.value();
+    }
+    float vi[3] = {me.v[4], me.v[5], me.v[6]};
+    defo_finish<DIM, OUT>(Lt, b0, (bi & kFixedBit) != 0, vi, i, n, K, RM, H, u, dFdt);
 }
 
 // ---------------------------------------------------------------- pack / unpack
@@ -582,9 +866,33 @@ int check_tl(const sph_tlsph_params* p, const sph_tlsph_state* st) {
     return SPH_OK;
 }
 
+// The state's tile plan as launch arguments (tile_m == nullptr: no plan).
+struct TlPlan {
+    GeoArgs mom, defo;
+    size_t mom_bytes, defo_bytes;
+    bool on;
+};
+
+TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim) {
+    TlPlan t;
+    t.on = st->plan && st->plan_nnz > 0 && st->plan_maxm > 0;
+    t.mom = GeoArgs{nullptr, nullptr, nullptr, nullptr, 0};
+    t.defo = t.mom;
+    t.mom_bytes = t.defo_bytes = 0;
+    if (!t.on) return t;
+    TilePlan tp = tile_plan_view(st->plan, n, st->plan_nnz);
+    int npl = dim == 3 ? 3 : 1;
+    int mm = stage_mcap(st->plan_maxm, npl, ctx->stage_cap), md = stage_mcap(st->plan_maxm, 1, ctx->stage_cap);
+    t.mom = GeoArgs{tp.tile_m, tp.tile_so, tp.uidx, tp.geo, mm};
+    t.defo = GeoArgs{tp.tile_m, tp.tile_so, tp.uidx, tp.geo, md};
+    t.mom_bytes = (size_t)mm * 16 * npl;
+    t.defo_bytes = (size_t)md * 16;
+    return t;
+}
+
 template <int DIM, int LANES, bool PER>
-void tl32_passes(int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K, double* r1, double* r2,
-                 cudaStream_t s) {
+void tl32_passes(int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K, double* r1,
+                 double* r2, cudaStream_t s) {
     const int block = 256;
     dim3 g(grid_for(n * LANES, block)), b(block);
     if (which == 0) {
@@ -602,9 +910,38 @@ void tl32_passes(int which, int out, int64_t n, const sph_tlsph_state* st, const
     }
 }
 
+template <int DIM>
+void tl32_plan_pass(int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K, const TlPlan& tp,
+                    double* r1, double* r2, cudaStream_t s) {
+    dim3 g((unsigned)((n + kTileRows - 1) / kTileRows)), b(kTileRows);
+    if (which == 0) {
+        if (out == OUT_RATES) {
+            auto* f = k_tl_mom32g<DIM, OUT_RATES>;
+            sph_allow_dynamic_smem((const void*)f);
+            f<<<g, b, tp.mom_bytes, s>>>(st->rm, st->rd, st->row_ptr, n, K, tp.mom, r1);
+        } else {
+            auto* f = k_tl_mom32g<DIM, OUT_STEP>;
+            sph_allow_dynamic_smem((const void*)f);
+            f<<<g, b, tp.mom_bytes, s>>>(st->rm, st->rd, st->row_ptr, n, K, tp.mom, nullptr);
+        }
+    } else {
+        if (out == OUT_RATES) {
+            auto* f = k_tl_defo32g<DIM, OUT_RATES>;
+            sph_allow_dynamic_smem((const void*)f);
+            f<<<g, b, tp.defo_bytes, s>>>(st->rd, st->rm, st->row_ptr, n, K, tp.defo, st->B32, st->H32, st->u32,
+                                          r2);
+        } else {
+            auto* f = k_tl_defo32g<DIM, OUT_STEP>;
+            sph_allow_dynamic_smem((const void*)f);
+            f<<<g, b, tp.defo_bytes, s>>>(st->rd, st->rm, st->row_ptr, n, K, tp.defo, st->B32, st->H32, st->u32,
+                                          nullptr);
+        }
+    }
+}
+
 template <int DIM, bool PER>
-void tl32_lanes(int lanes, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K, double* r1,
-                double* r2, cudaStream_t s) {
+void tl32_lanes(int lanes, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K,
+                double* r1, double* r2, cudaStream_t s) {
     switch (lanes) {
         case 1: tl32_passes<DIM, 1, PER>(which, out, n, st, K, r1, r2, s); break;
         case 2: tl32_passes<DIM, 2, PER>(which, out, n, st, K, r1, r2, s); break;
@@ -613,10 +950,13 @@ void tl32_lanes(int lanes, int which, int out, int64_t n, const sph_tlsph_state*
     }
 }
 
+// One float32 pass: on the tile plan when the state has one, else the gather form
+// with the context's lanes per row.
 template <int DIM>
-void tl32(int lanes, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K, double* r1,
-          double* r2, cudaStream_t s) {
-    if (K.periodic) tl32_lanes<DIM, true>(lanes, which, out, n, st, K, r1, r2, s);
+void tl32(int lanes, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K,
+          const TlPlan& tp, double* r1, double* r2, cudaStream_t s) {
+    if (tp.on) tl32_plan_pass<DIM>(which, out, n, st, K, tp, r1, r2, s);
+    else if (K.periodic) tl32_lanes<DIM, true>(lanes, which, out, n, st, K, r1, r2, s);
     else tl32_lanes<DIM, false>(lanes, which, out, n, st, K, r1, r2, s);
 }
 
@@ -625,7 +965,7 @@ bool fp64_ready(const sph_tlsph_state* st) { return st->x && st->v && st->H && s
 
 }  // namespace
 
-extern "C" int sph_tlsph_pack(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st, void* stream) {
+extern "C" int sph_tlsph_pack(sph_ctx* ctx, const sph_tlsph_params* p, sph_tlsph_state* st, void* stream) {
     if (!ctx) return SPH_ERR_ARG;
     int r = check_tl(p, st);
     if (r) return r;
@@ -642,6 +982,47 @@ extern "C" int sph_tlsph_pack(sph_ctx* ctx, const sph_tlsph_params* p, const sph
         k_tl_pack<3><<<grid_for(n, 256), 256, 0, s>>>(st->r0, st->V0, st->B0, st->fixed, st->x, st->v, st->H, n, g,
                                                       st->rd, st->rm, st->H32, st->u32, st->B32);
     SPH_LAUNCH_CHECK(ctx);
+    st->plan_nnz = 0;
+    st->plan_maxm = st->plan_maxp = 0;
+    if (st->plan) {
+        int64_t nnz = 0, maxrow = 0;
+        r = sph_row_stats(ctx, st->row_ptr, n, s, &nnz, &maxrow);
+        if (r) return r;
+        if (st->plan_bytes < (int64_t)tile_plan_bytes(n, nnz, maxrow)) return SPH_ERR_CAPACITY;
+        if (nnz > 0) {
+            int32_t mm = 0, mp = 0, mw = 0;
+            r = sph_build_tile_plan(ctx, st->row_ptr, st->col, n, nnz, st->plan, s, &mm, &mp, &mw);
+            if (r) return r;
+            TilePlan tp = tile_plan_view(st->plan, n, nnz);
+            TLK<double> K = make_tl_consts<double>(p);
+            unsigned nt = (unsigned)tp.ntiles;
+            if (p->dom.dim == 2)
+                k_tl_geo<2><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_e,
+                                                     tp.tile_so, n, K, tp.geo);
+            else
+                k_tl_geo<3><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_e,
+                                                     tp.tile_so, n, K, tp.geo);
+            SPH_LAUNCH_CHECK(ctx);
+            st->plan_nnz = nnz;
+            st->plan_maxm = mm;
+            st->plan_maxp = mp;
+        }
+    }
+    return SPH_OK;
+}
+
+// Bytes of the tile plan of this state's lists (synchronises the stream).
+extern "C" int sph_tlsph_plan_bytes(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st,
+                                    int64_t* bytes_host, void* stream) {
+    if (!ctx || !bytes_host) return SPH_ERR_ARG;
+    int r = check_tl(p, st);
+    if (r) return r;
+    int64_t n = p->dom.n, nnz = 0, maxrow = 0;
+    if (n > 0) {
+        r = sph_row_stats(ctx, st->row_ptr, n, as_stream(stream), &nnz, &maxrow);
+        if (r) return r;
+    }
+    *bytes_host = (int64_t)tile_plan_bytes(n, nnz, maxrow);
     return SPH_OK;
 }
 
@@ -689,15 +1070,16 @@ extern "C" int sph_tlsph_rates(sph_ctx* ctx, const sph_tlsph_params* p, const sp
     } else {
         if (!fp32_ready(st)) return SPH_ERR_ARG;
         TLK<float> K = make_tl_consts<float>(p);
+        TlPlan ts = tl_plan(ctx, st, n, dim);
         int lanes = ctx->lanes[SPH_PASS_TLSPH];
         if (dim == 2) {
             k_tl_stress32<2><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm);
-            tl32<2>(lanes, 0, OUT_RATES, n, st, K, dvdt, dFdt, s);
-            tl32<2>(lanes, 1, OUT_RATES, n, st, K, dvdt, dFdt, s);
+            tl32<2>(lanes, 0, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
+            tl32<2>(lanes, 1, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
         } else {
             k_tl_stress32<3><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm);
-            tl32<3>(lanes, 0, OUT_RATES, n, st, K, dvdt, dFdt, s);
-            tl32<3>(lanes, 1, OUT_RATES, n, st, K, dvdt, dFdt, s);
+            tl32<3>(lanes, 0, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
+            tl32<3>(lanes, 1, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
         }
     }
     SPH_LAUNCH_CHECK(ctx);
@@ -742,6 +1124,7 @@ extern "C" int sph_tlsph_step(sph_ctx* ctx, const sph_tlsph_params* p, const sph
     }
     if (!fp32_ready(st)) return SPH_ERR_ARG;
     TLK<float> K = make_tl_consts<float>(p);
+    TlPlan ts = tl_plan(ctx, st, n, dim);
     int lanes = ctx->lanes[SPH_PASS_TLSPH];
     int t = sph_timer_begin(ctx, SPH_TIMER_TL_STRESS, s);
     if (dim == 2) k_tl_stress32<2><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm);
@@ -749,12 +1132,12 @@ extern "C" int sph_tlsph_step(sph_ctx* ctx, const sph_tlsph_params* p, const sph
     sph_timer_end(ctx, t, s);
     for (int k = 0; k < nsteps; ++k) {
         t = sph_timer_begin(ctx, SPH_TIMER_TL_MOMENTUM, s);
-        if (dim == 2) tl32<2>(lanes, 0, OUT_STEP, n, st, K, nullptr, nullptr, s);
-        else tl32<3>(lanes, 0, OUT_STEP, n, st, K, nullptr, nullptr, s);
+        if (dim == 2) tl32<2>(lanes, 0, OUT_STEP, n, st, K, ts, nullptr, nullptr, s);
+        else tl32<3>(lanes, 0, OUT_STEP, n, st, K, ts, nullptr, nullptr, s);
         sph_timer_end(ctx, t, s);
         t = sph_timer_begin(ctx, SPH_TIMER_TL_DEFORM, s);
-        if (dim == 2) tl32<2>(lanes, 1, OUT_STEP, n, st, K, nullptr, nullptr, s);
-        else tl32<3>(lanes, 1, OUT_STEP, n, st, K, nullptr, nullptr, s);
+        if (dim == 2) tl32<2>(lanes, 1, OUT_STEP, n, st, K, ts, nullptr, nullptr, s);
+        else tl32<3>(lanes, 1, OUT_STEP, n, st, K, ts, nullptr, nullptr, s);
         sph_timer_end(ctx, t, s);
     }
     SPH_LAUNCH_CHECK(ctx);

@@ -1,9 +1,11 @@
 """GPU parity of the total-Lagrangian solid path (a7-a9) against the float64 oracle."""
 import numpy as np
 import pytest
+import torch
 
 from helpers import cuda, host, odom, rel_l2, rel_max, sample_rows, sorted_by_cells
 from oracle import kgc as OK
+from oracle import neighbors as ON
 from oracle import tlsph as OT
 from paper_2405_05155_gb300 import api, inputs
 
@@ -31,11 +33,17 @@ def _setup(ctx, dp=0.005, kappa=1.6, law=OT.NEO_HOOKEAN):
                 col_h=host(col), B0_h=host(B0), prm=prm)
 
 
-def _solid(ctx, s, precision, law, v=None, H=None):
+def _solid(ctx, s, precision, law, v=None, H=None, tiles=True):
     c = s["c"]
     return api.TLSolid(ctx, s["d"], cuda(s["r0"]), cuda(s["vol"]), s["B0"], s["fixed"], s["rp"], s["col"],
                        s["v"] if v is None else v, c["dt"], c["rho0"], c["lam"], c["G"], law=law,
-                       precision=precision, H=H)
+                       precision=precision, H=H, tiles=tiles)
+
+
+# float64, then float32 with the tiles staged in shared memory and float32 gathering
+# from global memory
+VARIANTS = ((api.SPH_FP64, True, 1e-12, rel_max), (api.SPH_FP32_KAHAN, True, 1e-5, rel_l2),
+            (api.SPH_FP32_KAHAN, False, 1e-5, rel_l2))
 
 
 def _F_from_H(H):
@@ -56,8 +64,8 @@ def test_rates_parity(ctx, law):
     a_o = OT.momentum_rate(s["r0"], s["vol"], M, s["rp_h"], s["col_h"], s["prm"].dom, s["prm"].rho0)
     Fd_o = OT.deformation_rate(s["r0"], s["vol"], v, s["B0_h"], s["rp_h"], s["col_h"], s["prm"].dom)
     Fd_o = Fd_o.reshape(n, 9).T
-    for prec, tol, err in ((api.SPH_FP64, 1e-12, rel_max), (api.SPH_FP32_KAHAN, 1e-5, rel_l2)):
-        sol = _solid(ctx, s, prec, law, v=v, H=H)
+    for prec, tiles, tol, err in VARIANTS:
+        sol = _solid(ctx, s, prec, law, v=v, H=H, tiles=tiles)
         a, Fd = sol.rates()
         assert err(host(a), a_o) < tol, (prec, err(host(a), a_o))
         assert err(host(Fd), Fd_o) < tol, (prec, err(host(Fd), Fd_o))
@@ -71,14 +79,91 @@ def test_steps_parity(ctx, kappa):
     x_o, v_o, F_o = OT.run(s["r0"], s["vol"], s["B0_h"], s["fixed"], s["r0"].copy(), s["v"], F0, s["rp_h"],
                            s["col_h"], s["prm"], 20)
     H_o = (F_o - np.eye(3)[None]).reshape(n, 9).T
-    for prec, tol, err in ((api.SPH_FP64, 1e-12, rel_max), (api.SPH_FP32_KAHAN, 1e-5, rel_l2)):
-        sol = _solid(ctx, s, prec, OT.NEO_HOOKEAN)
+    for prec, tiles, tol, err in VARIANTS:
+        sol = _solid(ctx, s, prec, OT.NEO_HOOKEAN, tiles=tiles)
         sol.step(20)
         x, v, H = sol.fields()
         assert err(host(v), v_o) < tol, (prec, err(host(v), v_o))
         assert err(host(H), H_o) < tol, (prec, err(host(H), H_o))
         assert err(host(x) - s["r0"], x_o - s["r0"]) < tol
         assert np.all(host(v)[:, s["fixed"] == 1] == 0.0)
+
+
+def _read_plan(plan, n, nnz, maxrow):
+    """Split a tile-plan buffer by its documented layout."""
+    raw = host(plan)
+    nt = (n + 127) // 128
+    a16 = lambda x: (x + 15) // 16 * 16
+    out = {"hdr": raw[:64].view(np.int32)}
+    o = 64
+    for name, size, dt in (("tile_m", 4 * nt, np.int32), ("tile_e", 4 * nt, np.int32),
+                           ("tile_so", 8 * (nt + 1), np.int64), ("uidx", 4 * nnz, np.int32),
+                           ("lcol", 2 * nnz, np.uint16)):
+        out[name] = raw[o:o + size].view(dt)
+        o += a16(size)
+    out["geo"] = raw[o:o + 16 * nt * 128 * maxrow].view(np.float32).reshape(-1, 4)
+    return out
+
+
+def test_tile_plan_is_exact(ctx):
+    # per tile of 128 rows: the ascending distinct columns, each pair's index among
+    # them and the sliced pair factors w_ij = grad0 W_ij V0_j, against numpy on the
+    # same lists (w in float64 by the oracle's kernel, rounded to float32 on the GPU)
+    s = _setup(ctx, dp=0.004)
+    n = s["r0"].shape[1]
+    rp, col = s["rp_h"], s["col_h"]
+    lens = np.diff(rp)
+    sol = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
+    P = _read_plan(sol.plan, n, col.size, int(lens.max()))
+    hdr = P["hdr"]
+    assert (sol.st.plan_maxm, sol.st.plan_maxp, sol.st.plan_nnz) == (hdr[0], hdr[1], col.size)
+    dom = s["prm"].dom
+    h = dom.h
+    from oracle import kernels as OKer
+    ms, ps = [], []
+    for b in range((n + 127) // 128):
+        i0, i1 = 128 * b, min(n, 128 * b + 128)
+        p0, p1 = rp[i0], rp[i1]
+        u = np.unique(col[p0:p1])
+        assert P["tile_m"][b] == u.size
+        assert np.array_equal(P["uidx"][p0:p0 + u.size], u)
+        lc = np.searchsorted(u, col[p0:p1])
+        assert np.array_equal(P["lcol"][p0:p1], lc)
+        width = int(lens[i0:i1].max())
+        assert P["tile_e"][b] == 128 * width
+        so = P["tile_so"][b]
+        assert P["tile_so"][b + 1] == so + 128 * width
+        for r in range(i1 - i0):
+            i = i0 + r
+            k = np.arange(lens[i])
+            ent = P["geo"][so + k * 128 + r]
+            j = col[rp[i]:rp[i + 1]]
+            dx = ON.min_image(s["r0"][:, i:i + 1] - s["r0"][:, j], dom)
+            q = np.sqrt(np.sum(dx * dx, axis=0)) / h
+            w = OKer.wendland_dwdr(q * h, h, 3, None) / (q * h) * s["vol"][j] * dx
+            assert np.allclose(ent[:, :3].T, w, rtol=2e-6, atol=1e-6 * np.abs(w).max())
+            assert np.array_equal(ent[:, 3].view(np.int32), lc[rp[i] - p0:rp[i + 1] - p0])
+            pad = P["geo"][so + np.arange(lens[i], width) * 128 + r]
+            assert np.all(pad == 0.0)
+        ms.append(u.size)
+        ps.append(p1 - p0)
+    assert hdr[0] == max(ms) and hdr[1] == max(ps) and hdr[2] == lens.max()
+    # Morton order makes tiles compact: each tile's distinct neighbours are a few times its rows
+    assert np.mean(ms) < 8 * 128
+
+
+def test_staged_and_unstaged_tiles_agree_bitwise(ctx):
+    # a planned pass reads its neighbours from shared memory, or from global memory for
+    # tiles over the stage capacity: the same arithmetic in the same order
+    s = _setup(ctx)
+    a = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
+    b = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
+    a.step(3)
+    ctx.set_stage_cap(16)
+    b.step(3)
+    ctx.set_stage_cap(0)
+    torch.cuda.synchronize()
+    assert torch.equal(a.rd, b.rd) and torch.equal(a.rm, b.rm) and torch.equal(a.H32, b.H32)
 
 
 def test_linear_field_and_momentum_invariants(ctx):

@@ -100,11 +100,42 @@ def test_minimum_image_once():
     assert np.array_equal(out[0], np.array([0.6 - 1.0, -0.6 + 1.0, 0.5, -0.5, 0.2]))
 
 
-def test_cell_order_is_stable_sort_by_cell():
+def test_cell_order_is_stable_sort_by_morton_key():
     pos, dom = _random_case(9, 3, 2.0, 2000, False)
     order = N.cell_order(pos, dom)
-    ids = N.cell_ids(pos, dom)[order]
+    ncell, _ = N.cell_grid(dom)
+    keys = N.morton_key(N.cell_coords(pos, dom), ncell)[order]
     assert sorted(order.tolist()) == list(range(pos.shape[1]))
-    assert np.all(np.diff(ids) >= 0)
-    same = np.diff(ids) == 0
+    assert np.all(np.diff(keys) >= 0)
+    same = np.diff(keys) == 0
     assert np.all(np.diff(order)[same] > 0)
+    # particles of one cell stay together: equal keys <=> equal cells
+    ids = N.cell_ids(pos, dom)[order]
+    assert np.array_equal(np.diff(keys) == 0, np.diff(ids) == 0)
+
+
+def test_morton_key_is_the_z_order():
+    # 4 x 4: the Z curve visits 2 x 2 quadrants in the order (x, y) = 00, 10, 01, 11,
+    # recursively (x in the even bits, y in the odd bits of the key)
+    z = [(0, 0), (1, 0), (0, 1), (1, 1), (2, 0), (3, 0), (2, 1), (3, 1),
+         (0, 2), (1, 2), (0, 3), (1, 3), (2, 2), (3, 2), (2, 3), (3, 3)]
+    c = np.array(z).T
+    assert N.morton_key(c, [4, 4]).tolist() == list(range(16))
+    # 2 x 2 x 2: key = x + 2 y + 4 z
+    g = np.array([(x, y, zz) for zz in range(2) for y in range(2) for x in range(2)]).T
+    assert N.morton_key(g, [2, 2, 2]).tolist() == list(range(8))
+    # uneven axes (5 x 2 x 3 cells: 3, 1 and 2 bits): once y is used up the key
+    # continues x, z, x; keys stay distinct and below 2^(3 + 1 + 2)
+    g = np.array([(x, y, zz) for zz in range(3) for y in range(2) for x in range(5)]).T
+    k = N.morton_key(g, [5, 2, 3])
+    assert len(set(k.tolist())) == 30 and k.max() < 64
+    for x, y, zz, kk in zip(g[0], g[1], g[2], k):
+        expect = (x & 1) | (y & 1) << 1 | (zz & 1) << 2 | ((x >> 1) & 1) << 3 | ((zz >> 1) & 1) << 4 | ((x >> 2) & 1) << 5
+        assert kk == expect
+    # locality: in an 8^3 grid every aligned 2^3 block holds 8 consecutive keys
+    g = np.array([(x, y, zz) for zz in range(8) for y in range(8) for x in range(8)]).T
+    k = N.morton_key(g, [8, 8, 8])
+    blocks = (g[0] // 2) + 4 * (g[1] // 2) + 16 * (g[2] // 2)
+    for b in range(64):
+        kb = np.sort(k[blocks == b])
+        assert np.array_equal(kb, np.arange(kb[0], kb[0] + 8)) and kb[0] % 8 == 0
