@@ -108,6 +108,11 @@ int sph_get_lanes(const sph_ctx* ctx, int pass);
  * many as the plan needs, within 96 KB); tiles with more read their neighbours from
  * global memory.  A launch-shape setting, like the lanes: results do not depend on it. */
 int sph_set_stage_cap(sph_ctx* ctx, int cap);
+/* Planned passes: on runs the persistent form (one block per SM, the next tile's
+ * pair entries and neighbours copied into shared memory by TMA while the current
+ * tile computes) when its buffers fit in shared memory; off (default) runs one
+ * block per tile.  A launch-shape setting: results do not depend on it. */
+int sph_set_tile_pipeline(sph_ctx* ctx, int on);
 
 /* Per-kernel device timing (not part of the paper: measurement support).
  * sph_timing_enable(ctx, 1) clears the counters and makes the step entry points
@@ -332,20 +337,20 @@ typedef struct {
  *   H32 [dim*dim][n], u32 [dim][n] (x - r0), B32 [nsym][n].
  *   The float32 path needs len_a >= 2 kappa h + 2 S_a along a periodic axis.
  * Tile plan (optional, float32 path): plan -> caller-owned device buffer of
- *   plan_bytes >= sph_tlsph_plan_bytes(...) bytes, 16-byte aligned.  When plan is
- *   set, sph_tlsph_pack builds in it, from row_ptr/col/r0/V0, (i) per tile of 128
+ *   plan_bytes >= sph_tlsph_plan_bytes(...) bytes, 16-byte aligned.  sph_tlsph_plan
+ *   builds in it, from row_ptr/col/r0/V0, (i) per tile of 128
  *   consecutive rows the list of its distinct neighbours and (ii) per pair the
  *   reference-configuration factor w_ij = grad0 W_ij V0_j of Eqs. 30-31, computed in
  *   float64 and stored in float32 with the neighbour's position in its tile's list,
  *   in a sliced order (pair k of row r of a tile at k*128 + r).  It writes plan_nnz,
- *   plan_maxm (most distinct neighbours of a tile) and plan_maxp (most pairs of a
- *   tile) into the struct.  The pair passes then stage each tile's neighbour M_j or
+ *   plan_maxm (most distinct neighbours of a tile) and plan_maxrow (longest row)
+ *   into the struct.  The pair passes then stage each tile's neighbour M_j or
  *   v_j in shared memory and read the pair factors from the plan: one thread per
  *   row, the context's lanes setting unused.  Rows are best in sph_cell_order
  *   (Morton) order, so that a tile is a compact group.  The plan must be rebuilt
- *   (sph_tlsph_pack) whenever row_ptr, col, r0 or V0 change.  plan = NULL: the pair
- *   factors are evaluated per pair from the records and neighbours are gathered from
- *   global memory. */
+ *   (sph_tlsph_plan) whenever row_ptr, col, r0 or V0 change.  plan = NULL or
+ *   plan_nnz = 0 (no plan built): the pair factors are evaluated per pair from the
+ *   records and neighbours are gathered from global memory. */
 typedef struct {
     const int64_t* row_ptr;
     const int32_t* col;
@@ -364,21 +369,27 @@ typedef struct {
     float*  B32;
     void*   plan;          /* optional tile plan buffer (see above) */
     int64_t plan_bytes;
-    int64_t plan_nnz;      /* written by sph_tlsph_pack */
-    int32_t plan_maxm;     /* written by sph_tlsph_pack */
-    int32_t plan_maxp;     /* written by sph_tlsph_pack */
+    int64_t plan_nnz;      /* written by sph_tlsph_plan */
+    int32_t plan_maxm;     /* written by sph_tlsph_plan */
+    int32_t plan_maxrow;   /* written by sph_tlsph_plan */
 } sph_tlsph_state;
 
-/* float64 state -> float32 records (and the tile plan when st->plan is set;
- * that build synchronises the stream).  SPH_ERR_CAPACITY when plan_bytes is too
- * small. */
+/* float64 state (x, v, H, r0, V0, B0, fixed) -> float32 records. */
 int sph_tlsph_pack(sph_ctx* ctx, const sph_tlsph_params* prm,
-                   sph_tlsph_state* st, void* stream);
+                   const sph_tlsph_state* st, void* stream);
+/* Builds the tile plan in st->plan (see above) and writes plan_nnz, plan_maxm and
+ * plan_maxrow.  Not an operation of the paper: a staging layout of the pair passes
+ * of Eqs. 30-31.  Synchronises the stream.  SPH_ERR_ARG without st->plan,
+ * SPH_ERR_CAPACITY when plan_bytes is too small. */
+int sph_tlsph_plan(sph_ctx* ctx, const sph_tlsph_params* prm, sph_tlsph_state* st, void* stream);
 /* Bytes of the tile-plan buffer for the state's lists (reads row_ptr; synchronises
  * the stream). */
 int sph_tlsph_plan_bytes(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_state* st,
                          int64_t* bytes_host, void* stream);
-/* packed float32 (rd, H32, u32) -> float64 (v, H, x = r0 + u). */
+/* packed float32 (rd, H32, u32) -> float64 (v, H, x = r0 + u).  After steps of
+ * the persistent planned form (sph_set_tile_pipeline) it synchronises the stream and
+ * returns SPH_ERR_TIMEOUT if a bounded device wait expired since the previous unpack
+ * (the results are then not valid). */
 int sph_tlsph_unpack(sph_ctx* ctx, const sph_tlsph_params* prm,
                      const sph_tlsph_state* st, void* stream);
 /* Rates at the current state: dvdt float64 [dim][n] (Eq. 30 / rho0) and

@@ -50,7 +50,7 @@ class TLParams(ctypes.Structure):
 class TLState(ctypes.Structure):
     _fields_ = [(name, c_vp) for name in ("row_ptr", "col", "r0", "V0", "B0", "fixed", "x", "v", "H", "M",
                                           "rd", "rm", "H32", "u32", "B32", "plan")] + [
-        ("plan_bytes", c_i64), ("plan_nnz", c_i64), ("plan_maxm", c_i32), ("plan_maxp", c_i32)]
+        ("plan_bytes", c_i64), ("plan_nnz", c_i64), ("plan_maxm", c_i32), ("plan_maxrow", c_i32)]
 
 
 class BatchCase(ctypes.Structure):
@@ -104,7 +104,9 @@ _SIGNATURES = {
                                           c_vp]),
     "sph_relax_propose": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, c_vp]),
     "sph_tlsph_plan_bytes": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), _P(c_i64), c_vp]),
+    "sph_tlsph_plan": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp]),
     "sph_set_stage_cap": (ctypes.c_int, [c_vp, ctypes.c_int]),
+    "sph_set_tile_pipeline": (ctypes.c_int, [c_vp, ctypes.c_int]),
     "sph_autotune_eulerian": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), ctypes.c_int,
                                              _P(ctypes.c_int), _P(c_dbl), c_vp]),
     "sph_autotune_tlsph": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), ctypes.c_int, _P(ctypes.c_int),

@@ -62,6 +62,9 @@ class Context:
         except Exception:
             pass
 
+    def set_tile_pipeline(self, on):
+        L.check("sph_set_tile_pipeline", self.lib.sph_set_tile_pipeline(self.h, 1 if on else 0), self.h)
+
     def set_stage_cap(self, cap):
         L.check("sph_set_stage_cap", self.lib.sph_set_stage_cap(self.h, int(cap)), self.h)
 
@@ -232,7 +235,7 @@ class TLSolid:
             setattr(self.st, name, getattr(self, name).data_ptr())
         self.plan = None
         if tiles and precision == SPH_FP32_KAHAN:
-            # tile plan: pair factors precomputed and neighbours staged per tile (built by pack)
+            # tile plan: pair factors precomputed and neighbours staged per tile (sph_tlsph_plan)
             nb = ctypes.c_int64()
             self._call("sph_tlsph_plan_bytes", ctypes.byref(nb), _stream())
             self.plan = torch.empty(max(nb.value, 16), dtype=torch.uint8, device=dev)
@@ -240,6 +243,8 @@ class TLSolid:
             self.st.plan_bytes = self.plan.numel()
         if precision == SPH_FP32_KAHAN:
             self.pack()
+            if self.plan is not None:
+                self._call("sph_tlsph_plan", _stream())
 
     def _call(self, name, *args):
         fn = getattr(self.ctx.lib, name)

@@ -42,6 +42,8 @@ struct sph_ctx {
     void* pinned = nullptr;        // small pinned host buffer for read-backs
     int lanes[4] = {4, 4, 4, 4};   // lanes per particle of the float32 pair passes (SPH_PASS_*)
     int stage_cap = 0;             // most neighbour records a tile stages in shared memory (0: default)
+    bool no_pipe = true;           // planned passes: skip the persistent double-buffered form
+    bool waits_pending = false;    // a kernel with bounded waits ran since the timeout flag was read
     // batched Eulerian step: launch shape, captured graph and the case table it was made for
     int batch_block = 256;
     cudaGraphExec_t batch_graph = nullptr;
@@ -58,7 +60,7 @@ enum ScratchSlot {
 };
 
 // device status words
-enum { FLAG_BAD_INPUT = 0, FLAG_NONFINITE = 1, FLAG_CAPACITY = 2, FLAG_COUNT = 8 };
+enum { FLAG_BAD_INPUT = 0, FLAG_NONFINITE = 1, FLAG_CAPACITY = 2, FLAG_TIMEOUT = 3, FLAG_COUNT = 8 };
 
 #define SPH_CUDA(ctx, call)                                                     \
     do {                                                                        \
@@ -312,6 +314,10 @@ int sph_exclusive_scan_i32_buf(const int32_t* in, int32_t* out, int64_t n, int32
 // Raises a kernel's dynamic shared-memory limit to the per-block maximum, once
 // per (kernel, device); thread-safe.
 void sph_allow_dynamic_smem(const void* kernel);
+
+// Reads and clears the device timeout flag: SPH_ERR_TIMEOUT when a bounded wait of
+// a kernel expired since the last call (synchronises the stream).
+int sph_take_timeout(sph_ctx* ctx, cudaStream_t s);
 
 // Grid size helper.
 static inline unsigned grid_for(int64_t n, int block) {

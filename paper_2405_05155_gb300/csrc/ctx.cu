@@ -72,6 +72,24 @@ extern "C" int sph_get_lanes(const sph_ctx* ctx, int pass) {
     return ctx->lanes[pass];
 }
 
+extern "C" int sph_set_tile_pipeline(sph_ctx* ctx, int on) {
+    if (!ctx) return SPH_ERR_ARG;
+    ctx->no_pipe = (on == 0);
+    return SPH_OK;
+}
+
+// Reads and clears the device timeout flag (synchronises the stream).
+int sph_take_timeout(sph_ctx* ctx, cudaStream_t s) {
+    int* h = (int*)ctx->pinned;
+    SPH_CUDA(ctx, cudaMemcpyAsync(h, ctx->flags + FLAG_TIMEOUT, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(ctx, cudaStreamSynchronize(s));
+    if (*h) {
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags + FLAG_TIMEOUT, 0, sizeof(int), s));
+        return SPH_ERR_TIMEOUT;
+    }
+    return SPH_OK;
+}
+
 extern "C" int sph_set_stage_cap(sph_ctx* ctx, int cap) {
     if (!ctx || cap < 0) return SPH_ERR_ARG;
     ctx->stage_cap = cap;

@@ -13,6 +13,7 @@
 // the small strains of a solid.
 #include "common.cuh"
 #include "tiles.cuh"
+#include "async.cuh"
 
 namespace {
 
@@ -456,11 +457,13 @@ __global__ void __launch_bounds__(256, 4) k_tl_mom32(const float* __restrict__ R
 
 // Deformation-rate epilogue shared by both forms of the pass: F_i += dt L B0_i
 // (F = I on clamped particles), x_i += dt v_i and the next step's M_i = P(F_i) B0_i^T.
+// hold/uold: the row's current H and u when already loaded (else read here).
 template <int DIM, int OUT>
 __device__ __forceinline__ void defo_finish(const float* Lt, const float* b0, bool fx, const float* vi, int64_t i,
                                             int64_t n, const TLK<float>& K, float* __restrict__ RM,
                                             float* __restrict__ H, float* __restrict__ u,
-                                            double* __restrict__ dFdt) {
+                                            double* __restrict__ dFdt, const float* hold = nullptr,
+                                            const float* uold = nullptr) {
     float Fd[DIM * DIM];
     times_b0<DIM, float>(Lt, b0, Fd);
     if (OUT == OUT_RATES) {
@@ -470,11 +473,11 @@ __device__ __forceinline__ void defo_finish(const float* Lt, const float* b0, bo
     float h[DIM * DIM], m[DIM * DIM];
 #pragma unroll
     for (int k = 0; k < DIM * DIM; ++k) {
-        h[k] = fx ? 0.0f : H[k * n + i] + K.dt * Fd[k];
+        h[k] = fx ? 0.0f : (hold ? hold[k] : H[k * n + i]) + K.dt * Fd[k];
         H[k * n + i] = h[k];
     }
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) u[a * n + i] += K.dt * vi[a];
+    for (int a = 0; a < DIM; ++a) u[a * n + i] = (uold ? uold[a] : u[a * n + i]) + K.dt * vi[a];
     stress_factor<DIM, float>(h, b0, K, m);
     store_M<DIM>(RM, i, m);
 }
@@ -559,6 +562,13 @@ struct GeoArgs {
     int mcap;
 };
 
+// Row order of the sliced entries: a row's pairs are laid out by their offset
+// r_i - r_j quantised to h/2 (then by j), so that at a given position the threads of
+// a warp, neighbouring rows, tend to read neighbours at the same offset, which lie
+// close together in their tile's list and so in different shared-memory banks.
+// Rows longer than kSortCap keep the list order.
+constexpr int kSortCap = 128;
+
 template <int DIM>
 __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__ r0, const double* __restrict__ V0,
                                                       const int64_t* __restrict__ row_ptr,
@@ -577,10 +587,33 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
     double xi[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) xi[a] = active ? r0[a * n + i] : 0.0;
+    uint32_t order[kSortCap];
+    const bool sorted = len <= kSortCap;
+    if (sorted) {
+        const double inv = 2.0 * K.inv_h;
+        for (int k = 0; k < len; ++k) {
+            double r[DIM], d2;
+            pair_r64<DIM>(xi, r0, n, col[b + k], K, r, d2);
+            uint32_t key = 0;
+#pragma unroll
+            for (int a = DIM - 1; a >= 0; --a) {
+                double q = rint(r[a] * inv);
+                int c = (int)fmin(fmax(q, -8.0), 7.0) + 8;
+                key = key * 16u + (uint32_t)c;
+            }
+            uint32_t v = (key << 20) | (uint32_t)k;
+            int at = k;
+            while (at > 0 && order[at - 1] > v) {
+                order[at] = order[at - 1];
+                --at;
+            }
+            order[at] = v;
+        }
+    }
     for (int k = 0; k < width; ++k) {
         float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (k < len) {
-            int64_t p = b + k;
+            int64_t p = b + (sorted ? (int)(order[k] & 0xFFFFFu) : k);
             int j = col[p];
             double r[DIM], d2;
             pair_r64<DIM>(xi, r0, n, j, K, r, d2);
@@ -594,6 +627,22 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
     }
 }
 
+// Asks the TMA unit to bring the tile's sliced pair entries (one contiguous range)
+// into L2 while the block stages its neighbours, so that the pair loop's loads hit L2.
+__device__ __forceinline__ void prefetch_tile_entries(const GeoArgs& A, int64_t tile) {
+    if (threadIdx.x == 0) {
+        int64_t e0 = A.tile_so[tile], e1 = A.tile_so[tile + 1];
+        const float4* p = A.geo + e0;
+        int64_t bytes = (e1 - e0) * 16;
+        while (bytes > 0) {
+            uint32_t chunk = (uint32_t)(bytes < (1 << 20) ? bytes : (1 << 20));
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(chunk) : "memory");
+            p += chunk / 16;
+            bytes -= chunk;
+        }
+    }
+}
+
 // Stage chunks 1..NPL of the tile's distinct neighbours' records (record stride
 // RECF floats) at sp[c * mcap + s].  Returns false, staging nothing, for a tile
 // with more distinct neighbours than mcap.  Block-uniform.
@@ -602,12 +651,14 @@ __device__ __forceinline__ bool stage_neighbours(const float* __restrict__ R, in
                                                  const GeoArgs& A, float4* sp) {
     const bool staged = m <= A.mcap;
     if (staged) {
-        for (int s = threadIdx.x; s < m; s += blockDim.x) {
+        // consecutive threads copy consecutive chunks of consecutive neighbours: the
+        // tile's neighbours come in runs of consecutive indices (Morton order), so the
+        // loads of a warp mostly fall on contiguous records
+        for (int q = threadIdx.x; q < m * NPL; q += blockDim.x) {
+            int s = q / NPL, c = q - s * NPL;
             // a plan out of date with the lists reads wrong but in-bounds records
             int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
-            const float4* rec = reinterpret_cast<const float4*>(R + RECF * j) + 1;
-#pragma unroll
-            for (int c = 0; c < NPL; ++c) sp[c * A.mcap + s] = __ldg(rec + c);
+            sp[c * A.mcap + s] = __ldg(reinterpret_cast<const float4*>(R + RECF * j) + 1 + c);
         }
     }
     __syncthreads();
@@ -615,7 +666,7 @@ __device__ __forceinline__ bool stage_neighbours(const float* __restrict__ R, in
 }
 
 template <int DIM, int OUT>
-__global__ void __launch_bounds__(kTileRows, 6) k_tl_mom32g(const float* __restrict__ RM, float* __restrict__ RD,
+__global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32g(const float* __restrict__ RM, float* __restrict__ RD,
                                                             const int64_t* __restrict__ row_ptr, int64_t n,
                                                             TLK<float> K, GeoArgs A, double* __restrict__ dvdt) {
     constexpr int W = DIM == 3 ? 16 : 8;
@@ -632,6 +683,7 @@ __global__ void __launch_bounds__(kTileRows, 6) k_tl_mom32g(const float* __restr
     const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
     const int m = A.tile_m[tile];
     const float4* g = A.geo + A.tile_so[tile] + threadIdx.x;
+    prefetch_tile_entries(A, tile);
     F8 a0 = ldg8(RM + W * ii);
     F8 a1 = DIM == 3 ? ldg8(RM + W * ii + 8) : a0;
     float vown[3] = {0.0f, 0.0f, 0.0f};
@@ -699,7 +751,7 @@ __global__ void __launch_bounds__(kTileRows, 6) k_tl_mom32g(const float* __restr
 }
 
 template <int DIM, int OUT>
-__global__ void __launch_bounds__(kTileRows, 6) k_tl_defo32g(const float* __restrict__ RD, float* __restrict__ RM,
+__global__ void __launch_bounds__(kTileRows, 8) k_tl_defo32g(const float* __restrict__ RD, float* __restrict__ RM,
                                                              const int64_t* __restrict__ row_ptr, int64_t n,
                                                              TLK<float> K, GeoArgs A, const float* __restrict__ B0,
                                                              float* __restrict__ H, float* __restrict__ u,
@@ -716,6 +768,7 @@ __global__ void __launch_bounds__(kTileRows, 6) k_tl_defo32g(const float* __rest
     const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
     const int m = A.tile_m[tile];
     const float4* g = A.geo + A.tile_so[tile] + threadIdx.x;
+    prefetch_tile_entries(A, tile);
     F8 me = ldg8(RD + 8 * ii);
     float b0[NS];
 #pragma unroll
@@ -866,11 +919,373 @@ int check_tl(const sph_tlsph_params* p, const sph_tlsph_state* st) {
     return SPH_OK;
 }
 
+// --------------------------- persistent, double-buffered form of the planned passes
+// One block per SM walks the tiles b, b + G, b + 2G, ... (G blocks).  While it
+// computes tile t, the TMA unit copies tile t+G's sliced pair entries into the
+// other entry buffer (completion on an mbarrier), per-thread asynchronous copies
+// stage t+G's neighbour chunks (from the list copied one tile earlier) and t+2G's
+// neighbour list, and the row's own data for t+G is loaded into registers.  Used
+// when both entry buffers fit in shared memory.
+struct PipeArgs {
+    int64_t ntiles;
+    int gw;      // entries per buffer: kTileRows * longest row
+    int mcap;    // neighbours staged per tile
+    int ucap;    // ints per list buffer
+};
+
+struct TileHdr {
+    int m, ne;
+    int64_t P0, so;
+};
+
+__device__ __forceinline__ TileHdr tile_hdr(const GeoArgs& A, const int64_t* __restrict__ row_ptr, int64_t t,
+                                            int64_t ntiles) {
+    TileHdr h{0, 0, 0, 0};
+    if (t < ntiles) {
+        h.m = A.tile_m[t];
+        h.so = A.tile_so[t];
+        h.ne = (int)(A.tile_so[t + 1] - h.so);
+        h.P0 = row_ptr[t * kTileRows];
+    }
+    return h;
+}
+
+constexpr uint32_t kWaitPolls = 1u << 22;
+
+template <int NPL>
+struct PipeSmem {
+    uint64_t* bar;
+    float4* gbuf;
+    float4* rbuf;
+    int32_t* ubuf;
+    __device__ PipeSmem(unsigned char* base, const PipeArgs& P) {
+        bar = reinterpret_cast<uint64_t*>(base);
+        gbuf = reinterpret_cast<float4*>(base + 16);
+        rbuf = gbuf + 2 * (size_t)P.gw;
+        ubuf = reinterpret_cast<int32_t*>(rbuf + 2 * (size_t)NPL * P.mcap);
+    }
+};
+
+static inline size_t pipe_smem_bytes(const PipeArgs& P, int npl) {
+    return 16 + 2 * (size_t)P.gw * 16 + 2 * (size_t)npl * P.mcap * 16 + 3 * (size_t)P.ucap * 4;
+}
+
+// Copy the neighbour list of tile t (when it will be staged) into ub.
+__device__ __forceinline__ void issue_list(const GeoArgs& A, const PipeArgs& P, int64_t t, const TileHdr& h,
+                                           int32_t* ub) {
+    if (t < P.ntiles && h.m <= P.mcap)
+        for (int s = threadIdx.x; s < h.m; s += blockDim.x) cp_async4(ub + s, A.uidx + h.P0 + s);
+}
+
+// Start tile t's entry copy (thread 0, on bar) and its neighbour chunks 1..NPL.
+template <int NPL, int RECF>
+__device__ __forceinline__ void issue_tile(const GeoArgs& A, const PipeArgs& P, const float* __restrict__ R,
+                                           int64_t n, int64_t t, const TileHdr& h, int b, const PipeSmem<NPL>& S,
+                                           const int32_t* ub) {
+    if (t >= P.ntiles) return;
+    if (threadIdx.x == 0) {
+        uint32_t bytes = (uint32_t)h.ne * 16u;
+        mbar_arrive_expect_tx(&S.bar[b], bytes);
+        if (bytes) tma_load_1d(S.gbuf + (size_t)b * P.gw, A.geo + h.so, bytes, &S.bar[b]);
+    }
+    if (h.m <= P.mcap) {
+        float4* rb = S.rbuf + (size_t)b * NPL * P.mcap;
+        for (int s = threadIdx.x; s < h.m; s += blockDim.x) {
+            int64_t j = min(max((int64_t)ub[s], (int64_t)0), n - 1);
+            const float4* src = reinterpret_cast<const float4*>(R + RECF * j) + 1;
+#pragma unroll
+            for (int c = 0; c < NPL; ++c) cp_async16(rb + (size_t)c * P.mcap + s, src + c);
+        }
+    }
+}
+
+struct OwnMom {
+    int len;
+    uint32_t bits;
+    float2 mi01[3];
+    float mi2[3];
+    float v[3];
+};
+
+template <int DIM, int OUT>
+__device__ __forceinline__ OwnMom own_mom(const float* __restrict__ RM, const float* __restrict__ RD,
+                                          const int64_t* __restrict__ row_ptr, int64_t i, int64_t n) {
+    constexpr int W = DIM == 3 ? 16 : 8;
+    OwnMom o;
+    bool active = i < n;
+    int64_t ii = active ? i : n - 1;
+    o.len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
+    F8 a0 = ldg8(RM + W * ii);
+    F8 a1 = DIM == 3 ? ldg8(RM + W * ii + 8) : a0;
+    o.bits = __float_as_uint(a0.v[DIM]);
+    o.mi2[0] = o.mi2[1] = o.mi2[2] = 0.0f;
+    own_M<DIM>(a0, a1, o.mi01, o.mi2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) o.v[a] = (OUT != OUT_RATES && a < DIM) ? RD[8 * ii + 4 + a] : 0.0f;
+    return o;
+}
+
+template <int DIM, int OUT>
+__global__ void __launch_bounds__(kTileRows, 1) k_tl_mom32p(const float* __restrict__ RM, float* __restrict__ RD,
+                                                            const int64_t* __restrict__ row_ptr, int64_t n,
+                                                            TLK<float> K, GeoArgs A, PipeArgs P,
+                                                            double* __restrict__ dvdt, int* __restrict__ flags) {
+    constexpr int W = DIM == 3 ? 16 : 8;
+    constexpr int NPL = DIM == 3 ? 3 : 1;
+    extern __shared__ __align__(16) unsigned char tl_smem[];
+    PipeSmem<NPL> S(tl_smem, P);
+    const int64_t G = gridDim.x, t0 = blockIdx.x;
+    if (t0 >= P.ntiles) return;
+    if (threadIdx.x == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    TileHdr h0 = tile_hdr(A, row_ptr, t0, P.ntiles), h1 = tile_hdr(A, row_ptr, t0 + G, P.ntiles);
+    TileHdr h2 = tile_hdr(A, row_ptr, t0 + 2 * G, P.ntiles);
+    issue_list(A, P, t0, h0, S.ubuf);
+    issue_list(A, P, t0 + G, h1, S.ubuf + P.ucap);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    issue_tile<NPL, W>(A, P, RM, n, t0, h0, 0, S, S.ubuf);
+    cp_async_commit();
+    OwnMom own = own_mom<DIM, OUT>(RM, RD, row_ptr, t0 * kTileRows + threadIdx.x, n);
+    bool ok = true;
+    for (int64_t it = 0;; ++it) {
+        const int64_t t = t0 + it * G;
+        if (t >= P.ntiles) break;
+        const int cur = (int)(it & 1);
+        TileHdr h3 = tile_hdr(A, row_ptr, t + 3 * G, P.ntiles);
+        cp_async_wait_all();
+        const bool late = !mbar_wait_bounded(&S.bar[cur], (uint32_t)((it >> 1) & 1), kWaitPolls);
+        // block-uniform decision: every thread leaves the loop together
+        if (__syncthreads_or(late)) {
+            ok = false;
+            if (threadIdx.x == 0) atomicExch(&flags[FLAG_TIMEOUT], 1);
+            break;
+        }
+        issue_tile<NPL, W>(A, P, RM, n, t + G, h1, cur ^ 1, S, S.ubuf + ((it + 1) % 3) * P.ucap);
+        issue_list(A, P, t + 2 * G, h2, S.ubuf + ((it + 2) % 3) * P.ucap);
+        cp_async_commit();
+        OwnMom nxt = own_mom<DIM, OUT>(RM, RD, row_ptr, (t + G) * kTileRows + threadIdx.x, n);
+        // tile t
+        const int64_t i = t * kTileRows + threadIdx.x;
+        const float4* gb = S.gbuf + (size_t)cur * P.gw + threadIdx.x;
+        const float4* rb = S.rbuf + (size_t)cur * NPL * P.mcap;
+        const bool staged = h0.m <= P.mcap;
+        const int smax = max(h0.m - 1, 0);
+        Kahan2 acc01;
+        Kahan<float> acc2;
+        acc01.init();
+        acc2.init();
+#pragma unroll 4
+        for (int k = 0; k < own.len; ++k) {
+            float4 e = gb[(size_t)k * kTileRows];
+            int s = min(max(__float_as_int(e.w), 0), smax);
+            float4 c1, c2, c3;
+            if (staged) {
+                c1 = rb[s];
+                c2 = DIM == 3 ? rb[P.mcap + s] : c1;
+                c3 = DIM == 3 ? rb[2 * P.mcap + s] : c1;
+            } else {
+                int64_t j = min(max((int64_t)A.uidx[h0.P0 + s], (int64_t)0), n - 1);
+                const float4* rec = reinterpret_cast<const float4*>(RM + W * j);
+                c1 = __ldg(rec + 1);
+                c2 = DIM == 3 ? __ldg(rec + 2) : c1;
+                c3 = DIM == 3 ? __ldg(rec + 3) : c1;
+            }
+            if (DIM == 2) {
+                float2 s0 = __fadd2_rn(own.mi01[0], make_float2(c1.x, c1.y));
+                float2 s1 = __fadd2_rn(own.mi01[1], make_float2(c1.z, c1.w));
+                acc01.add(__ffma2_rn(s1, make_float2(e.y, e.y), __fmul2_rn(s0, make_float2(e.x, e.x))));
+            } else {
+                float2 s0 = __fadd2_rn(own.mi01[0], make_float2(c1.x, c1.y));
+                float2 s1 = __fadd2_rn(own.mi01[1], make_float2(c2.x, c2.y));
+                float2 s2 = __fadd2_rn(own.mi01[DIM - 1], make_float2(c3.x, c3.y));
+                float2 t01 = __ffma2_rn(s2, make_float2(e.z, e.z),
+                                        __ffma2_rn(s1, make_float2(e.y, e.y),
+                                                   __fmul2_rn(s0, make_float2(e.x, e.x))));
+                float t2 = fmaf(own.mi2[2] + c3.z, e.z, fmaf(own.mi2[1] + c2.z, e.y, (own.mi2[0] + c1.z) * e.x));
+                acc01.add(t01);
+                acc2.add(t2);
+            }
+        }
+        if (i < n) {
+            float2 v01 = acc01.value();
+            float tot[3] = {v01.x, v01.y, DIM == 3 ? acc2.value() : 0.0f};
+            if (OUT == OUT_RATES) {
+                for (int a = 0; a < DIM; ++a) dvdt[a * n + i] = (double)(tot[a] * K.inv_rho0);
+            } else {
+                bool fx = (own.bits & kFixedBit) != 0;
+                float* vrec = RD + 8 * i + 4;
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) vrec[a] = fx ? 0.0f : own.v[a] + K.dt * (tot[a] * K.inv_rho0);
+            }
+        }
+        __syncthreads();
+        own = nxt;
+        h0 = h1;
+        h1 = h2;
+        h2 = h3;
+    }
+    if (!ok) {
+        // let the copies in flight land before the block's shared memory is released
+        cp_async_wait_all();
+        mbar_wait_bounded(&S.bar[0], 0, kWaitPolls);
+        mbar_wait_bounded(&S.bar[1], 0, kWaitPolls);
+    }
+}
+
+template <int DIM>
+struct OwnDefo {
+    int len;
+    uint32_t bits;
+    float v[3];
+    float b0[DIM == 2 ? 3 : 6];
+    float h[DIM * DIM];
+    float u[DIM];
+};
+
+template <int DIM, int OUT>
+__device__ __forceinline__ OwnDefo<DIM> own_defo(const float* __restrict__ RD, const int64_t* __restrict__ row_ptr,
+                                                 const float* __restrict__ B0, const float* __restrict__ H,
+                                                 const float* __restrict__ u, int64_t i, int64_t n) {
+    constexpr int NS = DIM == 2 ? 3 : 6;
+    OwnDefo<DIM> o;
+    bool active = i < n;
+    int64_t ii = active ? i : n - 1;
+    o.len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
+    F8 me = ldg8(RD + 8 * ii);
+    o.bits = __float_as_uint(me.v[DIM]);
+    o.v[0] = me.v[4]; o.v[1] = me.v[5]; o.v[2] = me.v[6];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) o.b0[s] = B0[s * n + ii];
+#pragma unroll
+    for (int k = 0; k < DIM * DIM; ++k) o.h[k] = OUT == OUT_RATES ? 0.0f : H[k * n + ii];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) o.u[a] = OUT == OUT_RATES ? 0.0f : u[a * n + ii];
+    return o;
+}
+
+template <int DIM, int OUT>
+__global__ void __launch_bounds__(kTileRows, 1) k_tl_defo32p(const float* __restrict__ RD, float* __restrict__ RM,
+                                                             const int64_t* __restrict__ row_ptr, int64_t n,
+                                                             TLK<float> K, GeoArgs A, PipeArgs P,
+                                                             const float* __restrict__ B0, float* __restrict__ H,
+                                                             float* __restrict__ u, double* __restrict__ dFdt,
+                                                             int* __restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char tl_smem[];
+    PipeSmem<1> S(tl_smem, P);
+    const int64_t G = gridDim.x, t0 = blockIdx.x;
+    if (t0 >= P.ntiles) return;
+    if (threadIdx.x == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    TileHdr h0 = tile_hdr(A, row_ptr, t0, P.ntiles), h1 = tile_hdr(A, row_ptr, t0 + G, P.ntiles);
+    TileHdr h2 = tile_hdr(A, row_ptr, t0 + 2 * G, P.ntiles);
+    issue_list(A, P, t0, h0, S.ubuf);
+    issue_list(A, P, t0 + G, h1, S.ubuf + P.ucap);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    issue_tile<1, 8>(A, P, RD, n, t0, h0, 0, S, S.ubuf);
+    cp_async_commit();
+    OwnDefo<DIM> own = own_defo<DIM, OUT>(RD, row_ptr, B0, H, u, t0 * kTileRows + threadIdx.x, n);
+    bool ok = true;
+    for (int64_t it = 0;; ++it) {
+        const int64_t t = t0 + it * G;
+        if (t >= P.ntiles) break;
+        const int cur = (int)(it & 1);
+        TileHdr h3 = tile_hdr(A, row_ptr, t + 3 * G, P.ntiles);
+        cp_async_wait_all();
+        const bool late = !mbar_wait_bounded(&S.bar[cur], (uint32_t)((it >> 1) & 1), kWaitPolls);
+        // block-uniform decision: every thread leaves the loop together
+        if (__syncthreads_or(late)) {
+            ok = false;
+            if (threadIdx.x == 0) atomicExch(&flags[FLAG_TIMEOUT], 1);
+            break;
+        }
+        issue_tile<1, 8>(A, P, RD, n, t + G, h1, cur ^ 1, S, S.ubuf + ((it + 1) % 3) * P.ucap);
+        issue_list(A, P, t + 2 * G, h2, S.ubuf + ((it + 2) % 3) * P.ucap);
+        cp_async_commit();
+        OwnDefo<DIM> nxt = own_defo<DIM, OUT>(RD, row_ptr, B0, H, u, (t + G) * kTileRows + threadIdx.x, n);
+        const int64_t i = t * kTileRows + threadIdx.x;
+        const float4* gb = S.gbuf + (size_t)cur * P.gw + threadIdx.x;
+        const float4* rb = S.rbuf + (size_t)cur * P.mcap;
+        const bool staged = h0.m <= P.mcap;
+        const int smax = max(h0.m - 1, 0);
+        const float2 nv01 = make_float2(-own.v[0], -own.v[1]);
+        const float nv2 = -own.v[2];
+        Kahan2 c01[DIM];
+        Kahan2 r2;
+        Kahan<float> l22;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) c01[c].init();
+        r2.init();
+        l22.init();
+#pragma unroll 4
+        for (int k = 0; k < own.len; ++k) {
+            float4 e = gb[(size_t)k * kTileRows];
+            int s = min(max(__float_as_int(e.w), 0), smax);
+            float4 vj;
+            if (staged) {
+                vj = rb[s];
+            } else {
+                int64_t j = min(max((int64_t)A.uidx[h0.P0 + s], (int64_t)0), n - 1);
+                vj = __ldg(reinterpret_cast<const float4*>(RD + 8 * j) + 1);
+            }
+            float2 dv01 = __fadd2_rn(make_float2(vj.x, vj.y), nv01);
+            c01[0].add(__fmul2_rn(dv01, make_float2(e.x, e.x)));
+            c01[1].add(__fmul2_rn(dv01, make_float2(e.y, e.y)));
+            if (DIM == 3) {
+                float dv2 = vj.z + nv2;
+                c01[DIM - 1].add(__fmul2_rn(dv01, make_float2(e.z, e.z)));
+                r2.add(__fmul2_rn(make_float2(dv2, dv2), make_float2(e.x, e.y)));
+                l22.add(dv2 * e.z);
+            }
+        }
+        if (i < n) {
+            float Lt[DIM * DIM];
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+                float2 v = c01[c].value();
+                Lt[0 * DIM + c] = v.x;
+                Lt[1 * DIM + c] = v.y;
+            }
+            if (DIM == 3) {
+                float2 v = r2.value();
+                Lt[2 * DIM + 0] = v.x;
+                Lt[2 * DIM + 1] = v.y;
+                Lt[2 * DIM + 2] = l22.value();
+            }
+            defo_finish<DIM, OUT>(Lt, own.b0, (own.bits & kFixedBit) != 0, own.v, i, n, K, RM, H, u, dFdt, own.h,
+                                  own.u);
+        }
+        __syncthreads();
+        own = nxt;
+        h0 = h1;
+        h1 = h2;
+        h2 = h3;
+    }
+    if (!ok) {
+        cp_async_wait_all();
+        mbar_wait_bounded(&S.bar[0], 0, kWaitPolls);
+        mbar_wait_bounded(&S.bar[1], 0, kWaitPolls);
+    }
+}
+
 // The state's tile plan as launch arguments (tile_m == nullptr: no plan).
 struct TlPlan {
     GeoArgs mom, defo;
-    size_t mom_bytes, defo_bytes;
-    bool on;
+    PipeArgs pmom, pdefo;
+    size_t mom_bytes, defo_bytes, pmom_bytes, pdefo_bytes;
+    bool on, pipe_mom, pipe_defo;
+    int grid;
 };
 
 TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim) {
@@ -878,7 +1293,9 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
     t.on = st->plan && st->plan_nnz > 0 && st->plan_maxm > 0;
     t.mom = GeoArgs{nullptr, nullptr, nullptr, nullptr, 0};
     t.defo = t.mom;
-    t.mom_bytes = t.defo_bytes = 0;
+    t.mom_bytes = t.defo_bytes = t.pmom_bytes = t.pdefo_bytes = 0;
+    t.pipe_mom = t.pipe_defo = false;
+    t.grid = 0;
     if (!t.on) return t;
     TilePlan tp = tile_plan_view(st->plan, n, st->plan_nnz);
     int npl = dim == 3 ? 3 : 1;
@@ -887,6 +1304,17 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
     t.defo = GeoArgs{tp.tile_m, tp.tile_so, tp.uidx, tp.geo, md};
     t.mom_bytes = (size_t)mm * 16 * npl;
     t.defo_bytes = (size_t)md * 16;
+    // persistent form: both entry buffers, both staging buffers and three lists
+    const size_t limit = 220 * 1024;
+    int gw = kTileRows * st->plan_maxrow;
+    t.pmom = PipeArgs{tp.ntiles, gw, mm, (mm + 3) & ~3};
+    t.pdefo = PipeArgs{tp.ntiles, gw, md, (md + 3) & ~3};
+    t.pmom_bytes = pipe_smem_bytes(t.pmom, npl);
+    t.pdefo_bytes = pipe_smem_bytes(t.pdefo, 1);
+    t.pipe_mom = !ctx->no_pipe && t.pmom_bytes <= limit;
+    t.pipe_defo = !ctx->no_pipe && t.pdefo_bytes <= limit;
+    int64_t g = ctx->num_sms > 0 ? ctx->num_sms : 1;
+    t.grid = (int)(g < tp.ntiles ? g : tp.ntiles);
     return t;
 }
 
@@ -911,30 +1339,33 @@ void tl32_passes(int which, int out, int64_t n, const sph_tlsph_state* st, const
 }
 
 template <int DIM>
-void tl32_plan_pass(int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K, const TlPlan& tp,
-                    double* r1, double* r2, cudaStream_t s) {
-    dim3 g((unsigned)((n + kTileRows - 1) / kTileRows)), b(kTileRows);
+void tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K,
+                    const TlPlan& tp, double* r1, double* r2, cudaStream_t s) {
+    dim3 g((unsigned)((n + kTileRows - 1) / kTileRows)), b(kTileRows), gp((unsigned)tp.grid);
     if (which == 0) {
-        if (out == OUT_RATES) {
-            auto* f = k_tl_mom32g<DIM, OUT_RATES>;
+        if (tp.pipe_mom) {
+            ctx->waits_pending = true;
+            auto* f = out == OUT_RATES ? k_tl_mom32p<DIM, OUT_RATES> : k_tl_mom32p<DIM, OUT_STEP>;
             sph_allow_dynamic_smem((const void*)f);
-            f<<<g, b, tp.mom_bytes, s>>>(st->rm, st->rd, st->row_ptr, n, K, tp.mom, r1);
+            f<<<gp, b, tp.pmom_bytes, s>>>(st->rm, st->rd, st->row_ptr, n, K, tp.mom, tp.pmom,
+                                           out == OUT_RATES ? r1 : nullptr, ctx->flags);
         } else {
-            auto* f = k_tl_mom32g<DIM, OUT_STEP>;
+            auto* f = out == OUT_RATES ? k_tl_mom32g<DIM, OUT_RATES> : k_tl_mom32g<DIM, OUT_STEP>;
             sph_allow_dynamic_smem((const void*)f);
-            f<<<g, b, tp.mom_bytes, s>>>(st->rm, st->rd, st->row_ptr, n, K, tp.mom, nullptr);
+            f<<<g, b, tp.mom_bytes, s>>>(st->rm, st->rd, st->row_ptr, n, K, tp.mom, out == OUT_RATES ? r1 : nullptr);
         }
     } else {
-        if (out == OUT_RATES) {
-            auto* f = k_tl_defo32g<DIM, OUT_RATES>;
+        if (tp.pipe_defo) {
+            ctx->waits_pending = true;
+            auto* f = out == OUT_RATES ? k_tl_defo32p<DIM, OUT_RATES> : k_tl_defo32p<DIM, OUT_STEP>;
             sph_allow_dynamic_smem((const void*)f);
-            f<<<g, b, tp.defo_bytes, s>>>(st->rd, st->rm, st->row_ptr, n, K, tp.defo, st->B32, st->H32, st->u32,
-                                          r2);
+            f<<<gp, b, tp.pdefo_bytes, s>>>(st->rd, st->rm, st->row_ptr, n, K, tp.defo, tp.pdefo, st->B32, st->H32,
+                                            st->u32, out == OUT_RATES ? r2 : nullptr, ctx->flags);
         } else {
-            auto* f = k_tl_defo32g<DIM, OUT_STEP>;
+            auto* f = out == OUT_RATES ? k_tl_defo32g<DIM, OUT_RATES> : k_tl_defo32g<DIM, OUT_STEP>;
             sph_allow_dynamic_smem((const void*)f);
             f<<<g, b, tp.defo_bytes, s>>>(st->rd, st->rm, st->row_ptr, n, K, tp.defo, st->B32, st->H32, st->u32,
-                                          nullptr);
+                                          out == OUT_RATES ? r2 : nullptr);
         }
     }
 }
@@ -953,9 +1384,9 @@ void tl32_lanes(int lanes, int which, int out, int64_t n, const sph_tlsph_state*
 // One float32 pass: on the tile plan when the state has one, else the gather form
 // with the context's lanes per row.
 template <int DIM>
-void tl32(int lanes, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K,
+void tl32(sph_ctx* ctx, int lanes, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K,
           const TlPlan& tp, double* r1, double* r2, cudaStream_t s) {
-    if (tp.on) tl32_plan_pass<DIM>(which, out, n, st, K, tp, r1, r2, s);
+    if (tp.on) tl32_plan_pass<DIM>(ctx, which, out, n, st, K, tp, r1, r2, s);
     else if (K.periodic) tl32_lanes<DIM, true>(lanes, which, out, n, st, K, r1, r2, s);
     else tl32_lanes<DIM, false>(lanes, which, out, n, st, K, r1, r2, s);
 }
@@ -965,7 +1396,7 @@ bool fp64_ready(const sph_tlsph_state* st) { return st->x && st->v && st->H && s
 
 }  // namespace
 
-extern "C" int sph_tlsph_pack(sph_ctx* ctx, const sph_tlsph_params* p, sph_tlsph_state* st, void* stream) {
+extern "C" int sph_tlsph_pack(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st, void* stream) {
     if (!ctx) return SPH_ERR_ARG;
     int r = check_tl(p, st);
     if (r) return r;
@@ -982,32 +1413,42 @@ extern "C" int sph_tlsph_pack(sph_ctx* ctx, const sph_tlsph_params* p, sph_tlsph
         k_tl_pack<3><<<grid_for(n, 256), 256, 0, s>>>(st->r0, st->V0, st->B0, st->fixed, st->x, st->v, st->H, n, g,
                                                       st->rd, st->rm, st->H32, st->u32, st->B32);
     SPH_LAUNCH_CHECK(ctx);
+    return SPH_OK;
+}
+
+// Tile plan of the state's lists and reference configuration (see sph.h).
+extern "C" int sph_tlsph_plan(sph_ctx* ctx, const sph_tlsph_params* p, sph_tlsph_state* st, void* stream) {
+    if (!ctx) return SPH_ERR_ARG;
+    int r = check_tl(p, st);
+    if (r) return r;
+    if (!st->plan) return SPH_ERR_ARG;
+    int64_t n = p->dom.n;
+    cudaStream_t s = as_stream(stream);
     st->plan_nnz = 0;
-    st->plan_maxm = st->plan_maxp = 0;
-    if (st->plan) {
-        int64_t nnz = 0, maxrow = 0;
-        r = sph_row_stats(ctx, st->row_ptr, n, s, &nnz, &maxrow);
-        if (r) return r;
-        if (st->plan_bytes < (int64_t)tile_plan_bytes(n, nnz, maxrow)) return SPH_ERR_CAPACITY;
-        if (nnz > 0) {
-            int32_t mm = 0, mp = 0, mw = 0;
-            r = sph_build_tile_plan(ctx, st->row_ptr, st->col, n, nnz, st->plan, s, &mm, &mp, &mw);
-            if (r) return r;
-            TilePlan tp = tile_plan_view(st->plan, n, nnz);
-            TLK<double> K = make_tl_consts<double>(p);
-            unsigned nt = (unsigned)tp.ntiles;
-            if (p->dom.dim == 2)
-                k_tl_geo<2><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_e,
-                                                     tp.tile_so, n, K, tp.geo);
-            else
-                k_tl_geo<3><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_e,
-                                                     tp.tile_so, n, K, tp.geo);
-            SPH_LAUNCH_CHECK(ctx);
-            st->plan_nnz = nnz;
-            st->plan_maxm = mm;
-            st->plan_maxp = mp;
-        }
-    }
+    st->plan_maxm = st->plan_maxrow = 0;
+    if (n == 0) return SPH_OK;
+    int64_t nnz = 0, maxrow = 0;
+    r = sph_row_stats(ctx, st->row_ptr, n, s, &nnz, &maxrow);
+    if (r) return r;
+    if (st->plan_bytes < (int64_t)tile_plan_bytes(n, nnz, maxrow)) return SPH_ERR_CAPACITY;
+    if (nnz == 0) return SPH_OK;
+    int32_t mm = 0, mp = 0, mw = 0;
+    r = sph_build_tile_plan(ctx, st->row_ptr, st->col, n, nnz, st->plan, s, &mm, &mp, &mw);
+    if (r) return r;
+    TilePlan tp = tile_plan_view(st->plan, n, nnz);
+    TLK<double> K = make_tl_consts<double>(p);
+    unsigned nt = (unsigned)tp.ntiles;
+    if (p->dom.dim == 2)
+        k_tl_geo<2><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_e, tp.tile_so,
+                                             n, K, tp.geo);
+    else
+        k_tl_geo<3><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_e, tp.tile_so,
+                                             n, K, tp.geo);
+    SPH_LAUNCH_CHECK(ctx);
+    SPH_CUDA(ctx, cudaStreamSynchronize(s));
+    st->plan_nnz = nnz;
+    st->plan_maxm = mm;
+    st->plan_maxrow = mw;
     return SPH_OK;
 }
 
@@ -1039,7 +1480,10 @@ extern "C" int sph_tlsph_unpack(sph_ctx* ctx, const sph_tlsph_params* p, const s
     else
         k_tl_unpack<3><<<grid_for(n, 256), 256, 0, s>>>(st->r0, st->rd, st->H32, st->u32, n, st->x, st->v, st->H);
     SPH_LAUNCH_CHECK(ctx);
-    return SPH_OK;
+    // a bounded wait that expired in a persistent planned pass since the last unpack
+    if (!ctx->waits_pending) return SPH_OK;
+    ctx->waits_pending = false;
+    return sph_take_timeout(ctx, s);
 }
 
 extern "C" int sph_tlsph_rates(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st, double* dvdt,
@@ -1074,12 +1518,12 @@ extern "C" int sph_tlsph_rates(sph_ctx* ctx, const sph_tlsph_params* p, const sp
         int lanes = ctx->lanes[SPH_PASS_TLSPH];
         if (dim == 2) {
             k_tl_stress32<2><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm);
-            tl32<2>(lanes, 0, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
-            tl32<2>(lanes, 1, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
+            tl32<2>(ctx, lanes, 0, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
+            tl32<2>(ctx, lanes, 1, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
         } else {
             k_tl_stress32<3><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm);
-            tl32<3>(lanes, 0, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
-            tl32<3>(lanes, 1, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
+            tl32<3>(ctx, lanes, 0, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
+            tl32<3>(ctx, lanes, 1, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
         }
     }
     SPH_LAUNCH_CHECK(ctx);
@@ -1132,12 +1576,12 @@ extern "C" int sph_tlsph_step(sph_ctx* ctx, const sph_tlsph_params* p, const sph
     sph_timer_end(ctx, t, s);
     for (int k = 0; k < nsteps; ++k) {
         t = sph_timer_begin(ctx, SPH_TIMER_TL_MOMENTUM, s);
-        if (dim == 2) tl32<2>(lanes, 0, OUT_STEP, n, st, K, ts, nullptr, nullptr, s);
-        else tl32<3>(lanes, 0, OUT_STEP, n, st, K, ts, nullptr, nullptr, s);
+        if (dim == 2) tl32<2>(ctx, lanes, 0, OUT_STEP, n, st, K, ts, nullptr, nullptr, s);
+        else tl32<3>(ctx, lanes, 0, OUT_STEP, n, st, K, ts, nullptr, nullptr, s);
         sph_timer_end(ctx, t, s);
         t = sph_timer_begin(ctx, SPH_TIMER_TL_DEFORM, s);
-        if (dim == 2) tl32<2>(lanes, 1, OUT_STEP, n, st, K, ts, nullptr, nullptr, s);
-        else tl32<3>(lanes, 1, OUT_STEP, n, st, K, ts, nullptr, nullptr, s);
+        if (dim == 2) tl32<2>(ctx, lanes, 1, OUT_STEP, n, st, K, ts, nullptr, nullptr, s);
+        else tl32<3>(ctx, lanes, 1, OUT_STEP, n, st, K, ts, nullptr, nullptr, s);
         sph_timer_end(ctx, t, s);
     }
     SPH_LAUNCH_CHECK(ctx);
