@@ -121,10 +121,10 @@ def _setup_plate(api, inputs, ctx, kappa, dp=0.001):
                 nnz=int(col.numel()), n=int(r0.shape[1]), nfb=nfb)
 
 
-def _solid(api, ctx, s, precision):
+def _solid(api, ctx, s, precision, tiles=True):
     c = s["c"]
     return api.TLSolid(ctx, s["d"], s["r0"], s["vol"], s["B0"], s["fixed"], s["rp"], s["col"], s["v"], c["dt"],
-                       c["rho0"], c["lam"], c["G"], law=api.SPH_NEO_HOOKEAN, precision=precision)
+                       c["rho0"], c["lam"], c["G"], law=api.SPH_NEO_HOOKEAN, precision=precision, tiles=tiles)
 
 
 def _time_steps(ctx, sol, steps, warmup, world, clocks=None):
@@ -235,7 +235,7 @@ def _roof(bytes_per_launch, ms_per_launch, peak):
             "algorithmic_bytes_per_launch": bytes_per_launch}
 
 
-def _eulerian_case(api, ctx, case, precision):
+def _eulerian_case(api, ctx, case, precision, tiles=True):
     import torch
     d = case["domain"]
     dev = ctx.device
@@ -247,7 +247,7 @@ def _eulerian_case(api, ctx, case, precision):
     rp, col = api.build_neighbors(ctx, d, pos)
     B, _, nfb = api.kgc(ctx, d, pos, vol, rp, col)
     sim = api.Eulerian(ctx, d, pos, vol, B, rp, col, case["p"][oh] / case["c0"] ** 2, case["v"][:, oh], case["dt"],
-                       case["rho0"], case["c0"], case["mu"], precision=precision)
+                       case["rho0"], case["c0"], case["mu"], precision=precision, tiles=tiles)
     return sim, int(col.numel()), oh
 
 
@@ -420,12 +420,21 @@ def run_gpu(args):
     ctx = api.Context(torch.cuda.current_device())
     K, W = args.steps, args.warmup
 
+    if args.profile == "eu3d":
+        case = inputs.tgv3d(n=args.eu_n, kappa=args.kappa)
+        sim, nnz, _ = _eulerian_case(api, ctx, case, api.SPH_FP32_KAHAN, tiles=not args.no_tiles)
+        sim.step(W + K)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "eu3d", "n": args.eu_n, "kappa": args.kappa, "nnz": nnz, "steps": W + K}))
+        ctx.close()
+        return 0
     if args.profile:
         # profiling driver: the headline workload only (setup, then W + K float32 steps)
         s = _setup_plate(api, inputs, ctx, args.kappa)
         if args.lanes:
             ctx.set_lanes(api.SPH_PASS_TLSPH, args.lanes)
-        sol = _solid(api, ctx, s, api.SPH_FP64 if args.profile == "fp64" else api.SPH_FP32_KAHAN)
+        sol = _solid(api, ctx, s, api.SPH_FP64 if args.profile == "fp64" else api.SPH_FP32_KAHAN,
+                     tiles=not args.no_tiles)
         sol.step(W + K)
         torch.cuda.synchronize()
         print(json.dumps({"profile": args.profile, "kappa": args.kappa, "particles": s["n"], "nnz": s["nnz"],
@@ -582,8 +591,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--profile", choices=["fp32", "fp64"], default=None,
-                    help="run only the plate workload (setup + warmup + steps) for ncu captures")
+    ap.add_argument("--profile", choices=["fp32", "fp64", "eu3d"], default=None,
+                    help="run only one workload (setup + warmup + steps) for ncu captures: the plate "
+                         "(fp32 or fp64) or the 3D Taylor-Green vortex of side --eu-n (eu3d, float32)")
+    ap.add_argument("--eu-n", type=int, default=64, help="lattice side of the --profile eu3d workload")
+    ap.add_argument("--no-tiles", action="store_true", help="--profile: without tile plans (per-pair geometry)")
     ap.add_argument("--kappa", type=float, default=1.6)
     ap.add_argument("--lanes", type=int, default=0, help="lanes per particle of the TL passes (0: tuned)")
     ap.add_argument("--headline-only", action="store_true", help="skip the other rows' workloads")

@@ -249,11 +249,34 @@ typedef struct {
     double* v_tmp;
     float*  rec;
     float*  rec_tmp;
+    void*   plan;          /* optional tile plan buffer (see sph_eulerian_plan) */
+    int64_t plan_bytes;
+    int64_t plan_nnz;      /* written by sph_eulerian_plan */
+    int32_t plan_maxm;     /* written by sph_eulerian_plan */
+    int32_t plan_maxrow;   /* written by sph_eulerian_plan */
 } sph_eulerian_state;
 
 /* float64 (pos, vol, B, drho, v) -> packed float32 records (rec, rec_tmp). */
 int sph_eulerian_pack(sph_ctx* ctx, const sph_eulerian_params* prm,
                       const sph_eulerian_state* st, void* stream);
+/* Tile plan of the float32 passes (not an operation of the paper: a staging
+ * layout of the pair pass of Eq. 18).  Eulerian particles are fixed, so the pair
+ * geometry is too: sph_eulerian_plan builds in st->plan (caller-owned device
+ * buffer of plan_bytes >= sph_eulerian_plan_bytes(...) bytes, 32-byte aligned),
+ * from pos/vol/B/row_ptr/col and the parameters mu, h, per tile of 128 consecutive
+ * rows, the list of its distinct neighbours and, per pair, in float64 then stored
+ * in float32, the corrected gradient G = -2 V_j (B_i + B_j)/2 grad W_ij (Eq. 27),
+ * the viscous factor 2 mu V_j (r_ij . grad W_ij)/(r^2 + 0.01 h^2), the normal
+ * -r_ij/r and the neighbour's position in its tile's list, in the sliced order of
+ * sph_tlsph_state.  It writes plan_nnz, plan_maxm and plan_maxrow.  The float32
+ * passes then stage each tile's neighbour (v_j, drho_j) in shared memory, one
+ * thread per row (the lanes setting unused).  Rebuild it when the lists, pos, vol,
+ * B, h or mu change.  Synchronises the stream; SPH_ERR_CAPACITY when plan_bytes is
+ * too small.  plan = NULL or plan_nnz = 0: the float32 passes evaluate the geometry
+ * per pair from the records. */
+int sph_eulerian_plan_bytes(sph_ctx* ctx, const sph_eulerian_params* prm, const sph_eulerian_state* st,
+                            int64_t* bytes_host, void* stream);
+int sph_eulerian_plan(sph_ctx* ctx, const sph_eulerian_params* prm, sph_eulerian_state* st, void* stream);
 /* packed float32 rec -> float64 (drho, v). */
 int sph_eulerian_unpack(sph_ctx* ctx, const sph_eulerian_params* prm,
                         const sph_eulerian_state* st, void* stream);
@@ -337,7 +360,7 @@ typedef struct {
  *   H32 [dim*dim][n], u32 [dim][n] (x - r0), B32 [nsym][n].
  *   The float32 path needs len_a >= 2 kappa h + 2 S_a along a periodic axis.
  * Tile plan (optional, float32 path): plan -> caller-owned device buffer of
- *   plan_bytes >= sph_tlsph_plan_bytes(...) bytes, 16-byte aligned.  sph_tlsph_plan
+ *   plan_bytes >= sph_tlsph_plan_bytes(...) bytes, 32-byte aligned.  sph_tlsph_plan
  *   builds in it, from row_ptr/col/r0/V0, (i) per tile of 128
  *   consecutive rows the list of its distinct neighbours and (ii) per pair the
  *   reference-configuration factor w_ij = grad0 W_ij V0_j of Eqs. 30-31, computed in

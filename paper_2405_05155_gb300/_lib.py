@@ -39,7 +39,8 @@ class EulerianParams(ctypes.Structure):
 
 class EulerianState(ctypes.Structure):
     _fields_ = [(name, c_vp) for name in ("row_ptr", "col", "pos", "vol", "B", "drho", "v", "drho_tmp",
-                                          "v_tmp", "rec", "rec_tmp")]
+                                          "v_tmp", "rec", "rec_tmp", "plan")] + [
+        ("plan_bytes", c_i64), ("plan_nnz", c_i64), ("plan_maxm", c_i32), ("plan_maxrow", c_i32)]
 
 
 class TLParams(ctypes.Structure):
@@ -103,6 +104,8 @@ _SIGNATURES = {
     "sph_mlp_train_step": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_vp, c_vp, c_i64, _P(c_dbl),
                                           c_vp]),
     "sph_relax_propose": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, c_vp]),
+    "sph_eulerian_plan_bytes": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), _P(c_i64), c_vp]),
+    "sph_eulerian_plan": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), c_vp]),
     "sph_tlsph_plan_bytes": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), _P(c_i64), c_vp]),
     "sph_tlsph_plan": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp]),
     "sph_set_stage_cap": (ctypes.c_int, [c_vp, ctypes.c_int]),

@@ -140,7 +140,7 @@ class Eulerian:
     """Eulerian WCSPH state on the device (float64 arrays and, for float32 steps, packed records)."""
 
     def __init__(self, ctx, dom, pos, vol, B, row_ptr, col, drho, v, dt, rho0, c0, mu, eta=15.0,
-                 precision=SPH_FP64, integrator=SPH_TWO_PASS):
+                 precision=SPH_FP64, integrator=SPH_TWO_PASS, tiles=True):
         self.ctx = ctx
         dev = ctx.device
         self.n = pos.shape[1]
@@ -164,8 +164,18 @@ class Eulerian:
         self.st = L.EulerianState()
         for name in ("row_ptr", "col", "pos", "vol", "B", "drho", "v", "drho_tmp", "v_tmp", "rec", "rec_tmp"):
             setattr(self.st, name, getattr(self, name).data_ptr())
+        self.plan = None
+        if tiles and precision == SPH_FP32_KAHAN:
+            # tile plan: fixed pair geometry precomputed, neighbours staged per tile (sph_eulerian_plan)
+            nb = ctypes.c_int64()
+            self._call("sph_eulerian_plan_bytes", ctypes.byref(nb), _stream())
+            self.plan = torch.empty(max(nb.value, 16), dtype=torch.uint8, device=dev)
+            self.st.plan = self.plan.data_ptr()
+            self.st.plan_bytes = self.plan.numel()
         if precision == SPH_FP32_KAHAN:
             self.pack()
+            if self.plan is not None:
+                self._call("sph_eulerian_plan", _stream())
 
     def _call(self, name, *args):
         fn = getattr(self.ctx.lib, name)

@@ -174,6 +174,26 @@ struct __align__(32) F8 {
     float v[8];
 };
 
+// 256-bit streaming read of data used once: not kept in L1, and the L2 fetches the
+// surrounding 256 bytes (the next entries of the same stream).
+__device__ __forceinline__ F8 ldg8_stream(const float* p) {
+    F8 r;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]),
+          "=f"(r.v[7])
+        : "l"(p));
+    return r;
+}
+
+// 128-bit streaming read of data used once (as ldg8_stream).
+__device__ __forceinline__ float4 ldg4_stream(const float4* p) {
+    float4 r;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.f32 {%0,%1,%2,%3}, [%4];"
+        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+        : "l"(p));
+    return r;
+}
+
 // 256-bit read-only gather (the record must not be written during the kernel).
 __device__ __forceinline__ F8 ldg8(const float* p) {
     F8 r;

@@ -11,6 +11,7 @@
 // from momentum), so a step is one (fused) or two (momentum, continuity) launches.
 #include "common.cuh"
 #include "euler_core.cuh"
+#include "tiles.cuh"
 
 namespace {
 
@@ -101,6 +102,202 @@ __global__ void __launch_bounds__(256) k_euler32(const float* __restrict__ Rin, 
     float rm, rp[DIM];
     euler_row32<DIM, MODE, LANES, PER>(Rin, col, b, e, lane, oi, bi, Bi, vi, dri, K, rm, rp);
     if (!active || lane != 0) return;
+    if (OUT == OUT_RATES) {
+        if (MODE & WANT_MASS) rate_mass[i] = (double)rm;
+        if (MODE & WANT_MOM)
+            for (int a = 0; a < DIM; ++a) rate_mom[a * n + i] = (double)rp[a];
+        return;
+    }
+    float vn[DIM], drn;
+    euler_update32<DIM, OUT>(vi, dri, rm, rp, K, vn, drn);
+    store_dyn<DIM>(Rout, i, vn, drn);
+}
+
+// ---------------------------------------------------- float32 passes on a tile plan
+// Eulerian particles do not move, so every pair's geometry is fixed: k_eu_geo
+// computes it once in float64 (tiles.cuh layout, 32-byte entries, rows ordered by
+// offset) as
+//   (G, Vis, n, slot),  G = -2 V_j (B_i + B_j)/2 grad W_ij   (Eqs. 18, 27),
+//   Vis = 2 mu V_j (r_ij . grad W_ij) / (r^2 + 0.01 h^2),  n = -r_ij / r,
+// each rounded once to float32.  A planned pass then needs only the neighbour's
+// (v_j, drho_j), which a block stages per tile in shared memory, and evaluates the
+// acoustic Riemann flux (Eqs. 25-26) pair by pair.
+struct GeoArgsE {
+    const int32_t* tile_m;
+    const int64_t* tile_so;
+    const int32_t* uidx;
+    const float* geo;   // 8 floats per entry
+    int mcap;
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(kTileRows) k_eu_geo(const double* __restrict__ pos, const double* __restrict__ vol,
+                                                      const double* __restrict__ B,
+                                                      const int64_t* __restrict__ row_ptr,
+                                                      const int32_t* __restrict__ col,
+                                                      const uint16_t* __restrict__ lcol,
+                                                      const int32_t* __restrict__ tile_e,
+                                                      const int64_t* __restrict__ tile_so, int64_t n,
+                                                      EulerK<double> K, float* __restrict__ geo) {
+    constexpr int NS = NSym<DIM>::v;
+    const int64_t tile = blockIdx.x;
+    const int64_t i = tile * kTileRows + threadIdx.x;
+    const bool active = i < n;
+    const int64_t b = active ? row_ptr[i] : 0;
+    const int len = active ? (int)(row_ptr[i + 1] - b) : 0;
+    const int width = tile_e[tile] / kTileRows;
+    float* out = geo + 8 * (tile_so[tile] + threadIdx.x);
+    double xi[DIM], Bi[NS];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) xi[a] = active ? pos[a * n + i] : 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) Bi[s] = active ? B[s * n + i] : 0.0;
+    auto rij = [&](int j, double* r, double& d2) {
+        d2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            double dx = xi[a] - pos[a * n + j];
+            if ((K.periodic >> a) & 1u) {
+                if (dx > K.half[a]) dx -= K.Lh[a];
+                else if (dx < -K.half[a]) dx += K.Lh[a];
+            }
+            r[a] = dx;
+            d2 += dx * dx;
+        }
+    };
+    uint32_t order[kSortCap];
+    const bool sorted = offset_order<DIM>(
+        len, 2.0 * K.inv_h,
+        [&](int k, double* rr) {
+            double r[DIM], d2;
+            rij(col[b + k], r, d2);
+            for (int a = 0; a < DIM; ++a) rr[a] = r[a];
+        },
+        order);
+    for (int k = 0; k < width; ++k) {
+        float e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (k < len) {
+            int64_t p = b + (sorted ? (int)(order[k] & 0xFFFFFu) : k);
+            int j = col[p];
+            double r[DIM], d2, Bb[NS], gw[DIM], g[DIM];
+            rij(j, r, d2);
+            double gs = wendland_gs<double>(sqrt(d2) * K.inv_h, K.coef);
+            double Vj = vol[j];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) gw[a] = gs * r[a];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) Bb[s] = 0.5 * (Bi[s] + B[s * n + j]);
+            sym_matvec<DIM, double>(Bb, gw, g);
+            double rinv = 1.0 / sqrt(d2);
+            for (int a = 0; a < DIM; ++a) {
+                e[a] = (float)(-2.0 * Vj * g[a]);
+                e[4 + a] = (float)(-r[a] * rinv);
+            }
+            e[3] = (float)(K.mu2 * Vj * (gs * d2) / (d2 + K.eps_h2));
+            e[7] = __int_as_float((int)lcol[p]);
+        }
+        float4* o = reinterpret_cast<float4*>(out + (int64_t)8 * k * kTileRows);
+        o[0] = make_float4(e[0], e[1], e[2], e[3]);
+        o[1] = make_float4(e[4], e[5], e[6], e[7]);
+    }
+}
+
+// One pair of a planned pass from its entry and the neighbour's (v_j, drho_j).
+// Every operation is written out (fused multiply-adds explicit, products and sums
+// rounded on their own), so the result does not depend on where it is inlined.
+template <int DIM, int MODE>
+__device__ __forceinline__ void euler_pair_geo(const F8& e, float4 dj, const float* vi, float dri,
+                                               const EulerK<float>& K, Kahan<float>& am, Kahan<float>* ap) {
+    const float G[3] = {e.v[0], e.v[1], e.v[2]};
+    const float nrm[3] = {e.v[4], e.v[5], e.v[6]};
+    const float vj[3] = {dj.x, dj.y, dj.z};
+    const float drj = dj.w;
+    float ul = __fmul_rn(vi[0], nrm[0]), ur = __fmul_rn(vj[0], nrm[0]);
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) {
+        ul = fmaf(vi[a], nrm[a], ul);
+        ur = fmaf(vj[a], nrm[a], ur);
+    }
+    const float pi = __fmul_rn(K.c0sq, dri), pj = __fmul_rn(K.c0sq, drj);
+    const float rho_bar = fmaf(0.5f, __fadd_rn(dri, drj), K.rho0);
+    const float du = __fsub_rn(ul, ur);
+    const float beta = fminf(__fmul_rn(K.eta, fmaxf(__fmul_rn(du, K.inv_c0), 0.0f)), 1.0f);
+    const float ubar = __fmul_rn(0.5f, __fadd_rn(ul, ur));
+    const float rc = __fmul_rn(rho_bar, K.c0);
+    const float hb = __fmul_rn(0.5f, beta);
+    const float ustar = fmaf(__fmul_rn(hb, beta), __fdiv_rn(__fsub_rn(pi, pj), rc), ubar);   // Eq. 25
+    const float pstar = fmaf(__fmul_rn(hb, rc), du, __fmul_rn(0.5f, __fadd_rn(pi, pj)));
+    const float dus = __fsub_rn(ustar, ubar);
+    float vs[DIM];
+    float vG = 0.0f;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        vs[a] = fmaf(dus, nrm[a], __fmul_rn(0.5f, __fadd_rn(vi[a], vj[a])));
+        vG = a == 0 ? __fmul_rn(vs[0], G[0]) : fmaf(vs[a], G[a], vG);
+    }
+    if (MODE & WANT_MASS) am.add(__fmul_rn(rho_bar, vG));
+    if (MODE & WANT_MOM) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+            ap[a].add(fmaf(e.v[3], __fsub_rn(vi[a], vj[a]), fmaf(pstar, G[a], __fmul_rn(__fmul_rn(rho_bar, vs[a]), vG))));
+    }
+}
+
+template <int DIM, int MODE, int OUT>
+__global__ void __launch_bounds__(kTileRows, 6) k_euler32g(const float* __restrict__ Rin, float* __restrict__ Rout,
+                                                           const int64_t* __restrict__ row_ptr, int64_t n,
+                                                           EulerK<float> K, GeoArgsE A,
+                                                           double* __restrict__ rate_mass,
+                                                           double* __restrict__ rate_mom) {
+    extern __shared__ __align__(16) unsigned char eu_smem[];
+    float4* sp = reinterpret_cast<float4*>(eu_smem);
+    const int64_t tile = blockIdx.x;
+    const int64_t i0 = tile * kTileRows;
+    const int64_t i = i0 + threadIdx.x;
+    const bool active = i < n;
+    const int64_t ii = active ? i : i0;
+    const int64_t P0 = row_ptr[i0];
+    const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
+    const int m = A.tile_m[tile];
+    const int64_t so = A.tile_so[tile];
+    const float4 own = __ldg(reinterpret_cast<const float4*>(Rin + kRecWords * ii) + 3);
+    const bool staged = m <= A.mcap;
+    if (staged) {
+        for (int s = threadIdx.x; s < m; s += blockDim.x) {
+            int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
+            sp[s] = __ldg(reinterpret_cast<const float4*>(Rin + kRecWords * j) + 3);
+        }
+    }
+    __syncthreads();
+    const float vi[3] = {own.x, own.y, own.z};
+    const float dri = own.w;
+    Kahan<float> am;
+    Kahan<float> ap[DIM];
+    am.init();
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) ap[a].init();
+    const float* g = A.geo + 8 * (so + threadIdx.x);
+    const int smax = max(m - 1, 0);
+    if (staged) {
+#pragma unroll 4
+        for (int k = 0; k < len; ++k) {
+            F8 e = ldg8_stream(g + (int64_t)8 * k * kTileRows);
+            int s = min(max(__float_as_int(e.v[7]), 0), smax);
+            euler_pair_geo<DIM, MODE>(e, sp[s], vi, dri, K, am, ap);
+        }
+    } else {
+        for (int k = 0; k < len; ++k) {
+            F8 e = ldg8_stream(g + (int64_t)8 * k * kTileRows);
+            int s = min(max(__float_as_int(e.v[7]), 0), smax);
+            int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
+            euler_pair_geo<DIM, MODE>(e, __ldg(reinterpret_cast<const float4*>(Rin + kRecWords * j) + 3), vi, dri,
+                                      K, am, ap);
+        }
+    }
+    if (!active) return;
+    float rm = am.value(), rp[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) rp[a] = ap[a].value();
     if (OUT == OUT_RATES) {
         if (MODE & WANT_MASS) rate_mass[i] = (double)rm;
         if (MODE & WANT_MOM)
@@ -241,8 +438,51 @@ void dispatch32p(int lanes, int out, const sph_eulerian_params* p, const sph_eul
     }
 }
 
-void dispatch32(int lanes, int out, const sph_eulerian_params* p, const sph_eulerian_state* st,
+// The state's tile plan as launch arguments (tile_m == nullptr: none built).
+struct EuPlan {
+    GeoArgsE A;
+    size_t bytes;
+    bool on;
+};
+
+EuPlan eu_plan(const sph_ctx* ctx, const sph_eulerian_state* st, int64_t n) {
+    EuPlan t;
+    t.on = st->plan && st->plan_nnz > 0 && st->plan_maxm > 0;
+    t.A = GeoArgsE{nullptr, nullptr, nullptr, nullptr, 0};
+    t.bytes = 0;
+    if (!t.on) return t;
+    TilePlan tp = tile_plan_view(st->plan, n, st->plan_nnz);
+    int mc = stage_mcap(st->plan_maxm, 1, ctx->stage_cap);
+    t.A = GeoArgsE{tp.tile_m, tp.tile_so, tp.uidx, reinterpret_cast<const float*>(tp.geo), mc};
+    t.bytes = (size_t)mc * 16;
+    return t;
+}
+
+template <int DIM>
+void launch32g(int out, int64_t n, const sph_eulerian_state* st, const EulerK<float>& K, const EuPlan& ep,
+               const float* rin, float* rout, double* rm, double* rp, cudaStream_t s) {
+    dim3 g((unsigned)((n + kTileRows - 1) / kTileRows)), b(kTileRows);
+#define LG(M, O)                                                                    \
+    {                                                                               \
+        auto* f = k_euler32g<DIM, M, O>;                                            \
+        sph_allow_dynamic_smem((const void*)f);                                     \
+        f<<<g, b, ep.bytes, s>>>(rin, rout, st->row_ptr, n, K, ep.A, rm, rp);       \
+    }
+    if (out == OUT_RATES) LG(WANT_BOTH, OUT_RATES)
+    else if (out == OUT_MOM) LG(WANT_MOM, OUT_MOM)
+    else if (out == OUT_MASS) LG(WANT_MASS, OUT_MASS)
+    else LG(WANT_BOTH, OUT_FUSED)
+#undef LG
+}
+
+void dispatch32(const sph_ctx* ctx, int lanes, int out, const sph_eulerian_params* p, const sph_eulerian_state* st,
                 const EulerK<float>& K, const float* rin, float* rout, double* rm, double* rp, cudaStream_t s) {
+    EuPlan ep = eu_plan(ctx, st, p->dom.n);
+    if (ep.on) {
+        if (p->dom.dim == 2) launch32g<2>(out, p->dom.n, st, K, ep, rin, rout, rm, rp, s);
+        else launch32g<3>(out, p->dom.n, st, K, ep, rin, rout, rm, rp, s);
+        return;
+    }
     bool per = p->dom.periodic_mask != 0;
     if (p->dom.dim == 2) {
         if (per) dispatch32p<2, true>(lanes, out, p, st, K, rin, rout, rm, rp, s);
@@ -272,6 +512,57 @@ extern "C" int sph_eulerian_pack(sph_ctx* ctx, const sph_eulerian_params* p, con
         k_pack_rec<3><<<grid_for(n, 256), 256, 0, s>>>(st->pos, st->vol, st->B, st->drho, st->v, n, g, st->rec,
                                                        st->rec_tmp);
     SPH_LAUNCH_CHECK(ctx);
+    return SPH_OK;
+}
+
+// Tile plan of the state's lists and fixed geometry (see sph.h).
+extern "C" int sph_eulerian_plan_bytes(sph_ctx* ctx, const sph_eulerian_params* p, const sph_eulerian_state* st,
+                                       int64_t* bytes_host, void* stream) {
+    if (!ctx || !bytes_host) return SPH_ERR_ARG;
+    int r = check_params(p, st);
+    if (r) return r;
+    int64_t n = p->dom.n, nnz = 0, maxrow = 0;
+    if (n > 0) {
+        r = sph_row_stats(ctx, st->row_ptr, n, as_stream(stream), &nnz, &maxrow);
+        if (r) return r;
+    }
+    *bytes_host = (int64_t)tile_plan_bytes(n, nnz, maxrow, 32);
+    return SPH_OK;
+}
+
+extern "C" int sph_eulerian_plan(sph_ctx* ctx, const sph_eulerian_params* p, sph_eulerian_state* st, void* stream) {
+    if (!ctx) return SPH_ERR_ARG;
+    int r = check_params(p, st);
+    if (r) return r;
+    if (!st->plan || !st->pos || !st->vol || !st->B) return SPH_ERR_ARG;
+    int64_t n = p->dom.n;
+    cudaStream_t s = as_stream(stream);
+    st->plan_nnz = 0;
+    st->plan_maxm = st->plan_maxrow = 0;
+    if (n == 0) return SPH_OK;
+    int64_t nnz = 0, maxrow = 0;
+    r = sph_row_stats(ctx, st->row_ptr, n, s, &nnz, &maxrow);
+    if (r) return r;
+    if (st->plan_bytes < (int64_t)tile_plan_bytes(n, nnz, maxrow, 32)) return SPH_ERR_CAPACITY;
+    if (nnz == 0) return SPH_OK;
+    int32_t mm = 0, mp = 0, mw = 0;
+    r = sph_build_tile_plan(ctx, st->row_ptr, st->col, n, nnz, st->plan, s, &mm, &mp, &mw);
+    if (r) return r;
+    TilePlan tp = tile_plan_view(st->plan, n, nnz);
+    EulerK<double> K = make_consts<double>(p);
+    unsigned nt = (unsigned)tp.ntiles;
+    float* geo = reinterpret_cast<float*>(tp.geo);
+    if (p->dom.dim == 2)
+        k_eu_geo<2><<<nt, kTileRows, 0, s>>>(st->pos, st->vol, st->B, st->row_ptr, st->col, tp.lcol, tp.tile_e,
+                                             tp.tile_so, n, K, geo);
+    else
+        k_eu_geo<3><<<nt, kTileRows, 0, s>>>(st->pos, st->vol, st->B, st->row_ptr, st->col, tp.lcol, tp.tile_e,
+                                             tp.tile_so, n, K, geo);
+    SPH_LAUNCH_CHECK(ctx);
+    SPH_CUDA(ctx, cudaStreamSynchronize(s));
+    st->plan_nnz = nnz;
+    st->plan_maxm = mm;
+    st->plan_maxrow = mw;
     return SPH_OK;
 }
 
@@ -307,7 +598,7 @@ extern "C" int sph_eulerian_rates(sph_ctx* ctx, const sph_eulerian_params* p, co
     } else {
         if (!st->rec) return SPH_ERR_ARG;
         EulerK<float> K = make_consts<float>(p);
-        dispatch32(ctx->lanes[SPH_PASS_EULERIAN], OUT_RATES, p, st, K, st->rec, nullptr, drho_dt, dmom_dt, s);
+        dispatch32(ctx, ctx->lanes[SPH_PASS_EULERIAN], OUT_RATES, p, st, K, st->rec, nullptr, drho_dt, dmom_dt, s);
     }
     SPH_LAUNCH_CHECK(ctx);
     return SPH_OK;
@@ -360,14 +651,14 @@ extern "C" int sph_eulerian_step(sph_ctx* ctx, const sph_eulerian_params* p, con
     for (int k = 0; k < nsteps; ++k) {
         if (p->integrator == SPH_TWO_PASS) {
             int t = sph_timer_begin(ctx, SPH_TIMER_EU_MOMENTUM, s);
-            dispatch32(lanes, OUT_MOM, p, st, K, r0, r1, nullptr, nullptr, s);
+            dispatch32(ctx, lanes, OUT_MOM, p, st, K, r0, r1, nullptr, nullptr, s);
             sph_timer_end(ctx, t, s);
             t = sph_timer_begin(ctx, SPH_TIMER_EU_MASS, s);
-            dispatch32(lanes, OUT_MASS, p, st, K, r1, r0, nullptr, nullptr, s);
+            dispatch32(ctx, lanes, OUT_MASS, p, st, K, r1, r0, nullptr, nullptr, s);
             sph_timer_end(ctx, t, s);
         } else {
             int t = sph_timer_begin(ctx, SPH_TIMER_EU_FUSED, s);
-            dispatch32(lanes, OUT_FUSED, p, st, K, r0, r1, nullptr, nullptr, s);
+            dispatch32(ctx, lanes, OUT_FUSED, p, st, K, r0, r1, nullptr, nullptr, s);
             sph_timer_end(ctx, t, s);
             float* tt = r0; r0 = r1; r1 = tt;
         }

@@ -142,7 +142,7 @@ int sph_row_stats(sph_ctx* ctx, const int64_t* row_ptr, int64_t n, cudaStream_t 
 
 int sph_build_tile_plan(sph_ctx* ctx, const int64_t* row_ptr, const int32_t* col, int64_t n, int64_t nnz,
                         void* buf, cudaStream_t s, int32_t* maxm, int32_t* maxp, int32_t* maxw) {
-    if (((uintptr_t)buf & 15u) || n < 1) return SPH_ERR_ARG;
+    if (((uintptr_t)buf & 31u) || n < 1) return SPH_ERR_ARG;
     TilePlan t = tile_plan_view(buf, n, nnz);
     SPH_CUDA(ctx, cudaMemsetAsync(t.hdr, 0, 64, s));
     k_tile_plan<<<(unsigned)t.ntiles, kPlanThreads, 0, s>>>(row_ptr, col, n, t.hdr, t.tile_m, t.tile_e, t.uidx,

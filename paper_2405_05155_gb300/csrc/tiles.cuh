@@ -14,7 +14,8 @@
 
 constexpr int kTileRows = 128;
 
-// Plan buffer layout (16-byte aligned sections):
+// Plan buffer layout (a 32-byte aligned buffer; 16-byte aligned sections, the
+// entry section 32-byte aligned):
 //   int32  hdr[16]          [0] most distinct columns of a tile, [1] most pairs of a
 //                           tile, [2] longest row
 //   int32  tile_m[ntiles]   distinct columns of tile b
@@ -23,8 +24,9 @@ constexpr int kTileRows = 128;
 //   int32  uidx[nnz]        tile b's distinct columns at uidx[row_ptr[b*kTileRows] + k],
 //                           k < tile_m[b]
 //   uint16 lcol[nnz]        position of col[p] among its tile's distinct columns
-//   float4 geo[ntiles * kTileRows * maxrow]  sliced per-pair entries (filled by the
-//                           method that uses the plan; padding entries are zero)
+//   geo[ntiles * kTileRows * maxrow]  sliced per-pair entries of `ebytes` bytes (a
+//                           multiple of 16), filled by the method that uses the plan;
+//                           padding entries are zero
 struct TilePlan {
     int32_t* hdr;
     int32_t* tile_m;
@@ -38,10 +40,19 @@ struct TilePlan {
 
 static inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-static inline size_t tile_plan_bytes(int64_t n, int64_t nnz, int64_t maxrow) {
+static inline size_t align32(size_t x) { return (x + 31) & ~(size_t)31; }
+
+// Offset of the entry section: 32-byte aligned (entries are read with 256-bit
+// loads; the plan buffer itself must be 32-byte aligned).
+static inline size_t tile_plan_geo_offset(int64_t n, int64_t nnz) {
     int64_t ntiles = (n + kTileRows - 1) / kTileRows;
-    return 64 + 2 * align16((size_t)ntiles * 4) + align16((size_t)(ntiles + 1) * 8) + align16((size_t)nnz * 4) +
-           align16((size_t)nnz * 2) + (size_t)ntiles * kTileRows * (size_t)maxrow * 16;
+    return align32(64 + 2 * align16((size_t)ntiles * 4) + align16((size_t)(ntiles + 1) * 8) +
+                   align16((size_t)nnz * 4) + align16((size_t)nnz * 2));
+}
+
+static inline size_t tile_plan_bytes(int64_t n, int64_t nnz, int64_t maxrow, int ebytes = 16) {
+    int64_t ntiles = (n + kTileRows - 1) / kTileRows;
+    return tile_plan_geo_offset(n, nnz) + (size_t)ntiles * kTileRows * (size_t)maxrow * (size_t)ebytes;
 }
 
 static inline TilePlan tile_plan_view(void* buf, int64_t n, int64_t nnz) {
@@ -59,8 +70,7 @@ static inline TilePlan tile_plan_view(void* buf, int64_t n, int64_t nnz) {
     t.uidx = (int32_t*)b;
     b += align16((size_t)nnz * 4);
     t.lcol = (uint16_t*)b;
-    b += align16((size_t)nnz * 2);
-    t.geo = (float4*)b;
+    t.geo = (float4*)((unsigned char*)buf + tile_plan_geo_offset(n, nnz));
     return t;
 }
 
@@ -69,7 +79,7 @@ int sph_row_stats(sph_ctx* ctx, const int64_t* row_ptr, int64_t n, cudaStream_t 
                   int64_t* maxrow);
 
 // Builds the index part of the plan of (row_ptr, col) into buf (at least
-// tile_plan_bytes(n, nnz, maxrow) bytes, 16-byte aligned): hdr, tile_m, tile_e,
+// tile_plan_bytes(n, nnz, maxrow) bytes, 32-byte aligned): hdr, tile_m, tile_e,
 // tile_so, uidx and lcol.  Returns the three header maxima on the host
 // (synchronises the stream).
 int sph_build_tile_plan(sph_ctx* ctx, const int64_t* row_ptr, const int32_t* col, int64_t n, int64_t nnz,
@@ -86,4 +96,35 @@ static inline int stage_mcap(int32_t maxm, int planes, int cap) {
     if (m > room) m = room;
     if (cap > 0 && m > cap) m = cap;
     return (int)m;
+}
+
+// Row order of the sliced entries: a row's pairs are laid out by their offset
+// r_i - r_j quantised to h/2 (z, y, x major to minor), then by list position, so
+// that at a given position the threads of a warp, neighbouring rows, tend to read
+// neighbours at the same offset.  rfun(k, r) gives the float64 offset of the row's
+// k-th pair.  Returns false (list order kept) for rows longer than kSortCap.
+constexpr int kSortCap = 128;
+
+template <int DIM, typename RF>
+__device__ __forceinline__ bool offset_order(int len, double two_over_h, RF rfun, uint32_t* order) {
+    if (len > kSortCap) return false;
+    for (int k = 0; k < len; ++k) {
+        double r[3];
+        rfun(k, r);
+        uint32_t key = 0;
+#pragma unroll
+        for (int a = DIM - 1; a >= 0; --a) {
+            double q = rint(r[a] * two_over_h);
+            int c = (int)fmin(fmax(q, -8.0), 7.0) + 8;
+            key = key * 16u + (uint32_t)c;
+        }
+        uint32_t v = (key << 20) | (uint32_t)k;
+        int at = k;
+        while (at > 0 && order[at - 1] > v) {
+            order[at] = order[at - 1];
+            --at;
+        }
+        order[at] = v;
+    }
+    return true;
 }

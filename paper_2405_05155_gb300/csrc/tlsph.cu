@@ -562,13 +562,8 @@ struct GeoArgs {
     int mcap;
 };
 
-// Row order of the sliced entries: a row's pairs are laid out by their offset
-// r_i - r_j quantised to h/2 (then by j), so that at a given position the threads of
-// a warp, neighbouring rows, tend to read neighbours at the same offset, which lie
-// close together in their tile's list and so in different shared-memory banks.
-// Rows longer than kSortCap keep the list order.
-constexpr int kSortCap = 128;
-
+// Pair entries of the tile plan: w = grad0 W_ij V0_j in float64, stored float32,
+// with the neighbour's slot, rows laid out by offset (offset_order).
 template <int DIM>
 __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__ r0, const double* __restrict__ V0,
                                                       const int64_t* __restrict__ row_ptr,
@@ -588,28 +583,14 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
 #pragma unroll
     for (int a = 0; a < DIM; ++a) xi[a] = active ? r0[a * n + i] : 0.0;
     uint32_t order[kSortCap];
-    const bool sorted = len <= kSortCap;
-    if (sorted) {
-        const double inv = 2.0 * K.inv_h;
-        for (int k = 0; k < len; ++k) {
+    const bool sorted = offset_order<DIM>(
+        len, 2.0 * K.inv_h,
+        [&](int k, double* rr) {
             double r[DIM], d2;
             pair_r64<DIM>(xi, r0, n, col[b + k], K, r, d2);
-            uint32_t key = 0;
-#pragma unroll
-            for (int a = DIM - 1; a >= 0; --a) {
-                double q = rint(r[a] * inv);
-                int c = (int)fmin(fmax(q, -8.0), 7.0) + 8;
-                key = key * 16u + (uint32_t)c;
-            }
-            uint32_t v = (key << 20) | (uint32_t)k;
-            int at = k;
-            while (at > 0 && order[at - 1] > v) {
-                order[at] = order[at - 1];
-                --at;
-            }
-            order[at] = v;
-        }
-    }
+            for (int a = 0; a < DIM; ++a) rr[a] = r[a];
+        },
+        order);
     for (int k = 0; k < width; ++k) {
         float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (k < len) {
@@ -624,22 +605,6 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
             e.w = __int_as_float((int)lcol[p]);
         }
         out[(int64_t)k * kTileRows] = e;
-    }
-}
-
-// Asks the TMA unit to bring the tile's sliced pair entries (one contiguous range)
-// into L2 while the block stages its neighbours, so that the pair loop's loads hit L2.
-__device__ __forceinline__ void prefetch_tile_entries(const GeoArgs& A, int64_t tile) {
-    if (threadIdx.x == 0) {
-        int64_t e0 = A.tile_so[tile], e1 = A.tile_so[tile + 1];
-        const float4* p = A.geo + e0;
-        int64_t bytes = (e1 - e0) * 16;
-        while (bytes > 0) {
-            uint32_t chunk = (uint32_t)(bytes < (1 << 20) ? bytes : (1 << 20));
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(chunk) : "memory");
-            p += chunk / 16;
-            bytes -= chunk;
-        }
     }
 }
 
@@ -683,7 +648,6 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32g(const float* __restr
     const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
     const int m = A.tile_m[tile];
     const float4* g = A.geo + A.tile_so[tile] + threadIdx.x;
-    prefetch_tile_entries(A, tile);
     F8 a0 = ldg8(RM + W * ii);
     F8 a1 = DIM == 3 ? ldg8(RM + W * ii + 8) : a0;
     float vown[3] = {0.0f, 0.0f, 0.0f};
@@ -720,7 +684,7 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32g(const float* __restr
     if (staged) {
 #pragma unroll 4
         for (int k = 0; k < len; ++k) {
-            float4 e = __ldg(g + (int64_t)k * kTileRows);
+            float4 e = ldg4_stream(g + (int64_t)k * kTileRows);
             int s = min(max(__float_as_int(e.w), 0), max(m - 1, 0));
             float4 c1 = sp[s];
             float4 c2 = DIM == 3 ? sp[mc + s] : c1, c3 = DIM == 3 ? sp[2 * mc + s] : c1;
@@ -728,7 +692,7 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32g(const float* __restr
         }
     } else {
         for (int k = 0; k < len; ++k) {
-            float4 e = __ldg(g + (int64_t)k * kTileRows);
+            float4 e = ldg4_stream(g + (int64_t)k * kTileRows);
             int s = min(max(__float_as_int(e.w), 0), max(m - 1, 0));
             int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
             const float4* rec = reinterpret_cast<const float4*>(RM + W * j);
@@ -768,7 +732,6 @@ __global__ void __launch_bounds__(kTileRows, 8) k_tl_defo32g(const float* __rest
     const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
     const int m = A.tile_m[tile];
     const float4* g = A.geo + A.tile_so[tile] + threadIdx.x;
-    prefetch_tile_entries(A, tile);
     F8 me = ldg8(RD + 8 * ii);
     float b0[NS];
 #pragma unroll
@@ -798,13 +761,13 @@ __global__ void __launch_bounds__(kTileRows, 8) k_tl_defo32g(const float* __rest
     if (staged) {
 #pragma unroll 4
         for (int k = 0; k < len; ++k) {
-            float4 e = __ldg(g + (int64_t)k * kTileRows);
+            float4 e = ldg4_stream(g + (int64_t)k * kTileRows);
             int s = min(max(__float_as_int(e.w), 0), max(m - 1, 0));
             pair(e, sp[s]);
         }
     } else {
         for (int k = 0; k < len; ++k) {
-            float4 e = __ldg(g + (int64_t)k * kTileRows);
+            float4 e = ldg4_stream(g + (int64_t)k * kTileRows);
             int s = min(max(__float_as_int(e.w), 0), max(m - 1, 0));
             int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
             pair(e, __ldg(reinterpret_cast<const float4*>(RD + 8 * j) + 1));

@@ -61,7 +61,7 @@ def test_struct_layouts_match_header():
     # sph_domain: int32, uint32, int64, 2 doubles, 2 x 3 doubles = 80 bytes
     assert ctypes.sizeof(_lib.SphDomain) == 80
     assert ctypes.sizeof(_lib.EulerianParams) == 80 + 5 * 8 + 8
-    assert ctypes.sizeof(_lib.EulerianState) == 11 * 8
+    assert ctypes.sizeof(_lib.EulerianState) == 12 * 8 + 2 * 8 + 2 * 4
     assert ctypes.sizeof(_lib.TLParams) == 80 + 4 * 8 + 8
     assert ctypes.sizeof(_lib.TLState) == 16 * 8 + 2 * 8 + 2 * 4
     assert ctypes.sizeof(_lib.BatchCase) == 96

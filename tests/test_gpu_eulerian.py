@@ -6,6 +6,7 @@ import math
 
 import numpy as np
 import pytest
+import torch
 
 from helpers import cuda, host, odom, rel_l2, rel_max, sample_rows, sorted_by_cells
 from oracle import eulerian as OE
@@ -42,10 +43,17 @@ def _setup(ctx, case, jitter=0.0, seed=0, sort=True):
                 B_h=host(B), prm=prm, d=d)
 
 
-def _sim(ctx, s, case, precision, integrator=api.SPH_TWO_PASS, drho=None, v=None):
+def _sim(ctx, s, case, precision, integrator=api.SPH_TWO_PASS, drho=None, v=None, tiles=True):
     return api.Eulerian(ctx, s["d"], cuda(s["pos"]), cuda(s["vol"]), s["B"], s["rp"], s["col"],
                         s["drho"] if drho is None else drho, s["v"] if v is None else v, case["dt"],
-                        case["rho0"], case["c0"], case["mu"], precision=precision, integrator=integrator)
+                        case["rho0"], case["c0"], case["mu"], precision=precision, integrator=integrator,
+                        tiles=tiles)
+
+
+# float64; float32 on the tile plan (precomputed pair geometry); float32 evaluating
+# the geometry per pair from the records
+VARIANTS = ((api.SPH_FP64, True, 1e-12, rel_max), (api.SPH_FP32_KAHAN, True, 1e-5, rel_l2),
+            (api.SPH_FP32_KAHAN, False, 1e-5, rel_l2))
 
 
 @pytest.mark.parametrize("dim", [2, 3])
@@ -57,8 +65,8 @@ def test_rates_parity(ctx, dim, kappa):
     drho = s["drho"] + 1e-3 * rng.normal(size=s["drho"].shape)
     v = s["v"] + 0.1 * rng.normal(size=s["v"].shape)
     ro, mo = OE.eulerian_rates(s["pos"], s["vol"], drho, v, s["B_h"], s["rp_h"], s["col_h"], s["prm"])
-    for prec, tol, err in ((api.SPH_FP64, 1e-12, rel_max), (api.SPH_FP32_KAHAN, 1e-5, rel_l2)):
-        sim = _sim(ctx, s, case, prec, drho=drho, v=v)
+    for prec, tiles, tol, err in VARIANTS:
+        sim = _sim(ctx, s, case, prec, drho=drho, v=v, tiles=tiles)
         r, m = sim.rates()
         assert err(host(r), ro) < tol, (prec, err(host(r), ro))
         assert err(host(m), mo) < tol, (prec, err(host(m), mo))
@@ -79,11 +87,12 @@ def test_plain_method_tgv2d_200_steps(ctx):
     amp = np.sqrt(np.mean(host(v) ** 2)) / np.sqrt(np.mean(s["v"] ** 2))
     assert abs(amp / math.exp(-case["decay_rate"] * t) - 1.0) < 0.03
     # float32 + Kahan against the float64 oracle, same 200 steps
-    sim32 = _sim(ctx, s, case, api.SPH_FP32_KAHAN)
-    sim32.step(200)
-    dr32, v32 = sim32.fields()
-    assert rel_l2(host(v32), v_o) < 1e-5
-    assert rel_l2(host(dr32), d_o) < 1e-5
+    for tiles in (True, False):
+        sim32 = _sim(ctx, s, case, api.SPH_FP32_KAHAN, tiles=tiles)
+        sim32.step(200)
+        dr32, v32 = sim32.fields()
+        assert rel_l2(host(v32), v_o) < 1e-5, tiles
+        assert rel_l2(host(dr32), d_o) < 1e-5, (tiles, rel_l2(host(dr32), d_o))
 
 
 @pytest.mark.parametrize("integrator", [api.SPH_TWO_PASS, api.SPH_FUSED])
@@ -92,8 +101,8 @@ def test_steps_3d_both_integrators(ctx, integrator):
     s = _setup(ctx, case)
     run = OE.run(s["pos"], s["vol"], s["drho"], s["v"], s["B_h"], s["rp_h"], s["col_h"], s["prm"], 7,
                  fused=integrator == api.SPH_FUSED)
-    for prec, tol, err in ((api.SPH_FP64, 1e-12, rel_max), (api.SPH_FP32_KAHAN, 1e-5, rel_l2)):
-        sim = _sim(ctx, s, case, prec, integrator)
+    for prec, tiles, tol, err in VARIANTS:
+        sim = _sim(ctx, s, case, prec, integrator, tiles=tiles)
         sim.step(7)
         dr, v = sim.fields()
         assert err(host(dr), run[0]) < tol and err(host(v), run[1]) < tol
@@ -108,12 +117,70 @@ def test_launch_shapes_agree(ctx, lanes):
     d_o, v_o = OE.run(s["pos"], s["vol"], s["drho"], s["v"], s["B_h"], s["rp_h"], s["col_h"], s["prm"], 5)
     ctx.set_lanes(api.SPH_PASS_EULERIAN, lanes)
     try:
-        sim = _sim(ctx, s, case, api.SPH_FP32_KAHAN)
-        sim.step(5)
-        dr, v = sim.fields()
-        assert rel_l2(host(dr), d_o) < 1e-5 and rel_l2(host(v), v_o) < 1e-5
+        # the lanes apply to the per-pair form; the planned form (one thread per row) on the
+        # same unsorted input, whose tiles are not compact, must meet the tolerance too
+        for tiles in (False, True):
+            sim = _sim(ctx, s, case, api.SPH_FP32_KAHAN, tiles=tiles)
+            sim.step(5)
+            dr, v = sim.fields()
+            assert rel_l2(host(dr), d_o) < 1e-5 and rel_l2(host(v), v_o) < 1e-5, tiles
     finally:
         ctx.set_lanes(api.SPH_PASS_EULERIAN, 4)
+
+
+def test_plan_geometry_and_forms(ctx):
+    # the plan's pair entries against float64 numpy on the same lists (G, viscous factor,
+    # normal, slot), and the planned pass with its neighbours staged or read from global
+    # memory (stage capacity 16): identical arithmetic, identical results
+    case = inputs.tgv3d(n=12, kappa=1.6)
+    s = _setup(ctx, case, jitter=0.2, seed=5)
+    n = s["pos"].shape[1]
+    rp, col = s["rp_h"], s["col_h"]
+    lens = np.diff(rp)
+    sim = _sim(ctx, s, case, api.SPH_FP32_KAHAN)
+    raw = host(sim.plan)
+    nt = (n + 127) // 128
+    a16 = lambda x: (x + 15) // 16 * 16
+    o = 64 + 2 * a16(4 * nt)
+    tile_so = raw[o:o + 8 * (nt + 1)].view(np.int64)
+    o += a16(8 * (nt + 1)) + a16(4 * col.size) + a16(2 * col.size)
+    o = (o + 31) // 32 * 32
+    geo = raw[o:o + 32 * int(tile_so[-1])].view(np.float32).reshape(-1, 8)
+    prm = s["prm"]
+    dom = prm.dom
+    h = dom.h
+    from oracle import kernels as OKer
+    B = s["B_h"]
+    for i in range(0, n, 37):
+        t, r = i // 128, i % 128
+        ent = geo[tile_so[t] + np.arange(lens[i]) * 128 + r]
+        j = col[rp[i]:rp[i + 1]]
+        dx = ON.min_image(s["pos"][:, i:i + 1] - s["pos"][:, j], dom)
+        d2 = np.sum(dx * dx, axis=0)
+        rr = np.sqrt(d2)
+        gs = OKer.wendland_dwdr(rr, h, 3, None) / rr
+        Bi = OK.sym_to_full(B[:, i:i + 1], 3)[0]
+        Bj = OK.sym_to_full(B[:, j], 3)
+        g = np.einsum("kab,bk->ak", 0.5 * (Bi[None] + Bj), gs * dx)
+        G = -2.0 * s["vol"][j] * g
+        vis = 2.0 * prm.mu * s["vol"][j] * gs * d2 / (d2 + 0.01 * h * h)
+        c = np.clip(np.rint(dx * (2.0 * (1.0 / h))), -8, 7).astype(np.int64) + 8
+        order = np.lexsort((np.arange(j.size), (c[2] * 16 + c[1]) * 16 + c[0]))
+        scale = np.abs(G).max()
+        assert np.allclose(ent[:, :3].T, G[:, order], rtol=1e-6, atol=1e-6 * scale)
+        assert np.allclose(ent[:, 3], vis[order], rtol=1e-6, atol=1e-6 * np.abs(vis).max())
+        assert np.allclose(ent[:, 4:7].T, (-dx / rr)[:, order], rtol=1e-6, atol=1e-7)
+    ref = None
+    for cap in (0, 16):
+        ctx.set_stage_cap(cap)
+        sim = _sim(ctx, s, case, api.SPH_FP32_KAHAN)
+        sim.step(3)
+        got = sim.rec.clone()
+        if ref is None:
+            ref = got
+        else:
+            assert torch.equal(got, ref)
+    ctx.set_stage_cap(0)
 
 
 def test_conservation_on_gpu(ctx):

@@ -101,6 +101,7 @@ def _read_plan(plan, n, nnz, maxrow):
                            ("lcol", 2 * nnz, np.uint16)):
         out[name] = raw[o:o + size].view(dt)
         o += a16(size)
+    o = (o + 31) // 32 * 32
     out["geo"] = raw[o:o + 16 * nt * 128 * maxrow].view(np.float32).reshape(-1, 4)
     return out
 
