@@ -317,6 +317,13 @@ typedef struct {
     uint32_t periodic_mask;
     double h, dt, rho0, c0, mu, eta;
     double len[3];                  /* box lengths (minimum image on periodic axes) */
+    /* optional: the case's tile plan (sph_eulerian_plan of the case alone, with
+     * case-local indices) and the three fields that call wrote.  When every case has
+     * one, the step runs the planned form: one block per tile of any case, the lanes
+     * and block settings unused. */
+    const void* plan;
+    int64_t plan_nnz;
+    int32_t plan_maxm, plan_maxrow;
 } sph_batch_case;
 typedef struct {
     const int64_t* row_ptr;         /* [N+1] */

@@ -57,7 +57,8 @@ class TLState(ctypes.Structure):
 class BatchCase(ctypes.Structure):
     _fields_ = [("offset", c_i64), ("n", c_i64), ("dim", c_i32), ("periodic_mask", ctypes.c_uint32),
                 ("h", c_dbl), ("dt", c_dbl), ("rho0", c_dbl), ("c0", c_dbl), ("mu", c_dbl), ("eta", c_dbl),
-                ("len", c_dbl * 3)]
+                ("len", c_dbl * 3), ("plan", c_vp), ("plan_nnz", c_i64), ("plan_maxm", c_i32),
+                ("plan_maxrow", c_i32)]
 
 
 class BatchState(ctypes.Structure):

@@ -1,5 +1,5 @@
 """Batched Eulerian cases: per-case set-up through the C ABI (cell order, neighbour
-lists, correction matrices, float32 packing), then concatenation into the
+lists, correction matrices, float32 packing, tile plan), then concatenation into the
 sph_batch_state layout and stepping with sph_eulerian_step_batched.
 """
 import ctypes
@@ -11,7 +11,7 @@ from . import api
 
 
 class EulerianBatch:
-    def __init__(self, ctx, cases, integrator=api.SPH_TWO_PASS):
+    def __init__(self, ctx, cases, integrator=api.SPH_TWO_PASS, tiles=True):
         self.ctx = ctx
         dev = ctx.device
         self.cases = cases
@@ -32,7 +32,8 @@ class EulerianBatch:
             B, _, _ = api.kgc(ctx, d, pos, vol, rp, col)
             drho = case["p"][oh] / case["c0"] ** 2
             sim = api.Eulerian(ctx, d, pos, vol, B, rp, col, drho, case["v"][:, oh], case["dt"], case["rho0"],
-                               case["c0"], case["mu"], precision=api.SPH_FP32_KAHAN, integrator=integrator)
+                               case["c0"], case["mu"], precision=api.SPH_FP32_KAHAN, integrator=integrator,
+                               tiles=tiles)
             n = pos.shape[1]
             t = self.table[c]
             t.offset, t.n, t.dim = off, n, d["dim"]
@@ -40,6 +41,11 @@ class EulerianBatch:
             t.h, t.dt, t.rho0, t.c0, t.mu, t.eta = d["h"], case["dt"], case["rho0"], case["c0"], case["mu"], 15.0
             for k in range(3):
                 t.len[k] = d["len"][k] if k < d["dim"] else 1.0
+            if sim.plan is not None:
+                # the case's own tile plan (case-local indices); the batched step runs
+                # its planned form when every case has one
+                t.plan = sim.plan.data_ptr()
+                t.plan_nnz, t.plan_maxm, t.plan_maxrow = sim.st.plan_nnz, sim.st.plan_maxm, sim.st.plan_maxrow
             recs.append(sim.rec)
             rps.append(rp[:-1] + nnz_off)
             cols.append(col + off)

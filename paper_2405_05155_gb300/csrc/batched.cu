@@ -14,6 +14,7 @@
 #include <vector>
 #include "common.cuh"
 #include "euler_core.cuh"
+#include "tiles.cuh"
 
 using namespace euler;
 
@@ -60,6 +61,53 @@ __global__ void __launch_bounds__(256) k_euler32_batched(const float* __restrict
             store_dyn<DIM>(Rout, i, vn, drn);
         }
     }
+}
+
+// Planned form (every case carries a tile plan of its own lists, see
+// sph_eulerian_plan): one block per tile of any case, the tiles of case c being
+// blocks tile0[c] .. tile0[c] + ceil(n_c / kTileRows) - 1 of the launch.
+struct PlanCase {
+    GeoArgsE A;
+    int64_t offset, n, tile0;
+};
+
+template <int DIM, int MODE, int OUT>
+__global__ void __launch_bounds__(kTileRows, 6) k_euler32g_batched(const float* __restrict__ Rin,
+                                                                   float* __restrict__ Rout,
+                                                                   const int64_t* __restrict__ row_ptr, int ncases,
+                                                                   const EulerK<float>* __restrict__ cases,
+                                                                   const PlanCase* __restrict__ plans) {
+    extern __shared__ __align__(16) unsigned char eb_smem[];
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = ncases - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (plans[mid].tile0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const PlanCase C = plans[lo];
+    const EulerK<float> K = cases[lo];
+    euler_tile_g<DIM, MODE, OUT>(Rin, Rout, row_ptr, C.offset, row_ptr[C.offset], C.n, b - C.tile0, K, C.A,
+                                 reinterpret_cast<float4*>(eb_smem), nullptr, nullptr);
+}
+
+// Launch shape of the planned form: the tile count and a stage capacity common to
+// all cases (0 tiles: some case has no plan).
+struct PlanShape {
+    int64_t tiles;
+    int mcap;
+};
+
+PlanShape plan_shape(const sph_ctx* ctx, const sph_batch_case* cases, int ncases) {
+    PlanShape sh{0, 1};
+    int32_t maxm = 0;
+    for (int c = 0; c < ncases; ++c) {
+        if (!cases[c].plan || cases[c].plan_nnz < 1 || cases[c].plan_maxm < 1) return PlanShape{0, 1};
+        maxm = cases[c].plan_maxm > maxm ? cases[c].plan_maxm : maxm;
+        sh.tiles += (cases[c].n + kTileRows - 1) / kTileRows;
+    }
+    sh.mcap = stage_mcap(maxm, 1, ctx->stage_cap);
+    return sh;
 }
 
 EulerK<float> case_consts(const sph_batch_case& c, int dim) {
@@ -134,6 +182,29 @@ void launch_step(const BatchPlan& pl, int dim, const sph_batch_state* st, int64_
     }
 }
 
+void launch_step_planned(int dim, const sph_batch_state* st, int ncases, const EulerK<float>* dK,
+                         const PlanCase* dP, const PlanShape& sh, cudaStream_t s) {
+    dim3 g((unsigned)sh.tiles), b(kTileRows);
+    size_t smem = (size_t)sh.mcap * 16;
+    float* r0 = st->rec;
+    float* r1 = st->rec_tmp;
+    if (dim == 2) {
+        auto* fm = k_euler32g_batched<2, WANT_MOM, OUT_MOM>;
+        auto* fc = k_euler32g_batched<2, WANT_MASS, OUT_MASS>;
+        sph_allow_dynamic_smem((const void*)fm);
+        sph_allow_dynamic_smem((const void*)fc);
+        fm<<<g, b, smem, s>>>(r0, r1, st->row_ptr, ncases, dK, dP);
+        fc<<<g, b, smem, s>>>(r1, r0, st->row_ptr, ncases, dK, dP);
+    } else {
+        auto* fm = k_euler32g_batched<3, WANT_MOM, OUT_MOM>;
+        auto* fc = k_euler32g_batched<3, WANT_MASS, OUT_MASS>;
+        sph_allow_dynamic_smem((const void*)fm);
+        sph_allow_dynamic_smem((const void*)fc);
+        fm<<<g, b, smem, s>>>(r0, r1, st->row_ptr, ncases, dK, dP);
+        fc<<<g, b, smem, s>>>(r1, r0, st->row_ptr, ncases, dK, dP);
+    }
+}
+
 int check_batch(const sph_batch_case* cases, int ncases, const sph_batch_state* st, int64_t* ntotal, int* dim) {
     if (!cases || !st || ncases < 1 || ncases > kMaxCases) return SPH_ERR_ARG;
     if (!st->row_ptr || !st->col || !st->rec || !st->rec_tmp) return SPH_ERR_ARG;
@@ -164,7 +235,7 @@ int check_batch(const sph_batch_case* cases, int ncases, const sph_batch_state* 
 
 // Device copies of the case table and offsets (uploaded when they change).
 int upload_cases(sph_ctx* ctx, const sph_batch_case* cases, int ncases, int dim, EulerK<float>** dK, int64_t** dOff,
-                 cudaStream_t s, bool* changed) {
+                 PlanCase** dP, cudaStream_t s, bool* changed) {
     std::vector<EulerK<float>> K(ncases);
     std::vector<int64_t> off(ncases + 1);
     for (int c = 0; c < ncases; ++c) {
@@ -172,12 +243,25 @@ int upload_cases(sph_ctx* ctx, const sph_batch_case* cases, int ncases, int dim,
         off[c] = cases[c].offset;
     }
     off[ncases] = cases[ncases - 1].offset + cases[ncases - 1].n;
+    PlanShape sh = plan_shape(ctx, cases, ncases);
+    std::vector<PlanCase> P(sh.tiles ? ncases : 0);
+    int64_t t0 = 0;
+    for (size_t c = 0; c < P.size(); ++c) {
+        TilePlan tp = tile_plan_view(const_cast<void*>(cases[c].plan), cases[c].n, cases[c].plan_nnz);
+        P[c].A = GeoArgsE{tp.tile_m, tp.tile_so, tp.uidx, reinterpret_cast<const float*>(tp.geo), sh.mcap};
+        P[c].offset = cases[c].offset;
+        P[c].n = cases[c].n;
+        P[c].tile0 = t0;
+        t0 += (cases[c].n + kTileRows - 1) / kTileRows;
+    }
     // the offsets follow the constants at a 16-byte boundary (int64 loads need 8-byte alignment
     // and sizeof(EulerK<float>) is not a multiple of 8)
-    size_t kb = (sizeof(EulerK<float>) * ncases + 15) & ~size_t(15), ob = sizeof(int64_t) * (ncases + 1);
-    std::vector<unsigned char> blob(kb + ob, 0);
-    std::memcpy(blob.data(), K.data(), kb);
-    std::memcpy(blob.data() + kb, off.data(), ob);
+    size_t kb = (sizeof(EulerK<float>) * ncases + 15) & ~size_t(15);
+    size_t ob = (sizeof(int64_t) * (ncases + 1) + 15) & ~size_t(15), pb = sizeof(PlanCase) * P.size();
+    std::vector<unsigned char> blob(kb + ob + pb, 0);
+    std::memcpy(blob.data(), K.data(), sizeof(EulerK<float>) * ncases);
+    std::memcpy(blob.data() + kb, off.data(), sizeof(int64_t) * (ncases + 1));
+    if (pb) std::memcpy(blob.data() + kb + ob, P.data(), pb);
     *changed = blob != ctx->batch_blob;
     int st = SPH_OK;
     unsigned char* d = (unsigned char*)sph_scratch(ctx, S_BATCH, blob.size() + 256, &st);
@@ -190,6 +274,7 @@ int upload_cases(sph_ctx* ctx, const sph_batch_case* cases, int ncases, int dim,
     }
     *dK = reinterpret_cast<EulerK<float>*>(d);
     *dOff = reinterpret_cast<int64_t*>(d + kb);
+    *dP = pb ? reinterpret_cast<PlanCase*>(d + kb + ob) : nullptr;
     return SPH_OK;
 }
 
@@ -229,19 +314,22 @@ BatchPlan make_plan(sph_ctx* ctx, int lanes, int block, int dim, int64_t ntotal)
 }
 
 int run_steps(sph_ctx* ctx, const BatchPlan& pl, int dim, const sph_batch_state* st, int64_t ntotal, int ncases,
-              const EulerK<float>* dK, const int64_t* dOff, int nsteps, bool tables_changed, cudaStream_t s) {
+              const EulerK<float>* dK, const int64_t* dOff, const PlanCase* dP, const PlanShape& sh, int nsteps,
+              bool tables_changed, cudaStream_t s) {
     // (re)capture one step as a graph when anything it depends on changed
     BatchGraphKey key;
     std::memset(&key, 0, sizeof(key));
     key.row_ptr = st->row_ptr; key.col = st->col; key.rec = st->rec; key.rec_tmp = st->rec_tmp;
     key.ntotal = ntotal; key.ncases = ncases; key.lanes = pl.lanes; key.block = pl.block; key.grid = pl.grid;
     key.dK = dK; key.dim = dim;
+    if (dP) { key.lanes = 0; key.block = kTileRows; key.grid = sh.mcap; }
     if (!ctx->batch_graph || tables_changed || std::memcmp(&key, &ctx->batch_key, sizeof(key)) != 0) {
         if (ctx->batch_graph) { cudaGraphExecDestroy(ctx->batch_graph); ctx->batch_graph = nullptr; }
         if (!ctx->capture_stream) SPH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
         SPH_CUDA(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        launch_step(pl, dim, st, ntotal, ncases, dK, dOff, ctx->capture_stream);
+        if (dP) launch_step_planned(dim, st, ncases, dK, dP, sh, ctx->capture_stream);
+        else launch_step(pl, dim, st, ntotal, ncases, dK, dOff, ctx->capture_stream);
         cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &g);
         if (e != cudaSuccess) { ctx->last_cuda_error = (int)e; return SPH_ERR_CUDA; }
         e = cudaGraphInstantiate(&ctx->batch_graph, g, 0);
@@ -270,11 +358,13 @@ extern "C" int sph_eulerian_step_batched(sph_ctx* ctx, const sph_batch_case* cas
     cudaStream_t s = as_stream(stream);
     EulerK<float>* dK = nullptr;
     int64_t* dOff = nullptr;
+    PlanCase* dP = nullptr;
     bool changed = false;
-    r = upload_cases(ctx, cases, ncases, dim, &dK, &dOff, s, &changed);
+    r = upload_cases(ctx, cases, ncases, dim, &dK, &dOff, &dP, s, &changed);
     if (r) return r;
+    PlanShape sh = plan_shape(ctx, cases, ncases);
     BatchPlan pl = make_plan(ctx, ctx->lanes[SPH_PASS_BATCHED], ctx->batch_block, dim, ntotal);
-    return run_steps(ctx, pl, dim, st, ntotal, ncases, dK, dOff, nsteps, changed, s);
+    return run_steps(ctx, pl, dim, st, ntotal, ncases, dK, dOff, dP, sh, nsteps, changed, s);
 }
 
 extern "C" int sph_autotune_batched(sph_ctx* ctx, const sph_batch_case* cases, int ncases, const sph_batch_state* st,
@@ -288,9 +378,11 @@ extern "C" int sph_autotune_batched(sph_ctx* ctx, const sph_batch_case* cases, i
     cudaStream_t s = as_stream(stream);
     EulerK<float>* dK = nullptr;
     int64_t* dOff = nullptr;
+    PlanCase* dP = nullptr;
     bool changed = false;
-    r = upload_cases(ctx, cases, ncases, dim, &dK, &dOff, s, &changed);
+    r = upload_cases(ctx, cases, ncases, dim, &dK, &dOff, &dP, s, &changed);
     if (r) return r;
+    PlanShape sh = plan_shape(ctx, cases, ncases);
     // the trial steps advance the caller's state: it is saved first and restored after every variant
     int64_t qbytes = ntotal * kRecWords * 4;
     void* save = sph_scratch(ctx, S_MISC3, (size_t)qbytes, &r);
@@ -306,11 +398,11 @@ extern "C" int sph_autotune_batched(sph_ctx* ctx, const sph_batch_case* cases, i
     for (int li = 0; li < 4; ++li)
         for (int bi = 0; bi < 2; ++bi) {
             BatchPlan pl = make_plan(ctx, lanes_set[li], block_set[bi], dim, ntotal);
-            r = run_steps(ctx, pl, dim, st, ntotal, ncases, dK, dOff, 1, changed, s);   // warm + capture
+            r = run_steps(ctx, pl, dim, st, ntotal, ncases, dK, dOff, dP, sh, 1, changed, s);   // warm + capture
             if (r) return r;
             changed = false;
             SPH_CUDA(ctx, cudaEventRecord(e0, s));
-            r = run_steps(ctx, pl, dim, st, ntotal, ncases, dK, dOff, trial_steps, false, s);
+            r = run_steps(ctx, pl, dim, st, ntotal, ncases, dK, dOff, dP, sh, trial_steps, false, s);
             if (r) return r;
             SPH_CUDA(ctx, cudaEventRecord(e1, s));
             SPH_CUDA(ctx, cudaEventSynchronize(e1));

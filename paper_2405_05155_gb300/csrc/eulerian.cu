@@ -122,14 +122,6 @@ __global__ void __launch_bounds__(256) k_euler32(const float* __restrict__ Rin, 
 // each rounded once to float32.  A planned pass then needs only the neighbour's
 // (v_j, drho_j), which a block stages per tile in shared memory, and evaluates the
 // acoustic Riemann flux (Eqs. 25-26) pair by pair.
-struct GeoArgsE {
-    const int32_t* tile_m;
-    const int64_t* tile_so;
-    const int32_t* uidx;
-    const float* geo;   // 8 floats per entry
-    int mcap;
-};
-
 template <int DIM>
 __global__ void __launch_bounds__(kTileRows) k_eu_geo(const double* __restrict__ pos, const double* __restrict__ vol,
                                                       const double* __restrict__ B,
@@ -202,47 +194,6 @@ __global__ void __launch_bounds__(kTileRows) k_eu_geo(const double* __restrict__
     }
 }
 
-// One pair of a planned pass from its entry and the neighbour's (v_j, drho_j).
-// Every operation is written out (fused multiply-adds explicit, products and sums
-// rounded on their own), so the result does not depend on where it is inlined.
-template <int DIM, int MODE>
-__device__ __forceinline__ void euler_pair_geo(const F8& e, float4 dj, const float* vi, float dri,
-                                               const EulerK<float>& K, Kahan<float>& am, Kahan<float>* ap) {
-    const float G[3] = {e.v[0], e.v[1], e.v[2]};
-    const float nrm[3] = {e.v[4], e.v[5], e.v[6]};
-    const float vj[3] = {dj.x, dj.y, dj.z};
-    const float drj = dj.w;
-    float ul = __fmul_rn(vi[0], nrm[0]), ur = __fmul_rn(vj[0], nrm[0]);
-#pragma unroll
-    for (int a = 1; a < DIM; ++a) {
-        ul = fmaf(vi[a], nrm[a], ul);
-        ur = fmaf(vj[a], nrm[a], ur);
-    }
-    const float pi = __fmul_rn(K.c0sq, dri), pj = __fmul_rn(K.c0sq, drj);
-    const float rho_bar = fmaf(0.5f, __fadd_rn(dri, drj), K.rho0);
-    const float du = __fsub_rn(ul, ur);
-    const float beta = fminf(__fmul_rn(K.eta, fmaxf(__fmul_rn(du, K.inv_c0), 0.0f)), 1.0f);
-    const float ubar = __fmul_rn(0.5f, __fadd_rn(ul, ur));
-    const float rc = __fmul_rn(rho_bar, K.c0);
-    const float hb = __fmul_rn(0.5f, beta);
-    const float ustar = fmaf(__fmul_rn(hb, beta), __fdiv_rn(__fsub_rn(pi, pj), rc), ubar);   // Eq. 25
-    const float pstar = fmaf(__fmul_rn(hb, rc), du, __fmul_rn(0.5f, __fadd_rn(pi, pj)));
-    const float dus = __fsub_rn(ustar, ubar);
-    float vs[DIM];
-    float vG = 0.0f;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-        vs[a] = fmaf(dus, nrm[a], __fmul_rn(0.5f, __fadd_rn(vi[a], vj[a])));
-        vG = a == 0 ? __fmul_rn(vs[0], G[0]) : fmaf(vs[a], G[a], vG);
-    }
-    if (MODE & WANT_MASS) am.add(__fmul_rn(rho_bar, vG));
-    if (MODE & WANT_MOM) {
-#pragma unroll
-        for (int a = 0; a < DIM; ++a)
-            ap[a].add(fmaf(e.v[3], __fsub_rn(vi[a], vj[a]), fmaf(pstar, G[a], __fmul_rn(__fmul_rn(rho_bar, vs[a]), vG))));
-    }
-}
-
 template <int DIM, int MODE, int OUT>
 __global__ void __launch_bounds__(kTileRows, 6) k_euler32g(const float* __restrict__ Rin, float* __restrict__ Rout,
                                                            const int64_t* __restrict__ row_ptr, int64_t n,
@@ -250,63 +201,8 @@ __global__ void __launch_bounds__(kTileRows, 6) k_euler32g(const float* __restri
                                                            double* __restrict__ rate_mass,
                                                            double* __restrict__ rate_mom) {
     extern __shared__ __align__(16) unsigned char eu_smem[];
-    float4* sp = reinterpret_cast<float4*>(eu_smem);
-    const int64_t tile = blockIdx.x;
-    const int64_t i0 = tile * kTileRows;
-    const int64_t i = i0 + threadIdx.x;
-    const bool active = i < n;
-    const int64_t ii = active ? i : i0;
-    const int64_t P0 = row_ptr[i0];
-    const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
-    const int m = A.tile_m[tile];
-    const int64_t so = A.tile_so[tile];
-    const float4 own = __ldg(reinterpret_cast<const float4*>(Rin + kRecWords * ii) + 3);
-    const bool staged = m <= A.mcap;
-    if (staged) {
-        for (int s = threadIdx.x; s < m; s += blockDim.x) {
-            int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
-            sp[s] = __ldg(reinterpret_cast<const float4*>(Rin + kRecWords * j) + 3);
-        }
-    }
-    __syncthreads();
-    const float vi[3] = {own.x, own.y, own.z};
-    const float dri = own.w;
-    Kahan<float> am;
-    Kahan<float> ap[DIM];
-    am.init();
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) ap[a].init();
-    const float* g = A.geo + 8 * (so + threadIdx.x);
-    const int smax = max(m - 1, 0);
-    if (staged) {
-#pragma unroll 4
-        for (int k = 0; k < len; ++k) {
-            F8 e = ldg8_stream(g + (int64_t)8 * k * kTileRows);
-            int s = min(max(__float_as_int(e.v[7]), 0), smax);
-            euler_pair_geo<DIM, MODE>(e, sp[s], vi, dri, K, am, ap);
-        }
-    } else {
-        for (int k = 0; k < len; ++k) {
-            F8 e = ldg8_stream(g + (int64_t)8 * k * kTileRows);
-            int s = min(max(__float_as_int(e.v[7]), 0), smax);
-            int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
-            euler_pair_geo<DIM, MODE>(e, __ldg(reinterpret_cast<const float4*>(Rin + kRecWords * j) + 3), vi, dri,
-                                      K, am, ap);
-        }
-    }
-    if (!active) return;
-    float rm = am.value(), rp[DIM];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) rp[a] = ap[a].value();
-    if (OUT == OUT_RATES) {
-        if (MODE & WANT_MASS) rate_mass[i] = (double)rm;
-        if (MODE & WANT_MOM)
-            for (int a = 0; a < DIM; ++a) rate_mom[a * n + i] = (double)rp[a];
-        return;
-    }
-    float vn[DIM], drn;
-    euler_update32<DIM, OUT>(vi, dri, rm, rp, K, vn, drn);
-    store_dyn<DIM>(Rout, i, vn, drn);
+    euler_tile_g<DIM, MODE, OUT>(Rin, Rout, row_ptr, 0, 0, n, blockIdx.x, K, A, reinterpret_cast<float4*>(eu_smem),
+                                 rate_mass, rate_mom);
 }
 
 // ---------------------------------------------------------------- pack / unpack

@@ -64,6 +64,6 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.EulerianState) == 12 * 8 + 2 * 8 + 2 * 4
     assert ctypes.sizeof(_lib.TLParams) == 80 + 4 * 8 + 8
     assert ctypes.sizeof(_lib.TLState) == 16 * 8 + 2 * 8 + 2 * 4
-    assert ctypes.sizeof(_lib.BatchCase) == 96
+    assert ctypes.sizeof(_lib.BatchCase) == 96 + 8 + 8 + 2 * 4
     assert ctypes.sizeof(_lib.BatchState) == 4 * 8
     assert ctypes.sizeof(_lib.RelaxParams) == 80 + 3 * 8 + 16 + 64 * 8

@@ -25,12 +25,14 @@ def _small_cases():
     return inputs.batched_tgv2d(seed=3, ncases=7, scale=0.06)
 
 
-def test_batched_matches_single_case_runs(ctx):
+@pytest.mark.parametrize("tiles", [True, False])
+def test_batched_matches_single_case_runs(ctx, tiles):
+    # planned form (every case with a tile plan) or the persistent per-pair form
     cases = _small_cases()
     for lanes in (1, 4):
         ctx.set_lanes(api.SPH_PASS_EULERIAN, lanes)
         ctx.set_lanes(api.SPH_PASS_BATCHED, lanes)
-        b = batch.EulerianBatch(ctx, cases)
+        b = batch.EulerianBatch(ctx, cases, tiles=tiles)
         b.step(6)
         for c, sim in enumerate(b.sims):
             # the single-case path on the same initial packed state
@@ -40,15 +42,20 @@ def test_batched_matches_single_case_runs(ctx):
             single = sim.rec.clone()
             t = b.table[c]
             got = b.rec[16 * t.offset: 16 * (t.offset + t.n)]
-            # same arithmetic per particle; the two kernels may contract a multiply-add differently
-            assert rel_l2(host(got).astype(np.float64), host(single).astype(np.float64)) < 1e-6, c
+            if tiles:
+                # both run the planned tile body with explicit arithmetic: identical results
+                assert torch.equal(got, single), c
+            else:
+                # same arithmetic per particle; the two kernels may contract a multiply-add differently
+                assert rel_l2(host(got).astype(np.float64), host(single).astype(np.float64)) < 1e-6, c
     ctx.set_lanes(api.SPH_PASS_EULERIAN, 4)
     ctx.set_lanes(api.SPH_PASS_BATCHED, 4)
 
 
-def test_batched_against_oracle_and_autotune(ctx):
+@pytest.mark.parametrize("tiles", [True, False])
+def test_batched_against_oracle_and_autotune(ctx, tiles):
     cases = _small_cases()
-    b = batch.EulerianBatch(ctx, cases)
+    b = batch.EulerianBatch(ctx, cases, tiles=tiles)
     lanes, block, ms = b.autotune(trial_steps=3)
     assert lanes in (1, 2, 4, 8) and block in (128, 256) and ms > 0
     assert ctx.get_lanes(api.SPH_PASS_BATCHED) == lanes
