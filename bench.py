@@ -373,7 +373,12 @@ def _bench_mlp(api, inputs, ctx, peak_tflops):
     rows = feats.shape[0]
     params = torch.tensor(inputs.mlp_init(0), dtype=torch.float32, device=ctx.device)
     api.mlp_forward(ctx, params, feats)
-    ms = _event_ms(lambda: [api.mlp_forward(ctx, params, feats) for _ in range(5)]) / 5
+    ms_mma = _event_ms(lambda: [api.mlp_forward(ctx, params, feats) for _ in range(5)]) / 5
+    api.mlp_forward_tc(ctx, params, feats)
+    ms = _event_ms(lambda: [api.mlp_forward_tc(ctx, params, feats, check=False) for _ in range(20)]) / 20
+    y_tc = api.mlp_forward_tc(ctx, params, feats)
+    y_mma = api.mlp_forward(ctx, params, feats)
+    diff = float(torch.linalg.norm(y_tc - y_mma) / torch.linalg.norm(y_mma))
     flops = 2.0 * rows * (128 * 128 * 3 + 128 * 3)
     tr = api.MLPTrainer(ctx, inputs.mlp_init(0))
     x = feats[:4096].contiguous()
@@ -381,11 +386,13 @@ def _bench_mlp(api, inputs, ctx, peak_tflops):
     tr.step(x, t)
     ms_tr = _event_ms(lambda: [tr.step(x, t) for _ in range(20)]) / 20
     tflops = flops / (ms * 1e-3) / 1e12
-    return {"workload": "128-128-128-128-3 GELU MLP, BF16 mma.sync tensor cores, FP32 accumulate; forward over the "
-                        "features of a dp=1/128 body; Adam step at batch 4096",
-            "rows": rows, "forward_ms": ms, "forward_tflops": tflops, "train_step_ms_batch4096": ms_tr,
-            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": tflops / peak_tflops}}
+    return {"workload": "128-128-128-128-3 GELU MLP, BF16 operands, FP32 accumulate; fused forward on tcgen05 "
+                        "(TMEM accumulators) over the features of a dp=1/128 body; mma.sync forward and an Adam "
+                        "step at batch 4096 (training path)",
+            "rows": rows, "forward_ms": ms, "forward_tflops": tflops, "forward_mma_sync_ms": ms_mma,
+            "rel_l2_tcgen05_vs_mma_sync": diff, "train_step_ms_batch4096": ms_tr,
+            "roofline": {"bound": "tensor", "kernel": "k_mlp_forward_tc", "achieved": tflops, "peak": peak_tflops,
+                         "unit": "TFLOP/s", "frac": tflops / peak_tflops}}
 
 
 # --------------------------------------------------------------------------- arms
@@ -420,6 +427,17 @@ def run_gpu(args):
     ctx = api.Context(torch.cuda.current_device())
     K, W = args.steps, args.warmup
 
+    if args.profile == "mlp":
+        g = torch.Generator(device="cpu").manual_seed(0)
+        feats = (0.8 * torch.randn((args.mlp_rows, 128), generator=g)).to(ctx.device)
+        feats[:, 97:] = 0.0
+        params = torch.tensor(inputs.mlp_init(0), dtype=torch.float32, device=ctx.device)
+        for _ in range(W + K):
+            api.mlp_forward_tc(ctx, params, feats, check=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "mlp", "rows": args.mlp_rows, "launches": W + K}))
+        ctx.close()
+        return 0
     if args.profile == "eu3d":
         case = inputs.tgv3d(n=args.eu_n, kappa=args.kappa)
         sim, nnz, _ = _eulerian_case(api, ctx, case, api.SPH_FP32_KAHAN, tiles=not args.no_tiles)
@@ -591,9 +609,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--profile", choices=["fp32", "fp64", "eu3d"], default=None,
+    ap.add_argument("--profile", choices=["fp32", "fp64", "eu3d", "mlp"], default=None,
                     help="run only one workload (setup + warmup + steps) for ncu captures: the plate "
-                         "(fp32 or fp64) or the 3D Taylor-Green vortex of side --eu-n (eu3d, float32)")
+                         "(fp32 or fp64), the 3D Taylor-Green vortex of side --eu-n (eu3d, float32) or the "
+                         "fused MLP forward over --mlp-rows rows (mlp)")
+    ap.add_argument("--mlp-rows", type=int, default=262144, help="rows of the --profile mlp workload")
     ap.add_argument("--eu-n", type=int, default=64, help="lattice side of the --profile eu3d workload")
     ap.add_argument("--no-tiles", action="store_true", help="--profile: without tile plans (per-pair geometry)")
     ap.add_argument("--kappa", type=float, default=1.6)

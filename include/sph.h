@@ -484,6 +484,19 @@ int sph_mlp_features(sph_ctx* ctx, const sph_relax_params* prm, const double* po
 /* out [n][3] = network(feats [n][128]) */
 int sph_mlp_forward(sph_ctx* ctx, const float* params, const float* feats, float* out,
                     int64_t n, void* stream);
+/* The same forward, fused in one launch on the fifth-generation tensor cores
+ * (tcgen05.mma, bfloat16 operands in shared memory, float32 accumulation in tensor
+ * memory): the activations stay on chip, global memory sees feats (float32
+ * [n][128], 16-byte aligned) once and out [n][3].  Numerically the same network
+ * as sph_mlp_forward (bfloat16 operands, float32 accumulation, GELU in float32);
+ * the two differ by rounding order only.  A bounded wait that expires sets the
+ * timeout flag, reported by sph_take_status. */
+int sph_mlp_forward_tc(sph_ctx* ctx, const float* params, const float* feats, float* out,
+                       int64_t n, void* stream);
+/* Reads and clears the context's device timeout flag: SPH_ERR_TIMEOUT when a bounded
+ * wait of a kernel expired since the last read (the results of that launch are not
+ * valid), else SPH_OK.  Synchronises the stream. */
+int sph_take_status(sph_ctx* ctx, void* stream);
 /* gradient (float32 [SPH_MLP_NPARAM]) of the loss over a batch of b rows against
  * target [b][3]; *loss_host (nullable; if set the call synchronises) gets the loss */
 int sph_mlp_grad(sph_ctx* ctx, const float* params, const float* feats, const float* target,
@@ -492,8 +505,9 @@ int sph_mlp_grad(sph_ctx* ctx, const float* params, const float* feats, const fl
 int sph_mlp_train_step(sph_ctx* ctx, float* params, float* adam_m, float* adam_v,
                        int64_t step, double lr, const float* feats, const float* target,
                        int64_t b, double* loss_host, void* stream);
-/* proposal move: features at pos, forward, pos += h * out, then particles with
- * phi > -dp/2 are moved along grad phi to phi = -dp/2 */
+/* proposal move: features at pos, forward (the fused tensor-core form of
+ * sph_mlp_forward_tc), pos += h * out, then particles with phi > -dp/2 are moved
+ * along grad phi to phi = -dp/2 */
 int sph_relax_propose(sph_ctx* ctx, const sph_relax_params* prm, const float* params,
                       double* pos, void* stream);
 

@@ -101,6 +101,8 @@ _SIGNATURES = {
     "sph_relax_residual": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, _P(c_dbl), c_vp]),
     "sph_mlp_features": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, c_vp]),
     "sph_mlp_forward": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp]),
+    "sph_mlp_forward_tc": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp]),
+    "sph_take_status": (ctypes.c_int, [c_vp, c_vp]),
     "sph_mlp_grad": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_vp, _P(c_dbl), c_vp]),
     "sph_mlp_train_step": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_vp, c_vp, c_i64, _P(c_dbl),
                                           c_vp]),

@@ -345,6 +345,17 @@ def mlp_forward(ctx, params, feats):
     return out
 
 
+def mlp_forward_tc(ctx, params, feats, check=True):
+    """The fused forward on tcgen05 tensor cores (one launch); check=True reads back the
+    device status (a bounded wait that expired raises)."""
+    out = torch.empty((feats.shape[0], 3), dtype=torch.float32, device=feats.device)
+    L.check("sph_mlp_forward_tc", ctx.lib.sph_mlp_forward_tc(ctx.h, _p(params), _p(feats), _p(out), feats.shape[0],
+                                                              _stream()), ctx.h)
+    if check:
+        L.check("sph_take_status", ctx.lib.sph_take_status(ctx.h, _stream()), ctx.h)
+    return out
+
+
 def mlp_grad(ctx, params, feats, target, with_loss=True):
     grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=feats.device)
     loss = ctypes.c_double(float("nan"))

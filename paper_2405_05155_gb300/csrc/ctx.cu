@@ -396,3 +396,9 @@ void sph_allow_dynamic_smem(const void* kernel) {
     if (done.insert({kernel, dev}).second)
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
+
+extern "C" int sph_take_status(sph_ctx* ctx, void* stream) {
+    if (!ctx) return SPH_ERR_ARG;
+    ctx->waits_pending = false;
+    return sph_take_timeout(ctx, as_stream(stream));
+}

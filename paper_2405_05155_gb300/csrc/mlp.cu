@@ -492,7 +492,8 @@ extern "C" int sph_relax_propose(sph_ctx* ctx, const sph_relax_params* p, const 
     FeatSpheres S = feat_spheres(p);
     k_features<<<grid_for(n, 128), 128, 0, s>>>(pos, n, rp, cl, S, 1.0 / p->dom.h, feats);
     SPH_LAUNCH_CHECK(ctx);
-    st = sph_mlp_forward(ctx, params, feats, out, n, stream);
+    // the fused tensor-core forward (same network as sph_mlp_forward)
+    st = sph_mlp_forward_tc(ctx, params, feats, out, n, stream);
     if (st) return st;
     k_apply_proposal<<<grid_for(n, 256), 256, 0, s>>>(pos, n, out, S, p->dom.h, p->dp);
     SPH_LAUNCH_CHECK(ctx);

@@ -53,6 +53,23 @@ def test_forward_parity(ctx, rows):
     assert rel_l2(y, y_o) < 1e-2
 
 
+@pytest.mark.parametrize("rows", [1, 127, 128, 129, 5000, 40000])
+def test_forward_tcgen05_parity(ctx, rows):
+    # fused tcgen05 forward: within the bfloat16 tolerance of the float64 oracle and
+    # close to the mma.sync forward (same operands, different rounding order); ragged
+    # last tiles and more tiles than SMs
+    flat = inputs.mlp_init(1)
+    flat[OM.N_PARAM - 3:] = [0.01, -0.02, 0.03]
+    X, _ = _batch(3, rows)
+    y_o, _ = OM.forward(flat, X)
+    P, Xd = cuda(flat, torch.float32), cuda(X, torch.float32)
+    y = host(api.mlp_forward_tc(ctx, P, Xd))
+    assert np.all(np.isfinite(y))
+    assert rel_l2(y, y_o) < 1e-2, rel_l2(y, y_o)
+    y_mma = host(api.mlp_forward(ctx, P, Xd))
+    assert rel_l2(y, y_mma) < 5e-3
+
+
 def test_gradient_parity_per_block(ctx):
     flat = inputs.mlp_init(5)
     X, T = _batch(6, 4096)
