@@ -462,10 +462,13 @@ def run_gpu(args):
 
     # headline: truncated kernel (1.6h), float32 + Kahan, per-kernel timing on
     s16 = _setup_plate(api, inputs, ctx, 1.6)
-    sol = _solid(api, ctx, s16, api.SPH_FP32_KAHAN)
+    sol = _solid(api, ctx, s16, api.SPH_FP32_KAHAN, tiles=not args.no_tiles)
+    planned = sol.plan is not None
     if args.lanes:
         ctx.set_lanes(api.SPH_PASS_TLSPH, args.lanes)
         lanes16 = args.lanes
+    elif planned:
+        lanes16 = 1          # the planned passes run one thread per row
     else:
         lanes16, _ = sol.autotune(10)
     sol.step(W)
@@ -495,7 +498,7 @@ def run_gpu(args):
     # standard kernel (2h), same precision
     s20 = _setup_plate(api, inputs, ctx, 2.0)
     sol20 = _solid(api, ctx, s20, api.SPH_FP32_KAHAN)
-    lanes20 = args.lanes or sol20.autotune(10)[0]
+    lanes20 = args.lanes or (1 if sol20.plan is not None else sol20.autotune(10)[0])
     ctx.set_lanes(api.SPH_PASS_TLSPH, lanes20)
     ms20, _ = _time_steps(ctx, sol20, K, W, world)
     _, v20, H20 = sol20.fields()
@@ -514,7 +517,10 @@ def run_gpu(args):
     else:
         peak, peak_src = 6800.0, "fallback"
     achieved = dominant[1] / (dominant[2] * 1e-3) / 1e9
-    traffic = args.traffic
+    # ncu DRAM bytes (read + write) per launch of each planned TL pass, measured on this
+    # workload for the current kernels (profiles/tl_pair_passes_plate816k_full.md)
+    ncu_traffic = {"tl_momentum_pass": 446.2e6, "tl_deformation_pass": 508.0e6}
+    traffic = args.traffic if args.traffic is not None else ncu_traffic.get(dominant[0])
 
     # end to end through the C ABI with host buffers: per step, copy the float64
     # state (x, v, F - I) from pinned host memory, pack, step, unpack, copy back
@@ -571,7 +577,9 @@ def run_gpu(args):
                        "l2_policy": "inputs larger than L2 (working set %.0f MB > 129 MB L2), no flush" % (ws / 2 ** 20),
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "lanes_per_particle": lanes16, "lanes_per_particle_2h": lanes20,
-                       "launch_shape": "autotuned (sph_autotune_tlsph)" if not args.lanes else "fixed"},
+                       "launch_shape": ("tile plan: 128-row tiles, one thread per row, float64-precomputed "
+                                        "pair factors, neighbours staged in shared memory") if planned else
+                                       ("autotuned lanes (sph_autotune_tlsph)" if not args.lanes else "fixed lanes")},
             "kappa_2.0": {"ms_per_step": ms20 / K, "pair_interactions_per_s": 2 * s20["nnz"] * K / (ms20 * 1e-3),
                           "nnz": s20["nnz"]},
             "alpha_TW_over_SW": ms_step / (ms20 / K),
