@@ -320,6 +320,11 @@ __global__ void k_relax_pack_lo(const double* __restrict__ pos, const double* __
                         (float)(pos[2 * n + j] - (double)h.z), (float)vol[j]);
 }
 
+// Cells of edge >= rc / R: a particle's neighbours lie in the cells within R of its
+// own along every axis.  A cell whose box is farther than the screening threshold
+// is skipped; the outermost cells extend to infinity outwards (clamped particles
+// outside the box lie in them).
+template <int R>
 __global__ void __launch_bounds__(256) k_relax_acc_cells(const float4* __restrict__ p32, const float4* __restrict__ lo,
                                                         const int32_t* __restrict__ start, CellGrid g,
                                                         const unsigned* __restrict__ absmax, double rc2,
@@ -339,17 +344,33 @@ __global__ void __launch_bounds__(256) k_relax_acc_cells(const float4* __restric
         int ci[3];
         for (int a = 0; a < 3; ++a) ci[a] = nb::cell_coord(xi[a], a, g);
         nb::Band band = nb::make_band(absmax, 0.0, rc2, 3);
-        int lx[3], ly[3], lz[3];
-        int mx = nb::axis_cells(ci[0], 0, g, lx);
-        int my = nb::axis_cells(ci[1], 1, g, ly);
-        int mz = nb::axis_cells(ci[2], 2, g, lz);
+        const float thr = band.hi * 1.0001f;
+        // squared distance from the particle to the cell slabs c + d, d in [-R, R], per axis
+        float sd[3][2 * R + 1];
+        int clo[3], chi[3];
+        for (int a = 0; a < 3; ++a) {
+            clo[a] = max(ci[a] - R, 0);
+            chi[a] = min(ci[a] + R, g.n[a] - 1);
+            for (int d = -R; d <= R; ++d) {
+                int c = ci[a] + d;
+                float x = xh[a];
+                float b0 = (float)(g.lo[a] + c * g.size[a]), b1 = (float)(g.lo[a] + (c + 1) * g.size[a]);
+                float gap = 0.0f;
+                if (c > 0 && x < b0) gap = b0 - x;
+                if (c < g.n[a] - 1 && x > b1) gap = x - b1;
+                sd[a][d + R] = gap * gap;
+            }
+        }
         Kahan<float> s[3];
         for (int a = 0; a < 3; ++a) s[a].init();
-        for (int az = 0; az < mz; ++az)
-            for (int ay = 0; ay < my; ++ay) {
-                int rowbase = (lz[az] * g.n[1] + ly[ay]) * g.n[0];
-                for (int ax = 0; ax < mx; ++ax) {
-                    int c = rowbase + lx[ax];
+        for (int cz = clo[2]; cz <= chi[2]; ++cz)
+            for (int cy = clo[1]; cy <= chi[1]; ++cy) {
+                const float syz = sd[2][cz - ci[2] + R] + sd[1][cy - ci[1] + R];
+                if (syz > thr) continue;
+                int rowbase = (cz * g.n[1] + cy) * g.n[0];
+                for (int cx = clo[0]; cx <= chi[0]; ++cx) {
+                    if (syz + sd[0][cx - ci[0] + R] > thr) continue;
+                    int c = rowbase + cx;
                     int b = start[c], e = start[c + 1];
                     for (int m = b; m < e; ++m) {
                         float4 p = p32[m];
@@ -487,19 +508,23 @@ void acc32(const float4* geo, int64_t n, const RelaxLists& L, const Spheres& S, 
     k_relax_acc32<LANES><<<grid_for(n * LANES, 256), 256, 0, s>>>(geo, n, L.row_ptr, L.col, S, K, acc, amax, flags);
 }
 
-// float32 acceleration by the cell sweep (cells of the LG support 2h).
+// float32 acceleration by the cell sweep: cells of edge >= h (half the LG support),
+// the neighbours of a particle within two cells of its own along each axis.
 int acc_cells(sph_ctx* ctx, const sph_relax_params* p, const double* pos, const double* vol, const Spheres& S,
               const RelaxK& K, float4* acc, unsigned* amax, cudaStream_t s) {
     CellList cl;
-    int st = sph_build_cells(ctx, &p->dom, pos, s, &cl);
+    sph_domain half = p->dom;
+    half.kappa = 0.5 * p->dom.kappa;
+    int st = sph_build_cells(ctx, &half, pos, s, &cl);
     if (st) return st;
+    const double rc = p->dom.kappa * p->dom.h;
     int64_t n = p->dom.n;
     float4* lo = (float4*)sph_scratch(ctx, S_MISC1, (size_t)n * 16, &st);
     if (st) return st;
     k_relax_pack_lo<<<grid_for(n, 256), 256, 0, s>>>(pos, vol, n, cl.sorted, cl.p32, lo);
-    k_relax_acc_cells<<<grid_for(n, 256), 256, 0, s>>>(cl.p32, lo, cl.cell_start, cl.grid,
-                                                       (const unsigned*)cl.band, cl.grid.rc2, pos, n, S, K, acc,
-                                                       amax);
+    k_relax_acc_cells<2><<<grid_for(n, 256), 256, 0, s>>>(cl.p32, lo, cl.cell_start, cl.grid,
+                                                          (const unsigned*)cl.band, rc * rc, pos, n, S, K, acc,
+                                                          amax);
     SPH_LAUNCH_CHECK(ctx);
     return SPH_OK;
 }
