@@ -655,7 +655,27 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32g(const float* __restr
 #pragma unroll
         for (int a = 0; a < DIM; ++a) vown[a] = RD[8 * ii + 4 + a];
     }
-    const bool staged = stage_neighbours<NPL, W>(RM, n, P0, m, A, sp);
+    // 3D: each staged M_j as 9 floats, planes (M00, M10, M01, M11), (M02, M12, M20, M21)
+    // and M22, three shared-memory loads of 36 bytes per pair; 2D: one chunk
+    float* sp2 = reinterpret_cast<float*>(sp + 2 * A.mcap);
+    bool staged;
+    if (DIM == 3) {
+        staged = m <= A.mcap;
+        if (staged) {
+            for (int q = threadIdx.x; q < m; q += blockDim.x) {
+                // a plan out of date with the lists reads wrong but in-bounds records
+                int64_t j = min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1);
+                const float4* rec = reinterpret_cast<const float4*>(RM + W * j);
+                float4 c1 = __ldg(rec + 1), c2 = __ldg(rec + 2), c3 = __ldg(rec + 3);
+                sp[q] = make_float4(c1.x, c1.y, c2.x, c2.y);
+                sp[A.mcap + q] = make_float4(c3.x, c3.y, c1.z, c2.z);
+                sp2[q] = c3.z;
+            }
+        }
+        __syncthreads();
+    } else {
+        staged = stage_neighbours<NPL, W>(RM, n, P0, m, A, sp);
+    }
     const uint32_t bi = __float_as_uint(a0.v[DIM]);
     float2 mi01[DIM];
     float mi2[3] = {0.0f, 0.0f, 0.0f};
@@ -686,9 +706,16 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32g(const float* __restr
         for (int k = 0; k < len; ++k) {
             float4 e = ldg4_stream(g + (int64_t)k * kTileRows);
             int s = min(max(__float_as_int(e.w), 0), max(m - 1, 0));
-            float4 c1 = sp[s];
-            float4 c2 = DIM == 3 ? sp[mc + s] : c1, c3 = DIM == 3 ? sp[2 * mc + s] : c1;
-            pair(e, c1, c2, c3);
+            if (DIM == 3) {
+                const float4 p0 = sp[s], p1 = sp[mc + s];
+                const float m22 = sp2[s];
+                // the record chunks (M00, M10, M20, .) (M01, M11, M21, .) (M02, M12, M22, .)
+                pair(e, make_float4(p0.x, p0.y, p1.z, 0.0f), make_float4(p0.z, p0.w, p1.w, 0.0f),
+                     make_float4(p1.x, p1.y, m22, 0.0f));
+            } else {
+                float4 c1 = sp[s];
+                pair(e, c1, c1, c1);
+            }
         }
     } else {
         for (int k = 0; k < len; ++k) {
@@ -715,7 +742,7 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32g(const float* __restr
 }
 
 template <int DIM, int OUT>
-__global__ void __launch_bounds__(kTileRows, 8) k_tl_defo32g(const float* __restrict__ RD, float* __restrict__ RM,
+__global__ void __launch_bounds__(kTileRows, 6) k_tl_defo32g(const float* __restrict__ RD, float* __restrict__ RM,
                                                              const int64_t* __restrict__ row_ptr, int64_t n,
                                                              TLK<float> K, GeoArgs A, const float* __restrict__ B0,
                                                              float* __restrict__ H, float* __restrict__ u,
@@ -733,9 +760,14 @@ __global__ void __launch_bounds__(kTileRows, 8) k_tl_defo32g(const float* __rest
     const int m = A.tile_m[tile];
     const float4* g = A.geo + A.tile_so[tile] + threadIdx.x;
     F8 me = ldg8(RD + 8 * ii);
-    float b0[NS];
+    float b0[NS], hold[DIM * DIM], uold[DIM];
 #pragma unroll
     for (int s = 0; s < NS; ++s) b0[s] = B0[s * n + ii];
+    // the epilogue's own-row reads are issued here, their latency hidden by the loop
+#pragma unroll
+    for (int k = 0; k < DIM * DIM; ++k) hold[k] = OUT == OUT_RATES ? 0.0f : H[k * n + ii];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) uold[a] = OUT == OUT_RATES ? 0.0f : u[a * n + ii];
     const bool staged = stage_neighbours<1, 8>(RD, n, P0, m, A, sp);
     const uint32_t bi = __float_as_uint(me.v[DIM]);
     const float2 nv01 = make_float2(-me.v[4], -me.v[5]);
@@ -788,7 +820,7 @@ __global__ void __launch_bounds__(kTileRows, 8) k_tl_defo32g(const float* __rest
         Lt[2 * DIM + 2] = l22.value();
     }
     float vi[3] = {me.v[4], me.v[5], me.v[6]};
-    defo_finish<DIM, OUT>(Lt, b0, (bi & kFixedBit) != 0, vi, i, n, K, RM, H, u, dFdt);
+    defo_finish<DIM, OUT>(Lt, b0, (bi & kFixedBit) != 0, vi, i, n, K, RM, H, u, dFdt, hold, uold);
 }
 
 // ---------------------------------------------------------------- pack / unpack
@@ -1265,7 +1297,7 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
     int mm = stage_mcap(st->plan_maxm, npl, ctx->stage_cap), md = stage_mcap(st->plan_maxm, 1, ctx->stage_cap);
     t.mom = GeoArgs{tp.tile_m, tp.tile_so, tp.uidx, tp.geo, mm};
     t.defo = GeoArgs{tp.tile_m, tp.tile_so, tp.uidx, tp.geo, md};
-    t.mom_bytes = (size_t)mm * 16 * npl;
+    t.mom_bytes = dim == 3 ? (size_t)mm * 36 : (size_t)mm * 16;   // k_tl_mom32g: 9 floats per neighbour in 3D
     t.defo_bytes = (size_t)md * 16;
     // persistent form: both entry buffers, both staging buffers and three lists
     const size_t limit = 220 * 1024;
