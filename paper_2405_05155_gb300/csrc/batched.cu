@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(kTileRows, 6) k_euler32g_batched(const float* 
                                                                    const EulerK<float>* __restrict__ cases,
                                                                    const PlanCase* __restrict__ plans) {
     extern __shared__ __align__(16) unsigned char eb_smem[];
-    const int64_t b = blockIdx.x;
+    // momentum pass in reverse tile order, continuity pass forwards (pair entries reused from L2)
+    const int64_t b = MODE == WANT_MOM ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
     int lo = 0, hi = ncases - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;

@@ -201,7 +201,10 @@ __global__ void __launch_bounds__(kTileRows, 6) k_euler32g(const float* __restri
                                                            double* __restrict__ rate_mass,
                                                            double* __restrict__ rate_mom) {
     extern __shared__ __align__(16) unsigned char eu_smem[];
-    euler_tile_g<DIM, MODE, OUT>(Rin, Rout, row_ptr, 0, 0, n, blockIdx.x, K, A, reinterpret_cast<float4*>(eu_smem),
+    // the momentum pass of the two-pass step walks the tiles in reverse, the continuity
+    // pass forwards: each starts on the pair entries the previous one read last (in L2)
+    const int64_t tile = MODE == WANT_MOM ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+    euler_tile_g<DIM, MODE, OUT>(Rin, Rout, row_ptr, 0, 0, n, tile, K, A, reinterpret_cast<float4*>(eu_smem),
                                  rate_mass, rate_mom);
 }
 

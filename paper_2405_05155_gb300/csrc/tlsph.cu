@@ -638,7 +638,9 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32g(const float* __restr
     constexpr int NPL = DIM == 3 ? 3 : 1;
     extern __shared__ __align__(16) unsigned char tl_smem[];
     float4* sp = reinterpret_cast<float4*>(tl_smem);
-    const int64_t tile = blockIdx.x;
+    // tiles in reverse: the deformation pass walks them forwards, so each pass starts on
+    // the pair entries the previous one read last, still in L2
+    const int64_t tile = gridDim.x - 1 - blockIdx.x;
     const int64_t i0 = tile * kTileRows;
     const int64_t i = i0 + threadIdx.x;
     const bool active = i < n;
