@@ -519,7 +519,7 @@ def run_gpu(args):
     achieved = dominant[1] / (dominant[2] * 1e-3) / 1e9
     # ncu DRAM bytes (read + write) per launch of each planned TL pass, measured on this
     # workload for the current kernels (profiles/tl_pair_passes_plate816k_full.md)
-    ncu_traffic = {}
+    ncu_traffic = {"tl_momentum_pass": 446.3e6, "tl_deformation_pass": 509.1e6}
     traffic = args.traffic if args.traffic is not None else ncu_traffic.get(dominant[0])
 
     # end to end through the C ABI with host buffers: per step, copy the float64

@@ -41,11 +41,13 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint
 
 // C = op(A) op(B) (+ bias, GELU).  A stored [M][K] (aT = 0) or [K][M] (aT = 1);
 // B stored [K][N] (bT = 0) or [N][K] (bT = 1).  128 threads, 2 x 2 warps of 32 x 32.
+// blockIdx.z selects a slice [z kchunk, (z + 1) kchunk) of K whose product goes to
+// C + z * slice_stride (split-K; slices are summed by k_sum_slices).
 template <int EPI>
 __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const float* __restrict__ A, int lda, int aT,
                                                    const float* __restrict__ B, int ldb, int bT,
                                                    const float* __restrict__ bias, float* __restrict__ C, int ldc,
-                                                   float* __restrict__ Zout) {
+                                                   float* __restrict__ Zout, int kchunk, int64_t slice_stride) {
     __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
     __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];
     int tid = threadIdx.x;
@@ -60,7 +62,9 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const fl
         for (int b = 0; b < 4; ++b)
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.0f;
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    C += (int64_t)blockIdx.z * slice_stride;
+    for (int k0 = kb; k0 < ke; k0 += BK) {
 #pragma unroll 4
         for (int r = 0; r < (BM * BK) / 128; ++r) {
             int idx = tid + 128 * r;
@@ -69,7 +73,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const fl
             else { k = idx / BM; m = idx % BM; }
             int gm = m0 + m, gk = k0 + k;
             float v = 0.0f;
-            if (gm < M && gk < K) v = aT ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
+            if (gm < M && gk < ke) v = aT ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
             As[m][k] = __float2bfloat16_rn(v);
         }
 #pragma unroll 4
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const fl
             else { k = idx / BN; n = idx % BN; }
             int gn = n0 + n, gk = k0 + k;
             float v = 0.0f;
-            if (gn < N && gk < K) v = bT ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
+            if (gn < N && gk < ke) v = bT ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
             Bs[n][k] = __float2bfloat16_rn(v);
         }
         __syncthreads();
@@ -132,9 +136,67 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const fl
 void gemm(int epi, int M, int N, int K, const float* A, int lda, int aT, const float* B, int ldb, int bT,
           const float* bias, float* C, int ldc, float* Z, cudaStream_t s) {
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    if (epi == EPI_NONE) k_gemm_bf16<EPI_NONE><<<grid, 128, 0, s>>>(M, N, K, A, lda, aT, B, ldb, bT, bias, C, ldc, Z);
-    else if (epi == EPI_BIAS) k_gemm_bf16<EPI_BIAS><<<grid, 128, 0, s>>>(M, N, K, A, lda, aT, B, ldb, bT, bias, C, ldc, Z);
-    else k_gemm_bf16<EPI_BIAS_GELU><<<grid, 128, 0, s>>>(M, N, K, A, lda, aT, B, ldb, bT, bias, C, ldc, Z);
+    if (epi == EPI_NONE)
+        k_gemm_bf16<EPI_NONE><<<grid, 128, 0, s>>>(M, N, K, A, lda, aT, B, ldb, bT, bias, C, ldc, Z, K, 0);
+    else if (epi == EPI_BIAS)
+        k_gemm_bf16<EPI_BIAS><<<grid, 128, 0, s>>>(M, N, K, A, lda, aT, B, ldb, bT, bias, C, ldc, Z, K, 0);
+    else
+        k_gemm_bf16<EPI_BIAS_GELU><<<grid, 128, 0, s>>>(M, N, K, A, lda, aT, B, ldb, bT, bias, C, ldc, Z, K, 0);
+}
+
+// out[e] = sum over z of parts[z][e], z ascending (a fixed order: deterministic).
+__global__ void k_sum_slices(const float* __restrict__ parts, int slices, int64_t count, float* __restrict__ out) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    float acc = 0.0f, comp = 0.0f;
+    for (int z = 0; z < slices; ++z) {
+        float y = parts[(int64_t)z * count + e] - comp;
+        float t = acc + y;
+        comp = (t - acc) - y;
+        acc = t;
+    }
+    out[e] = acc - comp;
+}
+
+// Weight gradient C[M][N] (ldc = N) = op(A) op(B) over a long K (the batch): the K
+// range is cut into slices computed by separate blocks, then summed in order.
+void gemm_splitk(int M, int N, int K, const float* A, int lda, int aT, const float* B, int ldb, int bT, float* C,
+                 float* scratch, cudaStream_t s) {
+    int slices = (K + 255) / 256;
+    if (slices > 64) slices = 64;
+    int kchunk = ((K + slices - 1) / slices + BK - 1) / BK * BK;
+    slices = (K + kchunk - 1) / kchunk;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, slices);
+    k_gemm_bf16<EPI_NONE><<<grid, 128, 0, s>>>(M, N, K, A, lda, aT, B, ldb, bT, nullptr, scratch, N, nullptr, kchunk,
+                                                (int64_t)M * N);
+    k_sum_slices<<<grid_for((int64_t)M * N, 256), 256, 0, s>>>(scratch, slices, (int64_t)M * N, C);
+}
+
+// Column sums of X[rows][cols] (the bias gradients): per-slice partial sums, then
+// the slices summed in order.
+__global__ void k_colsum_slices(const float* __restrict__ X, int64_t rows, int cols, int64_t rchunk,
+                                float* __restrict__ parts) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    int64_t r0 = (int64_t)blockIdx.y * rchunk, r1 = r0 + rchunk < rows ? r0 + rchunk : rows;
+    float acc = 0.0f, comp = 0.0f;
+    for (int64_t r = r0; r < r1; ++r) {
+        float y = X[r * cols + c] - comp;
+        float t = acc + y;
+        comp = (t - acc) - y;
+        acc = t;
+    }
+    parts[(int64_t)blockIdx.y * cols + c] = acc - comp;
+}
+
+void colsum(const float* X, int64_t rows, int cols, float* out, float* scratch, cudaStream_t s) {
+    int slices = (int)((rows + 63) / 64);
+    if (slices > 64) slices = 64;
+    int64_t rchunk = (rows + slices - 1) / slices;
+    slices = (int)((rows + rchunk - 1) / rchunk);
+    dim3 grid((cols + 127) / 128, slices);
+    k_colsum_slices<<<grid, 128, 0, s>>>(X, rows, cols, rchunk, scratch);
+    k_sum_slices<<<grid_for(cols, 256), 256, 0, s>>>(scratch, slices, cols, out);
 }
 
 // ------------------------------------------------------------------ elementwise / reductions
@@ -178,18 +240,6 @@ __global__ void k_sum_partial(const double* __restrict__ partial, int nb, double
 }
 
 // column sums of X [rows][cols] in fixed row order (bias gradients)
-__global__ void k_colsum(const float* __restrict__ X, int64_t rows, int cols, float* __restrict__ out) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
-    float s = 0.0f, comp = 0.0f;
-    for (int64_t r = 0; r < rows; ++r) {
-        float y = X[r * cols + c] - comp;
-        float t = s + y;
-        comp = (t - s) - y;
-        s = t;
-    }
-    out[c] = s - comp;
-}
 
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
                        int64_t count, float lr, float b1, float b2, float eps, float bc1, float bc2) {
@@ -345,9 +395,12 @@ int mlp_grad_impl(sph_ctx* ctx, const float* P, const float* X, const float* T, 
     double inv = 1.0 / ((double)B * NOUT);
     k_mse<<<nb, 256, 0, s>>>(a.Y, T, B * NOUT, inv, dY, partial);
     k_sum_partial<<<1, 256, 0, s>>>(partial, nb, inv, loss_d);
+    // split-K partials of the weight gradients (64 slices of at most 128 x 128)
+    float* parts = (float*)sph_scratch(ctx, S_MLP_PARTS, (size_t)64 * NHID * NHID * 4 + 256, &st);
+    if (st) return st;
     // layer 4
-    gemm(EPI_NONE, NOUT, NHID, (int)B, dY, NOUT, 1, a.H3, NHID, 0, nullptr, grad + OFF_W4, NHID, nullptr, s);
-    k_colsum<<<1, 128, 0, s>>>(dY, B, NOUT, grad + OFF_B4);
+    gemm_splitk(NOUT, NHID, (int)B, dY, NOUT, 1, a.H3, NHID, 0, grad + OFF_W4, parts, s);
+    colsum(dY, B, NOUT, grad + OFF_B4, parts, s);
     gemm(EPI_NONE, (int)B, NHID, NOUT, dY, NOUT, 0, P + OFF_W4, NHID, 0, nullptr, dH, NHID, nullptr, s);
     const float* Zs[3] = {a.Z1, a.Z2, a.Z3};
     const float* Hin[3] = {X, a.H1, a.H2};
@@ -355,8 +408,8 @@ int mlp_grad_impl(sph_ctx* ctx, const float* P, const float* X, const float* T, 
     const int nin[3] = {NIN, NHID, NHID};
     for (int l = 2; l >= 0; --l) {
         k_gelu_backward<<<grid_for(B * NHID, 256), 256, 0, s>>>(dH, Zs[l], dZ, B * NHID);
-        gemm(EPI_NONE, NHID, nin[l], (int)B, dZ, NHID, 1, Hin[l], nin[l], 0, nullptr, grad + offW[l], nin[l], nullptr, s);
-        k_colsum<<<1, 128, 0, s>>>(dZ, B, NHID, grad + offB[l]);
+        gemm_splitk(NHID, nin[l], (int)B, dZ, NHID, 1, Hin[l], nin[l], 0, grad + offW[l], parts, s);
+        colsum(dZ, B, NHID, grad + offB[l], parts, s);
         if (l > 0)
             gemm(EPI_NONE, (int)B, nin[l], NHID, dZ, NHID, 0, P + offW[l], nin[l], 0, nullptr, dH, nin[l], nullptr, s);
     }
