@@ -131,6 +131,39 @@ def plate(dp=0.001, length=0.2, thickness=0.02, width=0.2, root_layers=4,
             "c0": c0, "dt": dt}
 
 
+def beam2d(dp=0.002, length=0.2, thickness=0.02, root_layers=4, periodic_x=False, rho0=1000.0, E=2.0e6,
+           nu=0.3975, amp_factor=0.05, kappa=KAPPA_TW):
+    """2D total-Lagrangian strip in x-y: the plate's section.
+
+    Clamped root x in [-root_layers dp, 0) with the first-mode velocity of `plate`, or,
+    with periodic_x, a strip periodic along x (no clamp) with v_y = amp c0 sin(2 pi x / L)."""
+    nx = int(round(length / dp)) + (0 if periodic_x else root_layers)
+    ny = int(round(thickness / dp))
+    lo = (0.0 if periodic_x else -root_layers * dp, 0.0)
+    r0 = lattice((nx, ny), dp, lo)
+    fixed = np.zeros(r0.shape[1], dtype=np.uint8) if periodic_x else (r0[0] < 0.0).astype(np.uint8)
+    K = E / (3.0 * (1.0 - 2.0 * nu))
+    c0 = math.sqrt(K / rho0)
+    v = np.zeros_like(r0)
+    if periodic_x:
+        v[1] = amp_factor * c0 * np.sin(2.0 * math.pi * r0[0] / (nx * dp))
+    else:
+        v[1] = amp_factor * c0 * cantilever_mode(r0[0], length)
+        v[:, fixed == 1] = 0.0
+    h = H_SOLID * dp
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    G = E / (2.0 * (1.0 + nu))
+    dt = 0.5 * h / (c0 + amp_factor * c0)
+    margin = 2.0 * dp
+    if periodic_x:
+        dom = domain(2, h, kappa, (0.0, -margin), (nx * dp, ny * dp + 2 * margin), (True, False))
+    else:
+        dom = domain(2, h, kappa, (lo[0] - margin, -margin), (nx * dp + 2 * margin, ny * dp + 2 * margin),
+                     (False, False))
+    return {"r0": r0, "v": v, "fixed": fixed, "vol": np.full(r0.shape[1], dp ** 2), "domain": dom, "dp": dp,
+            "rho0": rho0, "E": E, "nu": nu, "lam": lam, "G": G, "c0": c0, "dt": dt}
+
+
 def sphere_union(seed, count=8, rmin=0.1, rmax=0.3):
     """Seeded centres U(0,1)^3 and radii U(rmin, rmax); rows (cx, cy, cz, r)."""
     rng = np.random.default_rng(seed)

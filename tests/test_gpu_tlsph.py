@@ -19,8 +19,8 @@ def ctx():
     c.close()
 
 
-def _setup(ctx, dp=0.005, kappa=1.6, law=OT.NEO_HOOKEAN):
-    c = inputs.plate(dp=dp, kappa=kappa)
+def _setup(ctx, dp=0.005, kappa=1.6, law=OT.NEO_HOOKEAN, case=None):
+    c = inputs.plate(dp=dp, kappa=kappa) if case is None else case
     d = c["domain"]
     r0, order = sorted_by_cells(c["r0"], d)
     v = c["v"][:, order]
@@ -44,6 +44,38 @@ def _solid(ctx, s, precision, law, v=None, H=None, tiles=True):
 # from global memory
 VARIANTS = ((api.SPH_FP64, True, 1e-12, rel_max), (api.SPH_FP32_KAHAN, True, 1e-5, rel_l2),
             (api.SPH_FP32_KAHAN, False, 1e-5, rel_l2))
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_2d_strip_rates_and_steps(ctx, periodic):
+    # the 2D forms (clamped strip, and a strip periodic along x for the minimum image of
+    # the cell-relative positions and of the plan's pair factors)
+    case = inputs.beam2d(dp=0.002, periodic_x=periodic)
+    s = _setup(ctx, case=case)
+    n = s["r0"].shape[1]
+    rng = np.random.default_rng(11)
+    H = 0.01 * rng.normal(size=(4, n))
+    v = s["v"] + 0.05 * rng.normal(size=s["v"].shape)
+    F = _F_from_H(H)
+    M = OT.stress_matrix(F, s["B0_h"], s["prm"])
+    a_o = OT.momentum_rate(s["r0"], s["vol"], M, s["rp_h"], s["col_h"], s["prm"].dom, s["prm"].rho0)
+    Fd_o = OT.deformation_rate(s["r0"], s["vol"], v, s["B0_h"], s["rp_h"], s["col_h"], s["prm"].dom)
+    Fd_o = Fd_o.reshape(n, 4).T
+    for prec, tiles, tol, err in VARIANTS:
+        sol = _solid(ctx, s, prec, OT.NEO_HOOKEAN, v=v, H=H, tiles=tiles)
+        a, Fd = sol.rates()
+        assert err(host(a), a_o) < tol, (prec, tiles, err(host(a), a_o))
+        assert err(host(Fd), Fd_o) < tol, (prec, tiles, err(host(Fd), Fd_o))
+    F0 = np.tile(np.eye(2), (n, 1, 1))
+    x_o, v_o, F_o = OT.run(s["r0"], s["vol"], s["B0_h"], s["fixed"], s["r0"].copy(), s["v"], F0, s["rp_h"],
+                           s["col_h"], s["prm"], 10)
+    H_o = (F_o - np.eye(2)[None]).reshape(n, 4).T
+    for prec, tiles, tol, err in VARIANTS:
+        sol = _solid(ctx, s, prec, OT.NEO_HOOKEAN, tiles=tiles)
+        sol.step(10)
+        x, vv, HH = sol.fields()
+        assert err(host(vv), v_o) < tol, (prec, tiles, err(host(vv), v_o))
+        assert err(host(HH), H_o) < tol, (prec, tiles, err(host(HH), H_o))
 
 
 def _F_from_H(H):
