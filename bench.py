@@ -429,6 +429,14 @@ def run_gpu(args):
     ctx = api.Context(torch.cuda.current_device())
     K, W = args.steps, args.warmup
 
+    if args.profile == "relax":
+        from paper_2405_05155_gb300 import learned
+        b, prm, pos, vol = learned.body_on_device(ctx, 0, 1.0 / 128.0)
+        api.relax_step(ctx, prm, pos, vol, W + K)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "relax", "particles": int(pos.shape[1]), "steps": W + K}))
+        ctx.close()
+        return 0
     if args.profile == "mlp":
         g = torch.Generator(device="cpu").manual_seed(0)
         feats = (0.8 * torch.randn((args.mlp_rows, 128), generator=g)).to(ctx.device)
@@ -619,10 +627,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--profile", choices=["fp32", "fp64", "eu3d", "mlp"], default=None,
+    ap.add_argument("--profile", choices=["fp32", "fp64", "eu3d", "mlp", "relax"], default=None,
                     help="run only one workload (setup + warmup + steps) for ncu captures: the plate "
                          "(fp32 or fp64), the 3D Taylor-Green vortex of side --eu-n (eu3d, float32) or the "
-                         "fused MLP forward over --mlp-rows rows (mlp)")
+                         "fused MLP forward over --mlp-rows rows (mlp), or float32 relaxation steps of the "
+                         "8-sphere body at dp = 1/128 (relax)")
     ap.add_argument("--mlp-rows", type=int, default=262144, help="rows of the --profile mlp workload")
     ap.add_argument("--eu-n", type=int, default=64, help="lattice side of the --profile eu3d workload")
     ap.add_argument("--no-tiles", action="store_true", help="--profile: without tile plans (per-pair geometry)")
