@@ -338,31 +338,44 @@ def _bench_batched(api, inputs, ctx, steps, peak):
 
 def _bench_relax(api, inputs, ctx, steps, peak):
     """Laguerre-Gauss relaxation of the 8-sphere body at dp = 1/128 (float32 pair sums)."""
-    import torch
     from paper_2405_05155_gb300 import learned
     from paper_2405_05155_gb300._lib import SPH_TIMER_NEIGHBORS, SPH_TIMER_RELAX_ACCEL, SPH_TIMER_RELAX_UPDATE
     b, prm, pos, vol = learned.body_on_device(ctx, 0, 1.0 / 128.0)
     n = pos.shape[1]
+    skin = 0.2
+    ctx.set_relax_skin(skin)
     r0 = api.relax_residual(ctx, prm, pos, vol)
-    api.relax_step(ctx, prm, pos, vol, 2)
-    ctx.timing(True)
+    api.relax_step(ctx, prm, pos, vol, 3)
     ms = _event_ms(lambda: api.relax_step(ctx, prm, pos, vol, steps))
+    # the same call once more with per-kernel events, for the breakdown
+    ctx.timing(True)
+    api.relax_step(ctx, prm, pos, vol, steps)
     tn, nn = ctx.timer(SPH_TIMER_NEIGHBORS)
     ta, na = ctx.timer(SPH_TIMER_RELAX_ACCEL)
     tu, nu = ctx.timer(SPH_TIMER_RELAX_UPDATE)
     ctx.timing(False)
+    # the list-free form: a cell sweep every step
+    ctx.set_relax_skin(0.0)
+    sweep_steps = 10
+    ms_sweep = _event_ms(lambda: api.relax_step(ctx, prm, pos, vol, sweep_steps)) / sweep_steps
+    ctx.set_relax_skin(skin)
     r1 = api.relax_residual(ctx, prm, pos, vol)
     # pairs per step: the LG neighbour count of the current positions
     rp, col = api.build_neighbors(ctx, b["domain"], pos)
     nnz = int(col.numel())
-    acc_bytes = n * (32 + 8 + 16) + 4 * nnz
+    # walk: own records (32 B in, 16 B out) and the list stream, ~(2.2/2)^3 entries per pair
+    list_entries = nnz * ((2.0 + skin) / 2.0) ** 3
+    acc_bytes = n * (32 + 16 + 4) + 4 * list_entries
     return {"workload": "Laguerre-Gauss relaxation, union of 8 seeded spheres (seed 0), dp=1/128, h=1.3dp, "
-                        "cut-off 2h, jitter 0.25dp, FP32+Kahan pair sums, list rebuilt every step",
+                        "cut-off 2h, jitter 0.25dp, FP32+Kahan pair sums, list of cut-off 2h + %.1fh rebuilt "
+                        "when twice the largest displacement exceeds the skin" % skin,
             "particles": n, "nnz": nnz, "ms_per_step": ms / steps,
             "pair_interactions_per_s": nnz * steps / (ms * 1e-3),
-            "ms_breakdown": {"neighbour_rebuild": tn / max(nn, 1), "accel_pass": ta / max(na, 1),
+            "list_builds_per_%d_steps" % steps: nn,
+            "ms_breakdown": {"list_build": tn / max(nn, 1), "accel_pass": ta / max(na, 1),
                              "update": tu / max(nu, 1)},
-            "residual_lg": [r0[0], r1[0]], "residual_tw": [r0[1], r1[1]], "steps": 2 + steps,
+            "cell_sweep_every_step_ms_per_step": ms_sweep,
+            "residual_lg": [r0[0], r1[0]], "residual_tw": [r0[1], r1[1]], "steps": 3 + 2 * steps + sweep_steps,
             "roofline_accel_pass": _roof(acc_bytes, ta / max(na, 1), peak)}
 
 

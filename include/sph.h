@@ -95,9 +95,10 @@ const char* sph_status_string(int status);
 int sph_last_cuda_error(const sph_ctx* ctx);
 
 /* Launch shape of the float32 pair passes: `lanes` (1, 2, 4 or 8) consecutive
- * lanes of a warp share one particle's neighbour row and combine their partial
+ * lanes of a warp share one particle's neighbour row (for SPH_PASS_RELAX: the
+ * row of the float32 relaxation list) and combine their partial
  * sums with shuffles.  pass: SPH_PASS_*.  Results of different shapes differ
- * only by float32 rounding.  Defaults to 4.  sph_get_lanes returns the setting
+ * only by float32 rounding.  Defaults to 4 (1 for SPH_PASS_RELAX).  sph_get_lanes returns the setting
  * (or -1 on a bad argument).  Not part of the paper: a GPU launch parameter. */
 #define SPH_PASS_EULERIAN 0
 #define SPH_PASS_TLSPH    1
@@ -451,9 +452,20 @@ typedef struct {
     double spheres[4 * SPH_MAX_SPHERES];
 } sph_relax_params;
 
-/* Advance nsteps relaxation steps of pos (float64 [3][n], in place). */
+/* Advance nsteps relaxation steps of pos (float64 [3][n], in place).
+ * SPH_FP32_KAHAN keeps, within one call, a neighbour list of cut-off 2h + skin
+ * (sph_set_relax_skin) and rebuilds it only when twice the largest displacement
+ * since its build exceeds the skin; every step still decides each listed pair at
+ * 2h exactly, so the pair sets are those of a fresh list.  The list lives in the
+ * context; each call builds it anew from pos.  Synchronises the stream every few
+ * steps (to read the list's status) and at the end.  SPH_ERR_CAPACITY if a
+ * particle has 65,536 or more neighbours within 2h + skin. */
 int sph_relax_step(sph_ctx* ctx, const sph_relax_params* prm, double* pos,
                    const double* vol, int nsteps, void* stream);
+/* Skin of the float32 relaxation list in units of h, 0 <= skin_over_h <= 1
+ * (default 0.2).  0 sweeps the cells afresh every step (no list).  Not part of
+ * the paper: results differ only by float32 summation order. */
+int sph_set_relax_skin(sph_ctx* ctx, double skin_over_h);
 /* Acceleration a (float64 [3][n]) at the current positions (one neighbour
  * build + pair pass). */
 int sph_relax_accel(sph_ctx* ctx, const sph_relax_params* prm, const double* pos,

@@ -112,6 +112,7 @@ _SIGNATURES = {
     "sph_tlsph_plan_bytes": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), _P(c_i64), c_vp]),
     "sph_tlsph_plan": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp]),
     "sph_set_stage_cap": (ctypes.c_int, [c_vp, ctypes.c_int]),
+    "sph_set_relax_skin": (ctypes.c_int, [c_vp, ctypes.c_double]),
     "sph_set_tile_pipeline": (ctypes.c_int, [c_vp, ctypes.c_int]),
     "sph_autotune_eulerian": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), ctypes.c_int,
                                              _P(ctypes.c_int), _P(c_dbl), c_vp]),

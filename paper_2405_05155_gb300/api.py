@@ -10,7 +10,8 @@ import torch
 from . import _lib as L
 from ._lib import (SPH_FP32_KAHAN, SPH_FP64, SPH_FUSED, SPH_LAGUERRE_GAUSS,  # noqa: F401
                    SPH_NEO_HOOKEAN, SPH_SVK, SPH_TWO_PASS, SPH_WENDLAND_C2, SPH_PASS_BATCHED,
-                   SPH_PASS_EULERIAN, SPH_PASS_RELAX, SPH_PASS_TLSPH)
+                   SPH_PASS_EULERIAN, SPH_PASS_RELAX, SPH_PASS_TLSPH, SPH_TIMER_NEIGHBORS,
+                   SPH_TIMER_RELAX_ACCEL, SPH_TIMER_RELAX_UPDATE)
 
 NSYM = {2: 3, 3: 6}
 
@@ -67,6 +68,10 @@ class Context:
 
     def set_stage_cap(self, cap):
         L.check("sph_set_stage_cap", self.lib.sph_set_stage_cap(self.h, int(cap)), self.h)
+
+    def set_relax_skin(self, skin_over_h):
+        """Skin of the float32 relaxation list in units of h (0: a cell sweep every step)."""
+        L.check("sph_set_relax_skin", self.lib.sph_set_relax_skin(self.h, float(skin_over_h)), self.h)
 
     def set_lanes(self, which, lanes):
         L.check("sph_set_lanes", self.lib.sph_set_lanes(self.h, which, lanes), self.h)

@@ -40,10 +40,11 @@ struct sph_ctx {
     size_t slot_bytes[kSlots] = {};
     int* flags = nullptr;          // device status words (see FLAG_*)
     void* pinned = nullptr;        // small pinned host buffer for read-backs
-    int lanes[4] = {4, 4, 4, 4};   // lanes per particle of the float32 pair passes (SPH_PASS_*)
+    int lanes[4] = {4, 4, 1, 4};   // lanes per particle of the float32 pair passes (SPH_PASS_*)
     int stage_cap = 0;             // most neighbour records a tile stages in shared memory (0: default)
     bool no_pipe = true;           // planned passes: skip the persistent double-buffered form
     bool waits_pending = false;    // a kernel with bounded waits ran since the timeout flag was read
+    double relax_skin = 0.2;       // float32 relaxation: list skin / h (0: a cell sweep every step)
     // batched Eulerian step: launch shape, captured graph and the case table it was made for
     int batch_block = 256;
     cudaGraphExec_t batch_graph = nullptr;
@@ -60,7 +61,7 @@ enum ScratchSlot {
 };
 
 // device status words
-enum { FLAG_BAD_INPUT = 0, FLAG_NONFINITE = 1, FLAG_CAPACITY = 2, FLAG_TIMEOUT = 3, FLAG_COUNT = 8 };
+enum { FLAG_BAD_INPUT = 0, FLAG_NONFINITE = 1, FLAG_CAPACITY = 2, FLAG_TIMEOUT = 3, FLAG_STALE = 4, FLAG_COUNT = 8 };
 
 #define SPH_CUDA(ctx, call)                                                     \
     do {                                                                        \
@@ -182,6 +183,13 @@ __device__ __forceinline__ F8 ldg8_stream(const float* p) {
         : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]),
           "=f"(r.v[7])
         : "l"(p));
+    return r;
+}
+
+// 32-bit streaming read of data used once (as ldg8_stream).
+__device__ __forceinline__ int ldg1_stream(const int* p) {
+    int r;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.b32 %0, [%1];" : "=r"(r) : "l"(p));
     return r;
 }
 

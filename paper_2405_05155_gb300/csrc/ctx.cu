@@ -72,6 +72,12 @@ extern "C" int sph_get_lanes(const sph_ctx* ctx, int pass) {
     return ctx->lanes[pass];
 }
 
+extern "C" int sph_set_relax_skin(sph_ctx* ctx, double skin_over_h) {
+    if (!ctx || !(skin_over_h >= 0.0 && skin_over_h <= 1.0)) return SPH_ERR_ARG;
+    ctx->relax_skin = skin_over_h;
+    return SPH_OK;
+}
+
 extern "C" int sph_set_tile_pipeline(sph_ctx* ctx, int on) {
     if (!ctx) return SPH_ERR_ARG;
     ctx->no_pipe = (on == 0);

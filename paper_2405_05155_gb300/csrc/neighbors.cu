@@ -24,25 +24,27 @@ __global__ void k_cell_ids(const double* __restrict__ pos, int64_t n, CellGrid g
                            int32_t* __restrict__ cid, int32_t* __restrict__ count,
                            int* __restrict__ flags, unsigned* __restrict__ absmax) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int c[3] = {0, 0, 0};
     float m = 0.0f;
-    bool bad = false;
-    for (int k = 0; k < g.dim; ++k) {
-        double x = pos[k * n + i];
-        if (!isfinite(x)) bad = true;
-        if ((g.periodic >> k) & 1u) {
-            if (!(x >= g.lo[k] && x <= g.lo[k] + g.len[k])) bad = true;
+    if (i < n) {
+        int c[3] = {0, 0, 0};
+        bool bad = false;
+        for (int k = 0; k < g.dim; ++k) {
+            double x = pos[k * n + i];
+            if (!isfinite(x)) bad = true;
+            if ((g.periodic >> k) & 1u) {
+                if (!(x >= g.lo[k] && x <= g.lo[k] + g.len[k])) bad = true;
+            }
+            c[k] = cell_coord(x, k, g);
+            m = fmaxf(m, __double2float_ru(fabs(x)));
         }
-        c[k] = cell_coord(x, k, g);
-        m = fmaxf(m, __double2float_ru(fabs(x)));
+        if (bad) { atomicExch(&flags[FLAG_BAD_INPUT], 1); c[0] = c[1] = c[2] = 0; m = 0.0f; }
+        int id = (c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
+        cid[i] = id;
+        atomicAdd(&count[id], 1);
     }
-    if (bad) { atomicExch(&flags[FLAG_BAD_INPUT], 1); c[0] = c[1] = c[2] = 0; m = 0.0f; }
-    int id = (c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
-    cid[i] = id;
-    atomicAdd(&count[id], 1);
-    // non-negative floats order like their bit patterns
-    atomicMax(absmax, __float_as_uint(m));
+    // non-negative floats order like their bit patterns; one atomic per warp
+    unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0 && wm) atomicMax(absmax, wm);
 }
 
 // Morton (Z-order) key of a cell: bit l of the coordinate on axis a goes to the

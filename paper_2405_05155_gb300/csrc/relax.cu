@@ -1,14 +1,20 @@
 // a10/a11: Laguerre-Gauss particle relaxation (Sec. 2.3.2; Eqs. 7-8) and its
-// residual.  Positions move every step, so each step re-bins the particles into
-// cells and recomputes the neighbour sets.  The float32 step does this without a
-// list: one sweep over the 27 neighbouring cells screens every candidate (the
-// a2 screen and float64 band, so the pair set equals the list builder's) and
-// accumulates the acceleration at once, with a block-level max of |a|; a
-// pointwise update follows (dt = 0.25 sqrt(h/max|a|), x += a dt^2/2, projection
-// back inside the body).  The float64 step keeps explicit CSR lists (count,
-// scan, fill) launched back to back without host synchronisation; a device flag
-// records a list-capacity overflow, after which the remaining steps are no-ops
-// and the host regrows the list and resumes from the failed step.
+// residual.  Positions move every step, so the neighbour sets change.
+//  - float32 step (default): a buffered neighbour list of cut-off 2h + skin,
+//    rebuilt only when twice the largest displacement since its build exceeds the
+//    skin; every step decides each listed pair at 2h exactly, accumulates the
+//    acceleration with a block-level max of |a|, and a pointwise update follows
+//    (dt = 0.25 sqrt(h/max|a|), x += a dt^2/2, projection back inside the body).
+//  - float32 step with skin 0, and the single acceleration evaluation: no list; one
+//    sweep over the neighbouring cells screens every candidate (the a2 screen and
+//    float64 band, so the pair set equals the list builder's) and accumulates.
+//  - float64 step: explicit CSR lists (count, scan, fill) every step, launched back
+//    to back without host synchronisation.
+// In both list forms a device flag records a capacity overflow (or a stale list),
+// after which the remaining steps are no-ops and the host regrows (or rebuilds) the
+// list and resumes from that step.
+#include <algorithm>
+
 #include "common.cuh"
 #include "neighbors.cuh"
 
@@ -28,7 +34,7 @@ struct RelaxK {
     double inv_h;
     double rc2_tw;                 // (1.6 h)^2 for the truncated residual
     double surf_coef;              // 2 pi ahat / h
-    float gcoef_f, inv_h_f, scale_f, surf_coef_f, h_f, dp_f;
+    float gcoef_f, inv_h_f, inv_h2_f, scale_f, surf_coef_f, h_f, dp_f;
 };
 
 // Signed distance to the sphere union and its unit normal (first minimiser).
@@ -127,50 +133,46 @@ __global__ void k_amax64_exact(const double* __restrict__ acc, int64_t n, const 
     if (__double2float_ru(m) == bound) atomicMax(amax_d, (unsigned long long)__double_as_longlong(m));
 }
 
-template <int LANES>
-__global__ void __launch_bounds__(256) k_relax_acc32(const float4* __restrict__ geo, int64_t n,
-                                                     const int64_t* __restrict__ row_ptr,
-                                                     const int32_t* __restrict__ col, Spheres S, RelaxK K,
-                                                     float4* __restrict__ acc, unsigned* __restrict__ amax,
-                                                     const int* __restrict__ flags) {
-    __shared__ unsigned smax;
-    if (threadIdx.x == 0) smax = 0u;
-    __syncthreads();
-    int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t i = gt / LANES;
-    int lane = (int)(gt % LANES);
-    bool active = i < n && flags[FLAG_CAPACITY] == 0;
-    int64_t ii = i < n ? i : 0;
-    float4 A = __ldg(&geo[2 * ii]), B = __ldg(&geo[2 * ii + 1]);
-    float xh[3] = {A.x, A.y, A.z}, xl[3] = {B.x, B.y, B.z};
-    Kahan<float> s[3];
-    for (int a = 0; a < 3; ++a) s[a].init();
-    int64_t b = active ? row_ptr[ii] : 0, e = active ? row_ptr[ii + 1] : 0;
-    for (int64_t p = b + lane; p < e; p += LANES) {
-        int j = __ldg(&col[p]);
-        float4 Aj = __ldg(&geo[2 * j]), Bj = __ldg(&geo[2 * j + 1]);
-        float r[3];
-        r[0] = (xh[0] - Aj.x) + (xl[0] - Bj.x);
-        r[1] = (xh[1] - Aj.y) + (xl[1] - Bj.y);
-        r[2] = (xh[2] - Aj.z) + (xl[2] - Bj.z);
-        float d2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-        float gs = lg_gs<float>(sqrtf(d2) * K.inv_h_f, K.gcoef_f) * Aj.w;
-        for (int a = 0; a < 3; ++a) s[a].add(gs * r[a]);
+// pos[a][i] = xh + xl of slot m (i = sorted[m]): the positions back to the
+// caller's order, in float64.
+__global__ void k_relax_scatter_pos(const float4* __restrict__ rec, const int32_t* __restrict__ sorted, int64_t n,
+                                    double* __restrict__ pos) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    int i = sorted[m];
+    float4 a = rec[2 * m], b = rec[2 * m + 1];
+    pos[i] = (double)a.x + (double)b.x;
+    pos[n + i] = (double)a.y + (double)b.y;
+    pos[2 * n + i] = (double)a.z + (double)b.z;
+}
+
+// x + d for a float-float x = xh + xl and a float32 d: the sum xh + d and its
+// rounding error (Knuth's TwoSum), the error added to xl, and the pair
+// renormalised by a second TwoSum.  Every operation rounds on its own.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bv = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
+__device__ __forceinline__ void ff_add(float& xh, float& xl, float d) {
+    float s, e, h, l;
+    two_sum(xh, d, s, e);
+    two_sum(s, __fadd_rn(xl, e), h, l);
+    xh = h;
+    xl = l;
+}
+
+// The float64 neighbour predicate (unfused sum of squares, as the list builder's)
+// for the float-float positions xi and those of record r.
+__device__ __forceinline__ bool within_ff(const double* xi, const F8& r, double rc2) {
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double dx = __dsub_rn(xi[a], (double)r.v[a] + (double)r.v[4 + a]);
+        double sq = __dmul_rn(dx, dx);
+        d2 = a == 0 ? sq : __dadd_rn(d2, sq);
     }
-    float tot[3];
-    for (int a = 0; a < 3; ++a) tot[a] = group_sum<LANES>(s[a].value());
-    if (active && lane == 0) {
-        float g[3];
-        float phi = sdf32(S, xh, xl, g);
-        float I = surface_lg<float>(phi < 0.0f ? -phi : 0.0f, K.inv_h_f, K.surf_coef_f);
-        float a0 = -K.scale_f * (tot[0] + I * g[0]);
-        float a1 = -K.scale_f * (tot[1] + I * g[1]);
-        float a2 = -K.scale_f * (tot[2] + I * g[2]);
-        acc[i] = make_float4(a0, a1, a2, 0.0f);
-        atomic_max_nonneg(&smax, sqrtf(a0 * a0 + a1 * a1 + a2 * a2));
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && smax) atomicMax(amax, smax);
+    return d2 <= rc2;
 }
 
 // ---------------------------------------------------------------- update
@@ -196,7 +198,7 @@ __global__ void k_relax_update64(double* __restrict__ pos, int64_t n, const doub
 
 __global__ void k_relax_update32(double* __restrict__ pos, int64_t n, const float4* __restrict__ acc,
                                  const unsigned* __restrict__ amax, Spheres S, RelaxK K,
-                                 float4* __restrict__ geo, const int* __restrict__ flags) {
+                                 const int* __restrict__ flags) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || flags[FLAG_CAPACITY]) return;
     float am = __uint_as_float(*amax);
@@ -215,30 +217,7 @@ __global__ void k_relax_update32(double* __restrict__ pos, int64_t n, const floa
         float sh = phi + 0.5f * K.dp_f;
         for (int c = 0; c < 3; ++c) x[c] -= (double)(sh * g[c]);
     }
-    for (int c = 0; c < 3; ++c) {
-        pos[c * n + i] = x[c];
-        xh[c] = (float)x[c];
-        xl[c] = (float)(x[c] - (double)xh[c]);
-    }
-    if (geo) {
-        float4 A = geo[2 * i];
-        geo[2 * i] = make_float4(xh[0], xh[1], xh[2], A.w);
-        geo[2 * i + 1] = make_float4(xl[0], xl[1], xl[2], 0.0f);
-    }
-}
-
-__global__ void k_relax_pack(const double* __restrict__ pos, const double* __restrict__ vol, int64_t n,
-                             float4* __restrict__ geo) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float xh[3], xl[3];
-    for (int c = 0; c < 3; ++c) {
-        double x = pos[c * n + i];
-        xh[c] = (float)x;
-        xl[c] = (float)(x - (double)xh[c]);
-    }
-    geo[2 * i] = make_float4(xh[0], xh[1], xh[2], (float)vol[i]);
-    geo[2 * i + 1] = make_float4(xl[0], xl[1], xl[2], 0.0f);
+    for (int c = 0; c < 3; ++c) pos[c * n + i] = x[c];
 }
 
 // ---------------------------------------------------------------- residual
@@ -301,12 +280,10 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int nb, doubl
 }
 
 // ---------------------------------------------------------------- float32 cell sweep
-// The float32 step needs no neighbour list: one pass over the 27 neighbouring
-// cells screens every candidate with the float32 position copy of the cell sort
-// (the same screen and float64 band decision as the list builder, so the pair
-// set is the list's), and accumulates the Laguerre-Gauss gradient of the
-// accepted pairs at once.  Threads walk the particles in cell order, so the
-// candidates of neighbouring threads are the same cells (L1 reuse).
+// The float32 pair loops screen candidates with the float32 position copy of a
+// cell sort (the a2 screen, with the float64 decision inside the rounding band,
+// so the pair set is the list builder's).  Threads walk the particles in cell
+// order, so the candidates of neighbouring threads are the same cells (L1 reuse).
 
 // (x - float(x), V) per particle in sorted order: the float32 low parts of the position
 __global__ void k_relax_pack_lo(const double* __restrict__ pos, const double* __restrict__ vol, int64_t n,
@@ -320,10 +297,107 @@ __global__ void k_relax_pack_lo(const double* __restrict__ pos, const double* __
                         (float)(pos[2 * n + j] - (double)h.z), (float)vol[j]);
 }
 
-// Cells of edge >= rc / R: a particle's neighbours lie in the cells within R of its
-// own along every axis.  A cell whose box is farther than the screening threshold
-// is skipped; the outermost cells extend to infinity outwards (clamped particles
-// outside the box lie in them).
+template <int N>
+__device__ __forceinline__ float pick(const float (&a)[N], int k) {
+    float v = a[0];
+#pragma unroll
+    for (int t = 1; t < N; ++t) v = k == t ? a[t] : v;
+    return v;
+}
+
+// Visits, in cell order, the sorted slots of the cells within R of the particle's
+// cell ci (cells of edge >= rc / R) whose box lies within sqrt(thr) of xh.  The
+// outermost cells extend to infinity outwards (clamped particles outside the box
+// lie in them).  Along x the passing cells of a row are consecutive (the distance
+// to the slabs falls, then rises), so a row is one run of sorted slots.
+template <int R, typename F>
+__device__ __forceinline__ void sweep_cells(const float* xh, const int* ci, const CellGrid& g,
+                                            const int32_t* __restrict__ start, float thr, F&& visit) {
+    constexpr int W = 2 * R + 1;
+    float sd[3][W];   // squared distance to the cell slabs ci + d, d in [-R, R], per axis
+    int dlo[3], dhi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        dlo[a] = max(ci[a] - R, 0) - ci[a];
+        dhi[a] = min(ci[a] + R, g.n[a] - 1) - ci[a];
+#pragma unroll
+        for (int d = -R; d <= R; ++d) {
+            int c = ci[a] + d;
+            float x = xh[a];
+            float b0 = (float)(g.lo[a] + c * g.size[a]), b1 = (float)(g.lo[a] + (c + 1) * g.size[a]);
+            float gap = 0.0f;
+            if (c > 0 && x < b0) gap = b0 - x;
+            if (c < g.n[a] - 1 && x > b1) gap = x - b1;
+            sd[a][d + R] = gap * gap;
+        }
+    }
+#pragma unroll 1
+    for (int dz = dlo[2]; dz <= dhi[2]; ++dz) {
+        const float sz = pick<W>(sd[2], dz + R);
+#pragma unroll 1
+        for (int dy = dlo[1]; dy <= dhi[1]; ++dy) {
+            const float syz = sz + pick<W>(sd[1], dy + R);
+            if (syz > thr) continue;
+            int a = W, b = -1;
+#pragma unroll
+            for (int d = 0; d < W; ++d) {
+                bool ok = d - R >= dlo[0] && d - R <= dhi[0] && syz + sd[0][d] <= thr;
+                if (ok && a == W) a = d;
+                if (ok) b = d;
+            }
+            if (b < 0) continue;
+            int row = ((ci[2] + dz) * g.n[1] + ci[1] + dy) * g.n[0] + ci[0] - R;
+            int e = start[row + b + 1];
+            for (int m = start[row + a]; m < e; ++m) visit(m);
+        }
+    }
+}
+
+// Compensated sum of the pair terms: (x, y) on the paired float32 instructions,
+// z on its own; the same Kahan steps on every component.
+struct LgSum {
+    Kahan2 xy;
+    Kahan<float> z;
+    __device__ __forceinline__ void init() { xy.init(); z.init(); }
+    __device__ __forceinline__ void value(float* out) const {
+        float2 v = xy.value();
+        out[0] = v.x;
+        out[1] = v.y;
+        out[2] = z.value();
+    }
+};
+
+// Pair term of Eq. 7 for an accepted pair: r = x_i - x_j from the high parts'
+// difference (dx, dy, dz) and the low parts; grad W^LG_ij V_j = gs r with gs a
+// function of q^2 = r^2/h^2 alone (Eq. 8 divided by r), so no square root.
+__device__ __forceinline__ void lg_pair(LgSum& s, float dx, float dy, float dz, const float* xl, float4 q,
+                                        const RelaxK& K) {
+    const float2 lxy = __ffma2_rn(make_float2(q.x, q.y), make_float2(-1.0f, -1.0f), make_float2(xl[0], xl[1]));
+    const float2 rxy = __fadd2_rn(make_float2(dx, dy), lxy);
+    const float rz = __fadd_rn(dz, __fsub_rn(xl[2], q.z));
+    const float d2 = fmaf(rz, rz, fmaf(rxy.y, rxy.y, rxy.x * rxy.x));
+    const float q2 = d2 * K.inv_h2_f;
+    const float gs = K.gcoef_f * expf(-q2) * fmaf(q2, q2 - 5.0f, 9.0f) * q.w;
+    s.xy.add(__fmul2_rn(make_float2(gs, gs), rxy));
+    s.z.add(gs * rz);
+}
+
+// Acceleration of Eq. 8 from the pair sum and the surface term; returns |a|.
+__device__ __forceinline__ float lg_finish(const Spheres& S, const RelaxK& K, const float* xh, const float* xl,
+                                           const float* sum, float4* out) {
+    float g3[3];
+    float phi = sdf32(S, xh, xl, g3);
+    float I = surface_lg<float>(phi < 0.0f ? -phi : 0.0f, K.inv_h_f, K.surf_coef_f);
+    float a0 = -K.scale_f * (sum[0] + I * g3[0]);
+    float a1 = -K.scale_f * (sum[1] + I * g3[1]);
+    float a2 = -K.scale_f * (sum[2] + I * g3[2]);
+    *out = make_float4(a0, a1, a2, 0.0f);
+    return sqrtf(a0 * a0 + a1 * a1 + a2 * a2);
+}
+
+// One sweep over the cells of edge h within two of the particle's screens every
+// candidate and accumulates the Laguerre-Gauss gradient of the accepted pairs
+// at once (no list): the single-evaluation form and the skin-0 step.
 template <int R>
 __global__ void __launch_bounds__(256) k_relax_acc_cells(const float4* __restrict__ p32, const float4* __restrict__ lo,
                                                         const int32_t* __restrict__ start, CellGrid g,
@@ -344,61 +418,219 @@ __global__ void __launch_bounds__(256) k_relax_acc_cells(const float4* __restric
         int ci[3];
         for (int a = 0; a < 3; ++a) ci[a] = nb::cell_coord(xi[a], a, g);
         nb::Band band = nb::make_band(absmax, 0.0, rc2, 3);
-        const float thr = band.hi * 1.0001f;
-        // squared distance from the particle to the cell slabs c + d, d in [-R, R], per axis
-        float sd[3][2 * R + 1];
-        int clo[3], chi[3];
-        for (int a = 0; a < 3; ++a) {
-            clo[a] = max(ci[a] - R, 0);
-            chi[a] = min(ci[a] + R, g.n[a] - 1);
-            for (int d = -R; d <= R; ++d) {
-                int c = ci[a] + d;
-                float x = xh[a];
-                float b0 = (float)(g.lo[a] + c * g.size[a]), b1 = (float)(g.lo[a] + (c + 1) * g.size[a]);
-                float gap = 0.0f;
-                if (c > 0 && x < b0) gap = b0 - x;
-                if (c < g.n[a] - 1 && x > b1) gap = x - b1;
-                sd[a][d + R] = gap * gap;
-            }
-        }
-        Kahan<float> s[3];
-        for (int a = 0; a < 3; ++a) s[a].init();
-        for (int cz = clo[2]; cz <= chi[2]; ++cz)
-            for (int cy = clo[1]; cy <= chi[1]; ++cy) {
-                const float syz = sd[2][cz - ci[2] + R] + sd[1][cy - ci[1] + R];
-                if (syz > thr) continue;
-                int rowbase = (cz * g.n[1] + cy) * g.n[0];
-                for (int cx = clo[0]; cx <= chi[0]; ++cx) {
-                    if (syz + sd[0][cx - ci[0] + R] > thr) continue;
-                    int c = rowbase + cx;
-                    int b = start[c], e = start[c + 1];
-                    for (int m = b; m < e; ++m) {
-                        float4 p = p32[m];
-                        int j = __float_as_int(p.w);
-                        if (j == i) continue;
-                        float dx = xh[0] - p.x, dy = xh[1] - p.y, dz = xh[2] - p.z;
-                        float d2s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                        if (d2s > band.hi) continue;
-                        if (d2s >= band.lo && !nb::exact_within(pos, n, 3, xi, j, g, rc2)) continue;
-                        float4 q = lo[m];
-                        float r[3] = {dx + (xl[0] - q.x), dy + (xl[1] - q.y), dz + (xl[2] - q.z)};
-                        float d2 = fmaf(r[2], r[2], fmaf(r[1], r[1], r[0] * r[0]));
-                        float gs = lg_gs<float>(sqrtf(d2) * K.inv_h_f, K.gcoef_f) * q.w;
-                        for (int a = 0; a < 3; ++a) s[a].add(gs * r[a]);
-                    }
-                }
-            }
-        float g3[3];
-        float phi = sdf32(S, xh, xl, g3);
-        float I = surface_lg<float>(phi < 0.0f ? -phi : 0.0f, K.inv_h_f, K.surf_coef_f);
-        float a0 = -K.scale_f * (s[0].value() + I * g3[0]);
-        float a1 = -K.scale_f * (s[1].value() + I * g3[1]);
-        float a2 = -K.scale_f * (s[2].value() + I * g3[2]);
-        acc[i] = make_float4(a0, a1, a2, 0.0f);
-        atomic_max_nonneg(&smax, sqrtf(a0 * a0 + a1 * a1 + a2 * a2));
+        LgSum s;
+        s.init();
+        sweep_cells<R>(xh, ci, g, start, band.hi * 1.0001f, [&](int m) {
+            float4 p = p32[m];
+            int j = __float_as_int(p.w);
+            if (j == i) return;
+            float dx = xh[0] - p.x, dy = xh[1] - p.y, dz = xh[2] - p.z;
+            float d2s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (d2s > band.hi) return;
+            if (d2s >= band.lo && !nb::exact_within(pos, n, 3, xi, j, g, rc2)) return;
+            lg_pair(s, dx, dy, dz, xl, lo[m], K);
+        });
+        float sum[3];
+        s.value(sum);
+        atomic_max_nonneg(&smax, lg_finish(S, K, xh, xl, sum, &acc[i]));
     }
     __syncthreads();
     if (threadIdx.x == 0 && smax) atomicMax(amax, smax);
+}
+
+// ---------------------------------------------------------------- float32 skin lists
+// Positions move by at most h/32 per step, and after the first steps of a run the
+// largest net displacement grows slowly.  The float32 step therefore keeps a list
+// of cut-off 2h + skin (a buffered, Verlet-style list) and rebuilds it only when
+// two particles could have come within 2h unlisted: when twice the largest
+// displacement since the build exceeds the skin.  Every step still decides each
+// listed pair at 2h exactly (float32 screen, float64 inside the rounding band), so
+// the pair set is the one a fresh list gives.
+//
+// Everything runs in the cell order of the last build ("slots"): the list holds
+// slots; the current positions are kept per slot in one 32-byte record (rec[2m]:
+// float32 high parts and the particle index bits; rec[2m+1]: low parts and V), so
+// that a gathered neighbour costs one sector; the build's copies (p32, lo) are the
+// reference for the displacement.  While the list lives the position is that
+// pair, x = xh + xl (a float-float number: ~48 significant bits), updated with
+// float32 operations (GB300's float64 pipe is slow); float64 appears only in the
+// exact decisions inside the rounding band, and x is written back to the caller's
+// float64 array before a rebuild and at the end of the call.  The list is sliced by 32 slots (entry k of slot
+// m at (m / 32) * cap * 32 + k * 32 + m % 32), so a warp reads 128 contiguous bytes
+// per entry.
+//
+// Control words (ctl, float bits as unsigned): [0..1] max |a| of the steps of even
+// and odd index, [2..3] the largest displacement since the build, read by the step
+// of that parity, [4] the longest row found by a build that overflowed the list.
+// Each kernel clears the word of the other parity that the next kernel fills, so a
+// step needs no memset; a build clears them all.
+constexpr int kCtlAmax = 0, kCtlDisp = 2, kCtlNeed = 4;
+
+template <int R>
+__global__ void __launch_bounds__(256) k_relax_skin_build(const float4* __restrict__ p32, const float4* __restrict__ lo,
+                                                         const int32_t* __restrict__ start, CellGrid g,
+                                                         const unsigned* __restrict__ absmax, double rb2,
+                                                         const double* __restrict__ pos, int64_t n, int cap,
+                                                         int32_t* __restrict__ col, int32_t* __restrict__ rowlen,
+                                                         float4* __restrict__ rec, unsigned* __restrict__ ctl, int step,
+                                                         int* __restrict__ flags) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    float4 me = p32[m];
+    rec[2 * m] = me;
+    rec[2 * m + 1] = lo[m];
+    int i = __float_as_int(me.w);
+    float xh[3] = {me.x, me.y, me.z};
+    int ci[3];
+    for (int a = 0; a < 3; ++a) ci[a] = nb::cell_coord(pos[a * n + i], a, g);
+    // superset of the pairs within 2h + skin: the float32 screen's upper edge
+    nb::Band band = nb::make_band(absmax, 0.0, rb2, 3);
+    int32_t* out = col + (m >> 5) * (int64_t)cap * 32 + (m & 31);
+    int len = 0;
+    sweep_cells<R>(xh, ci, g, start, band.hi * 1.0001f, [&](int q) {
+        if (q == (int)m) return;
+        float4 p = p32[q];
+        float dx = xh[0] - p.x, dy = xh[1] - p.y, dz = xh[2] - p.z;
+        float d2s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        if (d2s > band.hi) return;
+        if (len < cap) out[(int64_t)len * 32] = q;
+        ++len;
+    });
+    rowlen[m] = len;
+    if (len > cap) {
+        atomicMax(&ctl[kCtlNeed], (unsigned)len);
+        atomicCAS(&flags[FLAG_CAPACITY], 0, step + 1);
+    }
+}
+
+__device__ __forceinline__ bool relax_halted(const int* flags) {
+    return (flags[FLAG_BAD_INPUT] | flags[FLAG_CAPACITY] | flags[FLAG_STALE]) != 0;
+}
+
+// Step `step`: the acceleration from the list, LANES lanes per slot.  Skips the
+// step (and flags it) when the list is stale, so that every later launch of the
+// batch is a no-op and the host resumes from this step after a rebuild.
+constexpr int kWalkChunk = 8;
+
+template <int LANES>
+__global__ void __launch_bounds__(256, 4) k_relax_walk(const float4* __restrict__ rec,
+                                                   const int32_t* __restrict__ col, const int32_t* __restrict__ rowlen,
+                                                   int cap, int64_t n,
+                                                   const unsigned* __restrict__ absmax, double lmax, double rc2,
+                                                   float skin, Spheres S, RelaxK K,
+                                                   float4* __restrict__ acc, unsigned* __restrict__ ctl, int step,
+                                                   int* __restrict__ flags) {
+    __shared__ unsigned smax;
+    __shared__ int skip;
+    if (threadIdx.x == 0) {
+        smax = 0u;
+        bool halted = relax_halted(flags);
+        float d = __uint_as_float(ctl[kCtlDisp + (step & 1)]);
+        bool stale = !(2.0f * d <= skin);     // also on a non-finite displacement
+        if (!halted && stale) atomicCAS(&flags[FLAG_STALE], 0, step + 1);
+        skip = halted || stale;
+        if (!skip && blockIdx.x == 0) ctl[kCtlDisp + ((step + 1) & 1)] = 0u;
+    }
+    __syncthreads();
+    if (skip) return;
+    int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t m = gt / LANES;
+    int lane = (int)(gt % LANES);
+    bool live = m < n;
+    int64_t mm = live ? m : 0;
+    const F8 own = ldg8((const float*)&rec[2 * mm]);
+    float xh[3] = {own.v[0], own.v[1], own.v[2]}, xl[3] = {own.v[4], own.v[5], own.v[6]};
+    double xi[3];
+    for (int a = 0; a < 3; ++a) xi[a] = (double)xh[a] + (double)xl[a];
+    // positions may have moved by skin/2 since the build's |x| maximum
+    nb::Band band = nb::make_band(absmax, lmax, rc2, 3);
+    const int32_t* rowc = col + (mm >> 5) * (int64_t)cap * 32 + (mm & 31);
+    int len = live ? rowlen[mm] : 0;
+    LgSum s;
+    s.init();
+    // the list entries are read kWalkChunk at a time, the next chunk's loads in
+    // flight while this chunk's records are gathered and summed
+    int qa[kWalkChunk], qb[kWalkChunk];
+    auto fetch = [&](int k0, int* q) {
+#pragma unroll
+        for (int u = 0; u < kWalkChunk; ++u) {
+            int k = k0 + u * LANES;
+            q[u] = k < len ? ldg1_stream(&rowc[(int64_t)k * 32]) : -1;
+        }
+    };
+    fetch(lane, qa);
+    for (int k0 = lane; k0 < len; k0 += kWalkChunk * LANES) {
+        fetch(k0 + kWalkChunk * LANES, qb);
+#pragma unroll
+        for (int u = 0; u < kWalkChunk; ++u) {
+            const int q = qa[u];
+            if (q < 0) break;
+            const F8 r = ldg8((const float*)&rec[2 * q]);
+            float dx = xh[0] - r.v[0], dy = xh[1] - r.v[1], dz = xh[2] - r.v[2];
+            float d2s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (d2s > band.hi) continue;
+            if (d2s >= band.lo && !within_ff(xi, r, rc2)) continue;
+            lg_pair(s, dx, dy, dz, xl, make_float4(r.v[4], r.v[5], r.v[6], r.v[7]), K);
+        }
+#pragma unroll
+        for (int u = 0; u < kWalkChunk; ++u) qa[u] = qb[u];
+    }
+    float sum[3];
+    s.value(sum);
+    for (int a = 0; a < 3; ++a) sum[a] = group_sum<LANES>(sum[a]);
+    if (live && lane == 0) atomic_max_nonneg(&smax, lg_finish(S, K, xh, xl, sum, &acc[m]));
+    __syncthreads();
+    if (threadIdx.x == 0 && smax) atomicMax(&ctl[kCtlAmax + (step & 1)], smax);
+}
+
+// Step `step`: x += a (h/32)/max|a| and the projection back inside the body (the
+// update of Eq. 8 with dt = 0.25 sqrt(h/max|a|)), per slot; refreshes the slot's
+// float32 copies and takes the largest displacement since the build.
+__global__ void __launch_bounds__(256) k_relax_update_skin(int64_t n, const float4* __restrict__ acc,
+                                                          const float4* __restrict__ p32,
+                                                          const float4* __restrict__ lo, float4* __restrict__ rec,
+                                                          Spheres S, RelaxK K,
+                                                          unsigned* __restrict__ ctl, int step,
+                                                          const int* __restrict__ flags) {
+    __shared__ unsigned smax;
+    __shared__ int skip;
+    if (threadIdx.x == 0) {
+        smax = 0u;
+        skip = relax_halted(flags);
+    }
+    __syncthreads();
+    if (skip) return;
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < n) {
+        float am = __uint_as_float(ctl[kCtlAmax + (step & 1)]);
+        const float4 ph = rec[2 * m], pl = rec[2 * m + 1];
+        float xh[3] = {ph.x, ph.y, ph.z}, xl[3] = {pl.x, pl.y, pl.z}, g[3];
+        if (am > 0.0f) {
+            float sc = (K.h_f * 0.03125f) / am;         // a dt^2/2 = a (h/32)/max|a|
+            float4 a = acc[m];
+            ff_add(xh[0], xl[0], a.x * sc);
+            ff_add(xh[1], xl[1], a.y * sc);
+            ff_add(xh[2], xl[2], a.z * sc);
+        }
+        float phi = sdf32(S, xh, xl, g);
+        if (phi > -0.5f * K.dp_f) {
+            float sh = phi + 0.5f * K.dp_f;
+            for (int c = 0; c < 3; ++c) ff_add(xh[c], xl[c], -(sh * g[c]));
+        }
+        float4 b = p32[m], bl = lo[m];
+        rec[2 * m] = make_float4(xh[0], xh[1], xh[2], ph.w);
+        rec[2 * m + 1] = make_float4(xl[0], xl[1], xl[2], pl.w);
+        float ex = (xh[0] - b.x) + (xl[0] - bl.x);
+        float ey = (xh[1] - b.y) + (xl[1] - bl.y);
+        float ez = (xh[2] - b.z) + (xl[2] - bl.z);
+        float d = sqrtf(ex * ex + ey * ey + ez * ez);
+        atomicMax(&smax, isfinite(d) ? __float_as_uint(d) : 0x7f800000u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (smax) atomicMax(&ctl[kCtlDisp + ((step + 1) & 1)], smax);
+        if (blockIdx.x == 0) ctl[kCtlAmax + ((step + 1) & 1)] = 0u;
+    }
 }
 
 __global__ void k_widen_acc(const float4* __restrict__ acc, int64_t n, double* __restrict__ out) {
@@ -454,6 +686,7 @@ RelaxK make_relax_consts(const sph_relax_params* p) {
     K.surf_coef = 2.0 * SPH_PI * lg_alpha(3) / h;
     K.gcoef_f = (float)K.gcoef;
     K.inv_h_f = (float)K.inv_h;
+    K.inv_h2_f = (float)(K.inv_h * K.inv_h);
     K.scale_f = (float)K.scale;
     K.surf_coef_f = (float)K.surf_coef;
     K.h_f = (float)h;
@@ -502,12 +735,6 @@ int ensure_lists(sph_ctx* ctx, int64_t n, int64_t cap, RelaxLists& L) {
 // and cut-off 2h has about 74), regrown on overflow.
 int64_t g_default_per_particle = 128;
 
-template <int LANES>
-void acc32(const float4* geo, int64_t n, const RelaxLists& L, const Spheres& S, const RelaxK& K, float4* acc,
-           unsigned* amax, const int* flags, cudaStream_t s) {
-    k_relax_acc32<LANES><<<grid_for(n * LANES, 256), 256, 0, s>>>(geo, n, L.row_ptr, L.col, S, K, acc, amax, flags);
-}
-
 // float32 acceleration by the cell sweep: cells of edge >= h (half the LG support),
 // the neighbours of a particle within two cells of its own along each axis.
 int acc_cells(sph_ctx* ctx, const sph_relax_params* p, const double* pos, const double* vol, const Spheres& S,
@@ -545,6 +772,111 @@ int read_capacity_flag(sph_ctx* ctx, cudaStream_t s, int* step_failed, int64_t* 
     return SPH_OK;
 }
 
+// Default list capacity of the float32 skin list (entries per slot), regrown on
+// overflow; steps issued between two reads of the status flags.
+constexpr int kSkinCap = 128;
+constexpr int kSkinBatch = 16;   // at most; after a rebuild, about the last list's lifetime
+
+template <int LANES>
+void walk(const float4* rec, const int32_t* col, const int32_t* rowlen, int cap, int64_t n, const unsigned* absmax,
+          double lmax, double rc2, float skin, const Spheres& S, const RelaxK& K, float4* acc, unsigned* ctl, int step,
+          int* flags, cudaStream_t s) {
+    k_relax_walk<LANES><<<grid_for(n * LANES, 256), 256, 0, s>>>(rec, col, rowlen, cap, n, absmax, lmax, rc2, skin, S,
+                                                                 K, acc, ctl, step, flags);
+}
+
+// float32 steps on the skin list.  Steps are issued in batches without host
+// synchronisation; after a batch the flags say whether the list overflowed at a
+// build (nothing ran: regrow and rebuild) or went stale at some step (the steps
+// from there on were no-ops: rebuild at the current positions and resume there).
+int relax_steps_skin(sph_ctx* ctx, const sph_relax_params* p, double* pos, const double* vol, int nsteps,
+                     const Spheres& S, const RelaxK& K, cudaStream_t s) {
+    const int64_t n = p->dom.n;
+    const double h = p->dom.h, rc = p->dom.kappa * h, skin = ctx->relax_skin * h;
+    sph_domain cells = p->dom;
+    cells.kappa = 0.5 * (rc + skin) / h;          // cells of edge >= (2h + skin) / 2
+    const int64_t slots = (n + 31) / 32 * 32;
+    int st = SPH_OK;
+    unsigned* ctl = (unsigned*)sph_scratch(ctx, S_RELAX_AMAX, 64, &st);
+    float4* acc = (float4*)sph_scratch(ctx, S_RELAX_ACC, (size_t)n * 16, &st);
+    float4* rec = (float4*)sph_scratch(ctx, S_MISC0, (size_t)n * 32, &st);
+    float4* lo = (float4*)sph_scratch(ctx, S_MISC1, (size_t)n * 16, &st);
+    int32_t* rowlen = (int32_t*)sph_scratch(ctx, S_RELAX_ROWPTR, (size_t)n * 4, &st);
+    if (st) return st;
+    int64_t have = (int64_t)(ctx->slot_bytes[S_RELAX_COL] / ((size_t)slots * 4));
+    int cap = (int)std::min<int64_t>(std::max<int64_t>(have, kSkinCap), 1 << 16);
+    const float skin_f = (float)(skin * (1.0 - 1e-3));
+    int* hf = (int*)ctx->pinned;
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+    CellList cl;
+    int32_t* col = nullptr;
+    bool build = true, moved = false;     // moved: rec holds steps not yet in pos
+    int done = 0, regrow = 0, built_at = 0, batch = kSkinBatch;
+    while (done < nsteps) {
+        if (build) {
+            col = (int32_t*)sph_scratch(ctx, S_RELAX_COL, (size_t)slots * cap * 4, &st);
+            if (st) return st;
+            int t = sph_timer_begin(ctx, SPH_TIMER_NEIGHBORS, s);
+            if (moved) k_relax_scatter_pos<<<grid_for(n, 256), 256, 0, s>>>(rec, cl.sorted, n, pos);
+            moved = false;
+            st = sph_build_cells(ctx, &cells, pos, s, &cl);
+            if (st) return st;
+            k_relax_pack_lo<<<grid_for(n, 256), 256, 0, s>>>(pos, vol, n, cl.sorted, cl.p32, lo);
+            SPH_CUDA(ctx, cudaMemsetAsync(ctl, 0, 64, s));
+            k_relax_skin_build<2><<<grid_for(n, 256), 256, 0, s>>>(cl.p32, lo, cl.cell_start, cl.grid,
+                                                                   (const unsigned*)cl.band, (rc + skin) * (rc + skin),
+                                                                   pos, n, cap, col, rowlen, rec, ctl, done,
+                                                                   ctx->flags);
+            sph_timer_end(ctx, t, s);
+            SPH_LAUNCH_CHECK(ctx);
+            built_at = done;
+        }
+        const int end = std::min(nsteps, done + batch);
+        const unsigned* absmax = (const unsigned*)cl.band;
+        for (int k = done; k < end; ++k) {
+            int t = sph_timer_begin(ctx, SPH_TIMER_RELAX_ACCEL, s);
+            switch (ctx->lanes[SPH_PASS_RELAX]) {
+                case 1: walk<1>(rec, col, rowlen, cap, n, absmax, skin, rc * rc, skin_f, S, K, acc, ctl, k, ctx->flags, s); break;
+                case 2: walk<2>(rec, col, rowlen, cap, n, absmax, skin, rc * rc, skin_f, S, K, acc, ctl, k, ctx->flags, s); break;
+                case 8: walk<8>(rec, col, rowlen, cap, n, absmax, skin, rc * rc, skin_f, S, K, acc, ctl, k, ctx->flags, s); break;
+                default: walk<4>(rec, col, rowlen, cap, n, absmax, skin, rc * rc, skin_f, S, K, acc, ctl, k, ctx->flags, s); break;
+            }
+            sph_timer_end(ctx, t, s);
+            t = sph_timer_begin(ctx, SPH_TIMER_RELAX_UPDATE, s);
+            k_relax_update_skin<<<grid_for(n, 256), 256, 0, s>>>(n, acc, cl.p32, lo, rec, S, K,
+                                                                 ctl, k, ctx->flags);
+            sph_timer_end(ctx, t, s);
+            SPH_LAUNCH_CHECK(ctx);
+        }
+        moved = moved || end > done;
+        SPH_CUDA(ctx, cudaMemcpyAsync(hf, ctx->flags, FLAG_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPH_CUDA(ctx, cudaMemcpyAsync(hf + 16, ctl + kCtlNeed, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        SPH_CUDA(ctx, cudaStreamSynchronize(s));
+        const int bad = hf[FLAG_BAD_INPUT], over = hf[FLAG_CAPACITY], stale = hf[FLAG_STALE];
+        const int need = hf[16];
+        if (bad || over || stale) SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+        if (bad) return SPH_ERR_ARG;     // non-finite positions (pos holds them)
+        if (over) {                       // the build overflowed: no step ran
+            if (++regrow > 4 || need >= (1 << 16)) return SPH_ERR_CAPACITY;
+            cap = (need + need / 8 + 8 + 7) / 8 * 8;
+            build = true;
+            continue;
+        }
+        if (stale) {                      // steps stale - 1 .. end - 1 were no-ops
+            done = stale - 1;
+            const int life = done - built_at;
+            batch = std::max(2, std::min(kSkinBatch, life + life / 4 + 1));
+            build = true;
+            continue;
+        }
+        done = end;
+        build = false;
+    }
+    if (moved) k_relax_scatter_pos<<<grid_for(n, 256), 256, 0, s>>>(rec, cl.sorted, n, pos);
+    SPH_LAUNCH_CHECK(ctx);
+    return SPH_OK;
+}
+
 }  // namespace
 
 extern "C" int sph_relax_step(sph_ctx* ctx, const sph_relax_params* p, double* pos, const double* vol, int nsteps,
@@ -558,6 +890,8 @@ extern "C" int sph_relax_step(sph_ctx* ctx, const sph_relax_params* p, double* p
     cudaStream_t s = as_stream(stream);
     Spheres S = make_spheres(p);
     RelaxK K = make_relax_consts(p);
+    if (p->precision == SPH_FP32_KAHAN && ctx->relax_skin > 0.0)
+        return relax_steps_skin(ctx, p, pos, vol, nsteps, S, K, s);
     if (p->precision == SPH_FP32_KAHAN) {
         unsigned* amax = (unsigned*)sph_scratch(ctx, S_RELAX_AMAX, 64, &st);
         float4* acc = (float4*)sph_scratch(ctx, S_RELAX_ACC, (size_t)n * 16, &st);
@@ -570,7 +904,7 @@ extern "C" int sph_relax_step(sph_ctx* ctx, const sph_relax_params* p, double* p
             if (st) return st;
             sph_timer_end(ctx, t, s);
             t = sph_timer_begin(ctx, SPH_TIMER_RELAX_UPDATE, s);
-            k_relax_update32<<<grid_for(n, 256), 256, 0, s>>>(pos, n, acc, amax, S, K, nullptr, ctx->flags);
+            k_relax_update32<<<grid_for(n, 256), 256, 0, s>>>(pos, n, acc, amax, S, K, ctx->flags);
             sph_timer_end(ctx, t, s);
             SPH_LAUNCH_CHECK(ctx);
         }
@@ -591,12 +925,9 @@ extern "C" int sph_relax_step(sph_ctx* ctx, const sph_relax_params* p, double* p
     unsigned* amax = (unsigned*)sph_scratch(ctx, S_RELAX_AMAX, 64, &st);
     if (st) return st;
     unsigned long long* amax_d = (unsigned long long*)(amax + 4);
-    bool fp32 = p->precision == SPH_FP32_KAHAN;
-    void* accbuf = sph_scratch(ctx, S_RELAX_ACC, (size_t)n * (fp32 ? 16 : 24), &st);
-    float4* geo = (float4*)sph_scratch(ctx, S_MISC0, (size_t)n * 32, &st);
+    double* acc = (double*)sph_scratch(ctx, S_RELAX_ACC, (size_t)n * 24, &st);
     if (st) return st;
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
-    if (fp32) k_relax_pack<<<grid_for(n, 256), 256, 0, s>>>(pos, vol, n, geo);
     int done = 0;
     for (int attempt = 0; attempt < 8 && done < nsteps; ++attempt) {
         for (int k = done; k < nsteps; ++k) {
@@ -606,27 +937,12 @@ extern "C" int sph_relax_step(sph_ctx* ctx, const sph_relax_params* p, double* p
             sph_timer_end(ctx, t, s);
             SPH_CUDA(ctx, cudaMemsetAsync(amax, 0, 64, s));
             t = sph_timer_begin(ctx, SPH_TIMER_RELAX_ACCEL, s);
-            if (fp32) {
-                float4* acc = (float4*)accbuf;
-                switch (ctx->lanes[SPH_PASS_RELAX]) {
-                    case 1: acc32<1>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
-                    case 2: acc32<2>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
-                    case 8: acc32<8>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
-                    default: acc32<4>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
-                }
-                sph_timer_end(ctx, t, s);
-                t = sph_timer_begin(ctx, SPH_TIMER_RELAX_UPDATE, s);
-                k_relax_update32<<<grid_for(n, 256), 256, 0, s>>>(pos, n, acc, amax, S, K, geo, ctx->flags);
-                sph_timer_end(ctx, t, s);
-            } else {
-                double* acc = (double*)accbuf;
-                k_relax_acc64<<<grid_for(n, 128), 128, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, acc, amax, ctx->flags);
-                k_amax64_exact<<<grid_for(n, 256), 256, 0, s>>>(acc, n, amax, amax_d, ctx->flags);
-                sph_timer_end(ctx, t, s);
-                t = sph_timer_begin(ctx, SPH_TIMER_RELAX_UPDATE, s);
-                k_relax_update64<<<grid_for(n, 256), 256, 0, s>>>(pos, n, acc, amax_d, S, K, ctx->flags);
-                sph_timer_end(ctx, t, s);
-            }
+            k_relax_acc64<<<grid_for(n, 128), 128, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, acc, amax, ctx->flags);
+            k_amax64_exact<<<grid_for(n, 256), 256, 0, s>>>(acc, n, amax, amax_d, ctx->flags);
+            sph_timer_end(ctx, t, s);
+            t = sph_timer_begin(ctx, SPH_TIMER_RELAX_UPDATE, s);
+            k_relax_update64<<<grid_for(n, 256), 256, 0, s>>>(pos, n, acc, amax_d, S, K, ctx->flags);
+            sph_timer_end(ctx, t, s);
             SPH_LAUNCH_CHECK(ctx);
         }
         int failed = 0;
@@ -687,21 +1003,7 @@ extern "C" int sph_relax_accel(sph_ctx* ctx, const sph_relax_params* p, const do
     unsigned* amax = (unsigned*)sph_scratch(ctx, S_RELAX_AMAX, 64, &st);
     if (st) return st;
     SPH_CUDA(ctx, cudaMemsetAsync(amax, 0, 64, s));
-    if (p->precision == SPH_FP64) {
-        k_relax_acc64<<<grid_for(n, 128), 128, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, acc_out, amax, ctx->flags);
-    } else {
-        float4* geo = (float4*)sph_scratch(ctx, S_MISC0, (size_t)n * 32, &st);
-        float4* acc = (float4*)sph_scratch(ctx, S_RELAX_ACC, (size_t)n * 16, &st);
-        if (st) return st;
-        k_relax_pack<<<grid_for(n, 256), 256, 0, s>>>(pos, vol, n, geo);
-        switch (ctx->lanes[SPH_PASS_RELAX]) {
-            case 1: acc32<1>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
-            case 2: acc32<2>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
-            case 8: acc32<8>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
-            default: acc32<4>(geo, n, L, S, K, acc, amax, ctx->flags, s); break;
-        }
-        k_widen_acc<<<grid_for(n, 256), 256, 0, s>>>(acc, n, acc_out);
-    }
+    k_relax_acc64<<<grid_for(n, 128), 128, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, acc_out, amax, ctx->flags);
     SPH_LAUNCH_CHECK(ctx);
     return SPH_OK;
 }

@@ -89,3 +89,93 @@ def test_capacity_regrowth(ctx):
     api.relax_step(ctx, prm, x, cuda(b["vol"]), 2)
     x_o = OR.run(pos, b["vol"], dom, b["spheres"], b["dp"], 2)
     assert np.max(np.abs(host(x) - x_o)) < 1e-12
+
+
+def _run(ctx, prm, pos, vol, k):
+    x = cuda(pos).clone()
+    api.relax_step(ctx, prm, x, cuda(vol), k)
+    return host(x)
+
+
+@pytest.mark.parametrize("skin,lanes", [(0.2, 4), (0.2, 1), (0.01, 2), (1.0, 8), (0.0, 4)])
+def test_skin_list_steps_track_the_oracle(ctx, skin, lanes):
+    # Runs of k and k - 1 steps from the same start are bitwise the same up to
+    # step k - 1, so x_k - step(x_(k-1)) tests step k on the list as it stands
+    # then: built at the start, rebuilt after the first step's projection, or
+    # (skin 0.01) rebuilt almost every step; skin 1.0 (cut-off 3h, ~250 entries
+    # per row) also overflows the default capacity of 128 and regrows.
+    b, pos = _body(seed=5)
+    dom = odom(b["domain"])
+    prm = api.relax_params(b["domain"], b["spheres"], b["dp"], precision=api.SPH_FP32_KAHAN)
+    ctx.set_relax_skin(skin)
+    ctx.set_lanes(api.SPH_PASS_RELAX, lanes)
+    try:
+        prev = pos
+        for k in range(1, 5):
+            x = _run(ctx, prm, pos, b["vol"], k)
+            x_o = OR.step(prev, b["vol"], dom, b["spheres"], b["dp"])
+            assert np.max(np.abs(x - x_o)) < 1e-3 * b["h"] / 32.0 + 1e-12, (skin, lanes, k)
+            prev = x
+        again = _run(ctx, prm, pos, b["vol"], 4)
+        assert np.array_equal(again, prev)
+    finally:
+        ctx.set_relax_skin(0.2)
+        ctx.set_lanes(api.SPH_PASS_RELAX, 1)
+
+
+def test_skin_list_rebuilds_only_when_stale(ctx):
+    b, pos = _body(seed=5)
+    prm = api.relax_params(b["domain"], b["spheres"], b["dp"], precision=api.SPH_FP32_KAHAN)
+    builds = {}
+    try:
+        for skin in (0.005, 0.5):
+            ctx.set_relax_skin(skin)
+            ctx.timing(True)
+            _run(ctx, prm, pos, b["vol"], 24)
+            builds[skin] = ctx.timer(api.SPH_TIMER_NEIGHBORS)[1]
+            ctx.timing(False)
+    finally:
+        ctx.set_relax_skin(0.2)
+    # a step moves no particle by more than h/32 (projection aside), so a skin of
+    # 0.005h goes stale after every step or so, and one of 0.5h lasts several steps
+    assert builds[0.005] >= 12
+    assert 1 <= builds[0.5] <= builds[0.005] // 3
+
+
+def test_skin_list_full_size_sampled(ctx):
+    # the 972k-particle body at dp = 1/128 as the benchmark runs it: the fifth step
+    # of a five-step call (on a list built before step 1) against the oracle's
+    # Eq. 7 at 256 sampled interior particles, neighbours found by brute force
+    from paper_2405_05155_gb300 import learned
+    b, prm, pos, vol = learned.body_on_device(ctx, 0, 1.0 / 128.0)
+    x4 = pos.clone()
+    api.relax_step(ctx, prm, x4, vol, 4)
+    x5 = x4.clone()
+    api.relax_step(ctx, prm, x5, vol, 1)     # step 5 of a fresh call: fresh list
+    y5 = pos.clone()
+    api.relax_step(ctx, prm, y5, vol, 5)     # step 5 on the list of the call
+    X4, X5, Y5, V = host(x4), host(x5), host(y5), host(vol)
+    h = b["h"]
+    dom = odom(b["domain"])
+    phi, _ = OR.sdf_spheres(X4, b["spheres"])
+    rng = np.random.default_rng(11)
+    rows = np.sort(rng.choice(np.flatnonzero(phi < -2.5 * h), 256, replace=False))
+    n = X4.shape[1]
+    lens = np.zeros(n, np.int64)
+    cols = []
+    for i in rows:
+        d = X4 - X4[:, i:i + 1]
+        d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2]
+        nbr = np.flatnonzero(d2 <= dom.rc2)
+        nbr = nbr[nbr != i]
+        lens[i] = nbr.size
+        cols.append(nbr)
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    col = np.concatenate(cols).astype(np.int32)
+    a = OR.acceleration(X4, V, rp, col, dom, b["spheres"])[:, rows]
+    for X in (X5, Y5):
+        disp = X[:, rows] - X4[:, rows]
+        c = float(np.sum(disp * a) / np.sum(a * a))   # (h/32)/max|a| over all particles
+        assert c > 0.0 and c <= (h / 32.0) / np.max(np.linalg.norm(a, axis=0)) * (1 + 1e-4)
+        assert rel_l2(disp, c * a) < 1e-4
