@@ -109,11 +109,21 @@ int sph_get_lanes(const sph_ctx* ctx, int pass);
  * many as the plan needs, within 96 KB); tiles with more read their neighbours from
  * global memory.  A launch-shape setting, like the lanes: results do not depend on it. */
 int sph_set_stage_cap(sph_ctx* ctx, int cap);
-/* Planned passes: on runs the persistent form (one block per SM, the next tile's
- * pair entries and neighbours copied into shared memory by TMA while the current
- * tile computes) when its buffers fit in shared memory; off (default) runs one
- * block per tile.  A launch-shape setting: results do not depend on it. */
-int sph_set_tile_pipeline(sph_ctx* ctx, int on);
+/* Planned TL passes, how pair entries reach a block (a launch-shape setting:
+ * results do not depend on it):
+ *   SPH_PIPE_STREAM     one block per tile, entries streamed from global memory
+ *                       (default: the fastest measured);
+ *   SPH_PIPE_PERSISTENT one block per SM, the next tile's entries and neighbours
+ *                       copied into shared memory by TMA while the current tile
+ *                       computes (when its buffers fit);
+ *   SPH_PIPE_BULK       one block per tile; the deformation pass copies the tile's
+ *                       whole entry block into shared memory with one TMA bulk copy
+ *                       while it stages the neighbours.
+ * SPH_ERR_ARG for any other mode. */
+#define SPH_PIPE_STREAM     0
+#define SPH_PIPE_PERSISTENT 1
+#define SPH_PIPE_BULK       2
+int sph_set_tile_pipeline(sph_ctx* ctx, int mode);
 
 /* Per-kernel device timing (not part of the paper: measurement support).
  * sph_timing_enable(ctx, 1) clears the counters and makes the step entry points
@@ -418,7 +428,7 @@ int sph_tlsph_plan(sph_ctx* ctx, const sph_tlsph_params* prm, sph_tlsph_state* s
 int sph_tlsph_plan_bytes(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_state* st,
                          int64_t* bytes_host, void* stream);
 /* packed float32 (rd, H32, u32) -> float64 (v, H, x = r0 + u).  After steps of
- * the persistent planned form (sph_set_tile_pipeline) it synchronises the stream and
+ * the persistent or bulk planned forms (sph_set_tile_pipeline) it synchronises the stream and
  * returns SPH_ERR_TIMEOUT if a bounded device wait expired since the previous unpack
  * (the results are then not valid). */
 int sph_tlsph_unpack(sph_ctx* ctx, const sph_tlsph_params* prm,

@@ -11,7 +11,8 @@ from . import _lib as L
 from ._lib import (SPH_FP32_KAHAN, SPH_FP64, SPH_FUSED, SPH_LAGUERRE_GAUSS,  # noqa: F401
                    SPH_NEO_HOOKEAN, SPH_SVK, SPH_TWO_PASS, SPH_WENDLAND_C2, SPH_PASS_BATCHED,
                    SPH_PASS_EULERIAN, SPH_PASS_RELAX, SPH_PASS_TLSPH, SPH_TIMER_NEIGHBORS,
-                   SPH_TIMER_RELAX_ACCEL, SPH_TIMER_RELAX_UPDATE)
+                   SPH_TIMER_RELAX_ACCEL, SPH_TIMER_RELAX_UPDATE, SPH_PIPE_STREAM, SPH_PIPE_PERSISTENT,
+                   SPH_PIPE_BULK)
 
 NSYM = {2: 3, 3: 6}
 
@@ -63,8 +64,9 @@ class Context:
         except Exception:
             pass
 
-    def set_tile_pipeline(self, on):
-        L.check("sph_set_tile_pipeline", self.lib.sph_set_tile_pipeline(self.h, 1 if on else 0), self.h)
+    def set_tile_pipeline(self, mode):
+        """How the planned TL passes get their pair entries: SPH_PIPE_STREAM, _PERSISTENT or _BULK."""
+        L.check("sph_set_tile_pipeline", self.lib.sph_set_tile_pipeline(self.h, int(mode)), self.h)
 
     def set_stage_cap(self, cap):
         L.check("sph_set_stage_cap", self.lib.sph_set_stage_cap(self.h, int(cap)), self.h)

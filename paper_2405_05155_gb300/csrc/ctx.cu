@@ -78,9 +78,9 @@ extern "C" int sph_set_relax_skin(sph_ctx* ctx, double skin_over_h) {
     return SPH_OK;
 }
 
-extern "C" int sph_set_tile_pipeline(sph_ctx* ctx, int on) {
-    if (!ctx) return SPH_ERR_ARG;
-    ctx->no_pipe = (on == 0);
+extern "C" int sph_set_tile_pipeline(sph_ctx* ctx, int mode) {
+    if (!ctx || mode < SPH_PIPE_STREAM || mode > SPH_PIPE_BULK) return SPH_ERR_ARG;
+    ctx->tile_pipe = mode;
     return SPH_OK;
 }
 

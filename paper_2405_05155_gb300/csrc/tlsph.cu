@@ -11,6 +11,8 @@
 // E = (H + H^T + H^T H)/2, neo-Hookean S = C^-1 (2 G E + lambda ln J I) with
 // ln J = log1p(det(I+H) - 1) expanded in H), which keeps float32 accurate for
 // the small strains of a solid.
+#include <algorithm>
+
 #include "common.cuh"
 #include "tiles.cuh"
 #include "async.cuh"
@@ -554,12 +556,17 @@ __global__ void __launch_bounds__(256, 4) k_tl_defo32(const float* __restrict__ 
 // the tile's distinct neighbours.  A block is one tile, one thread per row: it
 // stages the neighbours' M_j (momentum) or v_j (deformation) in shared memory and
 // its warps read the pair entries 512 contiguous bytes at a time.
+// Polls of a bounded mbarrier wait before a block gives up (FLAG_TIMEOUT).
+constexpr uint32_t kWaitPolls = 1u << 22;
+
 struct GeoArgs {
     const int32_t* tile_m;
     const int64_t* tile_so;
     const int32_t* uidx;
     const float4* geo;
     int mcap;
+    const int32_t* tile_e;   // bulk form: entries per tile
+    int ecap;                // bulk form: most entries a block copies into shared memory (0: none)
 };
 
 // Pair entries of the tile plan: w = grad0 W_ij V0_j in float64, stored float32,
@@ -743,12 +750,15 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32g(const float* __restr
     for (int a = 0; a < DIM; ++a) vrec[a] = fx ? 0.0f : vown[a] + K.dt * (tot[a] * K.inv_rho0);
 }
 
-template <int DIM, int OUT>
-__global__ void __launch_bounds__(kTileRows, 6) k_tl_defo32g(const float* __restrict__ RD, float* __restrict__ RM,
-                                                             const int64_t* __restrict__ row_ptr, int64_t n,
-                                                             TLK<float> K, GeoArgs A, const float* __restrict__ B0,
-                                                             float* __restrict__ H, float* __restrict__ u,
-                                                             double* __restrict__ dFdt) {
+// BULK: thread 0 copies the tile's whole entry block into shared memory with one
+// TMA bulk copy (completion on an mbarrier, bounded wait) while the block stages
+// the neighbours, so each block has its entire entry stream in flight at once;
+// tiles with more than A.ecap entries stream them from global memory as without.
+template <int DIM, int OUT, bool BULK>
+__global__ void __launch_bounds__(kTileRows, BULK ? 3 : 6) k_tl_defo32g(
+    const float* __restrict__ RD, float* __restrict__ RM, const int64_t* __restrict__ row_ptr, int64_t n,
+    TLK<float> K, GeoArgs A, const float* __restrict__ B0, float* __restrict__ H, float* __restrict__ u,
+    double* __restrict__ dFdt, int* __restrict__ flags) {
     constexpr int NS = DIM == 2 ? 3 : 6;
     extern __shared__ __align__(16) unsigned char tl_smem[];
     float4* sp = reinterpret_cast<float4*>(tl_smem);
@@ -757,6 +767,18 @@ __global__ void __launch_bounds__(kTileRows, 6) k_tl_defo32g(const float* __rest
     const int64_t i = i0 + threadIdx.x;
     const bool active = i < n;
     const int64_t ii = active ? i : i0;
+    float4* eb = sp + A.mcap;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(eb + A.ecap);
+    const int te = BULK ? A.tile_e[tile] : 0;
+    const bool bulk = BULK && te > 0 && te <= A.ecap;
+    if (BULK && threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+        if (bulk) {
+            mbar_arrive_expect_tx(bar, (uint32_t)te * 16u);
+            tma_load_1d(eb, A.geo + A.tile_so[tile], (uint32_t)te * 16u, bar);
+        }
+    }
     const int64_t P0 = row_ptr[i0];
     const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
     const int m = A.tile_m[tile];
@@ -771,6 +793,14 @@ __global__ void __launch_bounds__(kTileRows, 6) k_tl_defo32g(const float* __rest
 #pragma unroll
     for (int a = 0; a < DIM; ++a) uold[a] = OUT == OUT_RATES ? 0.0f : u[a * n + ii];
     const bool staged = stage_neighbours<1, 8>(RD, n, P0, m, A, sp);
+    if (bulk) {
+        const bool late = !mbar_wait_bounded(bar, 0, kWaitPolls);
+        if (__syncthreads_or(late)) {      // block-uniform: the copy never completed
+            if (threadIdx.x == 0) atomicExch(&flags[FLAG_TIMEOUT], 1);
+            mbar_wait_bounded(bar, 0, kWaitPolls);
+            return;
+        }
+    }
     const uint32_t bi = __float_as_uint(me.v[DIM]);
     const float2 nv01 = make_float2(-me.v[4], -me.v[5]);
     const float nv2 = -me.v[6];
@@ -792,7 +822,15 @@ __global__ void __launch_bounds__(kTileRows, 6) k_tl_defo32g(const float* __rest
             l22.add(dv2 * e.z);
         }
     };
-    if (staged) {
+    if (bulk && staged) {
+        const float4* gs = eb + threadIdx.x;
+#pragma unroll 4
+        for (int k = 0; k < len; ++k) {
+            float4 e = gs[k * kTileRows];
+            int s = min(max(__float_as_int(e.w), 0), max(m - 1, 0));
+            pair(e, sp[s]);
+        }
+    } else if (staged) {
 #pragma unroll 4
         for (int k = 0; k < len; ++k) {
             float4 e = ldg4_stream(g + (int64_t)k * kTileRows);
@@ -801,7 +839,7 @@ __global__ void __launch_bounds__(kTileRows, 6) k_tl_defo32g(const float* __rest
         }
     } else {
         for (int k = 0; k < len; ++k) {
-            float4 e = ldg4_stream(g + (int64_t)k * kTileRows);
+            float4 e = bulk ? eb[threadIdx.x + k * kTileRows] : ldg4_stream(g + (int64_t)k * kTileRows);
             int s = min(max(__float_as_int(e.w), 0), max(m - 1, 0));
             int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
             pair(e, __ldg(reinterpret_cast<const float4*>(RD + 8 * j) + 1));
@@ -946,8 +984,6 @@ __device__ __forceinline__ TileHdr tile_hdr(const GeoArgs& A, const int64_t* __r
     }
     return h;
 }
-
-constexpr uint32_t kWaitPolls = 1u << 22;
 
 template <int NPL>
 struct PipeSmem {
@@ -1281,7 +1317,7 @@ struct TlPlan {
     GeoArgs mom, defo;
     PipeArgs pmom, pdefo;
     size_t mom_bytes, defo_bytes, pmom_bytes, pdefo_bytes;
-    bool on, pipe_mom, pipe_defo;
+    bool on, pipe_mom, pipe_defo, bulk_defo;
     int grid;
 };
 
@@ -1291,7 +1327,7 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
     t.mom = GeoArgs{nullptr, nullptr, nullptr, nullptr, 0};
     t.defo = t.mom;
     t.mom_bytes = t.defo_bytes = t.pmom_bytes = t.pdefo_bytes = 0;
-    t.pipe_mom = t.pipe_defo = false;
+    t.pipe_mom = t.pipe_defo = t.bulk_defo = false;
     t.grid = 0;
     if (!t.on) return t;
     TilePlan tp = tile_plan_view(st->plan, n, st->plan_nnz);
@@ -1308,8 +1344,21 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
     t.pdefo = PipeArgs{tp.ntiles, gw, md, (md + 3) & ~3};
     t.pmom_bytes = pipe_smem_bytes(t.pmom, npl);
     t.pdefo_bytes = pipe_smem_bytes(t.pdefo, 1);
-    t.pipe_mom = !ctx->no_pipe && t.pmom_bytes <= limit;
-    t.pipe_defo = !ctx->no_pipe && t.pdefo_bytes <= limit;
+    const bool persistent = ctx->tile_pipe == SPH_PIPE_PERSISTENT;
+    t.pipe_mom = persistent && t.pmom_bytes <= limit;
+    t.pipe_defo = persistent && t.pdefo_bytes <= limit;
+    // bulk form of the deformation pass: three blocks per SM, each with its staged
+    // neighbours and up to ecap entries in shared memory
+    t.bulk_defo = ctx->tile_pipe == SPH_PIPE_BULK;
+    if (t.bulk_defo) {
+        const size_t per_block = (227 * 1024) / 3 - 1024;
+        int64_t room = ((int64_t)per_block - (int64_t)md * 16 - 16) / 16;
+        int64_t want = (int64_t)kTileRows * st->plan_maxrow;
+        t.defo.tile_e = tp.tile_e;
+        t.defo.ecap = (int)std::max<int64_t>(0, std::min(room, want));
+        t.bulk_defo = t.defo.ecap > 0;
+        t.defo_bytes = (size_t)(md + t.defo.ecap) * 16 + 16;
+    }
     int64_t g = ctx->num_sms > 0 ? ctx->num_sms : 1;
     t.grid = (int)(g < tp.ntiles ? g : tp.ntiles);
     return t;
@@ -1359,10 +1408,14 @@ void tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph
             f<<<gp, b, tp.pdefo_bytes, s>>>(st->rd, st->rm, st->row_ptr, n, K, tp.defo, tp.pdefo, st->B32, st->H32,
                                             st->u32, out == OUT_RATES ? r2 : nullptr, ctx->flags);
         } else {
-            auto* f = out == OUT_RATES ? k_tl_defo32g<DIM, OUT_RATES> : k_tl_defo32g<DIM, OUT_STEP>;
+            auto* f = tp.bulk_defo ? (out == OUT_RATES ? k_tl_defo32g<DIM, OUT_RATES, true>
+                                                       : k_tl_defo32g<DIM, OUT_STEP, true>)
+                                   : (out == OUT_RATES ? k_tl_defo32g<DIM, OUT_RATES, false>
+                                                       : k_tl_defo32g<DIM, OUT_STEP, false>);
+            if (tp.bulk_defo) ctx->waits_pending = true;
             sph_allow_dynamic_smem((const void*)f);
             f<<<g, b, tp.defo_bytes, s>>>(st->rd, st->rm, st->row_ptr, n, K, tp.defo, st->B32, st->H32, st->u32,
-                                          out == OUT_RATES ? r2 : nullptr);
+                                          out == OUT_RATES ? r2 : nullptr, ctx->flags);
         }
     }
 }

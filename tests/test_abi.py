@@ -67,3 +67,18 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.BatchCase) == 96 + 8 + 8 + 2 * 4
     assert ctypes.sizeof(_lib.BatchState) == 4 * 8
     assert ctypes.sizeof(_lib.RelaxParams) == 80 + 3 * 8 + 16 + 64 * 8
+
+
+def test_header_constants_match_the_binding():
+    import re
+    from paper_2405_05155_gb300 import _lib
+    hdr = open(os.path.join(ROOT, "include", "sph.h")).read()
+    defs = dict(re.findall(r"^#define\s+(SPH_[A-Z0-9_]+)\s+(-?\d+)\b", hdr, flags=re.M))
+    checked = 0
+    for name, val in defs.items():
+        if hasattr(_lib, name):
+            assert getattr(_lib, name) == int(val), name
+            checked += 1
+    for name in ("SPH_PIPE_STREAM", "SPH_PIPE_PERSISTENT", "SPH_PIPE_BULK", "SPH_PASS_RELAX", "SPH_TIMER_NEIGHBORS"):
+        assert name in defs and hasattr(_lib, name), name
+    assert checked >= 10

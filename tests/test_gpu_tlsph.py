@@ -190,12 +190,12 @@ def test_tile_plan_is_exact(ctx):
 
 @pytest.mark.parametrize("dp", [0.005, 0.002])
 def test_planned_pass_forms_agree_bitwise(ctx, dp):
-    # the persistent and the one-block-per-tile forms, each with its neighbours staged
-    # in shared memory or (tiles over the stage capacity) read from global memory: the
-    # same arithmetic in the same order
+    # the persistent, the streaming and the bulk-copy forms, each with its neighbours
+    # staged in shared memory or (tiles over the stage capacity) read from global
+    # memory: the same arithmetic in the same order
     s = _setup(ctx, dp=dp)
     ref = None
-    for pipe in (True, False):
+    for pipe in (api.SPH_PIPE_PERSISTENT, api.SPH_PIPE_STREAM, api.SPH_PIPE_BULK):
         for cap in (0, 16):
             ctx.set_tile_pipeline(pipe)
             ctx.set_stage_cap(cap)
@@ -208,7 +208,7 @@ def test_planned_pass_forms_agree_bitwise(ctx, dp):
                 ref = got
             else:
                 assert all(torch.equal(p, q) for p, q in zip(got, ref)), (pipe, cap)
-    ctx.set_tile_pipeline(False)
+    ctx.set_tile_pipeline(api.SPH_PIPE_STREAM)
     ctx.set_stage_cap(0)
 
 
