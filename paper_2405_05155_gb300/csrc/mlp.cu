@@ -9,6 +9,7 @@
 // for the backward pass).  Reductions (bias gradients, loss) use a fixed order.
 #include <cuda_bf16.h>
 #include "common.cuh"
+#include "gelu.cuh"
 #include "neighbors.cuh"
 
 namespace {
@@ -26,10 +27,8 @@ static_assert(NPARAM == SPH_MLP_NPARAM, "parameter layout");
 constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
 enum { EPI_NONE = 0, EPI_BIAS = 1, EPI_BIAS_GELU = 2 };
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad_f(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.3989422804014327f;
-}
+__device__ __forceinline__ float gelu_f(float z) { return gelu_as::gelu(z); }
+__device__ __forceinline__ float gelu_grad_f(float z) { return gelu_as::gelu_grad(z); }
 
 __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
     asm volatile(

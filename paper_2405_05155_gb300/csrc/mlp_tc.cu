@@ -22,6 +22,7 @@
 // 8-row groups 2048 bytes apart (stride byte offset).
 #include <cuda_bf16.h>
 #include "common.cuh"
+#include "gelu.cuh"
 #include "async.cuh"
 
 namespace {
@@ -139,7 +140,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu(float z) { return gelu_as::gelu(z); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -207,7 +208,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const float* __r
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
     uint32_t phase = 0;
     bool ok = true;
-    for (int64_t tile = (int64_t)blockIdx.x * kGroups + g; tile * kRows < n; tile += (int64_t)gridDim.x * kGroups) {
+    const int64_t tstride = (int64_t)gridDim.x * kGroups;
+    for (int64_t tile = (int64_t)blockIdx.x * kGroups + g; tile * kRows < n; tile += tstride) {
         // features (float32) -> bfloat16 operand; rows past n are zero
         {
             const int r = gtid >> 1, k0 = (gtid & 1) * 64;
