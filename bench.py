@@ -545,20 +545,31 @@ def run_gpu(args):
     ncu_traffic = {"tl_momentum_pass": 446.3e6, "tl_deformation_pass": 509.1e6}
     traffic = args.traffic if args.traffic is not None else ncu_traffic.get(dominant[0])
 
-    # end to end through the C ABI with host buffers: per step, copy the float64
-    # state (x, v, F - I) from pinned host memory, pack, step, unpack, copy back
+    # end to end through the C ABI with the float64 state (x, v, F - I) in host memory:
+    # every step reads it from the host, packs, steps, unpacks and writes it back.
+    # (a) the state in mapped page-locked host buffers (sph_host_alloc): pack reads and
+    #     unpack writes them in place over the host link (NVLink-C2C);
+    # (b) the state in pinned host tensors, moved by cudaMemcpyAsync around pack/unpack.
     e2e_steps = min(K, args.e2e_steps)
     sol_e = _solid(api, ctx, s16, api.SPH_FP32_KAHAN)
     hx = sol_e.x.cpu().pin_memory()
     hv = sol_e.v.cpu().pin_memory()
     hH = sol_e.H.cpu().pin_memory()
     h2d = (hx.numel() + hv.numel() + hH.numel()) * 8
-    torch.cuda.synchronize()
-    _barrier(world)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for _ in range(e2e_steps):
+
+    def _timed(body):
+        torch.cuda.synchronize()
+        _barrier(world)
+        t0.record()
+        for _ in range(e2e_steps):
+            body()
+        t1.record()
+        torch.cuda.synchronize()
+        return _max_over_ranks(t0.elapsed_time(t1), world)
+
+    def _with_copies():
         sol_e.x.copy_(hx, non_blocking=True)
         sol_e.v.copy_(hv, non_blocking=True)
         sol_e.H.copy_(hH, non_blocking=True)
@@ -568,10 +579,25 @@ def run_gpu(args):
         hx.copy_(sol_e.x, non_blocking=True)
         hv.copy_(sol_e.v, non_blocking=True)
         hH.copy_(sol_e.H, non_blocking=True)
-    t1.record()
-    torch.cuda.synchronize()
-    e2e_ms = _max_over_ranks(t0.elapsed_time(t1), world)
+
+    e2e_copy_ms = _timed(_with_copies)
+    mapped = [api.HostArray(t.shape) for t in (sol_e.x, sol_e.v, sol_e.H)]
+    for m, t in zip(mapped, (hx, hv, hH)):
+        m.t.copy_(t)
+    sol_m = _solid(api, ctx, s16, api.SPH_FP32_KAHAN)
+    sol_m.st.x, sol_m.st.v, sol_m.st.H = mapped[0].dev, mapped[1].dev, mapped[2].dev
+
+    def _in_place():
+        sol_m.pack()
+        sol_m.step(1)
+        sol_m.unpack()
+
+    e2e_ms = _timed(_in_place)
     e2e_value = _sum_over_ranks(pairs_step * e2e_steps, world) / (e2e_ms * 1e-3)
+    e2e_copy_value = _sum_over_ranks(pairs_step * e2e_steps, world) / (e2e_copy_ms * 1e-3)
+    e2e_ok = all(bool(torch.isfinite(m.t).all()) for m in mapped)
+    for m in mapped:
+        m.close()
 
     workloads = {}
     if not args.headline_only:
@@ -614,9 +640,13 @@ def run_gpu(args):
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                          "algorithmic_bytes_per_launch": dominant[1]},
             "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
-                    "what": "per step: float64 (x, v, F-I) pinned host -> device, pack, one step, unpack, "
-                            "device -> pinned host, through the C ABI"},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d, "state_finite": e2e_ok,
+                    "what": "per step, through the C ABI: the float64 state (x, v, F-I) in mapped page-locked "
+                            "host buffers (sph_host_alloc) read in place by pack over NVLink-C2C, one step, "
+                            "written back in place by unpack",
+                    "with_memcpy": {"value": e2e_copy_value, "ms_per_step": e2e_copy_ms / e2e_steps,
+                                    "what": "the same state in pinned host tensors, cudaMemcpyAsync to the "
+                                            "device, pack, one step, unpack, cudaMemcpyAsync back"}},
             "gpu_launches": n_mom + n_def + n_str,
             "clocks": clk,
             "workloads": workloads,

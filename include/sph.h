@@ -94,6 +94,19 @@ const char* sph_status_string(int status);
 /* The cudaError_t value of the most recent failed CUDA call in this context. */
 int sph_last_cuda_error(const sph_ctx* ctx);
 
+/* Host buffers the device reads and writes in place (not part of the paper: the
+ * end-to-end path with host state).  sph_host_alloc allocates `bytes` of page-
+ * locked host memory mapped into the device address space (cudaHostAlloc with
+ * cudaHostAllocMapped | cudaHostAllocPortable) and returns the host pointer in
+ * *host and the pointer device code uses in *dev.  Any array argument of the
+ * entry points may be such a device pointer: the kernels then move the data over
+ * the host link themselves (NVLink-C2C on Grace-Blackwell), with no separate copy.
+ * sph_host_free releases a buffer of sph_host_alloc.  SPH_ERR_ARG for null
+ * pointers or bytes == 0; SPH_ERR_CUDA if the runtime refuses (nothing is
+ * allocated then). */
+int sph_host_alloc(size_t bytes, void** host, void** dev);
+int sph_host_free(void* host);
+
 /* Launch shape of the float32 pair passes: `lanes` (1, 2, 4 or 8) consecutive
  * lanes of a warp share one particle's neighbour row (for SPH_PASS_RELAX: the
  * row of the float32 relaxation list) and combine their partial

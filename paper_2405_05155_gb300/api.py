@@ -94,6 +94,42 @@ class Context:
         return ms.value, cnt.value
 
 
+class HostArray:
+    """Page-locked host memory mapped into the device address space (sph_host_alloc).
+
+    ``t`` is a CPU tensor over the buffer; ``dev`` is the pointer device code uses,
+    which any array field of a state struct may hold: the kernels then read and write
+    the host buffer in place over the host link, with no separate copy."""
+
+    def __init__(self, shape, dtype=torch.float64):
+        import numpy as np
+        self._lib = L.load()
+        self.shape = tuple(int(x) for x in shape)
+        count = 1
+        for x in self.shape:
+            count *= x
+        npdt = {torch.float64: np.float64, torch.float32: np.float32}[dtype]
+        nbytes = count * np.dtype(npdt).itemsize
+        h, d = ctypes.c_void_p(), ctypes.c_void_p()
+        L.check("sph_host_alloc", self._lib.sph_host_alloc(nbytes, ctypes.byref(h), ctypes.byref(d)))
+        self._host = h.value
+        self.dev = d.value
+        buf = (ctypes.c_char * nbytes).from_address(self._host)
+        self.t = torch.from_numpy(np.frombuffer(buf, dtype=npdt).reshape(self.shape))
+
+    def close(self):
+        if self._host:
+            self.t = None
+            L.check("sph_host_free", self._lib.sph_host_free(self._host))
+            self._host = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def kernel_eval(kernel, dim, h, kappa, precision, r):
     lib = L.load()
     r = r.contiguous()

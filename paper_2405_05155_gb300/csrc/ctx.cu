@@ -96,6 +96,31 @@ int sph_take_timeout(sph_ctx* ctx, cudaStream_t s) {
     return SPH_OK;
 }
 
+extern "C" int sph_host_alloc(size_t bytes, void** host, void** dev) {
+    if (!host || !dev || bytes == 0) return SPH_ERR_ARG;
+    *host = nullptr;
+    *dev = nullptr;
+    void* h = nullptr;
+    if (cudaHostAlloc(&h, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return SPH_ERR_CUDA;
+    }
+    void* d = nullptr;
+    if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(h);
+        return SPH_ERR_CUDA;
+    }
+    *host = h;
+    *dev = d;
+    return SPH_OK;
+}
+
+extern "C" int sph_host_free(void* host) {
+    if (!host) return SPH_ERR_ARG;
+    return cudaFreeHost(host) == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
 extern "C" int sph_set_stage_cap(sph_ctx* ctx, int cap) {
     if (!ctx || cap < 0) return SPH_ERR_ARG;
     ctx->stage_cap = cap;

@@ -82,3 +82,10 @@ def test_header_constants_match_the_binding():
     for name in ("SPH_PIPE_STREAM", "SPH_PIPE_PERSISTENT", "SPH_PIPE_BULK", "SPH_PASS_RELAX", "SPH_TIMER_NEIGHBORS"):
         assert name in defs and hasattr(_lib, name), name
     assert checked >= 10
+
+
+def test_host_alloc_argument_checks(lib):
+    h, d = ctypes.c_void_p(), ctypes.c_void_p()
+    assert lib.sph_host_alloc(ctypes.c_size_t(0), ctypes.byref(h), ctypes.byref(d)) == _lib.SPH_ERR_ARG
+    assert lib.sph_host_alloc(ctypes.c_size_t(64), None, ctypes.byref(d)) == _lib.SPH_ERR_ARG
+    assert lib.sph_host_free(None) == _lib.SPH_ERR_ARG

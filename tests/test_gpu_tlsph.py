@@ -247,3 +247,30 @@ def test_full_size_plate_sampled(ctx):
     Fd_o = OT.deformation_rate(s["r0"], s["vol"], s["v"], s["B0_h"], rp_s, col_s, s["prm"].dom).reshape(n, 9).T
     assert rel_l2(a[:, rows], a_o[:, rows]) < 1e-5
     assert rel_l2(Fd[:, rows], Fd_o[:, rows]) < 1e-5
+
+
+def test_state_in_mapped_host_memory(ctx):
+    # the float64 state (x, v, F - I) in mapped page-locked host buffers, read and
+    # written in place by pack and unpack: the same results, bit for bit, as the
+    # state in device memory
+    s = _setup(ctx, dp=0.005)
+    ref = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
+    sol = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
+    mapped = [api.HostArray(t.shape) for t in (sol.x, sol.v, sol.H)]
+    try:
+        for m, t in zip(mapped, (sol.x, sol.v, sol.H)):
+            m.t.copy_(t.cpu())
+        sol.st.x, sol.st.v, sol.st.H = mapped[0].dev, mapped[1].dev, mapped[2].dev
+        for _ in range(3):
+            sol.pack()
+            sol.step(2)
+            sol.unpack()
+            ref.pack()
+            ref.step(2)
+            ref.unpack()
+        torch.cuda.synchronize()
+        for m, t in zip(mapped, (ref.x, ref.v, ref.H)):
+            assert torch.equal(m.t, t.cpu())
+    finally:
+        for m in mapped:
+            m.close()
