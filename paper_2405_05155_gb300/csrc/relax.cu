@@ -775,6 +775,8 @@ int read_capacity_flag(sph_ctx* ctx, cudaStream_t s, int* step_failed, int64_t* 
 // Default list capacity of the float32 skin list (entries per slot), regrown on
 // overflow; steps issued between two reads of the status flags.
 constexpr int kSkinCap = 128;
+// Reach of the list build's cell sweep: cells of edge (2h + skin) / kBuildReach.
+constexpr int kBuildReach = 2;
 constexpr int kSkinBatch = 16;   // at most; after a rebuild, about the last list's lifetime
 
 template <int LANES>
@@ -794,7 +796,7 @@ int relax_steps_skin(sph_ctx* ctx, const sph_relax_params* p, double* pos, const
     const int64_t n = p->dom.n;
     const double h = p->dom.h, rc = p->dom.kappa * h, skin = ctx->relax_skin * h;
     sph_domain cells = p->dom;
-    cells.kappa = 0.5 * (rc + skin) / h;          // cells of edge >= (2h + skin) / 2
+    cells.kappa = (rc + skin) / (kBuildReach * h);   // cells of edge >= (2h + skin) / reach
     const int64_t slots = (n + 31) / 32 * 32;
     int st = SPH_OK;
     unsigned* ctl = (unsigned*)sph_scratch(ctx, S_RELAX_AMAX, 64, &st);
@@ -823,7 +825,7 @@ int relax_steps_skin(sph_ctx* ctx, const sph_relax_params* p, double* pos, const
             if (st) return st;
             k_relax_pack_lo<<<grid_for(n, 256), 256, 0, s>>>(pos, vol, n, cl.sorted, cl.p32, lo);
             SPH_CUDA(ctx, cudaMemsetAsync(ctl, 0, 64, s));
-            k_relax_skin_build<2><<<grid_for(n, 256), 256, 0, s>>>(cl.p32, lo, cl.cell_start, cl.grid,
+            k_relax_skin_build<kBuildReach><<<grid_for(n, 256), 256, 0, s>>>(cl.p32, lo, cl.cell_start, cl.grid,
                                                                    (const unsigned*)cl.band, (rc + skin) * (rc + skin),
                                                                    pos, n, cap, col, rowlen, rec, ctl, done,
                                                                    ctx->flags);
