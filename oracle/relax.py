@@ -5,8 +5,10 @@ which vanishes at the steady state; the kernel is the Laguerre-Gauss kernel of
 Eq. 8 with cut-off 2h.  The paper refers to [zhu2021cad] for how the body
 surface is handled and gives no time-step rule.  Readings used here:
 
-* volume V = dp^3, h = 1.3 dp (the smoothing length of the error analysis,
-  Sec. 2.3.3), rho = 1, p0 = 1;
+* volume V = dp^d, h = 1.3 dp (the smoothing length of the error analysis,
+  Sec. 2.3.3), rho = 1, p0 = 1; 2D bodies are unions of circles;
+* the Wendland-relaxed distributions of Sec. 2.3.3 use the same step with the
+  standard Wendland kernel (cut-off 2h) in place of the Laguerre-Gauss kernel;
 * the body is a union of spheres with signed distance
   phi(x) = min_k (|x - c_k| - r_k) (negative inside) and unit normal
   grad phi = (x - c_k*)/|x - c_k*| for the first minimising sphere k*;
@@ -35,11 +37,13 @@ from .neighbors import neighbors_cells, pair_geometry, squared_distance
 
 
 def sdf_spheres(x, spheres):
-    """Signed distance to a union of spheres and its gradient.  spheres: (m, 4) rows (c, r)."""
+    """Signed distance to a union of spheres (circles in 2D) and its gradient.
+    spheres: (m, dim + 1) rows (centre, radius)."""
+    dim = x.shape[0]
     best = None
     arg = None
     for k in range(spheres.shape[0]):
-        dk = np.sqrt(np.sum((x - spheres[k, :3, None]) ** 2, axis=0)) - spheres[k, 3]
+        dk = np.sqrt(np.sum((x - spheres[k, :dim, None]) ** 2, axis=0)) - spheres[k, dim]
         if best is None:
             best = dk
             arg = np.zeros(x.shape[1], dtype=np.int64)
@@ -47,7 +51,7 @@ def sdf_spheres(x, spheres):
             upd = dk < best
             best = np.where(upd, dk, best)
             arg = np.where(upd, k, arg)
-    c = spheres[arg, :3].T
+    c = spheres[arg, :dim].T
     rel = x - c
     nrm = np.sqrt(np.sum(rel * rel, axis=0))
     with np.errstate(invalid="ignore", divide="ignore"):
@@ -72,6 +76,43 @@ def surface_integral_lg(d, h):
     return 2.0 * math.pi * ALPHA_LG[3] / h * val
 
 
+# Gauss-Legendre order of the surface integrals evaluated by quadrature.
+GL_ORDER = 48
+
+
+def surface_integral(kind, d, h, dim, kappa):
+    """I(d): the integral of -dW/dr z/|r| over the part of the support beyond a plane
+    at distance d (z measured from the particle along the normal), for a radial
+    kernel cut at kappa h.  Integrating over lines (2D) or planes (3D) of constant z
+    first:
+      2D: I(d) = 2 int_0^Y (W(sqrt(d^2 + y^2)) - W(kappa h)) dy,  Y = sqrt((kappa h)^2 - d^2);
+      3D: I(d) = 2 pi int_d^{kappa h} z (W(z) - W(kappa h)) dz.
+    The 3D Laguerre-Gauss case uses the closed form of surface_integral_lg; the others
+    a Gauss-Legendre rule of GL_ORDER nodes (the integrands are smooth)."""
+    d = np.clip(np.asarray(d, dtype=np.float64), 0.0, kappa * h)
+    if dim == 3 and kind == LAGUERRE_GAUSS and kappa == KAPPA_LG:
+        return surface_integral_lg(d, h)
+    from .kernels import kernel_w
+    rc = kappa * h
+    w_cut = float(kernel_w(kind, rc, h, dim, None))
+    x, w = np.polynomial.legendre.leggauss(GL_ORDER)
+    u = 0.5 * (x + 1.0)                      # nodes on [0, 1]
+    wt = 0.5 * w
+    flat = d.reshape(-1)
+    out = np.empty_like(flat)
+    for k, dk in enumerate(flat):
+        if dim == 2:
+            Y = math.sqrt(max(rc * rc - dk * dk, 0.0))
+            y = Y * u
+            f = kernel_w(kind, np.sqrt(dk * dk + y * y), h, 2, None) - w_cut
+            out[k] = 2.0 * Y * float(np.sum(wt * f))
+        else:
+            z = dk + (rc - dk) * u
+            f = z * (kernel_w(kind, z, h, 3, None) - w_cut)
+            out[k] = 2.0 * math.pi * (rc - dk) * float(np.sum(wt * f))
+    return out.reshape(d.shape)
+
+
 def gradient_sum(pos, vol, row_ptr, col, dom, kind):
     """s_i = sum_j grad W_ij V_j over the listed pairs with d^2 <= (kappa h)^2, shape (dim, n)."""
     n = pos.shape[1]
@@ -86,11 +127,13 @@ def gradient_sum(pos, vol, row_ptr, col, dom, kind):
     return s
 
 
-def acceleration(pos, vol, row_ptr, col, dom, spheres, p0=1.0, rho=1.0):
-    """Eq. 7 with the Laguerre-Gauss kernel and the surface term."""
-    s = gradient_sum(pos, vol, row_ptr, col, dom, LAGUERRE_GAUSS)
+def acceleration(pos, vol, row_ptr, col, dom, spheres, p0=1.0, rho=1.0, kind=LAGUERRE_GAUSS):
+    """Eq. 7 with the surface term; the Laguerre-Gauss kernel (Eq. 8) or, for the
+    Wendland-relaxed distributions of Sec. 2.3.3, the standard Wendland kernel, each
+    cut at dom.kappa h."""
+    s = gradient_sum(pos, vol, row_ptr, col, dom, kind)
     phi, gphi = sdf_spheres(pos, spheres)
-    surf = surface_integral_lg(np.maximum(-phi, 0.0), dom.h)
+    surf = surface_integral(kind, np.maximum(-phi, 0.0), dom.h, dom.dim, dom.kappa)
     return -(2.0 * p0 / rho) * (s + surf * gphi)
 
 
@@ -102,12 +145,12 @@ def bound(x, spheres, dp):
     return x - shift * gphi
 
 
-def step(pos, vol, dom, spheres, dp, p0=1.0, rho=1.0, csr=None):
+def step(pos, vol, dom, spheres, dp, p0=1.0, rho=1.0, csr=None, kind=LAGUERRE_GAUSS):
     """One relaxation step from ``pos`` (the CSR is rebuilt unless given)."""
     if csr is None:
         csr = neighbors_cells(pos, dom)
     row_ptr, col = csr
-    a = acceleration(pos, vol, row_ptr, col, dom, spheres, p0, rho)
+    a = acceleration(pos, vol, row_ptr, col, dom, spheres, p0, rho, kind)
     amax = float(np.max(np.sqrt(np.sum(a * a, axis=0)))) if a.shape[1] else 0.0
     if amax > 0.0:
         dt = 0.25 * math.sqrt(dom.h / amax)
@@ -117,9 +160,9 @@ def step(pos, vol, dom, spheres, dp, p0=1.0, rho=1.0, csr=None):
     return bound(x, spheres, dp)
 
 
-def run(pos, vol, dom, spheres, dp, nsteps, p0=1.0, rho=1.0):
+def run(pos, vol, dom, spheres, dp, nsteps, p0=1.0, rho=1.0, kind=LAGUERRE_GAUSS):
     for _ in range(nsteps):
-        pos = step(pos, vol, dom, spheres, dp, p0, rho)
+        pos = step(pos, vol, dom, spheres, dp, p0, rho, kind=kind)
     return pos
 
 

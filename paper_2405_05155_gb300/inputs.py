@@ -194,6 +194,25 @@ def sphere_body(seed, dp, jitter=0.25, count=8):
             "domain": dom, "dp": dp, "h": h}
 
 
+def circle_body(dp, diameter=2.0, jitter=0.0, seed=0):
+    """The geometry of the error analysis (Sec. 2.3.3): lattice points (k + 1/2) dp of
+    the square [-D/2, D/2]^2 inside the circle of diameter D about the origin,
+    optionally jittered by U(-j, j) dp; h = 1.3 dp, V = dp^2."""
+    R = 0.5 * diameter
+    m = int(math.ceil(diameter / dp - 1e-9))
+    lo = -0.5 * m * dp
+    pts = lattice([m, m], dp, [lo, lo])
+    pts = pts[:, np.sum(pts * pts, axis=0) <= R * R]
+    if jitter:
+        rng = np.random.default_rng(seed + 104729)
+        pts = pts + rng.uniform(-jitter, jitter, size=pts.shape) * dp
+    h = H_FLUID * dp
+    margin = 4.0 * dp
+    dom = domain(2, h, 2.0, [lo - margin, lo - margin], [m * dp + 2 * margin] * 2, (False, False))
+    return {"pos": pts, "spheres": np.array([[0.0, 0.0, R]]), "vol": np.full(pts.shape[1], dp * dp),
+            "domain": dom, "dp": dp, "h": h}
+
+
 MLP_SHAPES = [(128, 128), (128,), (128, 128), (128,), (128, 128), (128,), (3, 128), (3,)]
 
 
