@@ -379,6 +379,83 @@ def _bench_relax(api, inputs, ctx, steps, peak):
             "roofline_accel_pass": _roof(acc_bytes, ta / max(na, 1), peak)}
 
 
+def _bench_error_analysis(api, inputs, ctx, relax_steps=1000):
+    """Sec. 2.3.3: the L2 errors (Eq. 10) of the SPH summation of f = 1 and of the weak-form
+    df/dx of f = exp(-x^2/0.1) on a circle of diameter 2 (h = 1.3 dp), over the particles
+    at least 2h inside the surface, for the lattice and the Wendland- and Laguerre-Gauss-
+    relaxed distributions, standard (2h) and truncated (1.6h) Wendland kernels, with and
+    without the correction matrix.  Everything on the GPU (float64)."""
+    import math
+    import torch
+    dev = ctx.device
+    table = {}
+    approx_ms = None
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record()
+    for nres in (10, 20, 40):
+        dp = 2.0 / nres
+        lat = inputs.circle_body(dp)
+        jit = inputs.circle_body(dp, jitter=0.25, seed=0)
+        dists = {"lattice": torch.tensor(lat["pos"], dtype=torch.float64, device=dev)}
+        res = {}
+        for name, kernel in (("wendland_relaxed", api.SPH_WENDLAND_C2), ("laguerre_gauss_relaxed",
+                                                                         api.SPH_LAGUERRE_GAUSS)):
+            pos = torch.tensor(jit["pos"], dtype=torch.float64, device=dev)
+            vol = torch.tensor(jit["vol"], dtype=torch.float64, device=dev)
+            prm = api.relax_params(jit["domain"], jit["spheres"], dp, precision=api.SPH_FP64, kernel=kernel)
+            r0 = api.relax_residual(ctx, prm, pos, vol)
+            api.relax_step(ctx, prm, pos, vol, relax_steps)
+            r1 = api.relax_residual(ctx, prm, pos, vol)
+            dists[name] = pos
+            res[name] = {"residual_lg": [r0[0], r1[0]], "residual_tw": [r0[1], r1[1]]}
+        row = {}
+        for name, pos in dists.items():
+            n = pos.shape[1]
+            vol = torch.full((n,), dp * dp, dtype=torch.float64, device=dev)
+            x = pos[0]
+            interior = torch.sqrt(pos[0] ** 2 + pos[1] ** 2) - 1.0 < -2.0 * 1.3 * dp
+            f_exp = torch.exp(-x * x / 0.1)
+            dfdx = -2.0 * x / 0.1 * f_exp
+            ones = torch.ones(n, dtype=torch.float64, device=dev)
+            entry = {"particles": n, "interior": int(interior.sum())}
+            for label, kappa in (("SW", 2.0), ("TW", 1.6)):
+                d = dict(lat["domain"])
+                d["kappa"] = kappa
+                rp, col = api.build_neighbors(ctx, d, pos)
+                B, _, nfb = api.kgc(ctx, d, pos, vol, rp, col)
+                s1, _ = api.field_approx(ctx, d, pos, vol, rp, col, ones)
+                _, g = api.field_approx(ctx, d, pos, vol, rp, col, f_exp)
+                _, gB = api.field_approx(ctx, d, pos, vol, rp, col, f_exp, B=B)
+                if nres == 40 and label == "TW" and name == "laguerre_gauss_relaxed":
+                    approx_ms = _event_ms(lambda: api.field_approx(ctx, d, pos, vol, rp, col, f_exp, B=B))
+
+                def l2(ref, app):
+                    ref, app = ref[interior], app[interior]
+                    return float(torch.sqrt(torch.sum((ref - app) ** 2) / torch.sum(ref * ref)))
+
+                entry[label + "_f1_without_B"] = l2(ones, s1)
+                entry[label + "_dfdx_without_B"] = l2(dfdx, g[0])
+                entry[label + "_dfdx_with_B"] = l2(dfdx, gB[0])
+                entry[label + "_kgc_fallbacks"] = nfb
+            if name in res:
+                entry.update(res[name])
+            row[name] = entry
+        table["dp=D/%d" % nres] = row
+    stop.record()
+    torch.cuda.synchronize()
+    return {"workload": "error analysis of Sec. 2.3.3: circle D = 2, dp = D/10, D/20, D/40, h = 1.3 dp; lattice and "
+                        "distributions relaxed %d steps (float64) with the standard Wendland or the Laguerre-Gauss "
+                        "kernel from a lattice jittered by U(-dp/4, dp/4) (seed 0); L2 of Eq. 10 over particles "
+                        "with phi < -2h" % relax_steps,
+            "table": table,
+            "paper_table1_f1_dp_D10": {"lattice": {"SW": 0.010, "TW": 0.006},
+                                       "wendland_relaxed": {"SW": 0.034, "TW": 0.028},
+                                       "laguerre_gauss_relaxed": {"SW": 0.037, "TW": 0.031}},
+            "field_approx_ms_dp_D40": approx_ms,
+            "total_ms": start.elapsed_time(stop)}
+
+
 def _bench_mlp(api, inputs, ctx, peak_tflops):
     """BF16 tensor-core MLP: proposal forward over a 2.2M-row feature set, and training steps."""
     import torch
@@ -607,6 +684,7 @@ def run_gpu(args):
                          ("tgv2d_50_plain_fp64", lambda: _bench_tgv2d(api, inputs, ctx)),
                          ("batched_64_tgv2d", lambda: _bench_batched(api, inputs, ctx, args.other_steps, peak)),
                          ("relax_8spheres_dp128", lambda: _bench_relax(api, inputs, ctx, 50, peak)),
+                         ("error_analysis_circle", lambda: _bench_error_analysis(api, inputs, ctx)),
                          ("mlp_proposal", lambda: _bench_mlp(api, inputs, ctx, bf16))):
             try:
                 workloads[name] = fn()

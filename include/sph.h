@@ -458,24 +458,31 @@ int sph_autotune_tlsph(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsp
                        int trial_steps, int* lanes_host, double* ms_host, void* stream);
 
 /* ---- a10/a11: Laguerre-Gauss particle relaxation (Sec. 2.3.2, Eqs. 7-8) ----
- * 3D only.  Body = union of n_spheres spheres (cx, cy, cz, r) given by value,
- * signed distance phi = min_k(|x-c_k| - r_k), normal grad phi of the first
- * minimising sphere.  Per step: neighbour sets (cut-off 2h) from the current
- * positions; a_i = -(2 p0/rho)(sum_j grad W^LG_ij V_j + I(max(-phi_i,0)) grad phi_i)
- * with the half-space surface integral I(d) = 2 pi int_d^{2h} z (W(z) - W(2h)) dz;
- * dt = 0.25 sqrt(h / max|a|); x += a dt^2/2; then particles with
- * phi > -dp/2 are moved along grad phi to phi = -dp/2. */
+ * dim 2 or 3.  Body = union of n_spheres spheres (cx, cy, cz, r) given by value
+ * (2D: circles (cx, cy, unused, r)), signed distance phi = min_k(|x-c_k| - r_k),
+ * normal grad phi of the first minimising sphere.  Per step: neighbour sets
+ * (cut-off kappa h) from the current positions;
+ * a_i = -(2 p0/rho)(sum_j grad W_ij V_j + I(max(-phi_i,0)) grad phi_i), W the
+ * Laguerre-Gauss kernel (kappa = 2) or, for the Wendland-relaxed distributions of
+ * Sec. 2.3.3, the Wendland kernel, with the surface integral over the support
+ * beyond the tangent line or plane at distance d,
+ *   3D: I(d) = 2 pi int_d^{kappa h} z (W(z) - W(kappa h)) dz,
+ *   2D: I(d) = 2 int_0^Y (W(sqrt(d^2 + y^2)) - W(kappa h)) dy, Y = sqrt((kappa h)^2 - d^2)
+ * (closed form for the 3D Laguerre-Gauss kernel, a 48-node Gauss-Legendre rule
+ * otherwise); dt = 0.25 sqrt(h / max|a|); x += a dt^2/2; then particles with
+ * phi > -dp/2 are moved along grad phi to phi = -dp/2.  SPH_FP32_KAHAN: 3D
+ * Laguerre-Gauss only (SPH_ERR_ARG otherwise). */
 typedef struct {
-    sph_domain dom;                 /* dim 3, h, kappa = 2, cell box */
+    sph_domain dom;                 /* dim 2 or 3, h, kappa (2 for Laguerre-Gauss), cell box */
     double dp, p0, rho;
-    int32_t kernel;                 /* SPH_LAGUERRE_GAUSS */
+    int32_t kernel;                 /* SPH_LAGUERRE_GAUSS or SPH_WENDLAND_C2 */
     int32_t precision;              /* SPH_FP64 or SPH_FP32_KAHAN (pair sums) */
     int32_t n_spheres;              /* 1..SPH_MAX_SPHERES */
     int32_t reserved;
     double spheres[4 * SPH_MAX_SPHERES];
 } sph_relax_params;
 
-/* Advance nsteps relaxation steps of pos (float64 [3][n], in place).
+/* Advance nsteps relaxation steps of pos (float64 [dim][n], in place).
  * SPH_FP32_KAHAN keeps, within one call, a neighbour list of cut-off 2h + skin
  * (sph_set_relax_skin) and rebuilds it only when twice the largest displacement
  * since its build exceeds the skin; every step still decides each listed pair at
@@ -500,6 +507,21 @@ int sph_relax_accel(sph_ctx* ctx, const sph_relax_params* prm, const double* pos
  * Synchronises the stream. */
 int sph_relax_residual(sph_ctx* ctx, const sph_relax_params* prm, const double* pos,
                        const double* vol, double* out_host, void* stream);
+
+/* ---- x1: SPH approximations for the error analysis (Sec. 2.3.3) ----
+ * For a field f (float64 [n]) on the particles, over the pairs of CSR lists of
+ * sph_build_neighbors at dom->kappa and with the kernel `kernel`
+ * (SPH_WENDLAND_C2 or SPH_LAGUERRE_GAUSS):
+ *   sum[i]        = sum_j f_j W_ij V_j + f_i W(0) V_i       the kernel summation;
+ *                   for f = 1 the normalisation condition, Eq. 3 (Table 1);
+ *   grad[a*n + i] = sum_j (f_i + f_j) (B_i grad W_ij)_a V_j  the weak form of Eq. 4 with
+ *                   grad W_ij = grad_i W, with the correction matrix of Eq. 9 (B in
+ *                   sph_kgc's layout) or, when B is NULL, B_i = I.
+ * Either output may be NULL (then it is not computed).  Minimum image on the
+ * periodic axes.  Float64. */
+int sph_field_approx(sph_ctx* ctx, const sph_domain* dom, int kernel, const double* pos,
+                     const double* vol, const int64_t* row_ptr, const int32_t* col,
+                     const double* B, const double* f, double* sum, double* grad, void* stream);
 
 /* ---- a12: learned relaxation proposal (not in the paper) ----
  * A 128 -> 128 -> 128 -> 128 -> 3 multilayer perceptron with GELU (erf form)

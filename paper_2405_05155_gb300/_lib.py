@@ -114,6 +114,8 @@ _SIGNATURES = {
     "sph_tlsph_plan": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp]),
     "sph_set_stage_cap": (ctypes.c_int, [c_vp, ctypes.c_int]),
     "sph_set_relax_skin": (ctypes.c_int, [c_vp, ctypes.c_double]),
+    "sph_field_approx": (ctypes.c_int, [c_vp, _P(SphDomain), ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                        c_vp, c_vp, c_vp]),
     "sph_host_alloc": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp)]),
     "sph_host_free": (ctypes.c_int, [c_vp]),
     "sph_set_tile_pipeline": (ctypes.c_int, [c_vp, ctypes.c_int]),

@@ -18,7 +18,14 @@ NSYM = {2: 3, 3: 6}
 
 
 def _p(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    """Raw pointer of a tensor argument.  The C ABI reads arrays in row-major order
+    ([dim][n] and the like), so a tensor with other strides is refused rather than
+    passed (torch.tensor of a Fortran-ordered array, a transposed view)."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("libsph array arguments must be contiguous (got strides %s)" % (t.stride(),))
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _stream():
@@ -166,6 +173,18 @@ def build_neighbors(ctx, dom, pos, cap=None):
         L.check("sph_build_neighbors", st, ctx.h)
         return row_ptr, col[: nnz.value]
     raise RuntimeError("sph_build_neighbors: capacity retry failed")
+
+
+def field_approx(ctx, dom, pos, vol, row_ptr, col, f, B=None, kernel=SPH_WENDLAND_C2):
+    """(kernel summation [n], weak-form gradient [dim][n]) of the field f (sph_field_approx)."""
+    n = pos.shape[1]
+    d = make_domain(dom, n)
+    s = torch.empty(n, dtype=torch.float64, device=pos.device)
+    g = torch.empty((dom["dim"], n), dtype=torch.float64, device=pos.device)
+    L.check("sph_field_approx", ctx.lib.sph_field_approx(ctx.h, ctypes.byref(d), kernel, _p(pos), _p(vol),
+                                                          _p(row_ptr), _p(col), _p(B), _p(f), _p(s), _p(g),
+                                                          _stream()), ctx.h)
+    return s, g
 
 
 def kgc(ctx, dom, pos, vol, row_ptr, col, kernel=SPH_WENDLAND_C2):
@@ -332,21 +351,23 @@ class TLSolid:
         return self.x, self.v, self.H
 
 
-def relax_params(dom, spheres, dp, precision=SPH_FP32_KAHAN, p0=1.0, rho=1.0, n=0):
+def relax_params(dom, spheres, dp, precision=SPH_FP32_KAHAN, p0=1.0, rho=1.0, n=0, kernel=SPH_LAGUERRE_GAUSS):
+    """Relaxation parameters; spheres rows (cx, cy, cz, r), or circles (cx, cy, r) in 2D."""
     prm = L.RelaxParams()
     prm.dom = make_domain(dom, n)
     prm.dp, prm.p0, prm.rho = dp, p0, rho
-    prm.kernel = SPH_LAGUERRE_GAUSS
+    prm.kernel = kernel
     prm.precision = precision
     prm.n_spheres = len(spheres)
     for k, s in enumerate(spheres):
+        row = [s[0], s[1], 0.0, s[2]] if len(s) == 3 else list(s[:4])
         for c in range(4):
-            prm.spheres[4 * k + c] = float(s[c])
+            prm.spheres[4 * k + c] = float(row[c])
     return prm
 
 
 def relax_step(ctx, prm, pos, vol, nsteps=1):
-    """Advance ``nsteps`` relaxation steps of pos (float64 [3][n] device tensor, in place)."""
+    """Advance ``nsteps`` relaxation steps of pos (float64 [dim][n] device tensor, in place)."""
     prm.dom.n = pos.shape[1]
     L.check("sph_relax_step", ctx.lib.sph_relax_step(ctx.h, ctypes.byref(prm), _p(pos), _p(vol), int(nsteps),
                                                       _stream()), ctx.h)

@@ -14,6 +14,8 @@
 // after which the remaining steps are no-ops and the host regrows (or rebuilds) the
 // list and resumes from that step.
 #include <algorithm>
+#include <mutex>
+#include <set>
 
 #include "common.cuh"
 #include "neighbors.cuh"
@@ -29,27 +31,55 @@ struct Spheres {
 
 struct RelaxK {
     double h, dp, scale;           // scale = 2 p0 / rho
-    double gcoef;                  // LG gs coefficient -ahat h^-5 / 3
-    double gcoef_tw;               // Wendland gs coefficient -5 alpha h^-5
+    double gcoef;                  // gs coefficient of the relaxation kernel (h^-(d+2) included)
+    double gcoef_lg;               // LG gs coefficient -ahat h^-(d+2) / 3 (residual)
+    double gcoef_tw;               // Wendland gs coefficient -5 alpha h^-(d+2) (residual)
     double inv_h;
     double rc2_tw;                 // (1.6 h)^2 for the truncated residual
-    double surf_coef;              // 2 pi ahat / h
+    double surf_coef;              // 3D Laguerre-Gauss closed form: 2 pi ahat / h
+    double rc;                     // cut-off of the relaxation kernel, kappa h
+    double w_norm;                 // alpha_d h^-d of the relaxation kernel
+    int kernel;                    // SPH_LAGUERRE_GAUSS or SPH_WENDLAND_C2
     float gcoef_f, inv_h_f, inv_h2_f, scale_f, surf_coef_f, h_f, dp_f;
 };
 
-// Signed distance to the sphere union and its unit normal (first minimiser).
+// Gauss-Legendre rule of the surface integrals that have no closed form (nodes on
+// [0, 1] and their weights), set once per device from the host.
+constexpr int kGL = 48;
+__constant__ double c_gl_u[kGL], c_gl_w[kGL];
+
+// Shape of the relaxation kernel, W / (alpha_d h^-d), uncut.
+__device__ __forceinline__ double kernel_shape(int kernel, double q) {
+    if (kernel == SPH_WENDLAND_C2) {
+        double t = 1.0 - 0.5 * q;
+        return t * t * t * t * (2.0 * q + 1.0);
+    }
+    double q2 = q * q;
+    return (1.0 - 0.5 * q2 + q2 * q2 / 6.0) * exp(-q2);
+}
+
+// Signed distance to the union of spheres (circles in 2D) and its unit normal
+// (first minimiser).
+template <int DIM = 3>
 __device__ __forceinline__ double sdf64(const Spheres& S, const double* x, double* g) {
     double best = 0.0;
     int arg = 0;
     for (int k = 0; k < S.count; ++k) {
-        double dx = x[0] - S.c[k][0], dy = x[1] - S.c[k][1], dz = x[2] - S.c[k][2];
-        double d = sqrt(dx * dx + dy * dy + dz * dz) - S.r[k];
+        double d2 = 0.0;
+        for (int a = 0; a < DIM; ++a) {
+            double dx = x[a] - S.c[k][a];
+            d2 += dx * dx;
+        }
+        double d = sqrt(d2) - S.r[k];
         if (k == 0 || d < best) { best = d; arg = k; }
     }
-    double rx = x[0] - S.c[arg][0], ry = x[1] - S.c[arg][1], rz = x[2] - S.c[arg][2];
-    double nr = sqrt(rx * rx + ry * ry + rz * rz);
-    if (nr > 0.0) { g[0] = rx / nr; g[1] = ry / nr; g[2] = rz / nr; }
-    else { g[0] = 1.0; g[1] = 0.0; g[2] = 0.0; }
+    double rr[3] = {0.0, 0.0, 0.0}, nr2 = 0.0;
+    for (int a = 0; a < DIM; ++a) {
+        rr[a] = x[a] - S.c[arg][a];
+        nr2 += rr[a] * rr[a];
+    }
+    double nr = sqrt(nr2);
+    for (int a = 0; a < DIM; ++a) g[a] = nr > 0.0 ? rr[a] / nr : (a == 0 ? 1.0 : 0.0);
     return best;
 }
 
@@ -92,6 +122,39 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned* addr, float v) {
 }
 
 // ---------------------------------------------------------------- acceleration
+// Surface term I(d) of the relaxation kernel (the integral of -dW/dr z/|r| over the
+// support beyond the tangent line or plane at distance d): the closed form for the
+// 3D Laguerre-Gauss kernel, else
+//   2D: 2 int_0^Y (W(sqrt(d^2 + y^2)) - W(kappa h)) dy,  Y = sqrt((kappa h)^2 - d^2),
+//   3D: 2 pi int_d^{kappa h} z (W(z) - W(kappa h)) dz,
+// by the Gauss-Legendre rule in constant memory.
+template <int DIM>
+__device__ double surface_term(double d, const RelaxK& K) {
+    d = fmin(fmax(d, 0.0), K.rc);
+    if (DIM == 3 && K.kernel == SPH_LAGUERRE_GAUSS) return surface_lg<double>(d, K.inv_h, K.surf_coef);
+    const double wcut = kernel_shape(K.kernel, K.rc * K.inv_h);
+    double acc = 0.0;
+    if (DIM == 2) {
+        const double Y = sqrt(fmax(K.rc * K.rc - d * d, 0.0));
+        for (int k = 0; k < kGL; ++k) {
+            const double y = Y * c_gl_u[k];
+            acc += c_gl_w[k] * (kernel_shape(K.kernel, sqrt(d * d + y * y) * K.inv_h) - wcut);
+        }
+        return 2.0 * Y * K.w_norm * acc;
+    }
+    for (int k = 0; k < kGL; ++k) {
+        const double z = d + (K.rc - d) * c_gl_u[k];
+        acc += c_gl_w[k] * z * (kernel_shape(K.kernel, z * K.inv_h) - wcut);
+    }
+    return 2.0 * SPH_PI * (K.rc - d) * K.w_norm * acc;
+}
+
+template <int DIM>
+__device__ __forceinline__ double relax_gs(double q, const RelaxK& K) {
+    return K.kernel == SPH_WENDLAND_C2 ? wendland_gs<double>(q, K.gcoef) : lg_gs<double>(q, K.gcoef);
+}
+
+template <int DIM>
 __global__ void k_relax_acc64(const double* __restrict__ pos, const double* __restrict__ vol, int64_t n,
                               const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, Spheres S,
                               RelaxK K, double* __restrict__ acc, unsigned* __restrict__ amax,
@@ -102,20 +165,26 @@ __global__ void k_relax_acc64(const double* __restrict__ pos, const double* __re
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool skip = flags[FLAG_CAPACITY] != 0;
     if (i < n && !skip) {
-        double xi[3] = {pos[i], pos[n + i], pos[2 * n + i]};
-        double s[3] = {0.0, 0.0, 0.0};
+        double xi[DIM];
+        for (int a = 0; a < DIM; ++a) xi[a] = pos[a * n + i];
+        double s[DIM];
+        for (int a = 0; a < DIM; ++a) s[a] = 0.0;
         for (int64_t p = row_ptr[i], e = row_ptr[i + 1]; p < e; ++p) {
             int j = col[p];
-            double r[3], d2 = 0.0;
-            for (int a = 0; a < 3; ++a) { r[a] = xi[a] - pos[a * n + j]; d2 += r[a] * r[a]; }
-            double gs = lg_gs<double>(sqrt(d2) * K.inv_h, K.gcoef) * vol[j];
-            for (int a = 0; a < 3; ++a) s[a] += gs * r[a];
+            double r[DIM], d2 = 0.0;
+            for (int a = 0; a < DIM; ++a) { r[a] = xi[a] - pos[a * n + j]; d2 += r[a] * r[a]; }
+            double gs = relax_gs<DIM>(sqrt(d2) * K.inv_h, K) * vol[j];
+            for (int a = 0; a < DIM; ++a) s[a] += gs * r[a];
         }
-        double g[3];
-        double phi = sdf64(S, xi, g);
-        double I = surface_lg<double>(phi < 0.0 ? -phi : 0.0, K.inv_h, K.surf_coef);
-        double a[3], m2 = 0.0;
-        for (int c = 0; c < 3; ++c) { a[c] = -K.scale * (s[c] + I * g[c]); m2 += a[c] * a[c]; acc[c * n + i] = a[c]; }
+        double g[DIM];
+        double phi = sdf64<DIM>(S, xi, g);
+        double I = surface_term<DIM>(phi < 0.0 ? -phi : 0.0, K);
+        double m2 = 0.0;
+        for (int c = 0; c < DIM; ++c) {
+            double a = -K.scale * (s[c] + I * g[c]);
+            m2 += a * a;
+            acc[c * n + i] = a;
+        }
         atomic_max_nonneg(&smax, __double2float_ru(sqrt(m2)));
     }
     __syncthreads();
@@ -124,11 +193,14 @@ __global__ void k_relax_acc64(const double* __restrict__ pos, const double* __re
 
 // exact float64 max of |a| (the float32 block max above only bounds it; a second
 // pass takes the exact value among candidates >= the bound's float32 lower edge)
+template <int DIM>
 __global__ void k_amax64_exact(const double* __restrict__ acc, int64_t n, const unsigned* __restrict__ amax_f,
                                unsigned long long* __restrict__ amax_d, const int* __restrict__ flags) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || flags[FLAG_CAPACITY]) return;
-    double m = sqrt(acc[i] * acc[i] + acc[n + i] * acc[n + i] + acc[2 * n + i] * acc[2 * n + i]);
+    double m2 = 0.0;
+    for (int a = 0; a < DIM; ++a) m2 += acc[a * n + i] * acc[a * n + i];
+    double m = sqrt(m2);
     float bound = __uint_as_float(*amax_f);
     if (__double2float_ru(m) == bound) atomicMax(amax_d, (unsigned long long)__double_as_longlong(m));
 }
@@ -176,24 +248,26 @@ __device__ __forceinline__ bool within_ff(const double* xi, const F8& r, double 
 }
 
 // ---------------------------------------------------------------- update
+template <int DIM>
 __global__ void k_relax_update64(double* __restrict__ pos, int64_t n, const double* __restrict__ acc,
                                  const unsigned long long* __restrict__ amax_d, Spheres S, RelaxK K,
                                  const int* __restrict__ flags) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || flags[FLAG_CAPACITY]) return;
     double am = __longlong_as_double((long long)*amax_d);
-    double x[3] = {pos[i], pos[n + i], pos[2 * n + i]};
+    double x[DIM];
+    for (int c = 0; c < DIM; ++c) x[c] = pos[c * n + i];
     if (am > 0.0) {
         double dt = 0.25 * sqrt(K.h / am);
-        for (int c = 0; c < 3; ++c) x[c] = x[c] + 0.5 * acc[c * n + i] * (dt * dt);
+        for (int c = 0; c < DIM; ++c) x[c] = x[c] + 0.5 * acc[c * n + i] * (dt * dt);
     }
-    double g[3];
-    double phi = sdf64(S, x, g);
+    double g[DIM];
+    double phi = sdf64<DIM>(S, x, g);
     if (phi > -0.5 * K.dp) {
         double sh = phi + 0.5 * K.dp;
-        for (int c = 0; c < 3; ++c) x[c] = x[c] - sh * g[c];
+        for (int c = 0; c < DIM; ++c) x[c] = x[c] - sh * g[c];
     }
-    for (int c = 0; c < 3; ++c) pos[c * n + i] = x[c];
+    for (int c = 0; c < DIM; ++c) pos[c * n + i] = x[c];
 }
 
 __global__ void k_relax_update32(double* __restrict__ pos, int64_t n, const float4* __restrict__ acc,
@@ -221,6 +295,7 @@ __global__ void k_relax_update32(double* __restrict__ pos, int64_t n, const floa
 }
 
 // ---------------------------------------------------------------- residual
+template <int DIM>
 __global__ void k_relax_residual(const double* __restrict__ pos, const double* __restrict__ vol, int64_t n,
                                  const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, Spheres S,
                                  RelaxK K, double* __restrict__ partial) {
@@ -228,25 +303,32 @@ __global__ void k_relax_residual(const double* __restrict__ pos, const double* _
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double e_lg = 0.0, e_tw = 0.0, cnt = 0.0;
     if (i < n) {
-        double xi[3] = {pos[i], pos[n + i], pos[2 * n + i]};
-        double g[3];
-        double phi = sdf64(S, xi, g);
+        double xi[DIM];
+        for (int a = 0; a < DIM; ++a) xi[a] = pos[a * n + i];
+        double g[DIM];
+        double phi = sdf64<DIM>(S, xi, g);
         if (phi < -2.0 * K.h) {
-            double s1[3] = {0, 0, 0}, s2[3] = {0, 0, 0};
+            double s1[DIM], s2[DIM];
+            for (int a = 0; a < DIM; ++a) s1[a] = s2[a] = 0.0;
             for (int64_t p = row_ptr[i], e = row_ptr[i + 1]; p < e; ++p) {
                 int j = col[p];
-                double r[3];
-                for (int a = 0; a < 3; ++a) r[a] = xi[a] - pos[a * n + j];
-                double d2u = __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])), __dmul_rn(r[2], r[2]));
-                double q = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) * K.inv_h;
+                double r[DIM], d2 = 0.0, d2u = 0.0;
+                for (int a = 0; a < DIM; ++a) {
+                    r[a] = xi[a] - pos[a * n + j];
+                    d2 += r[a] * r[a];
+                    double sq = __dmul_rn(r[a], r[a]);
+                    d2u = a == 0 ? sq : __dadd_rn(d2u, sq);
+                }
+                double q = sqrt(d2) * K.inv_h;
                 double w = vol[j];
-                double g1 = lg_gs<double>(q, K.gcoef) * w;
+                double g1 = lg_gs<double>(q, K.gcoef_lg) * w;
                 double g2 = d2u <= K.rc2_tw ? wendland_gs<double>(q, K.gcoef_tw) * w : 0.0;
-                for (int a = 0; a < 3; ++a) { s1[a] += g1 * r[a]; s2[a] += g2 * r[a]; }
+                for (int a = 0; a < DIM; ++a) { s1[a] += g1 * r[a]; s2[a] += g2 * r[a]; }
             }
-            double h2 = K.h * K.h;
-            e_lg = h2 * (s1[0] * s1[0] + s1[1] * s1[1] + s1[2] * s1[2]);
-            e_tw = h2 * (s2[0] * s2[0] + s2[1] * s2[1] + s2[2] * s2[2]);
+            double h2 = K.h * K.h, m1 = 0.0, m2 = 0.0;
+            for (int a = 0; a < DIM; ++a) { m1 += s1[a] * s1[a]; m2 += s2[a] * s2[a]; }
+            e_lg = h2 * m1;
+            e_tw = h2 * m2;
             cnt = 1.0;
         }
     }
@@ -647,11 +729,54 @@ int check_relax(const sph_relax_params* p) {
     if (!p) return SPH_ERR_ARG;
     int s = sph_check_domain(&p->dom);
     if (s) return s;
-    if (p->dom.dim != 3 || p->dom.periodic_mask != 0) return SPH_ERR_ARG;   // a body: no periodic axes
-    if (p->kernel != SPH_LAGUERRE_GAUSS) return SPH_ERR_ARG;
+    if (p->dom.periodic_mask != 0) return SPH_ERR_ARG;   // a body: no periodic axes
+    if (p->dom.dim != 2 && p->dom.dim != 3) return SPH_ERR_ARG;
+    if (p->kernel == SPH_LAGUERRE_GAUSS) {
+        if (p->dom.kappa != 2.0) return SPH_ERR_ARG;     // Eq. 8's support
+    } else if (p->kernel != SPH_WENDLAND_C2) {
+        return SPH_ERR_ARG;
+    }
     if (p->precision != SPH_FP64 && p->precision != SPH_FP32_KAHAN) return SPH_ERR_ARG;
+    // the float32 forms: 3D Laguerre-Gauss only
+    if (p->precision == SPH_FP32_KAHAN && (p->dom.dim != 3 || p->kernel != SPH_LAGUERRE_GAUSS)) return SPH_ERR_ARG;
     if (p->n_spheres < 1 || p->n_spheres > SPH_MAX_SPHERES) return SPH_ERR_ARG;
     if (!(p->dp > 0.0) || !(p->rho > 0.0) || !(p->p0 > 0.0)) return SPH_ERR_ARG;
+    return SPH_OK;
+}
+
+// Legendre nodes by Newton's method on P_n (three-term recurrence), mapped to [0, 1];
+// weights 1 / ((1 - x^2) P_n'(x)^2) (half the [-1, 1] weights).
+void gauss_legendre01(int n, double* u, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double x = cos(SPH_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        // ascending order of the nodes
+        u[n - 1 - i] = 0.5 * (x + 1.0);
+        w[n - 1 - i] = 1.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+int ensure_gauss_legendre(sph_ctx* ctx) {
+    static std::mutex mu;
+    static std::set<int> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count(ctx->device)) return SPH_OK;
+    double u[kGL], w[kGL];
+    gauss_legendre01(kGL, u, w);
+    SPH_CUDA(ctx, cudaMemcpyToSymbol(c_gl_u, u, sizeof(u)));
+    SPH_CUDA(ctx, cudaMemcpyToSymbol(c_gl_w, w, sizeof(w)));
+    done.insert(ctx->device);
     return SPH_OK;
 }
 
@@ -673,13 +798,19 @@ Spheres make_spheres(const sph_relax_params* p) {
 
 RelaxK make_relax_consts(const sph_relax_params* p) {
     RelaxK K;
-    double h = p->dom.h;
-    double h5 = h * h * h * h * h;
+    const int d = p->dom.dim;
+    const double h = p->dom.h;
+    const double hd = d == 2 ? h * h : h * h * h;
+    const double hd2 = hd * h * h;
     K.h = h;
     K.dp = p->dp;
     K.scale = 2.0 * p->p0 / p->rho;
-    K.gcoef = -lg_alpha(3) / h5 / 3.0;
-    K.gcoef_tw = -5.0 * wendland_alpha(3) / h5;
+    K.kernel = p->kernel;
+    K.gcoef_lg = -lg_alpha(d) / hd2 / 3.0;
+    K.gcoef_tw = -5.0 * wendland_alpha(d) / hd2;
+    K.gcoef = p->kernel == SPH_WENDLAND_C2 ? K.gcoef_tw : K.gcoef_lg;
+    K.w_norm = (p->kernel == SPH_WENDLAND_C2 ? wendland_alpha(d) : lg_alpha(d)) / hd;
+    K.rc = p->dom.kappa * h;
     K.inv_h = 1.0 / h;
     double rtw = 1.6 * h;
     K.rc2_tw = rtw * rtw;
@@ -892,6 +1023,8 @@ extern "C" int sph_relax_step(sph_ctx* ctx, const sph_relax_params* p, double* p
     cudaStream_t s = as_stream(stream);
     Spheres S = make_spheres(p);
     RelaxK K = make_relax_consts(p);
+    st = ensure_gauss_legendre(ctx);
+    if (st) return st;
     if (p->precision == SPH_FP32_KAHAN && ctx->relax_skin > 0.0)
         return relax_steps_skin(ctx, p, pos, vol, nsteps, S, K, s);
     if (p->precision == SPH_FP32_KAHAN) {
@@ -939,11 +1072,21 @@ extern "C" int sph_relax_step(sph_ctx* ctx, const sph_relax_params* p, double* p
             sph_timer_end(ctx, t, s);
             SPH_CUDA(ctx, cudaMemsetAsync(amax, 0, 64, s));
             t = sph_timer_begin(ctx, SPH_TIMER_RELAX_ACCEL, s);
-            k_relax_acc64<<<grid_for(n, 128), 128, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, acc, amax, ctx->flags);
-            k_amax64_exact<<<grid_for(n, 256), 256, 0, s>>>(acc, n, amax, amax_d, ctx->flags);
+            if (p->dom.dim == 2) {
+                k_relax_acc64<2><<<grid_for(n, 128), 128, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, acc, amax,
+                                                                  ctx->flags);
+                k_amax64_exact<2><<<grid_for(n, 256), 256, 0, s>>>(acc, n, amax, amax_d, ctx->flags);
+            } else {
+                k_relax_acc64<3><<<grid_for(n, 128), 128, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, acc, amax,
+                                                                  ctx->flags);
+                k_amax64_exact<3><<<grid_for(n, 256), 256, 0, s>>>(acc, n, amax, amax_d, ctx->flags);
+            }
             sph_timer_end(ctx, t, s);
             t = sph_timer_begin(ctx, SPH_TIMER_RELAX_UPDATE, s);
-            k_relax_update64<<<grid_for(n, 256), 256, 0, s>>>(pos, n, acc, amax_d, S, K, ctx->flags);
+            if (p->dom.dim == 2)
+                k_relax_update64<2><<<grid_for(n, 256), 256, 0, s>>>(pos, n, acc, amax_d, S, K, ctx->flags);
+            else
+                k_relax_update64<3><<<grid_for(n, 256), 256, 0, s>>>(pos, n, acc, amax_d, S, K, ctx->flags);
             sph_timer_end(ctx, t, s);
             SPH_LAUNCH_CHECK(ctx);
         }
@@ -971,6 +1114,8 @@ extern "C" int sph_relax_accel(sph_ctx* ctx, const sph_relax_params* p, const do
     cudaStream_t s = as_stream(stream);
     Spheres S = make_spheres(p);
     RelaxK K = make_relax_consts(p);
+    st = ensure_gauss_legendre(ctx);
+    if (st) return st;
     if (p->precision == SPH_FP32_KAHAN) {
         unsigned* amax = (unsigned*)sph_scratch(ctx, S_RELAX_AMAX, 64, &st);
         float4* acc = (float4*)sph_scratch(ctx, S_RELAX_ACC, (size_t)n * 16, &st);
@@ -1005,7 +1150,12 @@ extern "C" int sph_relax_accel(sph_ctx* ctx, const sph_relax_params* p, const do
     unsigned* amax = (unsigned*)sph_scratch(ctx, S_RELAX_AMAX, 64, &st);
     if (st) return st;
     SPH_CUDA(ctx, cudaMemsetAsync(amax, 0, 64, s));
-    k_relax_acc64<<<grid_for(n, 128), 128, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, acc_out, amax, ctx->flags);
+    if (p->dom.dim == 2)
+        k_relax_acc64<2><<<grid_for(n, 128), 128, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, acc_out, amax,
+                                                          ctx->flags);
+    else
+        k_relax_acc64<3><<<grid_for(n, 128), 128, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, acc_out, amax,
+                                                          ctx->flags);
     SPH_LAUNCH_CHECK(ctx);
     return SPH_OK;
 }
@@ -1044,7 +1194,8 @@ extern "C" int sph_relax_residual(sph_ctx* ctx, const sph_relax_params* p, const
     double* partial = (double*)sph_scratch(ctx, S_RED_PARTIAL, (size_t)nb * 3 * 8 + 64, &st);
     if (st) return st;
     double* out_d = partial + (size_t)nb * 3;
-    k_relax_residual<<<nb, 256, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, partial);
+    if (p->dom.dim == 2) k_relax_residual<2><<<nb, 256, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, partial);
+    else k_relax_residual<3><<<nb, 256, 0, s>>>(pos, vol, n, L.row_ptr, L.col, S, K, partial);
     k_sum_partials<<<1, 256, 0, s>>>(partial, nb, out_d);
     SPH_LAUNCH_CHECK(ctx);
     double* hp = (double*)ctx->pinned;

@@ -209,7 +209,7 @@ def circle_body(dp, diameter=2.0, jitter=0.0, seed=0):
     h = H_FLUID * dp
     margin = 4.0 * dp
     dom = domain(2, h, 2.0, [lo - margin, lo - margin], [m * dp + 2 * margin] * 2, (False, False))
-    return {"pos": pts, "spheres": np.array([[0.0, 0.0, R]]), "vol": np.full(pts.shape[1], dp * dp),
+    return {"pos": np.ascontiguousarray(pts), "spheres": np.array([[0.0, 0.0, R]]), "vol": np.full(pts.shape[1], dp * dp),
             "domain": dom, "dp": dp, "h": h}
 
 

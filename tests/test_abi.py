@@ -89,3 +89,15 @@ def test_host_alloc_argument_checks(lib):
     assert lib.sph_host_alloc(ctypes.c_size_t(0), ctypes.byref(h), ctypes.byref(d)) == _lib.SPH_ERR_ARG
     assert lib.sph_host_alloc(ctypes.c_size_t(64), None, ctypes.byref(d)) == _lib.SPH_ERR_ARG
     assert lib.sph_host_free(None) == _lib.SPH_ERR_ARG
+
+
+def test_binding_refuses_strided_tensors():
+    import torch
+    from paper_2405_05155_gb300 import api
+    a = torch.zeros((2, 3), dtype=torch.float64)
+    assert api._p(a) is not None and api._p(None) is None
+    with pytest.raises(ValueError):
+        api._p(a.t())
+    import numpy as np
+    with pytest.raises(ValueError):
+        api._p(torch.tensor(np.asfortranarray(np.zeros((2, 3)))))
