@@ -456,6 +456,53 @@ def _bench_error_analysis(api, inputs, ctx, relax_steps=1000):
             "total_ms": start.elapsed_time(stop)}
 
 
+def _bench_dsl(api, inputs, ctx, t_end=1.2):
+    """The inviscid double shear layer of Sec. 5 (unit periodic square, float32 + Kahan, tile
+    plan): at dp = 1/128 the whole run to t = 1.2 with the truncated (1.6h) and standard (2h)
+    kernels, their ratio alpha (the paper: 0.59 on one CPU core), the difference of the two
+    velocity fields at the end and the vorticity range (weak-form gradients with B on the
+    GPU); at dp = 1/1024 (1M particles) the ms per step of both."""
+    import torch
+    out = {"workload": "inviscid double shear layer (rho = 1/30, delta = 0.05), unit periodic square, h = 1.3 dp, "
+                       "c0 = 10, acoustic Riemann two-pass step, float32 + Kahan on the tile plan"}
+    for nx in (128, 1024):
+        row = {}
+        fields = {}
+        for kappa in (2.0, 1.6):
+            case = inputs.double_shear_layer(nx, kappa=kappa)
+            sim, nnz, _ = _eulerian_case(api, ctx, case, api.SPH_FP32_KAHAN)
+            dt = case["dt"]
+            steps = int(round(t_end / dt)) if nx == 128 else 200
+            sim.step(3)
+            sim, _, order = _eulerian_case(api, ctx, case, api.SPH_FP32_KAHAN)
+            ms = _event_ms(lambda: sim.step(steps))
+            key = "kappa_%.1f" % kappa
+            row[key] = {"particles": case["pos"].shape[1], "nnz": nnz, "steps": steps,
+                        "ms_per_step": ms / steps, "pair_interactions_per_s": 2 * nnz * steps / (ms * 1e-3)}
+            if nx == 128:
+                row[key]["run_to_t_ms"] = ms
+                _, v = sim.fields()
+                d = dict(case["domain"])
+                _, gx = api.field_approx(ctx, d, sim.pos, sim.vol, sim.row_ptr, sim.col, v[0].contiguous(), B=sim.B)
+                _, gy = api.field_approx(ctx, d, sim.pos, sim.vol, sim.row_ptr, sim.col, v[1].contiguous(), B=sim.B)
+                omega = gy[0] - gx[1]
+                row[key]["vorticity_min_max_at_t_end"] = [float(omega.min()), float(omega.max())]
+                # back to the input order (the cell order depends on the cut-off)
+                inv = torch.empty(len(order), dtype=torch.int64, device=v.device)
+                inv[torch.as_tensor(order, device=v.device)] = torch.arange(len(order), device=v.device)
+                fields[kappa] = v[:, inv].clone()
+            del sim
+            torch.cuda.empty_cache()
+        row["alpha_TW_over_SW"] = row["kappa_1.6"]["ms_per_step"] / row["kappa_2.0"]["ms_per_step"]
+        if fields:
+            a, b = fields[1.6], fields[2.0]
+            row["rel_l2_TW_vs_SW_velocity_at_t_end"] = float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+            row["t_end"] = t_end
+        out["dp=1/%d" % nx] = row
+    out["paper"] = {"dp=1/128": {"cpu_s_SW": 29.99, "cpu_s_TW": 17.83, "alpha": 0.59}}
+    return out
+
+
 def _bench_mlp(api, inputs, ctx, peak_tflops):
     """BF16 tensor-core MLP: proposal forward over a 2.2M-row feature set, and training steps."""
     import torch
@@ -685,6 +732,7 @@ def run_gpu(args):
                          ("batched_64_tgv2d", lambda: _bench_batched(api, inputs, ctx, args.other_steps, peak)),
                          ("relax_8spheres_dp128", lambda: _bench_relax(api, inputs, ctx, 50, peak)),
                          ("error_analysis_circle", lambda: _bench_error_analysis(api, inputs, ctx)),
+                         ("double_shear_layer", lambda: _bench_dsl(api, inputs, ctx)),
                          ("mlp_proposal", lambda: _bench_mlp(api, inputs, ctx, bf16))):
             try:
                 workloads[name] = fn()

@@ -64,6 +64,25 @@ def tgv2d(nx=50, U=1.0, Re=100.0, rho0=1.0, c0_factor=10.0, kappa=KAPPA_TW):
             "nu": mu / rho0, "decay_rate": 8.0 * math.pi ** 2 * mu / rho0}
 
 
+def double_shear_layer(nx=128, rho=1.0 / 30.0, delta=0.05, rho0=1.0, c0_factor=10.0, kappa=KAPPA_TW):
+    """The inviscid double periodic shear layer of Sec. 5 (unit square, mu = 0):
+    u_x = tanh((y - 1/4)/rho) for y <= 1/2, tanh((3/4 - y)/rho) above; u_y = delta sin(2 pi x);
+    rho = 1/30, delta = 0.05, uniform initial pressure.  c0 = 10 U with U = max|u| = 1,
+    dt = 0.25 h/(c0 + U) (no viscous limit)."""
+    dp = 1.0 / nx
+    h = H_FLUID * dp
+    pos = lattice((nx, nx), dp)
+    x, y = pos
+    ux = np.where(y <= 0.5, np.tanh((y - 0.25) / rho), np.tanh((0.75 - y) / rho))
+    uy = delta * np.sin(2.0 * math.pi * x)
+    U = 1.0
+    c0 = c0_factor * U
+    return {"pos": pos, "v": np.stack([ux, uy]), "p": np.zeros(pos.shape[1]),
+            "vol": np.full(pos.shape[1], dp * dp),
+            "domain": domain(2, h, kappa, (0.0, 0.0), (1.0, 1.0), (True, True)),
+            "dp": dp, "rho0": rho0, "c0": c0, "mu": 0.0, "U": U, "dt": 0.25 * h / (c0 + U)}
+
+
 def tgv2d_exact_velocity(pos, U, nu, t):
     """Closed-form 2D Taylor-Green velocity at time t (incompressible solution)."""
     x, y = pos

@@ -227,3 +227,20 @@ def test_full_size_3d_tgv_sampled(ctx):
     d_o, v_o = _oracle_two_pass_sampled(s, rows)
     assert rel_l2(dr[rows], d_o) < 1e-5
     assert rel_l2(v[:, rows], v_o) < 1e-5
+
+
+def test_double_shear_layer_parity(ctx):
+    # the inviscid (mu = 0) double shear layer of Sec. 5 at 32^2, 20 steps: float64 and
+    # float32 on the tile plan against the oracle; momentum conserved on the periodic square
+    case = inputs.double_shear_layer(nx=32, kappa=1.6)
+    s = _setup(ctx, case)
+    d_o, v_o = OE.run(s["pos"], s["vol"], s["drho"], s["v"], s["B_h"], s["rp_h"], s["col_h"], s["prm"], 20)
+    for prec, tiles, tol, err in VARIANTS:
+        sim = _sim(ctx, s, case, prec, tiles=tiles)
+        sim.step(20)
+        dr, v = sim.fields()
+        assert err(host(v), v_o) < tol and err(host(dr), d_o) < max(tol, 1e-12), (prec, tiles)
+    rho = case["rho0"] + d_o
+    mom = np.sum(s["vol"] * rho * v_o, axis=1)
+    mom0 = np.sum(s["vol"] * case["rho0"] * s["v"], axis=1)
+    assert np.max(np.abs(mom - mom0)) < 1e-12

@@ -136,3 +136,24 @@ def test_two_pass_and_fused_agree_to_first_order():
         diffs.append(max(np.max(np.abs(a[1] - b[1])), np.max(np.abs(a[0] - b[0]))))
     # both are consistent one-step integrators: they differ by O(dt^2)
     assert 3.5 < diffs[0] / diffs[1] < 4.5
+
+
+def test_double_shear_layer_initial_field():
+    # the closed form of the initial velocity: u_x = +-1 far from the layers, 0 at y = 1/4
+    # and 3/4, tanh profile of thickness 1/30; u_y = 0.05 sin(2 pi x); divergence free
+    from paper_2405_05155_gb300 import inputs
+    c = inputs.double_shear_layer(nx=64)
+    x, y = c["pos"]
+    ux, uy = c["v"]
+    # +1 between the layers (y near 1/2), -1 outside them (y near 0 or 1)
+    assert np.allclose(ux[np.abs(y - 0.5) < 0.1], 1.0, atol=1e-3)
+    assert np.allclose(ux[(y < 0.1) | (y > 0.9)], -1.0, atol=1e-3)
+    # odd about each layer's centre line: u_x(1/4 + s) = -u_x(1/4 - s) on the lattice rows
+    rows = np.unique(np.round(y, 12))
+    below = rows[rows < 0.25]
+    for yb in below[-3:]:
+        ya = 0.5 - yb
+        assert np.allclose(ux[np.isclose(y, yb)], -ux[np.isclose(y, ya)])
+    assert np.allclose(ux, np.where(y <= 0.5, np.tanh((y - 0.25) * 30.0), np.tanh((0.75 - y) * 30.0)))
+    assert np.allclose(uy, 0.05 * np.sin(2.0 * np.pi * x))
+    assert c["mu"] == 0.0 and c["dt"] == 0.25 * c["domain"]["h"] / 11.0
