@@ -106,8 +106,13 @@ def _isnum(s):
 
 # --------------------------------------------------------------------------- setup
 def _setup_plate(api, inputs, ctx, kappa, dp=0.001):
+    return _setup_solid(api, ctx, inputs.plate(dp=dp, kappa=kappa))
+
+
+def _setup_solid(api, ctx, c):
+    """A total-Lagrangian case of inputs (plate, columns) on the device, in Morton order,
+    with its lists and correction matrices."""
     import torch
-    c = inputs.plate(dp=dp, kappa=kappa)
     d = c["domain"]
     dev = ctx.device
     r0 = torch.tensor(c["r0"], dtype=torch.float64, device=dev)
@@ -503,6 +508,51 @@ def _bench_dsl(api, inputs, ctx, t_end=1.2):
     return out
 
 
+def _bench_columns(api, inputs, ctx, steps=200):
+    """The twisting and bending columns of Sec. 5 (total-Lagrangian, neo-Hookean, float32 +
+    Kahan on the tile plan): ms per step with the truncated (1.6h) and standard (2h) kernels
+    at the paper's resolutions and their ratio alpha (the paper's Tables: CPU wall-clock
+    ratios); and, at the coarsest resolutions, a stability run of each column to its
+    end time with both kernels."""
+    import torch
+    out = {"workload": "3D columns, side 1 m x height 6 m, clamped base (3 layers), rho0 = 1100, E = 17 MPa, "
+                       "h = 1.15 dp; twisting: nu = 0.499, Omega = 105 sin(pi y / 12) rad/s about the axis; "
+                       "bending: nu = 0.45, v = 10 (sqrt 3 / 2, 1/2, 0) m/s",
+           "paper_alpha": {"twisting": {"1/10": 0.67, "1/20": 0.68, "1/30": 0.64},
+                           "bending": {"1/6": 0.69, "1/12": 0.47, "1/24": 0.56}}}
+    for kind, sides, t_end in (("twisting", (10, 20, 30), 0.0909), ("bending", (6, 12, 24), 0.5)):
+        rows = {}
+        for n_side in sides:
+            row = {}
+            for kappa in (2.0, 1.6):
+                c = inputs.column(kind, n_side, kappa=kappa)
+                s = _setup_solid(api, ctx, c)
+                sol = _solid(api, ctx, s, api.SPH_FP32_KAHAN)
+                sol.step(3)
+                ms = _event_ms(lambda: sol.step(steps))
+                key = "kappa_%.1f" % kappa
+                row[key] = {"particles": s["n"], "nnz": s["nnz"], "ms_per_step": ms / steps,
+                            "pair_interactions_per_s": 2 * s["nnz"] * steps / (ms * 1e-3), "dt": c["dt"]}
+                if n_side == sides[0]:
+                    # the whole run to t_end from the initial state
+                    sol = _solid(api, ctx, s, api.SPH_FP32_KAHAN)
+                    nsteps = int(round(t_end / c["dt"]))
+                    ms_run = _event_ms(lambda: sol.step(nsteps))
+                    x, v, H = sol.fields()
+                    top = s["r0"][1] >= s["r0"][1].max() - 1e-9
+                    disp = (x - s["r0"])[:, top].mean(dim=1)
+                    row[key].update({"t_end": t_end, "run_steps": nsteps, "run_ms": ms_run,
+                                     "finite": bool(torch.isfinite(x).all() and torch.isfinite(v).all()),
+                                     "top_mean_displacement_m": [float(u) for u in disp],
+                                     "max_speed": float(torch.sqrt((v * v).sum(0)).max())})
+                del sol
+                torch.cuda.empty_cache()
+            row["alpha_TW_over_SW"] = row["kappa_1.6"]["ms_per_step"] / row["kappa_2.0"]["ms_per_step"]
+            rows["1/%d" % n_side] = row
+        out[kind] = rows
+    return out
+
+
 def _bench_mlp(api, inputs, ctx, peak_tflops):
     """BF16 tensor-core MLP: proposal forward over a 2.2M-row feature set, and training steps."""
     import torch
@@ -733,6 +783,7 @@ def run_gpu(args):
                          ("relax_8spheres_dp128", lambda: _bench_relax(api, inputs, ctx, 50, peak)),
                          ("error_analysis_circle", lambda: _bench_error_analysis(api, inputs, ctx)),
                          ("double_shear_layer", lambda: _bench_dsl(api, inputs, ctx)),
+                         ("columns", lambda: _bench_columns(api, inputs, ctx)),
                          ("mlp_proposal", lambda: _bench_mlp(api, inputs, ctx, bf16))):
             try:
                 workloads[name] = fn()

@@ -150,6 +150,49 @@ def plate(dp=0.001, length=0.2, thickness=0.02, width=0.2, root_layers=4,
             "c0": c0, "dt": dt}
 
 
+def column(kind="twisting", n_side=10, side=1.0, height=6.0, root_layers=3, rho0=1100.0, E=17.0e6, nu=None,
+           omega0=105.0, v0=10.0, kappa=KAPPA_TW):
+    """The 3D columns of Sec. 5 (total-Lagrangian solids): a square section side x side in
+    x-z (side / dp = n_side), height along y in [0, height), clamped below, y in
+    [-root_layers dp, 0).
+      twisting: nu = 0.499, rotation about the column axis with rate
+                Omega(y) = omega0 sin(pi y / (2 height)): v = Omega(y) y_hat x (r - axis);
+      bending:  nu = 0.45, uniform v = v0 (sqrt(3)/2, 1/2, 0).
+    rho0 = 1100, E = 17 MPa, h = 1.15 dp, dt = 0.5 h/(c0 + v_max)."""
+    if nu is None:
+        nu = 0.499 if kind == "twisting" else 0.45
+    dp = side / n_side
+    ny = int(round(height / dp)) + root_layers
+    lo = (0.0, -root_layers * dp, 0.0)
+    r0 = lattice((n_side, ny, n_side), dp, lo)
+    fixed = (r0[1] < 0.0).astype(np.uint8)
+    v = np.zeros_like(r0)
+    if kind == "twisting":
+        rate = omega0 * np.sin(math.pi * r0[1] / (2.0 * height))
+        dx, dz = r0[0] - 0.5 * side, r0[2] - 0.5 * side
+        v[0] = rate * dz
+        v[2] = -rate * dx
+    elif kind == "bending":
+        v[0] = v0 * math.sqrt(3.0) / 2.0
+        v[1] = v0 * 0.5
+    else:
+        raise ValueError(kind)
+    v[:, fixed == 1] = 0.0
+    K = E / (3.0 * (1.0 - 2.0 * nu))
+    c0 = math.sqrt(K / rho0)
+    h = H_SOLID * dp
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    G = E / (2.0 * (1.0 + nu))
+    vmax = float(np.max(np.sqrt(np.sum(v * v, axis=0))))
+    dt = 0.5 * h / (c0 + vmax)
+    margin = 2.0 * dp
+    dom = domain(3, h, kappa, (-margin, lo[1] - margin, -margin),
+                 (side + 2 * margin, ny * dp + 2 * margin, side + 2 * margin), (False, False, False))
+    return {"r0": r0, "v": v, "fixed": fixed, "vol": np.full(r0.shape[1], dp ** 3),
+            "domain": dom, "dp": dp, "rho0": rho0, "E": E, "nu": nu, "lam": lam, "G": G,
+            "c0": c0, "dt": dt}
+
+
 def beam2d(dp=0.002, length=0.2, thickness=0.02, root_layers=4, periodic_x=False, rho0=1000.0, E=2.0e6,
            nu=0.3975, amp_factor=0.05, kappa=KAPPA_TW):
     """2D total-Lagrangian strip in x-y: the plate's section.

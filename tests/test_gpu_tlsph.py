@@ -274,3 +274,24 @@ def test_state_in_mapped_host_memory(ctx):
     finally:
         for m in mapped:
             m.close()
+
+
+@pytest.mark.parametrize("kind", ["twisting", "bending"])
+def test_columns_parity(ctx, kind):
+    # the columns of Sec. 5 at side / dp = 4: float64 and float32 (tile plan and per pair)
+    # against the oracle after 10 steps
+    case = inputs.column(kind, 4)
+    s = _setup(ctx, case=case)
+    n = s["r0"].shape[1]
+    x_o, v_o, F_o = s["r0"].copy(), s["v"].copy(), np.tile(np.eye(3), (n, 1, 1))
+    for _ in range(10):
+        x_o, v_o, F_o = OT.step(s["r0"], s["vol"], s["B0_h"], s["fixed"], x_o, v_o, F_o, s["rp_h"], s["col_h"],
+                                s["prm"])
+    H_o = (F_o - np.eye(3)).reshape(n, 9).T
+    for prec, tiles, tol, err in VARIANTS:
+        sol = _solid(ctx, s, prec, OT.NEO_HOOKEAN, tiles=tiles)
+        sol.step(10)
+        x, v, H = sol.fields()
+        assert err(host(v), v_o) < tol, (prec, tiles, err(host(v), v_o))
+        assert err(host(x) - s["r0"], x_o - s["r0"]) < tol
+        assert err(host(H), H_o) < tol, (prec, tiles, err(host(H), H_o))

@@ -88,3 +88,23 @@ def test_energy_is_nearly_conserved():
     assert pe > 0.01 * e0          # energy moved into the strain field
     assert abs(ke + pe - e0) < 0.01 * e0
     assert np.all(v[:, c["fixed"] == 1] == 0.0)
+
+
+def test_column_initial_fields():
+    # Sec. 5 columns: the twisting field is a rotation of each horizontal slice about the
+    # column axis at rate 105 sin(pi y / 12); the bending field is uniform; the base is clamped
+    from paper_2405_05155_gb300 import inputs
+    c = inputs.column("twisting", 6)
+    x, y, z = c["r0"]
+    vx, vy, vz = c["v"]
+    free = c["fixed"] == 0
+    dx, dz = x - 0.5, z - 0.5
+    assert np.all(c["v"][:, ~free] == 0.0)
+    assert np.max(np.abs((vx * dx + vz * dz)[free])) < 1e-12
+    rate = 105.0 * np.sin(np.pi * y / 12.0)
+    assert np.allclose(np.hypot(vx, vz)[free], (np.abs(rate) * np.hypot(dx, dz))[free])
+    assert np.all(vy == 0.0) and c["nu"] == 0.499
+    b = inputs.column("bending", 6)
+    free = b["fixed"] == 0
+    assert np.allclose(b["v"][:, free], np.array([[10 * np.sqrt(3) / 2], [5.0], [0.0]]))
+    assert b["nu"] == 0.45 and np.isclose(b["G"], 17e6 / 2.9)
