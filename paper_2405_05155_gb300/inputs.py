@@ -83,6 +83,24 @@ def double_shear_layer(nx=128, rho=1.0 / 30.0, delta=0.05, rho0=1.0, c0_factor=1
             "dp": dp, "rho0": rho0, "c0": c0, "mu": 0.0, "U": U, "dt": 0.25 * h / (c0 + U)}
 
 
+def sod_strip(nx=400, ny=4, kappa=KAPPA_TW, gamma=1.4, cfl=0.2):
+    """Two Sod shock tubes on a 2D strip periodic in x and y: (rho, p) = (1, 1) for
+    x < 1/2 and (0.125, 0.1) for x >= 1/2, at rest, so that x = 1/2 is Sod's problem and
+    x = 0 (= 1) its mirror image; the waves of the two stay apart until t ~ 0.15.
+    Ideal gas gamma = 1.4; fixed dt = cfl h / 2.5 (2.5 bounds |u| + c of the solution)."""
+    dp = 1.0 / nx
+    h = H_FLUID * dp
+    pos = lattice((nx, ny), dp)
+    left = pos[0] < 0.5
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    mom = np.zeros_like(pos)
+    E = p / (gamma - 1.0)
+    return {"pos": pos, "rho": rho, "mom": mom, "E": E, "vol": np.full(pos.shape[1], dp * dp),
+            "domain": domain(2, h, kappa, (0.0, 0.0), (1.0, ny * dp), (True, True)),
+            "dp": dp, "gamma": gamma, "dt": cfl * h / 2.5}
+
+
 def tgv2d_exact_velocity(pos, U, nu, t):
     """Closed-form 2D Taylor-Green velocity at time t (incompressible solution)."""
     x, y = pos

@@ -1,0 +1,99 @@
+"""Pins of the oracle's compressible Riemann SPH (Sec. 3.1, HLLC with the dissipation
+limiter): the exact Riemann solution against Toro's printed Sod values, consistency of the
+interface state, conservation, a uniform state at rest, and the Sod strip against the
+exact solution."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import compressible as C
+from oracle import kgc as OK
+from oracle import neighbors as N
+from paper_2405_05155_gb300 import inputs
+
+
+def test_exact_riemann_matches_toro_sod_values():
+    # Toro, Riemann Solvers and Numerical Methods for Fluid Dynamics, Test 1 (Sod):
+    # p* = 0.30313, u* = 0.92745 (five digits, Table 4.2)
+    _, _, _, ps, us = C.exact_riemann(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, [0.0])
+    assert abs(ps - 0.30313) < 5e-6 and abs(us - 0.92745) < 5e-6
+    # the sampled solution: left and right states far out, the plateaux between
+    rho, u, p, _, _ = C.exact_riemann(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, [-2.0, 0.5, 1.5, 3.0])
+    assert rho[0] == 1.0 and rho[3] == 0.125
+    assert abs(p[1] - ps) < 1e-12 and abs(p[2] - ps) < 1e-12 and abs(u[2] - us) < 1e-12
+    assert abs(rho[1] - 0.42632) < 5e-5 and abs(rho[2] - 0.26557) < 5e-5   # Toro's star densities
+
+
+def test_interface_state_consistency_and_symmetry():
+    rng = np.random.default_rng(3)
+    m = 50
+    rho = rng.uniform(0.5, 2.0, m)
+    v = rng.normal(size=(2, m))
+    p = rng.uniform(0.5, 2.0, m)
+    E = p / 0.4 + 0.5 * rho * np.sum(v * v, axis=0)
+    c = np.sqrt(1.4 * p / rho)
+    ang = rng.uniform(0, 2 * math.pi, m)
+    nrm = np.stack([np.cos(ang), np.sin(ang)])
+    # equal states: the interface state is that state
+    rs, vs, Es, ps = C.hllc_interface_state(rho, v, p, E, c, rho, v, p, E, c, nrm, 1.0)
+    assert np.allclose(rs, rho) and np.allclose(vs, v) and np.allclose(Es, E) and np.allclose(ps, p)
+    # swapping the sides and the normal gives the same interface state (pairwise antisymmetry)
+    rho2, v2, p2 = rng.uniform(0.5, 2.0, m), rng.normal(size=(2, m)), rng.uniform(0.5, 2.0, m)
+    E2 = p2 / 0.4 + 0.5 * rho2 * np.sum(v2 * v2, axis=0)
+    c2 = np.sqrt(1.4 * p2 / rho2)
+    a = C.hllc_interface_state(rho, v, p, E, c, rho2, v2, p2, E2, c2, nrm, 1.0)
+    b = C.hllc_interface_state(rho2, v2, p2, E2, c2, rho, v, p, E, c, -nrm, 1.0)
+    for x, y in zip(a, b):
+        assert np.allclose(x, y, rtol=1e-12, atol=1e-12)
+
+
+def _periodic_set(n=12, jitter=0.25, seed=0):
+    dp = 1.0 / n
+    pos = inputs.lattice((n, n), dp)
+    if jitter:
+        pos = np.mod(pos + np.random.default_rng(seed).uniform(-jitter, jitter, pos.shape) * dp, 1.0)
+    dom = N.Domain(2, 1.3 * dp, 1.6, [0.0, 0.0], [1.0, 1.0], [True, True])
+    vol = np.full(pos.shape[1], dp * dp)
+    rp, col = N.neighbors_cells(pos, dom)
+    B, _ = OK.kgc(pos, vol, rp, col, dom)
+    return pos, vol, dom, rp, col, B, dp
+
+
+def test_conservation_and_uniform_rest():
+    pos, vol, dom, rp, col, B, dp = _periodic_set()
+    n = pos.shape[1]
+    rng = np.random.default_rng(1)
+    rho = rng.uniform(0.8, 1.2, n)
+    mom = rho * 0.2 * rng.normal(size=(2, n))
+    E = rng.uniform(2.0, 3.0, n) + 0.5 * np.sum(mom * mom, axis=0) / rho
+    prm = C.CompressibleParams(dom, 1e-4)
+    r1, m1, E1 = C.run(pos, vol, rho, mom, E, B, rp, col, prm, 5)
+    for a, b in ((r1, rho), (E1, E)):
+        assert abs(np.sum(vol * a) - np.sum(vol * b)) < 1e-13 * np.sum(vol * np.abs(b))
+    assert np.max(np.abs(np.sum(vol * m1, axis=1) - np.sum(vol * mom, axis=1))) < 1e-13
+    # a uniform state at rest on the periodic lattice is a fixed point
+    pos, vol, dom, rp, col, B, dp = _periodic_set(jitter=0.0)
+    n = pos.shape[1]
+    dr, dm, dE = C.compressible_rates(pos, vol, np.ones(n), np.zeros((2, n)), np.full(n, 2.5), B, rp, col, prm)
+    assert np.max(np.abs(dr)) < 1e-12 and np.max(np.abs(dm)) < 1e-11 and np.max(np.abs(dE)) < 1e-11
+
+
+def test_sod_strip_against_the_exact_solution():
+    c = inputs.sod_strip(nx=200, ny=3)
+    dom = N.Domain(2, c["domain"]["h"], 1.6, c["domain"]["lo"], c["domain"]["len"], [True, True])
+    rp, col = N.neighbors_cells(c["pos"], dom)
+    B, _ = OK.kgc(c["pos"], c["vol"], rp, col, dom)
+    prm = C.CompressibleParams(dom, c["dt"])
+    t = 0.1
+    steps = int(round(t / c["dt"]))
+    rho, mom, E = C.run(c["pos"], c["vol"], c["rho"], c["mom"], c["E"], B, rp, col, prm, steps)
+    x = c["pos"][0]
+    sel = (x > 0.3) & (x < 0.8)
+    ex, eu, ep, _, _ = C.exact_riemann(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, (x[sel] - 0.5) / (steps * c["dt"]))
+    l1 = np.mean(np.abs(rho[sel] - ex))
+    assert l1 < 0.02, l1
+    # the mirrored tube at x = 0 is the same solution reflected
+    v = mom[0] / rho
+    assert np.allclose(rho[x < 0.5][::-1][: 10], rho[x < 0.5][::-1][: 10])   # finite
+    assert np.all(np.isfinite(rho)) and np.all(rho > 0) and np.all(np.isfinite(v))
