@@ -553,6 +553,61 @@ def _bench_columns(api, inputs, ctx, steps=200):
     return out
 
 
+def _compressible_case(api, ctx, c):
+    import torch
+    d = c["domain"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pos = torch.as_tensor(c["pos"], dtype=torch.float64, device=dev)
+    order = api.cell_order(ctx, d, pos)
+    pos = pos[:, order].contiguous()
+    vol = torch.as_tensor(c["vol"], dtype=torch.float64, device=dev)[order].contiguous()
+    rp, col = api.build_neighbors(ctx, d, pos)
+    B, _, _ = api.kgc(ctx, d, pos, vol, rp, col)
+    oh = order.cpu().numpy()
+    sim = api.Compressible(ctx, d, pos, vol, B, rp, col, c["rho"][oh], c["mom"][:, oh], c["E"][oh], c["dt"],
+                           gamma=c["gamma"])
+    return sim, int(col.numel()), oh
+
+
+def _bench_compressible(api, inputs, ctx, steps=200):
+    """Compressible Riemann SPH (Sec. 3.1, limited HLLC, float64): ms per step of a
+    4096 x 64 Sod strip (262,144 particles) with the truncated (1.6h) and standard (2h)
+    kernels and their ratio alpha; and at 1024 x 8 the whole run to t = 0.1 with both
+    kernels and the relative L1 difference of their density fields."""
+    import numpy as np
+    import torch
+    out = {"workload": "2D Sod strip periodic in x and y (two mirrored Sod tubes), ideal gas gamma = 1.4, "
+                       "h = 1.3 dp, dt = 0.2 h / 2.5, forward Euler, HLLC with the dissipation limiter (eta = 1), "
+                       "float64, one thread per particle"}
+    for nx, ny, full in ((4096, 64, False), (1024, 8, True)):
+        row = {}
+        rho_end = {}
+        for kappa in (2.0, 1.6):
+            c = inputs.sod_strip(nx=nx, ny=ny, kappa=kappa)
+            sim, nnz, oh = _compressible_case(api, ctx, c)
+            nsteps = int(round(0.1 / c["dt"])) if full else steps
+            if not full:
+                sim.step(3)
+            ms = _event_ms(lambda: sim.step(nsteps))
+            key = "kappa_%.1f" % kappa
+            row[key] = {"particles": int(sim.n), "nnz": nnz, "steps": nsteps, "ms_per_step": ms / nsteps,
+                        "pair_evaluations_per_s": nnz * nsteps / (ms * 1e-3)}
+            if full:
+                rho = np.empty(sim.n)
+                rho[oh] = sim.rho.cpu().numpy()          # back to the input order
+                rho_end[kappa] = rho
+                row[key]["run_to_t_ms"] = ms
+                row[key]["rho_min_max_at_t_end"] = [float(rho.min()), float(rho.max())]
+            del sim
+            torch.cuda.empty_cache()
+        row["alpha_TW_over_SW"] = row["kappa_1.6"]["ms_per_step"] / row["kappa_2.0"]["ms_per_step"]
+        if rho_end:
+            a, b = rho_end[1.6], rho_end[2.0]
+            row["rel_l1_TW_vs_SW_density_at_t_0.1"] = float(np.sum(np.abs(a - b)) / np.sum(np.abs(b)))
+        out["%dx%d" % (nx, ny)] = row
+    return out
+
+
 def _bench_mlp(api, inputs, ctx, peak_tflops):
     """BF16 tensor-core MLP: proposal forward over a 2.2M-row feature set, and training steps."""
     import torch
@@ -784,7 +839,10 @@ def run_gpu(args):
                          ("error_analysis_circle", lambda: _bench_error_analysis(api, inputs, ctx)),
                          ("double_shear_layer", lambda: _bench_dsl(api, inputs, ctx)),
                          ("columns", lambda: _bench_columns(api, inputs, ctx)),
+                         ("compressible_sod", lambda: _bench_compressible(api, inputs, ctx)),
                          ("mlp_proposal", lambda: _bench_mlp(api, inputs, ctx, bf16))):
+            if args.rows and name not in args.rows.split(","):
+                continue
             try:
                 workloads[name] = fn()
             except Exception as exc:      # report, do not hide: the headline line still prints
@@ -858,6 +916,7 @@ def main():
     ap.add_argument("--kappa", type=float, default=1.6)
     ap.add_argument("--lanes", type=int, default=0, help="lanes per particle of the TL passes (0: tuned)")
     ap.add_argument("--headline-only", action="store_true", help="skip the other rows' workloads")
+    ap.add_argument("--rows", default="", help="comma-separated names of the other rows to run (default: all)")
     ap.add_argument("--other-steps", type=int, default=100, help="timed steps of the other Eulerian workloads")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured for this build")

@@ -508,6 +508,53 @@ int sph_relax_accel(sph_ctx* ctx, const sph_relax_params* prm, const double* pos
 int sph_relax_residual(sph_ctx* ctx, const sph_relax_params* prm, const double* pos,
                        const double* vol, double* out_host, void* stream);
 
+/* ---- x2: compressible Riemann SPH (Sec. 3.1, Eqs. 15-24) ----
+ * Eulerian particles (fixed positions, volumes V_i) carry the conserved rho, rho v and
+ * E = rho |v|^2/2 + rho e of an ideal gas, p = (gamma - 1) rho e, c^2 = gamma p/rho.
+ * Eq. 18 divided by V_i, with g_ij = (B_i + B_j)/2 grad W_ij (Eq. 27, Wendland kernel
+ * cut at dom.kappa, B of sph_kgc):
+ *   d rho_i/dt     = -2 sum_j V_j rho_s (v_s . g_ij)
+ *   d(rho v)_i/dt  = -2 sum_j V_j [rho_s v_s (v_s . g_ij) + p_s g_ij]
+ *   dE_i/dt        = -2 sum_j V_j (E_s + p_s) (v_s . g_ij)
+ * where (rho_s, v_s, E_s, p_s) is the interface state of the HLLC solver with the
+ * dissipation limiter along n = -e_ij (left = i):
+ *   S_l = u_l - c_l, S_r = u_r + c_r, beta = min(eta max((u_l - u_r)/c_bar, 0), 1),
+ *   u* = (rho_l c_l u_l + rho_r c_r u_r + beta^2 (p_l - p_r))/(rho_l c_l + rho_r c_r),
+ *   p* = (p_l + p_r)/2 + beta [rho_r c_r (u* - u_r) + rho_l c_l (u_l - u*)]/2,
+ *   v* = u* n + (v_l + v_r)/2 - (u_l + u_r) n/2,
+ *   rho*_k = rho_k (S_k - u_k)/(S_k - u*), E*_k = ((S_k - u_k) E_k - p_k u_k + p* u*)/(S_k - u*);
+ * the left (right) state when S_l >= 0 and S_r > 0 (S_r <= 0 and S_l < 0), else the left
+ * star (u* > 0), the right star (u* < 0) or their mean (u* = 0).  The paper prints |v|
+ * in rho* and E*, and a minus in the limited p*: the normal velocity and the plus of the
+ * unlimited HLLC p* are used (both needed for the pairwise antisymmetry that conserves
+ * mass, momentum and energy).  Time integration: forward Euler with the fixed dt.
+ * Float64 only (precision must be SPH_FP64).  Minimum image on periodic axes. */
+typedef struct {
+    sph_domain dom;
+    double dt, gamma, eta;          /* gamma = 1.4 and eta = 1 in the paper */
+    int32_t precision;              /* SPH_FP64 */
+    int32_t reserved;
+} sph_compressible_params;
+
+typedef struct {
+    const int64_t* row_ptr;         /* CSR lists of sph_build_neighbors */
+    const int32_t* col;
+    const double* pos;              /* [dim][n] */
+    const double* vol;              /* [n] */
+    const double* B;                /* [d(d+1)/2][n], sph_kgc */
+    double* rho;                    /* [n], advanced in place by sph_compressible_step */
+    double* mom;                    /* [dim][n] */
+    double* E;                      /* [n] */
+} sph_compressible_state;
+
+/* Rates of Eq. 18 at the current state: drho [n], dmom [dim][n], dE [n]. */
+int sph_compressible_rates(sph_ctx* ctx, const sph_compressible_params* prm,
+                           const sph_compressible_state* st, double* drho, double* dmom,
+                           double* dE, void* stream);
+/* nsteps forward-Euler steps of (rho, rho v, E) in place. */
+int sph_compressible_step(sph_ctx* ctx, const sph_compressible_params* prm,
+                          const sph_compressible_state* st, int nsteps, void* stream);
+
 /* ---- x1: SPH approximations for the error analysis (Sec. 2.3.3) ----
  * For a field f (float64 [n]) on the particles, over the pairs of CSR lists of
  * sph_build_neighbors at dom->kappa and with the kernel `kernel`

@@ -33,6 +33,11 @@ class Domain:
         self.lo = np.array(lo, dtype=np.float64)[: self.dim]
         self.len = np.array(length, dtype=np.float64)[: self.dim]
         self.periodic = tuple(bool(p) for p in periodic)[: self.dim]
+        for k in range(self.dim):
+            # one minimum-image shift finds every neighbour only if the box spans two cut-offs
+            if self.periodic[k] and self.len[k] < 2.0 * self.kappa * self.h:
+                raise ValueError("periodic box %g on axis %d is below 2 kappa h = %g"
+                                 % (self.len[k], k, 2.0 * self.kappa * self.h))
 
     @property
     def rc(self):

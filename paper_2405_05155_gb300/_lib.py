@@ -72,6 +72,15 @@ class RelaxParams(ctypes.Structure):
                 ("spheres", c_dbl * (4 * SPH_MAX_SPHERES))]
 
 
+class CompressibleParams(ctypes.Structure):
+    _fields_ = [("dom", SphDomain), ("dt", c_dbl), ("gamma", c_dbl), ("eta", c_dbl), ("precision", c_i32),
+                ("reserved", c_i32)]
+
+
+class CompressibleState(ctypes.Structure):
+    _fields_ = [(name, c_vp) for name in ("row_ptr", "col", "pos", "vol", "B", "rho", "mom", "E")]
+
+
 _P = ctypes.POINTER
 _SIGNATURES = {
     "sph_create": (ctypes.c_int, [_P(c_vp), ctypes.c_int]),
@@ -114,6 +123,10 @@ _SIGNATURES = {
     "sph_tlsph_plan": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp]),
     "sph_set_stage_cap": (ctypes.c_int, [c_vp, ctypes.c_int]),
     "sph_set_relax_skin": (ctypes.c_int, [c_vp, ctypes.c_double]),
+    "sph_compressible_rates": (ctypes.c_int, [c_vp, _P(CompressibleParams), _P(CompressibleState), c_vp, c_vp,
+                                              c_vp, c_vp]),
+    "sph_compressible_step": (ctypes.c_int, [c_vp, _P(CompressibleParams), _P(CompressibleState), ctypes.c_int,
+                                             c_vp]),
     "sph_field_approx": (ctypes.c_int, [c_vp, _P(SphDomain), ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                         c_vp, c_vp, c_vp]),
     "sph_host_alloc": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp)]),

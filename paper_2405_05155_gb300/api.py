@@ -271,6 +271,43 @@ class Eulerian:
         return self.drho, self.v
 
 
+class Compressible:
+    """Compressible Eulerian SPH state on the device (sph_compressible_*, float64):
+    rho [n], mom = rho v [dim][n] and E [n] advanced in place."""
+
+    def __init__(self, ctx, dom, pos, vol, B, row_ptr, col, rho, mom, E, dt, gamma=1.4, eta=1.0):
+        dev = ctx.device
+        self.ctx = ctx
+        self.n = pos.shape[1]
+        self.dim = dom["dim"]
+        self.prm = L.CompressibleParams()
+        self.prm.dom = make_domain(dom, self.n)
+        self.prm.dt, self.prm.gamma, self.prm.eta = dt, gamma, eta
+        self.prm.precision = SPH_FP64
+        self.pos, self.vol, self.B = _dev_f64(pos, dev), _dev_f64(vol, dev), _dev_f64(B, dev)
+        self.row_ptr, self.col = row_ptr, col
+        self.rho, self.mom, self.E = (_dev_f64(rho, dev).clone(), _dev_f64(mom, dev).clone(),
+                                      _dev_f64(E, dev).clone())
+        self.st = L.CompressibleState()
+        for name in ("row_ptr", "col", "pos", "vol", "B", "rho", "mom", "E"):
+            setattr(self.st, name, getattr(self, name).data_ptr())
+
+    def _call(self, name, *args):
+        fn = getattr(self.ctx.lib, name)
+        L.check(name, fn(self.ctx.h, ctypes.byref(self.prm), ctypes.byref(self.st), *args), self.ctx.h)
+
+    def rates(self):
+        dev = self.rho.device
+        drho = torch.empty(self.n, dtype=torch.float64, device=dev)
+        dmom = torch.empty((self.dim, self.n), dtype=torch.float64, device=dev)
+        dE = torch.empty(self.n, dtype=torch.float64, device=dev)
+        self._call("sph_compressible_rates", _p(drho), _p(dmom), _p(dE), _stream())
+        return drho, dmom, dE
+
+    def step(self, nsteps=1):
+        self._call("sph_compressible_step", int(nsteps), _stream())
+
+
 class TLSolid:
     """Total-Lagrangian solid state on the device."""
 

@@ -83,13 +83,15 @@ def double_shear_layer(nx=128, rho=1.0 / 30.0, delta=0.05, rho0=1.0, c0_factor=1
             "dp": dp, "rho0": rho0, "c0": c0, "mu": 0.0, "U": U, "dt": 0.25 * h / (c0 + U)}
 
 
-def sod_strip(nx=400, ny=4, kappa=KAPPA_TW, gamma=1.4, cfl=0.2):
+def sod_strip(nx=400, ny=8, kappa=KAPPA_TW, gamma=1.4, cfl=0.2):
     """Two Sod shock tubes on a 2D strip periodic in x and y: (rho, p) = (1, 1) for
     x < 1/2 and (0.125, 0.1) for x >= 1/2, at rest, so that x = 1/2 is Sod's problem and
     x = 0 (= 1) its mirror image; the waves of the two stay apart until t ~ 0.15.
     Ideal gas gamma = 1.4; fixed dt = cfl h / 2.5 (2.5 bounds |u| + c of the solution)."""
     dp = 1.0 / nx
     h = H_FLUID * dp
+    if ny * dp < 2.0 * kappa * h:
+        raise ValueError("the strip must span two cut-offs: ny >= %g" % (2.0 * kappa * H_FLUID))
     pos = lattice((nx, ny), dp)
     left = pos[0] < 0.5
     rho = np.where(left, 1.0, 0.125)

@@ -80,7 +80,7 @@ def test_conservation_and_uniform_rest():
 
 
 def test_sod_strip_against_the_exact_solution():
-    c = inputs.sod_strip(nx=200, ny=3)
+    c = inputs.sod_strip(nx=200, ny=6)
     dom = N.Domain(2, c["domain"]["h"], 1.6, c["domain"]["lo"], c["domain"]["len"], [True, True])
     rp, col = N.neighbors_cells(c["pos"], dom)
     B, _ = OK.kgc(c["pos"], c["vol"], rp, col, dom)
@@ -97,3 +97,11 @@ def test_sod_strip_against_the_exact_solution():
     v = mom[0] / rho
     assert np.allclose(rho[x < 0.5][::-1][: 10], rho[x < 0.5][::-1][: 10])   # finite
     assert np.all(np.isfinite(rho)) and np.all(rho > 0) and np.all(np.isfinite(v))
+
+
+def test_narrow_periodic_strip_is_refused():
+    # a periodic box below two cut-offs would hide the second image of a neighbour
+    with pytest.raises(ValueError):
+        inputs.sod_strip(nx=200, ny=3, kappa=2.0)
+    with pytest.raises(ValueError):
+        N.Domain(2, 0.01, 2.0, [0, 0], [1.0, 0.03], [True, True])
