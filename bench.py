@@ -553,7 +553,7 @@ def _bench_columns(api, inputs, ctx, steps=200):
     return out
 
 
-def _compressible_case(api, ctx, c):
+def _compressible_case(api, ctx, c, precision):
     import torch
     d = c["domain"]
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -565,45 +565,61 @@ def _compressible_case(api, ctx, c):
     B, _, _ = api.kgc(ctx, d, pos, vol, rp, col)
     oh = order.cpu().numpy()
     sim = api.Compressible(ctx, d, pos, vol, B, rp, col, c["rho"][oh], c["mom"][:, oh], c["E"][oh], c["dt"],
-                           gamma=c["gamma"])
+                           gamma=c["gamma"], precision=precision)
     return sim, int(col.numel()), oh
 
 
-def _bench_compressible(api, inputs, ctx, steps=200):
-    """Compressible Riemann SPH (Sec. 3.1, limited HLLC, float64): ms per step of a
-    4096 x 64 Sod strip (262,144 particles) with the truncated (1.6h) and standard (2h)
-    kernels and their ratio alpha; and at 1024 x 8 the whole run to t = 0.1 with both
-    kernels and the relative L1 difference of their density fields."""
+def _comp_bytes(n, nnz, dim):
+    """Algorithmic bytes of one float32 compressible step: per pair the plan entry (20 B in
+    2D, 32 B in 3D); per particle its row offsets (16 B), its record (32 B), the float64
+    state read and written (2 x (dim + 2) x 8 B) and the next record written (32 B).  The
+    neighbours' records (32 B per particle) stay in L2 across the pairs that read them."""
+    per_pair = (20 if dim == 2 else 32)
+    return nnz * per_pair + n * (16 + 32 + 2 * (dim + 2) * 8 + 32)
+
+
+def _bench_compressible(api, inputs, ctx, peak, steps=200):
+    """Compressible Riemann SPH (Sec. 3.1, limited HLLC): ms per step of a 4096 x 64 Sod
+    strip (262,144 particles) with the truncated (1.6h) and standard (2h) kernels and their
+    ratio alpha, in the float32 form (the plan of fixed pair geometry, one kernel per step)
+    and the float64 form; and at 1024 x 8 the whole run to t = 0.1 with both kernels and
+    the relative L1 difference of their density fields."""
     import numpy as np
     import torch
     out = {"workload": "2D Sod strip periodic in x and y (two mirrored Sod tubes), ideal gas gamma = 1.4, "
-                       "h = 1.3 dp, dt = 0.2 h / 2.5, forward Euler, HLLC with the dissipation limiter (eta = 1), "
-                       "float64, one thread per particle"}
+                       "h = 1.3 dp, dt = 0.2 h / 2.5, forward Euler, HLLC with the dissipation limiter (eta = 1)"}
+    forms = (("fp32_kahan", api.SPH_FP32_KAHAN), ("fp64", api.SPH_FP64))
     for nx, ny, full in ((4096, 64, False), (1024, 8, True)):
         row = {}
-        rho_end = {}
-        for kappa in (2.0, 1.6):
-            c = inputs.sod_strip(nx=nx, ny=ny, kappa=kappa)
-            sim, nnz, oh = _compressible_case(api, ctx, c)
-            nsteps = int(round(0.1 / c["dt"])) if full else steps
-            if not full:
-                sim.step(3)
-            ms = _event_ms(lambda: sim.step(nsteps))
-            key = "kappa_%.1f" % kappa
-            row[key] = {"particles": int(sim.n), "nnz": nnz, "steps": nsteps, "ms_per_step": ms / nsteps,
-                        "pair_evaluations_per_s": nnz * nsteps / (ms * 1e-3)}
-            if full:
-                rho = np.empty(sim.n)
-                rho[oh] = sim.rho.cpu().numpy()          # back to the input order
-                rho_end[kappa] = rho
-                row[key]["run_to_t_ms"] = ms
-                row[key]["rho_min_max_at_t_end"] = [float(rho.min()), float(rho.max())]
-            del sim
-            torch.cuda.empty_cache()
-        row["alpha_TW_over_SW"] = row["kappa_1.6"]["ms_per_step"] / row["kappa_2.0"]["ms_per_step"]
-        if rho_end:
-            a, b = rho_end[1.6], rho_end[2.0]
-            row["rel_l1_TW_vs_SW_density_at_t_0.1"] = float(np.sum(np.abs(a - b)) / np.sum(np.abs(b)))
+        for fname, prec in forms:
+            frow = {}
+            rho_end = {}
+            for kappa in (2.0, 1.6):
+                c = inputs.sod_strip(nx=nx, ny=ny, kappa=kappa)
+                sim, nnz, oh = _compressible_case(api, ctx, c, prec)
+                nsteps = int(round(0.1 / c["dt"])) if full else (steps if prec == api.SPH_FP64 else 10 * steps)
+                if not full:
+                    sim.step(3)
+                ms = _event_ms(lambda: sim.step(nsteps))
+                key = "kappa_%.1f" % kappa
+                frow[key] = {"particles": int(sim.n), "nnz": nnz, "steps": nsteps, "ms_per_step": ms / nsteps,
+                             "pair_evaluations_per_s": nnz * nsteps / (ms * 1e-3)}
+                if prec == api.SPH_FP32_KAHAN and not full:
+                    frow[key]["roofline"] = _roof(_comp_bytes(sim.n, nnz, 2), ms / nsteps, peak)
+                    frow[key]["roofline"]["kernel"] = "k_comp32"
+                if full:
+                    rho = np.empty(sim.n)
+                    rho[oh] = sim.rho.cpu().numpy()          # back to the input order
+                    rho_end[kappa] = rho
+                    frow[key]["run_to_t_ms"] = ms
+                    frow[key]["rho_min_max_at_t_end"] = [float(rho.min()), float(rho.max())]
+                del sim
+                torch.cuda.empty_cache()
+            frow["alpha_TW_over_SW"] = frow["kappa_1.6"]["ms_per_step"] / frow["kappa_2.0"]["ms_per_step"]
+            if rho_end:
+                a, b = rho_end[1.6], rho_end[2.0]
+                frow["rel_l1_TW_vs_SW_density_at_t_0.1"] = float(np.sum(np.abs(a - b)) / np.sum(np.abs(b)))
+            row[fname] = frow
         out["%dx%d" % (nx, ny)] = row
     return out
 
@@ -688,6 +704,15 @@ def run_gpu(args):
             api.mlp_forward_tc(ctx, params, feats, check=False)
         torch.cuda.synchronize()
         print(json.dumps({"profile": "mlp", "rows": args.mlp_rows, "launches": W + K}))
+        ctx.close()
+        return 0
+    if args.profile == "comp":
+        c = inputs.sod_strip(nx=args.comp_nx, ny=64, kappa=args.kappa)
+        sim, nnz, _ = _compressible_case(api, ctx, c, api.SPH_FP32_KAHAN)
+        sim.step(W + K)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "comp", "particles": int(sim.n), "nnz": nnz, "steps": W + K}))
+        del sim
         ctx.close()
         return 0
     if args.profile == "eu3d":
@@ -839,7 +864,7 @@ def run_gpu(args):
                          ("error_analysis_circle", lambda: _bench_error_analysis(api, inputs, ctx)),
                          ("double_shear_layer", lambda: _bench_dsl(api, inputs, ctx)),
                          ("columns", lambda: _bench_columns(api, inputs, ctx)),
-                         ("compressible_sod", lambda: _bench_compressible(api, inputs, ctx)),
+                         ("compressible_sod", lambda: _bench_compressible(api, inputs, ctx, peak)),
                          ("mlp_proposal", lambda: _bench_mlp(api, inputs, ctx, bf16))):
             if args.rows and name not in args.rows.split(","):
                 continue
@@ -905,13 +930,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--profile", choices=["fp32", "fp64", "eu3d", "mlp", "relax"], default=None,
+    ap.add_argument("--profile", choices=["fp32", "fp64", "eu3d", "mlp", "relax", "comp"], default=None,
                     help="run only one workload (setup + warmup + steps) for ncu captures: the plate "
                          "(fp32 or fp64), the 3D Taylor-Green vortex of side --eu-n (eu3d, float32) or the "
                          "fused MLP forward over --mlp-rows rows (mlp), or float32 relaxation steps of the "
                          "8-sphere body at dp = 1/128 (relax)")
     ap.add_argument("--mlp-rows", type=int, default=262144, help="rows of the --profile mlp workload")
     ap.add_argument("--eu-n", type=int, default=64, help="lattice side of the --profile eu3d workload")
+    ap.add_argument("--comp-nx", type=int, default=4096, help="strip length (particles) of the --profile comp workload")
     ap.add_argument("--no-tiles", action="store_true", help="--profile: without tile plans (per-pair geometry)")
     ap.add_argument("--kappa", type=float, default=1.6)
     ap.add_argument("--lanes", type=int, default=0, help="lanes per particle of the TL passes (0: tuned)")

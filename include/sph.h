@@ -528,11 +528,16 @@ int sph_relax_residual(sph_ctx* ctx, const sph_relax_params* prm, const double* 
  * in rho* and E*, and a minus in the limited p*: the normal velocity and the plus of the
  * unlimited HLLC p* are used (both needed for the pairwise antisymmetry that conserves
  * mass, momentum and energy).  Time integration: forward Euler with the fixed dt.
- * Float64 only (precision must be SPH_FP64).  Minimum image on periodic axes. */
+ * Minimum image on periodic axes.
+ * precision SPH_FP64: everything in float64, the pair geometry evaluated per pair.
+ * precision SPH_FP32_KAHAN: the state stays float64 (advanced in float64 by the float32
+ * rates); per step the neighbours' (rho, v, p, c, E) are read as float32 records, the
+ * solver runs in float32 and the row sums are compensated; the pair geometry comes from
+ * the plan (sph_compressible_plan), which the state must carry. */
 typedef struct {
     sph_domain dom;
     double dt, gamma, eta;          /* gamma = 1.4 and eta = 1 in the paper */
-    int32_t precision;              /* SPH_FP64 */
+    int32_t precision;              /* SPH_FP64 or SPH_FP32_KAHAN */
     int32_t reserved;
 } sph_compressible_params;
 
@@ -545,7 +550,24 @@ typedef struct {
     double* rho;                    /* [n], advanced in place by sph_compressible_step */
     double* mom;                    /* [dim][n] */
     double* E;                      /* [n] */
+    void* plan;                     /* SPH_FP32_KAHAN: caller-owned device buffer, 16-byte aligned */
+    int64_t plan_bytes;             /* >= sph_compressible_plan_bytes(...) */
+    int32_t plan_width;             /* written by sph_compressible_plan: longest row */
+    int32_t reserved;
 } sph_compressible_state;
+
+/* Pair geometry of the float32 form (a layout, not an operation of the paper):
+ * particles are fixed, so sph_compressible_plan computes once, in float64 from pos, vol,
+ * B and the lists, per pair G_ij = -2 V_j (B_i + B_j)/2 grad W_ij and n = -r_ij/r, stores
+ * them rounded to float32 with the neighbour index, pair k of row i at entry
+ * (i/32)*32*W + 32k + i%32 (W = longest row), and writes plan_width = W.  Rebuild it when
+ * the lists, pos, vol, B or h change (a plan of other lists gives wrong results; rows
+ * longer than its width are cut, never read past).  Both calls synchronise the stream;
+ * SPH_ERR_CAPACITY when plan_bytes is too small. */
+int sph_compressible_plan_bytes(sph_ctx* ctx, const sph_compressible_params* prm,
+                                const sph_compressible_state* st, int64_t* bytes_host, void* stream);
+int sph_compressible_plan(sph_ctx* ctx, const sph_compressible_params* prm, sph_compressible_state* st,
+                          void* stream);
 
 /* Rates of Eq. 18 at the current state: drho [n], dmom [dim][n], dE [n]. */
 int sph_compressible_rates(sph_ctx* ctx, const sph_compressible_params* prm,

@@ -170,8 +170,9 @@ def _neighbour_cell_lists(c, ncell, periodic, dim):
     return per_axis
 
 
-def neighbors_cells(pos, dom, chunk=4096):
-    """Same set as ``neighbors_bruteforce``, found through the cell list."""
+def neighbors_cells(pos, dom, chunk=4096, rows=None):
+    """Same set as ``neighbors_bruteforce``, found through the cell list.  With ``rows``,
+    only those rows are filled (the others are empty): a sample of a large set."""
     pos = np.asarray(pos, dtype=np.float64)
     dim = dom.dim
     n = pos.shape[1]
@@ -186,8 +187,9 @@ def neighbors_cells(pos, dom, chunk=4096):
     rc2 = dom.rc2
     out_i = []
     out_j = []
-    for s in range(0, n, chunk):
-        idx = np.arange(s, min(n, s + chunk))
+    sel = np.arange(n) if rows is None else np.unique(np.asarray(rows, dtype=np.int64))
+    for s in range(0, len(sel), chunk):
+        idx = sel[s:s + chunk]
         cs = c[:, idx]
         per_axis = _neighbour_cell_lists(cs, ncell, dom.periodic, dim)
         # all 3^dim combinations of per-axis candidates, then drop duplicates

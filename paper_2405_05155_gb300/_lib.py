@@ -78,7 +78,8 @@ class CompressibleParams(ctypes.Structure):
 
 
 class CompressibleState(ctypes.Structure):
-    _fields_ = [(name, c_vp) for name in ("row_ptr", "col", "pos", "vol", "B", "rho", "mom", "E")]
+    _fields_ = [(name, c_vp) for name in ("row_ptr", "col", "pos", "vol", "B", "rho", "mom", "E", "plan")] + [
+        ("plan_bytes", ctypes.c_int64), ("plan_width", c_i32), ("reserved", c_i32)]
 
 
 _P = ctypes.POINTER
@@ -127,6 +128,9 @@ _SIGNATURES = {
                                               c_vp, c_vp]),
     "sph_compressible_step": (ctypes.c_int, [c_vp, _P(CompressibleParams), _P(CompressibleState), ctypes.c_int,
                                              c_vp]),
+    "sph_compressible_plan_bytes": (ctypes.c_int, [c_vp, _P(CompressibleParams), _P(CompressibleState),
+                                                   _P(ctypes.c_int64), c_vp]),
+    "sph_compressible_plan": (ctypes.c_int, [c_vp, _P(CompressibleParams), _P(CompressibleState), c_vp]),
     "sph_field_approx": (ctypes.c_int, [c_vp, _P(SphDomain), ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                         c_vp, c_vp, c_vp]),
     "sph_host_alloc": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp)]),

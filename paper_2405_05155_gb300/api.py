@@ -275,7 +275,8 @@ class Compressible:
     """Compressible Eulerian SPH state on the device (sph_compressible_*, float64):
     rho [n], mom = rho v [dim][n] and E [n] advanced in place."""
 
-    def __init__(self, ctx, dom, pos, vol, B, row_ptr, col, rho, mom, E, dt, gamma=1.4, eta=1.0):
+    def __init__(self, ctx, dom, pos, vol, B, row_ptr, col, rho, mom, E, dt, gamma=1.4, eta=1.0,
+                 precision=SPH_FP64):
         dev = ctx.device
         self.ctx = ctx
         self.n = pos.shape[1]
@@ -283,7 +284,7 @@ class Compressible:
         self.prm = L.CompressibleParams()
         self.prm.dom = make_domain(dom, self.n)
         self.prm.dt, self.prm.gamma, self.prm.eta = dt, gamma, eta
-        self.prm.precision = SPH_FP64
+        self.prm.precision = precision
         self.pos, self.vol, self.B = _dev_f64(pos, dev), _dev_f64(vol, dev), _dev_f64(B, dev)
         self.row_ptr, self.col = row_ptr, col
         self.rho, self.mom, self.E = (_dev_f64(rho, dev).clone(), _dev_f64(mom, dev).clone(),
@@ -291,6 +292,13 @@ class Compressible:
         self.st = L.CompressibleState()
         for name in ("row_ptr", "col", "pos", "vol", "B", "rho", "mom", "E"):
             setattr(self.st, name, getattr(self, name).data_ptr())
+        self.plan = None
+        if precision == SPH_FP32_KAHAN:
+            nb = ctypes.c_int64(0)
+            self._call("sph_compressible_plan_bytes", ctypes.byref(nb), _stream())
+            self.plan = torch.empty(max(nb.value, 16), dtype=torch.uint8, device=dev)
+            self.st.plan, self.st.plan_bytes = self.plan.data_ptr(), self.plan.numel()
+            self._call("sph_compressible_plan", _stream())
 
     def _call(self, name, *args):
         fn = getattr(self.ctx.lib, name)

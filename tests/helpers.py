@@ -2,6 +2,7 @@
 import numpy as np
 import torch
 
+from oracle import kgc as OK
 from oracle import neighbors as ON
 
 
@@ -48,3 +49,37 @@ def sorted_by_cells(pos, d):
     """Positions reordered by (cell id, index): the layout the pair loops use."""
     order = ON.cell_order(pos, odom(d))
     return pos[:, order], order
+
+
+class OracleLists(dict):
+    """A test setup whose oracle-side neighbour list and correction matrices (``rp_h``,
+    ``col_h`` and the key ``b_key``) the oracle builds from the setup's own positions, on
+    first use, so that no oracle input comes from the device."""
+
+    def __init__(self, pos_key, b_key, **kw):
+        super().__init__(**kw)
+        self._pos_key = pos_key
+        self._b_key = b_key
+
+    def __missing__(self, key):
+        if key not in ("rp_h", "col_h", self._b_key):
+            raise KeyError(key)
+        od = self["prm"].dom
+        pos = self[self._pos_key]
+        rp, col = ON.neighbors_cells(pos, od)
+        B, _ = OK.kgc(pos, self["vol"], rp, col, od)
+        self.update({"rp_h": rp, "col_h": col, self._b_key: B})
+        return self[key]
+
+
+def oracle_rows(pos, vol, od, rows, hops):
+    """The oracle's neighbour list and correction matrices on the rows within ``hops``
+    neighbour hops of ``rows`` (every other row empty): what a sampled check of a large set
+    needs.  Returns (row_ptr, col, B, those rows)."""
+    level = np.unique(np.asarray(rows, dtype=np.int64))
+    for _ in range(hops):
+        _, col = ON.neighbors_cells(pos, od, rows=level)
+        level = np.unique(np.concatenate([level, col.astype(np.int64)]))
+    rp, col = ON.neighbors_cells(pos, od, rows=level)
+    B, _ = OK.kgc(pos, vol, rp, col, od)
+    return rp, col, B, level

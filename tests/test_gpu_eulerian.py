@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import cuda, host, odom, rel_l2, rel_max, sample_rows, sorted_by_cells
+from helpers import OracleLists, cuda, host, odom, oracle_rows, rel_l2, rel_max, sample_rows, sorted_by_cells
 from oracle import eulerian as OE
 from oracle import kgc as OK
 from oracle import neighbors as ON
@@ -39,8 +39,7 @@ def _setup(ctx, case, jitter=0.0, seed=0, sort=True):
     rp, col = api.build_neighbors(ctx, d, cuda(pos))
     B, fb, _ = api.kgc(ctx, d, cuda(pos), cuda(vol), rp, col)
     prm = OE.EulerianParams(odom(d), case["dt"], case["rho0"], case["c0"], case["mu"])
-    return dict(pos=pos, vol=vol, v=v, drho=drho, rp=rp, col=col, B=B, rp_h=host(rp), col_h=host(col),
-                B_h=host(B), prm=prm, d=d)
+    return OracleLists("pos", "B_h", pos=pos, vol=vol, v=v, drho=drho, rp=rp, col=col, B=B, prm=prm, d=d)
 
 
 def _sim(ctx, s, case, precision, integrator=api.SPH_TWO_PASS, drho=None, v=None, tiles=True):
@@ -135,7 +134,7 @@ def test_plan_geometry_and_forms(ctx):
     case = inputs.tgv3d(n=12, kappa=1.6)
     s = _setup(ctx, case, jitter=0.2, seed=5)
     n = s["pos"].shape[1]
-    rp, col = s["rp_h"], s["col_h"]
+    rp, col = host(s["rp"]), host(s["col"])           # the lists the plan was built from
     lens = np.diff(rp)
     sim = _sim(ctx, s, case, api.SPH_FP32_KAHAN)
     raw = host(sim.plan)
@@ -197,17 +196,17 @@ def test_conservation_on_gpu(ctx):
 
 def _oracle_two_pass_sampled(s, rows):
     """One two-pass step of the oracle evaluated only where the sampled rows need it."""
-    rp, col = s["rp_h"], s["col_h"]
+    rp, col, B, _ = oracle_rows(s["pos"], s["vol"], s["prm"].dom, rows, 2)
     nbrs = np.concatenate([col[rp[i]:rp[i + 1]] for i in rows])
     rows1 = np.unique(np.concatenate([rows, nbrs]))
     prm = s["prm"]
     rho_n = prm.rho0 + s["drho"]
     rp1, col1 = sample_rows(rp, col, rows1)
-    _, dmom = OE.eulerian_rates(s["pos"], s["vol"], s["drho"], s["v"], s["B_h"], rp1, col1, prm, want_mass=False)
+    _, dmom = OE.eulerian_rates(s["pos"], s["vol"], s["drho"], s["v"], B, rp1, col1, prm, want_mass=False)
     mom1 = rho_n * s["v"] + prm.dt * dmom
     v_half = mom1 / rho_n
     rps, cols = sample_rows(rp, col, rows)
-    drho_dt, _ = OE.eulerian_rates(s["pos"], s["vol"], s["drho"], v_half, s["B_h"], rps, cols, prm, want_mom=False)
+    drho_dt, _ = OE.eulerian_rates(s["pos"], s["vol"], s["drho"], v_half, B, rps, cols, prm, want_mom=False)
     drho1 = s["drho"] + prm.dt * drho_dt
     return drho1[rows], (mom1 / (prm.rho0 + drho1))[:, rows]
 
@@ -218,7 +217,7 @@ def test_full_size_3d_tgv_sampled(ctx):
     case = inputs.tgv3d(n=128, kappa=1.6)
     s = _setup(ctx, case)
     n = s["pos"].shape[1]
-    assert np.all(np.diff(s["rp_h"]) == 32)
+    assert np.all(np.diff(host(s["rp"])) == 32)
     sim = _sim(ctx, s, case, api.SPH_FP32_KAHAN)
     sim.step(1)
     dr, v = sim.fields()

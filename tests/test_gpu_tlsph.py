@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import cuda, host, odom, rel_l2, rel_max, sample_rows, sorted_by_cells
+from helpers import OracleLists, cuda, host, odom, oracle_rows, rel_l2, rel_max, sample_rows, sorted_by_cells
 from oracle import kgc as OK
 from oracle import neighbors as ON
 from oracle import tlsph as OT
@@ -29,8 +29,7 @@ def _setup(ctx, dp=0.005, kappa=1.6, law=OT.NEO_HOOKEAN, case=None):
     rp, col = api.build_neighbors(ctx, d, cuda(r0))
     B0, fb, _ = api.kgc(ctx, d, cuda(r0), cuda(vol), rp, col)
     prm = OT.TLParams(odom(d), c["dt"], c["rho0"], c["lam"], c["G"], law)
-    return dict(c=c, d=d, r0=r0, v=v, fixed=fixed, vol=vol, rp=rp, col=col, B0=B0, rp_h=host(rp),
-                col_h=host(col), B0_h=host(B0), prm=prm)
+    return OracleLists("r0", "B0_h", c=c, d=d, r0=r0, v=v, fixed=fixed, vol=vol, rp=rp, col=col, B0=B0, prm=prm)
 
 
 def _solid(ctx, s, precision, law, v=None, H=None, tiles=True):
@@ -144,7 +143,7 @@ def test_tile_plan_is_exact(ctx):
     # same lists (w in float64 by the oracle's kernel, rounded to float32 on the GPU)
     s = _setup(ctx, dp=0.004)
     n = s["r0"].shape[1]
-    rp, col = s["rp_h"], s["col_h"]
+    rp, col = host(s["rp"]), host(s["col"])           # the lists the plan was built from
     lens = np.diff(rp)
     sol = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
     P = _read_plan(sol.plan, n, col.size, int(lens.max()))
@@ -236,15 +235,15 @@ def test_full_size_plate_sampled(ctx):
     a, Fd = sol.rates()
     a, Fd = host(a), host(Fd)
     rows = rng.choice(n, 64, replace=False)
-    nb = np.unique(np.concatenate([rows, s["col_h"][np.concatenate([np.arange(s["rp_h"][i], s["rp_h"][i + 1])
-                                                                    for i in rows])]]))
+    # the oracle's list and B0 on the sampled rows and their neighbours
+    rp_o, col_o, B0_o, nb = oracle_rows(s["r0"], s["vol"], s["prm"].dom, rows, 1)
     Fm = np.tile(np.eye(3), (n, 1, 1))
     Fm[nb] = _F_from_H(H[:, nb])
     M = np.zeros((n, 3, 3))
-    M[nb] = OT.stress_matrix(Fm[nb], s["B0_h"][:, nb], s["prm"])
-    rp_s, col_s = sample_rows(s["rp_h"], s["col_h"], rows)
+    M[nb] = OT.stress_matrix(Fm[nb], B0_o[:, nb], s["prm"])
+    rp_s, col_s = sample_rows(rp_o, col_o, rows)
     a_o = OT.momentum_rate(s["r0"], s["vol"], M, rp_s, col_s, s["prm"].dom, s["prm"].rho0)
-    Fd_o = OT.deformation_rate(s["r0"], s["vol"], s["v"], s["B0_h"], rp_s, col_s, s["prm"].dom).reshape(n, 9).T
+    Fd_o = OT.deformation_rate(s["r0"], s["vol"], s["v"], B0_o, rp_s, col_s, s["prm"].dom).reshape(n, 9).T
     assert rel_l2(a[:, rows], a_o[:, rows]) < 1e-5
     assert rel_l2(Fd[:, rows], Fd_o[:, rows]) < 1e-5
 

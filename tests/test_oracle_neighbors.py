@@ -29,6 +29,18 @@ def test_cell_list_equals_brute_force(dim, kappa, periodic):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+@pytest.mark.parametrize("periodic", [True, False])
+def test_row_sample_equals_the_full_rows(periodic):
+    pos, dom = _random_case(5, 3, 1.6, 900, periodic)
+    rp, col = N.neighbors_cells(pos, dom)
+    rows = np.random.default_rng(1).choice(900, 40, replace=False)
+    srp, scol = N.neighbors_cells(pos, dom, chunk=7, rows=rows)
+    lens = np.diff(srp)
+    assert np.all(lens[np.setdiff1d(np.arange(900), rows)] == 0)
+    for i in rows:
+        assert np.array_equal(scol[srp[i]:srp[i + 1]], col[rp[i]:rp[i + 1]])
+
+
 @pytest.mark.parametrize("box_cells", [2, 3])
 def test_few_cells_periodic_no_duplicates(box_cells):
     # box of exactly 2 or 3 cells per axis: c-1 and c+1 can be the same cell
