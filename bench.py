@@ -570,12 +570,13 @@ def _compressible_case(api, ctx, c, precision):
 
 
 def _comp_bytes(n, nnz, dim):
-    """Algorithmic bytes of one float32 compressible step: per pair the plan entry (20 B in
-    2D, 32 B in 3D); per particle its row offsets (16 B), its record (32 B), the float64
-    state read and written (2 x (dim + 2) x 8 B) and the next record written (32 B).  The
-    neighbours' records (32 B per particle) stay in L2 across the pairs that read them."""
-    per_pair = (20 if dim == 2 else 32)
-    return nnz * per_pair + n * (16 + 32 + 2 * (dim + 2) * 8 + 32)
+    """Algorithmic bytes of one float32 compressible step, by the rule of the other planned
+    passes: per pair the int32 neighbour index; per particle its row offset (8 B), its
+    record (32 B), the float64 state read and written (2 x (dim + 2) x 8 B) and the next
+    record written (32 B).  The neighbours' records stay in L2 across the pairs that read
+    them; the plan's precomputed pair geometry (16 B more per pair in 2D, 28 B in 3D) is a
+    trade of arithmetic for bytes, not counted (ncu's DRAM bytes show it)."""
+    return nnz * 4 + n * (8 + 32 + 2 * (dim + 2) * 8 + 32)
 
 
 def _bench_compressible(api, inputs, ctx, peak, steps=200):
@@ -598,12 +599,23 @@ def _bench_compressible(api, inputs, ctx, peak, steps=200):
                 c = inputs.sod_strip(nx=nx, ny=ny, kappa=kappa)
                 sim, nnz, oh = _compressible_case(api, ctx, c, prec)
                 nsteps = int(round(0.1 / c["dt"])) if full else (steps if prec == api.SPH_FP64 else 10 * steps)
+                key = "kappa_%.1f" % kappa
+                by_lanes = {}
+                if prec == api.SPH_FP32_KAHAN and not full:
+                    # launch shape: lanes per row (results differ by float32 rounding only)
+                    for lanes in (1, 2, 4, 8):
+                        ctx.set_lanes(api.SPH_PASS_COMPRESSIBLE, lanes)
+                        sim.step(3)
+                        by_lanes[lanes] = _event_ms(lambda: sim.step(steps)) / steps
+                    ctx.set_lanes(api.SPH_PASS_COMPRESSIBLE, min(by_lanes, key=by_lanes.get))
                 if not full:
                     sim.step(3)
                 ms = _event_ms(lambda: sim.step(nsteps))
-                key = "kappa_%.1f" % kappa
                 frow[key] = {"particles": int(sim.n), "nnz": nnz, "steps": nsteps, "ms_per_step": ms / nsteps,
                              "pair_evaluations_per_s": nnz * nsteps / (ms * 1e-3)}
+                if by_lanes:
+                    frow[key]["lanes"] = ctx.get_lanes(api.SPH_PASS_COMPRESSIBLE)
+                    frow[key]["ms_per_step_by_lanes"] = by_lanes
                 if prec == api.SPH_FP32_KAHAN and not full:
                     frow[key]["roofline"] = _roof(_comp_bytes(sim.n, nnz, 2), ms / nsteps, peak)
                     frow[key]["roofline"]["kernel"] = "k_comp32"
@@ -708,6 +720,8 @@ def run_gpu(args):
         return 0
     if args.profile == "comp":
         c = inputs.sod_strip(nx=args.comp_nx, ny=64, kappa=args.kappa)
+        if args.lanes:
+            ctx.set_lanes(api.SPH_PASS_COMPRESSIBLE, args.lanes)
         sim, nnz, _ = _compressible_case(api, ctx, c, api.SPH_FP32_KAHAN)
         sim.step(W + K)
         torch.cuda.synchronize()

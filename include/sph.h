@@ -111,11 +111,13 @@ int sph_host_free(void* host);
  * lanes of a warp share one particle's neighbour row (for SPH_PASS_RELAX: the
  * row of the float32 relaxation list) and combine their partial
  * sums with shuffles.  pass: SPH_PASS_*.  Results of different shapes differ
- * only by float32 rounding.  Defaults to 4 (1 for SPH_PASS_RELAX).  sph_get_lanes returns the setting
+ * only by float32 rounding.  Defaults to 4 (1 for SPH_PASS_RELAX and
+ * SPH_PASS_COMPRESSIBLE, the float32 pass of sph_compressible_step).  sph_get_lanes returns the setting
  * (or -1 on a bad argument).  Not part of the paper: a GPU launch parameter. */
 #define SPH_PASS_EULERIAN 0
 #define SPH_PASS_TLSPH    1
 #define SPH_PASS_RELAX    2
+#define SPH_PASS_COMPRESSIBLE 4
 int sph_set_lanes(sph_ctx* ctx, int pass, int lanes);
 int sph_get_lanes(const sph_ctx* ctx, int pass);
 /* Most neighbour records a tile of a planned pass stages in shared memory (0: as

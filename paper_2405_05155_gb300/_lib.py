@@ -18,7 +18,7 @@ SPH_WENDLAND_C2, SPH_LAGUERRE_GAUSS = 0, 1
 SPH_FP64, SPH_FP32_KAHAN = 0, 1
 SPH_TWO_PASS, SPH_FUSED = 0, 1
 SPH_SVK, SPH_NEO_HOOKEAN = 0, 1
-SPH_PASS_EULERIAN, SPH_PASS_TLSPH, SPH_PASS_RELAX, SPH_PASS_BATCHED = 0, 1, 2, 3
+SPH_PASS_EULERIAN, SPH_PASS_TLSPH, SPH_PASS_RELAX, SPH_PASS_BATCHED, SPH_PASS_COMPRESSIBLE = 0, 1, 2, 3, 4
 SPH_PIPE_STREAM, SPH_PIPE_PERSISTENT, SPH_PIPE_BULK = 0, 1, 2
 SPH_TIMER_BATCH_STEP = 9
 SPH_MAX_SPHERES = 16

@@ -10,7 +10,7 @@ import torch
 from . import _lib as L
 from ._lib import (SPH_FP32_KAHAN, SPH_FP64, SPH_FUSED, SPH_LAGUERRE_GAUSS,  # noqa: F401
                    SPH_NEO_HOOKEAN, SPH_SVK, SPH_TWO_PASS, SPH_WENDLAND_C2, SPH_PASS_BATCHED,
-                   SPH_PASS_EULERIAN, SPH_PASS_RELAX, SPH_PASS_TLSPH, SPH_TIMER_NEIGHBORS,
+                   SPH_PASS_COMPRESSIBLE, SPH_PASS_EULERIAN, SPH_PASS_RELAX, SPH_PASS_TLSPH, SPH_TIMER_NEIGHBORS,
                    SPH_TIMER_RELAX_ACCEL, SPH_TIMER_RELAX_UPDATE, SPH_PIPE_STREAM, SPH_PIPE_PERSISTENT,
                    SPH_PIPE_BULK)
 

@@ -40,7 +40,7 @@ struct sph_ctx {
     size_t slot_bytes[kSlots] = {};
     int* flags = nullptr;          // device status words (see FLAG_*)
     void* pinned = nullptr;        // small pinned host buffer for read-backs
-    int lanes[4] = {4, 4, 1, 4};   // lanes per particle of the float32 pair passes (SPH_PASS_*)
+    int lanes[5] = {4, 4, 1, 4, 1};   // lanes per particle of the float32 pair passes (SPH_PASS_*)
     int stage_cap = 0;             // most neighbour records a tile stages in shared memory (0: default)
     int tile_pipe = SPH_PIPE_STREAM; // planned TL passes: how pair entries reach a block (SPH_PIPE_*)
     bool waits_pending = false;    // a kernel with bounded waits ran since the timeout flag was read

@@ -372,36 +372,43 @@ __device__ __forceinline__ int load_entry(const float4* __restrict__ ga, const v
     }
 }
 
-// One pass over the plan.  UPDATE: advance the float64 state of row i by dt and write its
-// next record (n0, n1); otherwise write the rates.  Sums: compensated, in pairs
-// (mass, energy), (momentum x, y), (momentum z).
-template <int DIM, bool UPDATE>
+// One pass over the plan, LANES consecutive lanes per row (pairs k = lane, lane + LANES,
+// ...), their partial sums combined with shuffles.  UPDATE: advance the float64 state of
+// row i by dt and write its next record (n0, n1); otherwise write the rates.  Sums:
+// compensated, in pairs (mass, energy), (momentum x, y), (momentum z).
+template <int DIM, bool UPDATE, int LANES>
 __global__ void __launch_bounds__(128) k_comp32(const float4* __restrict__ r0, const float4* __restrict__ r1,
                                                 const float4* __restrict__ ga, const void* __restrict__ gb,
                                                 const int64_t* __restrict__ row_ptr, int64_t n, int width,
                                                 float gamma, float eta, double dt, double* __restrict__ rho,
                                                 double* __restrict__ mom, double* __restrict__ E,
                                                 float4* __restrict__ n0, float4* __restrict__ n1) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const Prim<DIM, float> Pi = load_rec<DIM>(r0, r1, i);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t / LANES;
+    const int lane = (int)(t % LANES);
+    // the lanes of a row are all in range or all out of it; out of range they only take
+    // part in the shuffles
+    const bool active = i < n;
+    const Prim<DIM, float> Pi = load_rec<DIM>(r0, r1, active ? i : 0);
     // a plan of other lists is wrong but never read past: rows are cut at its width
-    const int len = min((int)(row_ptr[i + 1] - row_ptr[i]), width);
+    const int len = active ? min((int)(row_ptr[i + 1] - row_ptr[i]), width) : 0;
+    const int cnt = len > lane ? (len - lane + LANES - 1) / LANES : 0;
+    constexpr int64_t kStride = 32 * LANES;
     Kahan2 me, mxy, mz;
     me.init();
     mxy.init();
     mz.init();
-    // software pipeline: while pair k is evaluated, pair k + 1's neighbour record and
-    // pair k + 2's plan entry are in flight (the record load then never waits on the
+    // software pipeline: while pair m is evaluated, pair m + 1's neighbour record and
+    // pair m + 2's plan entry are in flight (the record load then never waits on the
     // entry load of the same iteration)
-    int64_t e = slot(i, 0, width);
+    int64_t e = active ? slot(i, lane, width) : 0;
     float G1[DIM], N1[DIM], G2[DIM] = {}, N2[DIM] = {};
     int j2 = 0;
     Prim<DIM, float> P1;
-    if (len > 0) P1 = load_rec<DIM>(r0, r1, load_entry<DIM>(ga, gb, e, G1, N1));
-    if (len > 1) j2 = load_entry<DIM>(ga, gb, e + 32, G2, N2);
-    e += 64;
-    for (int k = 0; k < len; ++k) {
+    if (cnt > 0) P1 = load_rec<DIM>(r0, r1, load_entry<DIM>(ga, gb, e, G1, N1));
+    if (cnt > 1) j2 = load_entry<DIM>(ga, gb, e + kStride, G2, N2);
+    e += 2 * kStride;
+    for (int m = 0; m < cnt; ++m) {
         float G[DIM], nrm[DIM];
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
@@ -411,9 +418,9 @@ __global__ void __launch_bounds__(128) k_comp32(const float4* __restrict__ r0, c
             N1[d] = N2[d];
         }
         const Prim<DIM, float> Pj = P1;
-        if (k + 1 < len) P1 = load_rec<DIM>(r0, r1, j2);
-        if (k + 2 < len) j2 = load_entry<DIM>(ga, gb, e, G2, N2);
-        e += 32;
+        if (m + 1 < cnt) P1 = load_rec<DIM>(r0, r1, j2);
+        if (m + 2 < cnt) j2 = load_entry<DIM>(ga, gb, e, G2, N2);
+        e += kStride;
         float rho_s, v_s[DIM], E_s, p_s;
         hllc32<DIM>(Pi, Pj, nrm, eta, rho_s, v_s, E_s, p_s);
         float vg = 0.0f;
@@ -424,7 +431,16 @@ __global__ void __launch_bounds__(128) k_comp32(const float4* __restrict__ r0, c
         mxy.add(make_float2(fm * v_s[0] + p_s * G[0], fm * v_s[1] + p_s * G[1]));
         if (DIM == 3) mz.add(make_float2(fm * v_s[DIM - 1] + p_s * G[DIM - 1], 0.0f));
     }
-    const float2 se = me.value(), sxy = mxy.value(), sz = mz.value();
+    float2 se = me.value(), sxy = mxy.value(), sz = mz.value();
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) {
+        se.x += __shfl_xor_sync(0xffffffffu, se.x, o);
+        se.y += __shfl_xor_sync(0xffffffffu, se.y, o);
+        sxy.x += __shfl_xor_sync(0xffffffffu, sxy.x, o);
+        sxy.y += __shfl_xor_sync(0xffffffffu, sxy.y, o);
+        if (DIM == 3) sz.x += __shfl_xor_sync(0xffffffffu, sz.x, o);
+    }
+    if (!active || lane != 0) return;
     const float sp[3] = {sxy.x, sxy.y, sz.x};
     if (UPDATE) {
         const double rn = rho[i] + dt * (double)se.x;
@@ -516,18 +532,33 @@ void launch_rec(const sph_compressible_params* p, const sph_compressible_state* 
         k_comp_rec<3><<<grid_for(n, 256), 256, 0, s>>>(st->rho, st->mom, st->E, n, (float)p->gamma, r0, r1);
 }
 
-template <bool UPDATE>
-void launch32(const sph_compressible_params* p, const sph_compressible_state* st, const float4* r0,
-              const float4* r1, double* a, double* b, double* c, float4* n0, float4* n1, cudaStream_t s) {
+template <int DIM, bool UPDATE, int LANES>
+void launch32_shape(const sph_compressible_params* p, const sph_compressible_state* st, const float4* r0,
+                    const float4* r1, double* a, double* b, double* c, float4* n0, float4* n1, cudaStream_t s) {
     const int64_t n = p->dom.n;
-    const Plan32 v = plan_view(st, p->dom.dim, n);
-    const float g = (float)p->gamma, eta = (float)p->eta;
+    const Plan32 v = plan_view(st, DIM, n);
+    k_comp32<DIM, UPDATE, LANES><<<grid_for(n * LANES, 128), 128, 0, s>>>(
+        r0, r1, v.ga, v.gb, st->row_ptr, n, st->plan_width, (float)p->gamma, (float)p->eta, p->dt, a, b, c, n0, n1);
+}
+
+template <int DIM, bool UPDATE>
+void launch32_dim(int lanes, const sph_compressible_params* p, const sph_compressible_state* st, const float4* r0,
+                  const float4* r1, double* a, double* b, double* c, float4* n0, float4* n1, cudaStream_t s) {
+    switch (lanes) {
+        case 2: launch32_shape<DIM, UPDATE, 2>(p, st, r0, r1, a, b, c, n0, n1, s); break;
+        case 4: launch32_shape<DIM, UPDATE, 4>(p, st, r0, r1, a, b, c, n0, n1, s); break;
+        case 8: launch32_shape<DIM, UPDATE, 8>(p, st, r0, r1, a, b, c, n0, n1, s); break;
+        default: launch32_shape<DIM, UPDATE, 1>(p, st, r0, r1, a, b, c, n0, n1, s); break;
+    }
+}
+
+template <bool UPDATE>
+void launch32(int lanes, const sph_compressible_params* p, const sph_compressible_state* st, const float4* r0,
+              const float4* r1, double* a, double* b, double* c, float4* n0, float4* n1, cudaStream_t s) {
     if (p->dom.dim == 2)
-        k_comp32<2, UPDATE><<<grid_for(n, 128), 128, 0, s>>>(r0, r1, v.ga, v.gb, st->row_ptr, n, st->plan_width, g,
-                                                             eta, p->dt, a, b, c, n0, n1);
+        launch32_dim<2, UPDATE>(lanes, p, st, r0, r1, a, b, c, n0, n1, s);
     else
-        k_comp32<3, UPDATE><<<grid_for(n, 128), 128, 0, s>>>(r0, r1, v.ga, v.gb, st->row_ptr, n, st->plan_width, g,
-                                                             eta, p->dt, a, b, c, n0, n1);
+        launch32_dim<3, UPDATE>(lanes, p, st, r0, r1, a, b, c, n0, n1, s);
 }
 
 }  // namespace
@@ -595,7 +626,7 @@ extern "C" int sph_compressible_rates(sph_ctx* ctx, const sph_compressible_param
         float4* rec = (float4*)sph_scratch(ctx, S_MISC2, (size_t)n * 32, &r);
         if (r) return r;
         launch_rec(p, st, rec, rec + n, s);
-        launch32<false>(p, st, rec, rec + n, drho, dmom, dE, nullptr, nullptr, s);
+        launch32<false>(ctx->lanes[SPH_PASS_COMPRESSIBLE], p, st, rec, rec + n, drho, dmom, dE, nullptr, nullptr, s);
     }
     SPH_LAUNCH_CHECK(ctx);
     return SPH_OK;
@@ -619,8 +650,9 @@ extern "C" int sph_compressible_step(sph_ctx* ctx, const sph_compressible_params
         float4* b = (float4*)sph_scratch(ctx, S_MISC3, (size_t)n * 32, &r);
         if (r) return r;
         launch_rec(p, st, a, a + n, s);
+        const int lanes = ctx->lanes[SPH_PASS_COMPRESSIBLE];
         for (int k = 0; k < nsteps; ++k) {
-            launch32<true>(p, st, a, a + n, st->rho, st->mom, st->E, b, b + n, s);
+            launch32<true>(lanes, p, st, a, a + n, st->rho, st->mom, st->E, b, b + n, s);
             SPH_LAUNCH_CHECK(ctx);
             float4* t = a;
             a = b;

@@ -61,14 +61,14 @@ extern "C" const char* sph_status_string(int status) {
 extern "C" int sph_last_cuda_error(const sph_ctx* ctx) { return ctx ? ctx->last_cuda_error : 0; }
 
 extern "C" int sph_set_lanes(sph_ctx* ctx, int pass, int lanes) {
-    if (!ctx || pass < 0 || pass > 3) return SPH_ERR_ARG;
+    if (!ctx || pass < 0 || pass > SPH_PASS_COMPRESSIBLE) return SPH_ERR_ARG;
     if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return SPH_ERR_ARG;
     ctx->lanes[pass] = lanes;
     return SPH_OK;
 }
 
 extern "C" int sph_get_lanes(const sph_ctx* ctx, int pass) {
-    if (!ctx || pass < 0 || pass > 3) return -1;
+    if (!ctx || pass < 0 || pass > SPH_PASS_COMPRESSIBLE) return -1;
     return ctx->lanes[pass];
 }
 

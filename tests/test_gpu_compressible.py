@@ -97,6 +97,29 @@ def test_limiter_strengths(ctx, eta, form):
         assert err(g, w) < tol, err(g, w)
 
 
+@pytest.mark.parametrize("dim,m", [(2, 24), (3, 9)])
+def test_fp32_lane_shapes(ctx, dim, m):
+    # 1 to 8 lanes per row: the same pairs, partial sums combined by shuffles; every
+    # shape within the float32 tolerance of the oracle, and 20 steps of each agree
+    pos, vol, d = _periodic(dim, m, 2.0, seed=11)
+    dev, (orp, ocol, oB, od) = _both(ctx, pos, vol, d)
+    rho, mom, E = _state(pos.shape[1], dim, seed=12)
+    want = OC.compressible_rates(pos, vol, rho, mom, E, oB, orp, ocol, OC.CompressibleParams(od, 1e-4))
+    ends = []
+    try:
+        for lanes in (1, 2, 4, 8):
+            ctx.set_lanes(api.SPH_PASS_COMPRESSIBLE, lanes)
+            sim = _sim(ctx, d, pos, vol, dev, rho, mom, E, 1e-4, precision=api.SPH_FP32_KAHAN)
+            for g, w in zip((host(t) for t in sim.rates()), want):
+                assert rel_l2(g, w) < 1e-5, (lanes, rel_l2(g, w))
+            sim.step(20)
+            ends.append(host(sim.E) - E)
+    finally:
+        ctx.set_lanes(api.SPH_PASS_COMPRESSIBLE, 1)
+    for x in ends[1:]:
+        assert rel_l2(x, ends[0]) < 1e-5
+
+
 def test_fp32_steps_and_conservation(ctx):
     # 20 float32 steps: the change of the float64 state against the oracle's, and the
     # totals (sums of float32 rates: conserved to float32 rounding of the fluxes)
