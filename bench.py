@@ -698,6 +698,9 @@ def run_gpu(args):
     from paper_2405_05155_gb300._lib import SPH_TIMER_TL_DEFORM, SPH_TIMER_TL_MOMENTUM, SPH_TIMER_TL_STRESS
     ctx = api.Context(torch.cuda.current_device())
     K, W = args.steps, args.warmup
+    if args.pipe:
+        ctx.set_tile_pipeline({"stream": api.SPH_PIPE_STREAM, "persistent": api.SPH_PIPE_PERSISTENT,
+                               "bulk": api.SPH_PIPE_BULK, "geom": api.SPH_PIPE_GEOM}[args.pipe])
 
     if args.profile == "relax":
         from paper_2405_05155_gb300 import learned
@@ -808,10 +811,13 @@ def run_gpu(args):
     else:
         peak, peak_src = 6800.0, "fallback"
     achieved = dominant[1] / (dominant[2] * 1e-3) / 1e9
-    # ncu DRAM bytes (read + write) per launch of each planned TL pass, measured on this
-    # workload for the current kernels (profiles/tl_pair_passes_plate816k_full.md)
-    ncu_traffic = {"tl_momentum_pass": 446.3e6, "tl_deformation_pass": 509.1e6}
-    traffic = args.traffic if args.traffic is not None else ncu_traffic.get(dominant[0])
+    # ncu DRAM bytes (read + write) per launch of each planned TL pass on this workload,
+    # by the deformation pass's form (profiles/tl_pair_passes_plate816k_full.md,
+    # profiles/tl_deformation_geometry_form_plate816k_full.md)
+    pipe = args.pipe or "geom"
+    ncu_traffic = {("tl_momentum_pass", "geom"): 446.3e6, ("tl_momentum_pass", "stream"): 446.3e6,
+                   ("tl_deformation_pass", "geom"): 214.8e6, ("tl_deformation_pass", "stream"): 509.1e6}
+    traffic = args.traffic if args.traffic is not None else ncu_traffic.get((dominant[0], pipe))
 
     # end to end through the C ABI with the float64 state (x, v, F - I) in host memory:
     # every step reads it from the host, packs, steps, unpacks and writes it back.
@@ -900,8 +906,12 @@ def run_gpu(args):
                        "l2_policy": "inputs larger than L2 (working set %.0f MB > 129 MB L2), no flush" % (ws / 2 ** 20),
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "lanes_per_particle": lanes16, "lanes_per_particle_2h": lanes20,
-                       "launch_shape": ("tile plan: 128-row tiles, one thread per row, float64-precomputed "
-                                        "pair factors, neighbours staged in shared memory") if planned else
+                       "launch_shape": ("tile plan: 128-row tiles, one thread per row, neighbours staged in "
+                                        "shared memory; momentum pass on float64-precomputed pair factors, "
+                                        "deformation pass %s" % ("evaluating grad0 W V0 from tile-relative staged "
+                                                                 "positions (SPH_PIPE_GEOM)" if pipe == "geom"
+                                                                 else "in pipeline mode '%s'" % pipe))
+                                       if planned else
                                        ("autotuned lanes (sph_autotune_tlsph)" if not args.lanes else "fixed lanes")},
             "kappa_2.0": {"ms_per_step": ms20 / K, "pair_interactions_per_s": 2 * s20["nnz"] * K / (ms20 * 1e-3),
                           "nnz": s20["nnz"]},
@@ -956,6 +966,8 @@ def main():
     ap.add_argument("--kappa", type=float, default=1.6)
     ap.add_argument("--lanes", type=int, default=0, help="lanes per particle of the TL passes (0: tuned)")
     ap.add_argument("--headline-only", action="store_true", help="skip the other rows' workloads")
+    ap.add_argument("--pipe", choices=["stream", "persistent", "bulk", "geom"], default=None,
+                    help="how the planned TL passes get their pair entries (default: the context's)")
     ap.add_argument("--rows", default="", help="comma-separated names of the other rows to run (default: all)")
     ap.add_argument("--other-steps", type=int, default=100, help="timed steps of the other Eulerian workloads")
     ap.add_argument("--traffic", type=float, default=None,

@@ -125,19 +125,25 @@ int sph_get_lanes(const sph_ctx* ctx, int pass);
  * global memory.  A launch-shape setting, like the lanes: results do not depend on it. */
 int sph_set_stage_cap(sph_ctx* ctx, int cap);
 /* Planned TL passes, how pair entries reach a block (a launch-shape setting:
- * results do not depend on it):
- *   SPH_PIPE_STREAM     one block per tile, entries streamed from global memory
- *                       (default: the fastest measured);
+ * results do not depend on it, apart from the rounding SPH_PIPE_GEOM notes):
+ *   SPH_PIPE_STREAM     one block per tile, entries streamed from global memory;
  *   SPH_PIPE_PERSISTENT one block per SM, the next tile's entries and neighbours
  *                       copied into shared memory by TMA while the current tile
  *                       computes (when its buffers fit);
  *   SPH_PIPE_BULK       one block per tile; the deformation pass copies the tile's
  *                       whole entry block into shared memory with one TMA bulk copy
- *                       while it stages the neighbours.
+ *                       while it stages the neighbours;
+ *   SPH_PIPE_GEOM       one block per tile; the deformation pass stages the
+ *                       neighbours' whole records and evaluates each pair's
+ *                       grad0 W_ij V0_j from them, reading only the entries' 2-byte
+ *                       neighbour slots (results differ from the other modes by
+ *                       float32 rounding of that factor); the momentum pass streams
+ *                       (default: the fastest measured).
  * SPH_ERR_ARG for any other mode. */
 #define SPH_PIPE_STREAM     0
 #define SPH_PIPE_PERSISTENT 1
 #define SPH_PIPE_BULK       2
+#define SPH_PIPE_GEOM       3
 int sph_set_tile_pipeline(sph_ctx* ctx, int mode);
 
 /* Per-kernel device timing (not part of the paper: measurement support).

@@ -19,7 +19,7 @@ SPH_FP64, SPH_FP32_KAHAN = 0, 1
 SPH_TWO_PASS, SPH_FUSED = 0, 1
 SPH_SVK, SPH_NEO_HOOKEAN = 0, 1
 SPH_PASS_EULERIAN, SPH_PASS_TLSPH, SPH_PASS_RELAX, SPH_PASS_BATCHED, SPH_PASS_COMPRESSIBLE = 0, 1, 2, 3, 4
-SPH_PIPE_STREAM, SPH_PIPE_PERSISTENT, SPH_PIPE_BULK = 0, 1, 2
+SPH_PIPE_STREAM, SPH_PIPE_PERSISTENT, SPH_PIPE_BULK, SPH_PIPE_GEOM = 0, 1, 2, 3
 SPH_TIMER_BATCH_STEP = 9
 SPH_MAX_SPHERES = 16
 (SPH_TIMER_TL_STRESS, SPH_TIMER_TL_MOMENTUM, SPH_TIMER_TL_DEFORM, SPH_TIMER_EU_MOMENTUM, SPH_TIMER_EU_MASS,

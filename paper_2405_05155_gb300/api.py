@@ -12,7 +12,7 @@ from ._lib import (SPH_FP32_KAHAN, SPH_FP64, SPH_FUSED, SPH_LAGUERRE_GAUSS,  # n
                    SPH_NEO_HOOKEAN, SPH_SVK, SPH_TWO_PASS, SPH_WENDLAND_C2, SPH_PASS_BATCHED,
                    SPH_PASS_COMPRESSIBLE, SPH_PASS_EULERIAN, SPH_PASS_RELAX, SPH_PASS_TLSPH, SPH_TIMER_NEIGHBORS,
                    SPH_TIMER_RELAX_ACCEL, SPH_TIMER_RELAX_UPDATE, SPH_PIPE_STREAM, SPH_PIPE_PERSISTENT,
-                   SPH_PIPE_BULK)
+                   SPH_PIPE_BULK, SPH_PIPE_GEOM)
 
 NSYM = {2: 3, 3: 6}
 
@@ -72,7 +72,8 @@ class Context:
             pass
 
     def set_tile_pipeline(self, mode):
-        """How the planned TL passes get their pair entries: SPH_PIPE_STREAM, _PERSISTENT or _BULK."""
+        """How the planned TL passes get their pair entries: SPH_PIPE_GEOM (default), _STREAM,
+        _PERSISTENT or _BULK."""
         L.check("sph_set_tile_pipeline", self.lib.sph_set_tile_pipeline(self.h, int(mode)), self.h)
 
     def set_stage_cap(self, cap):

@@ -42,7 +42,7 @@ struct sph_ctx {
     void* pinned = nullptr;        // small pinned host buffer for read-backs
     int lanes[5] = {4, 4, 1, 4, 1};   // lanes per particle of the float32 pair passes (SPH_PASS_*)
     int stage_cap = 0;             // most neighbour records a tile stages in shared memory (0: default)
-    int tile_pipe = SPH_PIPE_STREAM; // planned TL passes: how pair entries reach a block (SPH_PIPE_*)
+    int tile_pipe = SPH_PIPE_GEOM;   // planned TL passes: how pair entries reach a block (SPH_PIPE_*)
     bool waits_pending = false;    // a kernel with bounded waits ran since the timeout flag was read
     double relax_skin = 0.2;       // float32 relaxation: list skin / h (0: a cell sweep every step)
     // batched Eulerian step: launch shape, captured graph and the case table it was made for

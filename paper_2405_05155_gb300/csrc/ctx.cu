@@ -79,7 +79,7 @@ extern "C" int sph_set_relax_skin(sph_ctx* ctx, double skin_over_h) {
 }
 
 extern "C" int sph_set_tile_pipeline(sph_ctx* ctx, int mode) {
-    if (!ctx || mode < SPH_PIPE_STREAM || mode > SPH_PIPE_BULK) return SPH_ERR_ARG;
+    if (!ctx || mode < SPH_PIPE_STREAM || mode > SPH_PIPE_GEOM) return SPH_ERR_ARG;
     ctx->tile_pipe = mode;
     return SPH_OK;
 }

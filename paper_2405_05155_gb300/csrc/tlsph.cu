@@ -378,6 +378,47 @@ __device__ __forceinline__ void defo_pair(float4 c0, float4 c1, const float* oi,
     }
 }
 
+// Position relative to a reference cell, from an encoded record (offset o, cell bits):
+// x = (c - c_ref) S + o, S split as Sh + Sl as in rel_pair.  Non-periodic boxes only
+// (a periodic axis needs the pair's own minimum image, rel_pair).
+template <int DIM>
+__device__ __forceinline__ void rel_to_ref(const float* o, uint32_t b, uint32_t bref, const TLK<float>& K, float* x) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const float fdc = rel_cell_f<DIM>(b, a) - rel_cell_f<DIM>(bref, a);
+        x[a] = fmaf(fdc, K.S[a], fmaf(fdc, K.Sl[a], o[a]));
+    }
+}
+
+// One deformation-rate pair from tile-relative positions: xj = (x, y, z, V0_j) and
+// vj = (v_x, v_y, v_z, .) of the neighbour; the same sum as defo_pair.
+template <int DIM>
+__device__ __forceinline__ void defo_pair_rel(float4 xj, float4 vj, const float* xi, float2 nv01, float nv2,
+                                              const TLK<float>& K, Kahan2* c01, Kahan2& r2, Kahan<float>& l22) {
+    float r[DIM];
+    r[0] = xi[0] - xj.x;
+    r[1] = xi[1] - xj.y;
+    if (DIM == 3) r[DIM - 1] = xi[DIM - 1] - xj.z;
+    float d2 = r[0] * r[0];
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) d2 = fmaf(r[a], r[a], d2);
+    const float gs = gs_from_d2(d2, K);
+    const float w = xj.w;
+    float2 dv01 = __fmul2_rn(make_float2(w, w), __fadd2_rn(make_float2(vj.x, vj.y), nv01));
+    if (DIM == 2) {
+        c01[0].add(__fmul2_rn(dv01, make_float2(gs * r[0], gs * r[0])));
+        c01[1].add(__fmul2_rn(dv01, make_float2(gs * r[1], gs * r[1])));
+    } else {
+        float g0 = gs * r[0], g1 = gs * r[1], g2 = gs * r[DIM - 1];
+        float dv2 = w * (vj.z + nv2);
+        c01[0].add(__fmul2_rn(dv01, make_float2(g0, g0)));
+        c01[1].add(__fmul2_rn(dv01, make_float2(g1, g1)));
+        c01[DIM - 1].add(__fmul2_rn(dv01, make_float2(g2, g2)));
+        r2.add(__fmul2_rn(make_float2(dv2, dv2), make_float2(g0, g1)));
+        l22.add(dv2 * g2);
+    }
+}
+
 __device__ __forceinline__ float4 lo4(const F8& f) { return make_float4(f.v[0], f.v[1], f.v[2], f.v[3]); }
 __device__ __forceinline__ float4 hi4(const F8& f) { return make_float4(f.v[4], f.v[5], f.v[6], f.v[7]); }
 
@@ -567,7 +608,20 @@ struct GeoArgs {
     int mcap;
     const int32_t* tile_e;   // bulk form: entries per tile
     int ecap;                // bulk form: most entries a block copies into shared memory (0: none)
+    const uint16_t* slots;   // geometry form: the entries' neighbour slots alone, same sliced order
 };
+
+// The TL plan: the tile plan (tiles.cuh) with 16-byte entries, then the entries' slots
+// alone as a sliced uint16 section (read by the deformation pass that evaluates the pair
+// geometry from the staged records instead of reading the entries).
+static inline size_t tl_slot_offset(int64_t n, int64_t nnz, int64_t maxrow) {
+    return tile_plan_bytes(n, nnz, maxrow);
+}
+
+static inline size_t tl_plan_total(int64_t n, int64_t nnz, int64_t maxrow) {
+    const int64_t ntiles = (n + kTileRows - 1) / kTileRows;
+    return tl_slot_offset(n, nnz, maxrow) + align16((size_t)ntiles * kTileRows * (size_t)maxrow * 2);
+}
 
 // Pair entries of the tile plan: w = grad0 W_ij V0_j in float64, stored float32,
 // with the neighbour's slot, rows laid out by offset (offset_order).
@@ -578,7 +632,7 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
                                                       const uint16_t* __restrict__ lcol,
                                                       const int32_t* __restrict__ tile_e,
                                                       const int64_t* __restrict__ tile_so, int64_t n, TLK<double> K,
-                                                      float4* __restrict__ geo) {
+                                                      float4* __restrict__ geo, uint16_t* __restrict__ slots) {
     const int64_t tile = blockIdx.x;
     const int64_t i = tile * kTileRows + threadIdx.x;
     const bool active = i < n;
@@ -612,13 +666,14 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
             e.w = __int_as_float((int)lcol[p]);
         }
         out[(int64_t)k * kTileRows] = e;
+        slots[tile_so[tile] + threadIdx.x + (int64_t)k * kTileRows] = (uint16_t)__float_as_int(e.w);
     }
 }
 
-// Stage chunks 1..NPL of the tile's distinct neighbours' records (record stride
-// RECF floats) at sp[c * mcap + s].  Returns false, staging nothing, for a tile
+// Stage chunks FIRST..FIRST+NPL-1 of the tile's distinct neighbours' records (record
+// stride RECF floats) at sp[c * mcap + s].  Returns false, staging nothing, for a tile
 // with more distinct neighbours than mcap.  Block-uniform.
-template <int NPL, int RECF>
+template <int NPL, int RECF, int FIRST = 1>
 __device__ __forceinline__ bool stage_neighbours(const float* __restrict__ R, int64_t n, int64_t P0, int m,
                                                  const GeoArgs& A, float4* sp) {
     const bool staged = m <= A.mcap;
@@ -630,7 +685,7 @@ __device__ __forceinline__ bool stage_neighbours(const float* __restrict__ R, in
             int s = q / NPL, c = q - s * NPL;
             // a plan out of date with the lists reads wrong but in-bounds records
             int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
-            sp[c * A.mcap + s] = __ldg(reinterpret_cast<const float4*>(R + RECF * j) + 1 + c);
+            sp[c * A.mcap + s] = __ldg(reinterpret_cast<const float4*>(R + RECF * j) + FIRST + c);
         }
     }
     __syncthreads();
@@ -754,8 +809,11 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32g(const float* __restr
 // TMA bulk copy (completion on an mbarrier, bounded wait) while the block stages
 // the neighbours, so each block has its entire entry stream in flight at once;
 // tiles with more than A.ecap entries stream them from global memory as without.
-template <int DIM, int OUT, bool BULK>
-__global__ void __launch_bounds__(kTileRows, BULK ? 3 : 6) k_tl_defo32g(
+// GEOM: the pair geometry from the staged records (both halves of RD: position code and
+// velocity) and the sliced slot section, instead of the 16-byte entries: 2 bytes of the
+// plan per pair instead of 16, for about 30 more instructions per pair.
+template <int DIM, int OUT, bool BULK, bool GEOM = false, bool PER = false>
+__global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_defo32g(
     const float* __restrict__ RD, float* __restrict__ RM, const int64_t* __restrict__ row_ptr, int64_t n,
     TLK<float> K, GeoArgs A, const float* __restrict__ B0, float* __restrict__ H, float* __restrict__ u,
     double* __restrict__ dFdt, int* __restrict__ flags) {
@@ -785,14 +843,38 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : 6) k_tl_defo32g(
     const float4* g = A.geo + A.tile_so[tile] + threadIdx.x;
     F8 me = ldg8(RD + 8 * ii);
     float b0[NS], hold[DIM * DIM], uold[DIM];
+    // the epilogue's own-row reads: issued here, their latency hidden by the loop, or (the
+    // geometry form) after it, to keep 18 registers free for more resident warps
+    auto own_row = [&]() {
 #pragma unroll
-    for (int s = 0; s < NS; ++s) b0[s] = B0[s * n + ii];
-    // the epilogue's own-row reads are issued here, their latency hidden by the loop
+        for (int s = 0; s < NS; ++s) b0[s] = B0[s * n + ii];
 #pragma unroll
-    for (int k = 0; k < DIM * DIM; ++k) hold[k] = OUT == OUT_RATES ? 0.0f : H[k * n + ii];
+        for (int k = 0; k < DIM * DIM; ++k) hold[k] = OUT == OUT_RATES ? 0.0f : H[k * n + ii];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) uold[a] = OUT == OUT_RATES ? 0.0f : u[a * n + ii];
-    const bool staged = stage_neighbours<1, 8>(RD, n, P0, m, A, sp);
+        for (int a = 0; a < DIM; ++a) uold[a] = OUT == OUT_RATES ? 0.0f : u[a * n + ii];
+    };
+    if (!GEOM) own_row();
+    // GEOM without periodic axes: positions staged relative to the cell of the tile's
+    // first row (decoded once per neighbour, not per pair)
+    constexpr bool REL = GEOM && !PER;
+    const uint32_t bref = REL ? __float_as_uint(RD[8 * i0 + DIM]) : 0u;
+    bool staged;
+    if (REL) {
+        staged = m <= A.mcap;
+        if (staged) {
+            for (int q = threadIdx.x; q < m; q += blockDim.x) {
+                const int64_t j = min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1);
+                const F8 rj = ldg8(RD + 8 * j);
+                float x[3] = {0.0f, 0.0f, 0.0f};
+                rel_to_ref<DIM>(rj.v, __float_as_uint(rj.v[DIM]), bref, K, x);
+                sp[q] = make_float4(x[0], x[1], x[2], DIM == 3 ? rj.v[7] : rj.v[3]);
+                sp[A.mcap + q] = hi4(rj);
+            }
+        }
+        __syncthreads();
+    } else {
+        staged = GEOM ? stage_neighbours<2, 8, 0>(RD, n, P0, m, A, sp) : stage_neighbours<1, 8>(RD, n, P0, m, A, sp);
+    }
     if (bulk) {
         const bool late = !mbar_wait_bounded(bar, 0, kWaitPolls);
         if (__syncthreads_or(late)) {      // block-uniform: the copy never completed
@@ -822,7 +904,35 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : 6) k_tl_defo32g(
             l22.add(dv2 * e.z);
         }
     };
-    if (bulk && staged) {
+    if (REL && staged) {
+        float xi[3] = {0.0f, 0.0f, 0.0f};
+        rel_to_ref<DIM>(me.v, bi, bref, K, xi);
+        const uint16_t* sl = A.slots + A.tile_so[tile] + threadIdx.x;
+#pragma unroll 4
+        for (int k = 0; k < len; ++k) {
+            int s = min((int)__ldg(sl + (int64_t)k * kTileRows), max(m - 1, 0));
+            defo_pair_rel<DIM>(sp[s], sp[A.mcap + s], xi, nv01, nv2, K, c01, r2, l22);
+        }
+    } else if (GEOM) {
+        float oi[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) oi[a] = me.v[a];
+        const uint16_t* sl = A.slots + A.tile_so[tile] + threadIdx.x;
+        if (staged) {
+#pragma unroll 4
+            for (int k = 0; k < len; ++k) {
+                int s = min((int)__ldg(sl + (int64_t)k * kTileRows), max(m - 1, 0));
+                defo_pair<DIM, PER>(sp[s], sp[A.mcap + s], oi, bi, nv01, nv2, K, c01, r2, l22);
+            }
+        } else {
+            for (int k = 0; k < len; ++k) {
+                int s = min((int)__ldg(sl + (int64_t)k * kTileRows), max(m - 1, 0));
+                int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
+                F8 rj = ldg8(RD + 8 * j);
+                defo_pair<DIM, PER>(lo4(rj), hi4(rj), oi, bi, nv01, nv2, K, c01, r2, l22);
+            }
+        }
+    } else if (bulk && staged) {
         const float4* gs = eb + threadIdx.x;
 #pragma unroll 4
         for (int k = 0; k < len; ++k) {
@@ -860,6 +970,7 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : 6) k_tl_defo32g(
         Lt[2 * DIM + 2] = l22.value();
     }
     float vi[3] = {me.v[4], me.v[5], me.v[6]};
+    if (GEOM) own_row();
     defo_finish<DIM, OUT>(Lt, b0, (bi & kFixedBit) != 0, vi, i, n, K, RM, H, u, dFdt, hold, uold);
 }
 
@@ -1317,7 +1428,7 @@ struct TlPlan {
     GeoArgs mom, defo;
     PipeArgs pmom, pdefo;
     size_t mom_bytes, defo_bytes, pmom_bytes, pdefo_bytes;
-    bool on, pipe_mom, pipe_defo, bulk_defo;
+    bool on, pipe_mom, pipe_defo, bulk_defo, geom_defo;
     int grid;
 };
 
@@ -1327,7 +1438,7 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
     t.mom = GeoArgs{nullptr, nullptr, nullptr, nullptr, 0};
     t.defo = t.mom;
     t.mom_bytes = t.defo_bytes = t.pmom_bytes = t.pdefo_bytes = 0;
-    t.pipe_mom = t.pipe_defo = t.bulk_defo = false;
+    t.pipe_mom = t.pipe_defo = t.bulk_defo = t.geom_defo = false;
     t.grid = 0;
     if (!t.on) return t;
     TilePlan tp = tile_plan_view(st->plan, n, st->plan_nnz);
@@ -1358,6 +1469,16 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
         t.defo.ecap = (int)std::max<int64_t>(0, std::min(room, want));
         t.bulk_defo = t.defo.ecap > 0;
         t.defo_bytes = (size_t)(md + t.defo.ecap) * 16 + 16;
+    }
+    // geometry form of the deformation pass: both record halves staged, the slot section
+    t.geom_defo = ctx->tile_pipe == SPH_PIPE_GEOM &&
+                  st->plan_bytes >= (int64_t)tl_plan_total(n, st->plan_nnz, st->plan_maxrow);
+    if (t.geom_defo) {
+        int mg = stage_mcap(st->plan_maxm, 2, ctx->stage_cap);
+        t.defo.mcap = mg;
+        t.defo.slots = reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(st->plan) +
+                                                         tl_slot_offset(n, st->plan_nnz, st->plan_maxrow));
+        t.defo_bytes = (size_t)mg * 32;
     }
     int64_t g = ctx->num_sms > 0 ? ctx->num_sms : 1;
     t.grid = (int)(g < tp.ntiles ? g : tp.ntiles);
@@ -1412,6 +1533,14 @@ void tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph
                                                        : k_tl_defo32g<DIM, OUT_STEP, true>)
                                    : (out == OUT_RATES ? k_tl_defo32g<DIM, OUT_RATES, false>
                                                        : k_tl_defo32g<DIM, OUT_STEP, false>);
+            if (tp.geom_defo) {
+                if (K.periodic)
+                    f = out == OUT_RATES ? k_tl_defo32g<DIM, OUT_RATES, false, true, true>
+                                         : k_tl_defo32g<DIM, OUT_STEP, false, true, true>;
+                else
+                    f = out == OUT_RATES ? k_tl_defo32g<DIM, OUT_RATES, false, true, false>
+                                         : k_tl_defo32g<DIM, OUT_STEP, false, true, false>;
+            }
             if (tp.bulk_defo) ctx->waits_pending = true;
             sph_allow_dynamic_smem((const void*)f);
             f<<<g, b, tp.defo_bytes, s>>>(st->rd, st->rm, st->row_ptr, n, K, tp.defo, st->B32, st->H32, st->u32,
@@ -1480,20 +1609,23 @@ extern "C" int sph_tlsph_plan(sph_ctx* ctx, const sph_tlsph_params* p, sph_tlsph
     int64_t nnz = 0, maxrow = 0;
     r = sph_row_stats(ctx, st->row_ptr, n, s, &nnz, &maxrow);
     if (r) return r;
-    if (st->plan_bytes < (int64_t)tile_plan_bytes(n, nnz, maxrow)) return SPH_ERR_CAPACITY;
+    if (st->plan_bytes < (int64_t)tl_plan_total(n, nnz, maxrow)) return SPH_ERR_CAPACITY;
     if (nnz == 0) return SPH_OK;
     int32_t mm = 0, mp = 0, mw = 0;
     r = sph_build_tile_plan(ctx, st->row_ptr, st->col, n, nnz, st->plan, s, &mm, &mp, &mw);
     if (r) return r;
+    if (mw != maxrow) return SPH_ERR_ARG;     // both are the longest row of the same lists
     TilePlan tp = tile_plan_view(st->plan, n, nnz);
+    uint16_t* slots = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(st->plan) +
+                                                  tl_slot_offset(n, nnz, maxrow));
     TLK<double> K = make_tl_consts<double>(p);
     unsigned nt = (unsigned)tp.ntiles;
     if (p->dom.dim == 2)
         k_tl_geo<2><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_e, tp.tile_so,
-                                             n, K, tp.geo);
+                                             n, K, tp.geo, slots);
     else
         k_tl_geo<3><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_e, tp.tile_so,
-                                             n, K, tp.geo);
+                                             n, K, tp.geo, slots);
     SPH_LAUNCH_CHECK(ctx);
     SPH_CUDA(ctx, cudaStreamSynchronize(s));
     st->plan_nnz = nnz;
@@ -1513,7 +1645,7 @@ extern "C" int sph_tlsph_plan_bytes(sph_ctx* ctx, const sph_tlsph_params* p, con
         r = sph_row_stats(ctx, st->row_ptr, n, as_stream(stream), &nnz, &maxrow);
         if (r) return r;
     }
-    *bytes_host = (int64_t)tile_plan_bytes(n, nnz, maxrow);
+    *bytes_host = (int64_t)tl_plan_total(n, nnz, maxrow);
     return SPH_OK;
 }
 

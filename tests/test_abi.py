@@ -79,7 +79,7 @@ def test_header_constants_match_the_binding():
         if hasattr(_lib, name):
             assert getattr(_lib, name) == int(val), name
             checked += 1
-    for name in ("SPH_PIPE_STREAM", "SPH_PIPE_PERSISTENT", "SPH_PIPE_BULK", "SPH_PASS_RELAX", "SPH_PASS_COMPRESSIBLE", "SPH_TIMER_NEIGHBORS"):
+    for name in ("SPH_PIPE_STREAM", "SPH_PIPE_PERSISTENT", "SPH_PIPE_BULK", "SPH_PIPE_GEOM", "SPH_PASS_RELAX", "SPH_PASS_COMPRESSIBLE", "SPH_TIMER_NEIGHBORS"):
         assert name in defs and hasattr(_lib, name), name
     assert checked >= 10
 

@@ -32,17 +32,29 @@ def _setup(ctx, dp=0.005, kappa=1.6, law=OT.NEO_HOOKEAN, case=None):
     return OracleLists("r0", "B0_h", c=c, d=d, r0=r0, v=v, fixed=fixed, vol=vol, rp=rp, col=col, B0=B0, prm=prm)
 
 
+@pytest.fixture(autouse=True)
+def _default_pipeline(ctx):
+    yield
+    ctx.set_tile_pipeline(api.SPH_PIPE_GEOM)
+
+
 def _solid(ctx, s, precision, law, v=None, H=None, tiles=True):
+    # tiles = "geom" / "stream": the tile plan, the deformation pass evaluating the pair
+    # geometry from staged records (SPH_PIPE_GEOM, the default) or streaming the
+    # precomputed entries (SPH_PIPE_STREAM); the mode stays in force until the test ends
+    if tiles in ("geom", "stream"):
+        ctx.set_tile_pipeline(api.SPH_PIPE_GEOM if tiles == "geom" else api.SPH_PIPE_STREAM)
+        tiles = True
     c = s["c"]
     return api.TLSolid(ctx, s["d"], cuda(s["r0"]), cuda(s["vol"]), s["B0"], s["fixed"], s["rp"], s["col"],
                        s["v"] if v is None else v, c["dt"], c["rho0"], c["lam"], c["G"], law=law,
                        precision=precision, H=H, tiles=tiles)
 
 
-# float64, then float32 with the tiles staged in shared memory and float32 gathering
-# from global memory
-VARIANTS = ((api.SPH_FP64, True, 1e-12, rel_max), (api.SPH_FP32_KAHAN, True, 1e-5, rel_l2),
-            (api.SPH_FP32_KAHAN, False, 1e-5, rel_l2))
+# float64; float32 on the tile plan streaming its entries, float32 gathering from global
+# memory, and float32 on the plan with the deformation pass's geometry per pair
+VARIANTS = ((api.SPH_FP64, True, 1e-12, rel_max), (api.SPH_FP32_KAHAN, "stream", 1e-5, rel_l2),
+            (api.SPH_FP32_KAHAN, False, 1e-5, rel_l2), (api.SPH_FP32_KAHAN, "geom", 1e-5, rel_l2))
 
 
 @pytest.mark.parametrize("periodic", [False, True])
@@ -207,8 +219,34 @@ def test_planned_pass_forms_agree_bitwise(ctx, dp):
                 ref = got
             else:
                 assert all(torch.equal(p, q) for p, q in zip(got, ref)), (pipe, cap)
-    ctx.set_tile_pipeline(api.SPH_PIPE_STREAM)
+    ctx.set_tile_pipeline(api.SPH_PIPE_GEOM)
     ctx.set_stage_cap(0)
+
+
+def test_geometry_form_against_the_entry_form(ctx):
+    # SPH_PIPE_GEOM evaluates grad0 W_ij V0_j in float32 where the entries hold it
+    # rounded from float64, in the same pair order: the two agree to float32 rounding,
+    # and so does the geometry form with its neighbours read from global memory (stage
+    # capacity 16: the pair offsets from the cell codes instead of tile-relative positions)
+    s = _setup(ctx, dp=0.004)
+    n = s["r0"].shape[1]
+    rng = np.random.default_rng(3)
+    H = 0.01 * rng.normal(size=(9, n))
+    v = s["v"] + 0.1 * rng.normal(size=s["v"].shape)
+    out = {}
+    for pipe, cap in ((api.SPH_PIPE_STREAM, 0), (api.SPH_PIPE_GEOM, 0), (api.SPH_PIPE_GEOM, 16)):
+        ctx.set_tile_pipeline(pipe)
+        ctx.set_stage_cap(cap)
+        try:
+            sol = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN, v=v, H=H)
+            a, Fd = sol.rates()
+            sol.step(3)
+            out[(pipe, cap)] = [a, Fd] + list(sol.fields())
+        finally:
+            ctx.set_stage_cap(0)
+    ref, geo, glob = out[(api.SPH_PIPE_STREAM, 0)], out[(api.SPH_PIPE_GEOM, 0)], out[(api.SPH_PIPE_GEOM, 16)]
+    for p, q, r in zip(geo[:2], ref[:2], glob[:2]):
+        assert rel_l2(host(p), host(q)) < 1e-6 and rel_l2(host(r), host(q)) < 1e-6
 
 
 def test_linear_field_and_momentum_invariants(ctx):
