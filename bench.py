@@ -922,7 +922,13 @@ def run_gpu(args):
                                "tl_stress_initial": t_str / max(n_str, 1)},
             "roofline": {"bound": "hbm", "kernel": dominant[0], "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                         "algorithmic_bytes_per_launch": dominant[1]},
+                         "algorithmic_bytes_per_launch": dominant[1],
+                         "by_kernel": {name: {"ms_per_launch": t, "achieved": b / (t * 1e-3) / 1e9,
+                                              "frac": b / (t * 1e-3) / 1e9 / peak,
+                                              "algorithmic_bytes_per_launch": b,
+                                              "traffic": ncu_traffic.get((name, pipe))}
+                                       for name, b, t in (("tl_momentum_pass", mom_b, avg_mom),
+                                                          ("tl_deformation_pass", def_b, avg_def))}},
             "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d, "state_finite": e2e_ok,
                     "what": "per step, through the C ABI: the float64 state (x, v, F-I) in mapped page-locked "
