@@ -105,3 +105,68 @@ def test_narrow_periodic_strip_is_refused():
         inputs.sod_strip(nx=200, ny=3, kappa=2.0)
     with pytest.raises(ValueError):
         N.Domain(2, 0.01, 2.0, [0, 0], [1.0, 0.03], [True, True])
+
+
+def _states(seed, m, du):
+    """m pairs of subsonic states along random normals, with u_l - u_r = du c_bar on average."""
+    rng = np.random.default_rng(seed)
+    ang = rng.uniform(0, 2 * math.pi, m)
+    nrm = np.stack([np.cos(ang), np.sin(ang)])
+    tng = np.stack([-nrm[1], nrm[0]])
+    rho_l, rho_r = rng.uniform(0.8, 1.5, m), rng.uniform(0.8, 1.5, m)
+    p_l, p_r = rng.uniform(0.8, 1.5, m), rng.uniform(0.8, 1.5, m)
+    c_l, c_r = np.sqrt(1.4 * p_l / rho_l), np.sqrt(1.4 * p_r / rho_r)
+    cbar = 0.5 * (c_l + c_r)
+    ul = 0.5 * du * cbar + rng.uniform(-0.05, 0.05, m)
+    ur = -0.5 * du * cbar + rng.uniform(-0.05, 0.05, m)
+    wl, wr = rng.uniform(-0.3, 0.3, m), rng.uniform(-0.3, 0.3, m)
+    vl, vr = ul * nrm + wl * tng, ur * nrm + wr * tng
+    E_l = p_l / 0.4 + 0.5 * rho_l * np.sum(vl * vl, axis=0)
+    E_r = p_r / 0.4 + 0.5 * rho_r * np.sum(vr * vr, axis=0)
+    return dict(rho_l=rho_l, vl=vl, p_l=p_l, E_l=E_l, c_l=c_l, rho_r=rho_r, vr=vr, p_r=p_r, E_r=E_r, c_r=c_r,
+                nrm=nrm, tng=tng, ul=ul, ur=ur, wl=wl, wr=wr)
+
+
+def _solve(s, eta):
+    return C.hllc_interface_state(s["rho_l"], s["vl"], s["p_l"], s["E_l"], s["c_l"], s["rho_r"], s["vr"], s["p_r"],
+                                  s["E_r"], s["c_r"], s["nrm"], eta)
+
+
+def test_full_limiter_is_the_acoustic_riemann_solver():
+    # compression by more than c_bar saturates the limiter (beta = 1): u* and p* are then
+    # the textbook linearised (acoustic) Riemann solution with impedances Z = rho c,
+    #   u* = (Z_l u_l + Z_r u_r + p_l - p_r)/(Z_l + Z_r),
+    #   p* = (Z_r p_l + Z_l p_r + Z_l Z_r (u_l - u_r))/(Z_l + Z_r)
+    # (the printed minus in the limited p* would not give it); without the limiter
+    # (eta = 0) they are the impedance-weighted velocity and the plain mean pressure
+    s = _states(4, 40, du=1.5)
+    zl, zr = s["rho_l"] * s["c_l"], s["rho_r"] * s["c_r"]
+    _, v_s, _, p_s = _solve(s, 1.0)
+    u_s = np.sum(v_s * s["nrm"], axis=0)
+    assert np.allclose(u_s, (zl * s["ul"] + zr * s["ur"] + s["p_l"] - s["p_r"]) / (zl + zr), rtol=1e-12, atol=1e-12)
+    assert np.allclose(p_s, (zr * s["p_l"] + zl * s["p_r"] + zl * zr * (s["ul"] - s["ur"])) / (zl + zr), rtol=1e-12)
+    _, v_s, _, p_s = _solve(s, 0.0)
+    assert np.allclose(np.sum(v_s * s["nrm"], axis=0), (zl * s["ul"] + zr * s["ur"]) / (zl + zr), rtol=1e-12,
+                       atol=1e-12)
+    assert np.allclose(p_s, 0.5 * (s["p_l"] + s["p_r"]), rtol=1e-12)
+
+
+@pytest.mark.parametrize("du", [0.3, 1.5, -0.4])
+def test_star_state_satisfies_the_jump_conditions(du):
+    # the star state taken on the side u* points away from satisfies the Rankine-Hugoniot
+    # conditions for mass and energy across that side's wave S_k (S_l = u_l - c_l,
+    # S_r = u_r + c_r), with the normal velocity u* and pressure p*; its tangential
+    # velocity is the mean of the two sides'
+    s = _states(7, 60, du)
+    rho_s, v_s, E_s, p_s = _solve(s, 1.0)
+    u_s = np.sum(v_s * s["nrm"], axis=0)
+    left = u_s > 0.0
+    S = np.where(left, s["ul"] - s["c_l"], s["ur"] + s["c_r"])
+    rho_k = np.where(left, s["rho_l"], s["rho_r"])
+    u_k = np.where(left, s["ul"], s["ur"])
+    E_k = np.where(left, s["E_l"], s["E_r"])
+    p_k = np.where(left, s["p_l"], s["p_r"])
+    assert np.all((s["ul"] - s["c_l"] < 0) & (s["ur"] + s["c_r"] > 0))     # subsonic: a star state
+    assert np.allclose(S * (rho_s - rho_k), rho_s * u_s - rho_k * u_k, rtol=1e-12, atol=1e-12)
+    assert np.allclose(S * (E_s - E_k), (E_s + p_s) * u_s - (E_k + p_k) * u_k, rtol=1e-12, atol=1e-12)
+    assert np.allclose(np.sum(v_s * s["tng"], axis=0), 0.5 * (s["wl"] + s["wr"]), rtol=1e-12, atol=1e-12)
