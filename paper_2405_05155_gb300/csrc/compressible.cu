@@ -405,7 +405,8 @@ __global__ void __launch_bounds__(128) k_comp32(const float4* __restrict__ r0, c
     float G1[DIM], N1[DIM], G2[DIM] = {}, N2[DIM] = {};
     int j2 = 0;
     Prim<DIM, float> P1;
-    if (cnt > 0) P1 = load_rec<DIM>(r0, r1, load_entry<DIM>(ga, gb, e, G1, N1));
+    // a plan of other lists reads wrong but in-bounds records: j is clamped to [0, n)
+    if (cnt > 0) P1 = load_rec<DIM>(r0, r1, min(max(load_entry<DIM>(ga, gb, e, G1, N1), 0), (int)(n - 1)));
     if (cnt > 1) j2 = load_entry<DIM>(ga, gb, e + kStride, G2, N2);
     e += 2 * kStride;
     for (int m = 0; m < cnt; ++m) {
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__(128) k_comp32(const float4* __restrict__ r0, c
             N1[d] = N2[d];
         }
         const Prim<DIM, float> Pj = P1;
-        if (m + 1 < cnt) P1 = load_rec<DIM>(r0, r1, j2);
+        if (m + 1 < cnt) P1 = load_rec<DIM>(r0, r1, min(max(j2, 0), (int)(n - 1)));
         if (m + 2 < cnt) j2 = load_entry<DIM>(ga, gb, e, G2, N2);
         e += kStride;
         float rho_s, v_s[DIM], E_s, p_s;
