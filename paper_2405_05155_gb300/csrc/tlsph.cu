@@ -624,7 +624,7 @@ static inline size_t tl_plan_total(int64_t n, int64_t nnz, int64_t maxrow) {
 }
 
 // Pair entries of the tile plan: w = grad0 W_ij V0_j in float64, stored float32,
-// with the neighbour's slot, rows laid out by offset (offset_order).
+// with the neighbour's slot, each row's pairs in the bank-aware order (bank_order).
 template <int DIM>
 __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__ r0, const double* __restrict__ V0,
                                                       const int64_t* __restrict__ row_ptr,
@@ -643,15 +643,9 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
     double xi[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) xi[a] = active ? r0[a * n + i] : 0.0;
+    // pair order: bank-aware for the staged float4 gathers of both passes (see bank_order)
     uint32_t order[kSortCap];
-    const bool sorted = offset_order<DIM>(
-        len, 2.0 * K.inv_h,
-        [&](int k, double* rr) {
-            double r[DIM], d2;
-            pair_r64<DIM>(xi, r0, n, col[b + k], K, r, d2);
-            for (int a = 0; a < DIM; ++a) rr[a] = r[a];
-        },
-        order);
+    const bool sorted = bank_order(len, [&](int k) { return (int)lcol[b + k]; }, order);
     for (int k = 0; k < width; ++k) {
         float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (k < len) {

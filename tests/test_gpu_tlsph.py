@@ -132,6 +132,26 @@ def test_steps_parity(ctx, kappa):
         assert np.all(host(v)[:, s["fixed"] == 1] == 0.0)
 
 
+def _bank_order(slots):
+    """The bank-aware pair order of a tile (rows of 8-lane quarter warps, positions in turn,
+    lanes in turn: the first remaining pair whose slot mod 8 no earlier lane took at that
+    position, else the first remaining pair), written out from its description."""
+    orders = [np.zeros(len(sl), dtype=np.int64) for sl in slots]
+    for q0 in range(0, len(slots), 8):
+        group = list(range(q0, min(q0 + 8, len(slots))))
+        rem = {r: list(range(len(slots[r]))) for r in group}
+        for p in range(max(len(slots[r]) for r in group)):
+            used = set()
+            for r in group:
+                if p >= len(slots[r]):
+                    continue
+                pick = next((k for k in rem[r] if slots[r][k] % 8 not in used), rem[r][0])
+                rem[r].remove(pick)
+                orders[r][p] = pick
+                used.add(int(slots[r][pick]) % 8)
+    return orders
+
+
 def _read_plan(plan, n, nnz, maxrow):
     """Split a tile-plan buffer by its documented layout."""
     raw = host(plan)
@@ -146,6 +166,8 @@ def _read_plan(plan, n, nnz, maxrow):
         o += a16(size)
     o = (o + 31) // 32 * 32
     out["geo"] = raw[o:o + 16 * nt * 128 * maxrow].view(np.float32).reshape(-1, 4)
+    o += 16 * nt * 128 * maxrow
+    out["slots"] = raw[o:o + 2 * nt * 128 * maxrow].view(np.uint16)     # the TL plan's slot section
     return out
 
 
@@ -177,6 +199,8 @@ def test_tile_plan_is_exact(ctx):
         assert P["tile_e"][b] == 128 * width
         so = P["tile_so"][b]
         assert P["tile_so"][b + 1] == so + 128 * width
+        slots = [lc[rp[i] - p0:rp[i + 1] - p0] for i in range(i0, i1)]
+        orders = _bank_order(slots) if b < 12 else None
         for r in range(i1 - i0):
             i = i0 + r
             k = np.arange(lens[i])
@@ -185,13 +209,17 @@ def test_tile_plan_is_exact(ctx):
             dx = ON.min_image(s["r0"][:, i:i + 1] - s["r0"][:, j], dom)
             q = np.sqrt(np.sum(dx * dx, axis=0)) / h
             w = OKer.wendland_dwdr(q * h, h, 3, None) / (q * h) * s["vol"][j] * dx
-            # entries ordered by the offset quantised to h/2 (z, y, x major to minor), then list order
-            c = np.clip(np.rint(dx * (2.0 * (1.0 / h))), -8, 7).astype(np.int64) + 8
-            o = np.lexsort((k, (c[2] * 16 + c[1]) * 16 + c[0]))
+            # the entries are the row's pairs, each once: the slot says which
+            got = ent[:, 3].view(np.int32)
+            o = np.array([np.flatnonzero(slots[r] == g)[0] for g in got], dtype=np.int64)
+            assert np.array_equal(np.sort(o), k)
+            if orders is not None:
+                assert np.array_equal(o, orders[r])
             assert np.allclose(ent[:, :3].T, w[:, o], rtol=2e-6, atol=1e-6 * np.abs(w).max())
-            assert np.array_equal(ent[:, 3].view(np.int32), lc[rp[i] - p0:rp[i + 1] - p0][o])
             pad = P["geo"][so + np.arange(lens[i], width) * 128 + r]
             assert np.all(pad == 0.0)
+            # the slot section repeats the entries' slots in the same sliced order
+            assert np.array_equal(P["slots"][so + k * 128 + r], got.astype(np.uint16))
         ms.append(u.size)
         ps.append(p1 - p0)
     assert hdr[0] == max(ms) and hdr[1] == max(ps) and hdr[2] == lens.max()
