@@ -184,7 +184,9 @@ def _sum_over_ranks(x, world):
 
 
 def _alg_bytes_tl(n, nnz):
-    """Algorithmic bytes of one float32 TL step, by pass (see the roofline notes in the design doc).
+    """Algorithmic bytes of one float32 TL step, by pass: the bytes the method must move
+    (state once per pass, indices, row offsets); a plan's precomputed pair entries are not
+    counted (they trade arithmetic for bytes).
 
     momentum pass:  row_ptr 8 + own RM record 64 + own velocity read/write 32 per particle,
                     col 4 per pair;
