@@ -980,7 +980,7 @@ def main():
     ap.add_argument("--rows", default="", help="comma-separated names of the other rows to run (default: all)")
     ap.add_argument("--other-steps", type=int, default=100, help="timed steps of the other Eulerian workloads")
     ap.add_argument("--traffic", type=float, default=None,
-                    help="ncu dram bytes per launch of the dominant kernel, if measured for this build")
+                    help="ncu dram bytes per launch of the dominant kernel, if measured for the current kernels")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
