@@ -186,7 +186,7 @@ void launch_step(const BatchPlan& pl, int dim, const sph_batch_state* st, int64_
 void launch_step_planned(int dim, const sph_batch_state* st, int ncases, const EulerK<float>* dK,
                          const PlanCase* dP, const PlanShape& sh, cudaStream_t s) {
     dim3 g((unsigned)sh.tiles), b(kTileRows);
-    size_t smem = (size_t)sh.mcap * 16;
+    size_t smem = (size_t)sh.mcap * 16 + kEntryRingBytes;
     float* r0 = st->rec;
     float* r1 = st->rec_tmp;
     if (dim == 2) {

@@ -1,6 +1,7 @@
 // Per-pair physics and packed-record helpers of the Eulerian WCSPH passes, shared by the
 // single-case kernels (eulerian.cu) and the batched persistent kernel (batched.cu).
 #pragma once
+#include "async.cuh"
 #include "common.cuh"
 #include "tiles.cuh"
 
@@ -189,6 +190,10 @@ __device__ __forceinline__ void euler_update32(const float* vi, float dri, float
 }
 
 // ------------------------------------------------- planned passes (tile plans)
+// Entry ring of a planned pass: slots of 32 bytes per thread (see euler_tile_g).
+constexpr int kEntryRing = 4;
+constexpr size_t kEntryRingBytes = (size_t)kEntryRing * kTileRows * 32;
+
 struct GeoArgsE {
     const int32_t* tile_m;
     const int64_t* tile_so;
@@ -278,18 +283,36 @@ __device__ __forceinline__ void euler_tile_g(const float* __restrict__ Rin, floa
     for (int a = 0; a < DIM; ++a) ap[a].init();
     const float* g = A.geo + 8 * (so + threadIdx.x);
     const int smax = max(m - 1, 0);
-    if (staged) {
-#pragma unroll 4
-        for (int k = 0; k < len; ++k) {
-            F8 e = ldg8_stream(g + (int64_t)8 * k * kTileRows);
-            int s = min(max(__float_as_int(e.v[7]), 0), smax);
+    // each thread streams its own entries through a ring of kEntryRing 32-byte slots in
+    // shared memory (after the staged neighbours), kEntryRing - 1 entries ahead with
+    // cp.async: a steady stream of loads in flight without holding them in registers.
+    // A slot is refilled only after the pair that read it was evaluated.
+    float4* ring = sp + A.mcap + 2 * threadIdx.x;
+    auto issue = [&](int k) {
+        float4* d = ring + (k % kEntryRing) * (2 * kTileRows);
+        const float* src = g + (int64_t)8 * k * kTileRows;
+        cp_async16(d, src);
+        cp_async16(d + 1, src + 4);
+    };
+#pragma unroll
+    for (int k = 0; k < kEntryRing - 1; ++k) {
+        if (k < len) issue(k);
+        cp_async_commit();
+    }
+    for (int k = 0; k < len; ++k) {
+        if (k + kEntryRing - 1 < len) issue(k + kEntryRing - 1);
+        cp_async_commit();
+        cp_async_wait_group<kEntryRing - 1>();
+        const float4* d = ring + (k % kEntryRing) * (2 * kTileRows);
+        const float4 lo = d[0], hi = d[1];
+        F8 e;
+        e.v[0] = lo.x; e.v[1] = lo.y; e.v[2] = lo.z; e.v[3] = lo.w;
+        e.v[4] = hi.x; e.v[5] = hi.y; e.v[6] = hi.z; e.v[7] = hi.w;
+        const int s = min(max(__float_as_int(e.v[7]), 0), smax);
+        if (staged) {
             euler_pair_geo<DIM, MODE>(e, sp[s], vi, dri, K, am, ap);
-        }
-    } else {
-        for (int k = 0; k < len; ++k) {
-            F8 e = ldg8_stream(g + (int64_t)8 * k * kTileRows);
-            int s = min(max(__float_as_int(e.v[7]), 0), smax);
-            int64_t j = row_base + min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
+        } else {
+            const int64_t j = row_base + min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
             euler_pair_geo<DIM, MODE>(e, __ldg(reinterpret_cast<const float4*>(Rin + kRecWords * j) + 3), vi, dri,
                                       K, am, ap);
         }

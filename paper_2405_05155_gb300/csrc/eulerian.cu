@@ -353,7 +353,7 @@ EuPlan eu_plan(const sph_ctx* ctx, const sph_eulerian_state* st, int64_t n) {
     TilePlan tp = tile_plan_view(st->plan, n, st->plan_nnz);
     int mc = stage_mcap(st->plan_maxm, 1, ctx->stage_cap);
     t.A = GeoArgsE{tp.tile_m, tp.tile_so, tp.uidx, reinterpret_cast<const float*>(tp.geo), mc};
-    t.bytes = (size_t)mc * 16;
+    t.bytes = (size_t)mc * 16 + kEntryRingBytes;
     return t;
 }
 
