@@ -852,6 +852,19 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
     // first row (decoded once per neighbour, not per pair)
     constexpr bool REL = GEOM && !PER;
     const uint32_t bref = REL ? __float_as_uint(RD[8 * i0 + DIM]) : 0u;
+    // REL: the tile's slot block (its entries' 2-byte slots, 256 bytes per position)
+    // copied into shared memory after the two staged planes with cp.async while the
+    // neighbours are staged, when the plan's longest row allows (A.ecap positions)
+    uint16_t* ssl = reinterpret_cast<uint16_t*>(sp + 2 * A.mcap);
+    const int width = REL ? A.tile_e[tile] / kTileRows : 0;
+    const bool sslot = REL && width <= A.ecap;
+    if (sslot) {
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(A.slots + A.tile_so[tile]);
+        const int chunks = width * (2 * kTileRows / 16);
+        for (int c = threadIdx.x; c < chunks; c += blockDim.x)
+            cp_async16(reinterpret_cast<unsigned char*>(ssl) + 16 * c, src + 16 * c);
+        cp_async_commit();
+    }
     bool staged;
     if (REL) {
         staged = m <= A.mcap;
@@ -865,6 +878,7 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
                 sp[A.mcap + q] = hi4(rj);
             }
         }
+        if (sslot) cp_async_wait_all();
         __syncthreads();
     } else {
         staged = GEOM ? stage_neighbours<2, 8, 0>(RD, n, P0, m, A, sp) : stage_neighbours<1, 8>(RD, n, P0, m, A, sp);
@@ -901,11 +915,20 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
     if (REL && staged) {
         float xi[3] = {0.0f, 0.0f, 0.0f};
         rel_to_ref<DIM>(me.v, bi, bref, K, xi);
-        const uint16_t* sl = A.slots + A.tile_so[tile] + threadIdx.x;
+        if (sslot) {
+            const uint16_t* sl = ssl + threadIdx.x;
 #pragma unroll 4
-        for (int k = 0; k < len; ++k) {
-            int s = min((int)__ldg(sl + (int64_t)k * kTileRows), max(m - 1, 0));
-            defo_pair_rel<DIM>(sp[s], sp[A.mcap + s], xi, nv01, nv2, K, c01, r2, l22);
+            for (int k = 0; k < len; ++k) {
+                int s = min((int)sl[k * kTileRows], max(m - 1, 0));
+                defo_pair_rel<DIM>(sp[s], sp[A.mcap + s], xi, nv01, nv2, K, c01, r2, l22);
+            }
+        } else {
+            const uint16_t* sl = A.slots + A.tile_so[tile] + threadIdx.x;
+#pragma unroll 4
+            for (int k = 0; k < len; ++k) {
+                int s = min((int)__ldg(sl + (int64_t)k * kTileRows), max(m - 1, 0));
+                defo_pair_rel<DIM>(sp[s], sp[A.mcap + s], xi, nv01, nv2, K, c01, r2, l22);
+            }
         }
     } else if (GEOM) {
         float oi[DIM];
@@ -1472,7 +1495,10 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
         t.defo.mcap = mg;
         t.defo.slots = reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(st->plan) +
                                                          tl_slot_offset(n, st->plan_nnz, st->plan_maxrow));
-        t.defo_bytes = (size_t)mg * 32;
+        // the tile's slot block in shared memory too, up to 128 positions (32 KB)
+        t.defo.tile_e = tp.tile_e;
+        t.defo.ecap = st->plan_maxrow <= 128 ? (int)st->plan_maxrow : 0;
+        t.defo_bytes = (size_t)mg * 32 + (size_t)t.defo.ecap * kTileRows * 2;
     }
     int64_t g = ctx->num_sms > 0 ? ctx->num_sms : 1;
     t.grid = (int)(g < tp.ntiles ? g : tp.ntiles);
