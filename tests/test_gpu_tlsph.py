@@ -277,6 +277,42 @@ def test_geometry_form_against_the_entry_form(ctx):
         assert rel_l2(host(p), host(q)) < 1e-6 and rel_l2(host(r), host(q)) < 1e-6
 
 
+def _dense_random_solid(n=1500, seed=3):
+    """Random points in the unit cube with about 170 neighbours per interior particle at
+    kappa = 1.6: rows longer than the 128 pairs the plan's ordering and the shared-memory
+    slot block handle, so the list-order and global-slot fallbacks run."""
+    rng = np.random.default_rng(seed)
+    r0 = rng.uniform(0.0, 1.0, size=(3, n))
+    h = 0.1875
+    d = inputs.domain(3, h, 1.6, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (False, False, False))
+    fixed = (r0[0] < 0.1).astype(np.uint8)
+    v = 0.01 * rng.normal(size=(3, n))
+    v[:, fixed == 1] = 0.0
+    rho0, E, nu = 1000.0, 2.0e6, 0.3
+    lam, G = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+    c0 = np.sqrt((lam + 2 * G) / rho0)
+    return {"r0": r0, "v": v, "fixed": fixed, "vol": np.full(n, 1.0 / n), "domain": d, "dt": 0.1 * h / c0,
+            "rho0": rho0, "lam": lam, "G": G}
+
+
+def test_long_rows_against_the_oracle(ctx):
+    # rows above 128 pairs: every float32 form, 3 steps, against the oracle
+    case = _dense_random_solid()
+    s = _setup(ctx, case=case)
+    n = s["r0"].shape[1]
+    assert np.max(np.diff(host(s["rp"]))) > 128
+    F0 = np.tile(np.eye(3), (n, 1, 1))
+    x_o, v_o, F_o = OT.run(s["r0"], s["vol"], s["B0_h"], s["fixed"], s["r0"].copy(), s["v"], F0, s["rp_h"],
+                           s["col_h"], s["prm"], 3)
+    H_o = (F_o - np.eye(3)[None]).reshape(n, 9).T
+    for prec, tiles, tol, err in VARIANTS:
+        sol = _solid(ctx, s, prec, OT.NEO_HOOKEAN, tiles=tiles)
+        sol.step(3)
+        x, v, H = sol.fields()
+        assert err(host(v), v_o) < tol, (prec, tiles, err(host(v), v_o))
+        assert err(host(H), H_o) < tol, (prec, tiles, err(host(H), H_o))
+
+
 def test_linear_field_and_momentum_invariants(ctx):
     s = _setup(ctx)
     n = s["r0"].shape[1]
