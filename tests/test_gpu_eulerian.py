@@ -71,6 +71,27 @@ def test_rates_parity(ctx, dim, kappa):
         assert err(host(m), mo) < tol, (prec, err(host(m), mo))
 
 
+def test_long_rows_rates_parity(ctx):
+    # random points in a periodic unit cube with about 180 neighbours each (rows above the
+    # 128 pairs the plan's offset ordering handles): every form against the oracle
+    n = 1500
+    rng = np.random.default_rng(21)
+    pos = rng.uniform(0.0, 1.0, size=(3, n))
+    h = 0.19
+    case = {"domain": inputs.domain(3, h, 1.6, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (True, True, True)),
+            "pos": pos, "dp": 1.0 / n ** (1.0 / 3.0), "v": 0.1 * rng.normal(size=(3, n)),
+            "p": 0.01 * rng.normal(size=n), "c0": 1.0, "vol": np.full(n, 1.0 / n), "dt": 1e-3, "rho0": 1.0,
+            "mu": 0.01}
+    s = _setup(ctx, case)
+    assert np.max(np.diff(host(s["rp"]))) > 128
+    ro, mo = OE.eulerian_rates(s["pos"], s["vol"], s["drho"], s["v"], s["B_h"], s["rp_h"], s["col_h"], s["prm"])
+    for prec, tiles, tol, err in VARIANTS:
+        sim = _sim(ctx, s, case, prec, tiles=tiles)
+        r, m = sim.rates()
+        assert err(host(r), ro) < tol, (prec, tiles, err(host(r), ro))
+        assert err(host(m), mo) < tol, (prec, tiles, err(host(m), mo))
+
+
 def test_plain_method_tgv2d_200_steps(ctx):
     # 2D Taylor-Green vortex, 50x50, h = 1.3 dp, kappa = 1.6, Re = 100, 200 steps in float64
     case = inputs.tgv2d(nx=50, kappa=1.6)
