@@ -137,6 +137,24 @@ def test_fp32_steps_and_conservation(ctx):
         assert abs(np.sum(vol * (g - x0))) < 1e-6 * np.sum(vol * np.abs(w - x0))
 
 
+def test_long_rows_rates_parity(ctx):
+    # random points in a periodic unit cube, about 180 neighbours each (plan width above 128)
+    n = 1500
+    rng = np.random.default_rng(31)
+    pos = rng.uniform(0.0, 1.0, size=(3, n))
+    d = inputs.domain(3, 0.19, 1.6, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (True, True, True))
+    pos, _ = sorted_by_cells(pos, d)
+    vol = np.full(n, 1.0 / n)
+    dev, (orp, ocol, oB, od) = _both(ctx, pos, vol, d)
+    assert np.max(np.diff(orp)) > 128
+    rho, mom, E = _state(n, 3, seed=32)
+    want = OC.compressible_rates(pos, vol, rho, mom, E, oB, orp, ocol, OC.CompressibleParams(od, 1e-4))
+    for prec, tol, err in FORMS:
+        sim = _sim(ctx, d, pos, vol, dev, rho, mom, E, 1e-4, precision=prec)
+        for g, w in zip((host(t) for t in sim.rates()), want):
+            assert err(g, w) < tol, (prec, err(g, w))
+
+
 def test_plan_arguments(ctx):
     pos, vol, d = _periodic(2, 8, 1.6)
     dev, _ = _both(ctx, pos, vol, d)
