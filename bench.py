@@ -96,6 +96,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+TIMER_EVERY = 10      # headline: CUDA events around every 10th launch of each pass
+
+
 def _isnum(s):
     try:
         float(s)
@@ -769,12 +772,15 @@ def run_gpu(args):
         lanes16, _ = sol.autotune(10)
     sol.step(W)
     torch.cuda.synchronize()
-    ctx.timing(True)
+    # per-kernel CUDA events inside the timed region around every TIMER_EVERY-th launch of
+    # each pass (events around every launch cost about 9 us of a 0.17 ms step)
+    ctx.timing(True, every=TIMER_EVERY)
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     ms, clk = _time_steps(ctx, sol, K, 0, world, clocks)
     t_mom, n_mom = ctx.timer(SPH_TIMER_TL_MOMENTUM)
     t_def, n_def = ctx.timer(SPH_TIMER_TL_DEFORM)
     t_str, n_str = ctx.timer(SPH_TIMER_TL_STRESS)
+    launches = sum(ctx.launches(k) for k in (SPH_TIMER_TL_MOMENTUM, SPH_TIMER_TL_DEFORM, SPH_TIMER_TL_STRESS))
     ctx.timing(False)
     ms_step = ms / K
     pairs_step = 2 * s16["nnz"]
@@ -940,7 +946,8 @@ def run_gpu(args):
                     "with_memcpy": {"value": e2e_copy_value, "ms_per_step": e2e_copy_ms / e2e_steps,
                                     "what": "the same state in pinned host tensors, cudaMemcpyAsync to the "
                                             "device, pack, one step, unpack, cudaMemcpyAsync back"}},
-            "gpu_launches": n_mom + n_def + n_str,
+            "gpu_launches": launches,
+            "kernel_timing": {"events_every_nth_launch": TIMER_EVERY, "timed_launches": n_mom + n_def + n_str},
             "clocks": clk,
             "workloads": workloads,
         }

@@ -147,11 +147,14 @@ int sph_set_stage_cap(sph_ctx* ctx, int cap);
 int sph_set_tile_pipeline(sph_ctx* ctx, int mode);
 
 /* Per-kernel device timing (not part of the paper: measurement support).
- * sph_timing_enable(ctx, 1) clears the counters and makes the step entry points
- * record a CUDA event pair around every kernel launch they make, on the launch
- * stream; sph_timing_enable(ctx, 0) stops recording.  sph_timing_read
- * synchronises on the recorded events and returns, for one SPH_TIMER_* slot,
- * the summed device time in milliseconds and the number of launches. */
+ * sph_timing_enable(ctx, k) with k >= 1 clears the counters and makes the step
+ * entry points record a CUDA event pair, on the launch stream, around every k-th
+ * kernel launch of each slot (k = 1: every launch; a larger k keeps the events' own
+ * cost out of a timed run); sph_timing_enable(ctx, 0) stops recording (SPH_ERR_ARG
+ * for k < 0).  sph_timing_read synchronises on the recorded events and returns, for
+ * one SPH_TIMER_* slot, the summed device time in milliseconds of the timed launches
+ * and their number; sph_timing_launches returns all launches of the slot since
+ * timing was enabled, timed or not. */
 #define SPH_TIMER_TL_STRESS    0
 #define SPH_TIMER_TL_MOMENTUM  1
 #define SPH_TIMER_TL_DEFORM    2
@@ -165,6 +168,7 @@ int sph_set_tile_pipeline(sph_ctx* ctx, int mode);
 #define SPH_TIMER_SLOTS        16
 int sph_timing_enable(sph_ctx* ctx, int on);
 int sph_timing_read(sph_ctx* ctx, int slot, double* total_ms_host, int64_t* launches_host);
+int sph_timing_launches(const sph_ctx* ctx, int slot, int64_t* launches_host);
 
 /* ---- a3: kernel values and radial derivatives ----
  * Eq. 6 (Wendland C2, Sec. 2.3.1) or Eq. 8 (Laguerre-Gauss, Sec. 2.3.2).

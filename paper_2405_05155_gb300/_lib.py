@@ -92,6 +92,7 @@ _SIGNATURES = {
     "sph_get_lanes": (ctypes.c_int, [c_vp, ctypes.c_int]),
     "sph_timing_enable": (ctypes.c_int, [c_vp, ctypes.c_int]),
     "sph_timing_read": (ctypes.c_int, [c_vp, ctypes.c_int, _P(c_dbl), _P(c_i64)]),
+    "sph_timing_launches": (ctypes.c_int, [c_vp, ctypes.c_int, _P(ctypes.c_int64)]),
     "sph_kernel_eval": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_dbl, c_dbl, ctypes.c_int, c_vp, c_vp, c_vp,
                                        c_i64, c_vp]),
     "sph_cell_order": (ctypes.c_int, [c_vp, _P(SphDomain), c_vp, c_vp, c_vp]),

@@ -89,9 +89,16 @@ class Context:
     def get_lanes(self, which):
         return self.lib.sph_get_lanes(self.h, which)
 
-    def timing(self, on):
-        """Start (clearing the counters) or stop per-kernel event timing."""
-        L.check("sph_timing_enable", self.lib.sph_timing_enable(self.h, 1 if on else 0), self.h)
+    def timing(self, on, every=1):
+        """Start (clearing the counters; events around every `every`-th launch of each
+        slot) or stop per-kernel event timing."""
+        L.check("sph_timing_enable", self.lib.sph_timing_enable(self.h, int(every) if on else 0), self.h)
+
+    def launches(self, slot):
+        """All launches of one SPH_TIMER_* slot since timing was enabled, timed or not."""
+        cnt = ctypes.c_int64()
+        L.check("sph_timing_launches", self.lib.sph_timing_launches(self.h, slot, ctypes.byref(cnt)), self.h)
+        return cnt.value
 
     def timer(self, slot):
         """(total device milliseconds, launches) recorded for one SPH_TIMER_* slot."""

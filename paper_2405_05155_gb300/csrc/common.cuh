@@ -27,11 +27,12 @@ struct BatchGraphKey {
 
 struct sph_ctx {
     // per-kernel timing (sph_timing_enable): events recorded around launches
-    bool timing = false;
+    int timing = 0;                 // 0: off; k >= 1: every k-th launch of a slot is timed
     std::vector<TimerRec> pending;
     std::vector<cudaEvent_t> pool;
     double t_ms[SPH_TIMER_SLOTS] = {};
     long long t_n[SPH_TIMER_SLOTS] = {};
+    long long t_all[SPH_TIMER_SLOTS] = {};   // launches seen while timing was on (timed or not)
     int device = 0;
     int last_cuda_error = 0;
     int num_sms = 0;

@@ -139,7 +139,9 @@ static cudaEvent_t pool_get(sph_ctx* ctx) {
 }
 
 int sph_timer_begin(sph_ctx* ctx, int slot, cudaStream_t s) {
-    if (!ctx->timing) return -1;
+    if (ctx->timing <= 0) return -1;
+    const long long c = ctx->t_all[slot]++;
+    if (c % ctx->timing) return -1;                // not a sampled launch
     TimerRec r;
     r.slot = slot;
     r.start = pool_get(ctx);
@@ -173,9 +175,16 @@ static int drain_timers(sph_ctx* ctx) {
 extern "C" int sph_timing_enable(sph_ctx* ctx, int on) {
     if (!ctx) return SPH_ERR_ARG;
     int st = drain_timers(ctx);
-    for (int k = 0; k < SPH_TIMER_SLOTS; ++k) { ctx->t_ms[k] = 0.0; ctx->t_n[k] = 0; }
-    ctx->timing = on != 0;
+    if (on < 0) return SPH_ERR_ARG;
+    for (int k = 0; k < SPH_TIMER_SLOTS; ++k) { ctx->t_ms[k] = 0.0; ctx->t_n[k] = 0; ctx->t_all[k] = 0; }
+    ctx->timing = on;
     return st;
+}
+
+extern "C" int sph_timing_launches(const sph_ctx* ctx, int slot, int64_t* launches_host) {
+    if (!ctx || slot < 0 || slot >= SPH_TIMER_SLOTS || !launches_host) return SPH_ERR_ARG;
+    *launches_host = ctx->t_all[slot];
+    return SPH_OK;
 }
 
 extern "C" int sph_timing_read(sph_ctx* ctx, int slot, double* total_ms_host, int64_t* launches_host) {

@@ -588,8 +588,8 @@ extern "C" int sph_autotune_eulerian(sph_ctx* ctx, const sph_eulerian_params* p,
     SPH_CUDA(ctx, cudaEventCreate(&e1));
     const int lanes_set[4] = {1, 2, 4, 8};
     int keep = ctx->lanes[SPH_PASS_EULERIAN];
-    bool timing = ctx->timing;
-    ctx->timing = false;
+    const int timing = ctx->timing;
+    ctx->timing = 0;
     double best = 1e300;
     int bl = keep;
     for (int li = 0; li < 4; ++li) {

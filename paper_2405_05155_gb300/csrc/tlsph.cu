@@ -1816,8 +1816,8 @@ extern "C" int sph_autotune_tlsph(sph_ctx* ctx, const sph_tlsph_params* p, const
     SPH_CUDA(ctx, cudaEventCreate(&e1));
     const int lanes_set[4] = {1, 2, 4, 8};
     int keep = ctx->lanes[SPH_PASS_TLSPH];
-    bool timing = ctx->timing;
-    ctx->timing = false;
+    const int timing = ctx->timing;
+    ctx->timing = 0;
     double best = 1e300;
     int bl = keep;
     for (int li = 0; li < 4; ++li) {

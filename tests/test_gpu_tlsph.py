@@ -396,3 +396,22 @@ def test_columns_parity(ctx, kind):
         assert err(host(v), v_o) < tol, (prec, tiles, err(host(v), v_o))
         assert err(host(x) - s["r0"], x_o - s["r0"]) < tol
         assert err(host(H), H_o) < tol, (prec, tiles, err(host(H), H_o))
+
+
+def test_sampled_kernel_timing(ctx):
+    # events around every 3rd launch of each pass: 10 steps launch the stress once and
+    # each pass 10 times; launches 1, 4, 7 and 10 of a pass are timed
+    s = _setup(ctx, dp=0.005)
+    sol = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
+    ctx.timing(True, every=3)
+    try:
+        sol.step(10)
+        counts = {k: ctx.launches(k) for k in (api.L.SPH_TIMER_TL_STRESS, api.L.SPH_TIMER_TL_MOMENTUM,
+                                               api.L.SPH_TIMER_TL_DEFORM)}
+        timed = {k: ctx.timer(k) for k in counts}
+    finally:
+        ctx.timing(False)
+    assert counts == {api.L.SPH_TIMER_TL_STRESS: 1, api.L.SPH_TIMER_TL_MOMENTUM: 10, api.L.SPH_TIMER_TL_DEFORM: 10}
+    assert timed[api.L.SPH_TIMER_TL_STRESS][1] == 1
+    assert timed[api.L.SPH_TIMER_TL_MOMENTUM][1] == 4 and timed[api.L.SPH_TIMER_TL_DEFORM][1] == 4
+    assert all(ms > 0.0 for ms, _ in timed.values())
