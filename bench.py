@@ -275,7 +275,7 @@ def _bench_tgv3d(api, inputs, ctx, steps, peak):
         sim, nnz, _ = _eulerian_case(api, ctx, case, api.SPH_FP32_KAHAN)
         lanes, _ = sim.autotune(3)
         sim.step(3)
-        ctx.timing(True)
+        ctx.timing(True, every=TIMER_EVERY)
         ms = _event_ms(lambda: sim.step(steps))
         tm, nm = ctx.timer(SPH_TIMER_EU_MOMENTUM)
         tc, nc = ctx.timer(SPH_TIMER_EU_MASS)
@@ -334,7 +334,7 @@ def _bench_batched(api, inputs, ctx, steps, peak):
     b = batch.EulerianBatch(ctx, cases)
     lanes, block, _ = b.autotune(trial_steps=3)
     b.step(10)
-    ctx.timing(True)
+    ctx.timing(True, every=TIMER_EVERY)
     ms = _event_ms(lambda: b.step(steps))
     tstep, nstep = ctx.timer(SPH_TIMER_BATCH_STEP)
     ctx.timing(False)
@@ -357,7 +357,7 @@ def _bench_relax(api, inputs, ctx, steps, peak):
     r0 = api.relax_residual(ctx, prm, pos, vol)
     api.relax_step(ctx, prm, pos, vol, 3)
     ms = _event_ms(lambda: api.relax_step(ctx, prm, pos, vol, steps))
-    # the same call once more with per-kernel events, for the breakdown
+    # the same call once more with per-kernel events around every launch, for the breakdown
     ctx.timing(True)
     api.relax_step(ctx, prm, pos, vol, steps)
     tn, nn = ctx.timer(SPH_TIMER_NEIGHBORS)
