@@ -881,6 +881,27 @@ def run_gpu(args):
     e2e_ok = all(bool(torch.isfinite(m.t).all()) for m in mapped)
     for m in mapped:
         m.close()
+    # (c) the float32 form's own state (u = x - r0, v, F - I) in float32 mapped host
+    #     buffers, written into the records by load32 and read back by store32 around
+    #     each step: the same values the step keeps, half the bytes of (a)
+    sol_f = _solid(api, ctx, s16, api.SPH_FP32_KAHAN)
+    n16 = s16["n"]
+    b32 = [api.HostArray((3, n16), torch.float32), api.HostArray((3, n16), torch.float32),
+           api.HostArray((9, n16), torch.float32)]
+    sol_f.store32(*b32)
+    torch.cuda.synchronize()
+
+    def _f32_state():
+        sol_f.load32(*b32)
+        sol_f.step(1)
+        sol_f.store32(*b32)
+
+    e2e32_ms = _timed(_f32_state)
+    e2e32_value = _sum_over_ranks(pairs_step * e2e_steps, world) / (e2e32_ms * 1e-3)
+    h2d32 = sum(b.t.numel() for b in b32) * 4
+    e2e32_ok = all(bool(torch.isfinite(b.t).all()) for b in b32)
+    for b in b32:
+        b.close()
 
     workloads = {}
     if not args.headline_only:
@@ -938,13 +959,20 @@ def run_gpu(args):
                                               "traffic": ncu_traffic.get((name, pipe))}
                                        for name, b, t in (("tl_momentum_pass", mom_b, avg_mom),
                                                           ("tl_deformation_pass", def_b, avg_def))}},
-            "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d, "state_finite": e2e_ok,
-                    "what": "per step, through the C ABI: the float64 state (x, v, F-I) in mapped page-locked "
-                            "host buffers (sph_host_alloc) read in place by pack over NVLink-C2C, one step, "
-                            "written back in place by unpack",
+            "e2e": {"value": e2e32_value, "unit": UNIT, "steps": e2e_steps, "ms_per_step": e2e32_ms / e2e_steps,
+                    "h2d_bytes_per_step": h2d32, "d2h_bytes_per_step": h2d32, "state_finite": e2e32_ok,
+                    "what": "per step, through the C ABI: the float32 form's state (u = x - r0, v, F - I) in "
+                            "float32 mapped page-locked host buffers (sph_host_alloc), read in place by "
+                            "sph_tlsph_load32 over NVLink-C2C, one step, written back in place by "
+                            "sph_tlsph_store32",
+                    "with_f64_state": {"value": e2e_value, "ms_per_step": e2e_ms / e2e_steps,
+                                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+                                       "state_finite": e2e_ok,
+                                       "what": "the float64 state (x, v, F - I) in mapped host buffers, read "
+                                               "in place by pack, one step, written back by unpack"},
                     "with_memcpy": {"value": e2e_copy_value, "ms_per_step": e2e_copy_ms / e2e_steps,
-                                    "what": "the same state in pinned host tensors, cudaMemcpyAsync to the "
+                                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+                                    "what": "the float64 state in pinned host tensors, cudaMemcpyAsync to the "
                                             "device, pack, one step, unpack, cudaMemcpyAsync back"}},
             "gpu_launches": launches,
             "kernel_timing": {"events_every_nth_launch": TIMER_EVERY, "timed_launches": n_mom + n_def + n_str},

@@ -458,6 +458,18 @@ int sph_tlsph_plan_bytes(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tl
  * (the results are then not valid). */
 int sph_tlsph_unpack(sph_ctx* ctx, const sph_tlsph_params* prm,
                      const sph_tlsph_state* st, void* stream);
+/* The float32 form's own dynamic state in float32, for callers that keep it outside
+ * the device between steps: u = x - r0 [dim][n], v [dim][n], H = F - I [dim*dim][n]
+ * (device pointers, or mapped host memory of sph_host_alloc, read or written in place).
+ * sph_tlsph_load32 replaces the state of the float32 records (after one
+ * sph_tlsph_pack, which also sets their fixed part); sph_tlsph_store32 copies it out.
+ * The float32 step keeps exactly these values, so a load32 / step / store32 round trip
+ * loses nothing against the device-resident state (half the bytes of the float64
+ * pack/unpack pair). */
+int sph_tlsph_load32(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_state* st,
+                     const float* u, const float* v, const float* H, void* stream);
+int sph_tlsph_store32(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_state* st,
+                      float* u, float* v, float* H, void* stream);
 /* Rates at the current state: dvdt float64 [dim][n] (Eq. 30 / rho0) and
  * dFdt float64 [dim*dim][n] (Eq. 31 with the current v). */
 int sph_tlsph_rates(sph_ctx* ctx, const sph_tlsph_params* prm,

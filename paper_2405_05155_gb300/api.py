@@ -28,6 +28,13 @@ def _p(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _ptr(x):
+    """Pointer of a device tensor (contiguous) or of a mapped HostArray buffer."""
+    if isinstance(x, HostArray):
+        return ctypes.c_void_p(x.dev)
+    return _p(x)
+
+
 def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -380,6 +387,15 @@ class TLSolid:
 
     def unpack(self):
         self._call("sph_tlsph_unpack", _stream())
+
+    def load32(self, u, v, H):
+        """Replace the float32 form's state with u = x - r0, v, H = F - I (float32 device
+        tensors or mapped HostArray buffers of shapes [dim][n], [dim][n], [dim*dim][n])."""
+        self._call("sph_tlsph_load32", _ptr(u), _ptr(v), _ptr(H), _stream())
+
+    def store32(self, u, v, H):
+        """Copy the float32 form's state (u = x - r0, v, H = F - I) out, as load32 takes it."""
+        self._call("sph_tlsph_store32", _ptr(u), _ptr(v), _ptr(H), _stream())
 
     def step(self, nsteps=1):
         self._call("sph_tlsph_step", int(nsteps), _stream())

@@ -1669,6 +1669,66 @@ extern "C" int sph_tlsph_plan_bytes(sph_ctx* ctx, const sph_tlsph_params* p, con
     return SPH_OK;
 }
 
+// The float32 form's dynamic state exchanged in float32: u = x - r0, v, H = F - I.
+template <int DIM>
+__global__ void k_tl_load32(const float* __restrict__ u, const float* __restrict__ v, const float* __restrict__ H,
+                            int64_t n, float* __restrict__ RD, float* __restrict__ u32, float* __restrict__ H32) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        u32[a * n + i] = u[a * n + i];
+        RD[8 * i + 4 + a] = v[a * n + i];
+    }
+#pragma unroll
+    for (int k = 0; k < DIM * DIM; ++k) H32[k * n + i] = H[k * n + i];
+}
+
+template <int DIM>
+__global__ void k_tl_store32(const float* __restrict__ RD, const float* __restrict__ u32,
+                             const float* __restrict__ H32, int64_t n, float* __restrict__ u, float* __restrict__ v,
+                             float* __restrict__ H) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        u[a * n + i] = u32[a * n + i];
+        v[a * n + i] = RD[8 * i + 4 + a];
+    }
+#pragma unroll
+    for (int k = 0; k < DIM * DIM; ++k) H[k * n + i] = H32[k * n + i];
+}
+
+extern "C" int sph_tlsph_load32(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st, const float* u,
+                                const float* v, const float* H, void* stream) {
+    if (!ctx) return SPH_ERR_ARG;
+    int r = check_tl(p, st);
+    if (r) return r;
+    const int64_t n = p->dom.n;
+    if (n == 0) return SPH_OK;
+    if (!u || !v || !H || !st->rd || !st->u32 || !st->H32) return SPH_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    if (p->dom.dim == 2) k_tl_load32<2><<<grid_for(n, 256), 256, 0, s>>>(u, v, H, n, st->rd, st->u32, st->H32);
+    else k_tl_load32<3><<<grid_for(n, 256), 256, 0, s>>>(u, v, H, n, st->rd, st->u32, st->H32);
+    SPH_LAUNCH_CHECK(ctx);
+    return SPH_OK;
+}
+
+extern "C" int sph_tlsph_store32(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st, float* u,
+                                 float* v, float* H, void* stream) {
+    if (!ctx) return SPH_ERR_ARG;
+    int r = check_tl(p, st);
+    if (r) return r;
+    const int64_t n = p->dom.n;
+    if (n == 0) return SPH_OK;
+    if (!u || !v || !H || !st->rd || !st->u32 || !st->H32) return SPH_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    if (p->dom.dim == 2) k_tl_store32<2><<<grid_for(n, 256), 256, 0, s>>>(st->rd, st->u32, st->H32, n, u, v, H);
+    else k_tl_store32<3><<<grid_for(n, 256), 256, 0, s>>>(st->rd, st->u32, st->H32, n, u, v, H);
+    SPH_LAUNCH_CHECK(ctx);
+    return SPH_OK;
+}
+
 extern "C" int sph_tlsph_unpack(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st, void* stream) {
     if (!ctx) return SPH_ERR_ARG;
     int r = check_tl(p, st);

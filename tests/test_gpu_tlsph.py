@@ -377,6 +377,39 @@ def test_state_in_mapped_host_memory(ctx):
             m.close()
 
 
+def test_float32_state_round_trip(ctx):
+    # the float32 form's state kept in mapped host memory as float32 (u = x - r0, v, F - I)
+    # and exchanged every 2 steps with load32 / store32: bit for bit the device-resident run;
+    # and the float64 unpack of the same state agrees with it
+    s = _setup(ctx, dp=0.005)
+    n = s["r0"].shape[1]
+    ref = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
+    sol = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
+    bufs = [api.HostArray((3, n), torch.float32), api.HostArray((3, n), torch.float32),
+            api.HostArray((9, n), torch.float32)]
+    try:
+        ref.pack()
+        sol.pack()
+        sol.store32(*bufs)
+        for _ in range(3):
+            sol.load32(*bufs)
+            sol.step(2)
+            sol.store32(*bufs)
+            ref.step(2)
+        dev = [torch.empty((3, n), dtype=torch.float32, device="cuda"),
+               torch.empty((3, n), dtype=torch.float32, device="cuda"),
+               torch.empty((9, n), dtype=torch.float32, device="cuda")]
+        ref.store32(*dev)
+        torch.cuda.synchronize()
+        for b, d in zip(bufs, dev):
+            assert torch.equal(b.t, d.cpu())
+        x, v, H = ref.fields()
+        assert torch.equal(v.cpu().float(), bufs[1].t) and torch.equal(H.cpu().float(), bufs[2].t)
+    finally:
+        for b in bufs:
+            b.close()
+
+
 @pytest.mark.parametrize("kind", ["twisting", "bending"])
 def test_columns_parity(ctx, kind):
     # the columns of Sec. 5 at side / dp = 4: float64 and float32 (tile plan and per pair)
