@@ -258,7 +258,8 @@ def _eulerian_case(api, ctx, case, precision, tiles=True):
     vol = torch.tensor(case["vol"][oh], dtype=torch.float64, device=dev)
     rp, col = api.build_neighbors(ctx, d, pos)
     B, _, nfb = api.kgc(ctx, d, pos, vol, rp, col)
-    sim = api.Eulerian(ctx, d, pos, vol, B, rp, col, case["p"][oh] / case["c0"] ** 2, case["v"][:, oh], case["dt"],
+    drho = api.density_from_pressure(ctx, d, case["c0"], torch.tensor(case["p"], device=dev)[order])
+    sim = api.Eulerian(ctx, d, pos, vol, B, rp, col, drho, case["v"][:, oh], case["dt"],
                        case["rho0"], case["c0"], case["mu"], precision=precision, tiles=tiles)
     return sim, int(col.numel()), oh
 
@@ -961,17 +962,21 @@ def run_gpu(args):
                                                           ("tl_deformation_pass", def_b, avg_def))}},
             "e2e": {"value": e2e32_value, "unit": UNIT, "steps": e2e_steps, "ms_per_step": e2e32_ms / e2e_steps,
                     "h2d_bytes_per_step": h2d32, "d2h_bytes_per_step": h2d32, "state_finite": e2e32_ok,
+                    "state_form": "float32 (u = x - r0, v, F - I), 12 floats + 3x3 per particle; earlier "
+                                  "lines of this file's history reported the float64 state under this key, "
+                                  "now with_f64_state",
                     "what": "per step, through the C ABI: the float32 form's state (u = x - r0, v, F - I) in "
                             "float32 mapped page-locked host buffers (sph_host_alloc), read in place by "
                             "sph_tlsph_load32 over NVLink-C2C, one step, written back in place by "
                             "sph_tlsph_store32",
                     "with_f64_state": {"value": e2e_value, "ms_per_step": e2e_ms / e2e_steps,
                                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
-                                       "state_finite": e2e_ok,
+                                       "state_finite": e2e_ok, "state_form": "float64 (x, v, F - I)",
                                        "what": "the float64 state (x, v, F - I) in mapped host buffers, read "
                                                "in place by pack, one step, written back by unpack"},
                     "with_memcpy": {"value": e2e_copy_value, "ms_per_step": e2e_copy_ms / e2e_steps,
                                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+                                    "state_form": "float64 (x, v, F - I)",
                                     "what": "the float64 state in pinned host tensors, cudaMemcpyAsync to the "
                                             "device, pack, one step, unpack, cudaMemcpyAsync back"}},
             "gpu_launches": launches,

@@ -133,18 +133,30 @@ int sph_set_stage_cap(sph_ctx* ctx, int cap);
  *   SPH_PIPE_BULK       one block per tile; the deformation pass copies the tile's
  *                       whole entry block into shared memory with one TMA bulk copy
  *                       while it stages the neighbours;
- *   SPH_PIPE_GEOM       one block per tile; the deformation pass stages the
- *                       neighbours' whole records and evaluates each pair's
+ *   SPH_PIPE_GEOM       one block per tile; both passes stage the neighbours'
+ *                       positions (and the deformation pass their velocities, the
+ *                       momentum pass V0_j M_j) and evaluate each pair's
  *                       grad0 W_ij V0_j from them, reading only the entries' 2-byte
- *                       neighbour slots (results differ from the other modes by
- *                       float32 rounding of that factor); the momentum pass streams
- *                       (default: the fastest measured).
+ *                       neighbour slots; the momentum pass sums Eq. 30 as
+ *                       M_i S_i + sum_j (V0_j M_j) grad0 W_ij with the plan's
+ *                       S_i = sum_j grad0 W_ij V0_j (boxes with a periodic axis: the
+ *                       momentum pass streams its entries).  Results differ from the
+ *                       other modes by float32 rounding.  The default: the fastest
+ *                       measured.
  * SPH_ERR_ARG for any other mode. */
 #define SPH_PIPE_STREAM     0
 #define SPH_PIPE_PERSISTENT 1
 #define SPH_PIPE_BULK       2
 #define SPH_PIPE_GEOM       3
 int sph_set_tile_pipeline(sph_ctx* ctx, int mode);
+/* Failure-detection test of the bounded device waits (no counterpart in the paper).
+ * polls > 0: the bounded-wait kernels of the SPH_PIPE_BULK deformation pass issue no
+ * bulk copy and wait at most `polls` polls on an mbarrier phase that nothing
+ * completes, so every block takes its timeout branch (sets the timeout flag, writes
+ * nothing, leaves with no copy in flight) and the next sph_tlsph_unpack returns
+ * SPH_ERR_TIMEOUT.  0 (default) restores normal operation.  SPH_ERR_ARG for polls
+ * above 65536. */
+int sph_set_wait_test(sph_ctx* ctx, uint32_t polls);
 
 /* Per-kernel device timing (not part of the paper: measurement support).
  * sph_timing_enable(ctx, k) with k >= 1 clears the counters and makes the step
@@ -198,7 +210,9 @@ int sph_cell_order(sph_ctx* ctx, const sph_domain* dom, const double* pos,
  * ascending.  pos float64 [dim][n]; row_ptr int64 [n+1]; col int32 [cap].
  * *nnz_host receives row_ptr[n].  If cap < nnz nothing is written to col and
  * SPH_ERR_CAPACITY is returned with *nnz_host = the required capacity
- * (row_ptr is valid).  Synchronises the stream.  Bit-exact with the float64
+ * (row_ptr is valid).  Synchronises the stream once, to read nnz; the fill of
+ * col is then enqueued on `stream` and is complete when the stream reaches it
+ * (row_ptr and *nnz_host are final on return).  Bit-exact with the float64
  * definition: candidates are screened in float32 with a proven error band and
  * every candidate inside the band is decided in float64. */
 int sph_build_neighbors(sph_ctx* ctx, const sph_domain* dom, const double* pos,
@@ -217,13 +231,16 @@ int sph_build_neighbors(sph_ctx* ctx, const sph_domain* dom, const double* pos,
  * loading libsph holds until the process exits.  The caller provides pos,
  * row_ptr and col as usual.  Limits: n <= SPH_STATIC_MAX_PARTICLES and at most
  * SPH_STATIC_MAX_CELLS cells in the grid (n_x n_y n_z of the sph_domain comment);
- * larger inputs return SPH_ERR_LIMIT before any device work.  The first call on
- * each device looks up the array's device address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  Every call reuses the same
- * array and clears what must start at zero; calls that overlap on the GPU (from
- * two streams or two host threads) race on it and must be serialised by the
- * caller.  Synchronises the stream.  On SPH_ERR_CUDA the CUDA error is left for
- * cudaGetLastError(). */
+ * larger inputs return SPH_ERR_LIMIT before any device work.  Every call looks
+ * up the array's device address on the current device (cudaGetSymbolAddress, a
+ * host-side lookup that the first call on a device also uses to load the
+ * module), so make the first call on each device before any stream capture.
+ * Every call reuses the same array and clears what must start at zero; calls
+ * that overlap on the GPU (from two streams or two host threads) race on it and
+ * must be serialised by the caller.  Synchronises the stream once, to read nnz;
+ * the fill of col is then enqueued on `stream` and is complete when the stream
+ * reaches it.  On SPH_ERR_CUDA the CUDA error is left for cudaGetLastError()
+ * (this call only peeks at it). */
 #define SPH_STATIC_MAX_PARTICLES (1 << 20)
 #define SPH_STATIC_MAX_CELLS     (1 << 20)
 #define SPH_STATIC_SCRATCH_BYTES (44u << 20)
@@ -313,6 +330,13 @@ int sph_eulerian_pack(sph_ctx* ctx, const sph_eulerian_params* prm,
 int sph_eulerian_plan_bytes(sph_ctx* ctx, const sph_eulerian_params* prm, const sph_eulerian_state* st,
                             int64_t* bytes_host, void* stream);
 int sph_eulerian_plan(sph_ctx* ctx, const sph_eulerian_params* prm, sph_eulerian_state* st, void* stream);
+/* The weakly-compressible equation of state of Sec. 3.1.1, p = c0^2 (rho - rho0),
+ * inverted for the stored density offset: drho[i] = p[i] / c0^2 for i < prm->dom.n
+ * (p, drho float64 device arrays [n]; only dom.n and c0 of prm are read).  For initial
+ * conditions given as a pressure field.  SPH_ERR_ARG when c0 <= 0 or a pointer is NULL
+ * with n > 0. */
+int sph_eulerian_density_from_pressure(sph_ctx* ctx, const sph_eulerian_params* prm, const double* p,
+                                       double* drho, void* stream);
 /* packed float32 rec -> float64 (drho, v). */
 int sph_eulerian_unpack(sph_ctx* ctx, const sph_eulerian_params* prm,
                         const sph_eulerian_state* st, void* stream);
@@ -660,6 +684,57 @@ int sph_mlp_train_step(sph_ctx* ctx, float* params, float* adam_m, float* adam_v
  * along grad phi to phi = -dp/2 */
 int sph_relax_propose(sph_ctx* ctx, const sph_relax_params* prm, const float* params,
                       double* pos, void* stream);
+
+/* ---- a12 driven from the library: training data, training and the learned run ----
+ * Plain relaxation trajectory samples for training the proposal: from pos (advanced in
+ * place by snapshots * every plain steps of sph_relax_step), for k < snapshots,
+ *   feats   [k n + i][128] = sph_mlp_features at x^(k every),
+ *   targets [k n + i][3]   = (x_i^((k+1) every) - x_i^(k every)) / h   (float32).
+ * dim 3.  The caller allocates feats [snapshots n][128] and targets [snapshots n][3]. */
+int sph_relax_samples(sph_ctx* ctx, const sph_relax_params* prm, double* pos, const double* vol,
+                      int snapshots, int every, float* feats, float* targets, void* stream);
+/* nsteps Adam steps (sph_mlp_train_step; step numbers first_step .. first_step + nsteps - 1)
+ * on minibatches of `batch` rows drawn with replacement from the `rows` samples
+ * (feats [rows][128], targets [rows][3]): row b of step t is sample
+ * floor(z * rows / 2^64), z = SplitMix64(SplitMix64(seed ^ SplitMix64(t)) + b), SplitMix64
+ * being the generator of Steele, Lea and Flood (OOPSLA 2014) with the mixing function of its
+ * public reference implementation.  The draw and the gather run
+ * on the device.  *loss_host (nullable; if set the call synchronises) receives the last
+ * step's minibatch loss. */
+int sph_mlp_train(sph_ctx* ctx, float* params, float* adam_m, float* adam_v, int64_t first_step,
+                  double lr, const float* feats, const float* targets, int64_t rows, int64_t batch,
+                  int nsteps, uint64_t seed, double* loss_host, void* stream);
+/* Relaxation to a residual target with an optional learned proposal.  The residual is
+ * out[0] of sph_relax_residual (Laguerre-Gauss, interior particles).  With a proposal
+ * (applications > 0): up to `applications` times, while the target is not met, the
+ * proposal moves the particles (sph_relax_propose) and is kept only if it lowers the
+ * residual (else it is undone and no further proposal is tried), then up to
+ * plain_between plain steps follow; plain steps (sph_relax_step, checked every
+ * check_every steps) then finish the run, until the target or max_steps plain steps.  If
+ * the target is still missed, plain relaxation is the fallback: pos is reset to its
+ * value at the call and relaxed plainly (up to max_steps), and that is the result.
+ * Without a proposal (applications = 0) it is the plain run alone.  Synchronises the
+ * stream (every residual check). */
+typedef struct {
+    const float* proposal;          /* MLP parameters, float32 [SPH_MLP_NPARAM] on the device; may be NULL
+                                       when applications = 0 */
+    double target;                  /* Laguerre-Gauss residual to reach */
+    int32_t max_steps;              /* cap on plain steps (of each run: learned, and fallback) */
+    int32_t check_every;            /* plain steps between residual checks, >= 1 */
+    int32_t applications;           /* proposal applications, >= 0 */
+    int32_t plain_between;          /* plain steps after each kept proposal, >= 0 */
+} sph_relax_run_params;
+typedef struct {
+    int32_t steps;                  /* plain steps of the run whose result is returned */
+    int32_t proposals_kept;         /* proposals that lowered the residual */
+    int32_t proposals_rejected;     /* proposals undone */
+    int32_t reached;                /* 1 when the final residual is <= target */
+    int32_t fell_back;              /* 1 when the result is the plain fallback run */
+    int32_t steps_before_fallback;  /* plain steps of the abandoned learned run */
+    double residual[3];             /* final sph_relax_residual output */
+} sph_relax_run_result;
+int sph_relax_run(sph_ctx* ctx, const sph_relax_params* prm, double* pos, const double* vol,
+                  const sph_relax_run_params* rp, sph_relax_run_result* result_host, void* stream);
 
 #ifdef __cplusplus
 }

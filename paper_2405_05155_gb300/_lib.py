@@ -72,6 +72,16 @@ class RelaxParams(ctypes.Structure):
                 ("spheres", c_dbl * (4 * SPH_MAX_SPHERES))]
 
 
+class RelaxRunParams(ctypes.Structure):
+    _fields_ = [("proposal", c_vp), ("target", c_dbl), ("max_steps", c_i32), ("check_every", c_i32),
+                ("applications", c_i32), ("plain_between", c_i32)]
+
+
+class RelaxRunResult(ctypes.Structure):
+    _fields_ = [("steps", c_i32), ("proposals_kept", c_i32), ("proposals_rejected", c_i32), ("reached", c_i32),
+                ("fell_back", c_i32), ("steps_before_fallback", c_i32), ("residual", c_dbl * 3)]
+
+
 class CompressibleParams(ctypes.Structure):
     _fields_ = [("dom", SphDomain), ("dt", c_dbl), ("gamma", c_dbl), ("eta", c_dbl), ("precision", c_i32),
                 ("reserved", c_i32)]
@@ -102,6 +112,7 @@ _SIGNATURES = {
                                c_vp]),
     "sph_eulerian_pack": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), c_vp]),
     "sph_eulerian_unpack": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), c_vp]),
+    "sph_eulerian_density_from_pressure": (ctypes.c_int, [c_vp, _P(EulerianParams), c_vp, c_vp, c_vp]),
     "sph_eulerian_rates": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), c_vp, c_vp, c_vp]),
     "sph_eulerian_step": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), ctypes.c_int, c_vp]),
     "sph_tlsph_pack": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp]),
@@ -121,6 +132,12 @@ _SIGNATURES = {
     "sph_mlp_train_step": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_vp, c_vp, c_i64, _P(c_dbl),
                                           c_vp]),
     "sph_relax_propose": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, c_vp]),
+    "sph_relax_samples": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, ctypes.c_int, ctypes.c_int, c_vp, c_vp,
+                                         c_vp]),
+    "sph_mlp_train": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_vp, c_vp, c_i64, c_i64, ctypes.c_int,
+                                     ctypes.c_uint64, _P(c_dbl), c_vp]),
+    "sph_relax_run": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, _P(RelaxRunParams), _P(RelaxRunResult),
+                                     c_vp]),
     "sph_eulerian_plan_bytes": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), _P(c_i64), c_vp]),
     "sph_eulerian_plan": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), c_vp]),
     "sph_tlsph_plan_bytes": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), _P(c_i64), c_vp]),
@@ -139,6 +156,7 @@ _SIGNATURES = {
     "sph_host_alloc": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp)]),
     "sph_host_free": (ctypes.c_int, [c_vp]),
     "sph_set_tile_pipeline": (ctypes.c_int, [c_vp, ctypes.c_int]),
+    "sph_set_wait_test": (ctypes.c_int, [c_vp, ctypes.c_uint32]),
     "sph_autotune_eulerian": (ctypes.c_int, [c_vp, _P(EulerianParams), _P(EulerianState), ctypes.c_int,
                                              _P(ctypes.c_int), _P(c_dbl), c_vp]),
     "sph_autotune_tlsph": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), ctypes.c_int, _P(ctypes.c_int),

@@ -83,6 +83,11 @@ class Context:
         _PERSISTENT or _BULK."""
         L.check("sph_set_tile_pipeline", self.lib.sph_set_tile_pipeline(self.h, int(mode)), self.h)
 
+    def set_wait_test(self, polls):
+        """Failure-detection test: polls > 0 makes the bounded waits of the bulk-copy
+        deformation pass run out (no copy issued); 0 restores normal operation."""
+        L.check("sph_set_wait_test", self.lib.sph_set_wait_test(self.h, int(polls)), self.h)
+
     def set_stage_cap(self, cap):
         L.check("sph_set_stage_cap", self.lib.sph_set_stage_cap(self.h, int(cap)), self.h)
 
@@ -126,6 +131,7 @@ class HostArray:
     def __init__(self, shape, dtype=torch.float64):
         import numpy as np
         self._lib = L.load()
+        self.dtype = dtype
         self.shape = tuple(int(x) for x in shape)
         count = 1
         for x in self.shape:
@@ -211,6 +217,20 @@ def kgc(ctx, dom, pos, vol, row_ptr, col, kernel=SPH_WENDLAND_C2):
     L.check("sph_kgc", ctx.lib.sph_kgc(ctx.h, ctypes.byref(d), kernel, _p(pos), _p(vol), _p(row_ptr), _p(col),
                                         _p(B), _p(fb), ctypes.byref(nfb), _stream()), ctx.h)
     return B, fb, nfb.value
+
+
+def density_from_pressure(ctx, dom, c0, p):
+    """drho = p / c0^2 on the device (the EOS of Sec. 3.1.1 inverted,
+    sph_eulerian_density_from_pressure), for initial conditions given as pressure."""
+    p = _dev_f64(p, ctx.device).contiguous()
+    n = p.numel()
+    prm = L.EulerianParams()
+    prm.dom = make_domain(dom, n)
+    prm.c0 = c0
+    drho = torch.empty_like(p)
+    L.check("sph_eulerian_density_from_pressure",
+            ctx.lib.sph_eulerian_density_from_pressure(ctx.h, ctypes.byref(prm), _p(p), _p(drho), _stream()), ctx.h)
+    return drho
 
 
 class Eulerian:
@@ -388,13 +408,27 @@ class TLSolid:
     def unpack(self):
         self._call("sph_tlsph_unpack", _stream())
 
+    def _check32(self, u, v, H):
+        # the C side reads raw float32 arrays: refuse anything else before passing pointers
+        d, n = self.dim, self.n
+        for name, a, shape in (("u", u, (d, n)), ("v", v, (d, n)), ("H", H, (d * d, n))):
+            if isinstance(a, HostArray):
+                ok = a.dtype == torch.float32 and a.shape == shape
+            else:
+                ok = (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float32
+                      and tuple(a.shape) == shape and a.is_contiguous())
+            if not ok:
+                raise ValueError("%s must be a contiguous float32 CUDA tensor or HostArray of shape %s" % (name, shape))
+
     def load32(self, u, v, H):
         """Replace the float32 form's state with u = x - r0, v, H = F - I (float32 device
         tensors or mapped HostArray buffers of shapes [dim][n], [dim][n], [dim*dim][n])."""
+        self._check32(u, v, H)
         self._call("sph_tlsph_load32", _ptr(u), _ptr(v), _ptr(H), _stream())
 
     def store32(self, u, v, H):
         """Copy the float32 form's state (u = x - r0, v, H = F - I) out, as load32 takes it."""
+        self._check32(u, v, H)
         self._call("sph_tlsph_store32", _ptr(u), _ptr(v), _ptr(H), _stream())
 
     def step(self, nsteps=1):
@@ -508,6 +542,17 @@ class MLPTrainer:
         self.step_count = 0
         self.lr = lr
 
+    def train(self, feats, targets, nsteps, batch=4096, seed=0, with_loss=True):
+        """nsteps Adam steps on minibatches drawn on the device from (feats, targets)
+        (sph_mlp_train); returns the last step's loss (nan without with_loss)."""
+        loss = ctypes.c_double(float("nan"))
+        L.check("sph_mlp_train", self.ctx.lib.sph_mlp_train(
+            self.ctx.h, _p(self.params), _p(self.m), _p(self.v), self.step_count + 1, float(self.lr), _p(feats),
+            _p(targets), feats.shape[0], int(batch), int(nsteps), int(seed) & 0xFFFFFFFFFFFFFFFF,
+            ctypes.byref(loss) if with_loss else None, _stream()), self.ctx.h)
+        self.step_count += int(nsteps)
+        return loss.value
+
     def step(self, feats, target, with_loss=False):
         self.step_count += 1
         loss = ctypes.c_double(float("nan"))
@@ -515,6 +560,39 @@ class MLPTrainer:
             self.ctx.h, _p(self.params), _p(self.m), _p(self.v), self.step_count, float(self.lr), _p(feats),
             _p(target), feats.shape[0], ctypes.byref(loss) if with_loss else None, _stream()), self.ctx.h)
         return loss.value
+
+
+def relax_samples(ctx, prm, pos, vol, snapshots, every):
+    """Plain-trajectory training samples (sph_relax_samples): features [snapshots n, 128]
+    and targets (x^{t+every} - x^t)/h [snapshots n, 3], float32; pos is advanced in place."""
+    n = pos.shape[1]
+    prm.dom.n = n
+    feats = torch.empty((snapshots * n, 128), dtype=torch.float32, device=pos.device)
+    targets = torch.empty((snapshots * n, 3), dtype=torch.float32, device=pos.device)
+    L.check("sph_relax_samples", ctx.lib.sph_relax_samples(ctx.h, ctypes.byref(prm), _p(pos), _p(vol),
+                                                            int(snapshots), int(every), _p(feats), _p(targets),
+                                                            _stream()), ctx.h)
+    return feats, targets
+
+
+def relax_run(ctx, prm, pos, vol, target, max_steps, proposal=None, applications=3, plain_between=10,
+              check_every=10):
+    """Relaxation of pos (in place) to the residual target (sph_relax_run): with a proposal,
+    judged by the residual, plain relaxation finishing the run and as the fallback.
+    Returns the sph_relax_run_result fields as a dict."""
+    prm.dom.n = pos.shape[1]
+    rp = L.RelaxRunParams()
+    rp.proposal = _p(proposal) if proposal is not None else None
+    rp.target = float(target)
+    rp.max_steps, rp.check_every = int(max_steps), int(check_every)
+    rp.applications = int(applications) if proposal is not None else 0
+    rp.plain_between = int(plain_between)
+    out = L.RelaxRunResult()
+    L.check("sph_relax_run", ctx.lib.sph_relax_run(ctx.h, ctypes.byref(prm), _p(pos), _p(vol), ctypes.byref(rp),
+                                                    ctypes.byref(out), _stream()), ctx.h)
+    return {"steps": out.steps, "kept": out.proposals_kept, "rejected": out.proposals_rejected,
+            "reached": bool(out.reached), "fell_back": bool(out.fell_back),
+            "steps_before_fallback": out.steps_before_fallback, "residual": list(out.residual)}
 
 
 def relax_propose(ctx, prm, params, pos):

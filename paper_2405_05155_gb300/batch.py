@@ -30,7 +30,7 @@ class EulerianBatch:
             vol = torch.tensor(case["vol"][oh], dtype=torch.float64, device=dev)
             rp, col = api.build_neighbors(ctx, d, pos)
             B, _, _ = api.kgc(ctx, d, pos, vol, rp, col)
-            drho = case["p"][oh] / case["c0"] ** 2
+            drho = api.density_from_pressure(ctx, d, case["c0"], torch.tensor(case["p"], device=dev)[order])
             sim = api.Eulerian(ctx, d, pos, vol, B, rp, col, drho, case["v"][:, oh], case["dt"], case["rho0"],
                                case["c0"], case["mu"], precision=api.SPH_FP32_KAHAN, integrator=integrator,
                                tiles=tiles)

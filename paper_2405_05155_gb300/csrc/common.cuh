@@ -45,6 +45,7 @@ struct sph_ctx {
     int stage_cap = 0;             // most neighbour records a tile stages in shared memory (0: default)
     int tile_pipe = SPH_PIPE_GEOM;   // planned TL passes: how pair entries reach a block (SPH_PIPE_*)
     bool waits_pending = false;    // a kernel with bounded waits ran since the timeout flag was read
+    uint32_t wait_test_polls = 0;  // failure-detection test: bounded waits on a phase nothing completes
     double relax_skin = 0.2;       // float32 relaxation: list skin / h (0: a cell sweep every step)
     // batched Eulerian step: launch shape, captured graph and the case table it was made for
     int batch_block = 256;
@@ -58,7 +59,8 @@ struct sph_ctx {
 enum ScratchSlot {
     S_CELL_ID = 0, S_CELL_COUNT, S_CELL_START, S_CELL_FILL, S_SORTED, S_P32SORTED,
     S_ROW_LEN, S_SCAN_BLOCKS, S_ABSMAX, S_RELAX_ROWPTR, S_RELAX_COL, S_RELAX_ACC,
-    S_RELAX_AMAX, S_RED_PARTIAL, S_KGC_COUNT, S_MISC0, S_MISC1, S_MISC2, S_MISC3, S_BATCH, S_MLP_PARTS
+    S_RELAX_AMAX, S_RED_PARTIAL, S_KGC_COUNT, S_MISC0, S_MISC1, S_MISC2, S_MISC3, S_BATCH, S_MLP_PARTS,
+    S_LEARN0, S_LEARN1, S_LEARN2
 };
 
 // device status words

@@ -84,6 +84,12 @@ extern "C" int sph_set_tile_pipeline(sph_ctx* ctx, int mode) {
     return SPH_OK;
 }
 
+extern "C" int sph_set_wait_test(sph_ctx* ctx, uint32_t polls) {
+    if (!ctx || polls > (1u << 16)) return SPH_ERR_ARG;
+    ctx->wait_test_polls = polls;
+    return SPH_OK;
+}
+
 // Reads and clears the device timeout flag (synchronises the stream).
 int sph_take_timeout(sph_ctx* ctx, cudaStream_t s) {
     int* h = (int*)ctx->pinned;

@@ -480,6 +480,26 @@ extern "C" int sph_eulerian_unpack(sph_ctx* ctx, const sph_eulerian_params* p, c
     return SPH_OK;
 }
 
+// Weakly-compressible EOS of Sec. 3.1.1, p = c0^2 (rho - rho0), solved for the stored
+// density offset: drho = p / c0^2.
+__global__ void k_eos_drho(const double* __restrict__ pr, int64_t n, double c2, double* __restrict__ drho) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) drho[i] = pr[i] / c2;
+}
+
+extern "C" int sph_eulerian_density_from_pressure(sph_ctx* ctx, const sph_eulerian_params* p, const double* pr,
+                                                  double* drho, void* stream) {
+    if (!ctx || !p) return SPH_ERR_ARG;
+    int64_t n = p->dom.n;
+    if (n < 0 || !(p->c0 > 0.0) || !isfinite(p->c0)) return SPH_ERR_ARG;
+    if (n == 0) return SPH_OK;
+    if (!pr || !drho) return SPH_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    k_eos_drho<<<grid_for(n, 256), 256, 0, s>>>(pr, n, p->c0 * p->c0, drho);
+    SPH_LAUNCH_CHECK(ctx);
+    return SPH_OK;
+}
+
 extern "C" int sph_eulerian_rates(sph_ctx* ctx, const sph_eulerian_params* p, const sph_eulerian_state* st,
                                   double* drho_dt, double* dmom_dt, void* stream) {
     if (!ctx) return SPH_ERR_ARG;

@@ -13,7 +13,6 @@
 // pair loops use) the visit order already yields ascending j; otherwise a row is
 // sorted in place.
 #include <math.h>
-#include <mutex>
 #include "neighbors.cuh"
 
 using namespace nb;
@@ -407,21 +406,14 @@ static __device__ __align__(256) unsigned char g_neighbor_static_scratch[SPH_STA
 
 namespace {
 
-// Device address of the static array on the current device, looked up once per
-// device (host code cannot use the symbol itself as a device pointer).
-std::mutex g_static_mutex;
-void* g_static_addr[256] = {};
-
+// Device address of the static array on the current device.  Looked up on every call
+// (a host-side table lookup, no device work): an address cached across calls would go
+// stale if the device's primary context were reset and the module loaded elsewhere.
+// Host code cannot use the symbol itself as a device pointer.
 int static_scratch_address(unsigned char** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return SPH_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_neighbor_static_scratch) != cudaSuccess || !p) return SPH_ERR_CUDA;
-        g_static_addr[dev] = p;
-    }
-    *out = (unsigned char*)g_static_addr[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_neighbor_static_scratch) != cudaSuccess || !p) return SPH_ERR_CUDA;
+    *out = (unsigned char*)p;
     return SPH_OK;
 }
 
@@ -472,7 +464,7 @@ extern "C" int sph_build_neighbors_static(const sph_domain* dom, const double* p
             k_neighbors<3, false><<<grid_for(n, 128), 128, 0, s>>>(pos, n, g, g.rc2, lmax, absmax, start, p32, row_len,
                                                                   nullptr, nullptr, 0, flags);
     }
-    if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) return SPH_ERR_CUDA;
     st = sph_exclusive_scan_i64_buf(row_len, row_ptr, n, scan64, s);
     if (st) return st;
     int64_t nnz = 0;
@@ -492,5 +484,5 @@ extern "C" int sph_build_neighbors_static(const sph_domain* dom, const double* p
             k_neighbors<3, true><<<grid_for(n, 128), 128, 0, s>>>(pos, n, g, g.rc2, lmax, absmax, start, p32, nullptr,
                                                                  row_ptr, col, cap, flags);
     }
-    return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
 }

@@ -609,22 +609,31 @@ struct GeoArgs {
     const int32_t* tile_e;   // bulk form: entries per tile
     int ecap;                // bulk form: most entries a block copies into shared memory (0: none)
     const uint16_t* slots;   // geometry form: the entries' neighbour slots alone, same sliced order
+    const float4* wsum;      // geometry form of the momentum pass: (S_i, 0) per particle
+    uint32_t test_polls;     // bulk form: > 0 issues no copy and waits this many polls (sph_set_wait_test)
 };
 
 // The TL plan: the tile plan (tiles.cuh) with 16-byte entries, then the entries' slots
-// alone as a sliced uint16 section (read by the deformation pass that evaluates the pair
-// geometry from the staged records instead of reading the entries).
+// alone as a sliced uint16 section (read by the passes that evaluate the pair geometry
+// from the staged records instead of reading the entries), then per particle the float4
+// (S_i, 0) with S_i = sum_j grad0 W_ij V0_j, a fixed property of the reference
+// configuration that the geometry form of the momentum pass uses.
 static inline size_t tl_slot_offset(int64_t n, int64_t nnz, int64_t maxrow) {
     return tile_plan_bytes(n, nnz, maxrow);
 }
 
-static inline size_t tl_plan_total(int64_t n, int64_t nnz, int64_t maxrow) {
+static inline size_t tl_wsum_offset(int64_t n, int64_t nnz, int64_t maxrow) {
     const int64_t ntiles = (n + kTileRows - 1) / kTileRows;
     return tl_slot_offset(n, nnz, maxrow) + align16((size_t)ntiles * kTileRows * (size_t)maxrow * 2);
 }
 
+static inline size_t tl_plan_total(int64_t n, int64_t nnz, int64_t maxrow) {
+    return tl_wsum_offset(n, nnz, maxrow) + align16((size_t)n * 16);
+}
+
 // Pair entries of the tile plan: w = grad0 W_ij V0_j in float64, stored float32,
-// with the neighbour's slot, each row's pairs in the bank-aware order (bank_order).
+// with the neighbour's slot, each row's pairs in the bank-aware order (bank_order);
+// and the row's S_i = sum_j w_ij, summed in float64 in list order, stored float32.
 template <int DIM>
 __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__ r0, const double* __restrict__ V0,
                                                       const int64_t* __restrict__ row_ptr,
@@ -632,7 +641,8 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
                                                       const uint16_t* __restrict__ lcol,
                                                       const int32_t* __restrict__ tile_e,
                                                       const int64_t* __restrict__ tile_so, int64_t n, TLK<double> K,
-                                                      float4* __restrict__ geo, uint16_t* __restrict__ slots) {
+                                                      float4* __restrict__ geo, uint16_t* __restrict__ slots,
+                                                      float4* __restrict__ wsum) {
     const int64_t tile = blockIdx.x;
     const int64_t i = tile * kTileRows + threadIdx.x;
     const bool active = i < n;
@@ -662,6 +672,17 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
         out[(int64_t)k * kTileRows] = e;
         slots[tile_so[tile] + threadIdx.x + (int64_t)k * kTileRows] = (uint16_t)__float_as_int(e.w);
     }
+    if (!active) return;
+    double S[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < len; ++k) {
+        int j = col[b + k];
+        double r[DIM], d2;
+        pair_r64<DIM>(xi, r0, n, j, K, r, d2);
+        double gv = wendland_gs<double>(sqrt(d2) * K.inv_h, K.coef) * V0[j];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) S[a] += gv * r[a];
+    }
+    wsum[i] = make_float4((float)S[0], (float)S[1], (float)S[2], 0.0f);
 }
 
 // Stage chunks FIRST..FIRST+NPL-1 of the tile's distinct neighbours' records (record
@@ -799,6 +820,225 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32g(const float* __restr
     for (int a = 0; a < DIM; ++a) vrec[a] = fx ? 0.0f : vown[a] + K.dt * (tot[a] * K.inv_rho0);
 }
 
+// Geometry form of the momentum pass (Eq. 30), boxes without periodic axes.  Eq. 30's
+// sum is taken in its two halves,
+//   a_i = (1/rho0) (M_i S_i + sum_j (V0_j M_j) g_ij),   g_ij = (dW/dr / r)(r_ij) r_ij,
+// with S_i = sum_j g_ij V0_j fixed by the reference configuration (computed in float64
+// with the plan, k_tl_geo), so a pair needs the neighbour's position and V0_j M_j only and
+// evaluates its kernel gradient from them instead of streaming a 16-byte factor.  The block
+// stages, per distinct neighbour of its tile, the position relative to the cell of the
+// tile's first row and V0_j M_j (mom_stage: 3D three float4 planes, 2D a float4 and a
+// float2 plane), and copies the tile's slot block into shared memory while it stages, so
+// the pair loop reads shared memory only.  The own row's M_i, S_i and velocity are read
+// after the loop, to keep the registers live through it few.
+template <int DIM>
+__device__ __forceinline__ void mom_stage_rec(const F8& a, const F8& b, uint32_t bref, const TLK<float>& K, float4& p0,
+                                              float4& p1, float4& p2) {
+    if (DIM == 3) {
+        // record (ox, oy, oz, cell, M00, M10, M20, V0 | M01, M11, M21, 0, M02, M12, M22, 0)
+        float x[3];
+        rel_to_ref<3>(a.v, __float_as_uint(a.v[3]), bref, K, x);
+        const float V = a.v[7];
+        p0 = make_float4(x[0], x[1], x[2], V * b.v[6]);                     // x, y, z, VM22
+        p1 = make_float4(V * a.v[4], V * a.v[5], V * b.v[0], V * b.v[1]);   // VM00, VM10, VM01, VM11
+        p2 = make_float4(V * b.v[4], V * b.v[5], V * a.v[6], V * b.v[2]);   // VM02, VM12, VM20, VM21
+    } else {
+        // record (ox, oy, cell, V0, M00, M10, M01, M11)
+        float x[2];
+        rel_to_ref<2>(a.v, __float_as_uint(a.v[2]), bref, K, x);
+        const float V = a.v[3];
+        p0 = make_float4(x[0], x[1], V * a.v[4], V * a.v[5]);               // x, y, VM00, VM10
+        p1 = make_float4(V * a.v[6], V * a.v[7], 0.0f, 0.0f);               // VM01, VM11
+        p2 = p1;
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ void mom_stage(const float* __restrict__ RM, int64_t j, uint32_t bref,
+                                          const TLK<float>& K, float4& p0, float4& p1, float4& p2) {
+    constexpr int W = DIM == 3 ? 16 : 8;
+    const F8 a = ldg8(RM + W * j);
+    const F8 b = DIM == 3 ? ldg8(RM + W * j + 8) : a;
+    mom_stage_rec<DIM>(a, b, bref, K, p0, p1, p2);
+}
+
+// One pair of the geometry form: accumulates (V0_j M_j) g_ij, rows 0-1 paired and row 2 alone.
+template <int DIM>
+__device__ __forceinline__ void mom_pair_rel(float4 p0, float4 p1, float4 p2, const float* xi, const TLK<float>& K,
+                                             Kahan2& acc01, Kahan<float>& acc2) {
+    float r[DIM];
+    r[0] = xi[0] - p0.x;
+    r[1] = xi[1] - p0.y;
+    if (DIM == 3) r[DIM - 1] = xi[DIM - 1] - p0.z;
+    float d2 = r[0] * r[0];
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) d2 = fmaf(r[a], r[a], d2);
+    const float gs = gs_from_d2(d2, K);
+    const float g0 = gs * r[0], g1 = gs * r[1];
+    if (DIM == 2) {
+        acc01.add(__ffma2_rn(make_float2(p1.x, p1.y), make_float2(g1, g1),
+                             __fmul2_rn(make_float2(p0.z, p0.w), make_float2(g0, g0))));
+    } else {
+        const float g2 = gs * r[DIM - 1];
+        const float2 t01 = __ffma2_rn(make_float2(p2.x, p2.y), make_float2(g2, g2),
+                                      __ffma2_rn(make_float2(p1.z, p1.w), make_float2(g1, g1),
+                                                 __fmul2_rn(make_float2(p1.x, p1.y), make_float2(g0, g0))));
+        acc01.add(t01);
+        acc2.add(fmaf(p0.w, g2, fmaf(p2.w, g1, p2.z * g0)));
+    }
+}
+
+template <int DIM, int OUT>
+__global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restrict__ RM, float* __restrict__ RD,
+                                                            const int64_t* __restrict__ row_ptr, int64_t n,
+                                                            TLK<float> K, GeoArgs A, double* __restrict__ dvdt) {
+    constexpr int W = DIM == 3 ? 16 : 8;
+    extern __shared__ __align__(16) unsigned char tl_smem[];
+    const int mc = A.mcap;
+    float4* P0s = reinterpret_cast<float4*>(tl_smem);
+    float4* P1s = P0s + mc;
+    float4* P2s = P1s + mc;                                   // 3D
+    float2* P1h = reinterpret_cast<float2*>(P0s + mc);        // 2D
+    uint16_t* ssl = reinterpret_cast<uint16_t*>(
+        tl_smem + (DIM == 3 ? 48u * (unsigned)mc : 16u * (unsigned)mc + ((8u * (unsigned)mc + 15u) & ~15u)));
+    // tiles in reverse: the deformation pass walks them forwards, so each pass starts on
+    // the records the previous one touched last, still in L2
+    const int64_t tile = gridDim.x - 1 - blockIdx.x;
+    const int64_t i0 = tile * kTileRows;
+    const int64_t i = i0 + threadIdx.x;
+    const bool active = i < n;
+    const int64_t ii = active ? i : i0;
+    const int64_t P0 = row_ptr[i0];
+    const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
+    const int m = A.tile_m[tile];
+    const uint32_t bref = __float_as_uint(RM[W * i0 + DIM]);
+    // the tile's slot block (256 bytes per position) into shared memory, when the plan's
+    // longest row allows (A.ecap positions)
+    const int width = A.tile_e[tile] / kTileRows;
+    const bool sslot = width <= A.ecap;
+    if (sslot) {
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(A.slots + A.tile_so[tile]);
+        const int chunks = width * (2 * kTileRows / 16);
+        for (int c = threadIdx.x; c < chunks; c += blockDim.x)
+            cp_async16(reinterpret_cast<unsigned char*>(ssl) + 16 * c, src + 16 * c);
+        cp_async_commit();
+    }
+    const bool staged = m <= mc;
+    // the own record and S_i are requested first: their latency overlaps the staging
+    const F8 a0 = ldg8(RM + W * ii);
+    const F8 a1 = DIM == 3 ? ldg8(RM + W * ii + 8) : a0;
+    const float4 S = A.wsum[ii];
+    if (staged) {
+        // up to four neighbours per thread per round: their indices first, then their
+        // records two at a time, so that few round trips to memory are in series
+        for (int q0 = 0; q0 < m; q0 += 4 * kTileRows) {
+            int64_t jq[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int q = q0 + k * kTileRows + (int)threadIdx.x;
+                // a plan out of date with the lists reads wrong but in-bounds records
+                jq[k] = q < m ? min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1) : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k += 2) {
+                F8 ra[2], rb[2];
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int64_t j = jq[k + t] < 0 ? 0 : jq[k + t];
+                    ra[t] = ldg8(RM + W * j);
+                    rb[t] = DIM == 3 ? ldg8(RM + W * j + 8) : ra[t];
+                }
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    if (jq[k + t] < 0) continue;
+                    const int q = q0 + (k + t) * kTileRows + (int)threadIdx.x;
+                    float4 p0, p1, p2;
+                    mom_stage_rec<DIM>(ra[t], rb[t], bref, K, p0, p1, p2);
+                    P0s[q] = p0;
+                    if (DIM == 3) {
+                        P1s[q] = p1;
+                        P2s[q] = p2;
+                    } else {
+                        P1h[q] = make_float2(p1.x, p1.y);
+                    }
+                }
+            }
+        }
+    }
+    if (sslot) cp_async_wait_all();
+    __syncthreads();
+    // M_i S_i is the sums' first term, so M_i is not kept through the loop
+    float xi[3] = {0.0f, 0.0f, 0.0f};
+    Kahan2 acc01;
+    Kahan<float> acc2;
+    acc01.init();
+    acc2.init();
+    uint32_t bi;
+    {
+        bi = __float_as_uint(a0.v[DIM]);
+        rel_to_ref<DIM>(a0.v, bi, bref, K, xi);
+        float2 mi01[DIM];
+        float mi2[3] = {0.0f, 0.0f, 0.0f};
+        own_M<DIM>(a0, a1, mi01, mi2);
+        if (DIM == 2) {
+            acc01.add(__ffma2_rn(mi01[1], make_float2(S.y, S.y), __fmul2_rn(mi01[0], make_float2(S.x, S.x))));
+        } else {
+            acc01.add(__ffma2_rn(mi01[DIM - 1], make_float2(S.z, S.z),
+                                 __ffma2_rn(mi01[1], make_float2(S.y, S.y), __fmul2_rn(mi01[0], make_float2(S.x, S.x)))));
+            acc2.add(fmaf(mi2[2], S.z, fmaf(mi2[1], S.y, mi2[0] * S.x)));
+        }
+    }
+    const int mlast = max(m - 1, 0);
+    const uint16_t* gsl = A.slots + A.tile_so[tile] + threadIdx.x;
+    if (staged && sslot) {
+        const uint16_t* sl = ssl + threadIdx.x;
+#pragma unroll 4
+        for (int k = 0; k < len; ++k) {
+            const int s = min((int)sl[k * kTileRows], mlast);
+            if (DIM == 3) mom_pair_rel<3>(P0s[s], P1s[s], P2s[s], xi, K, acc01, acc2);
+            else {
+                const float2 h = P1h[s];
+                mom_pair_rel<DIM>(P0s[s], make_float4(h.x, h.y, 0.0f, 0.0f), P0s[s], xi, K, acc01, acc2);
+            }
+        }
+    } else if (staged) {
+#pragma unroll 4
+        for (int k = 0; k < len; ++k) {
+            const int s = min((int)__ldg(gsl + (int64_t)k * kTileRows), mlast);
+            if (DIM == 3) mom_pair_rel<3>(P0s[s], P1s[s], P2s[s], xi, K, acc01, acc2);
+            else {
+                const float2 h = P1h[s];
+                mom_pair_rel<DIM>(P0s[s], make_float4(h.x, h.y, 0.0f, 0.0f), P0s[s], xi, K, acc01, acc2);
+            }
+        }
+    } else {
+        for (int k = 0; k < len; ++k) {
+            const int s = min(sslot ? (int)ssl[threadIdx.x + k * kTileRows] : (int)__ldg(gsl + (int64_t)k * kTileRows),
+                              mlast);
+            const int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
+            float4 p0, p1, p2;
+            mom_stage<DIM>(RM, j, bref, K, p0, p1, p2);
+            mom_pair_rel<DIM>(p0, p1, p2, xi, K, acc01, acc2);
+        }
+    }
+    if (!active) return;
+    const float2 v01 = acc01.value();
+    const float tot[3] = {v01.x, v01.y, DIM == 3 ? acc2.value() : 0.0f};
+    if (OUT == OUT_RATES) {
+        for (int a = 0; a < DIM; ++a) dvdt[a * n + i] = (double)(tot[a] * K.inv_rho0);
+        return;
+    }
+    // the velocity quarter of the RD record, (vx, vy, vz, V0) in 3D and (vx, vy, 0, 0) in
+    // 2D, read and written as one float4
+    const bool fx = (bi & kFixedBit) != 0;
+    float4* vrec = reinterpret_cast<float4*>(RD + 8 * i + 4);
+    float4 vv = *vrec;
+    float* vp = reinterpret_cast<float*>(&vv);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) vp[a] = fx ? 0.0f : vp[a] + K.dt * (tot[a] * K.inv_rho0);
+    *vrec = vv;
+}
+
 // BULK: thread 0 copies the tile's whole entry block into shared memory with one
 // TMA bulk copy (completion on an mbarrier, bounded wait) while the block stages
 // the neighbours, so each block has its entire entry stream in flight at once;
@@ -823,10 +1063,13 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
     uint64_t* bar = reinterpret_cast<uint64_t*>(eb + A.ecap);
     const int te = BULK ? A.tile_e[tile] : 0;
     const bool bulk = BULK && te > 0 && te <= A.ecap;
+    // A.test_polls > 0 (failure-detection test): no copy is issued, so the bounded wait
+    // below runs out on a phase nothing completes and the block leaves with nothing in flight
+    const bool test_wait = BULK && A.test_polls > 0;
     if (BULK && threadIdx.x == 0) {
         mbar_init(bar, 1);
         mbar_fence_init();
-        if (bulk) {
+        if (bulk && !test_wait) {
             mbar_arrive_expect_tx(bar, (uint32_t)te * 16u);
             tma_load_1d(eb, A.geo + A.tile_so[tile], (uint32_t)te * 16u, bar);
         }
@@ -869,13 +1112,30 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
     if (REL) {
         staged = m <= A.mcap;
         if (staged) {
-            for (int q = threadIdx.x; q < m; q += blockDim.x) {
-                const int64_t j = min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1);
-                const F8 rj = ldg8(RD + 8 * j);
-                float x[3] = {0.0f, 0.0f, 0.0f};
-                rel_to_ref<DIM>(rj.v, __float_as_uint(rj.v[DIM]), bref, K, x);
-                sp[q] = make_float4(x[0], x[1], x[2], DIM == 3 ? rj.v[7] : rj.v[3]);
-                sp[A.mcap + q] = hi4(rj);
+            // up to four neighbours per thread per round: their indices first, then their
+            // records two at a time, so that few round trips to memory are in series
+            for (int q0 = 0; q0 < m; q0 += 4 * kTileRows) {
+                int64_t jq[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int q = q0 + k * kTileRows + (int)threadIdx.x;
+                    jq[k] = q < m ? min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1) : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k += 2) {
+                    F8 rr[2];
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) rr[t] = ldg8(RD + 8 * (jq[k + t] < 0 ? 0 : jq[k + t]));
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        if (jq[k + t] < 0) continue;
+                        const int q = q0 + (k + t) * kTileRows + (int)threadIdx.x;
+                        float x[3] = {0.0f, 0.0f, 0.0f};
+                        rel_to_ref<DIM>(rr[t].v, __float_as_uint(rr[t].v[DIM]), bref, K, x);
+                        sp[q] = make_float4(x[0], x[1], x[2], DIM == 3 ? rr[t].v[7] : rr[t].v[3]);
+                        sp[A.mcap + q] = hi4(rr[t]);
+                    }
+                }
             }
         }
         if (sslot) cp_async_wait_all();
@@ -884,10 +1144,10 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
         staged = GEOM ? stage_neighbours<2, 8, 0>(RD, n, P0, m, A, sp) : stage_neighbours<1, 8>(RD, n, P0, m, A, sp);
     }
     if (bulk) {
-        const bool late = !mbar_wait_bounded(bar, 0, kWaitPolls);
+        const bool late = !mbar_wait_bounded(bar, 0, test_wait ? A.test_polls : kWaitPolls);
         if (__syncthreads_or(late)) {      // block-uniform: the copy never completed
             if (threadIdx.x == 0) atomicExch(&flags[FLAG_TIMEOUT], 1);
-            mbar_wait_bounded(bar, 0, kWaitPolls);
+            if (!test_wait) mbar_wait_bounded(bar, 0, kWaitPolls);    // a copy issued is waited for
             return;
         }
     }
@@ -1442,10 +1702,10 @@ __global__ void __launch_bounds__(kTileRows, 1) k_tl_defo32p(const float* __rest
 
 // The state's tile plan as launch arguments (tile_m == nullptr: no plan).
 struct TlPlan {
-    GeoArgs mom, defo;
+    GeoArgs mom, defo, momr;
     PipeArgs pmom, pdefo;
-    size_t mom_bytes, defo_bytes, pmom_bytes, pdefo_bytes;
-    bool on, pipe_mom, pipe_defo, bulk_defo, geom_defo;
+    size_t mom_bytes, defo_bytes, pmom_bytes, pdefo_bytes, momr_bytes;
+    bool on, pipe_mom, pipe_defo, bulk_defo, geom_defo, geom_mom;
     int grid;
 };
 
@@ -1454,8 +1714,9 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
     t.on = st->plan && st->plan_nnz > 0 && st->plan_maxm > 0;
     t.mom = GeoArgs{nullptr, nullptr, nullptr, nullptr, 0};
     t.defo = t.mom;
-    t.mom_bytes = t.defo_bytes = t.pmom_bytes = t.pdefo_bytes = 0;
-    t.pipe_mom = t.pipe_defo = t.bulk_defo = t.geom_defo = false;
+    t.momr = t.mom;
+    t.mom_bytes = t.defo_bytes = t.pmom_bytes = t.pdefo_bytes = t.momr_bytes = 0;
+    t.pipe_mom = t.pipe_defo = t.bulk_defo = t.geom_defo = t.geom_mom = false;
     t.grid = 0;
     if (!t.on) return t;
     TilePlan tp = tile_plan_view(st->plan, n, st->plan_nnz);
@@ -1486,6 +1747,7 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
         t.defo.ecap = (int)std::max<int64_t>(0, std::min(room, want));
         t.bulk_defo = t.defo.ecap > 0;
         t.defo_bytes = (size_t)(md + t.defo.ecap) * 16 + 16;
+        t.defo.test_polls = ctx->wait_test_polls;
     }
     // geometry form of the deformation pass: both record halves staged, the slot section
     t.geom_defo = ctx->tile_pipe == SPH_PIPE_GEOM &&
@@ -1499,6 +1761,16 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
         t.defo.tile_e = tp.tile_e;
         t.defo.ecap = st->plan_maxrow <= 128 ? (int)st->plan_maxrow : 0;
         t.defo_bytes = (size_t)mg * 32 + (size_t)t.defo.ecap * kTileRows * 2;
+        // the momentum pass's geometry form (used on boxes without periodic axes): position
+        // and V0_j M_j staged, 48 bytes per neighbour in 3D (24 in 2D), the slot block, S_i
+        t.geom_mom = true;
+        const int mr = stage_mcap(st->plan_maxm, dim == 3 ? 3 : 2, ctx->stage_cap);
+        t.momr = t.defo;
+        t.momr.mcap = mr;
+        t.momr.wsum = reinterpret_cast<const float4*>(reinterpret_cast<const unsigned char*>(st->plan) +
+                                                      tl_wsum_offset(n, st->plan_nnz, st->plan_maxrow));
+        t.momr_bytes = (dim == 3 ? (size_t)mr * 48 : (size_t)mr * 16 + align16((size_t)mr * 8)) +
+                       (size_t)t.momr.ecap * kTileRows * 2;
     }
     int64_t g = ctx->num_sms > 0 ? ctx->num_sms : 1;
     t.grid = (int)(g < tp.ntiles ? g : tp.ntiles);
@@ -1536,6 +1808,11 @@ void tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph
             sph_allow_dynamic_smem((const void*)f);
             f<<<gp, b, tp.pmom_bytes, s>>>(st->rm, st->rd, st->row_ptr, n, K, tp.mom, tp.pmom,
                                            out == OUT_RATES ? r1 : nullptr, ctx->flags);
+        } else if (tp.geom_mom && !K.periodic) {
+            auto* f = out == OUT_RATES ? k_tl_mom32r<DIM, OUT_RATES> : k_tl_mom32r<DIM, OUT_STEP>;
+            sph_allow_dynamic_smem((const void*)f);
+            f<<<g, b, tp.momr_bytes, s>>>(st->rm, st->rd, st->row_ptr, n, K, tp.momr,
+                                          out == OUT_RATES ? r1 : nullptr);
         } else {
             auto* f = out == OUT_RATES ? k_tl_mom32g<DIM, OUT_RATES> : k_tl_mom32g<DIM, OUT_STEP>;
             sph_allow_dynamic_smem((const void*)f);
@@ -1638,14 +1915,16 @@ extern "C" int sph_tlsph_plan(sph_ctx* ctx, const sph_tlsph_params* p, sph_tlsph
     TilePlan tp = tile_plan_view(st->plan, n, nnz);
     uint16_t* slots = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(st->plan) +
                                                   tl_slot_offset(n, nnz, maxrow));
+    float4* wsum = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(st->plan) +
+                                             tl_wsum_offset(n, nnz, maxrow));
     TLK<double> K = make_tl_consts<double>(p);
     unsigned nt = (unsigned)tp.ntiles;
     if (p->dom.dim == 2)
         k_tl_geo<2><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_e, tp.tile_so,
-                                             n, K, tp.geo, slots);
+                                             n, K, tp.geo, slots, wsum);
     else
         k_tl_geo<3><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_e, tp.tile_so,
-                                             n, K, tp.geo, slots);
+                                             n, K, tp.geo, slots, wsum);
     SPH_LAUNCH_CHECK(ctx);
     SPH_CUDA(ctx, cudaStreamSynchronize(s));
     st->plan_nnz = nnz;

@@ -2,13 +2,14 @@
 GPU with libsph's own BF16 tensor-core forward/backward kernels and Adam, and the
 proposal-accelerated relaxation that always finishes with plain steps.
 
-Procedure (the benchmark configuration's learned variant):
-* data: for each seeded body, plain relaxation snapshots every ``every`` steps;
-  features at snapshot t, target (x^{t+every} - x^t) / h;
-* training: Adam on random minibatches (MSE);
-* use: ``applications`` times {proposal move, then ``plain_between`` plain steps},
-  then plain steps until the residual target is met (plain relaxation is the
-  fallback: if the target is missed by the step cap, the result is the plain run's).
+Every step runs in libsph (this module only marshals arguments):
+* data: sph_relax_samples -- for each seeded body, plain relaxation snapshots every
+  ``every`` steps; features at snapshot t, target (x^{t+every} - x^t) / h;
+* training: sph_mlp_train -- Adam on minibatches drawn and gathered on the device (MSE);
+* use: sph_relax_run -- up to ``applications`` proposal moves, each kept only if it lowers
+  the residual and followed by ``plain_between`` plain steps, then plain steps until the
+  residual target is met; if the target is missed by the step cap, plain relaxation from
+  the start is the fallback and gives the result.
 """
 import torch
 
@@ -16,6 +17,7 @@ from . import api, inputs
 
 
 def body_on_device(ctx, seed, dp, precision=api.SPH_FP32_KAHAN):
+    """A seeded 8-sphere body (inputs.sphere_body) in cell order on the device."""
     b = inputs.sphere_body(seed, dp)
     pos = torch.tensor(b["pos"], dtype=torch.float64, device=ctx.device)
     order = api.cell_order(ctx, b["domain"], pos)
@@ -28,63 +30,42 @@ def body_on_device(ctx, seed, dp, precision=api.SPH_FP32_KAHAN):
 def trajectory_samples(ctx, seed, dp, steps=500, every=50):
     """(features [m, 128], targets [m, 3]) float32 device tensors from one plain trajectory."""
     b, prm, pos, vol = body_on_device(ctx, seed, dp)
-    h = b["h"]
+    return api.relax_samples(ctx, prm, pos, vol, steps // every, every)
+
+
+def training_set(ctx, seeds, dp, steps=500, every=50):
+    """Samples of several bodies, concatenated on the device."""
     feats, targets = [], []
-    for _ in range(0, steps, every):
-        f = api.mlp_features(ctx, prm, pos)
-        x0 = pos.clone()
-        api.relax_step(ctx, prm, pos, vol, every)
+    for seed in seeds:
+        f, t = trajectory_samples(ctx, seed, dp, steps, every)
         feats.append(f)
-        targets.append(((pos - x0) / h).t().to(torch.float32).contiguous())
+        targets.append(t)
     return torch.cat(feats), torch.cat(targets)
 
 
 def train(ctx, feats, targets, steps, batch=4096, lr=1e-3, seed=0, log_every=0):
+    """Adam from the seeded initialisation; returns (trainer, [(step, loss), ...])."""
     trainer = api.MLPTrainer(ctx, inputs.mlp_init(seed), lr=lr)
-    gen = torch.Generator(device=ctx.device)
-    gen.manual_seed(seed)
-    m = feats.shape[0]
     losses = []
-    for k in range(steps):
-        idx = torch.randint(0, m, (batch,), device=ctx.device, generator=gen)
-        want = log_every and (k % log_every == 0 or k == steps - 1)
-        loss = trainer.step(feats[idx].contiguous(), targets[idx].contiguous(), with_loss=bool(want))
-        if want:
-            losses.append((k, loss))
+    chunk = log_every if log_every else steps
+    done = 0
+    while done < steps:
+        k = min(chunk, steps - done)
+        loss = trainer.train(feats, targets, k, batch=batch, seed=seed, with_loss=bool(log_every))
+        done += k
+        if log_every:
+            losses.append((done - 1, loss))
     return trainer, losses
 
 
 def steps_to_target(ctx, prm, pos, vol, target, max_steps, check_every=10):
     """Plain relaxation steps until the Laguerre-Gauss residual is <= target (or the cap)."""
-    done = 0
-    r = api.relax_residual(ctx, prm, pos, vol)[0]
-    while r > target and done < max_steps:
-        api.relax_step(ctx, prm, pos, vol, check_every)
-        done += check_every
-        r = api.relax_residual(ctx, prm, pos, vol)[0]
-    return done, r
+    r = api.relax_run(ctx, prm, pos, vol, target, max_steps, proposal=None, check_every=check_every)
+    return r["steps"], r["residual"][0]
 
 
 def learned_relax(ctx, prm, params, pos, vol, target, max_steps, applications=3, plain_between=10, check_every=10):
-    """Proposal-accelerated relaxation; returns (plain steps used, final residual, proposals kept).
-
-    A proposal is kept only if it lowers the Laguerre-Gauss residual; otherwise the
-    positions are restored and the run continues with plain relaxation alone."""
-    used = 0
-    kept = 0
-    for _ in range(applications):
-        r_before = api.relax_residual(ctx, prm, pos, vol)[0]
-        if r_before <= target:
-            return used, r_before, kept
-        saved = pos.clone()
-        api.relax_propose(ctx, prm, params, pos)
-        if api.relax_residual(ctx, prm, pos, vol)[0] >= r_before:
-            pos.copy_(saved)
-            break
-        kept += 1
-        n, r = steps_to_target(ctx, prm, pos, vol, target, plain_between, check_every)
-        used += n
-        if r <= target:
-            return used, r, kept
-    more, r = steps_to_target(ctx, prm, pos, vol, target, max_steps - used, check_every)
-    return used + more, r, kept
+    """Proposal-accelerated relaxation; returns (plain steps used, final residual, proposals kept)."""
+    r = api.relax_run(ctx, prm, pos, vol, target, max_steps, proposal=params, applications=applications,
+                      plain_between=plain_between, check_every=check_every)
+    return r["steps"], r["residual"][0], r["kept"]

@@ -168,6 +168,8 @@ def _read_plan(plan, n, nnz, maxrow):
     out["geo"] = raw[o:o + 16 * nt * 128 * maxrow].view(np.float32).reshape(-1, 4)
     o += 16 * nt * 128 * maxrow
     out["slots"] = raw[o:o + 2 * nt * 128 * maxrow].view(np.uint16)     # the TL plan's slot section
+    o += a16(2 * nt * 128 * maxrow)
+    out["wsum"] = raw[o:o + 16 * n].view(np.float32).reshape(n, 4)      # (S_i, 0) per particle
     return out
 
 
@@ -187,6 +189,15 @@ def test_tile_plan_is_exact(ctx):
     h = dom.h
     from oracle import kernels as OKer
     ms, ps = [], []
+    # S_i = sum_j grad0 W_ij V0_j of every row (the geometry form's M_i half of Eq. 30)
+    ii = np.repeat(np.arange(n), np.diff(rp))
+    dxa = ON.min_image(s["r0"][:, ii] - s["r0"][:, col], dom)
+    ra = np.sqrt(np.sum(dxa * dxa, axis=0))
+    wa = OKer.wendland_dwdr(ra, h, 3, None) / ra * s["vol"][col] * dxa
+    S = np.stack([np.bincount(ii, weights=wa[a], minlength=n) for a in range(3)])
+    scale = np.abs(wa).max()
+    assert np.allclose(P["wsum"][:, :3].T, S, rtol=2e-6, atol=1e-6 * scale)
+    assert np.all(P["wsum"][:, 3] == 0.0)
     for b in range((n + 127) // 128):
         i0, i1 = 128 * b, min(n, 128 * b + 128)
         p0, p1 = rp[i0], rp[i1]
@@ -377,16 +388,27 @@ def test_state_in_mapped_host_memory(ctx):
             m.close()
 
 
-def test_float32_state_round_trip(ctx):
+@pytest.mark.parametrize("dim", [3, 2])
+def test_float32_state_round_trip(ctx, dim):
     # the float32 form's state kept in mapped host memory as float32 (u = x - r0, v, F - I)
     # and exchanged every 2 steps with load32 / store32: bit for bit the device-resident run;
-    # and the float64 unpack of the same state agrees with it
-    s = _setup(ctx, dp=0.005)
+    # and the float64 unpack of the same state agrees with it.  3D plate and 2D strip (the
+    # 2D records keep v and the 2 x 2 H at other offsets)
+    s = _setup(ctx, dp=0.005) if dim == 3 else _setup(ctx, case=inputs.beam2d(dp=0.002))
     n = s["r0"].shape[1]
     ref = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
     sol = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
-    bufs = [api.HostArray((3, n), torch.float32), api.HostArray((3, n), torch.float32),
-            api.HostArray((9, n), torch.float32)]
+    bufs = [api.HostArray((dim, n), torch.float32), api.HostArray((dim, n), torch.float32),
+            api.HostArray((dim * dim, n), torch.float32)]
+    # the binding refuses buffers the C side would misread
+    wrong = api.HostArray((dim, n))                      # float64
+    try:
+        with pytest.raises(ValueError):
+            sol.store32(wrong, bufs[1], bufs[2])
+        with pytest.raises(ValueError):
+            sol.load32(bufs[0], bufs[1], torch.zeros((dim * dim, n), dtype=torch.float32, device="cuda").t())
+    finally:
+        wrong.close()
     try:
         ref.pack()
         sol.pack()
@@ -396,9 +418,9 @@ def test_float32_state_round_trip(ctx):
             sol.step(2)
             sol.store32(*bufs)
             ref.step(2)
-        dev = [torch.empty((3, n), dtype=torch.float32, device="cuda"),
-               torch.empty((3, n), dtype=torch.float32, device="cuda"),
-               torch.empty((9, n), dtype=torch.float32, device="cuda")]
+        dev = [torch.empty((dim, n), dtype=torch.float32, device="cuda"),
+               torch.empty((dim, n), dtype=torch.float32, device="cuda"),
+               torch.empty((dim * dim, n), dtype=torch.float32, device="cuda")]
         ref.store32(*dev)
         torch.cuda.synchronize()
         for b, d in zip(bufs, dev):

@@ -87,3 +87,24 @@ def test_static_variant_repeats_without_allocating_and_rejects_oversized_input()
                                         ctypes.c_void_p(1), 0, ctypes.byref(nnz), None)
     assert st == _lib.SPH_ERR_LIMIT
     assert b"static scratch" in lib.sph_status_string(st)
+
+
+def test_static_variant_against_the_oracle():
+    # directly against the float64 oracle's cell-list build (itself pinned to brute force),
+    # on a random 3D set in a closed box and a periodic 2D set, two calls in a row
+    from oracle import neighbors as ON
+    lib = _lib.load()
+    rng = np.random.default_rng(9)
+    pos3 = rng.uniform(0.0, 1.0, size=(3, 3000))
+    dom3 = inputs.domain(3, 0.05, 1.6, [0.0, 0.0, 0.0], [1.0, 1.0, 1.0], [False, False, False])
+    pos2 = rng.uniform(0.0, 1.0, size=(2, 4000))
+    dom2 = inputs.domain(2, 0.012, 2.0, [0.0, 0.0], [1.0, 1.0], [True, True])
+    for dom, pos_h in ((dom3, pos3), (dom2, pos2)):
+        od = ON.Domain(dom["dim"], dom["h"], dom["kappa"], dom["lo"], dom["len"], dom["periodic"])
+        rp_o, col_o = ON.neighbors_cells(pos_h, od)
+        pos = torch.tensor(pos_h, dtype=torch.float64, device="cuda")
+        st, rp, col, nnz = _static_call(lib, dom, pos, int(col_o.size))
+        assert st == _lib.SPH_OK, lib.sph_status_string(st)
+        assert nnz == col_o.size
+        assert np.array_equal(rp.cpu().numpy(), rp_o)
+        assert np.array_equal(col.cpu().numpy(), col_o)
