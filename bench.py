@@ -201,31 +201,47 @@ def _alg_bytes_tl(n, nnz):
     return mom, defo
 
 
-def _cpu_baseline(steps_cap_s=12.0):
-    """The oracle's TL step on a reduced plate (dp = 4 mm), timed on the host cores."""
+def _cpu_baseline(steps_cap_s=12.0, dp=0.003):
+    """The oracle's TL step on a reduced plate (dp = 3 mm), timed on the host cores: on all
+    of them (the pair sums over row blocks on a spawned process pool, oracle.pool, bitwise
+    the single-process step) and on one (plain numpy).  About steps_cap_s seconds each."""
     from oracle import kgc as OK
     from oracle import neighbors as ON
+    from oracle import pool as OP
     from oracle import tlsph as OT
     from paper_2405_05155_gb300 import inputs
-    c = inputs.plate(dp=0.004, kappa=1.6)
+    c = inputs.plate(dp=dp, kappa=1.6)
     d = c["domain"]
     dom = ON.Domain(d["dim"], d["h"], d["kappa"], d["lo"], d["len"], d["periodic"])
     rp, col = ON.neighbors_cells(c["r0"], dom)
     B0, _ = OK.kgc(c["r0"], c["vol"], rp, col, dom)
     prm = OT.TLParams(dom, c["dt"], c["rho0"], c["lam"], c["G"], OT.NEO_HOOKEAN)
     n = c["r0"].shape[1]
-    x, v, F = c["r0"].copy(), c["v"].copy(), np.tile(np.eye(3), (n, 1, 1))
-    steps = 0
-    t0 = time.perf_counter()
-    while time.perf_counter() - t0 < steps_cap_s or steps < 3:
-        x, v, F = OT.step(c["r0"], c["vol"], B0, c["fixed"], x, v, F, rp, col, prm)
-        steps += 1
-    el = time.perf_counter() - t0
-    pairs = 2 * col.size * steps
-    return {"value": pairs / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "float64 numpy oracle, plate at dp=0.004 m (%d particles, nnz=%d), %d time steps in %.1f s "
-                      "(%.1f ms/step); single-threaded numpy" % (n, col.size, steps, el, 1e3 * el / steps),
-            "ms_per_step": 1e3 * el / steps, "particles": n}
+
+    def timed(step):
+        x, v, F = c["r0"].copy(), c["v"].copy(), np.tile(np.eye(3), (n, 1, 1))
+        x, v, F = step(x, v, F)          # warm-up (the pool's workers start here)
+        steps = 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < steps_cap_s or steps < 3:
+            x, v, F = step(x, v, F)
+            steps += 1
+        return steps, time.perf_counter() - t0, v
+
+    cores = OP.host_cores()
+    with OP.PoolStep(c["r0"], c["vol"], B0, c["fixed"], rp, col, prm, workers=cores) as ps:
+        steps_all, el_all, v_all = timed(ps.step)
+    steps_one, el_one, _ = timed(lambda x, v, F: OT.step(c["r0"], c["vol"], B0, c["fixed"], x, v, F, rp, col, prm))
+    pairs = 2 * col.size
+    return {"value": pairs * steps_all / el_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "float64 numpy oracle, plate at dp=%g m (%d particles, nnz=%d): %d time steps in %.1f s "
+                      "(%.1f ms/step) on %d host cores (the two pair sums over row blocks on a spawned process "
+                      "pool, bitwise the single-process step); single core: %d steps in %.1f s (%.1f ms/step)"
+                      % (dp, n, col.size, steps_all, el_all, 1e3 * el_all / steps_all, cores, steps_one, el_one,
+                         1e3 * el_one / steps_one),
+            "ms_per_step": 1e3 * el_all / steps_all, "particles": n,
+            "single_core": {"value": pairs * steps_one / el_one, "ms_per_step": 1e3 * el_one / steps_one,
+                            "cores": 1}}
 
 
 # --------------------------------------------------------------------------- other rows
@@ -673,6 +689,58 @@ def _bench_mlp(api, inputs, ctx, peak_tflops):
                          "unit": "TFLOP/s", "frac": tflops / peak_tflops}}
 
 
+def _bench_relax_learned(api, inputs, ctx, train_bodies=200, train_steps=4000, target_steps=50):
+    """The learned proposal at the relaxation configuration's scale, all through the C ABI:
+    training data from plain trajectories of `train_bodies` seeded bodies at dp = 1/40
+    (sph_relax_samples: 500 steps, a snapshot every 50), Adam on device-drawn minibatches of
+    4096 (sph_mlp_train), then wall-clock to a residual target on the dp = 1/128 body of seed
+    0 (sph_relax_run): plain float64, plain float32 and float32 with the proposal.  The
+    target is the residual plain float32 relaxation reaches after `target_steps` steps."""
+    import time
+    import torch
+    from paper_2405_05155_gb300 import learned
+    t0 = time.perf_counter()
+    feats, targets = learned.training_set(ctx, range(train_bodies), 1.0 / 40.0, steps=500, every=50)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    rows = int(feats.shape[0])
+    t0 = time.perf_counter()
+    trainer, losses = learned.train(ctx, feats, targets, steps=train_steps, batch=4096, lr=1e-3, seed=0,
+                                    log_every=1000)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del feats, targets
+    torch.cuda.empty_cache()
+    b, prm32, pos0, vol = learned.body_on_device(ctx, 0, 1.0 / 128.0)
+    prm64 = api.relax_params(b["domain"], b["spheres"], b["dp"], precision=api.SPH_FP64, n=pos0.shape[1])
+    ref = pos0.clone()
+    api.relax_step(ctx, prm32, ref, vol, target_steps)
+    target = api.relax_residual(ctx, prm32, ref, vol)[0]
+    r_start = api.relax_residual(ctx, prm32, pos0, vol)[0]
+    del ref
+    arms = {}
+    for name, prm, proposal in (("plain_fp32", prm32, None), ("learned_fp32", prm32, trainer.params),
+                                ("plain_fp64", prm64, None)):
+        p = pos0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = api.relax_run(ctx, prm, p, vol, target, 20 * target_steps, proposal=proposal, applications=3,
+                            plain_between=10, check_every=10)
+        torch.cuda.synchronize()
+        out["ms"] = (time.perf_counter() - t0) * 1e3
+        arms[name] = out
+        del p
+    return {"workload": "learned relaxation proposal: trained on %d seeded 8-sphere bodies at dp=1/40 (%d samples, "
+                        "snapshots every 50 of 500 plain steps), Adam lr 1e-3, batch 4096, %d steps; applied to the "
+                        "dp=1/128 body of seed 0 (%d particles), residual target = plain float32 residual after %d "
+                        "steps; residual checked every 10 plain steps" % (train_bodies, rows, train_steps,
+                                                                           int(pos0.shape[1]), target_steps),
+            "training_data_s": t_data, "training_s": t_train, "loss": losses, "residual_start": r_start,
+            "residual_target": target, "arms": arms,
+            "speedup_learned_vs_plain_fp32": arms["plain_fp32"]["ms"] / arms["learned_fp32"]["ms"],
+            "speedup_learned_vs_plain_fp64": arms["plain_fp64"]["ms"] / arms["learned_fp32"]["ms"]}
+
+
 # --------------------------------------------------------------------------- arms
 def run_reference(args):
     rank, world, _ = _dist_info()
@@ -685,7 +753,7 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": WORKLOAD, "reference": "float64 CPU oracle (oracle/), "
                                             "bounded sample of the same workload"},
             "cpu_baseline": {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
-                             "sample": cb["sample"]},
+                             "sample": cb["sample"], "single_core": cb["single_core"]},
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -916,7 +984,8 @@ def run_gpu(args):
                          ("double_shear_layer", lambda: _bench_dsl(api, inputs, ctx)),
                          ("columns", lambda: _bench_columns(api, inputs, ctx)),
                          ("compressible_sod", lambda: _bench_compressible(api, inputs, ctx, peak)),
-                         ("mlp_proposal", lambda: _bench_mlp(api, inputs, ctx, bf16))):
+                         ("mlp_proposal", lambda: _bench_mlp(api, inputs, ctx, bf16)),
+                         ("relax_learned_8spheres_dp128", lambda: _bench_relax_learned(api, inputs, ctx))):
             if args.rows and name not in args.rows.split(","):
                 continue
             try:
@@ -985,7 +1054,7 @@ def run_gpu(args):
             "workloads": workloads,
         }
         if cb is not None:
-            line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "single_core")}
         print(json.dumps(line))
     ctx.close()
     if world > 1:

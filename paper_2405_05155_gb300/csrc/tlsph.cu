@@ -419,6 +419,62 @@ __device__ __forceinline__ void defo_pair_rel(float4 xj, float4 vj, const float*
     }
 }
 
+// The products one deformation-rate pair adds (as defo_pair_rel): columns (L0c, L1c) of
+// V0_j (v_j - v_i) (x) g_ij, (L20, L21) and L22.  FUSE adds them to `t` with one rounding
+// each (a block of two pairs is summed first and enters the compensated sums once).
+struct DefoTerms {
+    float2 c[3];
+    float2 r2;
+    float l22;
+};
+
+template <int DIM, bool FUSE>
+__device__ __forceinline__ void defo_terms_rel(float4 xj, float4 vj, const float* xi, float2 nv01, float nv2,
+                                               const TLK<float>& K, DefoTerms& t) {
+    float r[DIM];
+    r[0] = xi[0] - xj.x;
+    r[1] = xi[1] - xj.y;
+    if (DIM == 3) r[DIM - 1] = xi[DIM - 1] - xj.z;
+    float d2 = r[0] * r[0];
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) d2 = fmaf(r[a], r[a], d2);
+    const float gs = gs_from_d2(d2, K);
+    const float w = xj.w;
+    const float2 dv01 = __fmul2_rn(make_float2(w, w), __fadd2_rn(make_float2(vj.x, vj.y), nv01));
+    const float g0 = gs * r[0], g1 = gs * r[1];
+    if (FUSE) {
+        t.c[0] = __ffma2_rn(dv01, make_float2(g0, g0), t.c[0]);
+        t.c[1] = __ffma2_rn(dv01, make_float2(g1, g1), t.c[1]);
+    } else {
+        t.c[0] = __fmul2_rn(dv01, make_float2(g0, g0));
+        t.c[1] = __fmul2_rn(dv01, make_float2(g1, g1));
+    }
+    if (DIM == 3) {
+        const float g2 = gs * r[DIM - 1];
+        const float dv2 = w * (vj.z + nv2);
+        if (FUSE) {
+            t.c[DIM - 1] = __ffma2_rn(dv01, make_float2(g2, g2), t.c[DIM - 1]);
+            t.r2 = __ffma2_rn(make_float2(dv2, dv2), make_float2(g0, g1), t.r2);
+            t.l22 = fmaf(dv2, g2, t.l22);
+        } else {
+            t.c[DIM - 1] = __fmul2_rn(dv01, make_float2(g2, g2));
+            t.r2 = __fmul2_rn(make_float2(dv2, dv2), make_float2(g0, g1));
+            t.l22 = dv2 * g2;
+        }
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ void defo_add_terms(const DefoTerms& t, Kahan2* c01, Kahan2& r2, Kahan<float>& l22) {
+    c01[0].add(t.c[0]);
+    c01[1].add(t.c[1]);
+    if (DIM == 3) {
+        c01[DIM - 1].add(t.c[DIM - 1]);
+        r2.add(t.r2);
+        l22.add(t.l22);
+    }
+}
+
 __device__ __forceinline__ float4 lo4(const F8& f) { return make_float4(f.v[0], f.v[1], f.v[2], f.v[3]); }
 __device__ __forceinline__ float4 hi4(const F8& f) { return make_float4(f.v[4], f.v[5], f.v[6], f.v[7]); }
 
@@ -608,8 +664,10 @@ struct GeoArgs {
     int mcap;
     const int32_t* tile_e;   // bulk form: entries per tile
     int ecap;                // bulk form: most entries a block copies into shared memory (0: none)
-    const uint16_t* slots;   // geometry form: the entries' neighbour slots alone, same sliced order
+    const uint16_t* slots;   // geometry form: the pairs' staging positions alone, same sliced order
     const float4* wsum;      // geometry form of the momentum pass: (S_i, 0) per particle
+    const uint16_t* spos;    // geometry form: staging position of each distinct neighbour (uidx order)
+    const uint16_t* sinv;    // geometry form: the distinct neighbour at each staging position
     uint32_t test_polls;     // bulk form: > 0 issues no copy and waits this many polls (sph_set_wait_test)
 };
 
@@ -627,35 +685,111 @@ static inline size_t tl_wsum_offset(int64_t n, int64_t nnz, int64_t maxrow) {
     return tl_slot_offset(n, nnz, maxrow) + align16((size_t)ntiles * kTileRows * (size_t)maxrow * 2);
 }
 
-static inline size_t tl_plan_total(int64_t n, int64_t nnz, int64_t maxrow) {
+// Then two uint16 sections indexed like uidx (tile b's k-th distinct neighbour at
+// row_ptr[b * kTileRows] + k): spos, the shared-memory position the geometry-form passes
+// stage that neighbour at, and sinv, its inverse (the neighbour at each position).
+static inline size_t tl_spos_offset(int64_t n, int64_t nnz, int64_t maxrow) {
     return tl_wsum_offset(n, nnz, maxrow) + align16((size_t)n * 16);
 }
 
+static inline size_t tl_sinv_offset(int64_t n, int64_t nnz, int64_t maxrow) {
+    return tl_spos_offset(n, nnz, maxrow) + align16((size_t)nnz * 2);
+}
+
+static inline size_t tl_plan_total(int64_t n, int64_t nnz, int64_t maxrow) {
+    return tl_sinv_offset(n, nnz, maxrow) + align16((size_t)nnz * 2);
+}
+
+// Most distinct neighbours of a tile whose staging positions are balanced over the bank
+// groups (tiles with more keep their list order).
+constexpr int kPermCap = 2048;
+
 // Pair entries of the tile plan: w = grad0 W_ij V0_j in float64, stored float32,
-// with the neighbour's slot, each row's pairs in the bank-aware order (bank_order);
-// and the row's S_i = sum_j w_ij, summed in float64 in list order, stored float32.
+// with the neighbour's slot (its position in the tile's distinct list); the row's
+// S_i = sum_j w_ij, summed in float64 in list order, stored float32; and the staging
+// positions of the geometry forms.
+//
+// Staging positions: a quarter warp's 16-byte shared-memory gathers take one wavefront
+// when its 8 lanes read positions in 8 different groups (position mod 8), so the tile's
+// distinct neighbours are given positions whose groups balance, in every quarter warp
+// (8 consecutive rows), the pairs over the 8 groups.  Greedily, in list order: each
+// neighbour takes the group with room (group c holds the positions c, c + 8, ... below
+// m) that adds least to sum over quarter warps and groups of (pairs in the group)^2,
+// i.e. the smallest sum_Q cnt_Q * load_Q[c], ties to the lower group.  Each row's pairs
+// are then laid out in the bank-aware order (bank_order) of these positions.
 template <int DIM>
 __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__ r0, const double* __restrict__ V0,
                                                       const int64_t* __restrict__ row_ptr,
                                                       const int32_t* __restrict__ col,
                                                       const uint16_t* __restrict__ lcol,
+                                                      const int32_t* __restrict__ tile_m,
                                                       const int32_t* __restrict__ tile_e,
                                                       const int64_t* __restrict__ tile_so, int64_t n, TLK<double> K,
                                                       float4* __restrict__ geo, uint16_t* __restrict__ slots,
-                                                      float4* __restrict__ wsum) {
+                                                      float4* __restrict__ wsum, uint16_t* __restrict__ spos,
+                                                      uint16_t* __restrict__ sinv) {
+    __shared__ uint32_t s_cnt[kPermCap * 4];   // per neighbour, the 16 quarter warps' pair counts, a byte each
+    __shared__ uint16_t s_pos[kPermCap];
+    __shared__ int s_load[16 * 8];
+    __shared__ int s_used[8];
     const int64_t tile = blockIdx.x;
     const int64_t i = tile * kTileRows + threadIdx.x;
     const bool active = i < n;
     const int64_t b = active ? row_ptr[i] : 0;
     const int len = active ? (int)(row_ptr[i + 1] - b) : 0;
     const int width = tile_e[tile] / kTileRows;
+    const int m = tile_m[tile];
+    const int64_t P0 = row_ptr[tile * kTileRows];
     float4* out = geo + tile_so[tile] + threadIdx.x;
     double xi[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) xi[a] = active ? r0[a * n + i] : 0.0;
-    // pair order: bank-aware for the staged float4 gathers of both passes (see bank_order)
+    const bool balance = m <= kPermCap;
+    if (balance) {
+        for (int q = threadIdx.x; q < 4 * m; q += blockDim.x) s_cnt[q] = 0u;
+        for (int q = threadIdx.x; q < 16 * 8; q += blockDim.x) s_load[q] = 0;
+        if (threadIdx.x < 8) s_used[threadIdx.x] = 0;
+        __syncthreads();
+        const int Q = (int)threadIdx.x >> 3;
+        for (int k = 0; k < len; ++k)
+            atomicAdd(&s_cnt[4 * min((int)lcol[b + k], m - 1) + (Q >> 2)], 1u << (8 * (Q & 3)));
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int lane = (int)threadIdx.x;
+            for (int q = 0; q < m; ++q) {
+                uint32_t key = 0xFFFFFFFFu;
+                if (lane < 8 && s_used[lane] < (m - lane + 7) / 8) {
+                    uint32_t cost = 0u;
+#pragma unroll
+                    for (int qi = 0; qi < 16; ++qi)
+                        cost += ((s_cnt[4 * q + (qi >> 2)] >> (8 * (qi & 3))) & 0xFFu) * (uint32_t)s_load[8 * qi + lane];
+                    key = cost * 8u + (uint32_t)lane;
+                }
+                const int c = (int)(__reduce_min_sync(0xFFFFFFFFu, key) & 7u);
+                if (lane < 16) s_load[8 * lane + c] += (int)((s_cnt[4 * q + (lane >> 2)] >> (8 * (lane & 3))) & 0xFFu);
+                __syncwarp();
+                if (lane == 0) {
+                    s_pos[q] = (uint16_t)(8 * s_used[c] + c);
+                    s_used[c] += 1;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < m; q += blockDim.x) {
+            spos[P0 + q] = s_pos[q];
+            sinv[P0 + s_pos[q]] = (uint16_t)q;
+        }
+    } else {
+        for (int q = threadIdx.x; q < m; q += blockDim.x) {
+            spos[P0 + q] = (uint16_t)q;
+            sinv[P0 + q] = (uint16_t)q;
+        }
+    }
+    auto pos_of = [&](int q) { return balance ? (int)s_pos[min(q, m - 1)] : q; };
+    // pair order: bank-aware for the staged float4 gathers (see bank_order)
     uint32_t order[kSortCap];
-    const bool sorted = bank_order(len, [&](int k) { return (int)lcol[b + k]; }, order);
+    const bool sorted = bank_order(len, [&](int k) { return pos_of((int)lcol[b + k]); }, order);
     for (int k = 0; k < width; ++k) {
         float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (k < len) {
@@ -670,7 +804,8 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
             e.w = __int_as_float((int)lcol[p]);
         }
         out[(int64_t)k * kTileRows] = e;
-        slots[tile_so[tile] + threadIdx.x + (int64_t)k * kTileRows] = (uint16_t)__float_as_int(e.w);
+        slots[tile_so[tile] + threadIdx.x + (int64_t)k * kTileRows] =
+            k < len ? (uint16_t)pos_of(__float_as_int(e.w)) : (uint16_t)0;
     }
     if (!active) return;
     double S[3] = {0.0, 0.0, 0.0};
@@ -690,17 +825,19 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
 // with more distinct neighbours than mcap.  Block-uniform.
 template <int NPL, int RECF, int FIRST = 1>
 __device__ __forceinline__ bool stage_neighbours(const float* __restrict__ R, int64_t n, int64_t P0, int m,
-                                                 const GeoArgs& A, float4* sp) {
+                                                 const GeoArgs& A, float4* sp, const uint16_t* spos = nullptr) {
     const bool staged = m <= A.mcap;
     if (staged) {
         // consecutive threads copy consecutive chunks of consecutive neighbours: the
         // tile's neighbours come in runs of consecutive indices (Morton order), so the
-        // loads of a warp mostly fall on contiguous records
+        // loads of a warp mostly fall on contiguous records.  spos: the staging position
+        // of each neighbour (else its place in the list)
         for (int q = threadIdx.x; q < m * NPL; q += blockDim.x) {
             int s = q / NPL, c = q - s * NPL;
             // a plan out of date with the lists reads wrong but in-bounds records
             int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
-            sp[c * A.mcap + s] = __ldg(reinterpret_cast<const float4*>(R + RECF * j) + FIRST + c);
+            const int at = spos ? min((int)spos[P0 + s], m - 1) : s;
+            sp[c * A.mcap + at] = __ldg(reinterpret_cast<const float4*>(R + RECF * j) + FIRST + c);
         }
     }
     __syncthreads();
@@ -862,6 +999,34 @@ __device__ __forceinline__ void mom_stage(const float* __restrict__ RM, int64_t 
     mom_stage_rec<DIM>(a, b, bref, K, p0, p1, p2);
 }
 
+// The terms of one pair of the geometry form, (V0_j M_j) g_ij as rows 0-1 paired and row 2;
+// FUSE adds them to (t01, t2) with one rounding per product (blocks of two pairs).
+template <int DIM, bool FUSE>
+__device__ __forceinline__ void mom_terms_rel(float4 p0, float4 p1, float4 p2, const float* xi, const TLK<float>& K,
+                                              float2& t01, float& t2) {
+    float r[DIM];
+    r[0] = xi[0] - p0.x;
+    r[1] = xi[1] - p0.y;
+    if (DIM == 3) r[DIM - 1] = xi[DIM - 1] - p0.z;
+    float d2 = r[0] * r[0];
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) d2 = fmaf(r[a], r[a], d2);
+    const float gs = gs_from_d2(d2, K);
+    const float g0 = gs * r[0], g1 = gs * r[1];
+    if (DIM == 2) {
+        const float2 a0 = FUSE ? __ffma2_rn(make_float2(p0.z, p0.w), make_float2(g0, g0), t01)
+                               : __fmul2_rn(make_float2(p0.z, p0.w), make_float2(g0, g0));
+        t01 = __ffma2_rn(make_float2(p1.x, p1.y), make_float2(g1, g1), a0);
+    } else {
+        const float g2 = gs * r[DIM - 1];
+        const float2 a0 = FUSE ? __ffma2_rn(make_float2(p1.x, p1.y), make_float2(g0, g0), t01)
+                               : __fmul2_rn(make_float2(p1.x, p1.y), make_float2(g0, g0));
+        t01 = __ffma2_rn(make_float2(p2.x, p2.y), make_float2(g2, g2),
+                         __ffma2_rn(make_float2(p1.z, p1.w), make_float2(g1, g1), a0));
+        t2 = fmaf(p0.w, g2, fmaf(p2.w, g1, FUSE ? fmaf(p2.z, g0, t2) : p2.z * g0));
+    }
+}
+
 // One pair of the geometry form: accumulates (V0_j M_j) g_ij, rows 0-1 paired and row 2 alone.
 template <int DIM>
 __device__ __forceinline__ void mom_pair_rel(float4 p0, float4 p1, float4 p2, const float* xi, const TLK<float>& K,
@@ -933,11 +1098,13 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restr
         // records two at a time, so that few round trips to memory are in series
         for (int q0 = 0; q0 < m; q0 += 4 * kTileRows) {
             int64_t jq[4];
+            int pq[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int q = q0 + k * kTileRows + (int)threadIdx.x;
                 // a plan out of date with the lists reads wrong but in-bounds records
                 jq[k] = q < m ? min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1) : -1;
+                pq[k] = q < m ? min((int)A.spos[P0 + q], m - 1) : 0;
             }
 #pragma unroll
             for (int k = 0; k < 4; k += 2) {
@@ -951,7 +1118,7 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restr
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                     if (jq[k + t] < 0) continue;
-                    const int q = q0 + (k + t) * kTileRows + (int)threadIdx.x;
+                    const int q = pq[k + t];
                     float4 p0, p1, p2;
                     mom_stage_rec<DIM>(ra[t], rb[t], bref, K, p0, p1, p2);
                     P0s[q] = p0;
@@ -991,15 +1158,43 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restr
     const int mlast = max(m - 1, 0);
     const uint16_t* gsl = A.slots + A.tile_so[tile] + threadIdx.x;
     if (staged && sslot) {
+        // pairs in blocks of two: each block's terms summed with one rounding per product,
+        // then added to the compensated sums
         const uint16_t* sl = ssl + threadIdx.x;
-#pragma unroll 4
-        for (int k = 0; k < len; ++k) {
-            const int s = min((int)sl[k * kTileRows], mlast);
-            if (DIM == 3) mom_pair_rel<3>(P0s[s], P1s[s], P2s[s], xi, K, acc01, acc2);
-            else {
+        auto planes = [&](int s, float4& p0, float4& p1, float4& p2) {
+            p0 = P0s[s];
+            if (DIM == 3) {
+                p1 = P1s[s];
+                p2 = P2s[s];
+            } else {
                 const float2 h = P1h[s];
-                mom_pair_rel<DIM>(P0s[s], make_float4(h.x, h.y, 0.0f, 0.0f), P0s[s], xi, K, acc01, acc2);
+                p1 = make_float4(h.x, h.y, 0.0f, 0.0f);
+                p2 = p1;
             }
+        };
+        int k = 0;
+#pragma unroll 2
+        for (; k + 1 < len; k += 2) {
+            const int s0 = min((int)sl[k * kTileRows], mlast), s1 = min((int)sl[(k + 1) * kTileRows], mlast);
+            float4 a0, a1, a2, b0, b1, b2;
+            planes(s0, a0, a1, a2);
+            planes(s1, b0, b1, b2);
+            float2 t01;
+            float t2 = 0.0f;
+            mom_terms_rel<DIM, false>(a0, a1, a2, xi, K, t01, t2);
+            mom_terms_rel<DIM, true>(b0, b1, b2, xi, K, t01, t2);
+            acc01.add(t01);
+            if (DIM == 3) acc2.add(t2);
+        }
+        if (k < len) {
+            const int s0 = min((int)sl[k * kTileRows], mlast);
+            float4 a0, a1, a2;
+            planes(s0, a0, a1, a2);
+            float2 t01;
+            float t2 = 0.0f;
+            mom_terms_rel<DIM, false>(a0, a1, a2, xi, K, t01, t2);
+            acc01.add(t01);
+            if (DIM == 3) acc2.add(t2);
         }
     } else if (staged) {
 #pragma unroll 4
@@ -1015,7 +1210,8 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restr
         for (int k = 0; k < len; ++k) {
             const int s = min(sslot ? (int)ssl[threadIdx.x + k * kTileRows] : (int)__ldg(gsl + (int64_t)k * kTileRows),
                               mlast);
-            const int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
+            const int q = min((int)A.sinv[P0 + s], mlast);
+            const int64_t j = min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1);
             float4 p0, p1, p2;
             mom_stage<DIM>(RM, j, bref, K, p0, p1, p2);
             mom_pair_rel<DIM>(p0, p1, p2, xi, K, acc01, acc2);
@@ -1116,10 +1312,12 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
             // records two at a time, so that few round trips to memory are in series
             for (int q0 = 0; q0 < m; q0 += 4 * kTileRows) {
                 int64_t jq[4];
+                int pq[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int q = q0 + k * kTileRows + (int)threadIdx.x;
                     jq[k] = q < m ? min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1) : -1;
+                    pq[k] = q < m ? min((int)A.spos[P0 + q], m - 1) : 0;
                 }
 #pragma unroll
                 for (int k = 0; k < 4; k += 2) {
@@ -1129,7 +1327,7 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
 #pragma unroll
                     for (int t = 0; t < 2; ++t) {
                         if (jq[k + t] < 0) continue;
-                        const int q = q0 + (k + t) * kTileRows + (int)threadIdx.x;
+                        const int q = pq[k + t];
                         float x[3] = {0.0f, 0.0f, 0.0f};
                         rel_to_ref<DIM>(rr[t].v, __float_as_uint(rr[t].v[DIM]), bref, K, x);
                         sp[q] = make_float4(x[0], x[1], x[2], DIM == 3 ? rr[t].v[7] : rr[t].v[3]);
@@ -1141,7 +1339,8 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
         if (sslot) cp_async_wait_all();
         __syncthreads();
     } else {
-        staged = GEOM ? stage_neighbours<2, 8, 0>(RD, n, P0, m, A, sp) : stage_neighbours<1, 8>(RD, n, P0, m, A, sp);
+        staged = GEOM ? stage_neighbours<2, 8, 0>(RD, n, P0, m, A, sp, A.spos)
+                      : stage_neighbours<1, 8>(RD, n, P0, m, A, sp);
     }
     if (bulk) {
         const bool late = !mbar_wait_bounded(bar, 0, test_wait ? A.test_polls : kWaitPolls);
@@ -1176,11 +1375,24 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
         float xi[3] = {0.0f, 0.0f, 0.0f};
         rel_to_ref<DIM>(me.v, bi, bref, K, xi);
         if (sslot) {
+            // pairs in blocks of two: each block's products summed with one rounding per
+            // term, then added to the compensated sums
             const uint16_t* sl = ssl + threadIdx.x;
-#pragma unroll 4
-            for (int k = 0; k < len; ++k) {
-                int s = min((int)sl[k * kTileRows], max(m - 1, 0));
-                defo_pair_rel<DIM>(sp[s], sp[A.mcap + s], xi, nv01, nv2, K, c01, r2, l22);
+            const int mlast = max(m - 1, 0);
+            int k = 0;
+#pragma unroll 2
+            for (; k + 1 < len; k += 2) {
+                const int s0 = min((int)sl[k * kTileRows], mlast), s1 = min((int)sl[(k + 1) * kTileRows], mlast);
+                DefoTerms t;
+                defo_terms_rel<DIM, false>(sp[s0], sp[A.mcap + s0], xi, nv01, nv2, K, t);
+                defo_terms_rel<DIM, true>(sp[s1], sp[A.mcap + s1], xi, nv01, nv2, K, t);
+                defo_add_terms<DIM>(t, c01, r2, l22);
+            }
+            if (k < len) {
+                const int s0 = min((int)sl[k * kTileRows], mlast);
+                DefoTerms t;
+                defo_terms_rel<DIM, false>(sp[s0], sp[A.mcap + s0], xi, nv01, nv2, K, t);
+                defo_add_terms<DIM>(t, c01, r2, l22);
             }
         } else {
             const uint16_t* sl = A.slots + A.tile_so[tile] + threadIdx.x;
@@ -1204,7 +1416,8 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
         } else {
             for (int k = 0; k < len; ++k) {
                 int s = min((int)__ldg(sl + (int64_t)k * kTileRows), max(m - 1, 0));
-                int64_t j = min(max((int64_t)A.uidx[P0 + s], (int64_t)0), n - 1);
+                const int q = min((int)A.sinv[P0 + s], max(m - 1, 0));
+                int64_t j = min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1);
                 F8 rj = ldg8(RD + 8 * j);
                 defo_pair<DIM, PER>(lo4(rj), hi4(rj), oi, bi, nv01, nv2, K, c01, r2, l22);
             }
@@ -1757,6 +1970,10 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
         t.defo.mcap = mg;
         t.defo.slots = reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(st->plan) +
                                                          tl_slot_offset(n, st->plan_nnz, st->plan_maxrow));
+        t.defo.spos = reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(st->plan) +
+                                                        tl_spos_offset(n, st->plan_nnz, st->plan_maxrow));
+        t.defo.sinv = reinterpret_cast<const uint16_t*>(reinterpret_cast<const unsigned char*>(st->plan) +
+                                                        tl_sinv_offset(n, st->plan_nnz, st->plan_maxrow));
         // the tile's slot block in shared memory too, up to 128 positions (32 KB)
         t.defo.tile_e = tp.tile_e;
         t.defo.ecap = st->plan_maxrow <= 128 ? (int)st->plan_maxrow : 0;
@@ -1917,14 +2134,18 @@ extern "C" int sph_tlsph_plan(sph_ctx* ctx, const sph_tlsph_params* p, sph_tlsph
                                                   tl_slot_offset(n, nnz, maxrow));
     float4* wsum = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(st->plan) +
                                              tl_wsum_offset(n, nnz, maxrow));
+    uint16_t* spos = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(st->plan) +
+                                                 tl_spos_offset(n, nnz, maxrow));
+    uint16_t* sinv = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(st->plan) +
+                                                 tl_sinv_offset(n, nnz, maxrow));
     TLK<double> K = make_tl_consts<double>(p);
     unsigned nt = (unsigned)tp.ntiles;
     if (p->dom.dim == 2)
-        k_tl_geo<2><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_e, tp.tile_so,
-                                             n, K, tp.geo, slots, wsum);
+        k_tl_geo<2><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_m, tp.tile_e,
+                                             tp.tile_so, n, K, tp.geo, slots, wsum, spos, sinv);
     else
-        k_tl_geo<3><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_e, tp.tile_so,
-                                             n, K, tp.geo, slots, wsum);
+        k_tl_geo<3><<<nt, kTileRows, 0, s>>>(st->r0, st->V0, st->row_ptr, st->col, tp.lcol, tp.tile_m, tp.tile_e,
+                                             tp.tile_so, n, K, tp.geo, slots, wsum, spos, sinv);
     SPH_LAUNCH_CHECK(ctx);
     SPH_CUDA(ctx, cudaStreamSynchronize(s));
     st->plan_nnz = nnz;

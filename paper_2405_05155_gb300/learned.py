@@ -46,15 +46,16 @@ def training_set(ctx, seeds, dp, steps=500, every=50):
 def train(ctx, feats, targets, steps, batch=4096, lr=1e-3, seed=0, log_every=0):
     """Adam from the seeded initialisation; returns (trainer, [(step, loss), ...])."""
     trainer = api.MLPTrainer(ctx, inputs.mlp_init(seed), lr=lr)
-    losses = []
-    chunk = log_every if log_every else steps
-    done = 0
-    while done < steps:
-        k = min(chunk, steps - done)
-        loss = trainer.train(feats, targets, k, batch=batch, seed=seed, with_loss=bool(log_every))
-        done += k
-        if log_every:
-            losses.append((done - 1, loss))
+    if not log_every:
+        trainer.train(feats, targets, steps, batch=batch, seed=seed, with_loss=False)
+        return trainer, []
+    # the minibatch loss of steps 0, log_every, 2 log_every, ... and the last (each step's
+    # loss is taken before its update)
+    marks = sorted(set([0] + list(range(log_every, steps, log_every)) + [steps - 1]))
+    losses, prev = [], -1
+    for k in marks:
+        losses.append((k, trainer.train(feats, targets, k - prev, batch=batch, seed=seed, with_loss=True)))
+        prev = k
     return trainer, losses
 
 

@@ -131,3 +131,85 @@ def test_trained_proposal_reduces_relaxation_steps(ctx):
     print("plain steps, learned-run plain steps, proposals kept:", gains)
     # the proposal saves plain steps on every held-out body
     assert all(nl < npl for npl, nl, _ in gains)
+
+
+# ---------------------------------------------------------------- the learned loop's ABI
+def _splitmix64(x):
+    # SplitMix64 as published with the generator (Steele, Lea and Flood, OOPSLA 2014),
+    # written independently of the library: numpy uint64 wraps modulo 2^64
+    with np.errstate(over="ignore"):
+        z = np.uint64(x) + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def _draw(seed, step, batch, rows):
+    key = _splitmix64(np.uint64(seed) ^ _splitmix64(np.uint64(step)))
+    out = np.empty(batch, dtype=np.int64)
+    for b in range(batch):
+        with np.errstate(over="ignore"):
+            z = int(_splitmix64(key + np.uint64(b)))
+        out[b] = (z * rows) >> 64
+    return out
+
+
+def test_relax_samples_equal_the_composed_calls(ctx):
+    # sph_relax_samples = features at x^t, `every` plain steps, (x^{t+every} - x^t)/h
+    b, prm, pos, vol = learned.body_on_device(ctx, 5, 1.0 / 24.0)
+    ref = pos.clone()
+    f, t = api.relax_samples(ctx, prm, pos, vol, 3, 7)
+    n = pos.shape[1]
+    for k in range(3):
+        fk = api.mlp_features(ctx, prm, ref)
+        x0 = ref.clone()
+        api.relax_step(ctx, prm, ref, vol, 7)
+        tk = ((host(ref) - host(x0)) / b["h"]).T.astype(np.float32)
+        assert torch.equal(f[k * n:(k + 1) * n], fk)
+        assert np.array_equal(host(t[k * n:(k + 1) * n]), tk)
+    assert torch.equal(pos, ref)
+
+
+def test_mlp_train_draws_its_minibatches_as_documented(ctx):
+    # sph_mlp_train = for each step t: the SplitMix64 minibatch of (seed, t), gathered, and
+    # one sph_mlp_train_step; compared bit for bit with the host-drawn batches
+    rows, batch, seed = 3000, 256, 77
+    X, T = _batch(9, rows)
+    Xd, Td = cuda(X, torch.float32), cuda(T, torch.float32)
+    flat = inputs.mlp_init(2)
+    a = api.MLPTrainer(ctx, flat, lr=1e-3)
+    loss_a = a.train(Xd, Td, 4, batch=batch, seed=seed)
+    b = api.MLPTrainer(ctx, flat, lr=1e-3)
+    for step in range(1, 5):
+        idx = torch.tensor(_draw(seed, step, batch, rows), device=Xd.device)
+        loss_b = b.step(Xd[idx].contiguous(), Td[idx].contiguous(), with_loss=(step == 4))
+    assert torch.equal(a.params, b.params) and torch.equal(a.m, b.m) and torch.equal(a.v, b.v)
+    assert loss_a == loss_b and a.step_count == b.step_count == 4
+
+
+def test_relax_run_plain_and_fallback(ctx):
+    b, prm, pos, vol = learned.body_on_device(ctx, 6, 1.0 / 24.0, precision=api.SPH_FP64)
+    r0 = api.relax_residual(ctx, prm, pos, vol)[0]
+    # plain run to a reachable target, checked every 5 steps: the plain steps composed by hand
+    ref = pos.clone()
+    target = 0.9 * r0
+    done, r = 0, r0
+    while r > target and done < 100:
+        api.relax_step(ctx, prm, ref, vol, 5)
+        done += 5
+        r = api.relax_residual(ctx, prm, ref, vol)[0]
+    p = pos.clone()
+    out = api.relax_run(ctx, prm, p, vol, target, 100, proposal=None, check_every=5)
+    assert out["reached"] and out["steps"] == done and not out["fell_back"]
+    assert torch.equal(p, ref) and out["residual"][0] == r
+    # a proposal that only makes things worse (a network with large outputs) is undone; an
+    # unreachable target then makes plain relaxation from the start the result
+    bad = torch.tensor(inputs.mlp_init(3), dtype=torch.float32, device=ctx.device)
+    bad[-3 - 3 * 128:-3] *= 3.0          # untrained, output layer tripled: random moves of ~h
+    p = pos.clone()
+    out = api.relax_run(ctx, prm, p, vol, 0.0, 12, proposal=bad, applications=3, plain_between=4, check_every=4)
+    assert out["rejected"] == 1 and out["kept"] == 0
+    assert out["fell_back"] and not out["reached"] and out["steps"] == 12
+    plain = pos.clone()
+    api.relax_step(ctx, prm, plain, vol, 12)
+    assert torch.equal(p, plain)

@@ -170,7 +170,22 @@ def _read_plan(plan, n, nnz, maxrow):
     out["slots"] = raw[o:o + 2 * nt * 128 * maxrow].view(np.uint16)     # the TL plan's slot section
     o += a16(2 * nt * 128 * maxrow)
     out["wsum"] = raw[o:o + 16 * n].view(np.float32).reshape(n, 4)      # (S_i, 0) per particle
+    o += a16(16 * n)
+    out["spos"] = raw[o:o + 2 * nnz].view(np.uint16)                      # staging position per distinct neighbour
+    o += a16(2 * nnz)
+    out["sinv"] = raw[o:o + 2 * nnz].view(np.uint16)                      # its inverse
     return out
+
+
+def _quarter_loads(slots):
+    """Per quarter warp (8 consecutive rows), the largest number of its pairs in one group
+    (position mod 8), summed over the tile's quarter warps."""
+    tot = 0
+    for q0 in range(0, len(slots), 8):
+        allp = np.concatenate([np.asarray(sl) % 8 for sl in slots[q0:q0 + 8]]) if slots[q0:q0 + 8] else []
+        if len(allp):
+            tot += np.bincount(allp, minlength=8).max()
+    return tot
 
 
 def test_tile_plan_is_exact(ctx):
@@ -210,7 +225,16 @@ def test_tile_plan_is_exact(ctx):
         assert P["tile_e"][b] == 128 * width
         so = P["tile_so"][b]
         assert P["tile_so"][b + 1] == so + 128 * width
-        slots = [lc[rp[i] - p0:rp[i + 1] - p0] for i in range(i0, i1)]
+        # staging positions: a permutation of the tile's distinct neighbours, sinv its inverse
+        spos = P["spos"][p0:p0 + u.size].astype(np.int64)
+        assert np.array_equal(np.sort(spos), np.arange(u.size))
+        assert np.array_equal(P["sinv"][p0 + spos], np.arange(u.size))
+        lists = [lc[rp[i] - p0:rp[i + 1] - p0] for i in range(i0, i1)]
+        slots = [spos[x] for x in lists]
+        if b < 40:
+            # the positions balance each quarter warp's pairs over the 8 groups at least as
+            # well as the list order does
+            assert _quarter_loads(slots) <= _quarter_loads(lists)
         orders = _bank_order(slots) if b < 12 else None
         for r in range(i1 - i0):
             i = i0 + r
@@ -222,15 +246,15 @@ def test_tile_plan_is_exact(ctx):
             w = OKer.wendland_dwdr(q * h, h, 3, None) / (q * h) * s["vol"][j] * dx
             # the entries are the row's pairs, each once: the slot says which
             got = ent[:, 3].view(np.int32)
-            o = np.array([np.flatnonzero(slots[r] == g)[0] for g in got], dtype=np.int64)
+            o = np.array([np.flatnonzero(lists[r] == g)[0] for g in got], dtype=np.int64)
             assert np.array_equal(np.sort(o), k)
             if orders is not None:
                 assert np.array_equal(o, orders[r])
             assert np.allclose(ent[:, :3].T, w[:, o], rtol=2e-6, atol=1e-6 * np.abs(w).max())
             pad = P["geo"][so + np.arange(lens[i], width) * 128 + r]
             assert np.all(pad == 0.0)
-            # the slot section repeats the entries' slots in the same sliced order
-            assert np.array_equal(P["slots"][so + k * 128 + r], got.astype(np.uint16))
+            # the slot section holds the entries' staging positions in the same sliced order
+            assert np.array_equal(P["slots"][so + k * 128 + r], spos[got].astype(np.uint16))
         ms.append(u.size)
         ps.append(p1 - p0)
     assert hdr[0] == max(ms) and hdr[1] == max(ps) and hdr[2] == lens.max()
