@@ -287,9 +287,12 @@ def _bench_tgv3d(api, inputs, ctx, steps, peak):
     out = {"workload": "3D Eulerian WCSPH Taylor-Green vortex, periodic cube 2*pi, 128^3 = 2,097,152 particles, "
                        "Re=1600, h=1.3dp, two-pass step, FP32+Kahan (and FP64)"}
     res = {}
+    vend = {}
     for kappa in (1.6, 2.0):
         case = inputs.tgv3d(n=128, kappa=kappa)
         sim, nnz, _ = _eulerian_case(api, ctx, case, api.SPH_FP32_KAHAN)
+        _, v_start = sim.fields()
+        ke0 = float(torch.sum(v_start * v_start))
         lanes, _ = sim.autotune(3)
         sim.step(3)
         ctx.timing(True, every=TIMER_EVERY)
@@ -303,6 +306,15 @@ def _bench_tgv3d(api, inputs, ctx, steps, peak):
         r = {"ms_per_step": ms / steps, "pair_interactions_per_s": 2 * nnz * steps / (ms * 1e-3), "nnz": nnz,
              "lanes": lanes, "pass_ms": {"momentum": tm / max(nm, 1), "continuity": tc / max(nc, 1)},
              "roofline": _roof(per_pass, dom_ms, peak)}
+        _, v_end = sim.fields()
+        vend[kappa] = v_end.clone()
+        # kinetic-energy decay rate over the run against the initial viscous rate 6 nu of the
+        # Taylor-Green field (an eigenfunction of the Laplacian with eigenvalue -3; the
+        # nonlinear term conserves energy), a closed form for early times
+        t_run = (3 + steps) * case["dt"]
+        nu = case["mu"] / case["rho0"]
+        rate = -math.log(float(torch.sum(v_end * v_end)) / ke0) / t_run
+        r["ke_decay"] = {"t": t_run, "rate_fit": rate, "rate_viscous_6nu": 6.0 * nu, "ratio": rate / (6.0 * nu)}
         if kappa == 1.6:
             d32, v32 = [t.clone() for t in sim.fields()]
             sim64, _, _ = _eulerian_case(api, ctx, case, api.SPH_FP64)
@@ -321,6 +333,11 @@ def _bench_tgv3d(api, inputs, ctx, steps, peak):
         del sim
     out.update(res)
     out["alpha_TW_over_SW"] = res["kappa_1.6"]["ms_per_step"] / res["kappa_2.0"]["ms_per_step"]
+    out["l2_v_tw_vs_sw"] = float(torch.linalg.norm(vend[1.6] - vend[2.0]) / torch.linalg.norm(vend[2.0]))
+    out["matched_accuracy_criterion"] = ("kinetic-energy decay rate of 1.6h within 10 % of 2h's, and the velocity "
+                                         "fields within 1e-3 relative L2 after the same steps")
+    k16, k20 = res["kappa_1.6"]["ke_decay"]["rate_fit"], res["kappa_2.0"]["ke_decay"]["rate_fit"]
+    out["matched_accuracy"] = bool(abs(k16 / k20 - 1.0) <= 0.1 and out["l2_v_tw_vs_sw"] <= 1e-3)
     return out
 
 
@@ -340,6 +357,104 @@ def _bench_tgv2d(api, inputs, ctx):
                                      "l2_v_vs_closed_form": float(torch.linalg.norm(v - exact) /
                                                                   torch.linalg.norm(exact))}
     out["matched_accuracy"] = (out["kappa_1.6"]["l2_v_vs_closed_form"] <= 1.1 * out["kappa_2.0"]["l2_v_vs_closed_form"])
+    # the same cases run on to t = 1: the velocity amplitude A(t) = sqrt(2 <|v|^2>)/U sampled
+    # every 50 steps and its decay rate fitted (least squares on log A) against the closed
+    # form's 8 pi^2 nu (Sec. 3.1's viscous cases; 200 steps reach only t = 0.118)
+    for kappa in (1.6, 2.0):
+        case = inputs.tgv2d(nx=50, kappa=kappa)
+        sim, nnz, oh = _eulerian_case(api, ctx, case, api.SPH_FP64)
+        nsteps = int(math.ceil(1.0 / case["dt"]))
+        ts, amp = [], []
+        done = 0
+        while True:
+            _, v = sim.fields()
+            ts.append(done * case["dt"])
+            amp.append(math.sqrt(2.0 * float(torch.mean(torch.sum(v * v, dim=0)))) / case["U"])
+            if done >= nsteps:
+                break
+            k = min(50, nsteps - done)
+            sim.step(k)
+            done += k
+        ts, amp = np.array(ts), np.array(amp)
+        rate = -np.polyfit(ts, np.log(amp), 1)[0]
+        t = done * case["dt"]
+        _, v = sim.fields()
+        exact = torch.tensor(inputs.tgv2d_exact_velocity(case["pos"][:, oh], case["U"], case["nu"], t),
+                             device=ctx.device)
+        out["kappa_%.1f" % kappa]["t1"] = {
+            "t": t, "steps": done, "decay_rate_fit": rate, "decay_rate_exact": case["decay_rate"],
+            "decay_rate_rel_err": rate / case["decay_rate"] - 1.0,
+            "l2_v_vs_closed_form": float(torch.linalg.norm(v - exact) / torch.linalg.norm(exact))}
+    out["matched_accuracy_t1"] = (out["kappa_1.6"]["t1"]["l2_v_vs_closed_form"]
+                                  <= 1.1 * out["kappa_2.0"]["t1"]["l2_v_vs_closed_form"])
+    out["matched_accuracy_criterion"] = "L2(v - closed form) at 1.6h <= 1.1 x the same at 2h, same dp"
+    return out
+
+
+def _bench_plate_accuracy(api, inputs, ctx, every=100):
+    """The headline plate at 1.6h and 2h (float32 + Kahan, tile plan) run to just past half
+    the Euler-Bernoulli first-mode period: the tip deflection history (mean u_y over the
+    tip face), its first maximum and zero crossing (period = twice the crossing time),
+    against the Euler-Bernoulli plate estimate, and the energy drift (float64 reduction)."""
+    import torch
+    c16 = inputs.plate(dp=0.001, kappa=1.6)
+    L, t = 0.2, 0.02
+    E, nu, rho0 = 2.0e6, 0.3975, c16["rho0"]
+    # first bending mode of a clamped-free plate strip (plate modulus E / (1 - nu^2))
+    omega = 1.875104068711961 ** 2 * math.sqrt(E * t * t / (12.0 * rho0 * (1.0 - nu * nu))) / (L * L)
+    T_eb = 2.0 * math.pi / omega
+    out = {"workload": "cantilever plate, dp=1 mm (816,000 particles), neo-Hookean, float32 + Kahan on the tile "
+                       "plan, run to 0.55 of the Euler-Bernoulli first period; tip = particles with x > L - dp/2",
+           "euler_bernoulli_period_s": T_eb, "euler_bernoulli_tip_amplitude_m": 0.05 * c16["c0"] / omega}
+    curves = {}
+    for kappa in (1.6, 2.0):
+        s = _setup_plate(api, inputs, ctx, kappa)
+        sol = _solid(api, ctx, s, api.SPH_FP32_KAHAN)
+        dt = s["c"]["dt"]
+        nsteps = int(math.ceil(0.55 * T_eb / dt))
+        tip = s["r0"][0] > L - 0.0005
+        e0 = sol.energy()
+        ts, uy = [], []
+        done = 0
+        t0 = time.perf_counter()
+        while True:
+            x, _, _ = sol.fields()
+            ts.append(done * dt)
+            uy.append(float(torch.mean((x[1] - s["r0"][1])[tip])))
+            if done >= nsteps:
+                break
+            k = min(every, nsteps - done)
+            sol.step(k)
+            done += k
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        e1 = sol.energy()
+        ts, uy = np.array(ts), np.array(uy)
+        imax = int(np.argmax(uy))
+        cross = None
+        for k in range(imax, len(uy) - 1):
+            if uy[k] > 0.0 >= uy[k + 1]:
+                cross = ts[k] + (ts[k + 1] - ts[k]) * uy[k] / (uy[k] - uy[k + 1])
+                break
+        curves[kappa] = uy
+        out["kappa_%.1f" % kappa] = {
+            "steps": done, "t_end_s": done * dt, "wall_s_with_readbacks": wall,
+            "tip_max_m": float(uy[imax]), "t_tip_max_s": float(ts[imax]),
+            "t_zero_crossing_s": cross, "period_estimate_s": None if cross is None else 2.0 * cross,
+            "period_vs_euler_bernoulli": None if cross is None else 2.0 * cross / T_eb,
+            "energy_start_J": list(e0), "energy_end_J": list(e1),
+            "energy_drift_rel": (sum(e1) - sum(e0)) / sum(e0)}
+        del sol, s
+        torch.cuda.empty_cache()
+    a, b = curves[1.6], curves[2.0]
+    m = min(len(a), len(b))
+    out["tip_curve_rel_diff_max"] = float(np.max(np.abs(a[:m] - b[:m])) / np.max(np.abs(b[:m])))
+    p16, p20 = out["kappa_1.6"]["period_estimate_s"], out["kappa_2.0"]["period_estimate_s"]
+    out["period_rel_diff_tw_vs_sw"] = None if (p16 is None or p20 is None) else p16 / p20 - 1.0
+    out["matched_accuracy_criterion"] = ("tip deflection curves of 1.6h and 2h within 5 % of the 2h amplitude and "
+                                         "their periods within 2 %")
+    out["matched_accuracy"] = bool(out["tip_curve_rel_diff_max"] <= 0.05 and p16 is not None and p20 is not None
+                                   and abs(p16 / p20 - 1.0) <= 0.02)
     return out
 
 
@@ -978,6 +1093,7 @@ def run_gpu(args):
         bf16 = peaks.get("bf16_tflops", 1900.0)
         for name, fn in (("tgv3d_128", lambda: _bench_tgv3d(api, inputs, ctx, args.other_steps, peak)),
                          ("tgv2d_50_plain_fp64", lambda: _bench_tgv2d(api, inputs, ctx)),
+                         ("plate_matched_accuracy", lambda: _bench_plate_accuracy(api, inputs, ctx)),
                          ("batched_64_tgv2d", lambda: _bench_batched(api, inputs, ctx, args.other_steps, peak)),
                          ("relax_8spheres_dp128", lambda: _bench_relax(api, inputs, ctx, 50, peak)),
                          ("error_analysis_circle", lambda: _bench_error_analysis(api, inputs, ctx)),

@@ -494,6 +494,15 @@ int sph_tlsph_load32(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_
                      const float* u, const float* v, const float* H, void* stream);
 int sph_tlsph_store32(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_state* st,
                       float* u, float* v, float* H, void* stream);
+/* Energies of the float64 state (v, H; after float32 steps call sph_tlsph_unpack
+ * first): out_host[0] = kinetic sum_i rho0 V0_i |v_i|^2 / 2, out_host[1] = stored
+ * sum_i V0_i psi(F_i) with the law's stored-energy density (the potential of the
+ * stress of Sec. 3.2: SVK psi = lambda/2 (tr E)^2 + G E:E, neo-Hookean
+ * psi = G/2 (tr C - d) - G ln J + lambda/2 (ln J)^2).  Reduced in float64 in a fixed
+ * order (deterministic).  Synchronises the stream; SPH_ERR_NONFINITE when a sum is
+ * not finite. */
+int sph_tlsph_energy(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_state* st,
+                     double* out_host, void* stream);
 /* Rates at the current state: dvdt float64 [dim][n] (Eq. 30 / rho0) and
  * dFdt float64 [dim*dim][n] (Eq. 31 with the current v). */
 int sph_tlsph_rates(sph_ctx* ctx, const sph_tlsph_params* prm,

@@ -440,6 +440,15 @@ class TLSolid:
         self._call("sph_autotune_tlsph", int(trial_steps), ctypes.byref(lanes), ctypes.byref(ms), _stream())
         return lanes.value, ms.value
 
+    def energy(self):
+        """(kinetic, stored) energy of the float64 state in float64 (sph_tlsph_energy);
+        unpacks first after float32 steps."""
+        if self.prm.precision == SPH_FP32_KAHAN:
+            self.unpack()
+        out = (ctypes.c_double * 2)()
+        self._call("sph_tlsph_energy", out, _stream())
+        return out[0], out[1]
+
     def rates(self):
         d = self.dim
         dvdt = torch.empty((d, self.n), dtype=torch.float64, device=self.ctx.device)

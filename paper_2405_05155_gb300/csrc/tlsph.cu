@@ -2248,6 +2248,120 @@ extern "C" int sph_tlsph_unpack(sph_ctx* ctx, const sph_tlsph_params* p, const s
     return sph_take_timeout(ctx, s);
 }
 
+// Kinetic and stored energy of the float64 state, reduced in float64 in a fixed order:
+// per block a tree over its 256 particles, then one block over the partials.
+// psi: neo-Hookean G/2 (tr C - d) - G ln J + lambda/2 (ln J)^2 (the energy of
+// S = G (I - C^-1) + lambda ln J C^-1), SVK lambda/2 (tr E)^2 + G E:E (Eq. 29's law).
+template <int DIM>
+__global__ void k_tl_energy(const double* __restrict__ V0, const double* __restrict__ v,
+                            const double* __restrict__ H, int64_t n, double rho0, double lam, double G, int law,
+                            double* __restrict__ partial) {
+    __shared__ double sh[2][256];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double ke = 0.0, pe = 0.0;
+    if (i < n) {
+        double F[DIM][DIM], C[DIM][DIM];
+        for (int a = 0; a < DIM; ++a)
+            for (int b = 0; b < DIM; ++b) F[a][b] = (a == b ? 1.0 : 0.0) + H[(a * DIM + b) * n + i];
+        double vv = 0.0;
+        for (int a = 0; a < DIM; ++a) vv += v[a * n + i] * v[a * n + i];
+        for (int a = 0; a < DIM; ++a)
+            for (int b = 0; b < DIM; ++b) {
+                double c = 0.0;
+                for (int k = 0; k < DIM; ++k) c += F[k][a] * F[k][b];
+                C[a][b] = c;
+            }
+        double psi;
+        if (law == SPH_NEO_HOOKEAN) {
+            double J = DIM == 2 ? F[0][0] * F[1][1] - F[0][1] * F[1][0]
+                                : F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
+                                      F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
+                                      F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+            double trC = 0.0;
+            for (int a = 0; a < DIM; ++a) trC += C[a][a];
+            const double lnJ = log(J);
+            psi = 0.5 * G * (trC - DIM) - G * lnJ + 0.5 * lam * lnJ * lnJ;
+        } else {
+            double trE = 0.0, EE = 0.0;
+            for (int a = 0; a < DIM; ++a)
+                for (int b = 0; b < DIM; ++b) {
+                    const double e = 0.5 * (C[a][b] - (a == b ? 1.0 : 0.0));
+                    EE += e * e;
+                    if (a == b) trE += e;
+                }
+            psi = 0.5 * lam * trE * trE + G * EE;
+        }
+        ke = 0.5 * rho0 * V0[i] * vv;
+        pe = V0[i] * psi;
+    }
+    sh[0][threadIdx.x] = ke;
+    sh[1][threadIdx.x] = pe;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = sh[0][0];
+        partial[2 * blockIdx.x + 1] = sh[1][0];
+    }
+}
+
+__global__ void k_tl_energy_sum(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+    __shared__ double sh[2][256];
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        a += partial[2 * k];
+        b += partial[2 * k + 1];
+    }
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sh[0][0];
+        out[1] = sh[1][0];
+    }
+}
+
+extern "C" int sph_tlsph_energy(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st, double* out_host,
+                                void* stream) {
+    if (!ctx || !out_host) return SPH_ERR_ARG;
+    int r = check_tl(p, st);
+    if (r) return r;
+    out_host[0] = out_host[1] = 0.0;
+    const int64_t n = p->dom.n;
+    if (n == 0) return SPH_OK;
+    if (!st->v || !st->H || !st->V0) return SPH_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    const int nb = (int)grid_for(n, 256);
+    double* partial = (double*)sph_scratch(ctx, S_RED_PARTIAL, (size_t)nb * 16 + 64, &r);
+    if (r) return r;
+    double* out_d = partial + 2 * (size_t)nb;
+    if (p->dom.dim == 2)
+        k_tl_energy<2><<<nb, 256, 0, s>>>(st->V0, st->v, st->H, n, p->rho0, p->lambda, p->G, p->law, partial);
+    else
+        k_tl_energy<3><<<nb, 256, 0, s>>>(st->V0, st->v, st->H, n, p->rho0, p->lambda, p->G, p->law, partial);
+    k_tl_energy_sum<<<1, 256, 0, s>>>(partial, nb, out_d);
+    SPH_LAUNCH_CHECK(ctx);
+    double* hp = (double*)ctx->pinned;
+    SPH_CUDA(ctx, cudaMemcpyAsync(hp + 48, out_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(ctx, cudaStreamSynchronize(s));
+    if (!isfinite(hp[48]) || !isfinite(hp[49])) return SPH_ERR_NONFINITE;
+    out_host[0] = hp[48];
+    out_host[1] = hp[49];
+    return SPH_OK;
+}
+
 extern "C" int sph_tlsph_rates(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st, double* dvdt,
                                double* dFdt, void* stream) {
     if (!ctx) return SPH_ERR_ARG;

@@ -26,6 +26,14 @@ def rel_max(a, ref):
     return float(np.max(np.abs(a - ref)) / (den if den > 0 else 1.0))
 
 
+def rel_elem(a, ref, floor=1e-3):
+    """Element-wise relative error, each element against |ref| plus `floor` times the
+    field's largest magnitude (entries that cancel to near zero keep an absolute bound)."""
+    den = np.abs(ref) + floor * np.max(np.abs(ref))
+    den = np.where(den > 0, den, 1.0)
+    return float(np.max(np.abs(a - ref) / den))
+
+
 def rel_l2(a, ref):
     """Relative L2 error (Eq. 10 form), the float32 parity measure."""
     den = np.linalg.norm(ref)

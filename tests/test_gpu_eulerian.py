@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import OracleLists, cuda, host, odom, oracle_rows, rel_l2, rel_max, sample_rows, sorted_by_cells
+from helpers import OracleLists, cuda, host, odom, oracle_rows, rel_elem, rel_l2, rel_max, sample_rows, sorted_by_cells
 from oracle import eulerian as OE
 from oracle import kgc as OK
 from oracle import neighbors as ON
@@ -126,6 +126,27 @@ def test_steps_3d_both_integrators(ctx, integrator):
         sim.step(7)
         dr, v = sim.fields()
         assert err(host(dr), run[0]) < tol and err(host(v), run[1]) < tol
+
+
+def test_tgv3d_32_cubed_twenty_steps(ctx):
+    # the 3D Taylor-Green case at 32^3 (Re = 1600, 1.6h) over 20 two-pass steps: float64
+    # within 1e-12 normwise and element by element (each element against its own size down
+    # to 1e-3 of the field's), float32 + Kahan on the tile plan within 1e-5 relative L2
+    case = inputs.tgv3d(n=32, kappa=1.6)
+    s = _setup(ctx, case)
+    d_o, v_o = OE.run(s["pos"], s["vol"], s["drho"], s["v"], s["B_h"], s["rp_h"], s["col_h"], s["prm"], 20)
+    sim = _sim(ctx, s, case, api.SPH_FP64)
+    sim.step(20)
+    dr, v = sim.fields()
+    dr, v = host(dr), host(v)
+    assert rel_max(dr, d_o) < 1e-12 and rel_max(v, v_o) < 1e-12
+    assert rel_elem(dr, d_o) < 1e-10 and rel_elem(v, v_o) < 1e-10, (rel_elem(dr, d_o), rel_elem(v, v_o))
+    sim = _sim(ctx, s, case, api.SPH_FP32_KAHAN)
+    sim.step(20)
+    dr, v = sim.fields()
+    assert rel_l2(host(v), v_o) < 1e-5
+    # the change of the density offset over the run (the offset itself is small and smooth)
+    assert rel_l2(host(dr) - s["drho"], d_o - s["drho"]) < 1e-4
 
 
 @pytest.mark.parametrize("lanes", [1, 2, 4, 8])

@@ -348,6 +348,28 @@ def test_long_rows_against_the_oracle(ctx):
         assert err(host(H), H_o) < tol, (prec, tiles, err(host(H), H_o))
 
 
+@pytest.mark.parametrize("law", [OT.SVK, OT.NEO_HOOKEAN])
+def test_energy_against_the_oracle(ctx, law):
+    # kinetic and stored energy of a strained, moving state: float64 reduction at 1e-12
+    s = _setup(ctx, law=law)
+    n = s["r0"].shape[1]
+    rng = np.random.default_rng(4)
+    H = 0.02 * rng.normal(size=(9, n))
+    v = s["v"] + 0.1 * rng.normal(size=s["v"].shape)
+    ke_o, pe_o = OT.energies(s["r0"], s["vol"], v, _F_from_H(H), s["prm"])
+    sol = _solid(ctx, s, api.SPH_FP64, law, v=v, H=H)
+    ke, pe = sol.energy()
+    assert abs(ke - ke_o) <= 1e-12 * ke_o and abs(pe - pe_o) <= 1e-12 * pe_o
+    # a few steps later the float32 form's energy (read through its float64 unpack) stays
+    # within float32 accuracy of the float64 run's
+    a = _solid(ctx, s, api.SPH_FP64, law)
+    b = _solid(ctx, s, api.SPH_FP32_KAHAN, law)
+    a.step(20)
+    b.step(20)
+    ea, eb = a.energy(), b.energy()
+    assert abs(sum(ea) - sum(eb)) <= 1e-5 * sum(ea)
+
+
 def test_linear_field_and_momentum_invariants(ctx):
     s = _setup(ctx)
     n = s["r0"].shape[1]
