@@ -828,11 +828,16 @@ def _bench_relax_learned(api, inputs, ctx, train_bodies=200, train_steps=4000, t
     torch.cuda.empty_cache()
     b, prm32, pos0, vol = learned.body_on_device(ctx, 0, 1.0 / 128.0)
     prm64 = api.relax_params(b["domain"], b["spheres"], b["dp"], precision=api.SPH_FP64, n=pos0.shape[1])
+    # the judge: the residual from float32 pair sums (float64 reduction), every 10 plain steps;
+    # the target is what plain float32 relaxation reaches after target_steps steps, judged
+    # the same way
     ref = pos0.clone()
-    api.relax_step(ctx, prm32, ref, vol, target_steps)
-    target = api.relax_residual(ctx, prm32, ref, vol)[0]
-    r_start = api.relax_residual(ctx, prm32, pos0, vol)[0]
+    api.relax_run(ctx, prm32, ref, vol, 0.0, target_steps, check_every=target_steps, judge=api.SPH_FP32_KAHAN)
+    target = api.relax_residual_fp32(ctx, prm32, ref, vol)[0]
+    r_start = api.relax_residual_fp32(ctx, prm32, pos0, vol)[0]
     del ref
+    judge_ms = _event_ms(lambda: api.relax_residual_fp32(ctx, prm32, pos0, vol))
+    judge64_ms = _event_ms(lambda: api.relax_residual(ctx, prm32, pos0, vol))
     arms = {}
     for name, prm, proposal in (("plain_fp32", prm32, None), ("learned_fp32", prm32, trainer.params),
                                 ("plain_fp64", prm64, None)):
@@ -840,7 +845,7 @@ def _bench_relax_learned(api, inputs, ctx, train_bodies=200, train_steps=4000, t
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         out = api.relax_run(ctx, prm, p, vol, target, 20 * target_steps, proposal=proposal, applications=3,
-                            plain_between=10, check_every=10)
+                            plain_between=10, check_every=10, judge=api.SPH_FP32_KAHAN)
         torch.cuda.synchronize()
         out["ms"] = (time.perf_counter() - t0) * 1e3
         arms[name] = out
@@ -851,7 +856,8 @@ def _bench_relax_learned(api, inputs, ctx, train_bodies=200, train_steps=4000, t
                         "steps; residual checked every 10 plain steps" % (train_bodies, rows, train_steps,
                                                                            int(pos0.shape[1]), target_steps),
             "training_data_s": t_data, "training_s": t_train, "loss": losses, "residual_start": r_start,
-            "residual_target": target, "arms": arms,
+            "residual_target": target, "judge": "sph_relax_residual_fp32 (float32 pair sums, float64 reduction)",
+            "judge_ms": judge_ms, "float64_residual_ms": judge64_ms, "arms": arms,
             "speedup_learned_vs_plain_fp32": arms["plain_fp32"]["ms"] / arms["learned_fp32"]["ms"],
             "speedup_learned_vs_plain_fp64": arms["plain_fp64"]["ms"] / arms["learned_fp32"]["ms"]}
 

@@ -557,6 +557,14 @@ int sph_set_relax_skin(sph_ctx* ctx, double skin_over_h);
  * build + pair pass). */
 int sph_relax_accel(sph_ctx* ctx, const sph_relax_params* prm, const double* pos,
                     const double* vol, double* acc, void* stream);
+/* The residual out_host[0] of sph_relax_residual (Laguerre-Gauss) from float32 pair
+ * sums: one float32 acceleration evaluation (the cell sweep of SPH_FP32_KAHAN, with
+ * compensated sums) gives sum_j grad W_ij V_j = -a_i rho/(2 p0) for every particle with
+ * phi < -2h, where the surface term of Eq. 7 vanishes; h^2 |.|^2 and the count are reduced
+ * in float64 in a fixed order.  out_host[1] = NaN (the truncated-kernel residual is not
+ * formed), out_host[2] = the count.  3D, Laguerre-Gauss kernel.  Synchronises the stream. */
+int sph_relax_residual_fp32(sph_ctx* ctx, const sph_relax_params* prm, const double* pos,
+                            const double* vol, double* out_host, void* stream);
 /* Relaxation residual over particles with phi < -2h:
  * out_host[0] = sqrt(mean |h sum_j grad W^LG_ij V_j|^2),
  * out_host[1] = the same with the truncated Wendland kernel (cut-off 1.6h),
@@ -722,8 +730,11 @@ int sph_mlp_train(sph_ctx* ctx, float* params, float* adam_m, float* adam_v, int
  * check_every steps) then finish the run, until the target or max_steps plain steps.  If
  * the target is still missed, plain relaxation is the fallback: pos is reset to its
  * value at the call and relaxed plainly (up to max_steps), and that is the result.
- * Without a proposal (applications = 0) it is the plain run alone.  Synchronises the
- * stream (every residual check). */
+ * Without a proposal (applications = 0) it is the plain run alone.  judge selects the
+ * residual that decides: SPH_FP64 (sph_relax_residual) or SPH_FP32_KAHAN
+ * (sph_relax_residual_fp32, the float32 pair sums with a float64 reduction); the
+ * result's residual[] is always sph_relax_residual's.  Synchronises the stream (every
+ * residual check). */
 typedef struct {
     const float* proposal;          /* MLP parameters, float32 [SPH_MLP_NPARAM] on the device; may be NULL
                                        when applications = 0 */
@@ -732,6 +743,8 @@ typedef struct {
     int32_t check_every;            /* plain steps between residual checks, >= 1 */
     int32_t applications;           /* proposal applications, >= 0 */
     int32_t plain_between;          /* plain steps after each kept proposal, >= 0 */
+    int32_t judge;                  /* SPH_FP64 or SPH_FP32_KAHAN: the residual that decides */
+    int32_t reserved;
 } sph_relax_run_params;
 typedef struct {
     int32_t steps;                  /* plain steps of the run whose result is returned */
@@ -740,7 +753,8 @@ typedef struct {
     int32_t reached;                /* 1 when the final residual is <= target */
     int32_t fell_back;              /* 1 when the result is the plain fallback run */
     int32_t steps_before_fallback;  /* plain steps of the abandoned learned run */
-    double residual[3];             /* final sph_relax_residual output */
+    double residual[3];             /* final sph_relax_residual output (float64) */
+    double judged;                  /* the final residual as the judge evaluated it */
 } sph_relax_run_result;
 int sph_relax_run(sph_ctx* ctx, const sph_relax_params* prm, double* pos, const double* vol,
                   const sph_relax_run_params* rp, sph_relax_run_result* result_host, void* stream);

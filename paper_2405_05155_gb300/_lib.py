@@ -74,12 +74,12 @@ class RelaxParams(ctypes.Structure):
 
 class RelaxRunParams(ctypes.Structure):
     _fields_ = [("proposal", c_vp), ("target", c_dbl), ("max_steps", c_i32), ("check_every", c_i32),
-                ("applications", c_i32), ("plain_between", c_i32)]
+                ("applications", c_i32), ("plain_between", c_i32), ("judge", c_i32), ("reserved", c_i32)]
 
 
 class RelaxRunResult(ctypes.Structure):
     _fields_ = [("steps", c_i32), ("proposals_kept", c_i32), ("proposals_rejected", c_i32), ("reached", c_i32),
-                ("fell_back", c_i32), ("steps_before_fallback", c_i32), ("residual", c_dbl * 3)]
+                ("fell_back", c_i32), ("steps_before_fallback", c_i32), ("residual", c_dbl * 3), ("judged", c_dbl)]
 
 
 class CompressibleParams(ctypes.Structure):
@@ -133,6 +133,7 @@ _SIGNATURES = {
     "sph_mlp_train_step": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_vp, c_vp, c_i64, _P(c_dbl),
                                           c_vp]),
     "sph_relax_propose": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, c_vp]),
+    "sph_relax_residual_fp32": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, c_vp, c_vp]),
     "sph_relax_samples": (ctypes.c_int, [c_vp, _P(RelaxParams), c_vp, c_vp, ctypes.c_int, ctypes.c_int, c_vp, c_vp,
                                          c_vp]),
     "sph_mlp_train": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, c_dbl, c_vp, c_vp, c_i64, c_i64, ctypes.c_int,

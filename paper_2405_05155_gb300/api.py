@@ -584,8 +584,18 @@ def relax_samples(ctx, prm, pos, vol, snapshots, every):
     return feats, targets
 
 
+def relax_residual_fp32(ctx, prm, pos, vol):
+    """The Laguerre-Gauss residual from float32 pair sums (sph_relax_residual_fp32):
+    (residual, count)."""
+    prm.dom.n = pos.shape[1]
+    out = (ctypes.c_double * 3)()
+    L.check("sph_relax_residual_fp32", ctx.lib.sph_relax_residual_fp32(ctx.h, ctypes.byref(prm), _p(pos), _p(vol),
+                                                                        out, _stream()), ctx.h)
+    return out[0], int(out[2])
+
+
 def relax_run(ctx, prm, pos, vol, target, max_steps, proposal=None, applications=3, plain_between=10,
-              check_every=10):
+              check_every=10, judge=SPH_FP64):
     """Relaxation of pos (in place) to the residual target (sph_relax_run): with a proposal,
     judged by the residual, plain relaxation finishing the run and as the fallback.
     Returns the sph_relax_run_result fields as a dict."""
@@ -596,12 +606,14 @@ def relax_run(ctx, prm, pos, vol, target, max_steps, proposal=None, applications
     rp.max_steps, rp.check_every = int(max_steps), int(check_every)
     rp.applications = int(applications) if proposal is not None else 0
     rp.plain_between = int(plain_between)
+    rp.judge = int(judge)
     out = L.RelaxRunResult()
     L.check("sph_relax_run", ctx.lib.sph_relax_run(ctx.h, ctypes.byref(prm), _p(pos), _p(vol), ctypes.byref(rp),
                                                     ctypes.byref(out), _stream()), ctx.h)
     return {"steps": out.steps, "kept": out.proposals_kept, "rejected": out.proposals_rejected,
             "reached": bool(out.reached), "fell_back": bool(out.fell_back),
-            "steps_before_fallback": out.steps_before_fallback, "residual": list(out.residual)}
+            "steps_before_fallback": out.steps_before_fallback, "residual": list(out.residual),
+            "judged": out.judged}
 
 
 def relax_propose(ctx, prm, params, pos):

@@ -110,10 +110,16 @@ extern "C" int sph_relax_run(sph_ctx* ctx, const sph_relax_params* p, double* po
     const int64_t n = p->dom.n;
     if (n < 0) return SPH_ERR_ARG;
     if (n > 0 && (!pos || !vol)) return SPH_ERR_ARG;
+    if (rp->judge != SPH_FP64 && rp->judge != SPH_FP32_KAHAN) return SPH_ERR_ARG;
     cudaStream_t s = as_stream(stream);
     *out = sph_relax_run_result{};
+    // the residual that judges: float64 throughout, or from the float32 pair sums
+    auto judge = [&](double* r) {
+        return rp->judge == SPH_FP64 ? sph_relax_residual(ctx, p, pos, vol, r, stream)
+                                     : sph_relax_residual_fp32(ctx, p, pos, vol, r, stream);
+    };
     double r3[3] = {0.0, 0.0, 0.0};
-    int st = sph_relax_residual(ctx, p, pos, vol, r3, stream);
+    int st = judge(r3);
     if (st) return st;
     const size_t bytes = (size_t)n * p->dom.dim * 8;
     double* start = nullptr;
@@ -134,7 +140,7 @@ extern "C" int sph_relax_run(sph_ctx* ctx, const sph_relax_params* p, double* po
             if (e) return e;
             done += k;
             out->steps += k;
-            e = sph_relax_residual(ctx, p, pos, vol, r3, stream);
+            e = judge(r3);
             if (e) return e;
         }
         return SPH_OK;
@@ -147,7 +153,7 @@ extern "C" int sph_relax_run(sph_ctx* ctx, const sph_relax_params* p, double* po
         if (st) return st;
         st = sph_take_status(ctx, stream);      // the fused forward's bounded waits
         if (st) return st;
-        st = sph_relax_residual(ctx, p, pos, vol, r3, stream);
+        st = judge(r3);
         if (st) return st;
         if (!(r3[0] < before[0])) {
             // the residual judges the proposal: undo it and go on with plain relaxation
@@ -170,12 +176,16 @@ extern "C" int sph_relax_run(sph_ctx* ctx, const sph_relax_params* p, double* po
         out->fell_back = 1;
         out->steps_before_fallback = out->steps;
         out->steps = 0;
-        st = sph_relax_residual(ctx, p, pos, vol, r3, stream);
+        st = judge(r3);
         if (st) return st;
         st = plain(rp->max_steps);
         if (st) return st;
     }
     out->reached = r3[0] <= rp->target ? 1 : 0;
+    out->judged = r3[0];
+    // the result's residual in float64 (both kernels)
+    st = sph_relax_residual(ctx, p, pos, vol, r3, stream);
+    if (st) return st;
     for (int k = 0; k < 3; ++k) out->residual[k] = r3[k];
     return SPH_OK;
 }

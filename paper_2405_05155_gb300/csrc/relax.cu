@@ -1160,6 +1160,84 @@ extern "C" int sph_relax_accel(sph_ctx* ctx, const sph_relax_params* p, const do
     return SPH_OK;
 }
 
+// The Laguerre-Gauss residual from the float32 pair sums: for a particle with
+// phi < -2h the surface term of Eq. 7 vanishes (its support lies inside the body), so
+// sum_j grad W_ij V_j = -a_i / scale with a_i the float32 acceleration of one cell sweep
+// (compensated sums); h^2 |.|^2 and the count are reduced in float64 in a fixed order.
+__global__ void k_residual_from_acc(const float4* __restrict__ acc, const double* __restrict__ pos, int64_t n,
+                                    Spheres S, RelaxK K, double* __restrict__ partial) {
+    __shared__ double sh[2][256];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0, cnt = 0.0;
+    if (i < n) {
+        double xi[3] = {pos[i], pos[n + i], pos[2 * n + i]}, g[3];
+        if (sdf64<3>(S, xi, g) < -2.0 * K.h) {
+            const float4 a = acc[i];
+            const double sx = (double)a.x / K.scale, sy = (double)a.y / K.scale, sz = (double)a.z / K.scale;
+            e = K.h * K.h * (sx * sx + sy * sy + sz * sz);
+            cnt = 1.0;
+        }
+    }
+    sh[0][threadIdx.x] = e;
+    sh[1][threadIdx.x] = cnt;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[3 * blockIdx.x] = sh[0][0];
+        partial[3 * blockIdx.x + 1] = 0.0;
+        partial[3 * blockIdx.x + 2] = sh[1][0];
+    }
+}
+
+extern "C" int sph_relax_residual_fp32(sph_ctx* ctx, const sph_relax_params* p, const double* pos, const double* vol,
+                                       double* out_host, void* stream) {
+    if (!ctx || !out_host) return SPH_ERR_ARG;
+    int st = check_relax(p);
+    if (st) return st;
+    if (p->dom.dim != 3 || p->kernel != SPH_LAGUERRE_GAUSS) return SPH_ERR_ARG;
+    const int64_t n = p->dom.n;
+    out_host[0] = out_host[2] = 0.0;
+    out_host[1] = NAN;
+    if (n == 0) return SPH_OK;
+    if (!pos || !vol) return SPH_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    Spheres S = make_spheres(p);
+    RelaxK K = make_relax_consts(p);
+    st = ensure_gauss_legendre(ctx);
+    if (st) return st;
+    unsigned* amax = (unsigned*)sph_scratch(ctx, S_RELAX_AMAX, 64, &st);
+    float4* acc = (float4*)sph_scratch(ctx, S_RELAX_ACC, (size_t)n * 16, &st);
+    if (st) return st;
+    SPH_CUDA(ctx, cudaMemsetAsync(amax, 0, 64, s));
+    st = acc_cells(ctx, p, pos, vol, S, K, acc, amax, s);
+    if (st) return st;
+    const int nb = (int)grid_for(n, 256);
+    double* partial = (double*)sph_scratch(ctx, S_RED_PARTIAL, (size_t)nb * 3 * 8 + 64, &st);
+    if (st) return st;
+    double* out_d = partial + (size_t)nb * 3;
+    k_residual_from_acc<<<nb, 256, 0, s>>>(acc, pos, n, S, K, partial);
+    k_sum_partials<<<1, 256, 0, s>>>(partial, nb, out_d);
+    SPH_LAUNCH_CHECK(ctx);
+    double* hp = (double*)ctx->pinned;
+    SPH_CUDA(ctx, cudaMemcpyAsync(hp + 32, out_d, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    int* hf = (int*)ctx->pinned;
+    SPH_CUDA(ctx, cudaMemcpyAsync(hf, ctx->flags, FLAG_COUNT * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, FLAG_COUNT * sizeof(int), s));
+    SPH_CUDA(ctx, cudaStreamSynchronize(s));
+    if (hf[FLAG_BAD_INPUT]) return SPH_ERR_ARG;
+    const double m = hp[34];
+    if (!isfinite(hp[32])) return SPH_ERR_NONFINITE;
+    out_host[2] = m;
+    if (m > 0.0) out_host[0] = sqrt(hp[32] / m);
+    return SPH_OK;
+}
+
 extern "C" int sph_relax_residual(sph_ctx* ctx, const sph_relax_params* p, const double* pos, const double* vol,
                                   double* out_host, void* stream) {
     if (!ctx || !out_host) return SPH_ERR_ARG;
