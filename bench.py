@@ -125,8 +125,12 @@ def _setup_solid(api, ctx, c):
     vol = torch.tensor(c["vol"][oh], dtype=torch.float64, device=dev)
     rp, col = api.build_neighbors(ctx, d, r0)
     B0, fb, nfb = api.kgc(ctx, d, r0, vol, rp, col)
+    # inv: the position of each input particle in this case's cell order (the order depends
+    # on the cut-off, so fields of two cut-offs are compared through it)
+    inv = torch.empty_like(order)
+    inv[order] = torch.arange(order.numel(), device=order.device)
     return dict(c=c, d=d, r0=r0, vol=vol, rp=rp, col=col, B0=B0, v=c["v"][:, oh], fixed=c["fixed"][oh],
-                nnz=int(col.numel()), n=int(r0.shape[1]), nfb=nfb)
+                nnz=int(col.numel()), n=int(r0.shape[1]), nfb=nfb, inv=inv)
 
 
 def _solid(api, ctx, s, precision, tiles=True):
@@ -290,7 +294,7 @@ def _bench_tgv3d(api, inputs, ctx, steps, peak):
     vend = {}
     for kappa in (1.6, 2.0):
         case = inputs.tgv3d(n=128, kappa=kappa)
-        sim, nnz, _ = _eulerian_case(api, ctx, case, api.SPH_FP32_KAHAN)
+        sim, nnz, oh = _eulerian_case(api, ctx, case, api.SPH_FP32_KAHAN)
         _, v_start = sim.fields()
         ke0 = float(torch.sum(v_start * v_start))
         lanes, _ = sim.autotune(3)
@@ -307,7 +311,9 @@ def _bench_tgv3d(api, inputs, ctx, steps, peak):
              "lanes": lanes, "pass_ms": {"momentum": tm / max(nm, 1), "continuity": tc / max(nc, 1)},
              "roofline": _roof(per_pass, dom_ms, peak)}
         _, v_end = sim.fields()
-        vend[kappa] = v_end.clone()
+        inv = torch.empty(len(oh), dtype=torch.int64, device=v_end.device)
+        inv[torch.as_tensor(oh, device=v_end.device)] = torch.arange(len(oh), device=v_end.device)
+        vend[kappa] = v_end[:, inv].clone()       # input order: each cut-off has its own cell order
         # kinetic-energy decay rate over the run against the initial viscous rate 6 nu of the
         # Taylor-Green field (an eigenfunction of the Laplacian with eigenvalue -3; the
         # nonlinear term conserves energy), a closed form for early times
@@ -412,7 +418,7 @@ def _bench_plate_accuracy(api, inputs, ctx, every=100):
         sol = _solid(api, ctx, s, api.SPH_FP32_KAHAN)
         dt = s["c"]["dt"]
         nsteps = int(math.ceil(0.55 * T_eb / dt))
-        tip = s["r0"][0] > L - 0.0005
+        tip = s["r0"][0] > L - 0.001          # the last layer, x = L - dp/2
         e0 = sol.energy()
         ts, uy = [], []
         done = 0
@@ -994,7 +1000,10 @@ def run_gpu(args):
     ctx.set_lanes(api.SPH_PASS_TLSPH, lanes20)
     ms20, _ = _time_steps(ctx, sol20, K, W, world)
     _, v20, H20 = sol20.fields()
-    tw_vs_sw = {"v": rl2(v32, v20), "H": rl2(H32, H20)}
+    # in the input order of the particles (each cut-off has its own cell order)
+    i16, i20 = s16["inv"], s20["inv"]
+    tw_vs_sw = {"v": rl2(v32[:, i16], v20[:, i20]), "H": rl2(H32[:, i16], H20[:, i20]),
+                "after_steps": K + W}
     del sol20
 
     # roofline of the dominant kernel
@@ -1129,10 +1138,11 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "lanes_per_particle": lanes16, "lanes_per_particle_2h": lanes20,
                        "launch_shape": ("tile plan: 128-row tiles, one thread per row, neighbours staged in "
-                                        "shared memory; momentum pass on float64-precomputed pair factors, "
-                                        "deformation pass %s" % ("evaluating grad0 W V0 from tile-relative staged "
-                                                                 "positions (SPH_PIPE_GEOM)" if pipe == "geom"
-                                                                 else "in pipeline mode '%s'" % pipe))
+                                        "shared memory; %s" % ("both passes evaluating grad0 W V0 from tile-relative "
+                                                               "staged positions, the momentum pass as M_i S_i + "
+                                                               "sum_j (V0_j M_j) g_ij (SPH_PIPE_GEOM)"
+                                                               if pipe == "geom"
+                                                               else "pipeline mode '%s'" % pipe))
                                        if planned else
                                        ("autotuned lanes (sph_autotune_tlsph)" if not args.lanes else "fixed lanes")},
             "kappa_2.0": {"ms_per_step": ms20 / K, "pair_interactions_per_s": 2 * s20["nnz"] * K / (ms20 * 1e-3),

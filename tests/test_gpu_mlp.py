@@ -35,6 +35,24 @@ def test_features_parity(ctx):
     assert np.array_equal(X[:, :96] == 0.0, X_o[:, :96] == 0.0)
 
 
+def test_features_parity_long_rows(ctx):
+    # twice the density (each particle with a shifted copy): rows of more than 128
+    # neighbours take the one-thread-per-particle ranking, the others the warp sort
+    b = inputs.sphere_body(4, 1.0 / 20.0)
+    p = np.concatenate([b["pos"], b["pos"] + 0.31 * b["dp"] * np.array([[1.0], [0.7], [0.4]])], axis=1)
+    pos, _ = sorted_by_cells(p, b["domain"])
+    dom = odom(b["domain"])
+    rp, col = ON.neighbors_cells(pos, dom.with_kappa(2.0))
+    lens = np.diff(rp)
+    assert lens.max() > 128 and lens.min() <= 128
+    phi, _ = OR.sdf_spheres(pos, b["spheres"])
+    X_o = OM.features(pos, rp, col, dom, phi)
+    prm = api.relax_params(b["domain"], b["spheres"], b["dp"])
+    X = host(api.mlp_features(ctx, prm, cuda(pos)))
+    assert np.max(np.abs(X - X_o)) < 1e-6 * max(1.0, np.max(np.abs(X_o)))
+    assert np.array_equal(X[:, :96] == 0.0, X_o[:, :96] == 0.0)
+
+
 def _batch(seed, rows):
     rng = np.random.default_rng(seed)
     X = np.zeros((rows, 128))
