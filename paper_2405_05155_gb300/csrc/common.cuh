@@ -60,7 +60,7 @@ enum ScratchSlot {
     S_CELL_ID = 0, S_CELL_COUNT, S_CELL_START, S_CELL_FILL, S_SORTED, S_P32SORTED,
     S_ROW_LEN, S_SCAN_BLOCKS, S_ABSMAX, S_RELAX_ROWPTR, S_RELAX_COL, S_RELAX_ACC,
     S_RELAX_AMAX, S_RED_PARTIAL, S_KGC_COUNT, S_MISC0, S_MISC1, S_MISC2, S_MISC3, S_BATCH, S_MLP_PARTS,
-    S_LEARN0, S_LEARN1, S_LEARN2, S_TL_VM
+    S_LEARN0, S_LEARN1, S_LEARN2
 };
 
 // device status words

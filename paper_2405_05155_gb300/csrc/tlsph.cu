@@ -293,21 +293,9 @@ __device__ __forceinline__ void store_M(float* RM, int64_t i, const float* m) {
     }
 }
 
-// 3D: the momentum pass's staging record of particle i, VM [n][16] =
-// (ox, oy, oz, cell | VM00, VM10, VM01, VM11 | VM02, VM12, VM20, VM21 | VM22, 0, 0, 0)
-// with VM = V0 M (rounded like the staging's own product): chunks 1-2 are the staged planes
-// as they are, so the momentum pass copies them into shared memory without a transform.
-__device__ __forceinline__ void store_VM(float* VM, int64_t i, const float* m, float V, float4 code) {
-    float4* r = reinterpret_cast<float4*>(VM + 16 * i);
-    r[0] = code;
-    r[1] = make_float4(V * m[0], V * m[3], V * m[1], V * m[4]);
-    r[2] = make_float4(V * m[2], V * m[5], V * m[6], V * m[7]);
-    r[3] = make_float4(V * m[8], 0.0f, 0.0f, 0.0f);
-}
-
 template <int DIM>
 __global__ void k_tl_stress32(const float* __restrict__ H, const float* __restrict__ B0, int64_t n, TLK<float> K,
-                              float* __restrict__ RM, float* __restrict__ VM, const float* __restrict__ RD) {
+                              float* __restrict__ RM) {
     constexpr int NS = DIM == 2 ? 3 : 6;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -316,10 +304,6 @@ __global__ void k_tl_stress32(const float* __restrict__ H, const float* __restri
     for (int s = 0; s < NS; ++s) b[s] = B0[s * n + i];
     stress_factor<DIM, float>(h, b, K, m);
     store_M<DIM>(RM, i, m);
-    if (DIM == 3 && VM) {
-        const float4* rd = reinterpret_cast<const float4*>(RD + 8 * i);
-        store_VM(VM, i, m, rd[1].w, rd[0]);
-    }
 }
 
 // One momentum pair (Eq. 30) from the neighbour's RM chunks: accumulates
@@ -578,8 +562,7 @@ __device__ __forceinline__ void defo_finish(const float* Lt, const float* b0, bo
                                             int64_t n, const TLK<float>& K, float* __restrict__ RM,
                                             float* __restrict__ H, float* __restrict__ u,
                                             double* __restrict__ dFdt, const float* hold = nullptr,
-                                            const float* uold = nullptr, float* __restrict__ VM = nullptr,
-                                            const float* me = nullptr) {
+                                            const float* uold = nullptr) {
     float Fd[DIM * DIM];
     times_b0<DIM, float>(Lt, b0, Fd);
     if (OUT == OUT_RATES) {
@@ -596,7 +579,6 @@ __device__ __forceinline__ void defo_finish(const float* Lt, const float* b0, bo
     for (int a = 0; a < DIM; ++a) u[a * n + i] = (uold ? uold[a] : u[a * n + i]) + K.dt * vi[a];
     stress_factor<DIM, float>(h, b0, K, m);
     store_M<DIM>(RM, i, m);
-    if (DIM == 3 && VM) store_VM(VM, i, m, me[7], make_float4(me[0], me[1], me[2], me[3]));
 }
 
 // Deformation-rate pass (Eq. 31) with the fused stress update of the next step,
@@ -687,7 +669,6 @@ struct GeoArgs {
     const uint16_t* spos;    // geometry form: staging position of each distinct neighbour (uidx order)
     const uint16_t* sinv;    // geometry form: the distinct neighbour at each staging position
     uint32_t test_polls;     // bulk form: > 0 issues no copy and waits this many polls (sph_set_wait_test)
-    float* vm;               // 3D geometry forms: the momentum pass's staging records (store_VM), or null
 };
 
 // The TL plan: the tile plan (tiles.cuh) with 16-byte entries, then the entries' slots
@@ -1125,30 +1106,6 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restr
                 jq[k] = q < m ? min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1) : -1;
                 pq[k] = q < m ? min((int)A.spos[P0 + q], m - 1) : 0;
             }
-            if (DIM == 3 && A.vm) {
-                // from the staging records: planes 1-2 copied as they are (cp.async), the
-                // position code and VM22 through registers, all four neighbours in one round
-                float4 c0[4];
-                float v22[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (jq[k] < 0) continue;
-                    const float* r = A.vm + 16 * jq[k];
-                    cp_async16(P1s + pq[k], r + 4);
-                    cp_async16(P2s + pq[k], r + 8);
-                    c0[k] = __ldg(reinterpret_cast<const float4*>(r));
-                    v22[k] = __ldg(r + 12);
-                }
-                cp_async_commit();
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (jq[k] < 0) continue;
-                    const float o[3] = {c0[k].x, c0[k].y, c0[k].z};
-                    float x[3];
-                    rel_to_ref<3>(o, __float_as_uint(c0[k].w), bref, K, x);
-                    P0s[pq[k]] = make_float4(x[0], x[1], x[2], v22[k]);
-                }
-            } else {
 #pragma unroll
             for (int k = 0; k < 4; k += 2) {
                 F8 ra[2], rb[2];
@@ -1173,10 +1130,9 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restr
                     }
                 }
             }
-            }
         }
     }
-    if (sslot || (DIM == 3 && A.vm)) cp_async_wait_all();
+    if (sslot) cp_async_wait_all();
     __syncthreads();
     // M_i S_i is the sums' first term, so M_i is not kept through the loop
     float xi[3] = {0.0f, 0.0f, 0.0f};
@@ -1511,8 +1467,7 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
     }
     float vi[3] = {me.v[4], me.v[5], me.v[6]};
     if (GEOM) own_row();
-    defo_finish<DIM, OUT>(Lt, b0, (bi & kFixedBit) != 0, vi, i, n, K, RM, H, u, dFdt, hold, uold, GEOM ? A.vm : nullptr,
-                          me.v);
+    defo_finish<DIM, OUT>(Lt, b0, (bi & kFixedBit) != 0, vi, i, n, K, RM, H, u, dFdt, hold, uold);
 }
 
 // ---------------------------------------------------------------- pack / unpack
@@ -2135,20 +2090,6 @@ void tl32(sph_ctx* ctx, int lanes, int which, int out, int64_t n, const sph_tlsp
     else tl32_lanes<DIM, false>(lanes, which, out, n, st, K, r1, r2, s);
 }
 
-// 3D geometry forms (boxes without periodic axes): the context buffer of the momentum
-// pass's staging records, written by the stress kernel and the deformation pass.
-int tl_staging_records(sph_ctx* ctx, TlPlan& ts, const TLK<float>& K, int64_t n, int dim, float** vm) {
-    *vm = nullptr;
-    if (dim != 3 || !ts.on || !ts.geom_mom || K.periodic) return SPH_OK;
-    int r = SPH_OK;
-    float* p = (float*)sph_scratch(ctx, S_TL_VM, (size_t)n * 64, &r);
-    if (r) return r;
-    ts.momr.vm = p;
-    ts.defo.vm = p;
-    *vm = p;
-    return SPH_OK;
-}
-
 bool fp32_ready(const sph_tlsph_state* st) { return st->rd && st->rm && st->H32 && st->u32 && st->B32; }
 bool fp64_ready(const sph_tlsph_state* st) { return st->x && st->v && st->H && st->M; }
 
@@ -2456,16 +2397,13 @@ extern "C" int sph_tlsph_rates(sph_ctx* ctx, const sph_tlsph_params* p, const sp
         if (!fp32_ready(st)) return SPH_ERR_ARG;
         TLK<float> K = make_tl_consts<float>(p);
         TlPlan ts = tl_plan(ctx, st, n, dim);
-        float* vm = nullptr;
-        r = tl_staging_records(ctx, ts, K, n, dim, &vm);
-        if (r) return r;
         int lanes = ctx->lanes[SPH_PASS_TLSPH];
         if (dim == 2) {
-            k_tl_stress32<2><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm, nullptr, st->rd);
+            k_tl_stress32<2><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm);
             tl32<2>(ctx, lanes, 0, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
             tl32<2>(ctx, lanes, 1, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
         } else {
-            k_tl_stress32<3><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm, vm, st->rd);
+            k_tl_stress32<3><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm);
             tl32<3>(ctx, lanes, 0, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
             tl32<3>(ctx, lanes, 1, OUT_RATES, n, st, K, ts, dvdt, dFdt, s);
         }
@@ -2513,13 +2451,10 @@ extern "C" int sph_tlsph_step(sph_ctx* ctx, const sph_tlsph_params* p, const sph
     if (!fp32_ready(st)) return SPH_ERR_ARG;
     TLK<float> K = make_tl_consts<float>(p);
     TlPlan ts = tl_plan(ctx, st, n, dim);
-    float* vm = nullptr;
-    r = tl_staging_records(ctx, ts, K, n, dim, &vm);
-    if (r) return r;
     int lanes = ctx->lanes[SPH_PASS_TLSPH];
     int t = sph_timer_begin(ctx, SPH_TIMER_TL_STRESS, s);
-    if (dim == 2) k_tl_stress32<2><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm, nullptr, st->rd);
-    else k_tl_stress32<3><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm, vm, st->rd);
+    if (dim == 2) k_tl_stress32<2><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm);
+    else k_tl_stress32<3><<<grid_for(n, 128), 128, 0, s>>>(st->H32, st->B32, n, K, st->rm);
     sph_timer_end(ctx, t, s);
     for (int k = 0; k < nsteps; ++k) {
         t = sph_timer_begin(ctx, SPH_TIMER_TL_MOMENTUM, s);
