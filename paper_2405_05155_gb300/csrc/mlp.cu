@@ -289,105 +289,12 @@ __device__ __forceinline__ double feat_d2(const double* xi, const double* __rest
     return d2;
 }
 
-// (d2, j) ordering of the ranking: d2 >= 0, so its bits order like its value.
-__device__ __forceinline__ bool feat_less(unsigned long long da, int ja, unsigned long long db, int jb) {
-    return da < db || (da == db && ja < jb);
-}
-
-// Features with one warp per particle, for rows of at most 128 neighbours: the lanes take
-// the row's neighbours four each, the 128 (d2, j) keys (missing ones +inf) are sorted
-// ascending by a bitonic network across the warp (element e = 32 k + lane in register k),
-// and lane L writes the L-th nearest's offset.  The same ranking and values as k_features.
-constexpr int kFeatWarpCap = 128;
-
-__global__ void __launch_bounds__(256) k_features_warp(const double* __restrict__ pos, int64_t n,
-                                                       const int64_t* __restrict__ row_ptr,
-                                                       const int32_t* __restrict__ col, FeatSpheres S, double inv_h,
-                                                       float* __restrict__ feats) {
-    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (i >= n) return;
-    const int64_t p0 = row_ptr[i];
-    const int len = (int)(row_ptr[i + 1] - p0);
-    if (len > kFeatWarpCap) return;       // left to k_features (long rows only)
-    const double xi[3] = {pos[i], pos[n + i], pos[2 * n + i]};
-    unsigned long long d[4];
-    int jj[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int e = 32 * k + lane;
-        if (e < len) {
-            jj[k] = col[p0 + e];
-            d[k] = (unsigned long long)__double_as_longlong(feat_d2(xi, pos, n, jj[k]));
-        } else {
-            jj[k] = 0x7FFFFFFF;
-            d[k] = 0x7FF0000000000000ull;     // +inf
-        }
-    }
-    // bitonic sort of the 128 elements, ascending
-#pragma unroll
-    for (int size = 2; size <= 128; size <<= 1) {
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride >= 32) {
-                const int ks = stride >> 5;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (k & ks) continue;
-                    const int e = 32 * k + lane;
-                    const bool up = (e & size) == 0;
-                    const int k2 = k | ks;
-                    const bool sw = up ? feat_less(d[k2], jj[k2], d[k], jj[k]) : feat_less(d[k], jj[k], d[k2], jj[k2]);
-                    if (sw) {
-                        const unsigned long long td = d[k];
-                        d[k] = d[k2];
-                        d[k2] = td;
-                        const int tj = jj[k];
-                        jj[k] = jj[k2];
-                        jj[k2] = tj;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int e = 32 * k + lane;
-                    const unsigned long long od = __shfl_xor_sync(0xFFFFFFFFu, d[k], stride);
-                    const int oj = __shfl_xor_sync(0xFFFFFFFFu, jj[k], stride);
-                    const bool up = (e & size) == 0;
-                    const bool lower = (lane & stride) == 0;     // this element has the smaller index
-                    // keep the smaller key at the lower index when sorting up, else the larger
-                    const bool other_less = feat_less(od, oj, d[k], jj[k]);
-                    const bool take = (up == lower) ? other_less : !other_less && !(od == d[k] && oj == jj[k]);
-                    if (take) {
-                        d[k] = od;
-                        jj[k] = oj;
-                    }
-                }
-            }
-        }
-    }
-    float* f = feats + i * NIN;
-    const int cnt = min(len, NNEIGH);
-    if (lane < cnt) {
-        const int j = jj[0];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) f[3 * lane + a] = (float)((pos[a * n + j] - xi[a]) * inv_h);
-    } else {
-        f[3 * lane] = f[3 * lane + 1] = f[3 * lane + 2] = 0.0f;
-    }
-    if (lane == 0) f[3 * NNEIGH] = (float)(sdf_union(S, xi, nullptr) * inv_h);
-    else f[3 * NNEIGH + lane] = 0.0f;      // 97 .. 127
-}
-
 // 32 nearest neighbours by (float64 squared distance, j), offsets / h, then phi / h, one
-// thread per particle (LONG_ONLY: rows longer than kFeatWarpCap, the rest written by
-// k_features_warp).
-template <bool LONG_ONLY>
+// thread per particle.
 __global__ void k_features(const double* __restrict__ pos, int64_t n, const int64_t* __restrict__ row_ptr,
                            const int32_t* __restrict__ col, FeatSpheres S, double inv_h, float* __restrict__ feats) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (LONG_ONLY && row_ptr[i + 1] - row_ptr[i] <= kFeatWarpCap) return;
     double xi[3] = {pos[i], pos[n + i], pos[2 * n + i]};
     double bd[NNEIGH];
     int bj[NNEIGH];
@@ -423,8 +330,7 @@ __global__ void k_features(const double* __restrict__ pos, int64_t n, const int6
 
 void launch_features(const double* pos, int64_t n, const int64_t* rp, const int32_t* cl, const FeatSpheres& S,
                      double inv_h, float* feats, cudaStream_t s) {
-    k_features_warp<<<grid_for(n * 32, 256), 256, 0, s>>>(pos, n, rp, cl, S, inv_h, feats);
-    k_features<true><<<grid_for(n, 128), 128, 0, s>>>(pos, n, rp, cl, S, inv_h, feats);
+    k_features<<<grid_for(n, 128), 128, 0, s>>>(pos, n, rp, cl, S, inv_h, feats);
 }
 
 // x += h * dx_pred, then projection to phi <= -dp/2

@@ -37,7 +37,7 @@ def test_features_parity(ctx):
 
 def test_features_parity_long_rows(ctx):
     # twice the density (each particle with a shifted copy): rows of more than 128
-    # neighbours take the one-thread-per-particle ranking, the others the warp sort
+    # neighbours, ranked like the short ones
     b = inputs.sphere_body(4, 1.0 / 20.0)
     p = np.concatenate([b["pos"], b["pos"] + 0.31 * b["dp"] * np.array([[1.0], [0.7], [0.4]])], axis=1)
     pos, _ = sorted_by_cells(p, b["domain"])
