@@ -965,9 +965,9 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32g(const float* __restr
 // evaluates its kernel gradient from them instead of streaming a 16-byte factor.  The block
 // stages, per distinct neighbour of its tile, the position relative to the cell of the
 // tile's first row and V0_j M_j (mom_stage: 3D three float4 planes, 2D a float4 and a
-// float2 plane), and copies the tile's slot block into shared memory while it stages, so
-// the pair loop reads shared memory only.  The own row's M_i, S_i and velocity are read
-// after the loop, to keep the registers live through it few.
+// float2 plane); the pair slots come from the plan's slot section.  Without a shared slot
+// block 8 blocks of 4 warps fit an SM (48 bytes per staged neighbour), which hides more of
+// the staging's latency than a slot read from shared memory saves.
 template <int DIM>
 __device__ __forceinline__ void mom_stage_rec(const F8& a, const F8& b, uint32_t bref, const TLK<float>& K, float4& p0,
                                               float4& p1, float4& p2) {
@@ -1054,7 +1054,7 @@ __device__ __forceinline__ void mom_pair_rel(float4 p0, float4 p1, float4 p2, co
 }
 
 template <int DIM, int OUT>
-__global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restrict__ RM, float* __restrict__ RD,
+__global__ void __launch_bounds__(kTileRows, 8) k_tl_mom32r(const float* __restrict__ RM, float* __restrict__ RD,
                                                             const int64_t* __restrict__ row_ptr, int64_t n,
                                                             TLK<float> K, GeoArgs A, double* __restrict__ dvdt) {
     constexpr int W = DIM == 3 ? 16 : 8;
@@ -1064,8 +1064,6 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restr
     float4* P1s = P0s + mc;
     float4* P2s = P1s + mc;                                   // 3D
     float2* P1h = reinterpret_cast<float2*>(P0s + mc);        // 2D
-    uint16_t* ssl = reinterpret_cast<uint16_t*>(
-        tl_smem + (DIM == 3 ? 48u * (unsigned)mc : 16u * (unsigned)mc + ((8u * (unsigned)mc + 15u) & ~15u)));
     // tiles in reverse: the deformation pass walks them forwards, so each pass starts on
     // the records the previous one touched last, still in L2
     const int64_t tile = gridDim.x - 1 - blockIdx.x;
@@ -1077,17 +1075,8 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restr
     const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
     const int m = A.tile_m[tile];
     const uint32_t bref = __float_as_uint(RM[W * i0 + DIM]);
-    // the tile's slot block (256 bytes per position) into shared memory, when the plan's
-    // longest row allows (A.ecap positions)
-    const int width = A.tile_e[tile] / kTileRows;
-    const bool sslot = width <= A.ecap;
-    if (sslot) {
-        const unsigned char* src = reinterpret_cast<const unsigned char*>(A.slots + A.tile_so[tile]);
-        const int chunks = width * (2 * kTileRows / 16);
-        for (int c = threadIdx.x; c < chunks; c += blockDim.x)
-            cp_async16(reinterpret_cast<unsigned char*>(ssl) + 16 * c, src + 16 * c);
-        cp_async_commit();
-    }
+    // pair slots are read from the plan's slot section (a warp reads 64 contiguous bytes per
+    // position): without a shared slot block the stage fits 8 blocks per SM
     const bool staged = m <= mc;
     // the own record and S_i are requested first: their latency overlaps the staging
     const F8 a0 = ldg8(RM + W * ii);
@@ -1132,7 +1121,6 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restr
             }
         }
     }
-    if (sslot) cp_async_wait_all();
     __syncthreads();
     // M_i S_i is the sums' first term, so M_i is not kept through the loop
     float xi[3] = {0.0f, 0.0f, 0.0f};
@@ -1157,10 +1145,9 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restr
     }
     const int mlast = max(m - 1, 0);
     const uint16_t* gsl = A.slots + A.tile_so[tile] + threadIdx.x;
-    if (staged && sslot) {
+    if (staged) {
         // pairs in blocks of two: each block's terms summed with one rounding per product,
         // then added to the compensated sums
-        const uint16_t* sl = ssl + threadIdx.x;
         auto planes = [&](int s, float4& p0, float4& p1, float4& p2) {
             p0 = P0s[s];
             if (DIM == 3) {
@@ -1175,7 +1162,8 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restr
         int k = 0;
 #pragma unroll 2
         for (; k + 1 < len; k += 2) {
-            const int s0 = min((int)sl[k * kTileRows], mlast), s1 = min((int)sl[(k + 1) * kTileRows], mlast);
+            const int s0 = min((int)__ldg(gsl + (int64_t)k * kTileRows), mlast);
+            const int s1 = min((int)__ldg(gsl + (int64_t)(k + 1) * kTileRows), mlast);
             float4 a0, a1, a2, b0, b1, b2;
             planes(s0, a0, a1, a2);
             planes(s1, b0, b1, b2);
@@ -1187,7 +1175,7 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restr
             if (DIM == 3) acc2.add(t2);
         }
         if (k < len) {
-            const int s0 = min((int)sl[k * kTileRows], mlast);
+            const int s0 = min((int)__ldg(gsl + (int64_t)k * kTileRows), mlast);
             float4 a0, a1, a2;
             planes(s0, a0, a1, a2);
             float2 t01;
@@ -1196,20 +1184,9 @@ __global__ void __launch_bounds__(kTileRows, 7) k_tl_mom32r(const float* __restr
             acc01.add(t01);
             if (DIM == 3) acc2.add(t2);
         }
-    } else if (staged) {
-#pragma unroll 4
-        for (int k = 0; k < len; ++k) {
-            const int s = min((int)__ldg(gsl + (int64_t)k * kTileRows), mlast);
-            if (DIM == 3) mom_pair_rel<3>(P0s[s], P1s[s], P2s[s], xi, K, acc01, acc2);
-            else {
-                const float2 h = P1h[s];
-                mom_pair_rel<DIM>(P0s[s], make_float4(h.x, h.y, 0.0f, 0.0f), P0s[s], xi, K, acc01, acc2);
-            }
-        }
     } else {
         for (int k = 0; k < len; ++k) {
-            const int s = min(sslot ? (int)ssl[threadIdx.x + k * kTileRows] : (int)__ldg(gsl + (int64_t)k * kTileRows),
-                              mlast);
+            const int s = min((int)__ldg(gsl + (int64_t)k * kTileRows), mlast);
             const int q = min((int)A.sinv[P0 + s], mlast);
             const int64_t j = min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1);
             float4 p0, p1, p2;
@@ -1992,8 +1969,7 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
         t.momr.mcap = mr;
         t.momr.wsum = reinterpret_cast<const float4*>(reinterpret_cast<const unsigned char*>(st->plan) +
                                                       tl_wsum_offset(n, st->plan_nnz, st->plan_maxrow));
-        t.momr_bytes = (dim == 3 ? (size_t)mr * 48 : (size_t)mr * 16 + align16((size_t)mr * 8)) +
-                       (size_t)t.momr.ecap * kTileRows * 2;
+        t.momr_bytes = dim == 3 ? (size_t)mr * 48 : (size_t)mr * 16 + align16((size_t)mr * 8);
     }
     int64_t g = ctx->num_sms > 0 ? ctx->num_sms : 1;
     t.grid = (int)(g < tp.ntiles ? g : tp.ntiles);
