@@ -1025,13 +1025,12 @@ def run_gpu(args):
     else:
         peak, peak_src = 6800.0, "fallback"
     achieved = dominant[1] / (dominant[2] * 1e-3) / 1e9
-    # ncu DRAM bytes (read + write) per launch of each planned TL pass on this workload,
-    # by the deformation pass's form (profiles/tl_pair_passes_plate816k_full.md: the
-    # bank-aware plans for both passes in the geometry form, the entry form's deformation
-    # pass before them)
+    # ncu DRAM bytes (read + write) per launch of each planned TL pass on this workload, by
+    # pipeline mode (profiles/tl_plate816k_fp32_launches.md: the geometry forms of both
+    # passes; tl_pair_passes_plate816k_full.md: the entry forms of the stream mode)
     pipe = args.pipe or "geom"
-    ncu_traffic = {("tl_momentum_pass", "geom"): 446.8e6, ("tl_momentum_pass", "stream"): 446.8e6,
-                   ("tl_deformation_pass", "geom"): 214.2e6, ("tl_deformation_pass", "stream"): 509.1e6}
+    ncu_traffic = {("tl_momentum_pass", "geom"): 167.1e6, ("tl_momentum_pass", "stream"): 446.8e6,
+                   ("tl_deformation_pass", "geom"): 217.2e6, ("tl_deformation_pass", "stream"): 509.1e6}
     traffic = args.traffic if args.traffic is not None else ncu_traffic.get((dominant[0], pipe))
 
     # end to end through the C ABI with the float64 state (x, v, F - I) in host memory:

@@ -1962,7 +1962,8 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
         t.defo.ecap = st->plan_maxrow <= 128 ? (int)st->plan_maxrow : 0;
         t.defo_bytes = (size_t)mg * 32 + (size_t)t.defo.ecap * kTileRows * 2;
         // the momentum pass's geometry form (used on boxes without periodic axes): position
-        // and V0_j M_j staged, 48 bytes per neighbour in 3D (24 in 2D), the slot block, S_i
+        // and V0_j M_j staged, 48 bytes per neighbour in 3D (24 in 2D); slots and S_i read
+        // from the plan
         t.geom_mom = true;
         const int mr = stage_mcap(st->plan_maxm, dim == 3 ? 3 : 2, ctx->stage_cap);
         t.momr = t.defo;
