@@ -132,8 +132,23 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const fl
             }
 }
 
+}  // namespace
+
+// The tcgen05 form of the GEMM above (mlp_tc.cu): same operands, slices and epilogues.
+int sph_gemm_tc(sph_ctx* ctx, int epi, int M, int N, int K, const float* A, int lda, int aT, const float* B, int ldb,
+                int bT, const float* bias, float* C, int ldc, float* Z, int kchunk, int slices, int64_t slice_stride,
+                cudaStream_t s);
+
+namespace {
+
+// tc != nullptr: the tcgen05 GEMM (the training path); else the mma.sync one (the
+// reference forward, sph_mlp_forward).
 void gemm(int epi, int M, int N, int K, const float* A, int lda, int aT, const float* B, int ldb, int bT,
-          const float* bias, float* C, int ldc, float* Z, cudaStream_t s) {
+          const float* bias, float* C, int ldc, float* Z, cudaStream_t s, sph_ctx* tc = nullptr) {
+    if (tc) {
+        sph_gemm_tc(tc, epi, M, N, K, A, lda, aT, B, ldb, bT, bias, C, ldc, Z, K, 1, 0, s);
+        return;
+    }
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     if (epi == EPI_NONE)
         k_gemm_bf16<EPI_NONE><<<grid, 128, 0, s>>>(M, N, K, A, lda, aT, B, ldb, bT, bias, C, ldc, Z, K, 0);
@@ -160,14 +175,21 @@ __global__ void k_sum_slices(const float* __restrict__ parts, int slices, int64_
 // Weight gradient C[M][N] (ldc = N) = op(A) op(B) over a long K (the batch): the K
 // range is cut into slices computed by separate blocks, then summed in order.
 void gemm_splitk(int M, int N, int K, const float* A, int lda, int aT, const float* B, int ldb, int bT, float* C,
-                 float* scratch, cudaStream_t s) {
+                 float* scratch, cudaStream_t s, sph_ctx* tc = nullptr) {
     int slices = (K + 255) / 256;
     if (slices > 64) slices = 64;
-    int kchunk = ((K + slices - 1) / slices + BK - 1) / BK * BK;
+    // tcgen05: slices of whole 128-row chunks
+    const int kq = tc ? 128 : BK;
+    int kchunk = ((K + slices - 1) / slices + kq - 1) / kq * kq;
     slices = (K + kchunk - 1) / kchunk;
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, slices);
-    k_gemm_bf16<EPI_NONE><<<grid, 128, 0, s>>>(M, N, K, A, lda, aT, B, ldb, bT, nullptr, scratch, N, nullptr, kchunk,
-                                                (int64_t)M * N);
+    if (tc) {
+        sph_gemm_tc(tc, EPI_NONE, M, N, K, A, lda, aT, B, ldb, bT, nullptr, scratch, N, nullptr, kchunk, slices,
+                    (int64_t)M * N, s);
+    } else {
+        dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, slices);
+        k_gemm_bf16<EPI_NONE><<<grid, 128, 0, s>>>(M, N, K, A, lda, aT, B, ldb, bT, nullptr, scratch, N, nullptr,
+                                                    kchunk, (int64_t)M * N);
+    }
     k_sum_slices<<<grid_for((int64_t)M * N, 256), 256, 0, s>>>(scratch, slices, (int64_t)M * N, C);
 }
 
@@ -354,12 +376,12 @@ struct Act {
     float *Z1, *H1, *Z2, *H2, *Z3, *H3, *Y;
 };
 
-int forward_chunk(const float* P, const float* X, int64_t rows, Act& a, cudaStream_t s) {
+int forward_chunk(const float* P, const float* X, int64_t rows, Act& a, cudaStream_t s, sph_ctx* tc = nullptr) {
     int M = (int)rows;
-    gemm(EPI_BIAS_GELU, M, NHID, NIN, X, NIN, 0, P + OFF_W1, NIN, 1, P + OFF_B1, a.H1, NHID, a.Z1, s);
-    gemm(EPI_BIAS_GELU, M, NHID, NHID, a.H1, NHID, 0, P + OFF_W2, NHID, 1, P + OFF_B2, a.H2, NHID, a.Z2, s);
-    gemm(EPI_BIAS_GELU, M, NHID, NHID, a.H2, NHID, 0, P + OFF_W3, NHID, 1, P + OFF_B3, a.H3, NHID, a.Z3, s);
-    gemm(EPI_BIAS, M, NOUT, NHID, a.H3, NHID, 0, P + OFF_W4, NHID, 1, P + OFF_B4, a.Y, NOUT, nullptr, s);
+    gemm(EPI_BIAS_GELU, M, NHID, NIN, X, NIN, 0, P + OFF_W1, NIN, 1, P + OFF_B1, a.H1, NHID, a.Z1, s, tc);
+    gemm(EPI_BIAS_GELU, M, NHID, NHID, a.H1, NHID, 0, P + OFF_W2, NHID, 1, P + OFF_B2, a.H2, NHID, a.Z2, s, tc);
+    gemm(EPI_BIAS_GELU, M, NHID, NHID, a.H2, NHID, 0, P + OFF_W3, NHID, 1, P + OFF_B3, a.H3, NHID, a.Z3, s, tc);
+    gemm(EPI_BIAS, M, NOUT, NHID, a.H3, NHID, 0, P + OFF_W4, NHID, 1, P + OFF_B4, a.Y, NOUT, nullptr, s, tc);
     return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
 }
 
@@ -395,7 +417,8 @@ int mlp_grad_impl(sph_ctx* ctx, const float* P, const float* X, const float* T, 
     Act a;
     int st = alloc_act(ctx, B, a);
     if (st) return st;
-    st = forward_chunk(P, X, B, a, s);
+    // the training path's GEMMs on tcgen05 (tensor-memory accumulators)
+    st = forward_chunk(P, X, B, a, s, ctx);
     if (st) return st;
     int nb = (int)grid_for(B * NOUT, 256);
     float* dY = (float*)sph_scratch(ctx, S_MISC0, (size_t)B * NOUT * 4 + (size_t)B * NHID * 8 + 256, &st);
@@ -411,19 +434,20 @@ int mlp_grad_impl(sph_ctx* ctx, const float* P, const float* X, const float* T, 
     float* parts = (float*)sph_scratch(ctx, S_MLP_PARTS, (size_t)64 * NHID * NHID * 4 + 256, &st);
     if (st) return st;
     // layer 4
-    gemm_splitk(NOUT, NHID, (int)B, dY, NOUT, 1, a.H3, NHID, 0, grad + OFF_W4, parts, s);
+    gemm_splitk(NOUT, NHID, (int)B, dY, NOUT, 1, a.H3, NHID, 0, grad + OFF_W4, parts, s, ctx);
     colsum(dY, B, NOUT, grad + OFF_B4, parts, s);
-    gemm(EPI_NONE, (int)B, NHID, NOUT, dY, NOUT, 0, P + OFF_W4, NHID, 0, nullptr, dH, NHID, nullptr, s);
+    gemm(EPI_NONE, (int)B, NHID, NOUT, dY, NOUT, 0, P + OFF_W4, NHID, 0, nullptr, dH, NHID, nullptr, s, ctx);
     const float* Zs[3] = {a.Z1, a.Z2, a.Z3};
     const float* Hin[3] = {X, a.H1, a.H2};
     const int64_t offW[3] = {OFF_W1, OFF_W2, OFF_W3}, offB[3] = {OFF_B1, OFF_B2, OFF_B3};
     const int nin[3] = {NIN, NHID, NHID};
     for (int l = 2; l >= 0; --l) {
         k_gelu_backward<<<grid_for(B * NHID, 256), 256, 0, s>>>(dH, Zs[l], dZ, B * NHID);
-        gemm_splitk(NHID, nin[l], (int)B, dZ, NHID, 1, Hin[l], nin[l], 0, grad + offW[l], parts, s);
+        gemm_splitk(NHID, nin[l], (int)B, dZ, NHID, 1, Hin[l], nin[l], 0, grad + offW[l], parts, s, ctx);
         colsum(dZ, B, NHID, grad + offB[l], parts, s);
         if (l > 0)
-            gemm(EPI_NONE, (int)B, nin[l], NHID, dZ, NHID, 0, P + offW[l], nin[l], 0, nullptr, dH, nin[l], nullptr, s);
+            gemm(EPI_NONE, (int)B, nin[l], NHID, dZ, NHID, 0, P + offW[l], nin[l], 0, nullptr, dH, nin[l], nullptr, s,
+                 ctx);
     }
     SPH_LAUNCH_CHECK(ctx);
     if (loss_host) {
@@ -431,6 +455,9 @@ int mlp_grad_impl(sph_ctx* ctx, const float* P, const float* X, const float* T, 
         SPH_CUDA(ctx, cudaMemcpyAsync(hp + 40, loss_d, 8, cudaMemcpyDeviceToHost, s));
         SPH_CUDA(ctx, cudaStreamSynchronize(s));
         *loss_host = hp[40];
+        // the tcgen05 GEMMs' bounded waits: reported with the loss, when the call syncs
+        int r = sph_take_status(ctx, s);
+        if (r) return r;
     }
     return SPH_OK;
 }

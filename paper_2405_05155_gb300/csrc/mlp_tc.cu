@@ -277,6 +277,127 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const float* __r
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// ---------------------------------------------------------------- training GEMM
+// C = op(A) op(B) on tcgen05 for the training path (the dense layers of the forward, the
+// backward's products with the weights and the weight gradients): one block computes a
+// 128 x BNT tile of C (BNT = 32, or 16 for the 3-output layer), over the K range of its
+// slice in chunks of 128.  A is stored [M][K] (aT = 0) or [K][M] (aT = 1), B [K][N] (bT = 0)
+// or [N][K] (bT = 1), both float32 in global memory; the loader converts them to bfloat16 and
+// writes both operands K-major into the core-matrix layout of the fused forward (a
+// transpose is a strided read, never a different descriptor), zero beyond M, N and the
+// slice.  One thread issues 8 tcgen05.mma (K = 16) per chunk into 128 columns of tensor
+// memory; the 4 warps read the accumulator back (a lane quarter each) and apply the
+// epilogue: + bias, and GELU keeping the pre-activation in Zout.  Slice z of a split K
+// writes C + z * slice_stride.  A bounded mbarrier wait that expires sets the timeout flag
+// and the block writes nothing.
+constexpr int kGemmThreads = 128;
+
+__device__ __forceinline__ float tc_load(const float* __restrict__ X, int ld, int t, int r, int k, int R, int ke) {
+    // element (r, k) of the operand read as [rows][K]: X[r][k] (t = 0) or X[k][r] (t = 1)
+    if (r >= R || k >= ke) return 0.0f;
+    return t ? X[(int64_t)k * ld + r] : X[(int64_t)r * ld + k];
+}
+
+// rows x 128 operand chunk (K range [k0, k0 + 128) of [0, ke)) into the core-matrix layout.
+__device__ __forceinline__ void tc_stage(unsigned char* mat, int rows, const float* __restrict__ X, int ld, int t,
+                                         int r0, int R, int k0, int ke) {
+    const int groups = rows * (kWidth / 8);
+    for (int q = threadIdx.x; q < groups; q += kGemmThreads) {
+        // t = 0: consecutive threads take consecutive 8-column groups of a row (contiguous
+        // reads along K); t = 1: consecutive threads take consecutive rows (contiguous reads
+        // along the rows for each k)
+        const int r = t ? q % rows : q / (kWidth / 8);
+        const int kg = t ? q / rows : q % (kWidth / 8);
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = tc_load(X, ld, t, r0 + r, k0 + 8 * kg + e, R, ke);
+        store8(mat, r, 8 * kg, v);
+    }
+}
+
+template <int EPI, int BNT>
+__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(int M, int N, int K, const float* __restrict__ A,
+                                                              int lda, int aT, const float* __restrict__ B, int ldb,
+                                                              int bT, const float* __restrict__ bias,
+                                                              float* __restrict__ C, int ldc, float* __restrict__ Zout,
+                                                              int kchunk, int64_t slice_stride, int* __restrict__ flags) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* As = sm;                         // 128 x 128 bfloat16
+    unsigned char* Bs = sm + kMatBytes;             // BNT x 128 bfloat16
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kMatBytes + (uint32_t)BNT * kWidth * 2);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m0 = blockIdx.y * kRows, n0 = blockIdx.x * BNT;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    // tensor-memory columns: BNT, at least 32 (the allocation unit)
+    constexpr uint32_t kCols = BNT < 32 ? 32u : (uint32_t)BNT;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    tc_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t sA = smem_u32(As), sB = smem_u32(Bs);
+    constexpr uint32_t idesc = inst_desc(kRows, BNT);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int k0 = kb; k0 < ke && ok; k0 += kWidth) {
+        tc_stage(As, kRows, A, lda, aT, m0, M, k0, ke);
+        tc_stage(Bs, BNT, B, ldb, bT ? 0 : 1, n0, N, k0, ke);
+        tc_sync();
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < kWidth / 16; ++kk)
+                mma_bf16(tmem, mat_desc(sA + 256 * kk, 128, 2048), mat_desc(sB + 256 * kk, 128, 2048), idesc,
+                         (k0 > kb || kk > 0) ? 1u : 0u);
+            mma_commit(bar);
+        }
+        const bool late = !mbar_wait_bounded(bar, phase, kPolls);
+        phase ^= 1u;
+        if (__syncthreads_or(late)) {
+            ok = false;
+            if (tid == 0) atomicExch(&flags[FLAG_TIMEOUT], 1);
+        }
+        tc_fence_after();
+    }
+    if (ok && kb < ke) {
+        // warp w: rows 32 w .. 32 w + 31 of the tile, one per lane
+        const int row = warp * 32 + (tid & 31);
+        const int gm = m0 + row;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        float* Cz = C + (int64_t)blockIdx.z * slice_stride;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BNT; c0 += 32) {
+            float v[32];
+            tmem_ld32(trow + (uint32_t)c0, v);
+            if (gm < M) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int gn = n0 + c0 + c;
+                    if (c0 + c < BNT && gn < N) {
+                        float x = v[c];
+                        if (EPI != 0) x += bias[gn];
+                        if (EPI == 2) {
+                            Zout[(int64_t)gm * ldc + gn] = x;
+                            x = gelu(x);
+                        }
+                        Cz[(int64_t)gm * ldc + gn] = x;
+                    }
+                }
+            }
+        }
+    }
+    tc_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+}
+
 }  // namespace
 
 // Forward of the MLP on tcgen05 (see sph.h).
@@ -294,4 +415,34 @@ extern "C" int sph_mlp_forward_tc(sph_ctx* ctx, const float* params, const float
     k_mlp_forward_tc<<<grid, kThreads, kSmemBytes, s>>>(params, feats, out, n, ctx->flags);
     SPH_LAUNCH_CHECK(ctx);
     return SPH_OK;
+}
+
+// The training GEMM on tcgen05 (declared in mlp.cu's dispatch): epi 0 none, 1 bias, 2 bias
+// and GELU; K cut into `slices` slices of kchunk.
+int sph_gemm_tc(sph_ctx* ctx, int epi, int M, int N, int K, const float* A, int lda, int aT, const float* B, int ldb,
+                int bT, const float* bias, float* C, int ldc, float* Z, int kchunk, int slices, int64_t slice_stride,
+                cudaStream_t s) {
+    // 128 x 32 tiles: a batch of 4096 rows and 128 outputs makes 128 blocks (the K loop per
+    // block is then short; more blocks hide the operand staging)
+    const int bnt = N <= 16 ? 16 : 32;
+    dim3 grid((unsigned)((N + bnt - 1) / bnt), (unsigned)((M + kRows - 1) / kRows), (unsigned)slices);
+    const size_t smem = kMatBytes + (size_t)bnt * kWidth * 2 + 64;
+    ctx->waits_pending = true;
+#define SPH_GEMM_TC(E, BN)                                                                                 \
+    do {                                                                                                   \
+        sph_allow_dynamic_smem((const void*)k_gemm_tc<E, BN>);                                             \
+        k_gemm_tc<E, BN><<<grid, kGemmThreads, smem, s>>>(M, N, K, A, lda, aT, B, ldb, bT, bias, C, ldc, Z, \
+                                                          kchunk, slice_stride, ctx->flags);               \
+    } while (0)
+    if (bnt == 16) {
+        if (epi == 0) SPH_GEMM_TC(0, 16);
+        else if (epi == 1) SPH_GEMM_TC(1, 16);
+        else SPH_GEMM_TC(2, 16);
+    } else {
+        if (epi == 0) SPH_GEMM_TC(0, 32);
+        else if (epi == 1) SPH_GEMM_TC(1, 32);
+        else SPH_GEMM_TC(2, 32);
+    }
+#undef SPH_GEMM_TC
+    return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
 }

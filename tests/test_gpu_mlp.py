@@ -88,9 +88,12 @@ def test_forward_tcgen05_parity(ctx, rows):
     assert rel_l2(y, y_mma) < 5e-3
 
 
-def test_gradient_parity_per_block(ctx):
+@pytest.mark.parametrize("rows", [4096, 1000])
+def test_gradient_parity_per_block(ctx, rows):
+    # the training path's GEMMs run on tcgen05 (forward, products with the weights, split-K
+    # weight gradients); 1000 rows: a ragged last tile and slices
     flat = inputs.mlp_init(5)
-    X, T = _batch(6, 4096)
+    X, T = _batch(6, rows)
     loss_o, g_o = OM.loss_and_grad(flat, X, T)
     g, loss = api.mlp_grad(ctx, cuda(flat, torch.float32), cuda(X, torch.float32), cuda(T, torch.float32))
     g = host(g)
