@@ -803,7 +803,7 @@ def _bench_mlp(api, inputs, ctx, peak_tflops):
     ms_tr = _event_ms(lambda: [tr.step(x, t) for _ in range(20)]) / 20
     tflops = flops / (ms * 1e-3) / 1e12
     return {"workload": "128-128-128-128-3 GELU MLP, BF16 operands, FP32 accumulate; fused forward on tcgen05 "
-                        "(TMEM accumulators) over the features of a dp=1/128 body; mma.sync forward and an Adam "
+                        "(TMEM accumulators) over the features of a dp=1/128 body; mma.sync reference forward and an Adam "
                         "step at batch 4096 (training path)",
             "rows": rows, "forward_ms": ms, "forward_tflops": tflops, "forward_mma_sync_ms": ms_mma,
             "rel_l2_tcgen05_vs_mma_sync": diff, "train_step_ms_batch4096": ms_tr,
