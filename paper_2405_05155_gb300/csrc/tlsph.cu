@@ -715,8 +715,12 @@ constexpr int kPermCap = 2048;
 // (8 consecutive rows), the pairs over the 8 groups.  Greedily, in list order: each
 // neighbour takes the group with room (group c holds the positions c, c + 8, ... below
 // m) that adds least to sum over quarter warps and groups of (pairs in the group)^2,
-// i.e. the smallest sum_Q cnt_Q * load_Q[c], ties to the lower group.  Each row's pairs
-// are then laid out in the bank-aware order (bank_order) of these positions.
+// i.e. the smallest sum_Q cnt_Q * load_Q[c], ties to the lower group, among the groups
+// not yet taken in its aligned block of 8 consecutive neighbours (any group with room
+// when none is left).  The staging loops store 8 consecutive neighbours per quarter
+// warp, so their 16-byte stores fall in 8 different groups, while their loads follow
+// the column order.  Each row's pairs are then laid out in the bank-aware order
+// (bank_order) of these positions.
 template <int DIM>
 __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__ r0, const double* __restrict__ V0,
                                                       const int64_t* __restrict__ row_ptr,
@@ -756,6 +760,7 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
         __syncthreads();
         if (threadIdx.x < 32) {
             const int lane = (int)threadIdx.x;
+            uint32_t block_used = 0u;      // groups taken in the current aligned block of 8 neighbours
             for (int q = 0; q < m; ++q) {
                 uint32_t key = 0xFFFFFFFFu;
                 if (lane < 8 && s_used[lane] < (m - lane + 7) / 8) {
@@ -763,9 +768,10 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
 #pragma unroll
                     for (int qi = 0; qi < 16; ++qi)
                         cost += ((s_cnt[4 * q + (qi >> 2)] >> (8 * (qi & 3))) & 0xFFu) * (uint32_t)s_load[8 * qi + lane];
-                    key = cost * 8u + (uint32_t)lane;
+                    key = (((block_used >> lane) & 1u) << 31) | (cost * 8u + (uint32_t)lane);
                 }
                 const int c = (int)(__reduce_min_sync(0xFFFFFFFFu, key) & 7u);
+                block_used = (q & 7) == 7 ? 0u : (block_used | (1u << c));
                 if (lane < 16) s_load[8 * lane + c] += (int)((s_cnt[4 * q + (lane >> 2)] >> (8 * (lane & 3))) & 0xFFu);
                 __syncwarp();
                 if (lane == 0) {
