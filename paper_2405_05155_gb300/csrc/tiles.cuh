@@ -128,51 +128,3 @@ __device__ __forceinline__ bool offset_order(int len, double two_over_h, RF rfun
     }
     return true;
 }
-
-// Bank-aware pair order for the staged gathers of a planned pass.  A warp's 16-byte
-// shared-memory loads are served a quarter warp (8 lanes) per wavefront when the 8 slots
-// differ mod 8 (16-byte slots of a plane, 32 four-byte banks); random slots cost about
-// 2.1 wavefronts.  Here the rows of each quarter warp choose, position by position and lane
-// by lane, a pair whose slot mod 8 no earlier lane of the quarter took at that position,
-// else the first remaining pair (a conflict).  slot_of(k) gives the slot of the row's k-th
-// listed pair; order[k] receives the list position of its k-th pair in the new order.
-// Every thread of the warp must call it (shuffles, warp-uniform loop bounds).  Returns
-// false, taking no part and leaving list order, for a row longer than kSortCap.
-template <typename SF>
-__device__ __forceinline__ bool bank_order(int len, SF slot_of, uint32_t* order) {
-    const bool fits = len <= kSortCap;
-    const int my = fits ? len : 0;
-    uint8_t grp[kSortCap];
-    uint32_t rem[kSortCap / 32] = {0u, 0u, 0u, 0u};
-    for (int k = 0; k < my; ++k) {
-        grp[k] = (uint8_t)(slot_of(k) & 7);
-        rem[k >> 5] |= 1u << (k & 31);
-    }
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned qbase = lane & ~7u;
-    const int wmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)my);
-    for (int p = 0; p < wmax; ++p) {
-        uint32_t used = 0u;
-        for (int r = 0; r < 8; ++r) {
-            int g = -1;
-            if ((int)(lane & 7u) == r && p < my) {
-                int pick = -1, any = -1;
-                for (int k = 0; k < my; ++k) {
-                    if (!((rem[k >> 5] >> (k & 31)) & 1u)) continue;
-                    if (any < 0) any = k;
-                    if (!((used >> grp[k]) & 1u)) {
-                        pick = k;
-                        break;
-                    }
-                }
-                if (pick < 0) pick = any;      // p < my: a pair remains
-                rem[pick >> 5] &= ~(1u << (pick & 31));
-                order[p] = (uint32_t)pick;
-                g = grp[pick];
-            }
-            const int gg = __shfl_sync(0xffffffffu, g, (int)(qbase + (unsigned)r));
-            if (gg >= 0) used |= 1u << gg;
-        }
-    }
-    return fits;
-}

@@ -704,6 +704,144 @@ static inline size_t tl_plan_total(int64_t n, int64_t nnz, int64_t maxrow) {
 // groups (tiles with more keep their list order).
 constexpr int kPermCap = 2048;
 
+// Pair order of a tile's rows for the staged 16-byte gathers of the geometry-form passes.
+// The k-th pairs of a quarter warp's 8 rows (consecutive rows) are read by one gather, which
+// takes one wavefront when its lanes read 8 different groups (position mod 8) and as many as
+// the most lanes on one group otherwise.  Step by step, a maximum matching of the quarter's
+// active rows to groups in which they have pairs left is found by augmenting paths (Kuhn):
+// rows in order of most pairs left, each trying its groups in order of most of its pairs
+// left in them (ties to the lower row, the lower group).  A row left unmatched takes the
+// group picked least often so far in the step, then the one with most of its pairs left,
+// then the lower group.  In a group a row takes its pairs in list order.  One thread per
+// quarter warp computes the matchings; every thread of the block must call this (block
+// barriers).  scratch: kTileRows * (kSortCap + 8) bytes of shared memory.  order[k] receives
+// the list position of the row's k-th pair; rows longer than kSortCap keep list order, take
+// no part, and get false.
+template <typename SF>
+__device__ __forceinline__ bool quarter_match_order(int len, SF slot_of, uint32_t* order, uint8_t* scratch) {
+    const int row = (int)threadIdx.x;
+    const bool fits = len <= kSortCap;
+    const int my = fits ? len : 0;
+    uint8_t* s_choice = scratch;                                   // [row][step]: the group read
+    uint8_t* s_rem = scratch + kTileRows * kSortCap;               // [row][group]: pairs left
+    uint8_t grp[kSortCap];
+    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < my; ++k) {
+        grp[k] = (uint8_t)(slot_of(k) & 7);
+        cnt[grp[k]] += 1;
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g) s_rem[8 * row + g] = (uint8_t)cnt[g];
+    __syncthreads();
+    if ((row & 7) == 0) {
+        const int r0 = row;
+        uint8_t* rem = s_rem + 8 * r0;                              // rem[8 * r + g], r in 0..7
+        int steps = 0, left[8];
+        for (int r = 0; r < 8; ++r) {
+            left[r] = 0;
+            for (int g = 0; g < 8; ++g) left[r] += rem[8 * r + g];
+            steps = max(steps, left[r]);
+        }
+        for (int p = 0; p < steps; ++p) {
+            // active rows by pairs left (descending), stable
+            int act[8], na = 0;
+            for (int r = 0; r < 8; ++r) {
+                if (left[r] == 0) continue;
+                int at = na++;
+                while (at > 0 && left[act[at - 1]] < left[r]) {
+                    act[at] = act[at - 1];
+                    --at;
+                }
+                act[at] = r;
+            }
+            // each active row's groups with pairs left, fullest first, stable
+            uint8_t cand[8][8];
+            int ncand[8];
+            for (int a = 0; a < na; ++a) {
+                const int r = act[a];
+                int nc = 0;
+                for (int g = 0; g < 8; ++g) {
+                    const int c = rem[8 * r + g];
+                    if (c == 0) continue;
+                    int at = nc++;
+                    while (at > 0 && rem[8 * r + cand[r][at - 1]] < c) {
+                        cand[r][at] = cand[r][at - 1];
+                        --at;
+                    }
+                    cand[r][at] = (uint8_t)g;
+                }
+                ncand[r] = nc;
+            }
+            int owner[8], mg[8];
+            for (int g = 0; g < 8; ++g) owner[g] = -1;
+            for (int r = 0; r < 8; ++r) mg[r] = -1;
+            for (int a = 0; a < na; ++a) {
+                // augmenting path from act[a]: depth-first over the groups, each group visited
+                // once per search; at most 8 rows deep
+                int st_r[9], st_i[9], st_g[9];
+                int depth = 0;
+                uint32_t seen = 0u;
+                st_r[0] = act[a];
+                st_i[0] = 0;
+                while (depth >= 0) {
+                    const int r = st_r[depth];
+                    if (st_i[depth] >= ncand[r]) {
+                        --depth;
+                        continue;
+                    }
+                    const int g = cand[r][st_i[depth]++];
+                    if ((seen >> g) & 1u) continue;
+                    seen |= 1u << g;
+                    st_g[depth] = g;
+                    if (owner[g] < 0) {
+                        for (int d = 0; d <= depth; ++d) {
+                            owner[st_g[d]] = st_r[d];
+                            mg[st_r[d]] = st_g[d];
+                        }
+                        break;
+                    }
+                    if (depth + 1 >= 9) continue;                  // never: 8 groups bound the depth
+                    ++depth;
+                    st_r[depth] = owner[g];
+                    st_i[depth] = 0;
+                }
+            }
+            int picks[8];
+            for (int g = 0; g < 8; ++g) picks[g] = owner[g] >= 0 ? 1 : 0;
+            for (int a = 0; a < na; ++a) {
+                const int r = act[a];
+                if (mg[r] >= 0) continue;
+                int best = -1;
+                for (int g = 0; g < 8; ++g) {
+                    if (rem[8 * r + g] == 0) continue;
+                    if (best < 0 || picks[g] < picks[best] ||
+                        (picks[g] == picks[best] && rem[8 * r + g] > rem[8 * r + best]))
+                        best = g;
+                }
+                mg[r] = best;
+                picks[best] += 1;
+            }
+            for (int a = 0; a < na; ++a) {
+                const int r = act[a];
+                s_choice[(r0 + r) * kSortCap + p] = (uint8_t)mg[r];
+                rem[8 * r + mg[r]] -= 1;
+                left[r] -= 1;
+            }
+        }
+    }
+    __syncthreads();
+    uint32_t taken[kSortCap / 32] = {0u, 0u, 0u, 0u};
+    for (int p = 0; p < my; ++p) {
+        const int g = s_choice[row * kSortCap + p];
+        int k = 0;
+        while (k < my && (((taken[k >> 5] >> (k & 31)) & 1u) || grp[k] != g)) ++k;
+        k = min(k, my - 1);                                         // always found: the group has a pair left
+        taken[k >> 5] |= 1u << (k & 31);
+        order[p] = (uint32_t)k;
+    }
+    return fits;
+}
+
 // Pair entries of the tile plan: w = grad0 W_ij V0_j in float64, stored float32,
 // with the neighbour's slot (its position in the tile's distinct list); the row's
 // S_i = sum_j w_ij, summed in float64 in list order, stored float32; and the staging
@@ -775,10 +913,56 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
                 if (lane < 16) s_load[8 * lane + c] += (int)((s_cnt[4 * q + (lane >> 2)] >> (8 * (lane & 3))) & 0xFFu);
                 __syncwarp();
                 if (lane == 0) {
-                    s_pos[q] = (uint16_t)(8 * s_used[c] + c);
+                    s_pos[q] = (uint16_t)c;          // the group; positions follow the refinement
                     s_used[c] += 1;
                 }
                 __syncwarp();
+            }
+            // refinement: two neighbours of one aligned block exchange their groups when that
+            // lowers the sum over quarter warps and groups of load^2 (the block keeps its
+            // groups, each group its size), for at most three sweeps over the blocks
+            for (int sweep = 0; sweep < 3; ++sweep) {
+                bool changed = false;
+                for (int b0 = 0; b0 < m; b0 += 8) {
+                    const int bn = min(8, m - b0);
+                    for (int x = 0; x < bn; ++x)
+                        for (int y = x + 1; y < bn; ++y) {
+                            const int qa = b0 + x, qb = b0 + y;
+                            const int ga = s_pos[qa], gb = s_pos[qb];
+                            if (ga == gb) continue;
+                            int d = 0, delta = 0;
+                            if (lane < 16) {
+                                const int sh = 8 * (lane & 3);
+                                d = (int)((s_cnt[4 * qa + (lane >> 2)] >> sh) & 0xFFu) -
+                                    (int)((s_cnt[4 * qb + (lane >> 2)] >> sh) & 0xFFu);
+                                // (l_a - d)^2 + (l_b + d)^2 - l_a^2 - l_b^2
+                                delta = 2 * d * (s_load[8 * lane + gb] - s_load[8 * lane + ga] + d);
+                            }
+                            delta = __reduce_add_sync(0xFFFFFFFFu, delta);
+                            if (delta < 0) {
+                                if (lane < 16) {
+                                    s_load[8 * lane + ga] -= d;
+                                    s_load[8 * lane + gb] += d;
+                                }
+                                if (lane == 0) {
+                                    s_pos[qa] = (uint16_t)gb;
+                                    s_pos[qb] = (uint16_t)ga;
+                                }
+                                changed = true;
+                            }
+                            __syncwarp();
+                        }
+                }
+                if (!changed) break;
+            }
+            // positions: within its group, a neighbour's rank in list order
+            if (lane == 0) {
+                int rank[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                for (int q = 0; q < m; ++q) {
+                    const int c = s_pos[q] & 7;
+                    s_pos[q] = (uint16_t)(8 * rank[c] + c);
+                    rank[c] += 1;
+                }
             }
         }
         __syncthreads();
@@ -793,9 +977,12 @@ __global__ void __launch_bounds__(kTileRows) k_tl_geo(const double* __restrict__
         }
     }
     auto pos_of = [&](int q) { return balance ? (int)s_pos[min(q, m - 1)] : q; };
-    // pair order: bank-aware for the staged float4 gathers (see bank_order)
+    // pair order for the staged 16-byte gathers (see quarter_match_order); its tables reuse
+    // s_cnt, free once the positions are set
+    __syncthreads();
     uint32_t order[kSortCap];
-    const bool sorted = bank_order(len, [&](int k) { return pos_of((int)lcol[b + k]); }, order);
+    const bool sorted = quarter_match_order(len, [&](int k) { return pos_of((int)lcol[b + k]); }, order,
+                                            reinterpret_cast<uint8_t*>(s_cnt));
     for (int k = 0; k < width; ++k) {
         float4 e = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (k < len) {

@@ -132,23 +132,44 @@ def test_steps_parity(ctx, kappa):
         assert np.all(host(v)[:, s["fixed"] == 1] == 0.0)
 
 
-def _bank_order(slots):
-    """The bank-aware pair order of a tile (rows of 8-lane quarter warps, positions in turn,
-    lanes in turn: the first remaining pair whose slot mod 8 no earlier lane took at that
-    position, else the first remaining pair), written out from its description."""
+def _match_order(slots):
+    """The pair order of a tile for its staged gathers, written out from its description:
+    per quarter warp (8 consecutive rows) and step, a maximum matching of the active rows
+    to groups (slot mod 8) in which they have pairs left, by augmenting paths with rows
+    taken by most pairs left and each row trying its fullest groups first (ties to the
+    lower row, the lower group); an unmatched row takes the group picked least often in
+    the step, then its fullest, then the lower group; within a group, list order."""
     orders = [np.zeros(len(sl), dtype=np.int64) for sl in slots]
     for q0 in range(0, len(slots), 8):
-        group = list(range(q0, min(q0 + 8, len(slots))))
-        rem = {r: list(range(len(slots[r]))) for r in group}
-        for p in range(max(len(slots[r]) for r in group)):
-            used = set()
-            for r in group:
-                if p >= len(slots[r]):
-                    continue
-                pick = next((k for k in rem[r] if slots[r][k] % 8 not in used), rem[r][0])
-                rem[r].remove(pick)
-                orders[r][p] = pick
-                used.add(int(slots[r][pick]) % 8)
+        rows = list(range(q0, min(q0 + 8, len(slots))))
+        byg = {r: [[k for k in range(len(slots[r])) if int(slots[r][k]) % 8 == g] for g in range(8)] for r in rows}
+        left = {r: len(slots[r]) for r in rows}
+        for p in range(max(left.values())):
+            act = sorted([r for r in rows if left[r] > 0], key=lambda r: -left[r])
+            owner = [None] * 8
+
+            def augment(r, seen):
+                for g in sorted(range(8), key=lambda g: -len(byg[r][g])):
+                    if not byg[r][g] or g in seen:
+                        continue
+                    seen.add(g)
+                    if owner[g] is None or augment(owner[g], seen):
+                        owner[g] = r
+                        return True
+                return False
+
+            for r in act:
+                augment(r, set())
+            pick = {owner[g]: g for g in range(8) if owner[g] is not None}
+            picks = [1 if owner[g] is not None else 0 for g in range(8)]
+            for r in act:
+                if r not in pick:
+                    g = min((g for g in range(8) if byg[r][g]), key=lambda g: (picks[g], -len(byg[r][g]), g))
+                    pick[r] = g
+                    picks[g] += 1
+            for r in act:
+                orders[r][p] = byg[r][pick[r]].pop(0)
+                left[r] -= 1
     return orders
 
 
@@ -235,7 +256,7 @@ def test_tile_plan_is_exact(ctx):
             # the positions balance each quarter warp's pairs over the 8 groups at least as
             # well as the list order does
             assert _quarter_loads(slots) <= _quarter_loads(lists)
-        orders = _bank_order(slots) if b < 12 else None
+        orders = _match_order(slots) if b < 12 else None
         for r in range(i1 - i0):
             i = i0 + r
             k = np.arange(lens[i])
