@@ -281,13 +281,22 @@ __device__ __forceinline__ float gs_from_d2(float d2, const TLK<float>& K) {
     return K.coef * t * t * t;
 }
 
+// me: the particle's RD record, whose first quarter (position code) and V0 equal the RM
+// record's; given, the record's first 32-byte sector is written whole, so that L2 need not
+// fetch the rest of it from DRAM before writing it back.
 template <int DIM>
-__device__ __forceinline__ void store_M(float* RM, int64_t i, const float* m) {
+__device__ __forceinline__ void store_M(float* RM, int64_t i, const float* m, const F8* me = nullptr) {
     if (DIM == 2) {
+        if (me) *reinterpret_cast<float4*>(RM + 8 * i) = make_float4(me->v[0], me->v[1], me->v[2], me->v[3]);
         *reinterpret_cast<float4*>(RM + 8 * i + 4) = make_float4(m[0], m[2], m[1], m[3]);
     } else {
         float* rec = RM + 16 * i;
-        rec[4] = m[0]; rec[5] = m[3]; rec[6] = m[6];
+        if (me) {
+            *reinterpret_cast<float4*>(rec) = make_float4(me->v[0], me->v[1], me->v[2], me->v[3]);
+            *reinterpret_cast<float4*>(rec + 4) = make_float4(m[0], m[3], m[6], me->v[7]);
+        } else {
+            rec[4] = m[0]; rec[5] = m[3]; rec[6] = m[6];
+        }
         *reinterpret_cast<float4*>(rec + 8) = make_float4(m[1], m[4], m[7], 0.0f);
         *reinterpret_cast<float4*>(rec + 12) = make_float4(m[2], m[5], m[8], 0.0f);
     }
@@ -562,7 +571,7 @@ __device__ __forceinline__ void defo_finish(const float* Lt, const float* b0, bo
                                             int64_t n, const TLK<float>& K, float* __restrict__ RM,
                                             float* __restrict__ H, float* __restrict__ u,
                                             double* __restrict__ dFdt, const float* hold = nullptr,
-                                            const float* uold = nullptr) {
+                                            const float* uold = nullptr, const F8* me = nullptr) {
     float Fd[DIM * DIM];
     times_b0<DIM, float>(Lt, b0, Fd);
     if (OUT == OUT_RATES) {
@@ -578,7 +587,7 @@ __device__ __forceinline__ void defo_finish(const float* Lt, const float* b0, bo
 #pragma unroll
     for (int a = 0; a < DIM; ++a) u[a * n + i] = (uold ? uold[a] : u[a * n + i]) + K.dt * vi[a];
     stress_factor<DIM, float>(h, b0, K, m);
-    store_M<DIM>(RM, i, m);
+    store_M<DIM>(RM, i, m, me);
 }
 
 // Deformation-rate pass (Eq. 31) with the fused stress update of the next step,
@@ -643,7 +652,7 @@ __global__ void __launch_bounds__(256, 4) k_tl_defo32(const float* __restrict__ 
     float b0[NS], vi[3] = {me.v[4], me.v[5], me.v[6]};
 #pragma unroll
     for (int s = 0; s < NS; ++s) b0[s] = B0[s * n + i];
-    defo_finish<DIM, OUT>(Lt, b0, (bi & kFixedBit) != 0, vi, i, n, K, RM, H, u, dFdt);
+    defo_finish<DIM, OUT>(Lt, b0, (bi & kFixedBit) != 0, vi, i, n, K, RM, H, u, dFdt, nullptr, nullptr, &me);
 }
 
 // ------------------------------------------------ float32 passes on a tile plan
@@ -1636,8 +1645,11 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
         Lt[2 * DIM + 2] = l22.value();
     }
     float vi[3] = {me.v[4], me.v[5], me.v[6]};
+    // the own record again, with the epilogue's other own-row reads (keeping the first
+    // read live through the loop costs registers there)
+    const F8 own = ldg8(RD + 8 * i);
     if (GEOM) own_row();
-    defo_finish<DIM, OUT>(Lt, b0, (bi & kFixedBit) != 0, vi, i, n, K, RM, H, u, dFdt, hold, uold);
+    defo_finish<DIM, OUT>(Lt, b0, (bi & kFixedBit) != 0, vi, i, n, K, RM, H, u, dFdt, hold, uold, &own);
 }
 
 // ---------------------------------------------------------------- pack / unpack
