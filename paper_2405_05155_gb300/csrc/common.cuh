@@ -77,6 +77,31 @@ enum { FLAG_BAD_INPUT = 0, FLAG_NONFINITE = 1, FLAG_CAPACITY = 2, FLAG_TIMEOUT =
 
 #define SPH_LAUNCH_CHECK(ctx) SPH_CUDA(ctx, cudaGetLastError())
 
+// Programmatic dependent launch.  A kernel launched with the programmatic-serialization
+// attribute may start while the previous kernel of its stream is finishing: it reads only
+// data no kernel in flight writes before grid_dependency_wait(), which returns once that
+// previous kernel has completed and its writes are visible; grid_launch_dependents() lets
+// the next such kernel start.  Both are no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch with the programmatic-serialization attribute (see grid_dependency_wait).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*f)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                    Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, f, args...);
+}
+
 // Per-kernel timing: returns a token for sph_timer_end (or -1 when timing is off).
 int sph_timer_begin(sph_ctx* ctx, int slot, cudaStream_t s);
 void sph_timer_end(sph_ctx* ctx, int token, cudaStream_t s);

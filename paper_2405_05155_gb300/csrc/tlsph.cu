@@ -1276,27 +1276,37 @@ __global__ void __launch_bounds__(kTileRows, 8) k_tl_mom32r(const float* __restr
     const int64_t P0 = row_ptr[i0];
     const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
     const int m = A.tile_m[tile];
-    const uint32_t bref = __float_as_uint(RM[W * i0 + DIM]);
+    // the cell code of the tile's first row, from RD (whose position quarter no pass writes)
+    const uint32_t bref = __float_as_uint(RD[8 * i0 + DIM]);
     // pair slots are read from the plan's slot section (a warp reads 64 contiguous bytes per
     // position): without a shared slot block the stage fits 8 blocks per SM
     const bool staged = m <= mc;
-    // the own record and S_i are requested first: their latency overlaps the staging
+    const float4 S = A.wsum[ii];
+    // up to four neighbours per thread per round: their indices first, then their records
+    // two at a time, so that few round trips to memory are in series
+    int64_t jq[4];
+    int pq[4];
+    auto indices = [&](int q0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int q = q0 + k * kTileRows + (int)threadIdx.x;
+            // a plan out of date with the lists reads wrong but in-bounds records
+            jq[k] = q < m ? min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1) : -1;
+            pq[k] = q < m ? min((int)A.spos[P0 + q], m - 1) : 0;
+        }
+    };
+    // launched as a programmatic dependent of the previous pass: everything above reads
+    // the plan and the fixed lists only; the records the previous pass wrote are read after
+    // the wait
+    if (staged) indices(0);
+    grid_dependency_wait();
+    grid_launch_dependents();
+    // the own record is requested before the staging: its latency overlaps it
     const F8 a0 = ldg8(RM + W * ii);
     const F8 a1 = DIM == 3 ? ldg8(RM + W * ii + 8) : a0;
-    const float4 S = A.wsum[ii];
     if (staged) {
-        // up to four neighbours per thread per round: their indices first, then their
-        // records two at a time, so that few round trips to memory are in series
         for (int q0 = 0; q0 < m; q0 += 4 * kTileRows) {
-            int64_t jq[4];
-            int pq[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int q = q0 + k * kTileRows + (int)threadIdx.x;
-                // a plan out of date with the lists reads wrong but in-bounds records
-                jq[k] = q < m ? min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1) : -1;
-                pq[k] = q < m ? min((int)A.spos[P0 + q], m - 1) : 0;
-            }
+            if (q0 > 0) indices(q0);
 #pragma unroll
             for (int k = 0; k < 4; k += 2) {
                 F8 ra[2], rb[2];
@@ -1453,7 +1463,6 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
     const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
     const int m = A.tile_m[tile];
     const float4* g = A.geo + A.tile_so[tile] + threadIdx.x;
-    F8 me = ldg8(RD + 8 * ii);
     float b0[NS], hold[DIM * DIM], uold[DIM];
     // the epilogue's own-row reads: issued here, their latency hidden by the loop, or (the
     // geometry form) after it, to keep 18 registers free for more resident warps
@@ -1465,7 +1474,6 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
 #pragma unroll
         for (int a = 0; a < DIM; ++a) uold[a] = OUT == OUT_RATES ? 0.0f : u[a * n + ii];
     };
-    if (!GEOM) own_row();
     // GEOM without periodic axes: positions staged relative to the cell of the tile's
     // first row (decoded once per neighbour, not per pair)
     constexpr bool REL = GEOM && !PER;
@@ -1483,21 +1491,31 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
             cp_async16(reinterpret_cast<unsigned char*>(ssl) + 16 * c, src + 16 * c);
         cp_async_commit();
     }
-    bool staged;
-    if (REL) {
-        staged = m <= A.mcap;
-        if (staged) {
-            // up to four neighbours per thread per round: their indices first, then their
-            // records two at a time, so that few round trips to memory are in series
-            for (int q0 = 0; q0 < m; q0 += 4 * kTileRows) {
-                int64_t jq[4];
-                int pq[4];
+    // up to four neighbours per thread per round: their indices first, then their records
+    // two at a time, so that few round trips to memory are in series
+    int64_t jq[4];
+    int pq[4];
+    auto indices = [&](int q0) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int q = q0 + k * kTileRows + (int)threadIdx.x;
-                    jq[k] = q < m ? min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1) : -1;
-                    pq[k] = q < m ? min((int)A.spos[P0 + q], m - 1) : 0;
-                }
+        for (int k = 0; k < 4; ++k) {
+            const int q = q0 + k * kTileRows + (int)threadIdx.x;
+            jq[k] = q < m ? min(max((int64_t)A.uidx[P0 + q], (int64_t)0), n - 1) : -1;
+            pq[k] = q < m ? min((int)A.spos[P0 + q], m - 1) : 0;
+        }
+    };
+    bool staged = REL ? m <= A.mcap : false;
+    // launched as a programmatic dependent of the previous pass: everything above reads
+    // the plan, the fixed lists and RD's position quarter (which no pass writes); RD's
+    // velocities, H and u are read after the wait
+    if (REL && staged) indices(0);
+    grid_dependency_wait();
+    grid_launch_dependents();
+    F8 me = ldg8(RD + 8 * ii);
+    if (!GEOM) own_row();
+    if (REL) {
+        if (staged) {
+            for (int q0 = 0; q0 < m; q0 += 4 * kTileRows) {
+                if (q0 > 0) indices(q0);
 #pragma unroll
                 for (int k = 0; k < 4; k += 2) {
                     F8 rr[2];
@@ -2214,10 +2232,12 @@ void tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph
             f<<<gp, b, tp.pmom_bytes, s>>>(st->rm, st->rd, st->row_ptr, n, K, tp.mom, tp.pmom,
                                            out == OUT_RATES ? r1 : nullptr, ctx->flags);
         } else if (tp.geom_mom && !K.periodic) {
+            // programmatic dependent launch: the pass's plan reads overlap the previous
+            // pass's last blocks (a launch error is left to cudaGetLastError)
             auto* f = out == OUT_RATES ? k_tl_mom32r<DIM, OUT_RATES> : k_tl_mom32r<DIM, OUT_STEP>;
             sph_allow_dynamic_smem((const void*)f);
-            f<<<g, b, tp.momr_bytes, s>>>(st->rm, st->rd, st->row_ptr, n, K, tp.momr,
-                                          out == OUT_RATES ? r1 : nullptr);
+            (void)launch_dependent(f, g, b, tp.momr_bytes, s, (const float*)st->rm, st->rd,
+                                   (const int64_t*)st->row_ptr, n, K, tp.momr, out == OUT_RATES ? r1 : nullptr);
         } else {
             auto* f = out == OUT_RATES ? k_tl_mom32g<DIM, OUT_RATES> : k_tl_mom32g<DIM, OUT_STEP>;
             sph_allow_dynamic_smem((const void*)f);
@@ -2245,8 +2265,13 @@ void tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph
             }
             if (tp.bulk_defo) ctx->waits_pending = true;
             sph_allow_dynamic_smem((const void*)f);
-            f<<<g, b, tp.defo_bytes, s>>>(st->rd, st->rm, st->row_ptr, n, K, tp.defo, st->B32, st->H32, st->u32,
-                                          out == OUT_RATES ? r2 : nullptr, ctx->flags);
+            if (tp.geom_defo)
+                (void)launch_dependent(f, g, b, tp.defo_bytes, s, (const float*)st->rd, st->rm,
+                                       (const int64_t*)st->row_ptr, n, K, tp.defo, (const float*)st->B32, st->H32,
+                                       st->u32, out == OUT_RATES ? r2 : nullptr, ctx->flags);
+            else
+                f<<<g, b, tp.defo_bytes, s>>>(st->rd, st->rm, st->row_ptr, n, K, tp.defo, st->B32, st->H32, st->u32,
+                                              out == OUT_RATES ? r2 : nullptr, ctx->flags);
         }
     }
 }
