@@ -733,120 +733,147 @@ __device__ __forceinline__ bool quarter_match_order(int len, SF slot_of, uint32_
     const int my = fits ? len : 0;
     uint8_t* s_choice = scratch;                                   // [row][step]: the group read
     uint8_t* s_rem = scratch + kTileRows * kSortCap;               // [row][group]: pairs left
-    uint8_t grp[kSortCap];
+    // the row's pairs by group (a counting sort of list positions), in list order within one
+    uint8_t byg[kSortCap];
     int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int k = 0; k < my; ++k) {
-        grp[k] = (uint8_t)(slot_of(k) & 7);
-        cnt[grp[k]] += 1;
+        const int g = slot_of(k) & 7;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) cnt[c] += c == g ? 1 : 0;
     }
 #pragma unroll
     for (int g = 0; g < 8; ++g) s_rem[8 * row + g] = (uint8_t)cnt[g];
     __syncthreads();
     if ((row & 7) == 0) {
+        // one thread per quarter warp; its state in packed registers: owner (group -> row),
+        // mg (row -> group) and picks (group -> count) as 4-bit fields, left (row -> pairs
+        // left) as 8-bit fields, the search stack as 4-bit fields
         const int r0 = row;
-        uint8_t* rem = s_rem + 8 * r0;                              // rem[8 * r + g], r in 0..7
-        int steps = 0, left[8];
+        const uint8_t* rem = s_rem + 8 * r0;
+        uint64_t left = 0u;
+        int steps = 0;
         for (int r = 0; r < 8; ++r) {
-            left[r] = 0;
-            for (int g = 0; g < 8; ++g) left[r] += rem[8 * r + g];
-            steps = max(steps, left[r]);
+            int l = 0;
+            for (int g = 0; g < 8; ++g) l += rem[8 * r + g];
+            left |= (uint64_t)l << (8 * r);
+            steps = max(steps, l);
         }
+        auto lft = [&](int r) { return (int)((left >> (8 * r)) & 0xFFu); };
         for (int p = 0; p < steps; ++p) {
-            // active rows by pairs left (descending), stable
-            int act[8], na = 0;
-            for (int r = 0; r < 8; ++r) {
-                if (left[r] == 0) continue;
-                int at = na++;
-                while (at > 0 && left[act[at - 1]] < left[r]) {
-                    act[at] = act[at - 1];
-                    --at;
-                }
-                act[at] = r;
-            }
-            // each active row's groups with pairs left, fullest first, stable
-            uint8_t cand[8][8];
-            int ncand[8];
-            for (int a = 0; a < na; ++a) {
-                const int r = act[a];
-                int nc = 0;
-                for (int g = 0; g < 8; ++g) {
-                    const int c = rem[8 * r + g];
-                    if (c == 0) continue;
-                    int at = nc++;
-                    while (at > 0 && rem[8 * r + cand[r][at - 1]] < c) {
-                        cand[r][at] = cand[r][at - 1];
-                        --at;
+            uint32_t owner = 0x88888888u, mg = 0x88888888u;
+            uint32_t done = 0u;                                    // rows already taken this step
+            for (;;) {
+                // the next row: most pairs left, then the lower row
+                int rs = -1, ls = 0;
+                for (int r = 0; r < 8; ++r) {
+                    const int l = lft(r);
+                    if (((done >> r) & 1u) == 0u && l > ls) {
+                        rs = r;
+                        ls = l;
                     }
-                    cand[r][at] = (uint8_t)g;
                 }
-                ncand[r] = nc;
-            }
-            int owner[8], mg[8];
-            for (int g = 0; g < 8; ++g) owner[g] = -1;
-            for (int r = 0; r < 8; ++r) mg[r] = -1;
-            for (int a = 0; a < na; ++a) {
-                // augmenting path from act[a]: depth-first over the groups, each group visited
-                // once per search; at most 8 rows deep
-                int st_r[9], st_i[9], st_g[9];
+                if (rs < 0) break;
+                done |= 1u << rs;
+                // augmenting path from rs, depth first; at a row the unseen group with most of
+                // its pairs left, then the lower group; each group seen once per search
+                uint64_t st_r = (uint64_t)rs, st_g = 0u;
                 int depth = 0;
                 uint32_t seen = 0u;
-                st_r[0] = act[a];
-                st_i[0] = 0;
                 while (depth >= 0) {
-                    const int r = st_r[depth];
-                    if (st_i[depth] >= ncand[r]) {
+                    const int r = (int)((st_r >> (4 * depth)) & 15u);
+                    int best = -1, bc = 0;
+                    for (int g = 0; g < 8; ++g) {
+                        const int c = rem[8 * r + g];
+                        if (((seen >> g) & 1u) == 0u && c > bc) {
+                            best = g;
+                            bc = c;
+                        }
+                    }
+                    if (best < 0) {
                         --depth;
                         continue;
                     }
-                    const int g = cand[r][st_i[depth]++];
-                    if ((seen >> g) & 1u) continue;
-                    seen |= 1u << g;
-                    st_g[depth] = g;
-                    if (owner[g] < 0) {
+                    seen |= 1u << best;
+                    st_g = (st_g & ~(15ull << (4 * depth))) | ((uint64_t)best << (4 * depth));
+                    const int ow = (int)((owner >> (4 * best)) & 15u);
+                    if (ow == 8) {
                         for (int d = 0; d <= depth; ++d) {
-                            owner[st_g[d]] = st_r[d];
-                            mg[st_r[d]] = st_g[d];
+                            const int gd = (int)((st_g >> (4 * d)) & 15u), rd = (int)((st_r >> (4 * d)) & 15u);
+                            owner = (owner & ~(15u << (4 * gd))) | ((uint32_t)rd << (4 * gd));
+                            mg = (mg & ~(15u << (4 * rd))) | ((uint32_t)gd << (4 * rd));
                         }
                         break;
                     }
-                    if (depth + 1 >= 9) continue;                  // never: 8 groups bound the depth
+                    if (depth >= 7) continue;                      // never: 8 groups bound the depth
                     ++depth;
-                    st_r[depth] = owner[g];
-                    st_i[depth] = 0;
+                    st_r = (st_r & ~(15ull << (4 * depth))) | ((uint64_t)ow << (4 * depth));
                 }
             }
-            int picks[8];
-            for (int g = 0; g < 8; ++g) picks[g] = owner[g] >= 0 ? 1 : 0;
-            for (int a = 0; a < na; ++a) {
-                const int r = act[a];
-                if (mg[r] >= 0) continue;
+            uint32_t picks = 0u;
+            for (int g = 0; g < 8; ++g) picks |= (((owner >> (4 * g)) & 15u) != 8u ? 1u : 0u) << (4 * g);
+            // rows left unmatched, in the same order: the group picked least often, then the
+            // one with most of the row's pairs left, then the lower group
+            done = 0u;
+            for (;;) {
+                int rs = -1, ls = 0;
+                for (int r = 0; r < 8; ++r) {
+                    const int l = lft(r);
+                    if (((done >> r) & 1u) == 0u && l > ls) {
+                        rs = r;
+                        ls = l;
+                    }
+                }
+                if (rs < 0) break;
+                done |= 1u << rs;
+                if (((mg >> (4 * rs)) & 15u) != 8u) continue;
                 int best = -1;
                 for (int g = 0; g < 8; ++g) {
-                    if (rem[8 * r + g] == 0) continue;
-                    if (best < 0 || picks[g] < picks[best] ||
-                        (picks[g] == picks[best] && rem[8 * r + g] > rem[8 * r + best]))
-                        best = g;
+                    const int c = rem[8 * rs + g];
+                    if (c == 0) continue;
+                    const int pk = (int)((picks >> (4 * g)) & 15u);
+                    const int pb = best < 0 ? 0 : (int)((picks >> (4 * best)) & 15u);
+                    if (best < 0 || pk < pb || (pk == pb && c > rem[8 * rs + best])) best = g;
                 }
-                mg[r] = best;
-                picks[best] += 1;
+                mg = (mg & ~(15u << (4 * rs))) | ((uint32_t)best << (4 * rs));
+                picks += 1u << (4 * best);
             }
-            for (int a = 0; a < na; ++a) {
-                const int r = act[a];
-                s_choice[(r0 + r) * kSortCap + p] = (uint8_t)mg[r];
-                rem[8 * r + mg[r]] -= 1;
-                left[r] -= 1;
+            for (int r = 0; r < 8; ++r) {
+                if (lft(r) == 0) continue;
+                const int g = (int)((mg >> (4 * r)) & 15u);
+                s_choice[(r0 + r) * kSortCap + p] = (uint8_t)g;
+                s_rem[8 * (r0 + r) + g] -= 1;
+                left -= 1ull << (8 * r);
             }
         }
     }
     __syncthreads();
-    uint32_t taken[kSortCap / 32] = {0u, 0u, 0u, 0u};
+    // the row's pairs by group, list order within a group, then the chosen groups in turn
+    int start[8];
+    {
+        int acc = 0;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            start[g] = acc;
+            acc += cnt[g];
+        }
+    }
+    for (int k = 0; k < my; ++k) {
+        const int g = slot_of(k) & 7;
+        int at = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c == g) at = start[c]++;
+        byg[at] = (uint8_t)k;
+    }
+#pragma unroll
+    for (int g = 7; g >= 0; --g) start[g] = g == 0 ? 0 : start[g - 1];   // back to the first of each group
     for (int p = 0; p < my; ++p) {
         const int g = s_choice[row * kSortCap + p];
-        int k = 0;
-        while (k < my && (((taken[k >> 5] >> (k & 31)) & 1u) || grp[k] != g)) ++k;
-        k = min(k, my - 1);                                         // always found: the group has a pair left
-        taken[k >> 5] |= 1u << (k & 31);
-        order[p] = (uint32_t)k;
+        int at = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c == g) at = start[c]++;
+        order[p] = (uint32_t)byg[min(at, my - 1)];
     }
     return fits;
 }
