@@ -201,6 +201,10 @@ __global__ void __launch_bounds__(kTileRows, 6) k_euler32g(const float* __restri
                                                            double* __restrict__ rate_mass,
                                                            double* __restrict__ rate_mom) {
     extern __shared__ __align__(16) unsigned char eu_smem[];
+    // launched as a programmatic dependent of the previous pass: its blocks are scheduled
+    // while that pass finishes and read nothing before it has completed
+    grid_dependency_wait();
+    grid_launch_dependents();
     // the momentum pass of the two-pass step walks the tiles in reverse, the continuity
     // pass forwards: each starts on the pair entries the previous one read last (in L2)
     const int64_t tile = MODE == WANT_MOM ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
@@ -365,7 +369,7 @@ void launch32g(int out, int64_t n, const sph_eulerian_state* st, const EulerK<fl
     {                                                                               \
         auto* f = k_euler32g<DIM, M, O>;                                            \
         sph_allow_dynamic_smem((const void*)f);                                     \
-        f<<<g, b, ep.bytes, s>>>(rin, rout, st->row_ptr, n, K, ep.A, rm, rp);       \
+        (void)launch_dependent(f, g, b, ep.bytes, s, rin, rout, (const int64_t*)st->row_ptr, n, K, ep.A, rm, rp); \
     }
     if (out == OUT_RATES) LG(WANT_BOTH, OUT_RATES)
     else if (out == OUT_MOM) LG(WANT_MOM, OUT_MOM)
