@@ -1398,11 +1398,15 @@ __global__ void __launch_bounds__(kTileRows, 8) k_tl_mom32r(const float* __restr
                 p2 = p1;
             }
         };
+        // the next block's slots are requested before this block's pairs are evaluated
         int k = 0;
+        int s0n = len > 0 ? min((int)__ldg(gsl), mlast) : 0;
+        int s1n = len > 1 ? min((int)__ldg(gsl + kTileRows), mlast) : 0;
 #pragma unroll 2
         for (; k + 1 < len; k += 2) {
-            const int s0 = min((int)__ldg(gsl + (int64_t)k * kTileRows), mlast);
-            const int s1 = min((int)__ldg(gsl + (int64_t)(k + 1) * kTileRows), mlast);
+            const int s0 = s0n, s1 = s1n;
+            s0n = k + 2 < len ? min((int)__ldg(gsl + (int64_t)(k + 2) * kTileRows), mlast) : 0;
+            s1n = k + 3 < len ? min((int)__ldg(gsl + (int64_t)(k + 3) * kTileRows), mlast) : 0;
             float4 a0, a1, a2, b0, b1, b2;
             planes(s0, a0, a1, a2);
             planes(s1, b0, b1, b2);
@@ -1414,7 +1418,7 @@ __global__ void __launch_bounds__(kTileRows, 8) k_tl_mom32r(const float* __restr
             if (DIM == 3) acc2.add(t2);
         }
         if (k < len) {
-            const int s0 = min((int)__ldg(gsl + (int64_t)k * kTileRows), mlast);
+            const int s0 = s0n;
             float4 a0, a1, a2;
             planes(s0, a0, a1, a2);
             float2 t01;
