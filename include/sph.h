@@ -494,6 +494,19 @@ int sph_tlsph_load32(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_
                      const float* u, const float* v, const float* H, void* stream);
 int sph_tlsph_store32(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_state* st,
                       float* u, float* v, float* H, void* stream);
+/* nsteps float32 steps (Eqs. 30-31, as sph_tlsph_step) with the state kept by the caller
+ * in u, v, H (the arrays of sph_tlsph_load32, device or mapped host memory): each step
+ * reads the state in and writes it back, with the same values as sph_tlsph_load32,
+ * sph_tlsph_step(1) and sph_tlsph_store32 in turn.  The copies overlap the passes where
+ * the step allows: u is copied in by a copy engine on a second stream of the context
+ * while the momentum pass runs and v copied back (from a device buffer of the context)
+ * while the deformation pass runs; the stress factors are formed by the kernel that
+ * reads H.  u and v must be pinned (sph_host_alloc) or device memory.  Everything is enqueued on `stream` (which waits for the
+ * second stream before returning); u, v, H must not be touched until it completes.
+ * Requires precision SPH_FP32_KAHAN and the float32 records (one sph_tlsph_pack first);
+ * SPH_ERR_ARG otherwise. */
+int sph_tlsph_step_host32(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_state* st,
+                          float* u, float* v, float* H, int nsteps, void* stream);
 /* Energies of the float64 state (v, H; after float32 steps call sph_tlsph_unpack
  * first): out_host[0] = kinetic sum_i rho0 V0_i |v_i|^2 / 2, out_host[1] = stored
  * sum_i V0_i psi(F_i) with the law's stored-energy density (the potential of the

@@ -119,6 +119,7 @@ _SIGNATURES = {
     "sph_tlsph_unpack": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp]),
     "sph_tlsph_load32": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp, c_vp, c_vp, c_vp]),
     "sph_tlsph_store32": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp, c_vp, c_vp, c_vp]),
+    "sph_tlsph_step_host32": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp, c_vp, c_vp, ctypes.c_int, c_vp]),
     "sph_tlsph_energy": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp, c_vp]),
     "sph_tlsph_rates": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp, c_vp, c_vp]),
     "sph_tlsph_step": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), ctypes.c_int, c_vp]),

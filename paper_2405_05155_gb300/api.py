@@ -431,6 +431,12 @@ class TLSolid:
         self._check32(u, v, H)
         self._call("sph_tlsph_store32", _ptr(u), _ptr(v), _ptr(H), _stream())
 
+    def step_host32(self, u, v, H, nsteps=1):
+        """nsteps float32 steps with the state kept in u, v, H (as load32 takes them): each
+        step reads it in and writes it back, the copies overlapped with the passes."""
+        self._check32(u, v, H)
+        self._call("sph_tlsph_step_host32", _ptr(u), _ptr(v), _ptr(H), int(nsteps), _stream())
+
     def step(self, nsteps=1):
         self._call("sph_tlsph_step", int(nsteps), _stream())
 

@@ -51,6 +51,9 @@ struct sph_ctx {
     int batch_block = 256;
     cudaGraphExec_t batch_graph = nullptr;
     cudaStream_t capture_stream = nullptr;
+    // second stream and events of the float32 host-state step (sph_tlsph_step_host32)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t side_ev[4] = {};
     BatchGraphKey batch_key = {};
     std::vector<unsigned char> batch_blob;
 };
@@ -60,7 +63,7 @@ enum ScratchSlot {
     S_CELL_ID = 0, S_CELL_COUNT, S_CELL_START, S_CELL_FILL, S_SORTED, S_P32SORTED,
     S_ROW_LEN, S_SCAN_BLOCKS, S_ABSMAX, S_RELAX_ROWPTR, S_RELAX_COL, S_RELAX_ACC,
     S_RELAX_AMAX, S_RED_PARTIAL, S_KGC_COUNT, S_MISC0, S_MISC1, S_MISC2, S_MISC3, S_BATCH, S_MLP_PARTS,
-    S_LEARN0, S_LEARN1, S_LEARN2
+    S_LEARN0, S_LEARN1, S_LEARN2, S_TL_VOUT
 };
 
 // device status words
@@ -85,10 +88,11 @@ enum { FLAG_BAD_INPUT = 0, FLAG_NONFINITE = 1, FLAG_CAPACITY = 2, FLAG_TIMEOUT =
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Launch with the programmatic-serialization attribute (see grid_dependency_wait).
+// Launch with the programmatic-serialization attribute (see grid_dependency_wait), or
+// without it (dependent = false: an ordinary launch, e.g. after a cross-stream event wait).
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_dependent(void (*f)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                                    Args... args) {
+inline cudaError_t launch_dependent(bool dependent, void (*f)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -98,7 +102,7 @@ inline cudaError_t launch_dependent(void (*f)(KArgs...), dim3 grid, dim3 block, 
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = dependent ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, f, args...);
 }
 

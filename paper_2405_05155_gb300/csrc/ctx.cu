@@ -37,6 +37,9 @@ extern "C" int sph_destroy(sph_ctx* ctx) {
     ctx->pool.clear();
     if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+    for (cudaEvent_t e : ctx->side_ev)
+        if (e) cudaEventDestroy(e);
     for (int i = 0; i < sph_ctx::kSlots; ++i)
         if (ctx->slot_ptr[i]) cudaFree(ctx->slot_ptr[i]);
     if (ctx->flags) cudaFree(ctx->flags);

@@ -369,7 +369,7 @@ void launch32g(int out, int64_t n, const sph_eulerian_state* st, const EulerK<fl
     {                                                                               \
         auto* f = k_euler32g<DIM, M, O>;                                            \
         sph_allow_dynamic_smem((const void*)f);                                     \
-        (void)launch_dependent(f, g, b, ep.bytes, s, rin, rout, (const int64_t*)st->row_ptr, n, K, ep.A, rm, rp); \
+        (void)launch_dependent(true, f, g, b, ep.bytes, s, rin, rout, (const int64_t*)st->row_ptr, n, K, ep.A, rm, rp); \
     }
     if (out == OUT_RATES) LG(WANT_BOTH, OUT_RATES)
     else if (out == OUT_MOM) LG(WANT_MOM, OUT_MOM)

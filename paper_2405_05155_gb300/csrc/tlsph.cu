@@ -2253,7 +2253,7 @@ void tl32_passes(int which, int out, int64_t n, const sph_tlsph_state* st, const
 
 template <int DIM>
 void tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K,
-                    const TlPlan& tp, double* r1, double* r2, cudaStream_t s) {
+                    const TlPlan& tp, double* r1, double* r2, cudaStream_t s, bool dependent = true) {
     dim3 g((unsigned)((n + kTileRows - 1) / kTileRows)), b(kTileRows), gp((unsigned)tp.grid);
     if (which == 0) {
         if (tp.pipe_mom) {
@@ -2267,7 +2267,7 @@ void tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph
             // pass's last blocks (a launch error is left to cudaGetLastError)
             auto* f = out == OUT_RATES ? k_tl_mom32r<DIM, OUT_RATES> : k_tl_mom32r<DIM, OUT_STEP>;
             sph_allow_dynamic_smem((const void*)f);
-            (void)launch_dependent(f, g, b, tp.momr_bytes, s, (const float*)st->rm, st->rd,
+            (void)launch_dependent(dependent, f, g, b, tp.momr_bytes, s, (const float*)st->rm, st->rd,
                                    (const int64_t*)st->row_ptr, n, K, tp.momr, out == OUT_RATES ? r1 : nullptr);
         } else {
             auto* f = out == OUT_RATES ? k_tl_mom32g<DIM, OUT_RATES> : k_tl_mom32g<DIM, OUT_STEP>;
@@ -2297,7 +2297,7 @@ void tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph
             if (tp.bulk_defo) ctx->waits_pending = true;
             sph_allow_dynamic_smem((const void*)f);
             if (tp.geom_defo)
-                (void)launch_dependent(f, g, b, tp.defo_bytes, s, (const float*)st->rd, st->rm,
+                (void)launch_dependent(dependent, f, g, b, tp.defo_bytes, s, (const float*)st->rd, st->rm,
                                        (const int64_t*)st->row_ptr, n, K, tp.defo, (const float*)st->B32, st->H32,
                                        st->u32, out == OUT_RATES ? r2 : nullptr, ctx->flags);
             else
@@ -2322,8 +2322,8 @@ void tl32_lanes(int lanes, int which, int out, int64_t n, const sph_tlsph_state*
 // with the context's lanes per row.
 template <int DIM>
 void tl32(sph_ctx* ctx, int lanes, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K,
-          const TlPlan& tp, double* r1, double* r2, cudaStream_t s) {
-    if (tp.on) tl32_plan_pass<DIM>(ctx, which, out, n, st, K, tp, r1, r2, s);
+          const TlPlan& tp, double* r1, double* r2, cudaStream_t s, bool dependent = true) {
+    if (tp.on) tl32_plan_pass<DIM>(ctx, which, out, n, st, K, tp, r1, r2, s, dependent);
     else if (K.periodic) tl32_lanes<DIM, true>(lanes, which, out, n, st, K, r1, r2, s);
     else tl32_lanes<DIM, false>(lanes, which, out, n, st, K, r1, r2, s);
 }
@@ -2443,6 +2443,48 @@ __global__ void k_tl_store32(const float* __restrict__ RD, const float* __restri
     for (int k = 0; k < DIM * DIM; ++k) H[k * n + i] = H32[k * n + i];
 }
 
+// The pieces of sph_tlsph_step_host32: H and v read in, with the stress factor of the
+// read H (as k_tl_stress32); u read in; v written out; H and u written out.
+template <int DIM>
+__global__ void k_tl_load32_hv(const float* __restrict__ v, const float* __restrict__ H, int64_t n, TLK<float> K,
+                               const float* __restrict__ B32, float* __restrict__ RD, float* __restrict__ H32,
+                               float* __restrict__ RM) {
+    constexpr int NS = DIM == 2 ? 3 : 6;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float h[DIM * DIM], b[NS], m[DIM * DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) RD[8 * i + 4 + a] = v[a * n + i];
+#pragma unroll
+    for (int k = 0; k < DIM * DIM; ++k) {
+        h[k] = H[k * n + i];
+        H32[k * n + i] = h[k];
+    }
+#pragma unroll
+    for (int q = 0; q < NS; ++q) b[q] = B32[q * n + i];
+    stress_factor<DIM, float>(h, b, K, m);
+    store_M<DIM>(RM, i, m);
+}
+
+template <int DIM>
+__global__ void k_tl_store32_v(const float* __restrict__ RD, int64_t n, float* __restrict__ v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) v[a * n + i] = RD[8 * i + 4 + a];
+}
+
+template <int DIM>
+__global__ void k_tl_store32_hu(const float* __restrict__ H32, const float* __restrict__ u32, int64_t n,
+                                float* __restrict__ H, float* __restrict__ u) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) u[a * n + i] = u32[a * n + i];
+#pragma unroll
+    for (int k = 0; k < DIM * DIM; ++k) H[k * n + i] = H32[k * n + i];
+}
+
 extern "C" int sph_tlsph_load32(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st, const float* u,
                                 const float* v, const float* H, void* stream) {
     if (!ctx) return SPH_ERR_ARG;
@@ -2471,6 +2513,75 @@ extern "C" int sph_tlsph_store32(sph_ctx* ctx, const sph_tlsph_params* p, const 
     else k_tl_store32<3><<<grid_for(n, 256), 256, 0, s>>>(st->rd, st->u32, st->H32, n, u, v, H);
     SPH_LAUNCH_CHECK(ctx);
     return SPH_OK;
+}
+
+// nsteps float32 steps with the state kept by the caller (sph.h): per step the same
+// values as sph_tlsph_load32, sph_tlsph_step(1) and sph_tlsph_store32.  The stress update
+// is done by the kernel that reads H in; u is copied in by a copy engine on a second
+// stream while the momentum pass runs (only the deformation pass needs it), and v,
+// gathered from the records into a device buffer once the momentum pass has made it
+// final, is copied out there while the deformation pass runs.  Copy engines, not kernels,
+// move these two, so that they take no SM from the passes they overlap; events order the
+// two streams, and the caller's stream waits for the second at the end of each step.
+namespace {
+
+template <int DIM>
+int tl_step_host32(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st, float* u, float* v,
+                   float* H, int nsteps, cudaStream_t s) {
+    const int64_t n = p->dom.n;
+    if (!ctx->side_stream) SPH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : ctx->side_ev)
+        if (!e) SPH_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaStream_t s2 = ctx->side_stream;
+    cudaEvent_t hv_in = ctx->side_ev[0], u_in = ctx->side_ev[1], mom_done = ctx->side_ev[2], v_out = ctx->side_ev[3];
+    int r = SPH_OK;
+    float* vout = (float*)sph_scratch(ctx, S_TL_VOUT, (size_t)DIM * n * sizeof(float), &r);
+    if (r) return r;
+    const size_t ubytes = (size_t)DIM * n * sizeof(float);
+    TLK<float> K = make_tl_consts<float>(p);
+    TlPlan ts = tl_plan(ctx, st, n, DIM);
+    const int lanes = ctx->lanes[SPH_PASS_TLSPH];
+    const unsigned g = grid_for(n, 256);
+    for (int k = 0; k < nsteps; ++k) {
+        k_tl_load32_hv<DIM><<<g, 256, 0, s>>>(v, H, n, K, st->B32, st->rd, st->H32, st->rm);
+        SPH_CUDA(ctx, cudaEventRecord(hv_in, s));
+        SPH_CUDA(ctx, cudaStreamWaitEvent(s2, hv_in, 0));
+        SPH_CUDA(ctx, cudaMemcpyAsync(st->u32, u, ubytes, cudaMemcpyDefault, s2));
+        SPH_CUDA(ctx, cudaEventRecord(u_in, s2));
+        int t = sph_timer_begin(ctx, SPH_TIMER_TL_MOMENTUM, s);
+        tl32<DIM>(ctx, lanes, 0, OUT_STEP, n, st, K, ts, nullptr, nullptr, s, false);
+        sph_timer_end(ctx, t, s);
+        k_tl_store32_v<DIM><<<g, 256, 0, s>>>(st->rd, n, vout);
+        SPH_CUDA(ctx, cudaEventRecord(mom_done, s));
+        SPH_CUDA(ctx, cudaStreamWaitEvent(s2, mom_done, 0));
+        SPH_CUDA(ctx, cudaMemcpyAsync(v, vout, ubytes, cudaMemcpyDefault, s2));
+        SPH_CUDA(ctx, cudaEventRecord(v_out, s2));
+        SPH_CUDA(ctx, cudaStreamWaitEvent(s, u_in, 0));
+        t = sph_timer_begin(ctx, SPH_TIMER_TL_DEFORM, s);
+        tl32<DIM>(ctx, lanes, 1, OUT_STEP, n, st, K, ts, nullptr, nullptr, s, false);
+        sph_timer_end(ctx, t, s);
+        k_tl_store32_hu<DIM><<<g, 256, 0, s>>>(st->H32, st->u32, n, H, u);
+        // the next step's read of v (and the caller's use of it) after its write-back
+        SPH_CUDA(ctx, cudaStreamWaitEvent(s, v_out, 0));
+    }
+    SPH_LAUNCH_CHECK(ctx);
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" int sph_tlsph_step_host32(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st, float* u,
+                                     float* v, float* H, int nsteps, void* stream) {
+    if (!ctx || nsteps < 0) return SPH_ERR_ARG;
+    int r = check_tl(p, st);
+    if (r) return r;
+    if (p->precision != SPH_FP32_KAHAN || !fp32_ready(st)) return SPH_ERR_ARG;
+    const int64_t n = p->dom.n;
+    if (n == 0 || nsteps == 0) return SPH_OK;
+    if (!u || !v || !H) return SPH_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    return p->dom.dim == 2 ? tl_step_host32<2>(ctx, p, st, u, v, H, nsteps, s)
+                           : tl_step_host32<3>(ctx, p, st, u, v, H, nsteps, s);
 }
 
 extern "C" int sph_tlsph_unpack(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_state* st, void* stream) {

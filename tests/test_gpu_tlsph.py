@@ -456,6 +456,46 @@ def test_state_in_mapped_host_memory(ctx):
 
 
 @pytest.mark.parametrize("dim", [3, 2])
+def test_step_host32_equals_the_composed_calls(ctx, dim):
+    # sph_tlsph_step_host32 (copies overlapped with the passes on a second stream) gives
+    # the state of load32 / step(1) / store32 in turn, bit for bit, in mapped host memory
+    s = _setup(ctx, dp=0.005) if dim == 3 else _setup(ctx, case=inputs.beam2d(dp=0.002))
+    n = s["r0"].shape[1]
+    a = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
+    b = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
+    shapes = ((dim, n), (dim, n), (dim * dim, n))
+    ha = [api.HostArray(sh, torch.float32) for sh in shapes]
+    hb = [api.HostArray(sh, torch.float32) for sh in shapes]
+    try:
+        a.pack()
+        b.pack()
+        a.store32(*ha)
+        b.store32(*hb)
+        torch.cuda.synchronize()
+        for _ in range(4):
+            a.load32(*ha)
+            a.step(1)
+            a.store32(*ha)
+        b.step_host32(*hb, nsteps=4)
+        torch.cuda.synchronize()
+        for x, y in zip(ha, hb):
+            assert torch.equal(x.t, y.t)
+        assert torch.equal(a.rd, b.rd) and torch.equal(a.H32, b.H32) and torch.equal(a.u32, b.u32)
+        assert bool(torch.isfinite(hb[1].t).all()) and float(hb[1].t.abs().max()) > 0.0
+        # on device arrays too
+        dev = [torch.empty(sh, dtype=torch.float32, device="cuda") for sh in shapes]
+        a.store32(*dev)
+        a.step_host32(*dev, nsteps=2)
+        b.step_host32(*hb, nsteps=2)
+        torch.cuda.synchronize()
+        for x, y in zip(dev, hb):
+            assert torch.equal(x.cpu(), y.t)
+    finally:
+        for h in ha + hb:
+            h.close()
+
+
+@pytest.mark.parametrize("dim", [3, 2])
 def test_float32_state_round_trip(ctx, dim):
     # the float32 form's state kept in mapped host memory as float32 (u = x - r0, v, F - I)
     # and exchanged every 2 steps with load32 / store32: bit for bit the device-resident run;
