@@ -34,6 +34,14 @@ def rel_elem(a, ref, floor=1e-3):
     return float(np.max(np.abs(a - ref) / den))
 
 
+def rel_fp64(a, ref):
+    """The float64 parity measure: the normwise max relative error, and the element-wise one
+    (rel_elem, 1e-3 floor) scaled by 1e-3, so that a 1e-12 bound also holds every element
+    to 1e-9 of its own magnitude (fields evolved over tens of steps gather rounding from
+    sums taken in another order)."""
+    return max(rel_max(a, ref), 1e-3 * rel_elem(a, ref))
+
+
 def rel_l2(a, ref):
     """Relative L2 error (Eq. 10 form), the float32 parity measure."""
     den = np.linalg.norm(ref)

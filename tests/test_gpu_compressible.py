@@ -9,7 +9,7 @@ its float64 state over a run."""
 import numpy as np
 import pytest
 
-from helpers import cuda, host, odom, oracle_rows, rel_l2, rel_max, sample_rows, sorted_by_cells
+from helpers import cuda, host, odom, oracle_rows, rel_fp64, rel_l2, rel_max, sample_rows, sorted_by_cells
 from oracle import compressible as OC
 from oracle import kgc as OK
 from oracle import neighbors as ON
@@ -63,7 +63,7 @@ def _sim(ctx, d, pos, vol, dev, rho, mom, E, dt, eta=1.0, precision=api.SPH_FP64
 
 
 # (precision, tolerance, measure) of the rates
-FORMS = ((api.SPH_FP64, 1e-12, rel_max), (api.SPH_FP32_KAHAN, 1e-5, rel_l2))
+FORMS = ((api.SPH_FP64, 1e-12, rel_fp64), (api.SPH_FP32_KAHAN, 1e-5, rel_l2))
 
 
 @pytest.mark.parametrize("dim,m", [(2, 24), (3, 9)])

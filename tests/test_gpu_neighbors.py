@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import cuda, host, odom, rel_max, sample_rows, sorted_by_cells
+from helpers import cuda, host, odom, rel_fp64, rel_max, sample_rows, sorted_by_cells
 from oracle import kernels as OKr
 from oracle import kgc as OK
 from oracle import neighbors as ON
@@ -155,7 +155,7 @@ def test_kgc_parity(ctx, which):
     B, fb, nfb = api.kgc(ctx, d, cuda(pos), cuda(vol), rp, col)
     B_o, fb_o = OK.kgc(pos, vol, host(rp), host(col), odom(d))
     assert np.array_equal(host(fb), fb_o) and nfb == int(fb_o.sum())
-    assert rel_max(host(B), B_o) < 1e-12
+    assert rel_fp64(host(B), B_o) < 1e-12
 
 
 def test_kgc_fallback_and_lg_kernel(ctx):
@@ -169,7 +169,7 @@ def test_kgc_fallback_and_lg_kernel(ctx):
         B, fb, nfb = api.kgc(ctx, d, cuda(pos), cuda(vol), rp, col, kernel)
         B_o, fb_o = OK.kgc(pos, vol, host(rp), host(col), odom(d), kind)
         assert host(fb)[-1] == 1 and np.array_equal(host(fb), fb_o)
-        assert rel_max(host(B), B_o) < 1e-12
+        assert rel_fp64(host(B), B_o) < 1e-12
 
 
 def test_full_size_plate_neighbors_sampled(ctx):
