@@ -254,8 +254,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward_tc(const float* __r
                     const int c0 = chalf * 64 + h * 32;
                     float v[32];
                     tmem_ld32(trow + (uint32_t)c0, v);
+                    // + bias and GELU two columns at a time (the bias, in shared memory, read as float4)
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) v[c] = gelu(v[c] + b[c0 + c]);
+                    for (int c = 0; c < 32; c += 4) {
+                        const float4 bb = *reinterpret_cast<const float4*>(b + c0 + c);
+                        const float2 z0 = __fadd2_rn(make_float2(v[c], v[c + 1]), make_float2(bb.x, bb.y));
+                        const float2 z1 = __fadd2_rn(make_float2(v[c + 2], v[c + 3]), make_float2(bb.z, bb.w));
+                        const float2 g0 = gelu_as::gelu2(z0), g1 = gelu_as::gelu2(z1);
+                        v[c] = g0.x;
+                        v[c + 1] = g0.y;
+                        v[c + 2] = g1.x;
+                        v[c + 3] = g1.y;
+                    }
 #pragma unroll
                     for (int c = 0; c < 4; ++c) store8(A, row, c0 + 8 * c, v + 8 * c);
                 }
