@@ -1177,8 +1177,9 @@ def run_gpu(args):
             "e2e": {"value": e2e32_value, "unit": UNIT, "steps": e2e_steps, "ms_per_step": e2e32_ms / e2e_steps,
                     "h2d_bytes_per_step": h2d32, "d2h_bytes_per_step": h2d32, "state_finite": e2e32_ok,
                     "state_form": "float32 (u = x - r0, v, F - I), 12 floats + 3x3 per particle; earlier "
-                                  "lines of this file's history reported the float64 state under this key, "
-                                  "now with_f64_state",
+                                  "lines of this file's history reported the float64 state under this key "
+                                  "(now with_f64_state) and then the float32 state moved by three separate "
+                                  "calls (now three_calls)",
                     "what": "per step, one call through the C ABI (sph_tlsph_step_host32): the float32 form's "
                             "state (u = x - r0, v, F - I) in float32 mapped page-locked host buffers "
                             "(sph_host_alloc) read in place over NVLink-C2C, one step, written back in place; "
