@@ -140,7 +140,10 @@ int sph_set_stage_cap(sph_ctx* ctx, int cap);
  *                       neighbour slots; the momentum pass sums Eq. 30 as
  *                       M_i S_i + sum_j (V0_j M_j) grad0 W_ij with the plan's
  *                       S_i = sum_j grad0 W_ij V0_j (boxes with a periodic axis: the
- *                       momentum pass streams its entries).  Results differ from the
+ *                       momentum pass streams its entries); the deformation pass
+ *                       copies the tile's slots into shared memory with one TMA bulk
+ *                       copy (bounded wait); both passes are launched as programmatic
+ *                       dependents of the pass before.  Results differ from the
  *                       other modes by float32 rounding.  The default: the fastest
  *                       measured.
  * SPH_ERR_ARG for any other mode. */
@@ -477,7 +480,8 @@ int sph_tlsph_plan(sph_ctx* ctx, const sph_tlsph_params* prm, sph_tlsph_state* s
 int sph_tlsph_plan_bytes(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_state* st,
                          int64_t* bytes_host, void* stream);
 /* packed float32 (rd, H32, u32) -> float64 (v, H, x = r0 + u).  After steps of
- * the persistent or bulk planned forms (sph_set_tile_pipeline) it synchronises the stream and
+ * the planned forms with bounded waits (persistent, bulk, and the geometry form's slot
+ * copy; sph_set_tile_pipeline) it synchronises the stream and
  * returns SPH_ERR_TIMEOUT if a bounded device wait expired since the previous unpack
  * (the results are then not valid). */
 int sph_tlsph_unpack(sph_ctx* ctx, const sph_tlsph_params* prm,

@@ -1509,18 +1509,24 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
     // first row (decoded once per neighbour, not per pair)
     constexpr bool REL = GEOM && !PER;
     const uint32_t bref = REL ? __float_as_uint(RD[8 * i0 + DIM]) : 0u;
-    // REL: the tile's slot block (its entries' 2-byte slots, 256 bytes per position)
-    // copied into shared memory after the two staged planes with cp.async while the
-    // neighbours are staged, when the plan's longest row allows (A.ecap positions)
+    // REL: the tile's slot block (its entries' 2-byte slots, 256 bytes per position, one
+    // contiguous range of the plan) copied into shared memory after the two staged planes by
+    // one TMA bulk copy, issued first (plan data: before the dependency wait) and completed
+    // on an mbarrier (bounded wait), when the plan's longest row allows (A.ecap positions).
+    // A.test_polls > 0 (failure-detection test): no copy, and the wait runs out.
     uint16_t* ssl = reinterpret_cast<uint16_t*>(sp + 2 * A.mcap);
+    uint64_t* sbar = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(ssl) + (size_t)A.ecap * kTileRows * 2);
     const int width = REL ? A.tile_e[tile] / kTileRows : 0;
     const bool sslot = REL && width <= A.ecap;
-    if (sslot) {
-        const unsigned char* src = reinterpret_cast<const unsigned char*>(A.slots + A.tile_so[tile]);
-        const int chunks = width * (2 * kTileRows / 16);
-        for (int c = threadIdx.x; c < chunks; c += blockDim.x)
-            cp_async16(reinterpret_cast<unsigned char*>(ssl) + 16 * c, src + 16 * c);
-        cp_async_commit();
+    const bool slot_test = sslot && A.test_polls > 0;
+    if (sslot && threadIdx.x == 0) {
+        mbar_init(sbar, 1);
+        mbar_fence_init();
+        if (!slot_test) {
+            const uint32_t bytes = (uint32_t)width * kTileRows * 2u;
+            mbar_arrive_expect_tx(sbar, bytes);
+            tma_load_1d(ssl, A.slots + A.tile_so[tile], bytes, sbar);
+        }
     }
     // up to four neighbours per thread per round: their indices first, then their records
     // two at a time, so that few round trips to memory are in series
@@ -1564,8 +1570,15 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
                 }
             }
         }
-        if (sslot) cp_async_wait_all();
         __syncthreads();
+        if (sslot) {
+            const bool late = !mbar_wait_bounded(sbar, 0, slot_test ? A.test_polls : kWaitPolls);
+            if (__syncthreads_or(late)) {      // block-uniform: the copy never completed
+                if (threadIdx.x == 0) atomicExch(&flags[FLAG_TIMEOUT], 1);
+                if (!slot_test) mbar_wait_bounded(sbar, 0, kWaitPolls);    // a copy issued is waited for
+                return;
+            }
+        }
     } else {
         staged = GEOM ? stage_neighbours<2, 8, 0>(RD, n, P0, m, A, sp, A.spos)
                       : stage_neighbours<1, 8>(RD, n, P0, m, A, sp);
@@ -2214,7 +2227,8 @@ TlPlan tl_plan(const sph_ctx* ctx, const sph_tlsph_state* st, int64_t n, int dim
         // the tile's slot block in shared memory too, up to 128 positions (32 KB)
         t.defo.tile_e = tp.tile_e;
         t.defo.ecap = st->plan_maxrow <= 128 ? (int)st->plan_maxrow : 0;
-        t.defo_bytes = (size_t)mg * 32 + (size_t)t.defo.ecap * kTileRows * 2;
+        t.defo_bytes = (size_t)mg * 32 + (size_t)t.defo.ecap * kTileRows * 2 + 16;   // + the slot copy's mbarrier
+        t.defo.test_polls = ctx->wait_test_polls;
         // the momentum pass's geometry form (used on boxes without periodic axes): position
         // and V0_j M_j staged, 48 bytes per neighbour in 3D (24 in 2D); slots and S_i read
         // from the plan
@@ -2294,7 +2308,7 @@ void tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph
                     f = out == OUT_RATES ? k_tl_defo32g<DIM, OUT_RATES, false, true, false>
                                          : k_tl_defo32g<DIM, OUT_STEP, false, true, false>;
             }
-            if (tp.bulk_defo) ctx->waits_pending = true;
+            if (tp.bulk_defo || tp.geom_defo) ctx->waits_pending = true;
             sph_allow_dynamic_smem((const void*)f);
             if (tp.geom_defo)
                 (void)launch_dependent(dependent, f, g, b, tp.defo_bytes, s, (const float*)st->rd, st->rm,

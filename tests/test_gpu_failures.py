@@ -69,6 +69,30 @@ def test_bounded_wait_timeout_is_reported_and_the_context_recovers(ctx):
         ctx.set_tile_pipeline(api.SPH_PIPE_GEOM)
 
 
+def test_geometry_form_slot_copy_timeout_is_reported(ctx):
+    # the default (geometry-form) deformation pass copies each tile's slot block with one
+    # TMA bulk copy whose wait is bounded: under the wait test nothing is copied, the wait
+    # runs out, the step reports SPH_ERR_TIMEOUT, and the same context then runs as before
+    ctx.set_tile_pipeline(api.SPH_PIPE_GEOM)
+    ref = _plate_solid(ctx)
+    ref.step(2)
+    ref.unpack()
+    sol = _plate_solid(ctx)
+    ctx.set_wait_test(256)
+    try:
+        sol.step(1)
+        with pytest.raises(L.SphError) as e:
+            sol.unpack()
+        assert e.value.status == L.SPH_ERR_TIMEOUT
+    finally:
+        ctx.set_wait_test(0)
+    again = _plate_solid(ctx)
+    again.step(2)
+    again.unpack()
+    torch.cuda.synchronize()
+    assert torch.isfinite(again.v).all() and torch.equal(again.v, ref.v)
+
+
 def test_wait_test_argument_checks(ctx):
     with pytest.raises(L.SphError) as e:
         ctx.set_wait_test(1 << 20)
