@@ -1030,7 +1030,7 @@ def run_gpu(args):
     # passes; tl_pair_passes_plate816k_full.md: the entry forms of the stream mode)
     pipe = args.pipe or "geom"
     ncu_traffic = {("tl_momentum_pass", "geom"): 167.1e6, ("tl_momentum_pass", "stream"): 446.8e6,
-                   ("tl_deformation_pass", "geom"): 197.2e6, ("tl_deformation_pass", "stream"): 509.1e6}
+                   ("tl_deformation_pass", "geom"): 197.1e6, ("tl_deformation_pass", "stream"): 509.1e6}
     traffic = args.traffic if args.traffic is not None else ncu_traffic.get((dominant[0], pipe))
 
     # end to end through the C ABI with the float64 state (x, v, F - I) in host memory:
