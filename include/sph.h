@@ -124,6 +124,20 @@ int sph_get_lanes(const sph_ctx* ctx, int pass);
  * many as the plan needs, within 96 KB); tiles with more read their neighbours from
  * global memory.  A launch-shape setting, like the lanes: results do not depend on it. */
 int sph_set_stage_cap(sph_ctx* ctx, int cap);
+/* How the planned Eulerian passes (single and batched) read their pair entries (a
+ * launch-shape setting: results do not depend on it):
+ *   SPH_RING_AUTO    the chunk ring for launches of at least two waves of blocks
+ *                    (2 x 6 blocks per SM x SMs), else the thread ring (the default);
+ *   SPH_RING_THREAD  each thread streams its own entries through 4 slots in shared
+ *                    memory with cp.async (the shorter chain when one wave is the pass);
+ *   SPH_RING_CHUNK   one step of the tile's entries (4 KB) per TMA bulk copy, 4 in flight,
+ *                    each completing on an mbarrier and refilled when the block has read it
+ *                    (bounded waits: SPH_ERR_TIMEOUT at the next unpack).
+ * SPH_ERR_ARG for any other mode. */
+#define SPH_RING_AUTO   0
+#define SPH_RING_THREAD 1
+#define SPH_RING_CHUNK  2
+int sph_set_entry_ring(sph_ctx* ctx, int mode);
 /* Planned TL passes, how pair entries reach a block (a launch-shape setting:
  * results do not depend on it, apart from the rounding SPH_PIPE_GEOM notes):
  *   SPH_PIPE_STREAM     one block per tile, entries streamed from global memory;

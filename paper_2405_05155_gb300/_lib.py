@@ -20,6 +20,7 @@ SPH_TWO_PASS, SPH_FUSED = 0, 1
 SPH_SVK, SPH_NEO_HOOKEAN = 0, 1
 SPH_PASS_EULERIAN, SPH_PASS_TLSPH, SPH_PASS_RELAX, SPH_PASS_BATCHED, SPH_PASS_COMPRESSIBLE = 0, 1, 2, 3, 4
 SPH_PIPE_STREAM, SPH_PIPE_PERSISTENT, SPH_PIPE_BULK, SPH_PIPE_GEOM = 0, 1, 2, 3
+SPH_RING_AUTO, SPH_RING_THREAD, SPH_RING_CHUNK = 0, 1, 2
 SPH_TIMER_BATCH_STEP = 9
 SPH_MAX_SPHERES = 16
 (SPH_TIMER_TL_STRESS, SPH_TIMER_TL_MOMENTUM, SPH_TIMER_TL_DEFORM, SPH_TIMER_EU_MOMENTUM, SPH_TIMER_EU_MASS,
@@ -146,6 +147,7 @@ _SIGNATURES = {
     "sph_tlsph_plan_bytes": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), _P(c_i64), c_vp]),
     "sph_tlsph_plan": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp]),
     "sph_set_stage_cap": (ctypes.c_int, [c_vp, ctypes.c_int]),
+    "sph_set_entry_ring": (ctypes.c_int, [c_vp, ctypes.c_int]),
     "sph_set_relax_skin": (ctypes.c_int, [c_vp, ctypes.c_double]),
     "sph_compressible_rates": (ctypes.c_int, [c_vp, _P(CompressibleParams), _P(CompressibleState), c_vp, c_vp,
                                               c_vp, c_vp]),

@@ -12,7 +12,7 @@ from ._lib import (SPH_FP32_KAHAN, SPH_FP64, SPH_FUSED, SPH_LAGUERRE_GAUSS,  # n
                    SPH_NEO_HOOKEAN, SPH_SVK, SPH_TWO_PASS, SPH_WENDLAND_C2, SPH_PASS_BATCHED,
                    SPH_PASS_COMPRESSIBLE, SPH_PASS_EULERIAN, SPH_PASS_RELAX, SPH_PASS_TLSPH, SPH_TIMER_NEIGHBORS,
                    SPH_TIMER_RELAX_ACCEL, SPH_TIMER_RELAX_UPDATE, SPH_PIPE_STREAM, SPH_PIPE_PERSISTENT,
-                   SPH_PIPE_BULK, SPH_PIPE_GEOM)
+                   SPH_PIPE_BULK, SPH_PIPE_GEOM, SPH_RING_AUTO, SPH_RING_CHUNK, SPH_RING_THREAD)
 
 NSYM = {2: 3, 3: 6}
 
@@ -90,6 +90,11 @@ class Context:
 
     def set_stage_cap(self, cap):
         L.check("sph_set_stage_cap", self.lib.sph_set_stage_cap(self.h, int(cap)), self.h)
+
+    def set_entry_ring(self, mode):
+        """How the planned Eulerian passes read their pair entries: SPH_RING_AUTO (default),
+        SPH_RING_THREAD or SPH_RING_CHUNK (results do not depend on it)."""
+        L.check("sph_set_entry_ring", self.lib.sph_set_entry_ring(self.h, int(mode)), self.h)
 
     def set_relax_skin(self, skin_over_h):
         """Skin of the float32 relaxation list in units of h (0: a cell sweep every step)."""

@@ -71,12 +71,13 @@ struct PlanCase {
     int64_t offset, n, tile0;
 };
 
-template <int DIM, int MODE, int OUT>
+template <int DIM, int MODE, int OUT, bool CHUNK>
 __global__ void __launch_bounds__(kTileRows, 6) k_euler32g_batched(const float* __restrict__ Rin,
                                                                    float* __restrict__ Rout,
                                                                    const int64_t* __restrict__ row_ptr, int ncases,
                                                                    const EulerK<float>* __restrict__ cases,
-                                                                   const PlanCase* __restrict__ plans) {
+                                                                   const PlanCase* __restrict__ plans,
+                                                                   int* __restrict__ flags) {
     extern __shared__ __align__(16) unsigned char eb_smem[];
     // momentum pass in reverse tile order, continuity pass forwards (pair entries reused from L2)
     const int64_t b = MODE == WANT_MOM ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
@@ -88,8 +89,8 @@ __global__ void __launch_bounds__(kTileRows, 6) k_euler32g_batched(const float* 
     }
     const PlanCase C = plans[lo];
     const EulerK<float> K = cases[lo];
-    euler_tile_g<DIM, MODE, OUT>(Rin, Rout, row_ptr, C.offset, row_ptr[C.offset], C.n, b - C.tile0, K, C.A,
-                                 reinterpret_cast<float4*>(eb_smem), nullptr, nullptr);
+    euler_tile_g<DIM, MODE, OUT, CHUNK>(Rin, Rout, row_ptr, C.offset, row_ptr[C.offset], C.n, b - C.tile0, K, C.A,
+                                        reinterpret_cast<float4*>(eb_smem), nullptr, nullptr, flags);
 }
 
 // Launch shape of the planned form: the tile count and a stage capacity common to
@@ -97,17 +98,20 @@ __global__ void __launch_bounds__(kTileRows, 6) k_euler32g_batched(const float* 
 struct PlanShape {
     int64_t tiles;
     int mcap;
+    bool chunk;    // the entries through the TMA chunk ring (one launch covers every case's tiles)
 };
 
 PlanShape plan_shape(const sph_ctx* ctx, const sph_batch_case* cases, int ncases) {
-    PlanShape sh{0, 1};
+    PlanShape sh{0, 1, false};
     int32_t maxm = 0;
     for (int c = 0; c < ncases; ++c) {
-        if (!cases[c].plan || cases[c].plan_nnz < 1 || cases[c].plan_maxm < 1) return PlanShape{0, 1};
+        if (!cases[c].plan || cases[c].plan_nnz < 1 || cases[c].plan_maxm < 1) return PlanShape{0, 1, false};
         maxm = cases[c].plan_maxm > maxm ? cases[c].plan_maxm : maxm;
         sh.tiles += (cases[c].n + kTileRows - 1) / kTileRows;
     }
     sh.mcap = stage_mcap(maxm, 1, ctx->stage_cap);
+    const int64_t waves = kChunkRingWaves * (int64_t)6 * (ctx->num_sms > 0 ? ctx->num_sms : 1);
+    sh.chunk = ctx->entry_ring == SPH_RING_CHUNK || (ctx->entry_ring == SPH_RING_AUTO && sh.tiles >= waves);
     return sh;
 }
 
@@ -184,25 +188,27 @@ void launch_step(const BatchPlan& pl, int dim, const sph_batch_state* st, int64_
 }
 
 void launch_step_planned(int dim, const sph_batch_state* st, int ncases, const EulerK<float>* dK,
-                         const PlanCase* dP, const PlanShape& sh, cudaStream_t s) {
+                         const PlanCase* dP, const PlanShape& sh, int* flags, cudaStream_t s) {
     dim3 g((unsigned)sh.tiles), b(kTileRows);
     size_t smem = (size_t)sh.mcap * 16 + kEntryRingBytes;
     float* r0 = st->rec;
     float* r1 = st->rec_tmp;
     if (dim == 2) {
-        auto* fm = k_euler32g_batched<2, WANT_MOM, OUT_MOM>;
-        auto* fc = k_euler32g_batched<2, WANT_MASS, OUT_MASS>;
+        auto* fm = sh.chunk ? k_euler32g_batched<2, WANT_MOM, OUT_MOM, true> : k_euler32g_batched<2, WANT_MOM, OUT_MOM, false>;
+        auto* fc = sh.chunk ? k_euler32g_batched<2, WANT_MASS, OUT_MASS, true>
+                            : k_euler32g_batched<2, WANT_MASS, OUT_MASS, false>;
         sph_allow_dynamic_smem((const void*)fm);
         sph_allow_dynamic_smem((const void*)fc);
-        fm<<<g, b, smem, s>>>(r0, r1, st->row_ptr, ncases, dK, dP);
-        fc<<<g, b, smem, s>>>(r1, r0, st->row_ptr, ncases, dK, dP);
+        fm<<<g, b, smem, s>>>(r0, r1, st->row_ptr, ncases, dK, dP, flags);
+        fc<<<g, b, smem, s>>>(r1, r0, st->row_ptr, ncases, dK, dP, flags);
     } else {
-        auto* fm = k_euler32g_batched<3, WANT_MOM, OUT_MOM>;
-        auto* fc = k_euler32g_batched<3, WANT_MASS, OUT_MASS>;
+        auto* fm = sh.chunk ? k_euler32g_batched<3, WANT_MOM, OUT_MOM, true> : k_euler32g_batched<3, WANT_MOM, OUT_MOM, false>;
+        auto* fc = sh.chunk ? k_euler32g_batched<3, WANT_MASS, OUT_MASS, true>
+                            : k_euler32g_batched<3, WANT_MASS, OUT_MASS, false>;
         sph_allow_dynamic_smem((const void*)fm);
         sph_allow_dynamic_smem((const void*)fc);
-        fm<<<g, b, smem, s>>>(r0, r1, st->row_ptr, ncases, dK, dP);
-        fc<<<g, b, smem, s>>>(r1, r0, st->row_ptr, ncases, dK, dP);
+        fm<<<g, b, smem, s>>>(r0, r1, st->row_ptr, ncases, dK, dP, flags);
+        fc<<<g, b, smem, s>>>(r1, r0, st->row_ptr, ncases, dK, dP, flags);
     }
 }
 
@@ -246,10 +252,12 @@ int upload_cases(sph_ctx* ctx, const sph_batch_case* cases, int ncases, int dim,
     off[ncases] = cases[ncases - 1].offset + cases[ncases - 1].n;
     PlanShape sh = plan_shape(ctx, cases, ncases);
     std::vector<PlanCase> P(sh.tiles ? ncases : 0);
+    const int chunk_ring = sh.chunk ? 1 : 0;
     int64_t t0 = 0;
     for (size_t c = 0; c < P.size(); ++c) {
         TilePlan tp = tile_plan_view(const_cast<void*>(cases[c].plan), cases[c].n, cases[c].plan_nnz);
-        P[c].A = GeoArgsE{tp.tile_m, tp.tile_so, tp.uidx, reinterpret_cast<const float*>(tp.geo), sh.mcap};
+        P[c].A = GeoArgsE{tp.tile_m, tp.tile_so, tp.uidx, reinterpret_cast<const float*>(tp.geo), sh.mcap,
+                          ctx->wait_test_polls, chunk_ring};
         P[c].offset = cases[c].offset;
         P[c].n = cases[c].n;
         P[c].tile0 = t0;
@@ -323,13 +331,13 @@ int run_steps(sph_ctx* ctx, const BatchPlan& pl, int dim, const sph_batch_state*
     key.row_ptr = st->row_ptr; key.col = st->col; key.rec = st->rec; key.rec_tmp = st->rec_tmp;
     key.ntotal = ntotal; key.ncases = ncases; key.lanes = pl.lanes; key.block = pl.block; key.grid = pl.grid;
     key.dK = dK; key.dim = dim;
-    if (dP) { key.lanes = 0; key.block = kTileRows; key.grid = sh.mcap; }
+    if (dP) { key.lanes = sh.chunk ? -1 : 0; key.block = kTileRows; key.grid = sh.mcap; }
     if (!ctx->batch_graph || tables_changed || std::memcmp(&key, &ctx->batch_key, sizeof(key)) != 0) {
         if (ctx->batch_graph) { cudaGraphExecDestroy(ctx->batch_graph); ctx->batch_graph = nullptr; }
         if (!ctx->capture_stream) SPH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
         SPH_CUDA(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
-        if (dP) launch_step_planned(dim, st, ncases, dK, dP, sh, ctx->capture_stream);
+        if (dP) launch_step_planned(dim, st, ncases, dK, dP, sh, ctx->flags, ctx->capture_stream);
         else launch_step(pl, dim, st, ntotal, ncases, dK, dOff, ctx->capture_stream);
         cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &g);
         if (e != cudaSuccess) { ctx->last_cuda_error = (int)e; return SPH_ERR_CUDA; }
@@ -338,6 +346,7 @@ int run_steps(sph_ctx* ctx, const BatchPlan& pl, int dim, const sph_batch_state*
         if (e != cudaSuccess) { ctx->batch_graph = nullptr; ctx->last_cuda_error = (int)e; return SPH_ERR_CUDA; }
         ctx->batch_key = key;
     }
+    if (dP && sh.chunk) ctx->waits_pending = true;      // the chunk ring's bounded waits
     for (int k = 0; k < nsteps; ++k) {
         int t = sph_timer_begin(ctx, SPH_TIMER_BATCH_STEP, s);
         SPH_CUDA(ctx, cudaGraphLaunch(ctx->batch_graph, s));

@@ -44,6 +44,7 @@ struct sph_ctx {
     int lanes[5] = {4, 4, 1, 4, 1};   // lanes per particle of the float32 pair passes (SPH_PASS_*)
     int stage_cap = 0;             // most neighbour records a tile stages in shared memory (0: default)
     int tile_pipe = SPH_PIPE_GEOM;   // planned TL passes: how pair entries reach a block (SPH_PIPE_*)
+    int entry_ring = SPH_RING_AUTO;  // planned Eulerian passes: how a block reads its entries (SPH_RING_*)
     bool waits_pending = false;    // a kernel with bounded waits ran since the timeout flag was read
     uint32_t wait_test_polls = 0;  // failure-detection test: bounded waits on a phase nothing completes
     double relax_skin = 0.2;       // float32 relaxation: list skin / h (0: a cell sweep every step)

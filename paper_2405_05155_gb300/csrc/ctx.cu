@@ -136,6 +136,12 @@ extern "C" int sph_set_stage_cap(sph_ctx* ctx, int cap) {
     return SPH_OK;
 }
 
+extern "C" int sph_set_entry_ring(sph_ctx* ctx, int mode) {
+    if (!ctx || (mode != SPH_RING_AUTO && mode != SPH_RING_THREAD && mode != SPH_RING_CHUNK)) return SPH_ERR_ARG;
+    ctx->entry_ring = mode;
+    return SPH_OK;
+}
+
 static cudaEvent_t pool_get(sph_ctx* ctx) {
     if (!ctx->pool.empty()) {
         cudaEvent_t e = ctx->pool.back();

@@ -190,9 +190,17 @@ __device__ __forceinline__ void euler_update32(const float* vi, float dri, float
 }
 
 // ------------------------------------------------- planned passes (tile plans)
-// Entry ring of a planned pass: slots of 32 bytes per thread (see euler_tile_g).
-constexpr int kEntryRing = 4;
-constexpr size_t kEntryRingBytes = (size_t)kEntryRing * kTileRows * 32;
+// Entry ring of a planned pass (see euler_tile_g), after the stage: either kEntryChunks
+// chunks of one step of the tile's sliced entries (kTileRows entries of 32 bytes, 4 KB),
+// then a full and an empty mbarrier per chunk; or, per thread, kEntryChunks 32-byte slots
+// (the same 16 KB).
+constexpr int kEntryChunks = 4;
+constexpr uint32_t kChunkBytes = kTileRows * 32;
+constexpr size_t kEntryRingBytes = (size_t)kEntryChunks * kChunkBytes + 2 * kEntryChunks * 8;
+// The chunk ring's launches of at least this many waves of blocks (SPH_RING_AUTO).
+constexpr int kChunkRingWaves = 2;
+// Polls of a bounded mbarrier wait before a block gives up (FLAG_TIMEOUT).
+constexpr uint32_t kEuWaitPolls = 1u << 22;
 
 struct GeoArgsE {
     const int32_t* tile_m;
@@ -200,6 +208,9 @@ struct GeoArgsE {
     const int32_t* uidx;
     const float* geo;   // 8 floats per entry
     int mcap;
+    uint32_t test_polls;   // > 0 (sph_set_wait_test): no copy is issued, the waits run out after this many polls
+    int chunk_ring;        // 1: the TMA chunk ring, 0: the per-thread cp.async ring (SPH_RING_*; the
+                           // launch picks the kernel instantiation by it)
 };
 
 // One pair of a planned pass from its entry and the neighbour's (v_j, drho_j).
@@ -250,12 +261,12 @@ __device__ __forceinline__ void euler_pair_geo(const F8& e, float4 dj, const flo
 // whose neighbour indices are case-local.  The tile's neighbour (v_j, drho_j) are
 // staged in sp (A.mcap float4); a tile with more distinct neighbours reads them
 // from Rin.  The block must be kTileRows threads.
-template <int DIM, int MODE, int OUT>
+template <int DIM, int MODE, int OUT, bool CHUNK>
 __device__ __forceinline__ void euler_tile_g(const float* __restrict__ Rin, float* __restrict__ Rout,
                                              const int64_t* __restrict__ row_ptr, int64_t row_base, int64_t rp0,
                                              int64_t n, int64_t tile, const EulerK<float>& K, const GeoArgsE& A,
                                              float4* sp, double* __restrict__ rate_mass,
-                                             double* __restrict__ rate_mom) {
+                                             double* __restrict__ rate_mom, int* __restrict__ flags) {
     const int64_t i0 = tile * kTileRows;
     const int64_t i = i0 + threadIdx.x;
     const bool active = i < n;
@@ -264,6 +275,39 @@ __device__ __forceinline__ void euler_tile_g(const float* __restrict__ Rin, floa
     const int len = active ? (int)(row_ptr[ii + 1] - row_ptr[ii]) : 0;
     const int m = A.tile_m[tile];
     const int64_t so = A.tile_so[tile];
+    const int width = CHUNK ? (int)((A.tile_so[tile + 1] - so) / kTileRows) : 0;
+    // Chunk ring (CHUNK): the tile's entries arrive by TMA bulk copies, step k of the
+    // sliced layout (entry k of all kTileRows rows) being one contiguous 4 KB chunk.  Thread 0
+    // keeps kEntryChunks chunks in flight in a ring after the stage, each completing on its
+    // full mbarrier, and refills a slot once all the block's threads have read it (its empty
+    // mbarrier, kTileRows arrivals).  The first chunks are requested before the neighbours
+    // are staged.  Every wait is bounded; a block whose wait runs out sets FLAG_TIMEOUT, waits
+    // (bounded) for the copies it issued and leaves.  A.test_polls > 0: nothing is copied
+    // and the waits run out.  Thread ring (otherwise): each thread streams its own entries
+    // through kEntryChunks 32-byte slots, kEntryChunks - 1 entries ahead with cp.async, and
+    // refills a slot once it has evaluated the pair that read it: no thread waits for
+    // another, the shorter chain when one wave of blocks is the whole pass.
+    float4* ring = sp + A.mcap;
+    uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)kEntryChunks * 2 * kTileRows);
+    uint64_t* empty = full + kEntryChunks;
+    const float* g0 = A.geo + 8 * so;
+    const bool test_wait = A.test_polls > 0;
+    const uint32_t polls = test_wait ? A.test_polls : kEuWaitPolls;
+    int issued = 0;                                      // chunks thread 0 has requested
+    if (CHUNK && threadIdx.x == 0) {
+        for (int c = 0; c < kEntryChunks; ++c) {
+            mbar_init(&full[c], 1);
+            mbar_init(&empty[c], kTileRows);
+        }
+        mbar_fence_init();
+        if (!test_wait) {
+            for (; issued < kEntryChunks && issued < width; ++issued) {
+                mbar_arrive_expect_tx(&full[issued], kChunkBytes);
+                tma_load_1d(ring + (size_t)issued * 2 * kTileRows, g0 + (int64_t)8 * issued * kTileRows, kChunkBytes,
+                            &full[issued]);
+            }
+        }
+    }
     const float4 own = __ldg(reinterpret_cast<const float4*>(Rin + kRecWords * ii) + 3);
     const bool staged = m <= A.mcap;
     if (staged) {
@@ -281,29 +325,8 @@ __device__ __forceinline__ void euler_tile_g(const float* __restrict__ Rin, floa
     am.init();
 #pragma unroll
     for (int a = 0; a < DIM; ++a) ap[a].init();
-    const float* g = A.geo + 8 * (so + threadIdx.x);
     const int smax = max(m - 1, 0);
-    // each thread streams its own entries through a ring of kEntryRing 32-byte slots in
-    // shared memory (after the staged neighbours), kEntryRing - 1 entries ahead with
-    // cp.async: a steady stream of loads in flight without holding them in registers.
-    // A slot is refilled only after the pair that read it was evaluated.
-    float4* ring = sp + A.mcap + 2 * threadIdx.x;
-    auto issue = [&](int k) {
-        float4* d = ring + (k % kEntryRing) * (2 * kTileRows);
-        const float* src = g + (int64_t)8 * k * kTileRows;
-        cp_async16(d, src);
-        cp_async16(d + 1, src + 4);
-    };
-#pragma unroll
-    for (int k = 0; k < kEntryRing - 1; ++k) {
-        if (k < len) issue(k);
-        cp_async_commit();
-    }
-    for (int k = 0; k < len; ++k) {
-        if (k + kEntryRing - 1 < len) issue(k + kEntryRing - 1);
-        cp_async_commit();
-        cp_async_wait_group<kEntryRing - 1>();
-        const float4* d = ring + (k % kEntryRing) * (2 * kTileRows);
+    auto pair = [&](const float4* d) {
         const float4 lo = d[0], hi = d[1];
         F8 e;
         e.v[0] = lo.x; e.v[1] = lo.y; e.v[2] = lo.z; e.v[3] = lo.w;
@@ -316,6 +339,57 @@ __device__ __forceinline__ void euler_tile_g(const float* __restrict__ Rin, floa
             euler_pair_geo<DIM, MODE>(e, __ldg(reinterpret_cast<const float4*>(Rin + kRecWords * j) + 3), vi, dri,
                                       K, am, ap);
         }
+    };
+    bool late = false;
+    if constexpr (!CHUNK) {
+        float4* own_ring = ring + 2 * threadIdx.x;
+        const float* g = g0 + 8 * (int64_t)threadIdx.x;
+        auto issue = [&](int k) {
+            float4* d = own_ring + (k % kEntryChunks) * (2 * kTileRows);
+            const float* src = g + (int64_t)8 * k * kTileRows;
+            cp_async16(d, src);
+            cp_async16(d + 1, src + 4);
+        };
+#pragma unroll
+        for (int k = 0; k < kEntryChunks - 1; ++k) {
+            if (k < len) issue(k);
+            cp_async_commit();
+        }
+        for (int k = 0; k < len; ++k) {
+            if (k + kEntryChunks - 1 < len) issue(k + kEntryChunks - 1);
+            cp_async_commit();
+            cp_async_wait_group<kEntryChunks - 1>();
+            pair(own_ring + (k % kEntryChunks) * (2 * kTileRows));
+        }
+    }
+    for (int k = 0; k < width; ++k) {
+        const int slot = k % kEntryChunks;
+        const uint32_t par = (uint32_t)(k / kEntryChunks) & 1u;
+        if (!mbar_wait_bounded(&full[slot], par, polls)) {
+            late = true;
+            break;
+        }
+        if (k < len) pair(ring + (size_t)slot * 2 * kTileRows + 2 * threadIdx.x);
+        mbar_arrive(&empty[slot]);
+        if (threadIdx.x == 0 && k + kEntryChunks < width) {
+            if (!mbar_wait_bounded(&empty[slot], par, polls)) {
+                late = true;
+                break;
+            }
+            mbar_arrive_expect_tx(&full[slot], kChunkBytes);
+            tma_load_1d(ring + (size_t)slot * 2 * kTileRows, g0 + (int64_t)8 * (k + kEntryChunks) * kTileRows,
+                        kChunkBytes, &full[slot]);
+            ++issued;
+        }
+    }
+    if (CHUNK && __syncthreads_or(late)) {             // block-uniform from here
+        if (threadIdx.x == 0) {
+            atomicExch(&flags[FLAG_TIMEOUT], 1);
+            // the copies issued and perhaps in flight: the last one of each slot
+            for (int c = max(issued - kEntryChunks, 0); c < issued; ++c)
+                mbar_wait_bounded(&full[c % kEntryChunks], (uint32_t)(c / kEntryChunks) & 1u, kEuWaitPolls);
+        }
+        return;
     }
     if (!active) return;
     float rm = am.value(), rp[DIM];

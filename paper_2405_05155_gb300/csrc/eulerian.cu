@@ -194,12 +194,12 @@ __global__ void __launch_bounds__(kTileRows) k_eu_geo(const double* __restrict__
     }
 }
 
-template <int DIM, int MODE, int OUT>
+template <int DIM, int MODE, int OUT, bool CHUNK>
 __global__ void __launch_bounds__(kTileRows, 6) k_euler32g(const float* __restrict__ Rin, float* __restrict__ Rout,
                                                            const int64_t* __restrict__ row_ptr, int64_t n,
                                                            EulerK<float> K, GeoArgsE A,
                                                            double* __restrict__ rate_mass,
-                                                           double* __restrict__ rate_mom) {
+                                                           double* __restrict__ rate_mom, int* __restrict__ flags) {
     extern __shared__ __align__(16) unsigned char eu_smem[];
     // launched as a programmatic dependent of the previous pass: its blocks are scheduled
     // while that pass finishes and read nothing before it has completed
@@ -208,8 +208,8 @@ __global__ void __launch_bounds__(kTileRows, 6) k_euler32g(const float* __restri
     // the momentum pass of the two-pass step walks the tiles in reverse, the continuity
     // pass forwards: each starts on the pair entries the previous one read last (in L2)
     const int64_t tile = MODE == WANT_MOM ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
-    euler_tile_g<DIM, MODE, OUT>(Rin, Rout, row_ptr, 0, 0, n, tile, K, A, reinterpret_cast<float4*>(eu_smem),
-                                 rate_mass, rate_mom);
+    euler_tile_g<DIM, MODE, OUT, CHUNK>(Rin, Rout, row_ptr, 0, 0, n, tile, K, A,
+                                        reinterpret_cast<float4*>(eu_smem), rate_mass, rate_mom, flags);
 }
 
 // ---------------------------------------------------------------- pack / unpack
@@ -356,20 +356,22 @@ EuPlan eu_plan(const sph_ctx* ctx, const sph_eulerian_state* st, int64_t n) {
     if (!t.on) return t;
     TilePlan tp = tile_plan_view(st->plan, n, st->plan_nnz);
     int mc = stage_mcap(st->plan_maxm, 1, ctx->stage_cap);
-    t.A = GeoArgsE{tp.tile_m, tp.tile_so, tp.uidx, reinterpret_cast<const float*>(tp.geo), mc};
+    t.A = GeoArgsE{tp.tile_m, tp.tile_so, tp.uidx, reinterpret_cast<const float*>(tp.geo), mc, ctx->wait_test_polls};
+    const int64_t waves = kChunkRingWaves * (int64_t)6 * (ctx->num_sms > 0 ? ctx->num_sms : 1);
+    t.A.chunk_ring = ctx->entry_ring == SPH_RING_CHUNK || (ctx->entry_ring == SPH_RING_AUTO && tp.ntiles >= waves);
     t.bytes = (size_t)mc * 16 + kEntryRingBytes;
     return t;
 }
 
 template <int DIM>
 void launch32g(int out, int64_t n, const sph_eulerian_state* st, const EulerK<float>& K, const EuPlan& ep,
-               const float* rin, float* rout, double* rm, double* rp, cudaStream_t s) {
+               const float* rin, float* rout, double* rm, double* rp, int* flags, cudaStream_t s) {
     dim3 g((unsigned)((n + kTileRows - 1) / kTileRows)), b(kTileRows);
 #define LG(M, O)                                                                    \
     {                                                                               \
-        auto* f = k_euler32g<DIM, M, O>;                                            \
+        auto* f = ep.A.chunk_ring ? k_euler32g<DIM, M, O, true> : k_euler32g<DIM, M, O, false>; \
         sph_allow_dynamic_smem((const void*)f);                                     \
-        (void)launch_dependent(true, f, g, b, ep.bytes, s, rin, rout, (const int64_t*)st->row_ptr, n, K, ep.A, rm, rp); \
+        (void)launch_dependent(true, f, g, b, ep.bytes, s, rin, rout, (const int64_t*)st->row_ptr, n, K, ep.A, rm, rp, flags); \
     }
     if (out == OUT_RATES) LG(WANT_BOTH, OUT_RATES)
     else if (out == OUT_MOM) LG(WANT_MOM, OUT_MOM)
@@ -378,12 +380,13 @@ void launch32g(int out, int64_t n, const sph_eulerian_state* st, const EulerK<fl
 #undef LG
 }
 
-void dispatch32(const sph_ctx* ctx, int lanes, int out, const sph_eulerian_params* p, const sph_eulerian_state* st,
+void dispatch32(sph_ctx* ctx, int lanes, int out, const sph_eulerian_params* p, const sph_eulerian_state* st,
                 const EulerK<float>& K, const float* rin, float* rout, double* rm, double* rp, cudaStream_t s) {
     EuPlan ep = eu_plan(ctx, st, p->dom.n);
     if (ep.on) {
-        if (p->dom.dim == 2) launch32g<2>(out, p->dom.n, st, K, ep, rin, rout, rm, rp, s);
-        else launch32g<3>(out, p->dom.n, st, K, ep, rin, rout, rm, rp, s);
+        if (ep.A.chunk_ring) ctx->waits_pending = true;     // the chunk ring's bounded waits
+        if (p->dom.dim == 2) launch32g<2>(out, p->dom.n, st, K, ep, rin, rout, rm, rp, ctx->flags, s);
+        else launch32g<3>(out, p->dom.n, st, K, ep, rin, rout, rm, rp, ctx->flags, s);
         return;
     }
     bool per = p->dom.periodic_mask != 0;
@@ -481,7 +484,10 @@ extern "C" int sph_eulerian_unpack(sph_ctx* ctx, const sph_eulerian_params* p, c
     if (p->dom.dim == 2) k_unpack_rec<2><<<grid_for(n, 256), 256, 0, s>>>(st->rec, n, st->drho, st->v);
     else k_unpack_rec<3><<<grid_for(n, 256), 256, 0, s>>>(st->rec, n, st->drho, st->v);
     SPH_LAUNCH_CHECK(ctx);
-    return SPH_OK;
+    // a bounded wait that expired in a planned pass since the last read of the flag
+    if (!ctx->waits_pending) return SPH_OK;
+    ctx->waits_pending = false;
+    return sph_take_timeout(ctx, s);
 }
 
 // Weakly-compressible EOS of Sec. 3.1.1, p = c0^2 (rho - rho0), solved for the stored

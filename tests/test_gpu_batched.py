@@ -25,9 +25,12 @@ def _small_cases():
     return inputs.batched_tgv2d(seed=3, ncases=7, scale=0.06)
 
 
-@pytest.mark.parametrize("tiles", [True, False])
-def test_batched_matches_single_case_runs(ctx, tiles):
-    # planned form (every case with a tile plan) or the persistent per-pair form
+@pytest.mark.parametrize("tiles,ring", [(True, api.SPH_RING_THREAD), (True, api.SPH_RING_CHUNK), (False, None)])
+def test_batched_matches_single_case_runs(ctx, tiles, ring):
+    # planned form (every case with a tile plan; the entries through the thread ring or the
+    # TMA chunk ring, the same in both runs) or the persistent per-pair form
+    if ring is not None:
+        ctx.set_entry_ring(ring)
     cases = _small_cases()
     for lanes in (1, 4):
         ctx.set_lanes(api.SPH_PASS_EULERIAN, lanes)
@@ -50,6 +53,7 @@ def test_batched_matches_single_case_runs(ctx, tiles):
                 assert rel_l2(host(got).astype(np.float64), host(single).astype(np.float64)) < 1e-6, c
     ctx.set_lanes(api.SPH_PASS_EULERIAN, 4)
     ctx.set_lanes(api.SPH_PASS_BATCHED, 4)
+    ctx.set_entry_ring(api.SPH_RING_AUTO)
 
 
 @pytest.mark.parametrize("tiles", [True, False])

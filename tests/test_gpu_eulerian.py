@@ -172,7 +172,8 @@ def test_launch_shapes_agree(ctx, lanes):
 def test_plan_geometry_and_forms(ctx):
     # the plan's pair entries against float64 numpy on the same lists (G, viscous factor,
     # normal, slot), and the planned pass with its neighbours staged or read from global
-    # memory (stage capacity 16): identical arithmetic, identical results
+    # memory (stage capacity 16), its entries through the thread ring or the TMA chunk
+    # ring: identical arithmetic, identical results
     case = inputs.tgv3d(n=12, kappa=1.6)
     s = _setup(ctx, case, jitter=0.2, seed=5)
     n = s["pos"].shape[1]
@@ -212,16 +213,20 @@ def test_plan_geometry_and_forms(ctx):
         assert np.allclose(ent[:, 3], vis[order], rtol=1e-6, atol=1e-6 * np.abs(vis).max())
         assert np.allclose(ent[:, 4:7].T, (-dx / rr)[:, order], rtol=1e-6, atol=1e-7)
     ref = None
-    for cap in (0, 16):
-        ctx.set_stage_cap(cap)
-        sim = _sim(ctx, s, case, api.SPH_FP32_KAHAN)
-        sim.step(3)
-        got = sim.rec.clone()
-        if ref is None:
-            ref = got
-        else:
-            assert torch.equal(got, ref)
+    for ring in (api.SPH_RING_THREAD, api.SPH_RING_CHUNK):
+        ctx.set_entry_ring(ring)
+        for cap in (0, 16):
+            ctx.set_stage_cap(cap)
+            sim = _sim(ctx, s, case, api.SPH_FP32_KAHAN)
+            sim.step(3)
+            sim.unpack()                           # also reads the chunk ring's timeout flag
+            got = sim.rec.clone()
+            if ref is None:
+                ref = got
+            else:
+                assert torch.equal(got, ref), (ring, cap)
     ctx.set_stage_cap(0)
+    ctx.set_entry_ring(api.SPH_RING_AUTO)
 
 
 def test_conservation_on_gpu(ctx):

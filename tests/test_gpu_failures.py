@@ -3,10 +3,11 @@
 A bounded device wait that runs out must surface as SPH_ERR_TIMEOUT on the host, with
 the context still usable afterwards; a non-finite value met by a float64 reduction must
 surface as SPH_ERR_NONFINITE, and a non-finite position as SPH_ERR_ARG.  The timeout is
-provoked with the library's wait test (sph_set_wait_test): the bulk-copy deformation
-pass then issues no copy, so its bounded wait polls an mbarrier phase that nothing
-completes, runs out after a few hundred polls, and every block leaves through the
-timeout branch with nothing in flight.
+provoked with the library's wait test (sph_set_wait_test): the TMA copies of the
+bulk-copy and geometry-form deformation passes and of the planned Eulerian passes are then
+not issued, so their bounded waits poll mbarrier phases that nothing completes, run out
+after a few hundred polls, and every block leaves through the timeout branch with nothing
+in flight.
 """
 import numpy as np
 import pytest
@@ -25,6 +26,7 @@ def ctx():
     yield c
     c.set_wait_test(0)
     c.set_tile_pipeline(api.SPH_PIPE_GEOM)
+    c.set_entry_ring(api.SPH_RING_AUTO)
     c.close()
 
 
@@ -91,6 +93,46 @@ def test_geometry_form_slot_copy_timeout_is_reported(ctx):
     again.unpack()
     torch.cuda.synchronize()
     assert torch.isfinite(again.v).all() and torch.equal(again.v, ref.v)
+
+
+def _tgv_sim(ctx):
+    c = inputs.tgv3d(n=12, kappa=1.6)
+    d = c["domain"]
+    pos, order = sorted_by_cells(c["pos"], d)
+    pos = cuda(pos)
+    vol = cuda(c["vol"][order])
+    rp, col = api.build_neighbors(ctx, d, pos)
+    B, _, _ = api.kgc(ctx, d, pos, vol, rp, col)
+    drho = api.density_from_pressure(ctx, d, c["c0"], cuda(c["p"][order]))
+    return api.Eulerian(ctx, d, pos, vol, B, rp, col, drho, c["v"][:, order], c["dt"], c["rho0"], c["c0"], c["mu"],
+                        precision=api.SPH_FP32_KAHAN, tiles=True)
+
+
+def test_eulerian_entry_ring_timeout_is_reported(ctx):
+    # the planned Eulerian passes take their pair entries through a ring of TMA bulk copies
+    # with bounded waits: under the wait test nothing is copied, the waits run out, the
+    # unpack reports SPH_ERR_TIMEOUT, and the same context then runs as before
+    ctx.set_entry_ring(api.SPH_RING_CHUNK)
+    try:
+        ref = _tgv_sim(ctx)
+        ref.step(2)
+        ref.unpack()
+        sim = _tgv_sim(ctx)
+        ctx.set_wait_test(256)
+        try:
+            sim.step(1)
+            with pytest.raises(L.SphError) as e:
+                sim.unpack()
+            assert e.value.status == L.SPH_ERR_TIMEOUT
+        finally:
+            ctx.set_wait_test(0)
+        again = _tgv_sim(ctx)
+        again.step(2)
+        again.unpack()
+        torch.cuda.synchronize()
+        assert torch.isfinite(again.v).all() and torch.equal(again.v, ref.v) and torch.equal(again.drho, ref.drho)
+    finally:
+        ctx.set_entry_ring(api.SPH_RING_AUTO)
 
 
 def test_wait_test_argument_checks(ctx):
