@@ -519,7 +519,8 @@ int sph_tlsph_store32(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph
  * the step allows: u is copied in by a copy engine on a second stream of the context
  * while the momentum pass runs and v copied back (from a device buffer of the context)
  * while the deformation pass runs; the stress factors are formed by the kernel that
- * reads H.  u and v must be pinned (sph_host_alloc) or device memory.  Everything is enqueued on `stream` (which waits for the
+ * reads H, and the geometry form of the deformation pass (the default on a tile plan)
+ * writes H and u back itself, beside the device records.  u and v must be pinned (sph_host_alloc) or device memory.  Everything is enqueued on `stream` (which waits for the
  * second stream before returning); u, v, H must not be touched until it completes.
  * Requires precision SPH_FP32_KAHAN and the float32 records (one sph_tlsph_pack first);
  * SPH_ERR_ARG otherwise. */

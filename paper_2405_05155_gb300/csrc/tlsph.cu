@@ -565,13 +565,15 @@ __global__ void __launch_bounds__(256, 4) k_tl_mom32(const float* __restrict__ R
 
 // Deformation-rate epilogue shared by both forms of the pass: F_i += dt L B0_i
 // (F = I on clamped particles), x_i += dt v_i and the next step's M_i = P(F_i) B0_i^T.
-// hold/uold: the row's current H and u when already loaded (else read here).
+// hold/uold: the row's current H and u when already loaded (else read here).  Hx/ux: a
+// second copy of the new H and u (the caller's mapped host arrays), written beside H, u.
 template <int DIM, int OUT>
 __device__ __forceinline__ void defo_finish(const float* Lt, const float* b0, bool fx, const float* vi, int64_t i,
                                             int64_t n, const TLK<float>& K, float* __restrict__ RM,
                                             float* __restrict__ H, float* __restrict__ u,
                                             double* __restrict__ dFdt, const float* hold = nullptr,
-                                            const float* uold = nullptr, const F8* me = nullptr) {
+                                            const float* uold = nullptr, const F8* me = nullptr,
+                                            float* __restrict__ Hx = nullptr, float* __restrict__ ux = nullptr) {
     float Fd[DIM * DIM];
     times_b0<DIM, float>(Lt, b0, Fd);
     if (OUT == OUT_RATES) {
@@ -583,9 +585,14 @@ __device__ __forceinline__ void defo_finish(const float* Lt, const float* b0, bo
     for (int k = 0; k < DIM * DIM; ++k) {
         h[k] = fx ? 0.0f : (hold ? hold[k] : H[k * n + i]) + K.dt * Fd[k];
         H[k * n + i] = h[k];
+        if (Hx) Hx[k * n + i] = h[k];
     }
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) u[a * n + i] = (uold ? uold[a] : u[a * n + i]) + K.dt * vi[a];
+    for (int a = 0; a < DIM; ++a) {
+        const float ua = (uold ? uold[a] : u[a * n + i]) + K.dt * vi[a];
+        u[a * n + i] = ua;
+        if (ux) ux[a * n + i] = ua;
+    }
     stress_factor<DIM, float>(h, b0, K, m);
     store_M<DIM>(RM, i, m, me);
 }
@@ -1462,11 +1469,13 @@ __global__ void __launch_bounds__(kTileRows, 8) k_tl_mom32r(const float* __restr
 // GEOM: the pair geometry from the staged records (both halves of RD: position code and
 // velocity) and the sliced slot section, instead of the 16-byte entries: 2 bytes of the
 // plan per pair instead of 16, for about 30 more instructions per pair.
-template <int DIM, int OUT, bool BULK, bool GEOM = false, bool PER = false>
+// HX: the new H and u are also written to Hx, ux (mapped host memory of a caller that keeps
+// the state on the host), so that the write-back overlaps the pass.
+template <int DIM, int OUT, bool BULK, bool GEOM = false, bool PER = false, bool HX = false>
 __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_defo32g(
     const float* __restrict__ RD, float* __restrict__ RM, const int64_t* __restrict__ row_ptr, int64_t n,
     TLK<float> K, GeoArgs A, const float* __restrict__ B0, float* __restrict__ H, float* __restrict__ u,
-    double* __restrict__ dFdt, int* __restrict__ flags) {
+    double* __restrict__ dFdt, int* __restrict__ flags, float* __restrict__ Hx, float* __restrict__ ux) {
     constexpr int NS = DIM == 2 ? 3 : 6;
     extern __shared__ __align__(16) unsigned char tl_smem[];
     float4* sp = reinterpret_cast<float4*>(tl_smem);
@@ -1711,7 +1720,8 @@ __global__ void __launch_bounds__(kTileRows, BULK ? 3 : (GEOM ? 8 : 6)) k_tl_def
     // read live through the loop costs registers there)
     const F8 own = ldg8(RD + 8 * i);
     if (GEOM) own_row();
-    defo_finish<DIM, OUT>(Lt, b0, (bi & kFixedBit) != 0, vi, i, n, K, RM, H, u, dFdt, hold, uold, &own);
+    defo_finish<DIM, OUT>(Lt, b0, (bi & kFixedBit) != 0, vi, i, n, K, RM, H, u, dFdt, hold, uold, &own,
+                          HX ? Hx : nullptr, HX ? ux : nullptr);
 }
 
 // ---------------------------------------------------------------- pack / unpack
@@ -2265,9 +2275,12 @@ void tl32_passes(int which, int out, int64_t n, const sph_tlsph_state* st, const
     }
 }
 
+// hx/ux (a step's deformation pass, OUT_STEP): the caller's host copies of H and u, written
+// by the geometry form of the pass itself; returns whether the pass wrote them.
 template <int DIM>
-void tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K,
-                    const TlPlan& tp, double* r1, double* r2, cudaStream_t s, bool dependent = true) {
+bool tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K,
+                    const TlPlan& tp, double* r1, double* r2, cudaStream_t s, bool dependent = true,
+                    float* hx = nullptr, float* ux = nullptr) {
     dim3 g((unsigned)((n + kTileRows - 1) / kTileRows)), b(kTileRows), gp((unsigned)tp.grid);
     if (which == 0) {
         if (tp.pipe_mom) {
@@ -2300,12 +2313,15 @@ void tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph
                                                        : k_tl_defo32g<DIM, OUT_STEP, true>)
                                    : (out == OUT_RATES ? k_tl_defo32g<DIM, OUT_RATES, false>
                                                        : k_tl_defo32g<DIM, OUT_STEP, false>);
+            const bool host = tp.geom_defo && out == OUT_STEP && hx && ux;
             if (tp.geom_defo) {
                 if (K.periodic)
                     f = out == OUT_RATES ? k_tl_defo32g<DIM, OUT_RATES, false, true, true>
+                        : host           ? k_tl_defo32g<DIM, OUT_STEP, false, true, true, true>
                                          : k_tl_defo32g<DIM, OUT_STEP, false, true, true>;
                 else
                     f = out == OUT_RATES ? k_tl_defo32g<DIM, OUT_RATES, false, true, false>
+                        : host           ? k_tl_defo32g<DIM, OUT_STEP, false, true, false, true>
                                          : k_tl_defo32g<DIM, OUT_STEP, false, true, false>;
             }
             if (tp.bulk_defo || tp.geom_defo) ctx->waits_pending = true;
@@ -2313,12 +2329,15 @@ void tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph
             if (tp.geom_defo)
                 (void)launch_dependent(dependent, f, g, b, tp.defo_bytes, s, (const float*)st->rd, st->rm,
                                        (const int64_t*)st->row_ptr, n, K, tp.defo, (const float*)st->B32, st->H32,
-                                       st->u32, out == OUT_RATES ? r2 : nullptr, ctx->flags);
+                                       st->u32, out == OUT_RATES ? r2 : nullptr, ctx->flags, host ? hx : nullptr,
+                                       host ? ux : nullptr);
             else
                 f<<<g, b, tp.defo_bytes, s>>>(st->rd, st->rm, st->row_ptr, n, K, tp.defo, st->B32, st->H32, st->u32,
-                                              out == OUT_RATES ? r2 : nullptr, ctx->flags);
+                                              out == OUT_RATES ? r2 : nullptr, ctx->flags, nullptr, nullptr);
+            return host;
         }
     }
+    return false;
 }
 
 template <int DIM, bool PER>
@@ -2335,11 +2354,13 @@ void tl32_lanes(int lanes, int which, int out, int64_t n, const sph_tlsph_state*
 // One float32 pass: on the tile plan when the state has one, else the gather form
 // with the context's lanes per row.
 template <int DIM>
-void tl32(sph_ctx* ctx, int lanes, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K,
-          const TlPlan& tp, double* r1, double* r2, cudaStream_t s, bool dependent = true) {
-    if (tp.on) tl32_plan_pass<DIM>(ctx, which, out, n, st, K, tp, r1, r2, s, dependent);
-    else if (K.periodic) tl32_lanes<DIM, true>(lanes, which, out, n, st, K, r1, r2, s);
+bool tl32(sph_ctx* ctx, int lanes, int which, int out, int64_t n, const sph_tlsph_state* st, const TLK<float>& K,
+          const TlPlan& tp, double* r1, double* r2, cudaStream_t s, bool dependent = true, float* hx = nullptr,
+          float* ux = nullptr) {
+    if (tp.on) return tl32_plan_pass<DIM>(ctx, which, out, n, st, K, tp, r1, r2, s, dependent, hx, ux);
+    if (K.periodic) tl32_lanes<DIM, true>(lanes, which, out, n, st, K, r1, r2, s);
     else tl32_lanes<DIM, false>(lanes, which, out, n, st, K, r1, r2, s);
+    return false;
 }
 
 bool fp32_ready(const sph_tlsph_state* st) { return st->rd && st->rm && st->H32 && st->u32 && st->B32; }
@@ -2572,9 +2593,10 @@ int tl_step_host32(sph_ctx* ctx, const sph_tlsph_params* p, const sph_tlsph_stat
         SPH_CUDA(ctx, cudaEventRecord(v_out, s2));
         SPH_CUDA(ctx, cudaStreamWaitEvent(s, u_in, 0));
         t = sph_timer_begin(ctx, SPH_TIMER_TL_DEFORM, s);
-        tl32<DIM>(ctx, lanes, 1, OUT_STEP, n, st, K, ts, nullptr, nullptr, s, false);
+        // the geometry form writes H and u back itself, the write-back overlapping the pass
+        const bool direct = tl32<DIM>(ctx, lanes, 1, OUT_STEP, n, st, K, ts, nullptr, nullptr, s, false, H, u);
         sph_timer_end(ctx, t, s);
-        k_tl_store32_hu<DIM><<<g, 256, 0, s>>>(st->H32, st->u32, n, H, u);
+        if (!direct) k_tl_store32_hu<DIM><<<g, 256, 0, s>>>(st->H32, st->u32, n, H, u);
         // the next step's read of v (and the caller's use of it) after its write-back
         SPH_CUDA(ctx, cudaStreamWaitEvent(s, v_out, 0));
     }
