@@ -1117,6 +1117,8 @@ def run_gpu(args):
 
     workloads = {}
     if not args.headline_only:
+        # the other rows with the whole L2: the TL passes' persisting set-aside given back
+        ctx.set_l2_persist(False)
         peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
         bf16 = peaks.get("bf16_tflops", 1900.0)
         for name, fn in (("tgv3d_128", lambda: _bench_tgv3d(api, inputs, ctx, args.other_steps, peak)),

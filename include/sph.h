@@ -138,6 +138,19 @@ int sph_set_stage_cap(sph_ctx* ctx, int cap);
 #define SPH_RING_THREAD 1
 #define SPH_RING_CHUNK  2
 int sph_set_entry_ring(sph_ctx* ctx, int mode);
+/* L2 residency of the planned TL passes' gathered records (on = 1, the default): the
+ * geometry-form passes launch with an access-policy window that marks the float32 records
+ * they gather (rm in the momentum pass, rd in the deformation pass) persisting in L2, so
+ * that they stay there from one pass and step to the next.  On first use the context
+ * reserves a persisting set-aside of L2 (cudaLimitPersistingL2CacheSize: the records'
+ * bytes, at most the device's maximum; with more records than that a matching fraction of
+ * the accesses is marked) for the process's CUDA context on the device, which lasts until
+ * sph_set_l2_persist(ctx, 0) or sph_destroy: both synchronise the device, turn the lines
+ * marked persisting back to normal and set the set-aside to 0.  A launch-shape setting:
+ * results do not depend on it.  SPH_ERR_ARG for on other than 0 or 1; SPH_ERR_CUDA if the
+ * device synchronisation fails.  If the runtime refuses the set-aside the passes launch
+ * without windows and the setting reads as off. */
+int sph_set_l2_persist(sph_ctx* ctx, int on);
 /* Planned TL passes, how pair entries reach a block (a launch-shape setting:
  * results do not depend on it, apart from the rounding SPH_PIPE_GEOM notes):
  *   SPH_PIPE_STREAM     one block per tile, entries streamed from global memory;

@@ -148,6 +148,7 @@ _SIGNATURES = {
     "sph_tlsph_plan": (ctypes.c_int, [c_vp, _P(TLParams), _P(TLState), c_vp]),
     "sph_set_stage_cap": (ctypes.c_int, [c_vp, ctypes.c_int]),
     "sph_set_entry_ring": (ctypes.c_int, [c_vp, ctypes.c_int]),
+    "sph_set_l2_persist": (ctypes.c_int, [c_vp, ctypes.c_int]),
     "sph_set_relax_skin": (ctypes.c_int, [c_vp, ctypes.c_double]),
     "sph_compressible_rates": (ctypes.c_int, [c_vp, _P(CompressibleParams), _P(CompressibleState), c_vp, c_vp,
                                               c_vp, c_vp]),

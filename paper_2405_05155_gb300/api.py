@@ -96,6 +96,11 @@ class Context:
         SPH_RING_THREAD or SPH_RING_CHUNK (results do not depend on it)."""
         L.check("sph_set_entry_ring", self.lib.sph_set_entry_ring(self.h, int(mode)), self.h)
 
+    def set_l2_persist(self, on):
+        """Mark the records the planned TL passes gather persisting in L2 (default on); off
+        gives the context's L2 set-aside back (synchronises the device)."""
+        L.check("sph_set_l2_persist", self.lib.sph_set_l2_persist(self.h, 1 if on else 0), self.h)
+
     def set_relax_skin(self, skin_over_h):
         """Skin of the float32 relaxation list in units of h (0: a cell sweep every step)."""
         L.check("sph_set_relax_skin", self.lib.sph_set_relax_skin(self.h, float(skin_over_h)), self.h)

@@ -48,6 +48,10 @@ struct sph_ctx {
     bool waits_pending = false;    // a kernel with bounded waits ran since the timeout flag was read
     uint32_t wait_test_polls = 0;  // failure-detection test: bounded waits on a phase nothing completes
     double relax_skin = 0.2;       // float32 relaxation: list skin / h (0: a cell sweep every step)
+    // planned TL passes: their gathered records marked persisting in L2 (sph_set_l2_persist)
+    int l2_persist = 1;
+    size_t l2_setaside = 0;        // the persisting set-aside this context asked for (0: none)
+    size_t l2_max_window = 0;      // cudaDevAttrMaxAccessPolicyWindowSize
     // batched Eulerian step: launch shape, captured graph and the case table it was made for
     int batch_block = 256;
     cudaGraphExec_t batch_graph = nullptr;
@@ -89,22 +93,57 @@ enum { FLAG_BAD_INPUT = 0, FLAG_NONFINITE = 1, FLAG_CAPACITY = 2, FLAG_TIMEOUT =
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// An L2 access-policy window of one launch: accesses to [base, base + bytes) are marked
+// persisting with probability hit (the rest streaming); none when bytes == 0.
+struct L2Win {
+    const void* base = nullptr;
+    size_t bytes = 0;
+    float hit = 0.0f;
+};
+
+// The window for a buffer of `bytes` at `base` that a pass gathers from, `total` the bytes
+// of all buffers given windows between passes: reserves the context's persisting set-aside
+// (cudaLimitPersistingL2CacheSize, up to the device's maximum) on first use and scales hit so
+// that about the set-aside persists.  An empty window when the setting is off or the runtime
+// refuses it.
+L2Win sph_l2_window(sph_ctx* ctx, const void* base, size_t bytes, size_t total);
+
 // Launch with the programmatic-serialization attribute (see grid_dependency_wait), or
-// without it (dependent = false: an ordinary launch, e.g. after a cross-stream event wait).
+// without it (dependent = false: an ordinary launch, e.g. after a cross-stream event wait),
+// and with the access-policy window w when it is not empty.
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_dependent(bool dependent, void (*f)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                                    cudaStream_t s, Args... args) {
+inline cudaError_t launch_dependent_win(bool dependent, const L2Win& w, void (*f)(KArgs...), dim3 grid, dim3 block,
+                                        size_t smem, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute at[2];
+    unsigned na = 0;
+    if (dependent) {
+        at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    if (w.bytes) {
+        at[na].id = cudaLaunchAttributeAccessPolicyWindow;
+        at[na].val.accessPolicyWindow.base_ptr = const_cast<void*>(w.base);
+        at[na].val.accessPolicyWindow.num_bytes = w.bytes;
+        at[na].val.accessPolicyWindow.hitRatio = w.hit;
+        at[na].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        at[na].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        ++na;
+    }
     cfg.attrs = at;
-    cfg.numAttrs = dependent ? 1 : 0;
+    cfg.numAttrs = na;
     return cudaLaunchKernelEx(&cfg, f, args...);
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(bool dependent, void (*f)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t s, Args... args) {
+    return launch_dependent_win(dependent, L2Win{}, f, grid, block, smem, s, args...);
 }
 
 // Per-kernel timing: returns a token for sph_timer_end (or -1 when timing is off).

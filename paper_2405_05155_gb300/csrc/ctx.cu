@@ -27,10 +27,65 @@ extern "C" int sph_create(sph_ctx** out, int device) {
     return SPH_OK;
 }
 
+// Gives the persisting L2 set-aside back (and turns the lines marked persisting to normal);
+// the caller has synchronised the device, as the reset is not ordered with any stream.
+static void l2_release(sph_ctx* ctx) {
+    if (!ctx->l2_setaside) return;
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0);
+    cudaGetLastError();
+    ctx->l2_setaside = 0;
+}
+
+L2Win sph_l2_window(sph_ctx* ctx, const void* base, size_t bytes, size_t total) {
+    L2Win w;
+    if (!ctx->l2_persist || !base || !bytes || !total) return w;
+    if (!ctx->l2_setaside) {
+        int most = 0, win = 0;
+        if (cudaDeviceGetAttribute(&most, cudaDevAttrMaxPersistingL2CacheSize, ctx->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&win, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device) != cudaSuccess ||
+            most <= 0 || win <= 0) {
+            cudaGetLastError();
+            ctx->l2_persist = 0;
+            return w;
+        }
+        const size_t want = total < (size_t)most ? total : (size_t)most;
+        size_t got = 0;
+        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess ||
+            cudaDeviceGetLimit(&got, cudaLimitPersistingL2CacheSize) != cudaSuccess || got == 0) {
+            cudaGetLastError();
+            ctx->l2_persist = 0;
+            return w;
+        }
+        ctx->l2_setaside = got;
+        ctx->l2_max_window = (size_t)win;
+    }
+    w.base = base;
+    w.bytes = bytes < ctx->l2_max_window ? bytes : ctx->l2_max_window;
+    const double hit = (double)ctx->l2_setaside / (double)total;
+    w.hit = hit >= 1.0 ? 1.0f : (float)hit;
+    return w;
+}
+
+extern "C" int sph_set_l2_persist(sph_ctx* ctx, int on) {
+    if (!ctx || (on != 0 && on != 1)) return SPH_ERR_ARG;
+    if (!on && ctx->l2_setaside) {
+        cudaSetDevice(ctx->device);
+        if (cudaDeviceSynchronize() != cudaSuccess) {
+            cudaGetLastError();
+            return SPH_ERR_CUDA;
+        }
+        l2_release(ctx);
+    }
+    ctx->l2_persist = on;
+    return SPH_OK;
+}
+
 extern "C" int sph_destroy(sph_ctx* ctx) {
     if (!ctx) return SPH_ERR_ARG;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    l2_release(ctx);
     for (auto& r : ctx->pending) { ctx->pool.push_back(r.start); ctx->pool.push_back(r.stop); }
     ctx->pending.clear();
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);

@@ -2275,6 +2275,11 @@ void tl32_passes(int which, int out, int64_t n, const sph_tlsph_state* st, const
     }
 }
 
+// Bytes of the float32 records: RM (V0, the position code and M: 16 floats in 3D, 8 in 2D)
+// and RD (position code and velocity: 8 floats).
+static inline size_t tl_rm_bytes(int64_t n, int dim) { return (size_t)n * (dim == 3 ? 64 : 32); }
+static inline size_t tl_rd_bytes(int64_t n) { return (size_t)n * 32; }
+
 // hx/ux (a step's deformation pass, OUT_STEP): the caller's host copies of H and u, written
 // by the geometry form of the pass itself; returns whether the pass wrote them.
 template <int DIM>
@@ -2294,7 +2299,9 @@ bool tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph
             // pass's last blocks (a launch error is left to cudaGetLastError)
             auto* f = out == OUT_RATES ? k_tl_mom32r<DIM, OUT_RATES> : k_tl_mom32r<DIM, OUT_STEP>;
             sph_allow_dynamic_smem((const void*)f);
-            (void)launch_dependent(dependent, f, g, b, tp.momr_bytes, s, (const float*)st->rm, st->rd,
+            // the records the pass gathers (RM) kept in L2 between steps
+            const L2Win w = sph_l2_window(ctx, st->rm, tl_rm_bytes(n, DIM), tl_rm_bytes(n, DIM) + tl_rd_bytes(n));
+            (void)launch_dependent_win(dependent, w, f, g, b, tp.momr_bytes, s, (const float*)st->rm, st->rd,
                                    (const int64_t*)st->row_ptr, n, K, tp.momr, out == OUT_RATES ? r1 : nullptr);
         } else {
             auto* f = out == OUT_RATES ? k_tl_mom32g<DIM, OUT_RATES> : k_tl_mom32g<DIM, OUT_STEP>;
@@ -2326,8 +2333,11 @@ bool tl32_plan_pass(sph_ctx* ctx, int which, int out, int64_t n, const sph_tlsph
             }
             if (tp.bulk_defo || tp.geom_defo) ctx->waits_pending = true;
             sph_allow_dynamic_smem((const void*)f);
+            // the records the geometry form gathers (RD) kept in L2 between steps
+            const L2Win w = tp.geom_defo ? sph_l2_window(ctx, st->rd, tl_rd_bytes(n), tl_rm_bytes(n, DIM) + tl_rd_bytes(n))
+                                         : L2Win{};
             if (tp.geom_defo)
-                (void)launch_dependent(dependent, f, g, b, tp.defo_bytes, s, (const float*)st->rd, st->rm,
+                (void)launch_dependent_win(dependent, w, f, g, b, tp.defo_bytes, s, (const float*)st->rd, st->rm,
                                        (const int64_t*)st->row_ptr, n, K, tp.defo, (const float*)st->B32, st->H32,
                                        st->u32, out == OUT_RATES ? r2 : nullptr, ctx->flags, host ? hx : nullptr,
                                        host ? ux : nullptr);

@@ -7,6 +7,7 @@ from helpers import cuda, host, odom, oracle_rows, OracleLists, rel_fp64, rel_l2
 from oracle import kgc as OK
 from oracle import neighbors as ON
 from oracle import tlsph as OT
+from paper_2405_05155_gb300 import _lib
 from paper_2405_05155_gb300 import api, inputs
 
 pytestmark = pytest.mark.gpu
@@ -493,6 +494,31 @@ def test_step_host32_equals_the_composed_calls(ctx, dim):
     finally:
         for h in ha + hb:
             h.close()
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_l2_persistence_changes_nothing(ctx, dim):
+    # the access-policy windows of the geometry-form passes (sph_set_l2_persist, on by
+    # default) change only where the gathered records are cached: 10 steps with and without
+    # them give the same records bit for bit; off gives the set-aside back, and the setting
+    # takes only 0 or 1
+    s = _setup(ctx, dp=0.005) if dim == 3 else _setup(ctx, case=inputs.beam2d(dp=0.002))
+    a = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
+    b = _solid(ctx, s, api.SPH_FP32_KAHAN, OT.NEO_HOOKEAN)
+    try:
+        ctx.set_l2_persist(True)
+        a.step(10)
+        torch.cuda.synchronize()
+        ctx.set_l2_persist(False)
+        b.step(10)
+        torch.cuda.synchronize()
+        for x, y in ((a.rd, b.rd), (a.rm, b.rm), (a.H32, b.H32), (a.u32, b.u32)):
+            assert torch.equal(x, y)
+        assert float(a.rd.abs().max()) > 0.0
+        assert ctx.lib.sph_set_l2_persist(ctx.h, 2) == _lib.SPH_ERR_ARG
+        assert ctx.lib.sph_set_l2_persist(None, 1) == _lib.SPH_ERR_ARG
+    finally:
+        ctx.set_l2_persist(True)
 
 
 @pytest.mark.parametrize("dim", [3, 2])
