@@ -906,6 +906,8 @@ def run_gpu(args):
     from paper_2405_05155_gb300._lib import SPH_TIMER_TL_DEFORM, SPH_TIMER_TL_MOMENTUM, SPH_TIMER_TL_STRESS
     ctx = api.Context(torch.cuda.current_device())
     K, W = args.steps, args.warmup
+    if args.no_l2_persist:
+        ctx.set_l2_persist(False)
     if args.pipe:
         ctx.set_tile_pipeline({"stream": api.SPH_PIPE_STREAM, "persistent": api.SPH_PIPE_PERSISTENT,
                                "bulk": api.SPH_PIPE_BULK, "geom": api.SPH_PIPE_GEOM}[args.pipe])
@@ -1027,10 +1029,11 @@ def run_gpu(args):
     achieved = dominant[1] / (dominant[2] * 1e-3) / 1e9
     # ncu DRAM bytes (read + write) per launch of each planned TL pass on this workload, by
     # pipeline mode (profiles/tl_plate816k_fp32_launches.md: the geometry forms of both
-    # passes; tl_pair_passes_plate816k_full.md: the entry forms of the stream mode)
+    # passes, with their records persisting in L2, caches left as the program leaves them;
+    # tl_pair_passes_plate816k_full.md: the entry forms of the stream mode)
     pipe = args.pipe or "geom"
-    ncu_traffic = {("tl_momentum_pass", "geom"): 167.1e6, ("tl_momentum_pass", "stream"): 446.8e6,
-                   ("tl_deformation_pass", "geom"): 197.1e6, ("tl_deformation_pass", "stream"): 509.1e6}
+    ncu_traffic = {("tl_momentum_pass", "geom"): 143.3e6, ("tl_momentum_pass", "stream"): 446.8e6,
+                   ("tl_deformation_pass", "geom"): 198.0e6, ("tl_deformation_pass", "stream"): 509.1e6}
     traffic = args.traffic if args.traffic is not None else ncu_traffic.get((dominant[0], pipe))
 
     # end to end through the C ABI with the float64 state (x, v, F - I) in host memory:
@@ -1117,8 +1120,6 @@ def run_gpu(args):
 
     workloads = {}
     if not args.headline_only:
-        # the other rows with the whole L2: the TL passes' persisting set-aside given back
-        ctx.set_l2_persist(False)
         peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
         bf16 = peaks.get("bf16_tflops", 1900.0)
         for name, fn in (("tgv3d_128", lambda: _bench_tgv3d(api, inputs, ctx, args.other_steps, peak)),
@@ -1134,6 +1135,10 @@ def run_gpu(args):
                          ("relax_learned_8spheres_dp128", lambda: _bench_relax_learned(api, inputs, ctx))):
             if args.rows and name not in args.rows.split(","):
                 continue
+            # each row with the whole L2: the persisting lines of the rows before turned back
+            # to normal (off, then on again for the rows that gather records)
+            ctx.set_l2_persist(False)
+            ctx.set_l2_persist(not args.no_l2_persist)
             try:
                 workloads[name] = fn()
             except Exception as exc:      # report, do not hide: the headline line still prints
@@ -1237,6 +1242,8 @@ def main():
     ap.add_argument("--kappa", type=float, default=1.6)
     ap.add_argument("--lanes", type=int, default=0, help="lanes per particle of the TL passes (0: tuned)")
     ap.add_argument("--headline-only", action="store_true", help="skip the other rows' workloads")
+    ap.add_argument("--no-l2-persist", action="store_true",
+                    help="launch the TL passes without their L2 access-policy windows (sph_set_l2_persist off)")
     ap.add_argument("--pipe", choices=["stream", "persistent", "bulk", "geom"], default=None,
                     help="how the planned TL passes get their pair entries (default: the context's)")
     ap.add_argument("--rows", default="", help="comma-separated names of the other rows to run (default: all)")
