@@ -47,6 +47,9 @@ def test_status_strings_and_argument_checks(lib):
     assert lib.sph_kernel_eval(0, 3, -1.0, 2.0, 0, None, None, None, 0, None) == _lib.SPH_ERR_ARG
     assert lib.sph_kernel_eval(0, 3, 1.0, 2.5, 0, None, None, None, 0, None) == _lib.SPH_ERR_ARG
     assert lib.sph_cell_order(None, None, None, None, None) == _lib.SPH_ERR_ARG
+    # the context settings refuse a null context or an unknown value before touching it
+    assert lib.sph_set_l2_persist(None, 1) == _lib.SPH_ERR_ARG
+    assert lib.sph_set_entry_ring(None, _lib.SPH_RING_AUTO) == _lib.SPH_ERR_ARG
     d = _lib.SphDomain()
     d.dim, d.n, d.h, d.kappa = 3, 10, 0.1, 2.0
     for k in range(3):
