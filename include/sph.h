@@ -536,7 +536,9 @@ int sph_tlsph_store32(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph
  * writes H and u back itself, beside the device records.  u and v must be pinned (sph_host_alloc) or device memory.  Everything is enqueued on `stream` (which waits for the
  * second stream before returning); u, v, H must not be touched until it completes.
  * Requires precision SPH_FP32_KAHAN and the float32 records (one sph_tlsph_pack first);
- * SPH_ERR_ARG otherwise. */
+ * SPH_ERR_ARG otherwise.  The call does not wait for the device: a bounded wait that
+ * expires in a pass (the geometry form's slot copy) sets the context's timeout flag, which
+ * sph_take_status or the next sph_tlsph_unpack reports (u, v, H are then not valid). */
 int sph_tlsph_step_host32(sph_ctx* ctx, const sph_tlsph_params* prm, const sph_tlsph_state* st,
                           float* u, float* v, float* H, int nsteps, void* stream);
 /* Energies of the float64 state (v, H; after float32 steps call sph_tlsph_unpack
